@@ -1,0 +1,556 @@
+/*
+ * qm_oracle.c -- plain, slow CPU statement of the community-quality metrics of
+ * Chen, Liu & Szymanski, "Parallel Toolkit for Measuring the Quality of Network
+ * Community Structure" (arXiv 1507.05492).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call this file:
+ * it is used by tests/, by the smoke check and by the timed CPU baseline of the
+ * benchmark.  It shares no code, header, table or helper with the CUDA library.
+ *
+ * Every metric is the paper's definition written out literally, term by term,
+ * in long double with Neumaier-compensated summation.  No blocking, fusion or
+ * reordering beyond what the definitions state.
+ *
+ *   Sec. II-A.1  Eq. (1) VI, Eq. (2) NMI           -> oq_compare
+ *   Sec. II-A.2  Eq. (3) F-measure, Eq. (4) NVD    -> oq_compare
+ *   Sec. II-A.3  Eq. (5) RI, Eq. (6) ARI, Eq. (7) JI -> oq_compare (pair counts
+ *                from the contingency table), oq_pairs_bruteforce (Algorithm 4)
+ *   Sec. II-B.1  Eq. (8) modularity Q              -> oq_score
+ *   Sec. II-B.2  Eq. (9) modularity density Qds    -> oq_score
+ *   Sec. II-B.3  six per-community measures        -> oq_score
+ *
+ * Readings where the paper is silent (each also listed in the design doc):
+ *   - log is the natural log (Eq. 1);
+ *   - d_c = 0 for a one-node community (Eq. 9, 0/0);
+ *   - label ids with no member are absent communities, skipped everywhere;
+ *   - conductance = 0 when 2|E_in|+|E_out| = 0 (isolated node);
+ *   - partition-level value of a per-community measure = unweighted mean over
+ *     non-empty communities (Sec. II-B.3 defines them per community only);
+ *   - NMI = 1 when both entropies are 0; ARI = 1 and JI = 1 when their
+ *     denominators are 0 (both partitions trivial in the same way);
+ *   - pairs are unordered (A = |V|(|V|-1)/2, Sec. II-A.3), so the brute force
+ *     of Algorithm 4 counts i<j;
+ *   - the Qds split penalty sums over ordered pairs (c_i, c_j), j != i, as
+ *     written in Eq. (9): each unordered pair contributes to both communities;
+ *   - F-measure sums over the ground truth C (first argument) and maximises
+ *     over the detected C' (second argument), Eq. (3).
+ *
+ * Parity pins (tests/test_oracle_*.py): closed forms (two 5-cliques joined by
+ * one edge; a two-partition worked example), networkx modularity, scikit-learn
+ * pair/information indices, Algorithm 4 brute force, adjacency-matrix and
+ * set-intersection brute force, invariants.  The partition-level means of the
+ * six measures are pinned only against the reading above ("parity unpinned"
+ * against the paper's own toolkit, which prints no values).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+#define OQ_OK 0
+#define OQ_EINVAL 1
+#define OQ_ENOMEM 2
+#define OQ_ECHECK 3 /* an internal identity failed */
+
+/* ---- compensated summation (Neumaier) in long double ---- */
+typedef struct { long double s, c; } oq_sum;
+
+static void sum_add(oq_sum *k, long double x)
+{
+    long double t = k->s + x;
+    if (fabsl(k->s) >= fabsl(x))
+        k->c += (k->s - t) + x;
+    else
+        k->c += (x - t) + k->s;
+    k->s = t;
+}
+
+static long double sum_get(const oq_sum *k) { return k->s + k->c; }
+
+static int cmp_u64(const void *a, const void *b)
+{
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return (x > y) - (x < y);
+}
+
+static int cmp_i32(const void *a, const void *b)
+{
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+/*
+ * Graph validation: the method is defined for an unweighted, undirected graph
+ * (Sec. II-B.1).  A symmetric CSR with no self-loops and no repeated arcs is
+ * required.  Returns OQ_OK or OQ_EINVAL.
+ */
+int oq_validate_graph(const int64_t *row_ptr, const int32_t *col, int64_t n)
+{
+    if (n < 1 || row_ptr[0] != 0)
+        return OQ_EINVAL;
+    for (int64_t u = 0; u < n; u++)
+        if (row_ptr[u + 1] < row_ptr[u])
+            return OQ_EINVAL;
+    int64_t nnz = row_ptr[n];
+    int32_t *sorted = (int32_t *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));
+    if (!sorted)
+        return OQ_ENOMEM;
+    memcpy(sorted, col, (size_t)nnz * sizeof(int32_t));
+    int rc = OQ_OK;
+    for (int64_t u = 0; u < n && rc == OQ_OK; u++) {
+        int64_t b = row_ptr[u], e = row_ptr[u + 1];
+        qsort(sorted + b, (size_t)(e - b), sizeof(int32_t), cmp_i32);
+        for (int64_t k = b; k < e; k++) {
+            if (sorted[k] < 0 || sorted[k] >= n || sorted[k] == u) { rc = OQ_EINVAL; break; }
+            if (k > b && sorted[k] == sorted[k - 1]) { rc = OQ_EINVAL; break; }
+        }
+    }
+    /* symmetry: (u,v) present implies (v,u) present (binary search in v's sorted row) */
+    for (int64_t u = 0; u < n && rc == OQ_OK; u++) {
+        for (int64_t k = row_ptr[u]; k < row_ptr[u + 1]; k++) {
+            int32_t v = col[k];
+            int64_t lo = row_ptr[v], hi = row_ptr[v + 1];
+            int found = 0;
+            while (lo < hi) {
+                int64_t mid = lo + (hi - lo) / 2;
+                if (sorted[mid] == (int32_t)u) { found = 1; break; }
+                if (sorted[mid] < (int32_t)u) lo = mid + 1; else hi = mid;
+            }
+            if (!found) { rc = OQ_EINVAL; break; }
+        }
+    }
+    free(sorted);
+    return rc;
+}
+
+/*
+ * Output layout of oq_score (plain arrays, no shared struct):
+ *   dbl[0]  Q                      Eq. (8)
+ *   dbl[1]  Qds                    Eq. (9)
+ *   dbl[2]  mean intra-edges       Sec. II-B.3, |E_c^in|
+ *   dbl[3]  mean intra-density     d_c of Eq. (9)
+ *   dbl[4]  mean contraction       2|E_c^in|/|c|
+ *   dbl[5]  mean inter-edges       |E_c^out|
+ *   dbl[6]  mean expansion         |E_c^out|/|c|
+ *   dbl[7]  mean conductance       |E_c^out|/(2|E_c^in|+|E_c^out|)
+ *   dbl[8]  sum of |terms| of Q    (conditioning for tolerance checks)
+ *   dbl[9]  sum of |terms| of Qds
+ *   i64[0]  |V|, i64[1] |E|, i64[2] non-empty communities,
+ *   i64[3]  sum_c |E_c^in|, i64[4] cut edges = sum_c |E_c^out| / 2,
+ *   i64[5]  distinct unordered community pairs with |E_ij| > 0,
+ *   i64[6]  sum over those pairs of |E_ij| squared (integer check value)
+ * Per-community arrays (length K, each may be NULL): size, ein, eout (int64);
+ * intra_density, contraction, expansion, conductance, qds_term (double).
+ * Absent communities (size 0) get zeros.
+ */
+int oq_score(const int64_t *row_ptr, const int32_t *col, int64_t n,
+             const int32_t *label, int32_t K,
+             double *dbl, int64_t *i64,
+             int64_t *pc_size, int64_t *pc_ein, int64_t *pc_eout,
+             double *pc_density, double *pc_contraction, double *pc_expansion,
+             double *pc_conductance, double *pc_qds)
+{
+    if (n < 1 || K < 1)
+        return OQ_EINVAL;
+    for (int64_t u = 0; u < n; u++)
+        if (label[u] < 0 || label[u] >= K)
+            return OQ_EINVAL;
+    int64_t nnz = row_ptr[n];
+    if (nnz <= 0 || (nnz & 1))
+        return OQ_EINVAL;
+    const int64_t E = nnz / 2; /* |E|, each undirected edge stored as two arcs */
+
+    int64_t *size = (int64_t *)calloc((size_t)K, sizeof(int64_t));
+    int64_t *ein = (int64_t *)calloc((size_t)K, sizeof(int64_t));
+    int64_t *eout = (int64_t *)calloc((size_t)K, sizeof(int64_t));
+    uint64_t *keys = (uint64_t *)malloc((size_t)(E > 0 ? E : 1) * sizeof(uint64_t));
+    long double *split = (long double *)calloc((size_t)K, sizeof(long double));
+    if (!size || !ein || !eout || !keys || !split) {
+        free(size); free(ein); free(eout); free(keys); free(split);
+        return OQ_ENOMEM;
+    }
+    int rc = OQ_OK;
+
+    /* community sizes |c| */
+    for (int64_t u = 0; u < n; u++)
+        size[label[u]]++;
+
+    /* classify each undirected edge once (v > u):
+     * inside a community -> |E_c^in|; otherwise it is on the boundary of both
+     * communities (|E_c^out|) and joins the pair (min, max) for |E_ci,cj|. */
+    int64_t nkeys = 0;
+    for (int64_t u = 0; u < n; u++) {
+        int32_t lu = label[u];
+        for (int64_t k = row_ptr[u]; k < row_ptr[u + 1]; k++) {
+            int32_t v = col[k];
+            if (v <= u)
+                continue;
+            int32_t lv = label[v];
+            if (lu == lv) {
+                ein[lu]++;
+            } else {
+                eout[lu]++;
+                eout[lv]++;
+                uint64_t a = (uint64_t)(lu < lv ? lu : lv), b = (uint64_t)(lu < lv ? lv : lu);
+                keys[nkeys++] = (a << 32) | b;
+            }
+        }
+    }
+
+    /* identities: sum_c (2 Ein + Eout) = 2|E|; sum Ein + sum Eout / 2 = |E| */
+    int64_t s_in = 0, s_out = 0;
+    for (int32_t c = 0; c < K; c++) { s_in += ein[c]; s_out += eout[c]; }
+    if (2 * s_in + s_out != nnz || s_in + s_out / 2 != E || (s_out & 1) || s_out / 2 != nkeys)
+        rc = OQ_ECHECK;
+
+    /* |E_ci,cj| by sorting the pair keys and counting runs */
+    qsort(keys, (size_t)nkeys, sizeof(uint64_t), cmp_u64);
+    int64_t npairs = 0, sq_check = 0;
+    int64_t *pair_sum = (int64_t *)calloc((size_t)K, sizeof(int64_t));
+    if (!pair_sum) rc = OQ_ENOMEM;
+    for (int64_t s = 0; s < nkeys && rc == OQ_OK;) {
+        int64_t t = s;
+        while (t < nkeys && keys[t] == keys[s]) t++;
+        int64_t cnt = t - s;
+        int32_t ci = (int32_t)(keys[s] >> 32), cj = (int32_t)(keys[s] & 0xffffffffu);
+        npairs++;
+        sq_check += cnt * cnt;
+        pair_sum[ci] += cnt;
+        pair_sum[cj] += cnt;
+        /* Eq. (9): |E_ci,cj| / (2|E|) * d_ci,cj with d_ci,cj = |E_ci,cj| / (|ci||cj|);
+         * the ordered sum over c_j != c_i adds this term to both communities. */
+        long double eij = (long double)cnt;
+        long double term = (eij / (2.0L * (long double)E)) *
+                           (eij / ((long double)size[ci] * (long double)size[cj]));
+        split[ci] += term;
+        split[cj] += term;
+        s = t;
+    }
+    for (int32_t c = 0; c < K && rc == OQ_OK; c++)
+        if (pair_sum[c] != eout[c])
+            rc = OQ_ECHECK; /* sum_j |E_ij| = |E_i^out| */
+    free(pair_sum);
+
+    oq_sum q = {0, 0}, qabs = {0, 0}, qds = {0, 0}, qdsabs = {0, 0};
+    oq_sum m_in = {0, 0}, m_dens = {0, 0}, m_contr = {0, 0}, m_out = {0, 0}, m_exp = {0, 0}, m_cond = {0, 0};
+    int64_t nonempty = 0;
+    const long double LE = (long double)E;
+    for (int32_t c = 0; c < K && rc == OQ_OK; c++) {
+        if (size[c] == 0) {
+            if (pc_size) pc_size[c] = 0;
+            if (pc_ein) pc_ein[c] = 0;
+            if (pc_eout) pc_eout[c] = 0;
+            if (pc_density) pc_density[c] = 0;
+            if (pc_contraction) pc_contraction[c] = 0;
+            if (pc_expansion) pc_expansion[c] = 0;
+            if (pc_conductance) pc_conductance[c] = 0;
+            if (pc_qds) pc_qds[c] = 0;
+            continue;
+        }
+        nonempty++;
+        long double s = (long double)size[c], in = (long double)ein[c], out = (long double)eout[c];
+        /* Eq. (8) */
+        long double frac_in = in / LE;
+        long double frac_vol = (2.0L * in + out) / (2.0L * LE);
+        sum_add(&q, frac_in - frac_vol * frac_vol);
+        sum_add(&qabs, fabsl(frac_in) + frac_vol * frac_vol);
+        /* Eq. (9): d_c = 2|E_c^in| / (|c|(|c|-1)), 0 for |c| = 1 */
+        long double d = size[c] > 1 ? (2.0L * in) / (s * (s - 1.0L)) : 0.0L;
+        long double t1 = in / LE * d;
+        long double t2 = (2.0L * in + out) / (2.0L * LE) * d;
+        long double term = t1 - t2 * t2 - split[c];
+        sum_add(&qds, term);
+        sum_add(&qdsabs, fabsl(t1) + t2 * t2 + split[c]);
+        /* Sec. II-B.3 */
+        long double contraction = 2.0L * in / s;
+        long double expansion = out / s;
+        long double vol = 2.0L * in + out;
+        long double conductance = vol > 0 ? out / vol : 0.0L;
+        sum_add(&m_in, in);
+        sum_add(&m_dens, d);
+        sum_add(&m_contr, contraction);
+        sum_add(&m_out, out);
+        sum_add(&m_exp, expansion);
+        sum_add(&m_cond, conductance);
+        if (pc_size) pc_size[c] = size[c];
+        if (pc_ein) pc_ein[c] = ein[c];
+        if (pc_eout) pc_eout[c] = eout[c];
+        if (pc_density) pc_density[c] = (double)d;
+        if (pc_contraction) pc_contraction[c] = (double)contraction;
+        if (pc_expansion) pc_expansion[c] = (double)expansion;
+        if (pc_conductance) pc_conductance[c] = (double)conductance;
+        if (pc_qds) pc_qds[c] = (double)term;
+    }
+    if (rc == OQ_OK) {
+        long double ne = (long double)nonempty;
+        dbl[0] = (double)sum_get(&q);
+        dbl[1] = (double)sum_get(&qds);
+        dbl[2] = (double)(sum_get(&m_in) / ne);
+        dbl[3] = (double)(sum_get(&m_dens) / ne);
+        dbl[4] = (double)(sum_get(&m_contr) / ne);
+        dbl[5] = (double)(sum_get(&m_out) / ne);
+        dbl[6] = (double)(sum_get(&m_exp) / ne);
+        dbl[7] = (double)(sum_get(&m_cond) / ne);
+        dbl[8] = (double)sum_get(&qabs);
+        dbl[9] = (double)sum_get(&qdsabs);
+        i64[0] = n;
+        i64[1] = E;
+        i64[2] = nonempty;
+        i64[3] = s_in;
+        i64[4] = s_out / 2;
+        i64[5] = npairs;
+        i64[6] = sq_check;
+    }
+    free(size); free(ein); free(eout); free(keys); free(split);
+    return rc;
+}
+
+/*
+ * Output layout of oq_compare (C = first argument = ground truth, C' = second):
+ *   dbl[0] VI   Eq. (1)          dbl[1] NMI  Eq. (2)
+ *   dbl[2] F-measure Eq. (3)     dbl[3] NVD  Eq. (4)
+ *   dbl[4] RI   Eq. (5)          dbl[5] ARI  Eq. (6)     dbl[6] JI Eq. (7)
+ *   dbl[7] sum |terms| of VI     dbl[8] sum |terms| of the NMI numerator
+ *   dbl[9] |NMI denominator|
+ *   i64[0] |V|, i64[1] non-empty |C|, i64[2] non-empty |C'|, i64[3] non-zero cells,
+ *   i64[4] a11, i64[5] a10, i64[6] a01, i64[7] a00,
+ *   i64[8] sum_c max_c' |c n c'| + sum_c' max_c |c' n c|   (NVD numerator)
+ */
+int oq_compare(const int32_t *a, const int32_t *b, int64_t n, int32_t ka, int32_t kb,
+               double *dbl, int64_t *i64)
+{
+    if (n < 2 || ka < 1 || kb < 1)
+        return OQ_EINVAL;
+    for (int64_t i = 0; i < n; i++)
+        if (a[i] < 0 || a[i] >= ka || b[i] < 0 || b[i] >= kb)
+            return OQ_EINVAL;
+    int64_t *na = (int64_t *)calloc((size_t)ka, sizeof(int64_t));
+    int64_t *nb = (int64_t *)calloc((size_t)kb, sizeof(int64_t));
+    uint64_t *keys = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+    int64_t *rowmax = (int64_t *)calloc((size_t)ka, sizeof(int64_t));
+    int64_t *colmax = (int64_t *)calloc((size_t)kb, sizeof(int64_t));
+    long double *rowbest = (long double *)calloc((size_t)ka, sizeof(long double));
+    if (!na || !nb || !keys || !rowmax || !colmax || !rowbest) {
+        free(na); free(nb); free(keys); free(rowmax); free(colmax); free(rowbest);
+        return OQ_ENOMEM;
+    }
+    for (int64_t i = 0; i < n; i++) {
+        na[a[i]]++;
+        nb[b[i]]++;
+        keys[i] = ((uint64_t)(uint32_t)a[i] << 32) | (uint64_t)(uint32_t)b[i];
+    }
+    /* contingency cells |c n c'| by sorting (c, c') keys */
+    qsort(keys, (size_t)n, sizeof(uint64_t), cmp_u64);
+    const long double N = (long double)n;
+    oq_sum vi = {0, 0}, viabs = {0, 0}, num = {0, 0}, numabs = {0, 0}, den = {0, 0};
+    int64_t ncells = 0, a11 = 0, total = 0;
+    for (int64_t s = 0; s < n;) {
+        int64_t t = s;
+        while (t < n && keys[t] == keys[s]) t++;
+        int64_t cnt = t - s;
+        int32_t ca = (int32_t)(keys[s] >> 32), cb = (int32_t)(keys[s] & 0xffffffffu);
+        ncells++;
+        total += cnt;
+        long double x = (long double)cnt;
+        long double sa = (long double)na[ca], sb = (long double)nb[cb];
+        /* Eq. (1) term: |c n c'| log(|c n c'|^2 / (|c||c'|)) */
+        long double tv = x * logl(x * x / (sa * sb));
+        sum_add(&vi, tv);
+        sum_add(&viabs, fabsl(tv));
+        /* Eq. (2) numerator term: |c n c'|/|V| log(|c n c'||V| / (|c||c'|)) */
+        long double tn = x / N * logl(x * N / (sa * sb));
+        sum_add(&num, tn);
+        sum_add(&numabs, fabsl(tn));
+        /* Eq. (3): max over c' of 2|c n c'| / (|c| + |c'|) */
+        long double r = 2.0L * x / (sa + sb);
+        if (r > rowbest[ca]) rowbest[ca] = r;
+        /* Eq. (4): row and column maxima of |c n c'| */
+        if (cnt > rowmax[ca]) rowmax[ca] = cnt;
+        if (cnt > colmax[cb]) colmax[cb] = cnt;
+        /* Sec. II-A.3: pairs inside one cell are together in both partitions */
+        a11 += cnt * (cnt - 1) / 2;
+        s = t;
+    }
+    int rc = (total == n) ? OQ_OK : OQ_ECHECK;
+    int64_t sa2 = 0, sb2 = 0, nvdsum = 0, kan = 0, kbn = 0;
+    oq_sum f = {0, 0};
+    for (int32_t c = 0; c < ka; c++) {
+        if (na[c] == 0) continue;
+        kan++;
+        long double p = (long double)na[c] / N;
+        sum_add(&den, p * logl(p));
+        sa2 += na[c] * (na[c] - 1) / 2;
+        nvdsum += rowmax[c];
+        sum_add(&f, (long double)na[c] * rowbest[c]);
+    }
+    for (int32_t c = 0; c < kb; c++) {
+        if (nb[c] == 0) continue;
+        kbn++;
+        long double p = (long double)nb[c] / N;
+        sum_add(&den, p * logl(p));
+        sb2 += nb[c] * (nb[c] - 1) / 2;
+        nvdsum += colmax[c];
+    }
+    /* Sec. II-A.3 pair counts from the table: a11 + a10 = sum_c C(|c|,2),
+     * a11 + a01 = sum_c' C(|c'|,2), A = C(|V|,2) */
+    int64_t A = n * (n - 1) / 2;
+    int64_t a10 = sa2 - a11, a01 = sb2 - a11, a00 = A - a11 - a10 - a01;
+    if (a10 < 0 || a01 < 0 || a00 < 0)
+        rc = OQ_ECHECK;
+    if (rc == OQ_OK) {
+        long double LA = (long double)A;
+        long double l11 = (long double)a11, l10 = (long double)a10, l01 = (long double)a01, l00 = (long double)a00;
+        dbl[0] = (double)(-sum_get(&vi) / N);
+        long double dd = sum_get(&den);
+        dbl[1] = dd != 0.0L ? (double)(-2.0L * sum_get(&num) / dd) : 1.0;
+        dbl[2] = (double)(sum_get(&f) / N);
+        dbl[3] = (double)(1.0L - (long double)nvdsum / (2.0L * N));
+        dbl[4] = (double)((l11 + l00) / LA);
+        long double M = (l11 + l10) * (l11 + l01) / LA;  /* Eq. (6) */
+        long double ari_den = 0.5L * ((l11 + l10) + (l11 + l01)) - M;
+        dbl[5] = ari_den != 0.0L ? (double)((l11 - M) / ari_den) : 1.0;
+        long double ji_den = l11 + l10 + l01;
+        dbl[6] = ji_den != 0.0L ? (double)(l11 / ji_den) : 1.0;
+        dbl[7] = (double)(sum_get(&viabs) / N);
+        dbl[8] = (double)(2.0L * sum_get(&numabs));
+        dbl[9] = (double)fabsl(dd);
+        i64[0] = n; i64[1] = kan; i64[2] = kbn; i64[3] = ncells;
+        i64[4] = a11; i64[5] = a10; i64[6] = a01; i64[7] = a00; i64[8] = nvdsum;
+    }
+    free(na); free(nb); free(keys); free(rowmax); free(colmax); free(rowbest);
+    return rc;
+}
+
+/*
+ * Algorithm 4 (Pthreads pair counting), single thread: every unordered node
+ * pair i < j is classified by whether it is together in C and in C'.
+ * out[0..3] = a11, a10, a01, a00.  O(|V|^2): tiny inputs only.
+ */
+int oq_pairs_bruteforce(const int32_t *a, const int32_t *b, int64_t n, int64_t *out)
+{
+    if (n < 2)
+        return OQ_EINVAL;
+    int64_t a11 = 0, a10 = 0, a01 = 0, a00 = 0;
+    for (int64_t i = 0; i < n; i++)
+        for (int64_t j = i + 1; j < n; j++) {
+            int sa = a[i] == a[j], sb = b[i] == b[j];
+            if (sa && sb) a11++;
+            else if (sa) a10++;
+            else if (sb) a01++;
+            else a00++;
+        }
+    out[0] = a11; out[1] = a10; out[2] = a01; out[3] = a00;
+    return OQ_OK;
+}
+
+/*
+ * Set-intersection form of Eqs. (1)-(4), the cost model of Algorithms 1-2:
+ * for every community pair (c, c') count |c n c'| by scanning all nodes.
+ * O(|C||C'||V|): tiny inputs only.  dbl[0..3] = VI, NMI, F-measure, NVD.
+ */
+int oq_compare_bruteforce(const int32_t *a, const int32_t *b, int64_t n, int32_t ka, int32_t kb,
+                          double *dbl)
+{
+    if (n < 2)
+        return OQ_EINVAL;
+    const long double N = (long double)n;
+    oq_sum vi = {0, 0}, num = {0, 0}, den = {0, 0}, f = {0, 0};
+    int64_t nvd = 0;
+    for (int32_t c = 0; c < ka; c++) {
+        int64_t sc = 0;
+        for (int64_t i = 0; i < n; i++) sc += a[i] == c;
+        if (sc == 0) continue;
+        long double best = 0.0L;
+        int64_t bestn = 0;
+        for (int32_t d = 0; d < kb; d++) {
+            int64_t sd = 0, both = 0;
+            for (int64_t i = 0; i < n; i++) {
+                sd += b[i] == d;
+                both += (a[i] == c) && (b[i] == d);
+            }
+            if (sd == 0 || both == 0) continue;
+            long double x = (long double)both;
+            sum_add(&vi, x * logl(x * x / ((long double)sc * (long double)sd)));
+            sum_add(&num, x / N * logl(x * N / ((long double)sc * (long double)sd)));
+            long double r = 2.0L * x / ((long double)sc + (long double)sd);
+            if (r > best) best = r;
+            if (both > bestn) bestn = both;
+        }
+        sum_add(&f, (long double)sc * best);
+        nvd += bestn;
+        long double p = (long double)sc / N;
+        sum_add(&den, p * logl(p));
+    }
+    for (int32_t d = 0; d < kb; d++) {
+        int64_t sd = 0;
+        for (int64_t i = 0; i < n; i++) sd += b[i] == d;
+        if (sd == 0) continue;
+        int64_t bestn = 0;
+        for (int32_t c = 0; c < ka; c++) {
+            int64_t both = 0;
+            for (int64_t i = 0; i < n; i++) both += (a[i] == c) && (b[i] == d);
+            if (both > bestn) bestn = both;
+        }
+        nvd += bestn;
+        long double p = (long double)sd / N;
+        sum_add(&den, p * logl(p));
+    }
+    dbl[0] = (double)(-sum_get(&vi) / N);
+    long double dd = sum_get(&den);
+    dbl[1] = dd != 0.0L ? (double)(-2.0L * sum_get(&num) / dd) : 1.0;
+    dbl[2] = (double)(sum_get(&f) / N);
+    dbl[3] = (double)(1.0L - (long double)nvd / (2.0L * N));
+    return OQ_OK;
+}
+
+/*
+ * Definition-level form of Eqs. (8)-(9) for tiny graphs: for every ordered
+ * community pair (ci, cj) count |E_ci,cj| by scanning every arc, and count
+ * |E_c^in| and |E_c^out| per community by scanning every arc.  O(K^2 |E|).
+ * dbl[0] = Q, dbl[1] = Qds.
+ */
+int oq_score_bruteforce(const int64_t *row_ptr, const int32_t *col, int64_t n,
+                        const int32_t *label, int32_t K, double *dbl)
+{
+    int64_t nnz = row_ptr[n];
+    if (nnz <= 0)
+        return OQ_EINVAL;
+    const long double E = (long double)(nnz / 2);
+    oq_sum q = {0, 0}, qds = {0, 0};
+    for (int32_t ci = 0; ci < K; ci++) {
+        int64_t size = 0, in_arcs = 0, out_arcs = 0;
+        for (int64_t u = 0; u < n; u++) size += label[u] == ci;
+        if (size == 0) continue;
+        for (int64_t u = 0; u < n; u++) {
+            if (label[u] != ci) continue;
+            for (int64_t k = row_ptr[u]; k < row_ptr[u + 1]; k++) {
+                if (label[col[k]] == ci) in_arcs++;
+                else out_arcs++;
+            }
+        }
+        long double in = (long double)(in_arcs / 2), out = (long double)out_arcs;
+        long double frac_vol = (2.0L * in + out) / (2.0L * E);
+        sum_add(&q, in / E - frac_vol * frac_vol);
+        long double s = (long double)size;
+        long double d = size > 1 ? 2.0L * in / (s * (s - 1.0L)) : 0.0L;
+        long double split = 0.0L;
+        for (int32_t cj = 0; cj < K; cj++) {
+            if (cj == ci) continue;
+            int64_t sj = 0, eij = 0;
+            for (int64_t u = 0; u < n; u++) sj += label[u] == cj;
+            if (sj == 0) continue;
+            for (int64_t u = 0; u < n; u++) {
+                if (label[u] != ci) continue;
+                for (int64_t k = row_ptr[u]; k < row_ptr[u + 1]; k++)
+                    eij += label[col[k]] == cj;
+            }
+            long double x = (long double)eij;
+            split += x / (2.0L * E) * (x / (s * (long double)sj));
+        }
+        long double t2 = frac_vol * d;
+        sum_add(&qds, in / E * d - t2 * t2 - split);
+    }
+    dbl[0] = (double)sum_get(&q);
+    dbl[1] = (double)sum_get(&qds);
+    return OQ_OK;
+}
