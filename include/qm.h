@@ -1,0 +1,255 @@
+/*
+ * qm.h -- C ABI of the GB300 community-quality library (libqm.so).
+ *
+ * Scores community partitions of an unweighted, undirected graph with the
+ * metrics of Chen, Liu & Szymanski, "Parallel Toolkit for Measuring the Quality
+ * of Network Community Structure" (arXiv 1507.05492):
+ *   without ground truth (Sec. II-B): modularity Q (Eq. 8), modularity density
+ *     Qds (Eq. 9) and the six measures of Sec. II-B.3;
+ *   with ground truth (Sec. II-A): VI (Eq. 1), NMI (Eq. 2), F-measure (Eq. 3),
+ *     NVD (Eq. 4), RI (Eq. 5), ARI (Eq. 6), JI (Eq. 7).
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns a qm_status.  No C++ exception crosses the ABI.
+ *     On error nothing is written to the caller's output structs, and
+ *     qm_last_error() returns a one-line message for the calling thread.
+ *   - `where` says whether the label / CSR pointers are host memory (QM_HOST)
+ *     or device memory of the current CUDA device (QM_DEVICE).  Result structs
+ *     (qm_quality, qm_compare) are always host memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Work is stream-ordered; every call that produces results synchronises that
+ *     stream once before it returns, so outputs are valid on return.
+ *   - Label arrays are borrowed for the duration of the call only.
+ *   - A partition is an int32 label per node with every label in [0, K).  Label
+ *     ids with no member are absent communities and are skipped in every sum and
+ *     mean.  A label outside [0, K) makes the call return QM_EINVAL.
+ *   - Counts are exact int64.  Floating-point results are FP64; every sum of
+ *     per-community or per-cell terms is accumulated in 128-bit fixed point, so a
+ *     result does not depend on thread scheduling and is bit-identical whether a
+ *     partition is scored alone or inside a batch.
+ *   - Limits: n_nodes < 2^31, n_arcs <= 2^32 - 2^20.
+ *   - Calls on different streams may run concurrently from different threads;
+ *     each call takes its own scratch memory from an internal pool.
+ *
+ * Readings taken where the paper is silent: natural log in VI; d_c = 0 for a
+ * one-node community; conductance 0 when 2|E_in| + |E_out| = 0; the partition
+ * value of a per-community measure is its unweighted mean over non-empty
+ * communities; NMI = 1 when both entropies are 0; ARI = 1 and JI = 1 when their
+ * denominators are 0; pairs of nodes are unordered; the Qds split penalty sums
+ * over ordered community pairs as Eq. (9) is written.
+ */
+#ifndef QM_H
+#define QM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QM_OK = 0,
+    QM_EINVAL = 1,    /* bad argument, label out of range, malformed graph */
+    QM_ENOMEM = 2,    /* device or pinned host memory exhausted */
+    QM_ECUDA = 3,     /* a CUDA runtime call failed */
+    QM_ETIMEOUT = 4,  /* a bounded device-side wait gave up */
+    QM_EOVERFLOW = 5, /* size beyond the library limits (see above) */
+    QM_EBUSY = 6      /* resource temporarily unavailable */
+} qm_status;
+
+typedef enum { QM_HOST = 0, QM_DEVICE = 1 } qm_mem;
+
+/* qm_load_graph flags */
+#define QM_VALIDATE 1u /* check symmetry, no self-loops, no repeated arcs, ids in range */
+
+/* batched-compare flags */
+#define QM_SHARED_TRUTH 1u /* one truth labelling [n] shared by all P candidates */
+
+typedef struct qm_graph qm_graph; /* opaque; owns a device copy of the CSR */
+
+/*
+ * qm_load_graph -- copy a symmetric CSR into a library-owned device graph.
+ * The paper's graph is unweighted and undirected (Sec. II-B.1); each undirected
+ * edge {u,v} must appear as the two arcs (u,v) and (v,u).
+ *   row_ptr  int64[n_nodes + 1], row_ptr[0] = 0, non-decreasing, row_ptr[n] = n_arcs
+ *   col      int32[n_arcs], neighbour ids in [0, n_nodes)
+ *   where    QM_HOST or QM_DEVICE for row_ptr and col
+ *   flags    QM_VALIDATE runs a device check of the CSR (untimed set-up work)
+ *   out      receives the handle; free it with qm_free_graph
+ * The arrays are copied: the caller may free them when the call returns.
+ * Errors: QM_EINVAL (n_nodes < 1, n_arcs odd or 0, bad CSR with QM_VALIDATE),
+ * QM_EOVERFLOW, QM_ENOMEM, QM_ECUDA.
+ */
+qm_status qm_load_graph(const int64_t *row_ptr, const int32_t *col, int64_t n_nodes,
+                        int64_t n_arcs, qm_mem where, unsigned flags, void *stream,
+                        qm_graph **out);
+
+qm_status qm_free_graph(qm_graph *g);
+
+/* Sizes of a loaded graph; any output pointer may be NULL. */
+qm_status qm_graph_info(const qm_graph *g, int64_t *n_nodes, int64_t *n_edges,
+                        int64_t *max_degree, size_t *device_bytes);
+
+/* Result of scoring one partition without ground truth (Sec. II-B). */
+typedef struct {
+    int64_t n_nodes;
+    int64_t n_edges;                /* |E| */
+    int64_t n_communities_nonempty;
+    int64_t intra_edges_total;      /* sum_c |E_c^in| */
+    int64_t cut_edges_total;        /* sum_c |E_c^out| / 2 */
+    int64_t n_community_pairs;      /* unordered pairs (ci, cj) with |E_ci,cj| > 0 */
+    int64_t pair_count_sq_sum;      /* sum over those pairs of |E_ci,cj|^2 */
+    double modularity;              /* Q, Eq. (8) */
+    double modularity_density;      /* Qds, Eq. (9) */
+    double mean_intra_edges;        /* means over non-empty communities, Sec. II-B.3 */
+    double mean_intra_density;
+    double mean_contraction;
+    double mean_inter_edges;
+    double mean_expansion;
+    double mean_conductance;
+} qm_quality;
+
+/* Optional per-community outputs, length K each, memory kind given by `where`
+ * of the call; any pointer may be NULL.  Absent communities get zeros. */
+typedef struct {
+    int64_t *size;          /* |c| */
+    int64_t *intra_edges;   /* |E_c^in| */
+    int64_t *inter_edges;   /* |E_c^out| */
+    double *intra_density;  /* d_c */
+    double *contraction;    /* 2|E_c^in| / |c| */
+    double *expansion;      /* |E_c^out| / |c| */
+    double *conductance;    /* |E_c^out| / (2|E_c^in| + |E_c^out|) */
+    double *qds_term;       /* the bracketed term of Eq. (9) for community c */
+} qm_percomm;
+
+/*
+ * qm_score_partition -- Q, Qds and the six measures of one partition
+ * (Eqs. 8-9, Sec. II-B.3; the per-community decomposition of Sec. III-A).
+ *   labels  int32[n_nodes], labels in [0, K)
+ *   K       number of label ids (>= 1)
+ *   out     host struct, written on success
+ *   per_comm  NULL or per-community arrays (see qm_percomm)
+ * Errors: QM_EINVAL (bad label, K < 1, graph without edges), QM_ENOMEM, QM_ECUDA.
+ */
+qm_status qm_score_partition(const qm_graph *g, const int32_t *labels, int32_t K, qm_mem where,
+                             qm_quality *out, const qm_percomm *per_comm, void *stream);
+
+/* Result of comparing a detected partition with the ground truth (Sec. II-A). */
+typedef struct {
+    int64_t n_nodes;
+    int64_t k_truth;    /* non-empty communities of the ground truth C */
+    int64_t k_found;    /* non-empty communities of the detected C' */
+    int64_t n_cells;    /* non-zero cells |c n c'| */
+    int64_t a11, a10, a01, a00; /* node-pair counts of Sec. II-A.3 */
+    int64_t nvd_sum;    /* sum_c max_c' |c n c'| + sum_c' max_c |c n c'| */
+    double vi;          /* Eq. (1), natural log */
+    double nmi;         /* Eq. (2) */
+    double f_measure;   /* Eq. (3), sum over C, max over C' */
+    double nvd;         /* Eq. (4) */
+    double ri;          /* Eq. (5) */
+    double ari;         /* Eq. (6) */
+    double ji;          /* Eq. (7) */
+} qm_compare;
+
+/*
+ * qm_compare_partitions -- Eqs. (1)-(7) from the contingency table of two
+ * partitions of the same n_nodes nodes.  truth = C (ground truth), found = C'.
+ *   truth  int32[n_nodes] in [0, k_truth); found int32[n_nodes] in [0, k_found)
+ * Errors: QM_EINVAL (n_nodes < 2, bad label), QM_ENOMEM, QM_ECUDA.
+ */
+qm_status qm_compare_partitions(const int32_t *truth, const int32_t *found, int64_t n_nodes,
+                                int32_t k_truth, int32_t k_found, qm_mem where,
+                                qm_compare *out, void *stream);
+
+/*
+ * qm_score_partitions_batched -- score P partitions of one graph in a single
+ * persistent launch (replayed from a captured CUDA graph).
+ *   labels  int32[P][n_nodes] row-major
+ *   K       host int32[P], label-id count of each partition
+ *   out     host qm_quality[P]
+ * Each out[p] is bit-identical to qm_score_partition on partition p.
+ */
+qm_status qm_score_partitions_batched(const qm_graph *g, const int32_t *labels, int32_t P,
+                                      const int32_t *K, qm_mem where, qm_quality *out,
+                                      void *stream);
+
+/*
+ * qm_compare_partitions_batched -- compare P detected partitions with ground
+ * truth in one persistent launch.
+ *   truth   int32[n] when flags has QM_SHARED_TRUTH, else int32[P][n]
+ *   found   int32[P][n]
+ *   k_truth host int32[1] with QM_SHARED_TRUTH, else int32[P]; k_found host int32[P]
+ *   out     host qm_compare[P], each bit-identical to qm_compare_partitions
+ */
+qm_status qm_compare_partitions_batched(const int32_t *truth, const int32_t *found, int64_t n_nodes,
+                                        int32_t P, const int32_t *k_truth, const int32_t *k_found,
+                                        unsigned flags, qm_mem where, qm_compare *out,
+                                        void *stream);
+
+/*
+ * qm_evaluate_partitions_batched -- for each of P candidate partitions of one
+ * graph, every metric with and without ground truth, in one persistent launch:
+ * out_q[p] as qm_score_partition(labels[p]) and out_c[p] as
+ * qm_compare_partitions(truth, labels[p]).
+ *   truth int32[n] shared by all candidates, k_truth its label-id count
+ */
+qm_status qm_evaluate_partitions_batched(const qm_graph *g, const int32_t *labels, int32_t P,
+                                         const int32_t *K, const int32_t *truth, int32_t k_truth,
+                                         qm_mem where, qm_quality *out_q, qm_compare *out_c,
+                                         void *stream);
+
+/*
+ * qm_score_graphs_batched -- score one partition on each of `count` graphs of
+ * possibly different sizes in one persistent launch.
+ *   graphs  host array of count graph handles
+ *   labels  host array of count pointers, labels[i] = int32[n_nodes of graphs[i]]
+ *   K       host int32[count]; out host qm_quality[count]
+ */
+qm_status qm_score_graphs_batched(const qm_graph *const *graphs, const int32_t *const *labels,
+                                  const int32_t *K, int32_t count, qm_mem where, qm_quality *out,
+                                  void *stream);
+
+/*
+ * qm_workspace_bytes -- device scratch one scoring call of this graph with K
+ * label ids needs (with_compare != 0: also a compare against a truth with
+ * k_truth ids).  Used for admission control by memory budget.
+ */
+qm_status qm_workspace_bytes(const qm_graph *g, int32_t K, int32_t with_compare, int32_t k_truth,
+                             size_t *bytes);
+
+/* Drop cached scratch buffers and captured CUDA graphs (they are rebuilt on demand). */
+qm_status qm_release_cache(void);
+
+/*
+ * Tuning.  qm_autotune times the candidate launch shapes of the scoring and
+ * batched kernels on the given inputs and caches the fastest per size bucket
+ * (log2 n_nodes, log2 n_arcs, log2 K).  qm_get_tuning reports the shape the
+ * next call of that bucket will use: threads per block, shared-memory bytes per
+ * block, and the community size above which a whole block (not a warp) scores a
+ * community.
+ */
+typedef struct {
+    int32_t threads;
+    int32_t smem_bytes;
+    int32_t big_community;
+    int32_t blocks_per_sm;
+} qm_tuning;
+
+qm_status qm_autotune(const qm_graph *g, const int32_t *labels, int32_t K, qm_mem where,
+                      void *stream, qm_tuning *chosen);
+qm_status qm_get_tuning(const qm_graph *g, int32_t K, qm_tuning *t);
+qm_status qm_set_tuning(const qm_graph *g, int32_t K, const qm_tuning *t);
+
+/* Number of this library's kernel launches issued since load (for accounting). */
+int64_t qm_kernel_launches(void);
+
+const char *qm_strerror(qm_status s);
+/* Copies the calling thread's last error message into buf (always NUL-terminated). */
+qm_status qm_last_error(char *buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QM_H */

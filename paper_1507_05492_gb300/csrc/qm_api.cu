@@ -1,0 +1,889 @@
+// qm_api.cu -- host runtime behind the C ABI of include/qm.h: graph residency,
+// a scratch-memory pool, launch shapes and their autotuner, and the CUDA graphs
+// that replay the batched persistent launch.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "qm_internal.h"
+
+using namespace qm;
+
+// ------------------------------------------------------------------ errors
+
+static thread_local std::string t_err;
+static std::atomic<long long> g_launches{0};
+
+static qm_status fail(qm_status s, const std::string &msg)
+{
+    t_err = msg;
+    return s;
+}
+
+static qm_status cuda_fail(cudaError_t e, const char *what)
+{
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? QM_ENOMEM : QM_ECUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+    } while (0)
+
+// ------------------------------------------------------------------ device info
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Also performs the once-per-device kernel set-up (shared-memory limits), so
+// every path that launches work calls it first.
+static int num_sms_of(int dev)
+{
+    static std::mutex mu;
+    static std::map<int, int> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(dev);
+    if (it != cache.end()) return it->second;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+    prepare_kernels();
+    prepare_batched_kernel();
+    if (prev != dev) cudaSetDevice(prev);
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    if (v < 1) v = 1;
+    cache[dev] = v;
+    return v;
+}
+
+// ------------------------------------------------------------------ memory pool
+
+// Scratch buffers are allocated on first need and reused by later calls; a call
+// leases a block exclusively until it returns, so concurrent calls never share
+// scratch.
+struct PoolBlock {
+    void *ptr;
+    size_t bytes;
+    int device;
+    bool pinned;
+    bool busy;
+};
+
+class Pool {
+  public:
+    PoolBlock *acquire(size_t bytes, int device, bool pinned)
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        PoolBlock *best = nullptr;
+        for (auto &b : blocks_) {
+            if (b->busy || b->device != device || b->pinned != pinned || b->bytes < bytes) continue;
+            if (!best || b->bytes < best->bytes) best = b.get();
+        }
+        if (best) {
+            best->busy = true;
+            return best;
+        }
+        const size_t gran = pinned ? 4096 : (1u << 20);
+        size_t sz = (bytes + gran - 1) / gran * gran;
+        if (sz == 0) sz = gran;
+        void *p = nullptr;
+        cudaError_t e = pinned ? cudaMallocHost(&p, sz) : cudaMalloc(&p, sz);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            trim_locked(device, pinned);
+            e = pinned ? cudaMallocHost(&p, sz) : cudaMalloc(&p, sz);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return nullptr;
+            }
+        }
+        blocks_.emplace_back(new PoolBlock{p, sz, device, pinned, true});
+        return blocks_.back().get();
+    }
+    void release(PoolBlock *b)
+    {
+        if (!b) return;
+        std::lock_guard<std::mutex> lk(mu_);
+        b->busy = false;
+    }
+    void trim()
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        trim_locked(-1, false);
+        trim_locked(-1, true);
+    }
+
+  private:
+    void trim_locked(int device, bool pinned)
+    {
+        std::vector<std::unique_ptr<PoolBlock>> keep;
+        for (auto &b : blocks_) {
+            if (!b->busy && b->pinned == pinned && (device < 0 || b->device == device)) {
+                int prev = -1;
+                cudaGetDevice(&prev);
+                if (!pinned) cudaSetDevice(b->device);
+                if (pinned) cudaFreeHost(b->ptr); else cudaFree(b->ptr);
+                if (!pinned) cudaSetDevice(prev);
+                on_free(b.get());
+            } else {
+                keep.push_back(std::move(b));
+            }
+        }
+        blocks_.swap(keep);
+    }
+    void on_free(PoolBlock *b);
+    std::mutex mu_;
+    std::vector<std::unique_ptr<PoolBlock>> blocks_;
+};
+
+static Pool g_pool;
+
+struct Lease {
+    PoolBlock *b = nullptr;
+    Lease() = default;
+    explicit Lease(PoolBlock *x) : b(x) {}
+    ~Lease() { g_pool.release(b); }
+    Lease(const Lease &) = delete;
+    Lease &operator=(const Lease &) = delete;
+    char *ptr() const { return (char *)b->ptr; }
+};
+
+// ------------------------------------------------------------------ batched graph cache
+
+// A captured CUDA graph of one batched launch, valid for the scratch blocks it
+// was captured with.  Keyed by (device block, pinned block, shape of the call).
+struct GraphKey {
+    const void *dev, *pin;
+    int count, slots, threads, smem, big;
+    long long n_max;
+    int k_max, kt_max;
+    bool operator<(const GraphKey &o) const
+    {
+        return std::tie(dev, pin, count, slots, threads, smem, big, n_max, k_max, kt_max) <
+               std::tie(o.dev, o.pin, o.count, o.slots, o.threads, o.smem, o.big, o.n_max, o.k_max, o.kt_max);
+    }
+};
+
+static std::mutex g_graph_mu;
+static std::map<GraphKey, cudaGraphExec_t> g_graphs;
+
+void Pool::on_free(PoolBlock *b)
+{
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (auto it = g_graphs.begin(); it != g_graphs.end();) {
+        if (it->first.dev == b->ptr || it->first.pin == b->ptr) {
+            cudaGraphExecDestroy(it->second);
+            it = g_graphs.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+static cudaStream_t capture_stream(int dev)
+{
+    static std::mutex mu;
+    static std::map<int, cudaStream_t> streams;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = streams.find(dev);
+    if (it != streams.end()) return it->second;
+    cudaStream_t s = nullptr;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    streams[dev] = s;
+    return s;
+}
+
+// ------------------------------------------------------------------ graph handle
+
+struct qm_graph {
+    int device;
+    GraphDev d;
+    long long *row_ptr;
+    int *col;
+    long long n, n_arcs, max_degree;
+    size_t bytes;
+    std::mutex mu;
+    std::map<int, Shape> tuning;        // plain path, by size bucket
+    std::map<int, Shape> tuning_batch;  // batched path, by size bucket
+};
+
+static int log2i(long long x)
+{
+    int r = 0;
+    while (x > 1) { x >>= 1; ++r; }
+    return r;
+}
+
+static int bucket_of(long long n, long long arcs, long long K)
+{
+    return (log2i(n) << 16) | (log2i(arcs) << 8) | log2i(K);
+}
+
+static Shape default_shape()
+{
+    Shape s;
+    s.threads = 512;
+    s.smem_bytes = 96 * 1024;
+    s.big_community = 48;
+    s.blocks_per_sm = 0;
+    return s;
+}
+
+static Shape resolve_plain(Shape s)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    num_sms_of(dev);  // kernel set-up before the occupancy query
+    static std::mutex mu;
+    static std::map<std::tuple<int, int>, int> occ;
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_tuple(s.threads, s.smem_bytes);
+    auto it = occ.find(key);
+    if (it == occ.end()) it = occ.emplace(key, std::max(1, score_blocks_per_sm(s))).first;
+    s.blocks_per_sm = it->second;
+    return s;
+}
+
+static Shape resolve_batched(Shape s)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    num_sms_of(dev);
+    static std::mutex mu;
+    static std::map<std::tuple<int, int>, int> occ;
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_tuple(s.threads, s.smem_bytes);
+    auto it = occ.find(key);
+    if (it == occ.end()) it = occ.emplace(key, std::max(1, batched_blocks_per_sm(s))).first;
+    s.blocks_per_sm = it->second;
+    return s;
+}
+
+static Shape shape_for(qm_graph *g, int K, bool batched)
+{
+    std::lock_guard<std::mutex> lk(g->mu);
+    auto &m = batched ? g->tuning_batch : g->tuning;
+    auto it = m.find(bucket_of(g->n, g->n_arcs, K));
+    Shape s = it != m.end() ? it->second : default_shape();
+    return batched ? resolve_batched(s) : resolve_plain(s);
+}
+
+static bool shape_ok(const qm_tuning *t)
+{
+    return t && t->threads >= 64 && t->threads <= 1024 && t->threads % 32 == 0 && t->smem_bytes >= 16384 &&
+           t->smem_bytes <= MAX_DYN_SMEM && t->big_community >= 1 &&
+           plan_smem(t->threads, t->smem_bytes).max_used_w >= 32;
+}
+
+extern "C" {
+
+const char *qm_strerror(qm_status s)
+{
+    switch (s) {
+    case QM_OK: return "ok";
+    case QM_EINVAL: return "invalid argument";
+    case QM_ENOMEM: return "out of memory";
+    case QM_ECUDA: return "CUDA error";
+    case QM_ETIMEOUT: return "device wait timed out";
+    case QM_EOVERFLOW: return "size exceeds library limits";
+    case QM_EBUSY: return "busy";
+    }
+    return "unknown status";
+}
+
+qm_status qm_last_error(char *buf, size_t len)
+{
+    if (!buf || len == 0) return QM_EINVAL;
+    std::snprintf(buf, len, "%s", t_err.c_str());
+    return QM_OK;
+}
+
+int64_t qm_kernel_launches(void) { return g_launches.load(); }
+
+qm_status qm_load_graph(const int64_t *row_ptr, const int32_t *col, int64_t n_nodes, int64_t n_arcs,
+                        qm_mem where, unsigned flags, void *stream, qm_graph **out)
+{
+    if (!out || !row_ptr || !col) return fail(QM_EINVAL, "null argument");
+    *out = nullptr;
+    if (n_nodes < 1) return fail(QM_EINVAL, "n_nodes must be >= 1");
+    if (n_nodes >= (1LL << 31)) return fail(QM_EOVERFLOW, "n_nodes must be < 2^31");
+    if (n_arcs > (1LL << 32) - (1LL << 20)) return fail(QM_EOVERFLOW, "n_arcs must be <= 2^32 - 2^20");
+    if (n_arcs < 2 || (n_arcs & 1)) return fail(QM_EINVAL, "n_arcs must be even and >= 2 (symmetric CSR of a graph with edges)");
+    if (where != QM_HOST && where != QM_DEVICE) return fail(QM_EINVAL, "bad memory kind");
+    if (where == QM_HOST && (row_ptr[0] != 0 || row_ptr[n_nodes] != n_arcs))
+        return fail(QM_EINVAL, "row_ptr must start at 0 and end at n_arcs");
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    cudaStream_t s = (cudaStream_t)stream;
+    std::unique_ptr<qm_graph> g(new qm_graph());
+    g->device = dev;
+    g->n = n_nodes;
+    g->n_arcs = n_arcs;
+    g->row_ptr = nullptr;
+    g->col = nullptr;
+    cudaError_t e = cudaMalloc(&g->row_ptr, (size_t)(n_nodes + 1) * 8);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(row_ptr)");
+    e = cudaMalloc(&g->col, (size_t)n_arcs * 4);
+    if (e != cudaSuccess) {
+        cudaFree(g->row_ptr);
+        return cuda_fail(e, "cudaMalloc(col)");
+    }
+    auto cleanup = [&]() {
+        cudaFree(g->row_ptr);
+        cudaFree(g->col);
+    };
+    const cudaMemcpyKind kind = where == QM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    e = cudaMemcpyAsync(g->row_ptr, row_ptr, (size_t)(n_nodes + 1) * 8, kind, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->col, col, (size_t)n_arcs * 4, kind, s);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(e, "cudaMemcpyAsync(graph)");
+    }
+    g->d.row_ptr = g->row_ptr;
+    g->d.col = g->col;
+    g->d.n = n_nodes;
+    g->d.n_arcs = n_arcs;
+    g->d.max_degree = 0;
+    Lease ws(g_pool.acquire(256, dev, false));
+    Lease pin(g_pool.acquire(256, dev, true));
+    if (!ws.b || !pin.b) {
+        cleanup();
+        return fail(QM_ENOMEM, "scratch allocation failed");
+    }
+    int *status = (int *)ws.ptr();
+    unsigned long long *md = (unsigned long long *)(ws.ptr() + 64);
+    e = cudaMemsetAsync(ws.ptr(), 0, 128, s);
+    if (e != cudaSuccess || launch_validate(g->d, (flags & QM_VALIDATE) ? 1 : 0, status, md, num_sms_of(dev), s) < 0) {
+        cleanup();
+        return cuda_fail(e != cudaSuccess ? e : cudaGetLastError(), "graph validation launch");
+    }
+    g_launches += 1;
+    e = cudaMemcpyAsync(pin.ptr(), ws.ptr(), 128, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(e, "graph validation");
+    }
+    const int st = *(int *)pin.ptr();
+    if (st != 0) {
+        cleanup();
+        return fail(QM_EINVAL, (flags & QM_VALIDATE)
+                                   ? "graph is not a valid symmetric simple CSR with sorted rows"
+                                   : "row offsets or column ids out of range");
+    }
+    g->max_degree = (long long)*(unsigned long long *)(pin.ptr() + 64);
+    g->d.max_degree = g->max_degree;
+    g->bytes = (size_t)(n_nodes + 1) * 8 + (size_t)n_arcs * 4;
+    *out = g.release();
+    return QM_OK;
+}
+
+qm_status qm_free_graph(qm_graph *g)
+{
+    if (!g) return fail(QM_EINVAL, "null graph");
+    DeviceGuard dg(g->device);
+    cudaFree(g->row_ptr);
+    cudaFree(g->col);
+    delete g;
+    return QM_OK;
+}
+
+qm_status qm_graph_info(const qm_graph *g, int64_t *n_nodes, int64_t *n_edges, int64_t *max_degree,
+                        size_t *device_bytes)
+{
+    if (!g) return fail(QM_EINVAL, "null graph");
+    if (n_nodes) *n_nodes = g->n;
+    if (n_edges) *n_edges = g->n_arcs / 2;
+    if (max_degree) *max_degree = g->max_degree;
+    if (device_bytes) *device_bytes = g->bytes;
+    return QM_OK;
+}
+
+static size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+qm_status qm_workspace_bytes(const qm_graph *g, int32_t K, int32_t with_compare, int32_t k_truth, size_t *bytes)
+{
+    if (!g || !bytes || K < 1 || (with_compare && k_truth < 1)) return fail(QM_EINVAL, "bad argument");
+    size_t b = score_ws_bytes(g->n, K) + al256((size_t)g->n * 4);
+    if (with_compare) b += compare_ws_bytes(g->n, k_truth, K) + al256((size_t)g->n * 4);
+    *bytes = b;
+    return QM_OK;
+}
+
+// One plain scoring call on an already-leased workspace.
+static qm_status score_impl(qm_graph *g, const int32_t *labels, int32_t K, qm_mem where, qm_quality *out,
+                            const qm_percomm *pc, cudaStream_t s, const Shape &sh)
+{
+    const long long n = g->n;
+    size_t need = score_ws_bytes(n, K);
+    const size_t lab_off = need;
+    if (where == QM_HOST) need += al256((size_t)n * 4);
+    const size_t pc_off = need;
+    const bool pc_host = pc && where == QM_HOST;
+    if (pc_host) need += al256((size_t)K * 8) * 8;
+    Lease ws(g_pool.acquire(need, g->device, false));
+    Lease pin(g_pool.acquire(al256(sizeof(qm_quality)) + 256, g->device, true));
+    if (!ws.b || !pin.b) return fail(QM_ENOMEM, "scratch allocation failed");
+    ScoreWs w = carve_score_ws(ws.ptr(), n, K);
+    const int32_t *dl = labels;
+    if (where == QM_HOST) {
+        dl = (const int32_t *)(ws.ptr() + lab_off);
+        CK(cudaMemcpyAsync((void *)dl, labels, (size_t)n * 4, cudaMemcpyHostToDevice, s));
+    }
+    CK(cudaMemsetAsync(ws.ptr(), 0, w.zero_bytes, s));
+    PerCommDev pcd{};
+    void *const *hp = nullptr;
+    if (pc) {
+        hp = (void *const *)pc;
+        void **dp = (void **)&pcd;
+        for (int k = 0; k < 8; ++k) {
+            if (!hp[k]) { dp[k] = nullptr; continue; }
+            dp[k] = pc_host ? (void *)(ws.ptr() + pc_off + al256((size_t)K * 8) * k) : hp[k];
+            CK(cudaMemsetAsync(dp[k], 0, (size_t)K * 8, s));
+        }
+    }
+    const int L = launch_score(g->d, dl, K, w, sh, pc ? &pcd : nullptr, num_sms_of(g->device), s);
+    if (L < 0) return cuda_fail(cudaGetLastError(), "launch_score");
+    g_launches += L;
+    CK(cudaMemcpyAsync(pin.ptr(), w.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(pin.ptr() + 256, w.result, sizeof(qm_quality), cudaMemcpyDeviceToHost, s));
+    if (pc_host) {
+        void **dp = (void **)&pcd;
+        for (int k = 0; k < 8; ++k)
+            if (hp[k]) CK(cudaMemcpyAsync(hp[k], dp[k], (size_t)K * 8, cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    const int st = *(int *)pin.ptr();
+    if (st & 1) return fail(QM_EINVAL, "a label lies outside [0, K)");
+    if (st & 2) return fail(QM_EOVERFLOW, "a community borders too many distinct communities");
+    std::memcpy(out, pin.ptr() + 256, sizeof(qm_quality));
+    return QM_OK;
+}
+
+qm_status qm_score_partition(const qm_graph *gc, const int32_t *labels, int32_t K, qm_mem where, qm_quality *out,
+                             const qm_percomm *per_comm, void *stream)
+{
+    qm_graph *g = const_cast<qm_graph *>(gc);
+    if (!g || !labels || !out) return fail(QM_EINVAL, "null argument");
+    if (K < 1) return fail(QM_EINVAL, "K must be >= 1");
+    if (where != QM_HOST && where != QM_DEVICE) return fail(QM_EINVAL, "bad memory kind");
+    DeviceGuard dg(g->device);
+    return score_impl(g, labels, K, where, out, per_comm, (cudaStream_t)stream, shape_for(g, K, false));
+}
+
+qm_status qm_compare_partitions(const int32_t *truth, const int32_t *found, int64_t n, int32_t ka, int32_t kb,
+                                qm_mem where, qm_compare *out, void *stream)
+{
+    if (!truth || !found || !out) return fail(QM_EINVAL, "null argument");
+    if (n < 2) return fail(QM_EINVAL, "n_nodes must be >= 2 (no node pairs otherwise)");
+    if (n >= (1LL << 31)) return fail(QM_EOVERFLOW, "n_nodes must be < 2^31");
+    if (ka < 1 || kb < 1) return fail(QM_EINVAL, "k_truth and k_found must be >= 1");
+    if (where != QM_HOST && where != QM_DEVICE) return fail(QM_EINVAL, "bad memory kind");
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t need = compare_ws_bytes(n, ka, kb);
+    const size_t lab_off = need;
+    if (where == QM_HOST) need += 2 * al256((size_t)n * 4);
+    Lease ws(g_pool.acquire(need, dev, false));
+    Lease pin(g_pool.acquire(512, dev, true));
+    if (!ws.b || !pin.b) return fail(QM_ENOMEM, "scratch allocation failed");
+    CompareWs w = carve_compare_ws(ws.ptr(), n, ka, kb);
+    const int32_t *dt = truth, *df = found;
+    if (where == QM_HOST) {
+        dt = (const int32_t *)(ws.ptr() + lab_off);
+        df = (const int32_t *)(ws.ptr() + lab_off + al256((size_t)n * 4));
+        CK(cudaMemcpyAsync((void *)dt, truth, (size_t)n * 4, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync((void *)df, found, (size_t)n * 4, cudaMemcpyHostToDevice, s));
+    }
+    CK(cudaMemsetAsync(ws.ptr(), 0, w.zero_bytes, s));
+    Shape sh = resolve_plain(default_shape());
+    const int L = launch_compare(dt, df, n, ka, kb, w, sh, num_sms_of(dev), s);
+    if (L < 0) return cuda_fail(cudaGetLastError(), "launch_compare");
+    g_launches += L;
+    CK(cudaMemcpyAsync(pin.ptr(), w.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(pin.ptr() + 256, w.result, sizeof(qm_compare), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const int st = *(int *)pin.ptr();
+    if (st & 1) return fail(QM_EINVAL, "a label lies outside its range");
+    if (st & 2) return fail(QM_EOVERFLOW, "a community holds too many distinct communities");
+    std::memcpy(out, pin.ptr() + 256, sizeof(qm_compare));
+    return QM_OK;
+}
+
+// ------------------------------------------------------------------ batched
+
+struct BatchDesc {
+    std::vector<BatchItem> items;   // device pointers filled except outputs/status
+    long long n_max = 0;
+    int k_max = 1, kt_max = 1;
+    bool any_score = false, any_cmp = false;
+};
+
+// Runs the persistent kernel over `d.items`.  Labels must already be on the device.
+static qm_status run_batched(int dev, BatchDesc &d, const Shape &sh0, qm_quality *out_q, qm_compare *out_c,
+                             cudaStream_t s, Lease *extra_dev)
+{
+    (void)extra_dev;
+    const int count = (int)d.items.size();
+    const int num_sms = num_sms_of(dev);
+    Shape sh = resolve_batched(sh0);
+    int slots = std::min(count, num_sms * sh.blocks_per_sm);
+    // bound the per-block scratch to a quarter of free memory
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    while (slots > 1 && batch_scratch_bytes(d.n_max, d.k_max, d.kt_max, slots) > free_b / 4) slots /= 2;
+    const size_t items_b = al256((size_t)count * sizeof(BatchItem));
+    const size_t q_b = al256((size_t)count * sizeof(qm_quality));
+    const size_t c_b = al256((size_t)count * sizeof(qm_compare));
+    const size_t st_b = al256((size_t)count * sizeof(int) + 256);
+    const size_t scratch_b = batch_scratch_bytes(d.n_max, d.k_max, d.kt_max, slots);
+    Lease ws(g_pool.acquire(items_b + q_b + c_b + st_b + scratch_b, dev, false));
+    Lease pin(g_pool.acquire(items_b + q_b + c_b + st_b, dev, true));
+    if (!ws.b || !pin.b) return fail(QM_ENOMEM, "batched scratch allocation failed");
+    char *D = ws.ptr(), *H = pin.ptr();
+    BatchItem *items_dev = (BatchItem *)D;
+    qm_quality *q_dev = (qm_quality *)(D + items_b);
+    qm_compare *c_dev = (qm_compare *)(D + items_b + q_b);
+    int *st_dev = (int *)(D + items_b + q_b + c_b);          // [count] statuses, then the queue
+    int *queue = st_dev + count;
+    BatchScratch bs = carve_batch_scratch(D + items_b + q_b + c_b + st_b, d.n_max, d.k_max, d.kt_max, slots);
+    BatchItem *items_h = (BatchItem *)H;
+    for (int i = 0; i < count; ++i) {
+        items_h[i] = d.items[i];
+        items_h[i].out_q = q_dev + i;
+        items_h[i].out_c = c_dev + i;
+        items_h[i].status = st_dev + i;
+    }
+    GraphKey key{D, H, count, slots, sh.threads, sh.smem_bytes, sh.big_community, d.n_max, d.k_max, d.kt_max};
+    cudaGraphExec_t exec = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        auto it = g_graphs.find(key);
+        if (it != g_graphs.end()) exec = it->second;
+    }
+    if (!exec) {
+        cudaStream_t cs = capture_stream(dev);
+        CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        cudaMemcpyAsync(items_dev, items_h, (size_t)count * sizeof(BatchItem), cudaMemcpyHostToDevice, cs);
+        cudaMemsetAsync(st_dev, 0, (size_t)count * sizeof(int) + 256, cs);
+        const int L = launch_batched(items_dev, count, queue, bs, sh, num_sms, cs);
+        cudaMemcpyAsync(H + items_b, D + items_b, q_b + c_b + (size_t)count * sizeof(int), cudaMemcpyDeviceToHost, cs);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cs, &graph);
+        if (e != cudaSuccess || L < 0) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(e != cudaSuccess ? e : cudaErrorLaunchFailure, "batched graph capture");
+        }
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        g_graphs[key] = exec;
+    }
+    CK(cudaGraphLaunch(exec, s));
+    g_launches += 1;
+    CK(cudaStreamSynchronize(s));
+    const int *st_h = (const int *)(H + items_b + q_b + c_b);
+    for (int i = 0; i < count; ++i) {
+        if (st_h[i] & 1) return fail(QM_EINVAL, "item " + std::to_string(i) + ": a label lies outside its range");
+        if (st_h[i] & 2) return fail(QM_EOVERFLOW, "item " + std::to_string(i) + ": a community borders too many communities");
+    }
+    const qm_quality *qh = (const qm_quality *)(H + items_b);
+    const qm_compare *ch = (const qm_compare *)(H + items_b + q_b);
+    for (int i = 0; i < count; ++i) {
+        if (out_q && (d.items[i].flags & 1)) out_q[i] = qh[i];
+        if (out_c && (d.items[i].flags & 2)) out_c[i] = ch[i];
+    }
+    return QM_OK;
+}
+
+// Copies P label rows (and an optional truth) to the device when they are host memory.
+static qm_status stage_labels(int dev, const int32_t *labels, size_t n_labels, qm_mem where, cudaStream_t s,
+                              Lease &lease, const int32_t **out)
+{
+    if (where == QM_DEVICE) {
+        *out = labels;
+        return QM_OK;
+    }
+    lease.b = g_pool.acquire(n_labels * 4, dev, false);
+    if (!lease.b) return fail(QM_ENOMEM, "label staging allocation failed");
+    CK(cudaMemcpyAsync(lease.ptr(), labels, n_labels * 4, cudaMemcpyHostToDevice, s));
+    *out = (const int32_t *)lease.ptr();
+    return QM_OK;
+}
+
+static qm_status evaluate_batched(qm_graph *g, const int32_t *labels, int32_t P, const int32_t *K,
+                                  const int32_t *truth, int32_t kt, int flags, qm_mem where, qm_quality *out_q,
+                                  qm_compare *out_c, cudaStream_t s)
+{
+    if (!g || !labels || !K || P < 1) return fail(QM_EINVAL, "bad argument");
+    if ((flags & 2) && (!truth || kt < 1)) return fail(QM_EINVAL, "truth labels required");
+    if (where != QM_HOST && where != QM_DEVICE) return fail(QM_EINVAL, "bad memory kind");
+    DeviceGuard dg(g->device);
+    BatchDesc d;
+    int kmax = 1;
+    for (int p = 0; p < P; ++p) {
+        if (K[p] < 1) return fail(QM_EINVAL, "K must be >= 1");
+        kmax = std::max(kmax, K[p]);
+    }
+    Lease lab, tru;
+    const int32_t *dl = nullptr, *dt = nullptr;
+    qm_status st = stage_labels(g->device, labels, (size_t)P * g->n, where, s, lab, &dl);
+    if (st != QM_OK) return st;
+    if (flags & 2) {
+        st = stage_labels(g->device, truth, (size_t)g->n, where, s, tru, &dt);
+        if (st != QM_OK) return st;
+    }
+    d.n_max = g->n;
+    d.k_max = kmax;
+    d.kt_max = (flags & 2) ? kt : 1;
+    d.items.resize(P);
+    for (int p = 0; p < P; ++p) {
+        BatchItem &it = d.items[p];
+        std::memset(&it, 0, sizeof(it));
+        it.row_ptr = g->row_ptr;
+        it.col = g->col;
+        it.labels = dl + (size_t)p * g->n;
+        it.truth = (flags & 2) ? dt : nullptr;
+        it.n = g->n;
+        it.n_arcs = g->n_arcs;
+        it.K = K[p];
+        it.k_truth = (flags & 2) ? kt : 0;
+        it.flags = flags;
+    }
+    return run_batched(g->device, d, shape_for(g, kmax, true), out_q, out_c, s, nullptr);
+}
+
+qm_status qm_score_partitions_batched(const qm_graph *g, const int32_t *labels, int32_t P, const int32_t *K,
+                                      qm_mem where, qm_quality *out, void *stream)
+{
+    if (!out) return fail(QM_EINVAL, "null output");
+    return evaluate_batched(const_cast<qm_graph *>(g), labels, P, K, nullptr, 0, 1, where, out, nullptr,
+                            (cudaStream_t)stream);
+}
+
+qm_status qm_evaluate_partitions_batched(const qm_graph *g, const int32_t *labels, int32_t P, const int32_t *K,
+                                         const int32_t *truth, int32_t k_truth, qm_mem where, qm_quality *out_q,
+                                         qm_compare *out_c, void *stream)
+{
+    if (!out_q || !out_c) return fail(QM_EINVAL, "null output");
+    return evaluate_batched(const_cast<qm_graph *>(g), labels, P, K, truth, k_truth, 3, where, out_q, out_c,
+                            (cudaStream_t)stream);
+}
+
+qm_status qm_compare_partitions_batched(const int32_t *truth, const int32_t *found, int64_t n, int32_t P,
+                                        const int32_t *k_truth, const int32_t *k_found, unsigned flags,
+                                        qm_mem where, qm_compare *out, void *stream)
+{
+    if (!truth || !found || !k_truth || !k_found || !out || P < 1) return fail(QM_EINVAL, "bad argument");
+    if (n < 2) return fail(QM_EINVAL, "n_nodes must be >= 2");
+    if (n >= (1LL << 31)) return fail(QM_EOVERFLOW, "n_nodes must be < 2^31");
+    if (where != QM_HOST && where != QM_DEVICE) return fail(QM_EINVAL, "bad memory kind");
+    const bool shared = (flags & QM_SHARED_TRUTH) != 0;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    cudaStream_t s = (cudaStream_t)stream;
+    Lease lab, tru;
+    const int32_t *df = nullptr, *dt = nullptr;
+    qm_status st = stage_labels(dev, found, (size_t)P * n, where, s, lab, &df);
+    if (st != QM_OK) return st;
+    st = stage_labels(dev, truth, (size_t)(shared ? 1 : P) * n, where, s, tru, &dt);
+    if (st != QM_OK) return st;
+    BatchDesc d;
+    d.n_max = n;
+    d.items.resize(P);
+    for (int p = 0; p < P; ++p) {
+        const int kt = shared ? k_truth[0] : k_truth[p];
+        if (kt < 1 || k_found[p] < 1) return fail(QM_EINVAL, "label-id counts must be >= 1");
+        d.k_max = std::max(d.k_max, k_found[p]);
+        d.kt_max = std::max(d.kt_max, kt);
+        BatchItem &it = d.items[p];
+        std::memset(&it, 0, sizeof(it));
+        it.labels = df + (size_t)p * n;
+        it.truth = dt + (shared ? 0 : (size_t)p * n);
+        it.n = n;
+        it.K = k_found[p];
+        it.k_truth = kt;
+        it.flags = 2;
+    }
+    return run_batched(dev, d, default_shape(), nullptr, out, s, nullptr);
+}
+
+qm_status qm_score_graphs_batched(const qm_graph *const *graphs, const int32_t *const *labels, const int32_t *K,
+                                  int32_t count, qm_mem where, qm_quality *out, void *stream)
+{
+    if (!graphs || !labels || !K || !out || count < 1) return fail(QM_EINVAL, "bad argument");
+    if (where != QM_HOST && where != QM_DEVICE) return fail(QM_EINVAL, "bad memory kind");
+    const int dev = graphs[0] ? graphs[0]->device : -1;
+    BatchDesc d;
+    size_t total_labels = 0;
+    for (int i = 0; i < count; ++i) {
+        if (!graphs[i] || !labels[i] || K[i] < 1) return fail(QM_EINVAL, "bad graph, labels or K");
+        if (graphs[i]->device != dev) return fail(QM_EINVAL, "all graphs must live on one device");
+        d.n_max = std::max(d.n_max, graphs[i]->n);
+        d.k_max = std::max(d.k_max, K[i]);
+        total_labels += (size_t)graphs[i]->n;
+    }
+    DeviceGuard dg(dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    Lease lab;
+    std::vector<const int32_t *> dl(count);
+    if (where == QM_HOST) {
+        lab.b = g_pool.acquire(total_labels * 4 + 256 * (size_t)count, dev, false);
+        if (!lab.b) return fail(QM_ENOMEM, "label staging allocation failed");
+        size_t off = 0;
+        for (int i = 0; i < count; ++i) {
+            dl[i] = (const int32_t *)(lab.ptr() + off);
+            CK(cudaMemcpyAsync((void *)dl[i], labels[i], (size_t)graphs[i]->n * 4, cudaMemcpyHostToDevice, s));
+            off += al256((size_t)graphs[i]->n * 4);
+        }
+    } else {
+        for (int i = 0; i < count; ++i) dl[i] = labels[i];
+    }
+    d.items.resize(count);
+    for (int i = 0; i < count; ++i) {
+        BatchItem &it = d.items[i];
+        std::memset(&it, 0, sizeof(it));
+        it.row_ptr = graphs[i]->row_ptr;
+        it.col = graphs[i]->col;
+        it.labels = dl[i];
+        it.n = graphs[i]->n;
+        it.n_arcs = graphs[i]->n_arcs;
+        it.K = K[i];
+        it.flags = 1;
+    }
+    return run_batched(dev, d, default_shape(), out, nullptr, s, nullptr);
+}
+
+qm_status qm_release_cache(void)
+{
+    g_pool.trim();
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (auto &kv : g_graphs) cudaGraphExecDestroy(kv.second);
+    g_graphs.clear();
+    return QM_OK;
+}
+
+// ------------------------------------------------------------------ tuning
+
+qm_status qm_get_tuning(const qm_graph *gc, int32_t K, qm_tuning *t)
+{
+    qm_graph *g = const_cast<qm_graph *>(gc);
+    if (!g || !t || K < 1) return fail(QM_EINVAL, "bad argument");
+    DeviceGuard dg(g->device);
+    const Shape s = shape_for(g, K, false);
+    t->threads = s.threads;
+    t->smem_bytes = s.smem_bytes;
+    t->big_community = s.big_community;
+    t->blocks_per_sm = s.blocks_per_sm;
+    return QM_OK;
+}
+
+qm_status qm_set_tuning(const qm_graph *gc, int32_t K, const qm_tuning *t)
+{
+    qm_graph *g = const_cast<qm_graph *>(gc);
+    if (!g || K < 1 || !shape_ok(t)) return fail(QM_EINVAL, "bad tuning");
+    Shape s;
+    s.threads = t->threads;
+    s.smem_bytes = t->smem_bytes;
+    s.big_community = t->big_community;
+    s.blocks_per_sm = 0;
+    std::lock_guard<std::mutex> lk(g->mu);
+    g->tuning[bucket_of(g->n, g->n_arcs, K)] = s;
+    return QM_OK;
+}
+
+// Times every candidate shape of the plain path on these inputs (median of 3
+// runs each, CUDA events on the call's stream) and caches the fastest.
+qm_status qm_autotune(const qm_graph *gc, const int32_t *labels, int32_t K, qm_mem where, void *stream,
+                      qm_tuning *chosen)
+{
+    qm_graph *g = const_cast<qm_graph *>(gc);
+    if (!g || !labels || K < 1) return fail(QM_EINVAL, "bad argument");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    Lease lab;
+    const int32_t *dl = nullptr;
+    qm_status st = stage_labels(g->device, labels, (size_t)g->n, where, s, lab, &dl);
+    if (st != QM_OK) return st;
+    const int threads_c[] = {256, 512, 1024};
+    const int smem_c[] = {48 * 1024, 96 * 1024, 200 * 1024};
+    num_sms_of(g->device);
+    const int big_c[] = {24, 48, 96};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    Shape best = default_shape();
+    qm_quality q;
+    for (int th : threads_c)
+        for (int sm : smem_c)
+            for (int bg : big_c) {
+                Shape sh;
+                sh.threads = th;
+                sh.smem_bytes = sm;
+                sh.big_community = bg;
+                sh.blocks_per_sm = 0;
+                qm_tuning tt{th, sm, bg, 0};
+                if (!shape_ok(&tt)) continue;
+                sh = resolve_plain(sh);
+                if (sh.blocks_per_sm < 1) continue;
+                float times[3];
+                bool ok = true;
+                for (int r = 0; r < 3 && ok; ++r) {
+                    cudaEventRecord(e0, s);
+                    if (score_impl(g, dl, K, QM_DEVICE, &q, nullptr, s, sh) != QM_OK) ok = false;
+                    cudaEventRecord(e1, s);
+                    cudaEventSynchronize(e1);
+                    cudaEventElapsedTime(&times[r], e0, e1);
+                }
+                if (!ok) continue;
+                std::sort(times, times + 3);
+                if (times[1] < best_ms) {
+                    best_ms = times[1];
+                    best = sh;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    {
+        std::lock_guard<std::mutex> lk(g->mu);
+        Shape b = best;
+        b.blocks_per_sm = 0;
+        g->tuning[bucket_of(g->n, g->n_arcs, K)] = b;
+    }
+    if (chosen) {
+        chosen->threads = best.threads;
+        chosen->smem_bytes = best.smem_bytes;
+        chosen->big_community = best.big_community;
+        chosen->blocks_per_sm = best.blocks_per_sm;
+    }
+    return QM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,333 @@
+// qm_device.cuh -- device building blocks shared by every scoring kernel.
+//
+// * 128-bit fixed-point accumulation: every floating-point sum of the metrics
+//   (Eqs. 1-3, 9 and the means of Sec. II-B.3) is a sum of per-community or
+//   per-cell terms.  Each term is evaluated once in FP64 with round-to-nearest
+//   operations (the library is built with --fmad=false), converted to a signed
+//   128-bit integer at a fixed binary scale, and the integers are added.  Integer
+//   addition is associative, so a sum does not depend on how threads, warps,
+//   blocks or batches split the work.
+// * An open-addressing hash table in shared memory that counts how often each
+//   community id occurs (|E_ci,cj| of Eq. 9 and the cells |c n c'| of Eqs. 1-4).
+// * The per-community and per-cell term formulas.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace qmk {
+
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+// Binary scales of the fixed-point accumulators (value = integer * 2^-scale).
+// Each is chosen so that the largest possible sum stays below 2^126.
+constexpr int SC_QDS = 100;   // Qds terms: |sum| <= 3
+constexpr int SC_MEAN = 64;   // sums of d_c, 2E_in/|c|, E_out/|c|, conductance: < 2^34
+constexpr int SC_VI = 80;     // sum of n log(n^2/(n_a n_b)): |sum| < 43 N < 2^37
+constexpr int SC_H = 100;     // NMI numerator / denominator terms: |sum| < 44
+constexpr int SC_F = 80;      // F-measure sum of n_a * max ratio: < N < 2^31
+
+// ---------------------------------------------------------------- fixed point
+
+__device__ __forceinline__ i128 fp_from_double(double x, int scale)
+{
+    unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    int ex = (int)((bits >> 52) & 0x7FF);
+    unsigned long long man = bits & ((1ull << 52) - 1);
+    if (ex == 0 && man == 0) return 0;
+    if (ex == 0) ex = 1; else man |= (1ull << 52);
+    int sh = ex - 1075 + scale;               // |x| * 2^scale = man * 2^sh
+    u128 m = (u128)man, v;
+    if (sh >= 0) {
+        if (sh > 73) sh = 73;                 // out of range: saturate (never reached in range)
+        v = m << sh;
+    } else if (sh > -127) {
+        v = (m + ((u128)1 << (-sh - 1))) >> (-sh);   // round half up
+    } else {
+        v = 0;
+    }
+    return (bits >> 63) ? -(i128)v : (i128)v;
+}
+
+__device__ __forceinline__ double fp_to_double(i128 v, int scale)
+{
+    bool neg = v < 0;
+    u128 a = neg ? (u128)(-v) : (u128)v;
+    double hi = (double)(unsigned long long)(a >> 64);
+    double lo = (double)(unsigned long long)a;
+    double r = __dadd_rn(__dmul_rn(hi, 18446744073709551616.0), lo);
+    r = ldexp(r, -scale);
+    return neg ? -r : r;
+}
+
+// A 128-bit sum kept in global memory as three 64-bit limbs so that it can be
+// updated with 64-bit atomics: v = L2 * 2^86 + L1 * 2^43 + L0, where L0 and L1
+// add up non-negative 43-bit chunks (safe for fewer than 2^21 additions) and
+// L2 adds the signed high part.
+__device__ __forceinline__ void limbs_add(unsigned long long *L, i128 v)
+{
+    const u128 mask = (((u128)1) << 43) - 1;
+    u128 u = (u128)v;
+    unsigned long long l0 = (unsigned long long)(u & mask);
+    unsigned long long l1 = (unsigned long long)((u >> 43) & mask);
+    long long l2 = (long long)(v >> 86);
+    if (l0) atomicAdd(&L[0], l0);
+    if (l1) atomicAdd(&L[1], l1);
+    if (l2) atomicAdd(&L[2], (unsigned long long)l2);
+}
+
+__device__ __forceinline__ void limbs_store(unsigned long long *L, i128 v)
+{
+    const u128 mask = (((u128)1) << 43) - 1;
+    u128 u = (u128)v;
+    L[0] = (unsigned long long)(u & mask);
+    L[1] = (unsigned long long)((u >> 43) & mask);
+    L[2] = (unsigned long long)(long long)(v >> 86);
+}
+
+__device__ __forceinline__ i128 limbs_get(const unsigned long long *L)
+{
+    return (i128)(long long)L[2] * (((i128)1) << 86) + (i128)L[1] * (((i128)1) << 43) + (i128)L[0];
+}
+
+__device__ __forceinline__ i128 shfl_down_i128(i128 v, int d)
+{
+    unsigned long long lo = (unsigned long long)(u128)v;
+    unsigned long long hi = (unsigned long long)((u128)v >> 64);
+    lo = __shfl_down_sync(0xffffffffu, lo, d);
+    hi = __shfl_down_sync(0xffffffffu, hi, d);
+    return (i128)(((u128)hi << 64) | (u128)lo);
+}
+
+__device__ __forceinline__ i128 warp_sum_i128(i128 v)
+{
+    for (int d = 16; d > 0; d >>= 1) v += shfl_down_i128(v, d);
+    return v;  // valid in lane 0
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
+{
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+    return v;
+}
+
+// ---------------------------------------------------------------- accumulators
+
+// Per-thread partial sums of one partition's no-ground-truth metrics.
+struct ScoreAcc {
+    i128 qds_self;    // sum_c [E_in/|E| d_c - ((2E_in+E_out)/(2|E|) d_c)^2]   (SC_QDS)
+    i128 qds_pair;    // sum over ordered (ci,cj) of |E_ij|^2 / (2|E| |ci| |cj|)  (SC_QDS)
+    i128 dens;        // sum_c d_c                 (SC_MEAN)
+    i128 contr;       // sum_c 2 E_in / |c|        (SC_MEAN)
+    i128 expn;        // sum_c E_out / |c|         (SC_MEAN)
+    i128 cond;        // sum_c conductance         (SC_MEAN)
+    u128 vol2;        // sum_c (2 E_in + E_out)^2  (exact)
+    unsigned long long ein;       // sum_c E_in
+    unsigned long long eout;      // sum_c E_out
+    unsigned long long nonempty;  // communities with |c| > 0
+    unsigned long long slots;     // ordered pairs (ci,cj) with |E_ij| > 0
+    unsigned long long cnt2;      // sum over ordered pairs of |E_ij|^2
+};
+
+__device__ __forceinline__ void score_acc_zero(ScoreAcc &a)
+{
+    a.qds_self = a.qds_pair = a.dens = a.contr = a.expn = a.cond = 0;
+    a.vol2 = 0;
+    a.ein = a.eout = a.nonempty = a.slots = a.cnt2 = 0;
+}
+
+__device__ __forceinline__ void score_acc_add(ScoreAcc &d, const ScoreAcc &s)
+{
+    d.qds_self += s.qds_self;
+    d.qds_pair += s.qds_pair;
+    d.dens += s.dens;
+    d.contr += s.contr;
+    d.expn += s.expn;
+    d.cond += s.cond;
+    d.vol2 += s.vol2;
+    d.ein += s.ein;
+    d.eout += s.eout;
+    d.nonempty += s.nonempty;
+    d.slots += s.slots;
+    d.cnt2 += s.cnt2;
+}
+
+// Global (per-partition) accumulator layout, all unsigned long long:
+enum {
+    GS_QDS_SELF = 0, GS_QDS_PAIR = 3, GS_DENS = 6, GS_CONTR = 9, GS_EXPN = 12, GS_COND = 15,
+    GS_VOL2 = 18, GS_EIN = 21, GS_EOUT = 22, GS_NONEMPTY = 23, GS_SLOTS = 24, GS_CNT2 = 25,
+    GS_COUNT = 26
+};
+
+// Per-thread partial sums of one comparison (contingency table).
+struct CompareAcc {
+    i128 vi;     // sum over cells of n log(n^2 / (n_a n_b))        (SC_VI)
+    i128 hnum;   // sum over cells of (n/N) log(n N / (n_a n_b))    (SC_H)
+    i128 hden;   // sum over communities of both sides of p log p   (SC_H)
+    i128 f;      // sum over truth communities of n_a * max ratio   (SC_F)
+    unsigned long long a11;     // sum over cells C(n, 2)
+    unsigned long long sa;      // sum over truth communities C(n_a, 2)
+    unsigned long long sb;      // sum over found communities C(n_b, 2)
+    unsigned long long nvd;     // row maxima + column maxima
+    unsigned long long cells;   // non-zero cells
+    unsigned long long ka;      // non-empty truth communities
+    unsigned long long kb;      // non-empty found communities
+};
+
+__device__ __forceinline__ void compare_acc_zero(CompareAcc &a)
+{
+    a.vi = a.hnum = a.hden = a.f = 0;
+    a.a11 = a.sa = a.sb = a.nvd = a.cells = a.ka = a.kb = 0;
+}
+
+__device__ __forceinline__ void compare_acc_add(CompareAcc &d, const CompareAcc &s)
+{
+    d.vi += s.vi;
+    d.hnum += s.hnum;
+    d.hden += s.hden;
+    d.f += s.f;
+    d.a11 += s.a11;
+    d.sa += s.sa;
+    d.sb += s.sb;
+    d.nvd += s.nvd;
+    d.cells += s.cells;
+    d.ka += s.ka;
+    d.kb += s.kb;
+}
+
+enum {
+    GC_VI = 0, GC_HNUM = 3, GC_HDEN = 6, GC_F = 9, GC_A11 = 12, GC_SA = 13, GC_SB = 14,
+    GC_NVD = 15, GC_CELLS = 16, GC_KA = 17, GC_KB = 18, GC_COUNT = 19
+};
+
+// ---------------------------------------------------------------- term formulas
+
+// Eq. (9) self part and the Sec. II-B.3 measures of one non-empty community.
+// ein = |E_c^in|, eout = |E_c^out|, s = |c|, E = |E|.
+__device__ __forceinline__ void community_terms(long long ein, long long eout, long long s, long long E,
+                                                double &qds_self, double &dens, double &contr,
+                                                double &expn, double &cond)
+{
+    const double in = (double)ein, out = (double)eout, sz = (double)s, e = (double)E;
+    const double vol = __dadd_rn(__dmul_rn(2.0, in), out);
+    dens = (s > 1) ? __ddiv_rn(__dmul_rn(2.0, in), __dmul_rn(sz, __dsub_rn(sz, 1.0))) : 0.0;
+    const double t1 = __dmul_rn(__ddiv_rn(in, e), dens);
+    const double t2 = __dmul_rn(__ddiv_rn(vol, __dmul_rn(2.0, e)), dens);
+    qds_self = __dsub_rn(t1, __dmul_rn(t2, t2));
+    contr = __ddiv_rn(__dmul_rn(2.0, in), sz);
+    expn = __ddiv_rn(out, sz);
+    cond = (vol > 0.0) ? __ddiv_rn(out, vol) : 0.0;
+}
+
+// Eq. (9) split-penalty term of the ordered pair (ci, cj):
+// |E_ij| / (2|E|) * |E_ij| / (|ci| |cj|).
+__device__ __forceinline__ double pair_term(long long cnt, long long si, long long sj, long long E)
+{
+    const double x = (double)cnt;
+    const double a = __ddiv_rn(x, __dmul_rn(2.0, (double)E));
+    const double b = __ddiv_rn(x, __dmul_rn((double)si, (double)sj));
+    return __dmul_rn(a, b);
+}
+
+// Eq. (1) term n log(n^2 / (n_a n_b)) of one contingency cell.
+__device__ __forceinline__ double vi_term(long long n, long long na, long long nb)
+{
+    const double x = (double)n;
+    return __dmul_rn(x, log(__ddiv_rn(__dmul_rn(x, x), __dmul_rn((double)na, (double)nb))));
+}
+
+// Eq. (2) numerator term (n/N) log(n N / (n_a n_b)) of one cell.
+__device__ __forceinline__ double nmi_num_term(long long n, long long na, long long nb, long long N)
+{
+    const double x = (double)n, nn = (double)N;
+    return __dmul_rn(__ddiv_rn(x, nn), log(__ddiv_rn(__dmul_rn(x, nn), __dmul_rn((double)na, (double)nb))));
+}
+
+// Eq. (2) denominator term (n_c/N) log(n_c/N) of one community.
+__device__ __forceinline__ double entropy_term(long long nc, long long N)
+{
+    const double p = __ddiv_rn((double)nc, (double)N);
+    return __dmul_rn(p, log(p));
+}
+
+// Eq. (3) ratio 2 n / (n_a + n_b) of one cell.
+__device__ __forceinline__ double f_ratio(long long n, long long na, long long nb)
+{
+    return __ddiv_rn(__dmul_rn(2.0, (double)n), (double)(na + nb));
+}
+
+// ---------------------------------------------------------------- hash table
+
+// Open addressing with linear probing over `cap` 64-bit slots in shared memory.
+// A slot holds ((key + 1) << 32) | count; 0 means empty.  `used` lists the
+// occupied slot indices so that reading out and clearing cost O(occupied).
+struct SmemTable {
+    unsigned long long *slot;
+    int *used;
+    int *n_used;     // shared counter
+    int *overflow;   // shared flag
+    int cap;
+    int max_used;
+};
+
+__device__ __forceinline__ unsigned tab_hash(unsigned key, int cap)
+{
+    return __umulhi(key * 0x9E3779B1u + 0x7F4A7C15u, (unsigned)cap);
+}
+
+// Secondary hash that splits keys into R sub-ranges for multi-pass counting.
+__device__ __forceinline__ unsigned tab_split(unsigned key, unsigned R)
+{
+    unsigned h = key * 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h % R;
+}
+
+__device__ __forceinline__ void tab_insert(const SmemTable &t, unsigned key)
+{
+    const unsigned long long tag = (unsigned long long)(key + 1u) << 32;
+    unsigned h = tab_hash(key, t.cap);
+    for (int probe = 0; probe < t.cap; ++probe) {
+        unsigned long long cur = ((volatile unsigned long long *)t.slot)[h];
+        if (cur == 0ull) {
+            unsigned long long prev = atomicCAS(&t.slot[h], 0ull, tag | 1ull);
+            if (prev == 0ull) {
+                int idx = atomicAdd(t.n_used, 1);
+                if (idx < t.max_used) t.used[idx] = (int)h;
+                else *t.overflow = 1;
+                return;
+            }
+            cur = prev;
+        }
+        if ((cur & 0xFFFFFFFF00000000ull) == tag) {
+            atomicAdd(&t.slot[h], 1ull);
+            return;
+        }
+        h = (h + 1u == (unsigned)t.cap) ? 0u : h + 1u;
+    }
+    *t.overflow = 1;
+}
+
+// ---------------------------------------------------------------- misc
+
+// Number of entries of the sorted prefix a[0..n) that are <= x.
+__device__ __forceinline__ int upper_bound_smem(const unsigned *a, int n, unsigned x)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (a[mid] <= x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void group_sync(int group)
+{
+    if (group == 32) __syncwarp();
+    else __syncthreads();
+}
+
+}  // namespace qmk

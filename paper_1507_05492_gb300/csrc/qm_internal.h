@@ -1,0 +1,143 @@
+// qm_internal.h -- declarations shared by the library's translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/qm.h"
+
+namespace qm {
+
+// Device copy of a symmetric CSR (library-owned).
+struct GraphDev {
+    const long long *row_ptr;  // [n + 1]
+    const int *col;            // [n_arcs]
+    long long n;
+    long long n_arcs;
+    long long max_degree;
+};
+
+// Launch shape of the community-major kernels.
+struct Shape {
+    int threads;        // threads per block (multiple of 32, <= 1024)
+    int smem_bytes;     // dynamic shared memory per block
+    int big_community;  // communities with more members are scored by a whole block
+    int blocks_per_sm;  // resident blocks per SM (filled in from occupancy)
+};
+
+// Carving of the dynamic shared memory of a community-major block.
+struct SmemPlan {
+    int red_off, ctl_off, acc_off, offs_off, rs_off, slot_off, used_off;
+    int cap, max_used;        // whole-block table
+    int cap_w, max_used_w;    // one warp's table
+    int bytes;
+};
+SmemPlan plan_smem(int threads, int smem_bytes);
+
+// Device scratch of one plain scoring call (carved from one allocation).
+struct ScoreWs {
+    int *status;                // [1] bit 0: label out of range
+    int *counters;              // [8]
+    unsigned long long *gacc;   // [32]
+    qm_quality *result;         // [1]
+    int *size;                  // [K]
+    int *start;                 // [K + 1]
+    int *cursor;                // [K]
+    int *big_list;              // [K]
+    int *ovf_list;              // [K]
+    int *members;               // [n]
+    int *scan_tmp;              // [scan tiles + 1]
+    size_t zero_bytes;          // bytes from `status` that must start at zero
+};
+
+struct CompareWs {
+    int *status;
+    int *counters;
+    unsigned long long *gacc;
+    qm_compare *result;
+    int *size_a;                // [ka]
+    int *size_b;                // [kb]
+    unsigned *rowmax_n;         // [ka]
+    unsigned long long *rowmax_r; // [ka]
+    int *start;                 // [kb + 1]
+    int *cursor;                // [kb]
+    int *big_list;              // [kb]
+    int *members;               // [n]
+    int *scan_tmp;
+    size_t zero_bytes;
+};
+
+size_t score_ws_bytes(long long n, int K);
+size_t compare_ws_bytes(long long n, int ka, int kb);
+ScoreWs carve_score_ws(void *base, long long n, int K);
+CompareWs carve_compare_ws(void *base, long long n, int ka, int kb);
+
+// Optional per-community outputs (device pointers).
+struct PerCommDev {
+    long long *size, *ein, *eout;
+    double *dens, *contr, *expn, *cond, *qds;
+};
+
+// Plain path launchers (stream-ordered, no synchronisation).  Each returns the
+// number of kernels it launched, or -1 on a launch error.
+int launch_score(const GraphDev &g, const int *labels, int K, const ScoreWs &ws, const Shape &sh,
+                 const PerCommDev *pc, int num_sms, cudaStream_t s);
+int launch_compare(const int *truth, const int *found, long long n, int ka, int kb,
+                   const CompareWs &ws, const Shape &sh, int num_sms, cudaStream_t s);
+
+// Largest dynamic shared memory a community-major block may request.
+constexpr int MAX_DYN_SMEM = 220 * 1024;
+
+// Raises the dynamic shared-memory limit of the kernels to MAX_DYN_SMEM (once
+// per device, before any launch or capture).
+void prepare_kernels();
+void prepare_batched_kernel();
+
+// Occupancy of the community-major kernels for a shape.
+int score_blocks_per_sm(const Shape &sh);
+
+// ---- batched persistent kernel
+
+// One work item of the batched kernel: score and/or compare one partition.
+struct BatchItem {
+    const long long *row_ptr;
+    const int *col;
+    const int *labels;       // partition to score / detected partition
+    const int *truth;        // ground truth (compare), or null
+    long long n;
+    long long n_arcs;
+    int K;
+    int k_truth;
+    int flags;               // 1 = score, 2 = compare
+    int pad;
+    qm_quality *out_q;       // device result slots
+    qm_compare *out_c;
+    int *status;             // per-item status word
+};
+
+struct BatchScratch {
+    int *members;            // [slots][n_max]
+    int *size;               // [slots][k_max]
+    int *start;              // [slots][k_max + 1]
+    int *size_a;             // [slots][kt_max]
+    unsigned *rowmax_n;      // [slots][kt_max]
+    unsigned long long *rowmax_r; // [slots][kt_max]
+    int *big_list;           // [slots][k_max]
+    long long n_max;
+    int k_max, kt_max;
+    int slots;
+};
+
+size_t batch_scratch_bytes(long long n_max, int k_max, int kt_max, int slots);
+BatchScratch carve_batch_scratch(void *base, long long n_max, int k_max, int kt_max, int slots);
+
+int launch_batched(const BatchItem *items_dev, int count, int *queue, const BatchScratch &bs,
+                   const Shape &sh, int num_sms, cudaStream_t s);
+int batched_blocks_per_sm(const Shape &sh);
+
+// ---- graph validation
+int launch_validate(const GraphDev &g, int full, int *status, unsigned long long *max_deg, int num_sms,
+                    cudaStream_t s);
+
+}  // namespace qm

@@ -1,0 +1,693 @@
+// qm_kernels.cu -- the plain (one partition per call) scoring path.
+//
+// Pipeline of qm_score_partition, all on one stream:
+//   k_hist      |c| for every label id, with the label range check
+//   k_scan_*    exclusive prefix of |c| -> member offsets; list of large communities
+//   k_scatter   node ids grouped by community (a counting sort)
+//   k_score_cm  community-major pass (Sec. III-A decomposition): large communities
+//               by whole blocks, the rest by single warps
+//   k_score_cm  again over the communities whose warp table overflowed
+//   k_score_fin exact sums -> qm_quality
+// qm_compare_partitions runs the same counting sort on the detected labels,
+// hashes the ground-truth labels of each detected community's members into the
+// contingency cells, then walks the ground-truth communities for the row maxima.
+#include <climits>
+
+#include "qm_internal.h"
+#include "qm_community.cuh"
+#include "qm_finalize.cuh"
+
+namespace qm {
+using namespace qmk;
+
+enum { C_BIG_COUNT = 0, C_BIG_NEXT = 1, C_SMALL_NEXT = 2, C_OVF_COUNT = 3, C_OVF_NEXT = 4 };
+
+constexpr int SCAN_TILE = 4096;   // elements per block in the multi-block scan
+constexpr int SCAN_SINGLE_MAX = 1 << 16;
+
+SmemPlan plan_smem(int T, int S)
+{
+    SmemPlan p;
+    const int W = T / 32;
+    int off = 0;
+    p.red_off = off;
+    off += 72 * 8;
+    p.ctl_off = off;
+    off += ((2 * (W + 1) * 4 + 15) / 16) * 16;
+    p.acc_off = off;    // one ScoreAcc / CompareAcc per warp
+    off += W * 160;
+    p.offs_off = off;
+    off += (((T + W) * 4 + 15) / 16) * 16;
+    p.rs_off = off;
+    off += T * 8;
+    const int rest = S - off;
+    int cap = rest / 11;
+    cap = (cap / W) * W;
+    int mu = (cap * 3) / 4;
+    mu = (mu / W) * W;
+    p.slot_off = off;
+    off += cap * 8;
+    p.used_off = off;
+    off += mu * 4;
+    p.cap = cap;
+    p.max_used = mu;
+    p.cap_w = cap / W;
+    p.max_used_w = mu / W;
+    p.bytes = off;
+    return p;
+}
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+static int scan_tiles(int K) { return (K + SCAN_TILE - 1) / SCAN_TILE; }
+
+size_t score_ws_bytes(long long n, int K)
+{
+    size_t b = 0;
+    b += 256;                                   // status + counters
+    b += align_up(32 * 8, 256);                 // gacc
+    b += align_up(sizeof(qm_quality), 256);     // result
+    b += align_up((size_t)K * 4, 256);          // size (zeroed)
+    b += align_up((size_t)(K + 1) * 4, 256);    // start
+    b += align_up((size_t)K * 4, 256) * 3;      // cursor, big_list, ovf_list
+    b += align_up((size_t)n * 4, 256);          // members
+    b += align_up((size_t)(scan_tiles(K) + 1) * 4, 256);
+    return b;
+}
+
+ScoreWs carve_score_ws(void *base, long long n, int K)
+{
+    ScoreWs w;
+    char *p = (char *)base;
+    w.status = (int *)p;
+    w.counters = (int *)(p + 16);
+    p += 256;
+    w.gacc = (unsigned long long *)p;
+    p += align_up(32 * 8, 256);
+    w.result = (qm_quality *)p;
+    p += align_up(sizeof(qm_quality), 256);
+    w.size = (int *)p;
+    p += align_up((size_t)K * 4, 256);
+    w.zero_bytes = (size_t)(p - (char *)base);
+    w.start = (int *)p;
+    p += align_up((size_t)(K + 1) * 4, 256);
+    w.cursor = (int *)p;
+    p += align_up((size_t)K * 4, 256);
+    w.big_list = (int *)p;
+    p += align_up((size_t)K * 4, 256);
+    w.ovf_list = (int *)p;
+    p += align_up((size_t)K * 4, 256);
+    w.members = (int *)p;
+    p += align_up((size_t)n * 4, 256);
+    w.scan_tmp = (int *)p;
+    return w;
+}
+
+size_t compare_ws_bytes(long long n, int ka, int kb)
+{
+    size_t b = 0;
+    b += 256;
+    b += align_up(32 * 8, 256);
+    b += align_up(sizeof(qm_compare), 256);
+    b += align_up((size_t)ka * 4, 256) * 2;     // size_a, rowmax_n
+    b += align_up((size_t)kb * 4, 256);         // size_b
+    b += align_up((size_t)ka * 8, 256);         // rowmax_r
+    b += align_up((size_t)(kb + 1) * 4, 256);   // start
+    b += align_up((size_t)kb * 4, 256) * 2;     // cursor, big_list
+    b += align_up((size_t)n * 4, 256);          // members
+    b += align_up((size_t)(scan_tiles(kb) + 1) * 4, 256);
+    return b;
+}
+
+CompareWs carve_compare_ws(void *base, long long n, int ka, int kb)
+{
+    CompareWs w;
+    char *p = (char *)base;
+    w.status = (int *)p;
+    w.counters = (int *)(p + 16);
+    p += 256;
+    w.gacc = (unsigned long long *)p;
+    p += align_up(32 * 8, 256);
+    w.result = (qm_compare *)p;
+    p += align_up(sizeof(qm_compare), 256);
+    w.size_a = (int *)p;
+    p += align_up((size_t)ka * 4, 256);
+    w.rowmax_n = (unsigned *)p;
+    p += align_up((size_t)ka * 4, 256);
+    w.size_b = (int *)p;
+    p += align_up((size_t)kb * 4, 256);
+    w.rowmax_r = (unsigned long long *)p;
+    p += align_up((size_t)ka * 8, 256);
+    w.zero_bytes = (size_t)(p - (char *)base);
+    w.start = (int *)p;
+    p += align_up((size_t)(kb + 1) * 4, 256);
+    w.cursor = (int *)p;
+    p += align_up((size_t)kb * 4, 256);
+    w.big_list = (int *)p;
+    p += align_up((size_t)kb * 4, 256);
+    w.members = (int *)p;
+    p += align_up((size_t)n * 4, 256);
+    w.scan_tmp = (int *)p;
+    return w;
+}
+
+// ------------------------------------------------------------------ histogram
+
+// |c| for every label id (and the ground-truth sizes when `b` is given).
+// Labels outside [0, K) set bit 0 of *status and are skipped.  When the ids fit,
+// each block counts in shared memory first and adds its non-zero bins once.
+__global__ void k_hist(const int *__restrict__ a, int ka, int *size_a, const int *__restrict__ b,
+                       int kb, int *size_b, long long n, int *status, int use_smem)
+{
+    extern __shared__ int sh[];
+    if (use_smem) {
+        for (int i = threadIdx.x; i < ka + kb; i += blockDim.x) sh[i] = 0;
+        __syncthreads();
+    }
+    bool bad = false;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int la = __ldcs(&a[i]);
+        if ((unsigned)la >= (unsigned)ka) bad = true;
+        else if (use_smem) atomicAdd(&sh[la], 1);
+        else atomicAdd(&size_a[la], 1);
+        if (b) {
+            const int lb = __ldcs(&b[i]);
+            if ((unsigned)lb >= (unsigned)kb) bad = true;
+            else if (use_smem) atomicAdd(&sh[ka + lb], 1);
+            else atomicAdd(&size_b[lb], 1);
+        }
+    }
+    if (bad) atomicOr(status, 1);
+    if (use_smem) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < ka; i += blockDim.x)
+            if (sh[i]) atomicAdd(&size_a[i], sh[i]);
+        for (int i = threadIdx.x; i < kb; i += blockDim.x)
+            if (sh[ka + i]) atomicAdd(&size_b[i], sh[ka + i]);
+    }
+}
+
+// ------------------------------------------------------------------ scan
+
+// Exclusive prefix of size[0..K) by one block.  Writes start[0..K], optionally
+// cursor = start, and appends ids with size > big_thr to big_list.
+__global__ void k_scan_single(const int *size, int K, int *start, int *cursor, int big_thr,
+                              int *big_list, int *counters, const int *status)
+{
+    __shared__ unsigned long long red[72];
+    if (*status) return;
+    const int T = blockDim.x;
+    const long long per = ((long long)K + T - 1) / T;
+    const long long b = (long long)threadIdx.x * per, e = min(b + per, (long long)K);
+    unsigned sum = 0;
+    for (long long i = b; i < e; ++i) sum += (unsigned)size[i];
+    unsigned excl;
+    const unsigned total = group_exclusive_scan(sum, excl, T, red);
+    unsigned run = excl;
+    for (long long i = b; i < e; ++i) {
+        const int s = size[i];
+        start[i] = (int)run;
+        if (cursor) cursor[i] = (int)run;
+        if (s > big_thr) big_list[atomicAdd(&counters[C_BIG_COUNT], 1)] = (int)i;
+        run += (unsigned)s;
+    }
+    if (threadIdx.x == 0) start[K] = (int)total;
+}
+
+__global__ void k_scan_tiles(const int *size, int K, int *tile_sum, const int *status)
+{
+    __shared__ unsigned long long red[72];
+    if (*status) return;
+    const long long base = (long long)blockIdx.x * SCAN_TILE;
+    unsigned s = 0;
+    for (int j = threadIdx.x; j < SCAN_TILE; j += blockDim.x) {
+        const long long i = base + j;
+        if (i < K) s += (unsigned)size[i];
+    }
+    s = (unsigned)group_sum_u64(s, blockDim.x, red);
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = (int)s;
+}
+
+__global__ void k_scan_apply(const int *size, int K, const int *tile_off, int *start, int *cursor,
+                             int big_thr, int *big_list, int *counters, const int *status)
+{
+    __shared__ unsigned long long red[72];
+    if (*status) return;
+    const int per = SCAN_TILE / blockDim.x;
+    const long long b = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * per;
+    unsigned sum = 0;
+    for (int j = 0; j < per; ++j)
+        if (b + j < K) sum += (unsigned)size[b + j];
+    unsigned excl;
+    group_exclusive_scan(sum, excl, blockDim.x, red);
+    unsigned run = (unsigned)tile_off[blockIdx.x] + excl;
+    for (int j = 0; j < per; ++j) {
+        const long long i = b + j;
+        if (i >= K) break;
+        const int s = size[i];
+        start[i] = (int)run;
+        cursor[i] = (int)run;
+        if (s > big_thr) big_list[atomicAdd(&counters[C_BIG_COUNT], 1)] = (int)i;
+        run += (unsigned)s;
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) start[K] = tile_off[gridDim.x];
+}
+
+// ------------------------------------------------------------------ scatter
+
+__global__ void k_scatter(const int *__restrict__ labels, long long n, int *cursor, int *members,
+                          const int *status)
+{
+    if (*status) return;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int l = __ldg(&labels[i]);
+        const int pos = atomicAdd(&cursor[l], 1);
+        members[pos] = (int)i;
+    }
+}
+
+// ------------------------------------------------------------------ community pass
+
+struct ScoreKArgs {
+    ScoreCtx x;
+    const int *big_list;
+    const int *ovf_in;
+    int *ovf_out;
+    int *counters;
+    unsigned long long *gacc;
+    const int *status;
+    int big_thr;
+    int phase;   // 0: large communities then warps over all ids; 1: overflow list
+    SmemPlan plan;
+};
+
+// Adds the block's per-warp accumulators to the partition's global sums
+// (called by thread 0 after a barrier).
+__device__ __forceinline__ void flush_score(const ScoreAcc *sacc, int W, unsigned long long *g)
+{
+    ScoreAcc t = sacc[0];
+    for (int w = 1; w < W; ++w) score_acc_add(t, sacc[w]);
+    limbs_add(g + GS_QDS_SELF, t.qds_self);
+    limbs_add(g + GS_QDS_PAIR, t.qds_pair);
+    limbs_add(g + GS_DENS, t.dens);
+    limbs_add(g + GS_CONTR, t.contr);
+    limbs_add(g + GS_EXPN, t.expn);
+    limbs_add(g + GS_COND, t.cond);
+    limbs_add(g + GS_VOL2, (i128)t.vol2);
+    if (t.ein) atomicAdd(g + GS_EIN, t.ein);
+    if (t.eout) atomicAdd(g + GS_EOUT, t.eout);
+    if (t.nonempty) atomicAdd(g + GS_NONEMPTY, t.nonempty);
+    if (t.slots) atomicAdd(g + GS_SLOTS, t.slots);
+    if (t.cnt2) atomicAdd(g + GS_CNT2, t.cnt2);
+}
+
+__global__ void __launch_bounds__(1024) k_score_cm(ScoreKArgs a)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ int s_item;
+    if (*a.status) return;
+    const SmemPlan &p = a.plan;
+    unsigned long long *red = (unsigned long long *)(sm + p.red_off);
+    int *ctl = (int *)(sm + p.ctl_off);
+    unsigned *offs = (unsigned *)(sm + p.offs_off);
+    long long *rs = (long long *)(sm + p.rs_off);
+    unsigned long long *slot = (unsigned long long *)(sm + p.slot_off);
+    int *used = (int *)(sm + p.used_off);
+    const int T = blockDim.x, W = T >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    ScoreAcc *sacc = (ScoreAcc *)(sm + p.acc_off);
+    for (int i = threadIdx.x; i < p.cap; i += T) slot[i] = 0ull;
+    for (int i = threadIdx.x; i < 2 * (W + 1); i += T) ctl[i] = 0;
+    for (int i = threadIdx.x; i < W; i += T) score_acc_zero(sacc[i]);
+    __syncthreads();
+
+    const SmemTable tb{slot, used, &ctl[0], &ctl[1], p.cap, p.max_used};
+    const int *list = a.phase == 0 ? a.big_list : a.ovf_in;
+    int *next = &a.counters[a.phase == 0 ? C_BIG_NEXT : C_OVF_NEXT];
+    const int count = a.counters[a.phase == 0 ? C_BIG_COUNT : C_OVF_COUNT];
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int i = atomicAdd(next, 1);
+            s_item = i < count ? list[i] : -1;
+        }
+        __syncthreads();
+        const int c = s_item;
+        __syncthreads();
+        if (c < 0) break;
+        score_community(a.x, c, tb, offs, rs, &sacc[0], threadIdx.x, T, red);
+    }
+    if (a.phase == 0) {
+        const SmemTable tw{slot + wid * p.cap_w, used + wid * p.max_used_w, &ctl[2 + 2 * wid],
+                           &ctl[3 + 2 * wid], p.cap_w, p.max_used_w};
+        unsigned *offw = offs + wid * 33;
+        long long *rsw = rs + wid * 32;
+        for (;;) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&a.counters[C_SMALL_NEXT], 32);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base >= a.x.K) break;
+            const int c = base + lane;
+            int sz = 0;
+            if (c < a.x.K) sz = a.x.start[c + 1] - a.x.start[c];
+            unsigned mask = __ballot_sync(0xffffffffu, sz > 0 && sz <= a.big_thr);
+            while (mask) {
+                const int j = __ffs(mask) - 1;
+                mask &= mask - 1;
+                if (!score_community(a.x, base + j, tw, offw, rsw, &sacc[wid], lane, 32, red)) {
+                    if (lane == 0) a.ovf_out[atomicAdd(&a.counters[C_OVF_COUNT], 1)] = base + j;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) flush_score(sacc, W, a.gacc);
+}
+
+__global__ void k_score_fin(const unsigned long long *g, const int *status, long long n, long long E,
+                            qm_quality *out)
+{
+    if (threadIdx.x != 0 || *status) return;
+    ScoreTotals t;
+    t.qds_self = limbs_get(g + GS_QDS_SELF);
+    t.qds_pair = limbs_get(g + GS_QDS_PAIR);
+    t.dens = limbs_get(g + GS_DENS);
+    t.contr = limbs_get(g + GS_CONTR);
+    t.expn = limbs_get(g + GS_EXPN);
+    t.cond = limbs_get(g + GS_COND);
+    t.vol2 = limbs_get(g + GS_VOL2);
+    t.ein = g[GS_EIN];
+    t.eout = g[GS_EOUT];
+    t.nonempty = g[GS_NONEMPTY];
+    t.slots = g[GS_SLOTS];
+    t.cnt2 = g[GS_CNT2];
+    make_quality(t, n, E, out);
+}
+
+// ------------------------------------------------------------------ compare
+
+struct CompareKArgs {
+    CompareCtx x;
+    const int *big_list;
+    int *counters;
+    unsigned long long *gacc;
+    const int *status;
+    SmemPlan plan;
+};
+
+__device__ __forceinline__ void flush_compare(const CompareAcc &acc, unsigned long long *g,
+                                              unsigned long long *red)
+{
+    const int T = blockDim.x;
+    i128 v;
+    v = group_sum_i128(acc.vi, T, red);
+    if (threadIdx.x == 0) limbs_add(g + GC_VI, v);
+    v = group_sum_i128(acc.hnum, T, red);
+    if (threadIdx.x == 0) limbs_add(g + GC_HNUM, v);
+    v = group_sum_i128(acc.hden, T, red);
+    if (threadIdx.x == 0) limbs_add(g + GC_HDEN, v);
+    v = group_sum_i128(acc.f, T, red);
+    if (threadIdx.x == 0) limbs_add(g + GC_F, v);
+    const unsigned long long *src[7] = {&acc.a11, &acc.sa, &acc.sb, &acc.nvd, &acc.cells, &acc.ka, &acc.kb};
+    const int dst[7] = {GC_A11, GC_SA, GC_SB, GC_NVD, GC_CELLS, GC_KA, GC_KB};
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        const unsigned long long u = group_sum_u64(*src[k], T, red);
+        if (threadIdx.x == 0 && u) atomicAdd(g + dst[k], u);
+    }
+}
+
+__device__ __forceinline__ void flush_compare_one(const CompareAcc &t, unsigned long long *g)
+{
+    limbs_add(g + GC_VI, t.vi);
+    limbs_add(g + GC_HNUM, t.hnum);
+    limbs_add(g + GC_HDEN, t.hden);
+    limbs_add(g + GC_F, t.f);
+    if (t.a11) atomicAdd(g + GC_A11, t.a11);
+    if (t.sa) atomicAdd(g + GC_SA, t.sa);
+    if (t.sb) atomicAdd(g + GC_SB, t.sb);
+    if (t.nvd) atomicAdd(g + GC_NVD, t.nvd);
+    if (t.cells) atomicAdd(g + GC_CELLS, t.cells);
+    if (t.ka) atomicAdd(g + GC_KA, t.ka);
+    if (t.kb) atomicAdd(g + GC_KB, t.kb);
+}
+
+__global__ void __launch_bounds__(1024) k_compare_cm(CompareKArgs a)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ int s_item;
+    if (*a.status) return;
+    const SmemPlan &p = a.plan;
+    unsigned long long *red = (unsigned long long *)(sm + p.red_off);
+    int *ctl = (int *)(sm + p.ctl_off);
+    unsigned long long *slot = (unsigned long long *)(sm + p.slot_off);
+    int *used = (int *)(sm + p.used_off);
+    const int T = blockDim.x, W = T >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    CompareAcc *cacc = (CompareAcc *)(sm + p.acc_off);
+    for (int i = threadIdx.x; i < p.cap; i += T) slot[i] = 0ull;
+    for (int i = threadIdx.x; i < 2 * (W + 1); i += T) ctl[i] = 0;
+    for (int i = threadIdx.x; i < W; i += T) compare_acc_zero(cacc[i]);
+    __syncthreads();
+    const SmemTable tb{slot, used, &ctl[0], &ctl[1], p.cap, p.max_used};
+    const int count = a.counters[C_BIG_COUNT];
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int i = atomicAdd(&a.counters[C_BIG_NEXT], 1);
+            s_item = i < count ? a.big_list[i] : -1;
+        }
+        __syncthreads();
+        const int b = s_item;
+        __syncthreads();
+        if (b < 0) break;
+        compare_community(a.x, b, tb, &cacc[0], threadIdx.x, T, red);
+    }
+    const SmemTable tw{slot + wid * p.cap_w, used + wid * p.max_used_w, &ctl[2 + 2 * wid],
+                       &ctl[3 + 2 * wid], p.cap_w, p.max_used_w};
+    for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&a.counters[C_SMALL_NEXT], 32);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= a.x.kb) break;
+        const int b = base + lane;
+        int sz = 0;
+        if (b < a.x.kb) sz = a.x.start[b + 1] - a.x.start[b];
+        unsigned mask = __ballot_sync(0xffffffffu, sz > 0 && sz <= p.max_used_w);
+        while (mask) {
+            const int j = __ffs(mask) - 1;
+            mask &= mask - 1;
+            compare_community(a.x, base + j, tw, &cacc[wid], lane, 32, red);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        CompareAcc t = cacc[0];
+        for (int w = 1; w < W; ++w) compare_acc_add(t, cacc[w]);
+        flush_compare_one(t, a.gacc);
+    }
+}
+
+__global__ void k_compare_rows(CompareCtx x, unsigned long long *g, const int *status)
+{
+    __shared__ unsigned long long red[72];
+    if (*status) return;
+    CompareAcc acc;
+    compare_acc_zero(acc);
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < x.ka; a += gridDim.x * blockDim.x)
+        compare_row(x, a, acc);
+    flush_compare(acc, g, red);
+}
+
+__global__ void k_compare_fin(const unsigned long long *g, const int *status, long long n, qm_compare *out)
+{
+    if (threadIdx.x != 0 || *status) return;
+    CompareTotals t;
+    t.vi = limbs_get(g + GC_VI);
+    t.hnum = limbs_get(g + GC_HNUM);
+    t.hden = limbs_get(g + GC_HDEN);
+    t.f = limbs_get(g + GC_F);
+    t.a11 = g[GC_A11];
+    t.sa = g[GC_SA];
+    t.sb = g[GC_SB];
+    t.nvd = g[GC_NVD];
+    t.cells = g[GC_CELLS];
+    t.ka = g[GC_KA];
+    t.kb = g[GC_KB];
+    make_compare(t, n, out);
+}
+
+// ------------------------------------------------------------------ graph validation
+
+// Always: row offsets non-decreasing from 0 to n_arcs, column ids in [0, n),
+// maximum degree.  With `full`: rows strictly increasing (no repeated arcs), no
+// self-loops, and the reverse arc (v, u) present (binary search in the sorted
+// row of v).
+__global__ void k_validate(const long long *row_ptr, const int *col, long long n, long long n_arcs,
+                           int full, int *status, unsigned long long *max_deg)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    bool bad = false;
+    unsigned long long md = 0;
+    for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
+        const long long b = row_ptr[u], e = row_ptr[u + 1];
+        if (u == 0 && b != 0) bad = true;
+        if (u == n - 1 && e != n_arcs) bad = true;
+        if (e < b || b < 0 || e > n_arcs) { bad = true; continue; }
+        md = max(md, (unsigned long long)(e - b));
+        for (long long k = b; k < e; ++k) {
+            const int v = col[k];
+            if (v < 0 || v >= n) { bad = true; break; }
+            if (!full) continue;
+            if (v == u || (k > b && col[k - 1] >= v)) { bad = true; break; }
+            long long lo = row_ptr[v], hi = row_ptr[v + 1];
+            if (lo < 0 || hi > n_arcs || hi < lo) { bad = true; break; }
+            bool found = false;
+            while (lo < hi) {
+                const long long mid = (lo + hi) >> 1;
+                const int w = col[mid];
+                if (w == (int)u) { found = true; break; }
+                if (w < (int)u) lo = mid + 1; else hi = mid;
+            }
+            if (!found) { bad = true; break; }
+        }
+    }
+    if (bad) atomicOr(status, 1);
+    for (int d = 16; d > 0; d >>= 1) md = max(md, __shfl_down_sync(0xffffffffu, md, d));
+    if ((threadIdx.x & 31) == 0) atomicMax(max_deg, md);
+}
+
+// ------------------------------------------------------------------ launchers
+
+static int grid_for(long long n, int threads, int num_sms, int per_sm)
+{
+    long long g = (n + threads - 1) / threads;
+    const long long cap = (long long)num_sms * per_sm;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+void prepare_kernels()
+{
+    cudaFuncSetAttribute(k_score_cm, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+    cudaFuncSetAttribute(k_compare_cm, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+}
+
+int score_blocks_per_sm(const Shape &sh)
+{
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_score_cm, sh.threads, sh.smem_bytes);
+    return nb;
+}
+
+static int launch_scan(const int *size, int K, int *start, int *cursor, int big_thr, int *big_list,
+                       int *counters, int *tmp, const int *status, cudaStream_t s)
+{
+    if (K <= SCAN_SINGLE_MAX) {
+        k_scan_single<<<1, 1024, 0, s>>>(size, K, start, cursor, big_thr, big_list, counters, status);
+        return 1;
+    }
+    const int tiles = scan_tiles(K);
+    k_scan_tiles<<<tiles, 1024, 0, s>>>(size, K, tmp, status);
+    // exclusive prefix of the tile sums, in place into tmp[0..tiles] (tmp[tiles] = total)
+    k_scan_single<<<1, 1024, 0, s>>>(tmp, tiles, tmp, nullptr, INT_MAX, nullptr, counters, status);
+    k_scan_apply<<<tiles, 1024, 0, s>>>(size, K, tmp, start, cursor, big_thr, big_list, counters, status);
+    return 3;
+}
+
+int launch_score(const GraphDev &g, const int *labels, int K, const ScoreWs &ws, const Shape &sh,
+                 const PerCommDev *pc, int num_sms, cudaStream_t s)
+{
+    int launches = 0;
+    const long long n = g.n;
+    const int hist_smem = (K <= 12288) ? K * 4 : 0;
+    k_hist<<<grid_for(n, 512, num_sms, 4), 512, hist_smem, s>>>(labels, K, ws.size, nullptr, 0, nullptr, n,
+                                                                ws.status, hist_smem ? 1 : 0);
+    ++launches;
+    launches += launch_scan(ws.size, K, ws.start, ws.cursor, sh.big_community, ws.big_list, ws.counters,
+                            ws.scan_tmp, ws.status, s);
+    k_scatter<<<grid_for(n, 512, num_sms, 8), 512, 0, s>>>(labels, n, ws.cursor, ws.members, ws.status);
+    ++launches;
+
+    ScoreKArgs a;
+    a.x.row_ptr = g.row_ptr;
+    a.x.col = g.col;
+    a.x.labels = labels;
+    a.x.members = ws.members;
+    a.x.start = ws.start;
+    a.x.E = g.n_arcs / 2;
+    a.x.K = K;
+    a.x.err = ws.status;
+    a.x.pc_size = pc ? pc->size : nullptr;
+    a.x.pc_ein = pc ? pc->ein : nullptr;
+    a.x.pc_eout = pc ? pc->eout : nullptr;
+    a.x.pc_dens = pc ? pc->dens : nullptr;
+    a.x.pc_contr = pc ? pc->contr : nullptr;
+    a.x.pc_expn = pc ? pc->expn : nullptr;
+    a.x.pc_cond = pc ? pc->cond : nullptr;
+    a.x.pc_qds = pc ? pc->qds : nullptr;
+    a.big_list = ws.big_list;
+    a.ovf_in = ws.ovf_list;
+    a.ovf_out = ws.ovf_list;
+    a.counters = ws.counters;
+    a.gacc = ws.gacc;
+    a.status = ws.status;
+    a.big_thr = sh.big_community;
+    a.plan = plan_smem(sh.threads, sh.smem_bytes);
+    const int blocks = num_sms * (sh.blocks_per_sm > 0 ? sh.blocks_per_sm : 1);
+    a.phase = 0;
+    k_score_cm<<<blocks, sh.threads, sh.smem_bytes, s>>>(a);
+    a.phase = 1;
+    k_score_cm<<<blocks, sh.threads, sh.smem_bytes, s>>>(a);
+    k_score_fin<<<1, 32, 0, s>>>(ws.gacc, ws.status, n, g.n_arcs / 2, ws.result);
+    launches += 3;
+    return cudaGetLastError() == cudaSuccess ? launches : -1;
+}
+
+int launch_compare(const int *truth, const int *found, long long n, int ka, int kb,
+                   const CompareWs &ws, const Shape &sh, int num_sms, cudaStream_t s)
+{
+    int launches = 0;
+    const int hist_smem = (ka + kb <= 12288) ? (ka + kb) * 4 : 0;
+    k_hist<<<grid_for(n, 512, num_sms, 4), 512, hist_smem, s>>>(truth, ka, ws.size_a, found, kb, ws.size_b, n,
+                                                                ws.status, hist_smem ? 1 : 0);
+    ++launches;
+    const SmemPlan plan = plan_smem(sh.threads, sh.smem_bytes);
+    launches += launch_scan(ws.size_b, kb, ws.start, ws.cursor, plan.max_used_w, ws.big_list, ws.counters,
+                            ws.scan_tmp, ws.status, s);
+    k_scatter<<<grid_for(n, 512, num_sms, 8), 512, 0, s>>>(found, n, ws.cursor, ws.members, ws.status);
+    ++launches;
+    CompareKArgs a;
+    a.x.truth = truth;
+    a.x.members = ws.members;
+    a.x.start = ws.start;
+    a.x.size_a = ws.size_a;
+    a.x.rowmax_n = ws.rowmax_n;
+    a.x.rowmax_r = ws.rowmax_r;
+    a.x.N = n;
+    a.x.ka = ka;
+    a.x.kb = kb;
+    a.x.err = ws.status;
+    a.big_list = ws.big_list;
+    a.counters = ws.counters;
+    a.gacc = ws.gacc;
+    a.status = ws.status;
+    a.plan = plan;
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_compare_cm, sh.threads, sh.smem_bytes);
+    if (nb < 1) nb = 1;
+    k_compare_cm<<<num_sms * nb, sh.threads, sh.smem_bytes, s>>>(a);
+    k_compare_rows<<<grid_for(ka, 256, num_sms, 2), 256, 0, s>>>(a.x, ws.gacc, ws.status);
+    k_compare_fin<<<1, 32, 0, s>>>(ws.gacc, ws.status, n, ws.result);
+    launches += 3;
+    return cudaGetLastError() == cudaSuccess ? launches : -1;
+}
+
+int launch_validate(const GraphDev &g, int full, int *status, unsigned long long *max_deg, int num_sms,
+                    cudaStream_t s)
+{
+    k_validate<<<grid_for(g.n, 256, num_sms, 8), 256, 0, s>>>(g.row_ptr, g.col, g.n, g.n_arcs, full, status,
+                                                              max_deg);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+}  // namespace qm

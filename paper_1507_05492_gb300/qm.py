@@ -1,0 +1,338 @@
+"""Python binding of libqm.so (include/qm.h): argument marshalling only.
+
+Every metric is computed by the CUDA kernels behind the C ABI; this module only
+converts tensors/arrays to pointers and C structs to dicts.  There is no CPU
+fallback: if the library is not built, every call raises ``LibraryMissing``.
+
+Low-level functions carry the C names (``qm_load_graph``, ``qm_score_partition``
+...).  The ``Graph`` class and the ``score`` / ``compare`` / ``evaluate_batched``
+helpers wrap them for tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libqm.so")
+
+QM_OK, QM_EINVAL, QM_ENOMEM, QM_ECUDA, QM_ETIMEOUT, QM_EOVERFLOW, QM_EBUSY = range(7)
+QM_HOST, QM_DEVICE = 0, 1
+QM_VALIDATE = 1
+QM_SHARED_TRUTH = 1
+
+
+class LibraryMissing(RuntimeError):
+    pass
+
+
+class QmError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: status {status} ({detail})")
+        self.status = status
+
+
+class QmQuality(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "n_nodes", "n_edges", "n_communities_nonempty", "intra_edges_total", "cut_edges_total",
+        "n_community_pairs", "pair_count_sq_sum")] + [(n, ctypes.c_double) for n in (
+        "modularity", "modularity_density", "mean_intra_edges", "mean_intra_density",
+        "mean_contraction", "mean_inter_edges", "mean_expansion", "mean_conductance")]
+
+
+class QmCompare(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "n_nodes", "k_truth", "k_found", "n_cells", "a11", "a10", "a01", "a00", "nvd_sum")] + [
+        (n, ctypes.c_double) for n in ("vi", "nmi", "f_measure", "nvd", "ri", "ari", "ji")]
+
+
+class QmPercomm(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in (
+        "size", "intra_edges", "inter_edges", "intra_density", "contraction", "expansion",
+        "conductance", "qds_term")]
+
+
+class QmTuning(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("threads", "smem_bytes", "big_community", "blocks_per_sm")]
+
+
+_lib = None
+_lock = threading.Lock()
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+
+
+def _signatures(lib):
+    S = ctypes.c_int
+    table = {
+        "qm_load_graph": [_P, _P, _I64, _I64, S, ctypes.c_uint, _P, ctypes.POINTER(_P)],
+        "qm_free_graph": [_P],
+        "qm_graph_info": [_P, _P, _P, _P, _P],
+        "qm_score_partition": [_P, _P, _I32, S, _P, _P, _P],
+        "qm_compare_partitions": [_P, _P, _I64, _I32, _I32, S, _P, _P],
+        "qm_score_partitions_batched": [_P, _P, _I32, _P, S, _P, _P],
+        "qm_compare_partitions_batched": [_P, _P, _I64, _I32, _P, _P, ctypes.c_uint, S, _P, _P],
+        "qm_evaluate_partitions_batched": [_P, _P, _I32, _P, _P, _I32, S, _P, _P, _P],
+        "qm_score_graphs_batched": [_P, _P, _P, _I32, S, _P, _P],
+        "qm_workspace_bytes": [_P, _I32, _I32, _I32, _P],
+        "qm_release_cache": [],
+        "qm_autotune": [_P, _P, _I32, S, _P, _P],
+        "qm_get_tuning": [_P, _I32, _P],
+        "qm_set_tuning": [_P, _I32, _P],
+        "qm_last_error": [_P, ctypes.c_size_t],
+    }
+    for name, args in table.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.qm_strerror.argtypes = [ctypes.c_int]
+    lib.qm_strerror.restype = ctypes.c_char_p
+    lib.qm_kernel_launches.argtypes = []
+    lib.qm_kernel_launches.restype = ctypes.c_int64
+
+
+def lib():
+    """The loaded libqm.so; raises LibraryMissing when it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise LibraryMissing(f"{LIB_PATH} is not built; run __graft_entry__.build() "
+                                     "or python -m paper_1507_05492_gb300.build")
+            l = ctypes.CDLL(LIB_PATH)
+            _signatures(l)
+            _lib = l
+    return _lib
+
+
+def last_error() -> str:
+    buf = ctypes.create_string_buffer(512)
+    lib().qm_last_error(buf, 512)
+    return buf.value.decode(errors="replace")
+
+
+def _check(rc: int, where: str):
+    if rc != QM_OK:
+        raise QmError(rc, where, last_error())
+
+
+def kernel_launches() -> int:
+    return int(lib().qm_kernel_launches())
+
+
+# ------------------------------------------------------------------ marshalling
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return torch.cuda.current_stream().cuda_stream or None
+        return None
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream or None
+    return int(stream) or None
+
+
+def _labels_arg(x, name="labels"):
+    """Returns (pointer, memory kind, keep-alive object) for an int32 label array."""
+    if isinstance(x, torch.Tensor):
+        if x.dtype != torch.int32 or not x.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous int32 tensor")
+        return x.data_ptr(), (QM_DEVICE if x.is_cuda else QM_HOST), x
+    a = np.ascontiguousarray(np.asarray(x), dtype=np.int32)
+    return a.ctypes.data, QM_HOST, a
+
+
+def _struct_dict(s) -> dict:
+    return {name: getattr(s, name) for name, _ in s._fields_}
+
+
+# ------------------------------------------------------------------ graph
+
+class Graph:
+    """A symmetric CSR graph resident on the current CUDA device."""
+
+    def __init__(self, row_ptr, col, validate: bool = False, stream=None):
+        if isinstance(row_ptr, torch.Tensor):
+            rp = row_ptr.contiguous().to(torch.int64)
+            cl = col.contiguous().to(torch.int32)
+            where = QM_DEVICE if rp.is_cuda else QM_HOST
+            if (where == QM_DEVICE) != cl.is_cuda:
+                raise ValueError("row_ptr and col must live in the same memory")
+            keep = (rp, cl)
+            prp, pcl = rp.data_ptr(), cl.data_ptr()
+            n, arcs = rp.numel() - 1, cl.numel()
+        else:
+            rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+            cl = np.ascontiguousarray(col, dtype=np.int32)
+            keep = (rp, cl)
+            prp, pcl = rp.ctypes.data, cl.ctypes.data
+            where = QM_HOST
+            n, arcs = len(rp) - 1, len(cl)
+        h = ctypes.c_void_p()
+        _check(lib().qm_load_graph(prp, pcl, n, arcs, where, QM_VALIDATE if validate else 0,
+                                   _stream_ptr(stream), ctypes.byref(h)), "qm_load_graph")
+        del keep
+        self.handle = h
+        self.n = n
+        self.n_arcs = arcs
+        self.n_edges = arcs // 2
+
+    def info(self) -> dict:
+        vals = [ctypes.c_int64() for _ in range(3)]
+        nbytes = ctypes.c_size_t()
+        _check(lib().qm_graph_info(self.handle, *[ctypes.byref(v) for v in vals], ctypes.byref(nbytes)),
+               "qm_graph_info")
+        return dict(n_nodes=vals[0].value, n_edges=vals[1].value, max_degree=vals[2].value,
+                    device_bytes=nbytes.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().qm_free_graph(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ calls
+
+def score(graph: Graph, labels, K: int, per_community: bool = False, stream=None) -> dict:
+    """qm_score_partition: Q, Qds and the six measures of one partition."""
+    ptr, where, keep = _labels_arg(labels)
+    out = QmQuality()
+    pc = None
+    arrays = None
+    if per_community:
+        dev = where == QM_DEVICE
+        mk = (lambda dt: torch.empty(K, dtype=dt, device=labels.device)) if dev else \
+            (lambda dt: np.empty(K, dtype=np.int64 if dt is torch.int64 else np.float64))
+        names = ["size", "intra_edges", "inter_edges", "intra_density", "contraction", "expansion",
+                 "conductance", "qds_term"]
+        arrays = {k: mk(torch.int64 if i < 3 else torch.float64) for i, k in enumerate(names)}
+        ptrs = [(a.data_ptr() if dev else a.ctypes.data) for a in arrays.values()]
+        pc = QmPercomm(*ptrs)
+    rc = lib().qm_score_partition(graph.handle, ptr, int(K), where, ctypes.byref(out),
+                                  ctypes.byref(pc) if pc is not None else None, _stream_ptr(stream))
+    del keep
+    _check(rc, "qm_score_partition")
+    d = _struct_dict(out)
+    if arrays is not None:
+        d["per_community"] = arrays
+    return d
+
+
+def compare(truth, found, k_truth: int, k_found: int, stream=None) -> dict:
+    """qm_compare_partitions: Eqs. (1)-(7) for ground truth ``truth`` and detected ``found``."""
+    pt, wt, kt_ = _labels_arg(truth, "truth")
+    pf, wf, kf_ = _labels_arg(found, "found")
+    if wt != wf:
+        raise ValueError("truth and found must live in the same memory")
+    n = kt_.numel() if isinstance(kt_, torch.Tensor) else len(kt_)
+    out = QmCompare()
+    rc = lib().qm_compare_partitions(pt, pf, n, int(k_truth), int(k_found), wt, ctypes.byref(out),
+                                     _stream_ptr(stream))
+    _check(rc, "qm_compare_partitions")
+    return _struct_dict(out)
+
+
+def _k_array(K, P):
+    k = np.ascontiguousarray(np.broadcast_to(np.asarray(K, dtype=np.int32), (P,)))
+    return k
+
+
+def score_batched(graph: Graph, labels, K, stream=None) -> list[dict]:
+    """qm_score_partitions_batched over a [P, n] int32 label matrix."""
+    ptr, where, keep = _labels_arg(labels)
+    P = labels.shape[0]
+    k = _k_array(K, P)
+    out = (QmQuality * P)()
+    _check(lib().qm_score_partitions_batched(graph.handle, ptr, P, k.ctypes.data, where, out,
+                                             _stream_ptr(stream)), "qm_score_partitions_batched")
+    return [_struct_dict(o) for o in out]
+
+
+def evaluate_batched(graph: Graph, labels, K, truth, k_truth: int, stream=None):
+    """qm_evaluate_partitions_batched: (quality list, compare list) for P candidates."""
+    ptr, where, keep = _labels_arg(labels)
+    pt, wt, keep_t = _labels_arg(truth, "truth")
+    if wt != where:
+        raise ValueError("labels and truth must live in the same memory")
+    P = labels.shape[0]
+    k = _k_array(K, P)
+    oq = (QmQuality * P)()
+    oc = (QmCompare * P)()
+    _check(lib().qm_evaluate_partitions_batched(graph.handle, ptr, P, k.ctypes.data, pt, int(k_truth), where,
+                                                oq, oc, _stream_ptr(stream)), "qm_evaluate_partitions_batched")
+    return [_struct_dict(o) for o in oq], [_struct_dict(o) for o in oc]
+
+
+def compare_batched(truth, found, k_truth, k_found, shared_truth: bool = True, stream=None) -> list[dict]:
+    """qm_compare_partitions_batched over a [P, n] detected-label matrix."""
+    pf, wf, keep_f = _labels_arg(found, "found")
+    pt, wt, keep_t = _labels_arg(truth, "truth")
+    if wt != wf:
+        raise ValueError("truth and found must live in the same memory")
+    P, n = found.shape[0], found.shape[1]
+    kt = _k_array(k_truth, 1 if shared_truth else P)
+    kf = _k_array(k_found, P)
+    out = (QmCompare * P)()
+    _check(lib().qm_compare_partitions_batched(pt, pf, n, P, kt.ctypes.data, kf.ctypes.data,
+                                               QM_SHARED_TRUTH if shared_truth else 0, wf, out,
+                                               _stream_ptr(stream)), "qm_compare_partitions_batched")
+    return [_struct_dict(o) for o in out]
+
+
+def score_graphs_batched(graphs: list[Graph], labels: list, K: list[int], stream=None) -> list[dict]:
+    """qm_score_graphs_batched: one partition on each of several graphs."""
+    count = len(graphs)
+    args = [_labels_arg(l) for l in labels]
+    kinds = {a[1] for a in args}
+    if len(kinds) != 1:
+        raise ValueError("all label arrays must live in the same memory")
+    gs = (ctypes.c_void_p * count)(*[g.handle.value for g in graphs])
+    ls = (ctypes.c_void_p * count)(*[a[0] for a in args])
+    k = np.ascontiguousarray(K, dtype=np.int32)
+    out = (QmQuality * count)()
+    _check(lib().qm_score_graphs_batched(gs, ls, k.ctypes.data, count, kinds.pop(), out, _stream_ptr(stream)),
+           "qm_score_graphs_batched")
+    return [_struct_dict(o) for o in out]
+
+
+def workspace_bytes(graph: Graph, K: int, k_truth: int | None = None) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().qm_workspace_bytes(graph.handle, int(K), 1 if k_truth else 0, int(k_truth or 0),
+                                    ctypes.byref(b)), "qm_workspace_bytes")
+    return b.value
+
+
+def autotune(graph: Graph, labels, K: int, stream=None) -> dict:
+    ptr, where, keep = _labels_arg(labels)
+    t = QmTuning()
+    _check(lib().qm_autotune(graph.handle, ptr, int(K), where, _stream_ptr(stream), ctypes.byref(t)),
+           "qm_autotune")
+    return _struct_dict(t)
+
+
+def get_tuning(graph: Graph, K: int) -> dict:
+    t = QmTuning()
+    _check(lib().qm_get_tuning(graph.handle, int(K), ctypes.byref(t)), "qm_get_tuning")
+    return _struct_dict(t)
+
+
+def set_tuning(graph: Graph, K: int, threads: int, smem_bytes: int, big_community: int):
+    t = QmTuning(threads, smem_bytes, big_community, 0)
+    _check(lib().qm_set_tuning(graph.handle, int(K), ctypes.byref(t)), "qm_set_tuning")
+
+
+def release_cache():
+    _check(lib().qm_release_cache(), "qm_release_cache")

@@ -1,0 +1,96 @@
+"""The batched persistent launch: every result must equal, bit for bit, the
+plain one-partition call on the same inputs (which itself matches the oracle)."""
+import numpy as np
+import pytest
+import torch
+
+from helpers import check_compare, check_quality, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qm():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1507_05492_gb300 import qm as q
+    return q
+
+
+@pytest.fixture(scope="module")
+def setup(qm):
+    from paper_1507_05492_gb300 import gen
+    g = gen.lfr_graph(gen.LfrParams(n=20_000, seed=21))
+    graph = qm.Graph(*to_dev(g.row_ptr, g.col))
+    labs, Ks = [], []
+    for p in range(24):
+        lab, K, _ = gen.candidate_partition(g.labels, seed=10_000 + p, k_range=(100, 1200))
+        labs.append(lab)
+        Ks.append(K)
+    # pad the label matrix: each row keeps its own K
+    L = torch.stack(labs)
+    return g, graph, L, Ks
+
+
+def test_score_batched_equals_plain(qm, setup, oracle_mod):
+    g, graph, L, Ks = setup
+    out = qm.score_batched(graph, L.cuda(), Ks)
+    for p in range(L.shape[0]):
+        plain = qm.score(graph, L[p].cuda(), Ks[p])
+        assert out[p] == plain, p
+    o = oracle_mod.score(g.row_ptr.numpy(), g.col.numpy(), L[3].numpy(), Ks[3])
+    check_quality(out[3], o, "batched p=3")
+
+
+def test_evaluate_batched_equals_plain(qm, setup, oracle_mod):
+    g, graph, L, Ks = setup
+    truth = g.labels.cuda()
+    oq, oc = qm.evaluate_batched(graph, L.cuda(), Ks, truth, g.K)
+    for p in range(L.shape[0]):
+        assert oq[p] == qm.score(graph, L[p].cuda(), Ks[p]), p
+        assert oc[p] == qm.compare(truth, L[p].cuda(), g.K, Ks[p]), p
+    check_compare(oc[5], oracle_mod.compare(g.labels.numpy(), L[5].numpy(), g.K, Ks[5]), "p=5")
+    # host inputs give the same bits
+    oq2, oc2 = qm.evaluate_batched(graph, L.numpy(), Ks, g.labels.numpy(), g.K)
+    assert oq2 == oq and oc2 == oc
+    # repeated launches replay the captured graph with identical results
+    oq3, oc3 = qm.evaluate_batched(graph, L.cuda(), Ks, truth, g.K)
+    assert oq3 == oq and oc3 == oc
+
+
+def test_compare_batched(qm, setup):
+    g, graph, L, Ks = setup
+    shared = qm.compare_batched(g.labels.cuda(), L.cuda(), g.K, Ks, shared_truth=True)
+    per = qm.compare_batched(g.labels.expand(L.shape[0], -1).contiguous().cuda(), L.cuda(),
+                             [g.K] * L.shape[0], Ks, shared_truth=False)
+    for p in range(L.shape[0]):
+        plain = qm.compare(g.labels.cuda(), L[p].cuda(), g.K, Ks[p])
+        assert shared[p] == plain and per[p] == plain, p
+
+
+def test_graphs_of_uneven_sizes(qm, oracle_mod):
+    from paper_1507_05492_gb300 import gen
+    gs, graphs, labs, Ks = [], [], [], []
+    for i, n in enumerate((500, 7_000, 31_337, 2_000, 64_000)):
+        g = gen.lfr_graph(gen.LfrParams(n=n, seed=30 + i))
+        gs.append(g)
+        graphs.append(qm.Graph(*to_dev(g.row_ptr, g.col)))
+        lab = gen.perturb(g.labels, g.K, 0.05 * i, seed=40 + i)
+        labs.append(lab.cuda())
+        Ks.append(g.K)
+    out = qm.score_graphs_batched(graphs, labs, Ks)
+    for i in range(len(gs)):
+        assert out[i] == qm.score(graphs[i], labs[i], Ks[i]), i
+        o = oracle_mod.score(gs[i].row_ptr.numpy(), gs[i].col.numpy(), labs[i].cpu().numpy(), Ks[i])
+        check_quality(out[i], o, f"graph {i}")
+
+
+def test_batched_rejects_bad_item(qm, setup):
+    g, graph, L, Ks = setup
+    bad = L.clone()
+    bad[7, 11] = Ks[7]
+    with pytest.raises(qm.QmError) as e:
+        qm.score_batched(graph, bad.cuda(), Ks)
+    assert e.value.status == qm.QM_EINVAL
+    out = qm.score_batched(graph, L.cuda(), Ks)  # still usable
+    assert out[0] == qm.score(graph, L[0].cuda(), Ks[0])

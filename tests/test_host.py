@@ -1,0 +1,123 @@
+"""Host-side checks that need no GPU: the C ABI library builds and exports every
+entry point declared in include/qm.h, and the seeded workload generator makes
+the inputs it promises."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "qm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qm_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1507_05492_gb300 import build
+    return build.build()
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    syms = declared_symbols()
+    assert len(syms) >= 15
+    lib = ctypes.CDLL(libpath)
+    missing = [s for s in syms if not hasattr(lib, s)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (qm_\w+)", out))
+    assert set(syms) <= exported
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    from paper_1507_05492_gb300 import qm
+    monkeypatch.setattr(qm, "_lib", None)
+    monkeypatch.setattr(qm, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(qm.LibraryMissing):
+        qm.lib()
+
+
+def test_strerror_without_gpu(libpath):
+    lib = ctypes.CDLL(libpath)
+    lib.qm_strerror.restype = ctypes.c_char_p
+    assert lib.qm_strerror(0) == b"ok"
+    assert lib.qm_strerror(1) == b"invalid argument"
+
+
+def test_host_argument_checks_without_gpu(libpath):
+    """Argument errors are reported before any device work."""
+    from paper_1507_05492_gb300 import qm
+    l = qm.lib()
+    out = qm.QmCompare()
+    a = np.zeros(1, np.int32)
+    assert l.qm_compare_partitions(a.ctypes.data, a.ctypes.data, 1, 1, 1, qm.QM_HOST, ctypes.byref(out), None) \
+        == qm.QM_EINVAL
+    assert "n_nodes" in qm.last_error()
+    h = ctypes.c_void_p()
+    rp = np.array([0, 1], np.int64)
+    col = np.array([0], np.int32)
+    assert l.qm_load_graph(rp.ctypes.data, col.ctypes.data, 1, 1, qm.QM_HOST, 0, None, ctypes.byref(h)) \
+        == qm.QM_EINVAL
+    assert l.qm_load_graph(rp.ctypes.data, col.ctypes.data, 1 << 31, 2, qm.QM_HOST, 0, None, ctypes.byref(h)) \
+        == qm.QM_EOVERFLOW
+
+
+# ------------------------------------------------------------------ generator
+
+def test_generator_graph_is_simple_symmetric(oracle_mod):
+    from paper_1507_05492_gb300 import gen
+    g = gen.lfr_graph(gen.config_params("lfr10k"))
+    assert g.n == 10_000 and g.row_ptr[0] == 0 and g.row_ptr[-1] == g.col.numel()
+    assert oracle_mod.validate_graph(g.row_ptr.numpy(), g.col.numpy())
+    deg = (g.row_ptr[1:] - g.row_ptr[:-1]).numpy()
+    assert deg.max() <= 50
+    assert 16.0 <= deg.mean() <= 20.5
+    sizes = np.bincount(g.labels.numpy())
+    assert sizes.sum() == g.n and (sizes > 0).all() and len(sizes) == g.K
+    assert sizes.min() >= 20
+    mu = gen.mixing_fraction(g)
+    assert 0.25 <= mu <= 0.4
+
+
+def test_generator_is_deterministic_and_seeded():
+    from paper_1507_05492_gb300 import gen
+    p = gen.LfrParams(n=3000, seed=9)
+    a, b = gen.lfr_graph(p), gen.lfr_graph(p)
+    assert torch.equal(a.row_ptr, b.row_ptr) and torch.equal(a.col, b.col) and torch.equal(a.labels, b.labels)
+    c = gen.lfr_graph(gen.LfrParams(n=3000, seed=10))
+    assert not torch.equal(a.col[:1000], c.col[:1000]) or not torch.equal(a.labels, c.labels)
+
+
+def test_generator_degree_power_law_mean():
+    from paper_1507_05492_gb300 import gen
+    x = gen.solve_xmin(20.0, 50, 2.0)
+    assert abs(x - 9.9) < 0.2          # mean of x^-2 on [x, 50] is 20
+    x = gen.solve_xmin(20.0, 100, 2.0)
+    assert abs(x - 7.0) < 0.1
+
+
+def test_perturb_moves_exact_count():
+    from paper_1507_05492_gb300 import gen
+    lab = torch.randint(0, 50, (10_000,), dtype=torch.int32)
+    b = gen.perturb(lab, 50, 0.1, seed=3)
+    moved = (b != lab)
+    assert int(moved.sum()) == 1000
+    assert int(b.max()) < 50 and int(b.min()) >= 0
+
+
+def test_merge_split_reaches_target():
+    from paper_1507_05492_gb300 import gen
+    g = gen.lfr_graph(gen.LfrParams(n=20_000, seed=4))
+    for k_t in (50, g.K, 3 * g.K):
+        lab, K = gen.merge_split(g.labels, k_t, seed=5)
+        assert K == k_t == int(lab.max()) + 1
+        assert len(np.unique(lab.numpy())) == K
+    lab, K, f = gen.candidate_partition(g.labels, seed=10001)
+    assert 0 <= f <= 0.5 and K == int(lab.max()) + 1
