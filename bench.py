@@ -1,0 +1,450 @@
+#!/usr/bin/env python
+"""Benchmark of the community-quality library on GB300.
+
+Headline: edges scored per second, all metrics without ground truth (Q, Qds with
+its |E_ij| pair counts, the six Sec. II-B.3 measures), one qm_score_partition
+call per step on a seeded LFR-style graph of 100M nodes (mean degree 20, max
+100, mu = 0.3, communities of 20-1000 nodes) with its planted partition; graph
+and labels resident in HBM.  Inputs (8 GB of CSR) are far larger than L2.
+
+Also reported on the same JSON line:
+  roofline      the community-major kernel's algorithmic GB/s (8|E| + 12|V| bytes
+                per launch) from CUDA events around it on its own stream, against
+                the measured HBM copy bandwidth;
+  e2e           the same metric through the C ABI with labels in pinned host
+                memory (H2D of the labels and D2H of the result in every step);
+  cpu_baseline  the CPU oracle (single thread) on a bounded sample;
+  extras        batched (1,024 candidates per launch, one persistent graph-
+                captured kernel) vs plain per-call scoring, and the serving loop.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank scores its own replica of the workload (weak scaling,
+no collective on the data path); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "edges scored/s (all metrics) at 100M nodes"
+UNIT = "edges/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+PROFILE_FILE = os.path.join(ROOT, "profiles", "k_score_cm_lfr100m.md")
+FALLBACK_HBM = 6800.0
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1507_05492_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def hbm_peak():
+    try:
+        return float(json.load(open(PEAKS_FILE))["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+def recorded_traffic():
+    """Per-launch DRAM bytes of k_score_cm from the committed ncu summary, or
+    None when the kernel sources changed since it was captured."""
+    try:
+        text = open(PROFILE_FILE).read()
+        start = text.index("```json") + len("```json")
+        rec = json.loads(text[start:text.index("```", start)])
+        if rec.get("source_hash") == kernel_source_hash():
+            return float(rec["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during a timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"], stdout=open(self.path, "w"),
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(name)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ distributed plumbing
+
+def dist_setup(n_gpus: int):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        if torch.cuda.is_available():
+            torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dist.barrier(device_ids=[torch.cuda.current_device()])
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ CPU oracle baseline
+
+def oracle_sample(n_sample: int, device):
+    """A bounded sample of the workload: the same LFR-style generator and
+    parameters at n_sample nodes, planted partition."""
+    from paper_1507_05492_gb300 import gen
+    p = gen.config_params("lfr100m")
+    p.n = n_sample
+    p.seed = 303
+    g = gen.lfr_graph(p, device=device)
+    return g.row_ptr.cpu().numpy(), g.col.cpu().numpy(), g.labels.cpu().numpy(), g.K
+
+
+def time_oracle(rp, col, lab, K, reps=1):
+    from oracle import oracle
+    oracle.build()
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.score(rp, col, lab, K)
+        ts.append(time.perf_counter() - t0)
+    return statistics.median(ts)
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    """The oracle as it stands, timed on the host cores, on a bounded sample of
+    the workload (each step one oracle scoring of the sample)."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    rp, col, lab, K = oracle_sample(args.cpu_sample_nodes, dev)
+    E = len(col) // 2
+    for _ in range(args.warmup):
+        time_oracle(rp, col, lab, K)
+    ts = [time_oracle(rp, col, lab, K) for _ in range(args.steps)]
+    total = sum(ts)
+    value = E * args.steps / total
+    sample = (f"LFR-style graph with the 100M-node workload's parameters at {args.cpu_sample_nodes} nodes "
+              f"(|E| = {E}), planted partition; one oracle scoring per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64",
+        "data": "synthetic", "config": {"workload": "lfr100m (bounded sample, see cpu_baseline)",
+                                        "sample_nodes": args.cpu_sample_nodes, "n_edges": E},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+
+def bench_headline(args, world, rank, local):
+    import torch
+    from paper_1507_05492_gb300 import gen, qm
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    p = gen.config_params(args.workload)
+    t_gen = time.perf_counter()
+    g = gen.lfr_graph(p, device=dev)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    graph = qm.Graph(g.row_ptr, g.col)
+    n, E, K = g.n, g.n_edges, g.K
+    max_deg = graph.info()["max_degree"]
+    labels = g.labels
+    del g
+    torch.cuda.empty_cache()
+    stream = torch.cuda.current_stream()
+
+    # warm-up (also selects the launch shape)
+    for _ in range(args.warmup):
+        q = qm.score(graph, labels, K)
+    barrier(world)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    clocks.start()
+    qm.trace_enable(True)
+    l0 = qm.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    cm_ms, step_kernels = [], []
+    for _ in range(args.steps):
+        q = qm.score(graph, labels, K)
+        tr = qm.trace_read()
+        cm_ms.append(sum(ms for name, ms in tr if name == "k_score_cm"))
+        step_kernels.append(tr)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = qm.kernel_launches() - l0
+    qm.trace_enable(False)
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    ms_max = max_over_ranks(ms, world)
+    edges_all = sum_over_ranks(float(E) * args.steps, world)
+    value = edges_all / (ms_max / 1e3)
+
+    # end to end through the C ABI with host buffers
+    lab_h = labels.cpu().pin_memory()
+    for _ in range(2):
+        qm.score(graph, lab_h, K)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for _ in range(args.steps):
+        qe = qm.score(graph, lab_h, K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    barrier(world)
+    e2e_ms = max_over_ranks(max(e0.elapsed_time(e1), wall * 1e3), world)
+    assert qe == q, "host-buffer path differs from the device path"
+    e2e_value = edges_all / (e2e_ms / 1e3)
+
+    peak, peak_kind = hbm_peak()
+    b_alg = 8.0 * E + 12.0 * n
+    cm_avg = statistics.mean(cm_ms)
+    achieved = b_alg / (cm_avg / 1e3) / 1e9
+    kernel_shares = {}
+    for tr in step_kernels:
+        for name, t in tr:
+            kernel_shares[name] = kernel_shares.get(name, 0.0) + t
+    total_k = sum(kernel_shares.values()) or 1.0
+    res = dict(
+        value=value, ms_per_step=ms_max / args.steps, launches=launches,
+        e2e={"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * n,
+             "d2h_bytes_per_step": 4 + 120},
+        roofline={"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                  "frac": achieved / peak, "traffic": recorded_traffic(),
+                  "kernel": "k_score_cm", "peak_kind": f"{peak_kind} (burst copy)",
+                  "algorithmic_bytes_per_launch": b_alg, "kernel_ms": cm_avg,
+                  "step_algorithmic_gbs": b_alg / (ms_max / args.steps / 1e3) / 1e9},
+        clocks=clk,
+        config={"workload": f"{args.workload}: LFR-style, n={n}, |E|={E}, K={K}, max degree {max_deg}, "
+                            f"mean degree 20 target, mu=0.3, communities 20-1000, planted partition",
+                "n_nodes": n, "n_edges": E, "n_communities": K, "seed": p.seed,
+                "l2": "inputs (CSR 8 GB + labels 0.4 GB) far larger than the 129 MB L2",
+                "generation_s": round(t_gen, 1)},
+        kernel_share={k: round(v / total_k, 4) for k, v in sorted(kernel_shares.items(), key=lambda x: -x[1])},
+        result={k: q[k] for k in ("modularity", "modularity_density", "mean_conductance",
+                                  "n_community_pairs", "cut_edges_total")},
+    )
+    graph.close()
+    del labels, lab_h
+    torch.cuda.empty_cache()
+    return res
+
+
+def bench_batched(args):
+    """1,024 candidate partitions of 100k-node graphs (mu 0.1 / 0.3 / 0.5): one
+    persistent graph-captured launch per graph (all metrics with and without
+    ground truth) against the plain loop of one score + one compare call each."""
+    import torch
+    from paper_1507_05492_gb300 import gen, qm
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = {}
+    for name in ("lfr100k_mu01", "lfr100k_mu03", "lfr100k_mu05"):
+        g = gen.lfr_graph(gen.config_params(name), device=dev)
+        graph = qm.Graph(g.row_ptr, g.col)
+        t0 = time.perf_counter()
+        labs, Ks = gen.candidate_batch(g.labels, args.batch, seed=10_000)
+        t_cand = time.perf_counter() - t0
+        truth = g.labels
+        for _ in range(2):
+            oq, oc = qm.evaluate_batched(graph, labs, Ks, truth, g.K)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = 3
+        for _ in range(reps):
+            oq, oc = qm.evaluate_batched(graph, labs, Ks, truth, g.K)
+        t_b = (time.perf_counter() - t0) / reps
+        # the plain loop over the same candidates (and a bit-for-bit check)
+        n_plain = min(args.batch, args.plain_sample)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        same = True
+        for p in range(n_plain):
+            pq = qm.score(graph, labs[p], Ks[p])
+            pc = qm.compare(truth, labs[p], g.K, Ks[p])
+            same &= (pq == oq[p]) and (pc == oc[p])
+        t_p = (time.perf_counter() - t0) / n_plain
+        out[name] = {"partitions_per_s_batched": args.batch / t_b,
+                     "partitions_per_s_plain": 1.0 / t_p,
+                     "speedup": (args.batch / t_b) * t_p,
+                     "ms_per_launch": t_b * 1e3, "identical_to_plain": bool(same),
+                     "plain_checked": n_plain, "K_range": [int(min(Ks)), int(max(Ks))],
+                     "candidate_generation_s": round(t_cand, 1),
+                     "edge_scorings_per_s": args.batch * g.n_edges / t_b}
+        graph.close()
+        del g, labs
+        torch.cuda.empty_cache()
+    return out
+
+
+def bench_serving(args):
+    from paper_1507_05492_gb300 import server
+    return server.run_benchmark(duration_s=args.serve_seconds, rate=args.serve_rate, seed=11)
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup(args.gpus)
+    import __graft_entry__
+    __graft_entry__.build()
+    res = bench_headline(args, world, rank, local)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rp, col, lab, K = oracle_sample(args.cpu_sample_nodes, torch.device("cuda", local))
+        t = time_oracle(rp, col, lab, K, reps=1)
+        E = len(col) // 2
+        cpu = {"value": E / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"LFR-style graph with the workload's parameters at {args.cpu_sample_nodes} nodes "
+                         f"(|E| = {E}), planted partition, single-threaded oracle, {t:.1f} s"}
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_extras:
+        try:
+            extras["batched"] = bench_batched(args)
+        except Exception as e:  # reported, never silently dropped
+            extras["batched"] = {"error": repr(e)}
+        try:
+            extras["serving"] = bench_serving(args)
+        except Exception as e:
+            extras["serving"] = {"error": repr(e)}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64 counts + f64 (128-bit fixed-point sums)", "data": "synthetic",
+            "config": res["config"] | {"parallelism": f"replicas x{world}"},
+            "roofline": res["roofline"], "cpu_baseline": cpu, "e2e": res["e2e"],
+            "gpu_launches": res["launches"], "clocks": res["clocks"],
+            "kernel_share": res["kernel_share"], "result": res["result"], "extras": extras,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="lfr100m")
+    ap.add_argument("--cpu-sample-nodes", type=int, default=2_000_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--batch", type=int, default=1024)
+    ap.add_argument("--plain-sample", type=int, default=256)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

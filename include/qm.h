@@ -244,6 +244,24 @@ qm_status qm_set_tuning(const qm_graph *g, int32_t K, const qm_tuning *t);
 /* Number of this library's kernel launches issued since load (for accounting). */
 int64_t qm_kernel_launches(void);
 
+/*
+ * Kernel tracing (per calling thread).  With tracing on, every kernel a call
+ * launches is bracketed by CUDA events recorded on the call's stream, and after
+ * the call returns qm_trace_read reports each kernel of that call in launch
+ * order with its device time (the time between its two events).  A batched
+ * call reports its whole graph launch as one entry.  Tracing adds two event
+ * records per kernel; it is off by default.
+ *   events    caller array of `capacity` entries (may be NULL when capacity is 0)
+ *   count     receives the number of kernels of the last traced call
+ */
+typedef struct {
+    char name[28];
+    float ms;
+} qm_trace_event;
+
+qm_status qm_trace_enable(int32_t on);
+qm_status qm_trace_read(qm_trace_event *events, int32_t capacity, int32_t *count);
+
 const char *qm_strerror(qm_status s);
 /* Copies the calling thread's last error message into buf (always NUL-terminated). */
 qm_status qm_last_error(char *buf, size_t len);

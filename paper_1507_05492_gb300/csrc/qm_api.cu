@@ -41,6 +41,55 @@ static qm_status cuda_fail(cudaError_t e, const char *what)
         if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
     } while (0)
 
+// ------------------------------------------------------------------ tracing
+
+// Per-thread kernel timing.  When enabled, the launchers call trace_mark()
+// before each kernel and once after the last one; an event is recorded on the
+// launching stream at each mark, so kernel i took event[i+1] - event[i].
+struct TraceState {
+    bool on = false;
+    std::vector<std::string> names;
+    std::vector<cudaEvent_t> events;
+    size_t used = 0;
+    std::vector<std::pair<std::string, float>> last;
+};
+static thread_local TraceState t_trace;
+
+static void trace_mark(const char *name, cudaStream_t s)
+{
+    TraceState &t = t_trace;
+    if (t.used == t.events.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        t.events.push_back(e);
+    }
+    cudaEventRecord(t.events[t.used], s);
+    t.names.resize(t.used + 1);
+    t.names[t.used] = name ? name : "";
+    ++t.used;
+}
+
+static TraceFn trace_begin()
+{
+    if (!t_trace.on) return nullptr;
+    t_trace.used = 0;
+    return trace_mark;
+}
+
+// After the call's stream synchronisation: turn the marks into durations.
+static void trace_collect()
+{
+    TraceState &t = t_trace;
+    if (!t.on) return;
+    t.last.clear();
+    for (size_t i = 0; i + 1 < t.used; ++i) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, t.events[i], t.events[i + 1]);
+        t.last.emplace_back(t.names[i], ms);
+    }
+    t.used = 0;
+}
+
 // ------------------------------------------------------------------ device info
 
 struct DeviceGuard {
@@ -324,6 +373,26 @@ qm_status qm_last_error(char *buf, size_t len)
 
 int64_t qm_kernel_launches(void) { return g_launches.load(); }
 
+qm_status qm_trace_enable(int32_t on)
+{
+    t_trace.on = on != 0;
+    t_trace.used = 0;
+    t_trace.last.clear();
+    return QM_OK;
+}
+
+qm_status qm_trace_read(qm_trace_event *events, int32_t capacity, int32_t *count)
+{
+    if (!count || (capacity > 0 && !events)) return fail(QM_EINVAL, "bad argument");
+    const int32_t n = (int32_t)t_trace.last.size();
+    *count = n;
+    for (int32_t i = 0; i < n && i < capacity; ++i) {
+        std::snprintf(events[i].name, sizeof(events[i].name), "%s", t_trace.last[i].first.c_str());
+        events[i].ms = t_trace.last[i].second;
+    }
+    return QM_OK;
+}
+
 qm_status qm_load_graph(const int64_t *row_ptr, const int32_t *col, int64_t n_nodes, int64_t n_arcs,
                         qm_mem where, unsigned flags, void *stream, qm_graph **out)
 {
@@ -466,7 +535,7 @@ static qm_status score_impl(qm_graph *g, const int32_t *labels, int32_t K, qm_me
             CK(cudaMemsetAsync(dp[k], 0, (size_t)K * 8, s));
         }
     }
-    const int L = launch_score(g->d, dl, K, w, sh, pc ? &pcd : nullptr, num_sms_of(g->device), s);
+    const int L = launch_score(g->d, dl, K, w, sh, pc ? &pcd : nullptr, num_sms_of(g->device), s, trace_begin());
     if (L < 0) return cuda_fail(cudaGetLastError(), "launch_score");
     g_launches += L;
     CK(cudaMemcpyAsync(pin.ptr(), w.status, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -477,6 +546,7 @@ static qm_status score_impl(qm_graph *g, const int32_t *labels, int32_t K, qm_me
             if (hp[k]) CK(cudaMemcpyAsync(hp[k], dp[k], (size_t)K * 8, cudaMemcpyDeviceToHost, s));
     }
     CK(cudaStreamSynchronize(s));
+    trace_collect();
     const int st = *(int *)pin.ptr();
     if (st & 1) return fail(QM_EINVAL, "a label lies outside [0, K)");
     if (st & 2) return fail(QM_EOVERFLOW, "a community borders too many distinct communities");
@@ -522,12 +592,13 @@ qm_status qm_compare_partitions(const int32_t *truth, const int32_t *found, int6
     }
     CK(cudaMemsetAsync(ws.ptr(), 0, w.zero_bytes, s));
     Shape sh = resolve_plain(default_shape());
-    const int L = launch_compare(dt, df, n, ka, kb, w, sh, num_sms_of(dev), s);
+    const int L = launch_compare(dt, df, n, ka, kb, w, sh, num_sms_of(dev), s, trace_begin());
     if (L < 0) return cuda_fail(cudaGetLastError(), "launch_compare");
     g_launches += L;
     CK(cudaMemcpyAsync(pin.ptr(), w.status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(pin.ptr() + 256, w.result, sizeof(qm_compare), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    trace_collect();
     const int st = *(int *)pin.ptr();
     if (st & 1) return fail(QM_EINVAL, "a label lies outside its range");
     if (st & 2) return fail(QM_EOVERFLOW, "a community holds too many distinct communities");
@@ -591,7 +662,7 @@ static qm_status run_batched(int dev, BatchDesc &d, const Shape &sh0, qm_quality
         CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         cudaMemcpyAsync(items_dev, items_h, (size_t)count * sizeof(BatchItem), cudaMemcpyHostToDevice, cs);
         cudaMemsetAsync(st_dev, 0, (size_t)count * sizeof(int) + 256, cs);
-        const int L = launch_batched(items_dev, count, queue, bs, sh, num_sms, cs);
+        const int L = launch_batched(items_dev, count, queue, bs, sh, num_sms, cs, nullptr);
         cudaMemcpyAsync(H + items_b, D + items_b, q_b + c_b + (size_t)count * sizeof(int), cudaMemcpyDeviceToHost, cs);
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(cs, &graph);
@@ -605,9 +676,13 @@ static qm_status run_batched(int dev, BatchDesc &d, const Shape &sh0, qm_quality
         std::lock_guard<std::mutex> lk(g_graph_mu);
         g_graphs[key] = exec;
     }
+    TraceFn tr = trace_begin();
+    if (tr) tr("k_batched", s);
     CK(cudaGraphLaunch(exec, s));
+    if (tr) tr(nullptr, s);
     g_launches += 1;
     CK(cudaStreamSynchronize(s));
+    trace_collect();
     const int *st_h = (const int *)(H + items_b + q_b + c_b);
     for (int i = 0; i < count; ++i) {
         if (st_h[i] & 1) return fail(QM_EINVAL, "item " + std::to_string(i) + ": a label lies outside its range");

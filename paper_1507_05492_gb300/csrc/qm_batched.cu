@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(1024) k_batched(BatchKArgs a)
 
     for (int i = tid; i < p.cap; i += T) slot[i] = 0ull;
     for (int i = tid; i < 2 * (W + 1); i += T) ctl[i] = 0;
-    __syncthreads();
+    block_sync();
     const SmemTable tb{slot, used, &ctl[0], &ctl[1], p.cap, p.max_used};
     const SmemTable tw{slot + wid * p.cap_w, used + wid * p.max_used_w, &ctl[2 + 2 * wid], &ctl[3 + 2 * wid],
                        p.cap_w, p.max_used_w};
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(1024) k_batched(BatchKArgs a)
 
     for (;;) {
         if (tid == 0) s_item = atomicAdd(a.queue, 1);
-        __syncthreads();
+        block_sync();
         const int it = s_item;
         if (it >= a.count) break;
         const BatchItem I = a.items[it];
@@ -104,7 +104,11 @@ __global__ void __launch_bounds__(1024) k_batched(BatchKArgs a)
         const bool do_score = (I.flags & 1) != 0;
         const bool do_cmp = (I.flags & 2) != 0 && I.truth != nullptr;
         const int kt = do_cmp ? I.k_truth : 0;
+#ifdef QM_DBG_NO_SMEM_HIST
+        const bool smem_hist = false;
+#else
         const bool smem_hist = (long long)K + kt <= 2LL * p.cap;
+#endif
         int *cnt = smem_hist ? (int *)slot : gsize;       // label counts, then cursors
         int *cnt_a = smem_hist ? (int *)slot + K : size_a;
         if (tid == 0) { s_bad = 0; s_nbig = 0; s_ncmp = 0; s_next = 0; s_novf = 0; s_next2 = 0; }
@@ -113,7 +117,7 @@ __global__ void __launch_bounds__(1024) k_batched(BatchKArgs a)
             for (int i = tid; i < kt; i += T) size_a[i] = 0;
         }
         for (int i = tid; i < kt; i += T) { rowmax_n[i] = 0u; rowmax_r[i] = 0ull; }
-        __syncthreads();
+        block_sync();
 
         // 1. label histograms (with range checks)
         bool bad = false;
@@ -128,15 +132,17 @@ __global__ void __launch_bounds__(1024) k_batched(BatchKArgs a)
             }
         }
         if (bad) s_bad = 1;
-        __syncthreads();
+        block_sync();
         if (s_bad) {
             if (tid == 0) *I.status = 1;
             if (smem_hist) for (int i = tid; i < K + kt; i += T) ((int *)slot)[i] = 0;
-            __syncthreads();
+            block_sync();
             continue;
         }
         if (smem_hist)
             for (int i = tid; i < kt; i += T) size_a[i] = cnt_a[i];
+        // rowmax arrays and size_a written above are read later in this launch
+        __threadfence();
 
         // 2. exclusive prefix of the community sizes; lists of large communities;
         //    cnt[] becomes the scatter cursor
@@ -149,23 +155,44 @@ __global__ void __launch_bounds__(1024) k_batched(BatchKArgs a)
             if (c < K) {
                 start[c] = (int)(carry + excl);
                 cnt[c] = (int)(carry + excl);
-                if (do_score && s > a.big_thr) big_score[atomicAdd(&s_nbig, 1)] = c;
-                if (do_cmp && s > p.max_used_w) big_cmp[atomicAdd(&s_ncmp, 1)] = c;
+                if (do_score && s > a.big_thr) {
+                    const int k = atomicAdd(&s_nbig, 1);
+                    if (QM_CHK(k, bs.k_max, 12)) big_score[k] = c;
+                }
+                if (do_cmp && s > p.max_used_w) {
+                    const int k = atomicAdd(&s_ncmp, 1);
+                    if (QM_CHK(k, bs.k_max, 12)) big_cmp[k] = c;
+                }
             }
             carry += tot;
         }
         if (tid == 0) start[K] = (int)carry;
-        __syncthreads();
+        __threadfence();  // start[] and the lists are read by other warps below
+        block_sync();
 
         // 3. counting sort of the nodes by label
         for (long long u = tid; u < n; u += T) {
             const int l = __ldg(&I.labels[u]);
-            members[atomicAdd(&cnt[l], 1)] = (int)u;
+            if (!QM_CHK(l, K, 11)) continue;
+            const int pos = atomicAdd(&cnt[l], 1);
+            if (QM_CHK(pos, n, 10) && QM_CHK(pos, bs.n_max, 15)) members[pos] = (int)u;
         }
-        __syncthreads();
+        __threadfence();  // members[] is read by every warp below
+        block_sync();
+#ifdef QM_DBG_VERIFY_MEMBERS
+        // diagnostic: members[start[c] .. start[c+1]) must hold exactly the nodes labelled c
+        for (int c = tid; c < K; c += T) {
+            if (!QM_CHK(start[c], start[c + 1] + 1, 22)) continue;
+            for (int i = start[c]; i < start[c + 1]; ++i) {
+                const int m = members[i];
+                if (QM_CHK(m, n, 24)) QM_CHK(I.labels[m] == c ? 0 : 1, 1, 21);
+            }
+        }
+        if (tid == 0) QM_CHK(start[K] == n ? 0 : 1, 1, 25);
+#endif
         if (smem_hist) {
             for (int i = tid; i < K + kt; i += T) ((int *)slot)[i] = 0;
-            __syncthreads();
+            block_sync();
         }
 
         // 4. metrics without ground truth
@@ -177,34 +204,51 @@ __global__ void __launch_bounds__(1024) k_batched(BatchKArgs a)
             x.members = members;
             x.start = start;
             x.E = I.n_arcs / 2;
+            x.n = n;
+            x.n_arcs = I.n_arcs;
             x.K = K;
             x.err = I.status;
             x.pc_size = x.pc_ein = x.pc_eout = nullptr;
             x.pc_dens = x.pc_contr = x.pc_expn = x.pc_cond = x.pc_qds = nullptr;
             ScoreAcc *sacc = (ScoreAcc *)(sm + p.acc_off);
             for (int i = tid; i < W; i += T) score_acc_zero(sacc[i]);
-            __syncthreads();
+            block_sync();
             const int nbig = s_nbig;
-            for (int i = 0; i < nbig; ++i) score_community(x, big_score[i], tb, offs, rs, &sacc[0], tid, T, red);
+            for (int i = 0; i < nbig; ++i) {
+#ifdef QM_DBG_SYNC_F
+                block_sync();
+#endif
+                score_community(x, __ldcg(&big_score[i]), tb, offs, rs, &sacc[0], tid, T, red);
+#ifdef QM_DBG_SYNC_F
+                block_sync();
+#endif
+            }
+#ifdef QM_DBG_SYNC_G
+            block_sync();
+#endif
             for (;;) {
                 int base = 0;
                 if (lane == 0) base = atomicAdd(&s_next, 32);
                 base = __shfl_sync(0xffffffffu, base, 0);
                 if (base >= K) break;
                 const int c = base + lane;
-                const int sz = c < K ? start[c + 1] - start[c] : 0;
+                const int sz = c < K ? __ldcg(&start[c + 1]) - __ldcg(&start[c]) : 0;
                 unsigned mask = __ballot_sync(0xffffffffu, sz > 0 && sz <= a.big_thr);
                 while (mask) {
                     const int j = __ffs(mask) - 1;
                     mask &= mask - 1;
                     if (!score_community(x, base + j, tw, offw, rsw, &sacc[wid], lane, 32, red))
-                        if (lane == 0) ovf[atomicAdd(&s_novf, 1)] = base + j;
+                        if (lane == 0) {
+                            const int k = atomicAdd(&s_novf, 1);
+                            if (QM_CHK(k, bs.k_max, 13)) ovf[k] = base + j;
+                        }
                 }
             }
-            __syncthreads();
+            __threadfence();
+            block_sync();
             const int novf = s_novf;
-            for (int i = 0; i < novf; ++i) score_community(x, ovf[i], tb, offs, rs, &sacc[0], tid, T, red);
-            __syncthreads();
+            for (int i = 0; i < novf; ++i) score_community(x, __ldcg(&ovf[i]), tb, offs, rs, &sacc[0], tid, T, red);
+            block_sync();
             if (tid == 0) {
                 ScoreAcc t = sacc[0];
                 for (int w = 1; w < W; ++w) score_acc_add(t, sacc[w]);
@@ -239,18 +283,18 @@ __global__ void __launch_bounds__(1024) k_batched(BatchKArgs a)
             x.kb = K;
             x.err = I.status;
             CompareAcc *cacc = (CompareAcc *)(sm + p.acc_off);
-            __syncthreads();
+            block_sync();
             for (int i = tid; i < W; i += T) compare_acc_zero(cacc[i]);
-            __syncthreads();
+            block_sync();
             const int ncmp = s_ncmp;
-            for (int i = 0; i < ncmp; ++i) compare_community(x, big_cmp[i], tb, &cacc[0], tid, T, red);
+            for (int i = 0; i < ncmp; ++i) compare_community(x, __ldcg(&big_cmp[i]), tb, &cacc[0], tid, T, red);
             for (;;) {
                 int base = 0;
                 if (lane == 0) base = atomicAdd(&s_next2, 32);
                 base = __shfl_sync(0xffffffffu, base, 0);
                 if (base >= K) break;
                 const int b = base + lane;
-                const int sz = b < K ? start[b + 1] - start[b] : 0;
+                const int sz = b < K ? __ldcg(&start[b + 1]) - __ldcg(&start[b]) : 0;
                 unsigned mask = __ballot_sync(0xffffffffu, sz > 0 && sz <= p.max_used_w);
                 while (mask) {
                     const int j = __ffs(mask) - 1;
@@ -258,7 +302,8 @@ __global__ void __launch_bounds__(1024) k_batched(BatchKArgs a)
                     compare_community(x, base + j, tw, &cacc[wid], lane, 32, red);
                 }
             }
-            __syncthreads();  // row maxima complete
+            __threadfence();
+            block_sync();  // row maxima complete
             CompareAcc racc;
             compare_acc_zero(racc);
             for (int r = tid; r < kt; r += T) compare_row(x, r, racc);
@@ -285,7 +330,7 @@ __global__ void __launch_bounds__(1024) k_batched(BatchKArgs a)
                 make_compare(t, n, I.out_c);
             }
         }
-        __syncthreads();
+        block_sync();
     }
 }
 
@@ -302,7 +347,7 @@ int batched_blocks_per_sm(const Shape &sh)
 }
 
 int launch_batched(const BatchItem *items_dev, int count, int *queue, const BatchScratch &bs,
-                   const Shape &sh, int num_sms, cudaStream_t s)
+                   const Shape &sh, int num_sms, cudaStream_t s, TraceFn tr)
 {
     (void)num_sms;
     BatchKArgs a;
@@ -312,8 +357,18 @@ int launch_batched(const BatchItem *items_dev, int count, int *queue, const Batc
     a.bs = bs;
     a.plan = plan_smem(sh.threads, sh.smem_bytes);
     a.big_thr = sh.big_community;
+    if (tr) tr("k_batched", s);
     k_batched<<<bs.slots, sh.threads, sh.smem_bytes, s>>>(a);
+    if (tr) tr(nullptr, s);
     return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
 }  // namespace qm
+
+#ifdef QM_BOUNDS_CHECK
+// Diagnostic build only: (site, index, bound, violations) of the first bad index.
+extern "C" int qm_debug_read(unsigned long long *rec4)
+{
+    return (int)cudaMemcpyFromSymbol(rec4, qmk::qm_dbg_rec, sizeof(unsigned long long) * 8);
+}
+#endif

@@ -20,7 +20,10 @@
 
 namespace qmk {
 
-// Inputs of one partition on one graph.
+// Inputs of one partition on one graph.  The batched kernel writes `members`
+// and `start` earlier in the same launch, so they are always read through L2
+// (__ldcg) after the writer's fence and barrier, never through L1 or the
+// read-only path.
 struct ScoreCtx {
     const long long *row_ptr;
     const int *col;
@@ -28,6 +31,7 @@ struct ScoreCtx {
     const int *members;   // node ids grouped by label: members[start[c] .. start[c+1])
     const int *start;     // int[K + 1]
     long long E;          // |E|
+    long long n, n_arcs;  // graph size (bounds of the arrays above)
     int K;
     int *err;             // set to 2 when a community cannot be counted (see score_community)
     // optional per-community outputs (device pointers or null)
@@ -61,15 +65,15 @@ __device__ __forceinline__ unsigned long long group_sum_u64(unsigned long long v
     v = warp_sum_u64(v);
     if (gsize == 32) return __shfl_sync(0xffffffffu, v, 0);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    __syncthreads();
+    block_sync();
     if (lane == 0) red[wid] = v;
-    __syncthreads();
+    block_sync();
     if (wid == 0) {
         unsigned long long t = lane < nw ? red[lane] : 0ull;
         t = warp_sum_u64(t);
         if (lane == 0) red[32] = t;
     }
-    __syncthreads();
+    block_sync();
     return red[32];
 }
 
@@ -79,15 +83,15 @@ __device__ __forceinline__ unsigned group_max_u32(unsigned v, int gsize, unsigne
     v = __shfl_sync(0xffffffffu, v, 0);
     if (gsize == 32) return v;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    __syncthreads();
+    block_sync();
     if (lane == 0) red[wid] = v;
-    __syncthreads();
+    block_sync();
     if (wid == 0) {
         unsigned t = lane < nw ? (unsigned)red[lane] : 0u;
         for (int d = 16; d > 0; d >>= 1) t = max(t, __shfl_down_sync(0xffffffffu, t, d));
         if (lane == 0) red[32] = t;
     }
-    __syncthreads();
+    block_sync();
     return (unsigned)red[32];
 }
 
@@ -101,16 +105,16 @@ __device__ __forceinline__ i128 group_sum_i128(i128 v, int gsize, unsigned long 
         return (i128)(((u128)hi << 64) | lo);
     }
     const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    __syncthreads();
+    block_sync();
     if (lane == 0) { red[2 * wid] = (unsigned long long)(u128)v; red[2 * wid + 1] = (unsigned long long)((u128)v >> 64); }
-    __syncthreads();
+    block_sync();
     if (threadIdx.x == 0) {
         i128 t = 0;
         for (int w = 0; w < nw; ++w) t += (i128)(((u128)red[2 * w + 1] << 64) | red[2 * w]);
         red[64] = (unsigned long long)(u128)t;
         red[65] = (unsigned long long)((u128)t >> 64);
     }
-    __syncthreads();
+    block_sync();
     return (i128)(((u128)red[65] << 64) | red[64]);
 }
 
@@ -129,9 +133,9 @@ __device__ __forceinline__ unsigned group_exclusive_scan(unsigned v, unsigned &e
         return __shfl_sync(0xffffffffu, inc, 31);
     }
     const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    __syncthreads();
+    block_sync();
     if (lane == 31) red[wid] = inc;
-    __syncthreads();
+    block_sync();
     if (wid == 0) {
         unsigned t = lane < nw ? (unsigned)red[lane] : 0u, s = t;
         for (int d = 1; d < 32; d <<= 1) {
@@ -141,7 +145,7 @@ __device__ __forceinline__ unsigned group_exclusive_scan(unsigned v, unsigned &e
         if (lane < nw) red[lane] = s - t;  // exclusive warp offsets
         if (lane == 31) red[32] = s;
     }
-    __syncthreads();
+    block_sync();
     excl = (unsigned)red[wid] + inc - v;
     return (unsigned)red[32];
 }
@@ -153,6 +157,7 @@ __device__ __forceinline__ void tab_drain(const SmemTable &t, int gtid, int gsiz
     const int n = min(*t.n_used, t.max_used);
     for (int i = gtid; i < n; i += gsize) {
         const int h = t.used[i];
+        if (!QM_CHK(h, t.cap, 9)) continue;
         const unsigned long long s = t.slot[h];
         f((int)(s >> 32) - 1, (long long)(s & 0xFFFFFFFFull));
         t.slot[h] = 0ull;
@@ -175,8 +180,21 @@ __device__ __forceinline__ bool score_community(const ScoreCtx &x, int c, const 
                                                 unsigned *offs, long long *rs, ScoreAcc *acc,
                                                 int gtid, int gsize, unsigned long long *red)
 {
-    const int mb = x.start[c], me = x.start[c + 1];
+    const int mb = __ldcg(&x.start[c]), me = __ldcg(&x.start[c + 1]);
     const long long size = me - mb;
+#ifdef QM_DBG_VERIFY_AGREE
+    if (gsize == 32) {
+        QM_CHK(c == __shfl_sync(0xffffffffu, c, 0) && mb == __shfl_sync(0xffffffffu, mb, 0) &&
+               me == __shfl_sync(0xffffffffu, me, 0) ? 0 : 1, 1, 28);
+    } else {
+        __shared__ int dbg_agree[3];
+        block_sync();
+        if (gtid == 0) { dbg_agree[0] = c; dbg_agree[1] = mb; dbg_agree[2] = me; }
+        block_sync();
+        QM_CHK(c == dbg_agree[0] && mb == dbg_agree[1] && me == dbg_agree[2] ? 0 : 1, 1, 27);
+        block_sync();
+    }
+#endif
     unsigned R = 1;
     for (;;) {
         unsigned long long same = 0, vol = 0;
@@ -188,10 +206,12 @@ __device__ __forceinline__ bool score_community(const ScoreCtx &x, int c, const 
                 const int i = cb + gtid;
                 unsigned d = 0;
                 long long rsi = 0;
-                if (i < me) {
+                if (i < me && QM_CHK(i, x.n, 1)) {
                     const int u = __ldcg(&x.members[i]);
-                    rsi = __ldg(&x.row_ptr[u]);
-                    d = (unsigned)(__ldg(&x.row_ptr[u + 1]) - rsi);
+                    if (QM_CHK(u, x.n, 2)) {
+                        rsi = __ldg(&x.row_ptr[u]);
+                        d = (unsigned)(__ldg(&x.row_ptr[u + 1]) - rsi);
+                    }
                 }
                 if (r == 0) vol += d;
                 unsigned excl;
@@ -199,6 +219,14 @@ __device__ __forceinline__ bool score_community(const ScoreCtx &x, int c, const 
                 const unsigned total = group_exclusive_scan(d, excl, gsize, red);
                 if (gtid < nm) { offs[gtid] = excl; rs[gtid] = rsi; }
                 group_sync(gsize);
+#ifdef QM_DBG_VERIFY_OFFS
+                if (gtid < nm)
+                    QM_CHKX(offs[gtid] + d == (gtid + 1 < nm ? offs[gtid + 1] : total) ? 0 : 1, 1,
+                            23 + 100 * (gsize == 32 ? 1 : 2) + 1000 * (gtid + 1 < nm ? 1 : 2),
+                            c, gtid, ((long long)nm << 32) | (unsigned)(me - mb),
+                            ((long long)total << 32) | (unsigned)(offs[gtid] + d));
+                if (gtid == 0) QM_CHK(gsize == 32 || gsize == (int)blockDim.x ? 0 : 1, 1, 26);
+#endif
                 for (unsigned e0 = gtid; e0 < total; e0 += 4u * gsize) {
                     int v[4], lv[4];
 #pragma unroll
@@ -207,7 +235,9 @@ __device__ __forceinline__ bool score_community(const ScoreCtx &x, int c, const 
                         v[k] = -1;
                         if (e < total) {
                             const int o = upper_bound_smem(offs, nm, e) - 1;
-                            v[k] = __ldg(&x.col[rs[o] + (e - offs[o])]);
+                            if (QM_CHK(o, nm, 4) && QM_CHK(rs[o] + (e - offs[o]), x.n_arcs, 3))
+                                v[k] = __ldg(&x.col[rs[o] + (e - offs[o])]);
+                            if (!QM_CHK(v[k], x.n, 5)) v[k] = -1;
                         }
                     }
 #pragma unroll
@@ -215,6 +245,7 @@ __device__ __forceinline__ bool score_community(const ScoreCtx &x, int c, const 
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         if (v[k] < 0) continue;
+                        if (!QM_CHK(lv[k], x.K, 6)) continue;
                         if (lv[k] == c) {
                             if (r == 0) ++same;
                         } else if (R == 1 || tab_split((unsigned)lv[k], R) == r) {
@@ -229,7 +260,8 @@ __device__ __forceinline__ bool score_community(const ScoreCtx &x, int c, const 
                 break;
             }
             tab_drain(tab, gtid, gsize, [&](int key, long long cnt) {
-                const long long sj = x.start[key + 1] - x.start[key];
+                if (!QM_CHK(key, x.K, 7)) return;
+                const long long sj = __ldcg(&x.start[key + 1]) - __ldcg(&x.start[key]);
                 pair_fp += fp_from_double(pair_term(cnt, size, sj, x.E), SC_QDS);
                 ++slots;
                 cnt2 += (unsigned long long)(cnt * cnt);
@@ -300,7 +332,7 @@ __device__ __forceinline__ void compare_community(const CompareCtx &x, int b, co
                                                   CompareAcc *acc, int gtid, int gsize,
                                                   unsigned long long *red)
 {
-    const int mb = x.start[b], me = x.start[b + 1];
+    const int mb = __ldcg(&x.start[b]), me = __ldcg(&x.start[b + 1]);
     const long long nb = me - mb;
     unsigned R = 1;
     if (nb > tab.max_used) R = (unsigned)((nb * 4 + 3LL * tab.max_used - 1) / (3LL * tab.max_used));
@@ -321,7 +353,7 @@ __device__ __forceinline__ void compare_community(const CompareCtx &x, int b, co
             group_sync(gsize);
             if (*tab.overflow) { ok = false; break; }
             tab_drain(tab, gtid, gsize, [&](int a, long long n) {
-                const long long na = x.size_a[a];
+                const long long na = __ldcg(&x.size_a[a]);
                 a11 += (unsigned long long)(n * (n - 1) / 2);
                 ++cells;
                 colmax = max(colmax, (unsigned)n);
@@ -364,11 +396,11 @@ __device__ __forceinline__ void compare_community(const CompareCtx &x, int b, co
 // Row side of the contingency table for truth community a (Eqs. 2-4).
 __device__ __forceinline__ void compare_row(const CompareCtx &x, int a, CompareAcc &acc)
 {
-    const long long na = x.size_a[a];
+    const long long na = __ldcg(&x.size_a[a]);
     if (na == 0) return;
     acc.sa += (unsigned long long)(na * (na - 1) / 2);
-    acc.nvd += x.rowmax_n[a];
-    const double r = __longlong_as_double((long long)x.rowmax_r[a]);
+    acc.nvd += __ldcg(&x.rowmax_n[a]);
+    const double r = __longlong_as_double((long long)__ldcg(&x.rowmax_r[a]));
     acc.f += fp_from_double(__dmul_rn((double)na, r), SC_F);
     acc.hden += fp_from_double(entropy_term(na, x.N), SC_H);
     acc.ka += 1;

@@ -28,6 +28,34 @@ constexpr int SC_VI = 80;     // sum of n log(n^2/(n_a n_b)): |sum| < 43 N < 2^3
 constexpr int SC_H = 100;     // NMI numerator / denominator terms: |sum| < 44
 constexpr int SC_F = 80;      // F-measure sum of n_a * max ratio: < N < 2^31
 
+// ---------------------------------------------------------------- bounds checks
+// Compiled in only with -DQM_BOUNDS_CHECK (a diagnostic build): an index outside
+// [0, n) records (site, index, bound) in qm_dbg_rec and the access is skipped.
+#ifdef QM_BOUNDS_CHECK
+static __device__ unsigned long long qm_dbg_rec[8];
+__device__ __forceinline__ bool qm_chk_ex(long long i, long long n, int site, long long e0, long long e1,
+                                          long long e2, long long e3)
+{
+    if (i >= 0 && i < n) return true;
+    if (atomicCAS(&qm_dbg_rec[0], 0ull, (unsigned long long)site) == 0ull) {
+        qm_dbg_rec[1] = (unsigned long long)i;
+        qm_dbg_rec[2] = (unsigned long long)n;
+        qm_dbg_rec[4] = (unsigned long long)e0;
+        qm_dbg_rec[5] = (unsigned long long)e1;
+        qm_dbg_rec[6] = (unsigned long long)e2;
+        qm_dbg_rec[7] = (unsigned long long)e3;
+    }
+    atomicAdd(&qm_dbg_rec[3], 1ull);
+    return false;
+}
+#define QM_CHK(i, n, site) qm_chk_ex((long long)(i), (long long)(n), (site), 0, 0, 0, 0)
+#define QM_CHKX(i, n, site, a, b, c, d) \
+    qm_chk_ex((long long)(i), (long long)(n), (site), (long long)(a), (long long)(b), (long long)(c), (long long)(d))
+#else
+#define QM_CHK(i, n, site) true
+#define QM_CHKX(i, n, site, a, b, c, d) true
+#endif
+
 // ---------------------------------------------------------------- fixed point
 
 __device__ __forceinline__ i128 fp_from_double(double x, int scale)
@@ -290,7 +318,11 @@ __device__ __forceinline__ void tab_insert(const SmemTable &t, unsigned key)
 {
     const unsigned long long tag = (unsigned long long)(key + 1u) << 32;
     unsigned h = tab_hash(key, t.cap);
+    // Once the table has overflowed its pass is discarded: stop probing.
+    if (*(volatile int *)t.overflow) return;
     for (int probe = 0; probe < t.cap; ++probe) {
+        if (!QM_CHK(h, t.cap, 8)) return;
+        if ((probe & 15) == 15 && *(volatile int *)t.overflow) return;
         unsigned long long cur = ((volatile unsigned long long *)t.slot)[h];
         if (cur == 0ull) {
             unsigned long long prev = atomicCAS(&t.slot[h], 0ull, tag | 1ull);
@@ -324,10 +356,21 @@ __device__ __forceinline__ int upper_bound_smem(const unsigned *a, int n, unsign
     return lo;
 }
 
+// Block-wide barrier in its non-.aligned PTX form.  __syncthreads() is the
+// .aligned barrier, which requires each warp to arrive converged; the block
+// routines reach their barriers straight from data-dependent loops (hash-table
+// probing, ragged arc loops), so the warp may arrive in several pieces.  The
+// non-aligned barrier counts threads, not converged warps, and orders memory
+// like __syncthreads().
+__device__ __forceinline__ void block_sync()
+{
+    asm volatile("barrier.sync 0;" ::: "memory");
+}
+
 __device__ __forceinline__ void group_sync(int group)
 {
     if (group == 32) __syncwarp();
-    else __syncthreads();
+    else block_sync();
 }
 
 }  // namespace qmk

@@ -79,12 +79,16 @@ struct PerCommDev {
     double *dens, *contr, *expn, *cond, *qds;
 };
 
+// Optional tracing hook: called with a kernel name right before each launch
+// and with nullptr after the last one, on the launching stream.
+typedef void (*TraceFn)(const char *name, cudaStream_t s);
+
 // Plain path launchers (stream-ordered, no synchronisation).  Each returns the
 // number of kernels it launched, or -1 on a launch error.
 int launch_score(const GraphDev &g, const int *labels, int K, const ScoreWs &ws, const Shape &sh,
-                 const PerCommDev *pc, int num_sms, cudaStream_t s);
+                 const PerCommDev *pc, int num_sms, cudaStream_t s, TraceFn tr);
 int launch_compare(const int *truth, const int *found, long long n, int ka, int kb,
-                   const CompareWs &ws, const Shape &sh, int num_sms, cudaStream_t s);
+                   const CompareWs &ws, const Shape &sh, int num_sms, cudaStream_t s, TraceFn tr);
 
 // Largest dynamic shared memory a community-major block may request.
 constexpr int MAX_DYN_SMEM = 220 * 1024;
@@ -133,7 +137,7 @@ size_t batch_scratch_bytes(long long n_max, int k_max, int kt_max, int slots);
 BatchScratch carve_batch_scratch(void *base, long long n_max, int k_max, int kt_max, int slots);
 
 int launch_batched(const BatchItem *items_dev, int count, int *queue, const BatchScratch &bs,
-                   const Shape &sh, int num_sms, cudaStream_t s);
+                   const Shape &sh, int num_sms, cudaStream_t s, TraceFn tr);
 int batched_blocks_per_sm(const Shape &sh);
 
 // ---- graph validation

@@ -162,7 +162,7 @@ __global__ void k_hist(const int *__restrict__ a, int ka, int *size_a, const int
     extern __shared__ int sh[];
     if (use_smem) {
         for (int i = threadIdx.x; i < ka + kb; i += blockDim.x) sh[i] = 0;
-        __syncthreads();
+        block_sync();
     }
     bool bad = false;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -180,7 +180,7 @@ __global__ void k_hist(const int *__restrict__ a, int ka, int *size_a, const int
     }
     if (bad) atomicOr(status, 1);
     if (use_smem) {
-        __syncthreads();
+        block_sync();
         for (int i = threadIdx.x; i < ka; i += blockDim.x)
             if (sh[i]) atomicAdd(&size_a[i], sh[i]);
         for (int i = threadIdx.x; i < kb; i += blockDim.x)
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(1024) k_score_cm(ScoreKArgs a)
     for (int i = threadIdx.x; i < p.cap; i += T) slot[i] = 0ull;
     for (int i = threadIdx.x; i < 2 * (W + 1); i += T) ctl[i] = 0;
     for (int i = threadIdx.x; i < W; i += T) score_acc_zero(sacc[i]);
-    __syncthreads();
+    block_sync();
 
     const SmemTable tb{slot, used, &ctl[0], &ctl[1], p.cap, p.max_used};
     const int *list = a.phase == 0 ? a.big_list : a.ovf_in;
@@ -331,9 +331,9 @@ __global__ void __launch_bounds__(1024) k_score_cm(ScoreKArgs a)
             const int i = atomicAdd(next, 1);
             s_item = i < count ? list[i] : -1;
         }
-        __syncthreads();
+        block_sync();
         const int c = s_item;
-        __syncthreads();
+        block_sync();
         if (c < 0) break;
         score_community(a.x, c, tb, offs, rs, &sacc[0], threadIdx.x, T, red);
     }
@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(1024) k_score_cm(ScoreKArgs a)
             }
         }
     }
-    __syncthreads();
+    block_sync();
     if (threadIdx.x == 0) flush_score(sacc, W, a.gacc);
 }
 
@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(1024) k_compare_cm(CompareKArgs a)
     for (int i = threadIdx.x; i < p.cap; i += T) slot[i] = 0ull;
     for (int i = threadIdx.x; i < 2 * (W + 1); i += T) ctl[i] = 0;
     for (int i = threadIdx.x; i < W; i += T) compare_acc_zero(cacc[i]);
-    __syncthreads();
+    block_sync();
     const SmemTable tb{slot, used, &ctl[0], &ctl[1], p.cap, p.max_used};
     const int count = a.counters[C_BIG_COUNT];
     for (;;) {
@@ -455,9 +455,9 @@ __global__ void __launch_bounds__(1024) k_compare_cm(CompareKArgs a)
             const int i = atomicAdd(&a.counters[C_BIG_NEXT], 1);
             s_item = i < count ? a.big_list[i] : -1;
         }
-        __syncthreads();
+        block_sync();
         const int b = s_item;
-        __syncthreads();
+        block_sync();
         if (b < 0) break;
         compare_community(a.x, b, tb, &cacc[0], threadIdx.x, T, red);
     }
@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(1024) k_compare_cm(CompareKArgs a)
             compare_community(a.x, base + j, tw, &cacc[wid], lane, 32, red);
         }
     }
-    __syncthreads();
+    block_sync();
     if (threadIdx.x == 0) {
         CompareAcc t = cacc[0];
         for (int w = 1; w < W; ++w) compare_acc_add(t, cacc[w]);
@@ -579,32 +579,43 @@ int score_blocks_per_sm(const Shape &sh)
     return nb;
 }
 
+#define TRACE(name) \
+    do {            \
+        if (tr) tr(name, s); \
+    } while (0)
+
 static int launch_scan(const int *size, int K, int *start, int *cursor, int big_thr, int *big_list,
-                       int *counters, int *tmp, const int *status, cudaStream_t s)
+                       int *counters, int *tmp, const int *status, cudaStream_t s, TraceFn tr)
 {
     if (K <= SCAN_SINGLE_MAX) {
+        TRACE("k_scan_single");
         k_scan_single<<<1, 1024, 0, s>>>(size, K, start, cursor, big_thr, big_list, counters, status);
         return 1;
     }
     const int tiles = scan_tiles(K);
+    TRACE("k_scan_tiles");
     k_scan_tiles<<<tiles, 1024, 0, s>>>(size, K, tmp, status);
     // exclusive prefix of the tile sums, in place into tmp[0..tiles] (tmp[tiles] = total)
+    TRACE("k_scan_single");
     k_scan_single<<<1, 1024, 0, s>>>(tmp, tiles, tmp, nullptr, INT_MAX, nullptr, counters, status);
+    TRACE("k_scan_apply");
     k_scan_apply<<<tiles, 1024, 0, s>>>(size, K, tmp, start, cursor, big_thr, big_list, counters, status);
     return 3;
 }
 
 int launch_score(const GraphDev &g, const int *labels, int K, const ScoreWs &ws, const Shape &sh,
-                 const PerCommDev *pc, int num_sms, cudaStream_t s)
+                 const PerCommDev *pc, int num_sms, cudaStream_t s, TraceFn tr)
 {
     int launches = 0;
     const long long n = g.n;
     const int hist_smem = (K <= 12288) ? K * 4 : 0;
+    TRACE("k_hist");
     k_hist<<<grid_for(n, 512, num_sms, 4), 512, hist_smem, s>>>(labels, K, ws.size, nullptr, 0, nullptr, n,
                                                                 ws.status, hist_smem ? 1 : 0);
     ++launches;
     launches += launch_scan(ws.size, K, ws.start, ws.cursor, sh.big_community, ws.big_list, ws.counters,
-                            ws.scan_tmp, ws.status, s);
+                            ws.scan_tmp, ws.status, s, tr);
+    TRACE("k_scatter");
     k_scatter<<<grid_for(n, 512, num_sms, 8), 512, 0, s>>>(labels, n, ws.cursor, ws.members, ws.status);
     ++launches;
 
@@ -615,6 +626,8 @@ int launch_score(const GraphDev &g, const int *labels, int K, const ScoreWs &ws,
     a.x.members = ws.members;
     a.x.start = ws.start;
     a.x.E = g.n_arcs / 2;
+    a.x.n = g.n;
+    a.x.n_arcs = g.n_arcs;
     a.x.K = K;
     a.x.err = ws.status;
     a.x.pc_size = pc ? pc->size : nullptr;
@@ -635,25 +648,31 @@ int launch_score(const GraphDev &g, const int *labels, int K, const ScoreWs &ws,
     a.plan = plan_smem(sh.threads, sh.smem_bytes);
     const int blocks = num_sms * (sh.blocks_per_sm > 0 ? sh.blocks_per_sm : 1);
     a.phase = 0;
+    TRACE("k_score_cm");
     k_score_cm<<<blocks, sh.threads, sh.smem_bytes, s>>>(a);
     a.phase = 1;
+    TRACE("k_score_cm_overflow");
     k_score_cm<<<blocks, sh.threads, sh.smem_bytes, s>>>(a);
+    TRACE("k_score_fin");
     k_score_fin<<<1, 32, 0, s>>>(ws.gacc, ws.status, n, g.n_arcs / 2, ws.result);
+    TRACE(nullptr);
     launches += 3;
     return cudaGetLastError() == cudaSuccess ? launches : -1;
 }
 
 int launch_compare(const int *truth, const int *found, long long n, int ka, int kb,
-                   const CompareWs &ws, const Shape &sh, int num_sms, cudaStream_t s)
+                   const CompareWs &ws, const Shape &sh, int num_sms, cudaStream_t s, TraceFn tr)
 {
     int launches = 0;
     const int hist_smem = (ka + kb <= 12288) ? (ka + kb) * 4 : 0;
+    TRACE("k_hist2");
     k_hist<<<grid_for(n, 512, num_sms, 4), 512, hist_smem, s>>>(truth, ka, ws.size_a, found, kb, ws.size_b, n,
                                                                 ws.status, hist_smem ? 1 : 0);
     ++launches;
     const SmemPlan plan = plan_smem(sh.threads, sh.smem_bytes);
     launches += launch_scan(ws.size_b, kb, ws.start, ws.cursor, plan.max_used_w, ws.big_list, ws.counters,
-                            ws.scan_tmp, ws.status, s);
+                            ws.scan_tmp, ws.status, s, tr);
+    TRACE("k_scatter");
     k_scatter<<<grid_for(n, 512, num_sms, 8), 512, 0, s>>>(found, n, ws.cursor, ws.members, ws.status);
     ++launches;
     CompareKArgs a;
@@ -675,9 +694,13 @@ int launch_compare(const int *truth, const int *found, long long n, int ka, int 
     int nb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_compare_cm, sh.threads, sh.smem_bytes);
     if (nb < 1) nb = 1;
+    TRACE("k_compare_cm");
     k_compare_cm<<<num_sms * nb, sh.threads, sh.smem_bytes, s>>>(a);
+    TRACE("k_compare_rows");
     k_compare_rows<<<grid_for(ka, 256, num_sms, 2), 256, 0, s>>>(a.x, ws.gacc, ws.status);
+    TRACE("k_compare_fin");
     k_compare_fin<<<1, 32, 0, s>>>(ws.gacc, ws.status, n, ws.result);
+    TRACE(nullptr);
     launches += 3;
     return cudaGetLastError() == cudaSuccess ? launches : -1;
 }

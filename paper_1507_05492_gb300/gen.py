@@ -406,3 +406,14 @@ def config_params(name: str, seed: int | None = None) -> LfrParams:
     if seed is not None:
         p.seed = seed
     return p
+
+
+def candidate_batch(planted: torch.Tensor, P: int, seed: int, k_range=(500, 5000), frac_max=0.5):
+    """P candidate partitions (see candidate_partition) as a [P, n] int32 matrix on
+    the planted labels' device, with their label-id counts."""
+    rows, Ks = [], []
+    for p in range(P):
+        lab, K, _ = candidate_partition(planted, seed + p, k_range=k_range, frac_max=frac_max)
+        rows.append(lab)
+        Ks.append(K)
+    return torch.stack(rows), Ks

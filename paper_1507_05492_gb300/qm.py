@@ -56,6 +56,10 @@ class QmPercomm(ctypes.Structure):
         "conductance", "qds_term")]
 
 
+class QmTraceEvent(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 28), ("ms", ctypes.c_float)]
+
+
 class QmTuning(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in ("threads", "smem_bytes", "big_community", "blocks_per_sm")]
 
@@ -85,6 +89,8 @@ def _signatures(lib):
         "qm_get_tuning": [_P, _I32, _P],
         "qm_set_tuning": [_P, _I32, _P],
         "qm_last_error": [_P, ctypes.c_size_t],
+        "qm_trace_enable": [_I32],
+        "qm_trace_read": [_P, _I32, _P],
     }
     for name, args in table.items():
         f = getattr(lib, name)
@@ -332,6 +338,20 @@ def get_tuning(graph: Graph, K: int) -> dict:
 def set_tuning(graph: Graph, K: int, threads: int, smem_bytes: int, big_community: int):
     t = QmTuning(threads, smem_bytes, big_community, 0)
     _check(lib().qm_set_tuning(graph.handle, int(K), ctypes.byref(t)), "qm_set_tuning")
+
+
+def trace_enable(on: bool = True):
+    """Per-thread kernel timing with CUDA events on the launching stream."""
+    _check(lib().qm_trace_enable(1 if on else 0), "qm_trace_enable")
+
+
+def trace_read() -> list[tuple[str, float]]:
+    """(kernel name, device ms) of every kernel of the calling thread's last traced call."""
+    cap = 64
+    buf = (QmTraceEvent * cap)()
+    n = ctypes.c_int32()
+    _check(lib().qm_trace_read(buf, cap, ctypes.byref(n)), "qm_trace_read")
+    return [(buf[i].name.decode(), float(buf[i].ms)) for i in range(min(n.value, cap))]
 
 
 def release_cache():

@@ -1,0 +1,88 @@
+"""The serving loop: requests of different graph sizes admitted by a memory
+budget and batched as they arrive; each result in the mix must equal the
+result of the same request scored alone."""
+import threading
+import time
+
+import numpy as np
+import pytest
+import torch
+
+from helpers import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1507_05492_gb300 import gen, qm
+    graphs, truths, pools = {}, {}, {}
+    for gid, n in (("small", 3_000), ("mid", 60_000), ("large", 400_000)):
+        g = gen.lfr_graph(gen.LfrParams(n=n, k_max=100 if n > 100_000 else 50,
+                                        s_max=1000 if n > 100_000 else 100, seed=50 + n % 97), device="cuda")
+        graphs[gid] = qm.Graph(g.row_ptr, g.col)
+        truths[gid] = (g.labels, g.K)
+        pools[gid] = [gen.perturb(g.labels, g.K, 0.05 * (i % 10), seed=60 + i) for i in range(12)]
+    return qm, graphs, truths, pools
+
+
+def test_results_in_the_mix_equal_results_alone(env):
+    from paper_1507_05492_gb300.server import Server
+    qm, graphs, truths, pools = env
+    rng = np.random.default_rng(1)
+    reqs = []
+    for i in range(300):
+        gid = ("small", "mid", "large")[rng.integers(3)]
+        lab = pools[gid][rng.integers(len(pools[gid]))]
+        with_truth = rng.random() < 0.5
+        reqs.append((gid, lab, truths[gid][1], truths[gid][0] if with_truth else None,
+                     truths[gid][1] if with_truth else None))
+    srv = Server(graphs, budget_bytes=2 << 30, max_batch=64, n_streams=3)
+    futs = []
+    # arrivals in bursts from two client threads, so batches form while others run
+    def client(part):
+        for r in part:
+            futs.append((r, srv.submit(*r)))
+            if rng.random() < 0.1:
+                time.sleep(0.002)
+    ts = [threading.Thread(target=client, args=(reqs[k::2],)) for k in range(2)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    results = [(r, f.result(timeout=120)) for r, f in futs]
+    srv.close()
+    assert max(srv.batch_sizes) > 1, "no request was ever batched"
+    for (gid, lab, K, truth, kt), res in results:
+        alone = qm.score(graphs[gid], lab, K)
+        assert res["quality"] == alone
+        if truth is not None:
+            assert res["compare"] == qm.compare(truth, lab, kt, K)
+
+
+def test_admission_respects_budget(env):
+    from paper_1507_05492_gb300.server import Server
+    qm, graphs, truths, pools = env
+    need = qm.workspace_bytes(graphs["large"], truths["large"][1])
+    srv = Server(graphs, budget_bytes=int(need * 1.5), max_batch=64, n_streams=4)
+    peak = [0]
+    orig = srv._take_batch
+
+    def take():
+        b, total = orig()
+        peak[0] = max(peak[0], srv.in_flight + total)
+        return b, total
+    srv._take_batch = take
+    futs = [srv.submit("large", pools["large"][i % 12], truths["large"][1]) for i in range(12)]
+    for f in futs:
+        f.result(timeout=120)
+    srv.close()
+    assert peak[0] <= int(need * 1.5)
+    # a request larger than the whole budget is refused, not queued forever
+    tiny = Server(graphs, budget_bytes=1024, n_streams=1)
+    f = tiny.submit("large", pools["large"][0], truths["large"][1])
+    with pytest.raises(MemoryError):
+        f.result(timeout=5)
+    tiny.close()
