@@ -145,30 +145,18 @@ def dist_setup(n_gpus: int):
 
 
 def barrier(world):
-    if world > 1:
-        import torch
-        import torch.distributed as dist
-        dist.barrier(device_ids=[torch.cuda.current_device()])
+    from paper_1507_05492_gb300 import dist as qd
+    qd.barrier()
 
 
 def max_over_ranks(x: float, world: int) -> float:
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_1507_05492_gb300 import dist as qd
+    return qd.reduce_scalar(x, "max")
 
 
 def sum_over_ranks(x: float, world: int) -> float:
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    from paper_1507_05492_gb300 import dist as qd
+    return qd.reduce_scalar(x, "sum")
 
 
 # ------------------------------------------------------------------ CPU oracle baseline
