@@ -241,6 +241,38 @@ qm_status qm_autotune(const qm_graph *g, const int32_t *labels, int32_t K, qm_me
 qm_status qm_get_tuning(const qm_graph *g, int32_t K, qm_tuning *t);
 qm_status qm_set_tuning(const qm_graph *g, int32_t K, const qm_tuning *t);
 
+/*
+ * qm_score_partition_noalloc -- qm_score_partition for callers that cannot let
+ * a library allocate memory while it runs (no counterpart in the paper).
+ *
+ * Some hosts hand a plugin no allocator (all GPU memory is budgeted up front),
+ * and some latency-critical loops must not pay for the device-wide
+ * synchronisation that cudaMalloc / cudaFree can cause.  This call computes the
+ * same result as qm_score_partition (same kernels, bit-identical output) but
+ * allocates nothing: its scratch memory is one fixed device array of
+ * QM_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads the
+ * library keeps until the process exits, and the result is copied straight
+ * into *out.
+ *   g       graph loaded with qm_load_graph
+ *   labels  device int32[n_nodes], labels in [0, K)
+ *   out     host struct, written on success
+ * Limits and rules:
+ *   - The workspace of the call must fit the array: about 4 * n_nodes + 20 * K
+ *     bytes (for example 10,000,000 nodes with 100,000 label ids).  Larger
+ *     calls return QM_EOVERFLOW with the required size in qm_last_error().
+ *   - labels must be device memory (QM_EINVAL otherwise); no per-community
+ *     outputs.
+ *   - All calls share the one array, and each call clears what must start at
+ *     zero.  Calls whose GPU work overlaps (on different streams, or from
+ *     different threads) race on it: issue them one after the other.
+ *   - The first call on a device does a one-time set-up on that device (it
+ *     resolves the array's device address and the kernels' launch shape); make
+ *     that first call before any stream capture begins.
+ */
+#define QM_NOALLOC_SCRATCH_BYTES (48u * 1024u * 1024u)
+qm_status qm_score_partition_noalloc(const qm_graph *g, const int32_t *labels, int32_t K,
+                                     qm_quality *out, void *stream);
+
 /* Number of this library's kernel launches issued since load (for accounting). */
 int64_t qm_kernel_launches(void);
 

@@ -90,6 +90,11 @@ static void trace_collect()
     t.used = 0;
 }
 
+qm_status qm::set_error(qm_status s, const char *msg)
+{
+    return fail(s, msg ? msg : "");
+}
+
 // ------------------------------------------------------------------ device info
 
 struct DeviceGuard {
@@ -279,6 +284,14 @@ struct qm_graph {
     std::map<int, Shape> tuning;        // plain path, by size bucket
     std::map<int, Shape> tuning_batch;  // batched path, by size bucket
 };
+
+qm_status qm::graph_device_view(const qm_graph *g, GraphDev *out, int *device)
+{
+    if (!g || !out || !device) return QM_EINVAL;
+    *out = g->d;
+    *device = g->device;
+    return QM_OK;
+}
 
 static int log2i(long long x)
 {

@@ -140,6 +140,14 @@ int launch_batched(const BatchItem *items_dev, int count, int *queue, const Batc
                    const Shape &sh, int num_sms, cudaStream_t s, TraceFn tr);
 int batched_blocks_per_sm(const Shape &sh);
 
+// ---- used by the allocation-free entry point (qm_noalloc.cu)
+
+// Records the calling thread's error message (read by qm_last_error) and
+// returns s.
+qm_status set_error(qm_status s, const char *msg);
+// Device copy and device id of a loaded graph; QM_EINVAL for a null handle.
+qm_status graph_device_view(const qm_graph *g, GraphDev *out, int *device);
+
 // ---- graph validation
 int launch_validate(const GraphDev &g, int full, int *status, unsigned long long *max_deg, int num_sms,
                     cudaStream_t s);
