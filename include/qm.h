@@ -227,13 +227,21 @@ qm_status qm_release_cache(void);
  * (log2 n_nodes, log2 n_arcs, log2 K).  qm_get_tuning reports the shape the
  * next call of that bucket will use: threads per block, shared-memory bytes per
  * block, and the community size above which a whole block (not a warp) scores a
- * community.
+ * community (used by algorithm 0 only).  algorithm selects the scoring pipeline:
+ *   0  one kernel visits every community's members and gathers their
+ *      neighbours' labels itself;
+ *   1  (default) the neighbour labels are first written out in community order
+ *      (one streaming pass over the arcs), then a second kernel counts each
+ *      community's contiguous segment and a third forms the FP64 terms of all
+ *      communities in parallel.
+ * Both give bit-identical results.
  */
 typedef struct {
     int32_t threads;
     int32_t smem_bytes;
     int32_t big_community;
     int32_t blocks_per_sm;
+    int32_t algorithm;
 } qm_tuning;
 
 qm_status qm_autotune(const qm_graph *g, const int32_t *labels, int32_t K, qm_mem where,

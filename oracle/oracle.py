@@ -61,8 +61,9 @@ def _load():
     lib.oq_pairs_bruteforce.argtypes = [p, p, i64, p]
     lib.oq_compare_bruteforce.argtypes = [p, p, i64, i32, i32, p]
     lib.oq_score_bruteforce.argtypes = [p, p, i64, p, i32, p]
+    lib.oq_score_communities.argtypes = [p, p, i64, p, i32, p, i64, p, p]
     for f in (lib.oq_validate_graph, lib.oq_score, lib.oq_compare, lib.oq_pairs_bruteforce,
-              lib.oq_compare_bruteforce, lib.oq_score_bruteforce):
+              lib.oq_compare_bruteforce, lib.oq_score_bruteforce, lib.oq_score_communities):
         f.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -161,6 +162,21 @@ def score_bruteforce(row_ptr, col, labels, K: int) -> dict:
     _check(_load().oq_score_bruteforce(_ptr(row_ptr), _ptr(col), len(row_ptr) - 1, _ptr(labels),
                                        int(K), _ptr(dbl)), "score_bruteforce")
     return dict(modularity=float(dbl[0]), modularity_density=float(dbl[1]))
+
+
+def score_communities(row_ptr, col, labels, K: int, ids) -> dict:
+    """Per-community values of Eq. (9) and Sec. II-B.3 for the sampled ids only."""
+    row_ptr = _as(row_ptr, np.int64)
+    col = _as(col, np.int32)
+    labels = _as(labels, np.int32)
+    ids = _as(ids, np.int32)
+    m = len(ids)
+    i64 = np.zeros((m, 4), np.int64)
+    dbl = np.zeros((m, 2), np.float64)
+    _check(_load().oq_score_communities(_ptr(row_ptr), _ptr(col), len(row_ptr) - 1, _ptr(labels), int(K),
+                                        _ptr(ids), m, _ptr(i64), _ptr(dbl)), "score_communities")
+    return dict(size=i64[:, 0], intra_edges=i64[:, 1], inter_edges=i64[:, 2], distinct_neighbours=i64[:, 3],
+                qds_term=dbl[:, 0], split=dbl[:, 1])
 
 
 def within(gpu: float, ref: float, cond: float = 0.0, rel: float = 1e-12) -> bool:

@@ -554,3 +554,82 @@ int oq_score_bruteforce(const int64_t *row_ptr, const int32_t *col, int64_t n,
     dbl[1] = (double)sum_get(&qds);
     return OQ_OK;
 }
+
+/*
+ * Per-community evaluation for a sample of community ids (used to check very
+ * large inputs one community at a time).  For each sampled community c it
+ * collects the members of c, walks their rows, and counts |E_c^in|, |E_c^out|
+ * and |E_c,cj| for every neighbouring community cj (sorting the neighbour
+ * labels), then forms the bracketed term of Eq. (9) for c.  Community sizes come
+ * from one pass over all labels.
+ *   ids[m]   sampled community ids (any order, repeats allowed)
+ *   out_i64  [m][4]: |c|, |E_c^in|, |E_c^out|, number of distinct cj
+ *   out_dbl  [m][2]: Qds term of c (Eq. 9), split penalty sum_j |E_cj|^2/(2|E||c||cj|)
+ */
+int oq_score_communities(const int64_t *row_ptr, const int32_t *col, int64_t n,
+                         const int32_t *label, int32_t K, const int32_t *ids, int64_t m,
+                         int64_t *out_i64, double *out_dbl)
+{
+    if (n < 1 || K < 1 || m < 0)
+        return OQ_EINVAL;
+    int64_t nnz = row_ptr[n];
+    if (nnz <= 0)
+        return OQ_EINVAL;
+    const long double E = (long double)(nnz / 2);
+    int64_t *size = (int64_t *)calloc((size_t)K, sizeof(int64_t));
+    if (!size)
+        return OQ_ENOMEM;
+    for (int64_t u = 0; u < n; u++) {
+        if (label[u] < 0 || label[u] >= K) { free(size); return OQ_EINVAL; }
+        size[label[u]]++;
+    }
+    int rc = OQ_OK;
+    for (int64_t s = 0; s < m && rc == OQ_OK; s++) {
+        const int32_t c = ids[s];
+        if (c < 0 || c >= K) { rc = OQ_EINVAL; break; }
+        int64_t in_arcs = 0, out_arcs = 0, nb = 0;
+        int32_t *nbr = NULL;
+        size_t cap = 0;
+        for (int64_t u = 0; u < n; u++) {
+            if (label[u] != c) continue;
+            for (int64_t k = row_ptr[u]; k < row_ptr[u + 1]; k++) {
+                int32_t lv = label[col[k]];
+                if (lv == c) { in_arcs++; continue; }
+                out_arcs++;
+                if ((size_t)nb == cap) {
+                    cap = cap ? 2 * cap : 1024;
+                    int32_t *t = (int32_t *)realloc(nbr, cap * sizeof(int32_t));
+                    if (!t) { rc = OQ_ENOMEM; break; }
+                    nbr = t;
+                }
+                nbr[nb++] = lv;
+            }
+            if (rc != OQ_OK) break;
+        }
+        if (rc != OQ_OK) { free(nbr); break; }
+        qsort(nbr, (size_t)nb, sizeof(int32_t), cmp_i32);
+        long double split = 0.0L, sc = (long double)size[c];
+        int64_t distinct = 0;
+        for (int64_t a = 0; a < nb;) {
+            int64_t b = a;
+            while (b < nb && nbr[b] == nbr[a]) b++;
+            long double x = (long double)(b - a);
+            split += (x / (2.0L * E)) * (x / (sc * (long double)size[nbr[a]]));
+            distinct++;
+            a = b;
+        }
+        free(nbr);
+        long double in = (long double)(in_arcs / 2), out = (long double)out_arcs;
+        long double d = size[c] > 1 ? 2.0L * in / (sc * (sc - 1.0L)) : 0.0L;
+        long double t1 = in / E * d;
+        long double t2 = (2.0L * in + out) / (2.0L * E) * d;
+        out_i64[4 * s + 0] = size[c];
+        out_i64[4 * s + 1] = in_arcs / 2;
+        out_i64[4 * s + 2] = out_arcs;
+        out_i64[4 * s + 3] = distinct;
+        out_dbl[2 * s + 0] = size[c] ? (double)(t1 - t2 * t2 - split) : 0.0;
+        out_dbl[2 * s + 1] = (double)split;
+    }
+    free(size);
+    return rc;
+}

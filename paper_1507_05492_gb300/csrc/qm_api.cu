@@ -312,6 +312,7 @@ static Shape default_shape()
     s.smem_bytes = 96 * 1024;
     s.big_community = 48;
     s.blocks_per_sm = 0;
+    s.algo = 1;
     return s;
 }
 
@@ -321,11 +322,12 @@ static Shape resolve_plain(Shape s)
     cudaGetDevice(&dev);
     num_sms_of(dev);  // kernel set-up before the occupancy query
     static std::mutex mu;
-    static std::map<std::tuple<int, int>, int> occ;
+    static std::map<std::tuple<int, int, int>, int> occ;
     std::lock_guard<std::mutex> lk(mu);
-    auto key = std::make_tuple(s.threads, s.smem_bytes);
+    auto key = std::make_tuple(s.threads, s.smem_bytes, s.algo);
     auto it = occ.find(key);
-    if (it == occ.end()) it = occ.emplace(key, std::max(1, score_blocks_per_sm(s))).first;
+    if (it == occ.end())
+        it = occ.emplace(key, std::max(1, s.algo ? count_blocks_per_sm(s) : score_blocks_per_sm(s))).first;
     s.blocks_per_sm = it->second;
     return s;
 }
@@ -357,7 +359,7 @@ static Shape shape_for(qm_graph *g, int K, bool batched)
 static bool shape_ok(const qm_tuning *t)
 {
     return t && t->threads >= 64 && t->threads <= 1024 && t->threads % 32 == 0 && t->smem_bytes >= 16384 &&
-           t->smem_bytes <= MAX_DYN_SMEM && t->big_community >= 1 &&
+           t->smem_bytes <= MAX_DYN_SMEM && t->big_community >= 1 && (t->algorithm == 0 || t->algorithm == 1) &&
            plan_smem(t->threads, t->smem_bytes).max_used_w >= 32;
 }
 
@@ -510,7 +512,7 @@ static size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 qm_status qm_workspace_bytes(const qm_graph *g, int32_t K, int32_t with_compare, int32_t k_truth, size_t *bytes)
 {
     if (!g || !bytes || K < 1 || (with_compare && k_truth < 1)) return fail(QM_EINVAL, "bad argument");
-    size_t b = score_ws_bytes(g->n, K) + al256((size_t)g->n * 4);
+    size_t b = std::max(score_ws_bytes(g->n, K), score2_ws_bytes(g->n, g->n_arcs, K)) + al256((size_t)g->n * 4);
     if (with_compare) b += compare_ws_bytes(g->n, k_truth, K) + al256((size_t)g->n * 4);
     *bytes = b;
     return QM_OK;
@@ -521,7 +523,7 @@ static qm_status score_impl(qm_graph *g, const int32_t *labels, int32_t K, qm_me
                             const qm_percomm *pc, cudaStream_t s, const Shape &sh)
 {
     const long long n = g->n;
-    size_t need = score_ws_bytes(n, K);
+    size_t need = sh.algo ? score2_ws_bytes(n, g->n_arcs, K) : score_ws_bytes(n, K);
     const size_t lab_off = need;
     if (where == QM_HOST) need += al256((size_t)n * 4);
     const size_t pc_off = need;
@@ -530,7 +532,7 @@ static qm_status score_impl(qm_graph *g, const int32_t *labels, int32_t K, qm_me
     Lease ws(g_pool.acquire(need, g->device, false));
     Lease pin(g_pool.acquire(al256(sizeof(qm_quality)) + 256, g->device, true));
     if (!ws.b || !pin.b) return fail(QM_ENOMEM, "scratch allocation failed");
-    ScoreWs w = carve_score_ws(ws.ptr(), n, K);
+    ScoreWs w = sh.algo ? carve_score2_ws(ws.ptr(), n, g->n_arcs, K) : carve_score_ws(ws.ptr(), n, K);
     const int32_t *dl = labels;
     if (where == QM_HOST) {
         dl = (const int32_t *)(ws.ptr() + lab_off);
@@ -548,7 +550,10 @@ static qm_status score_impl(qm_graph *g, const int32_t *labels, int32_t K, qm_me
             CK(cudaMemsetAsync(dp[k], 0, (size_t)K * 8, s));
         }
     }
-    const int L = launch_score(g->d, dl, K, w, sh, pc ? &pcd : nullptr, num_sms_of(g->device), s, trace_begin());
+    const int L = sh.algo ? launch_score2(g->d, dl, K, w, sh, pc ? &pcd : nullptr, num_sms_of(g->device), s,
+                                          trace_begin())
+                          : launch_score(g->d, dl, K, w, sh, pc ? &pcd : nullptr, num_sms_of(g->device), s,
+                                         trace_begin());
     if (L < 0) return cuda_fail(cudaGetLastError(), "launch_score");
     g_launches += L;
     CK(cudaMemcpyAsync(pin.ptr(), w.status, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -604,7 +609,9 @@ qm_status qm_compare_partitions(const int32_t *truth, const int32_t *found, int6
         CK(cudaMemcpyAsync((void *)df, found, (size_t)n * 4, cudaMemcpyHostToDevice, s));
     }
     CK(cudaMemsetAsync(ws.ptr(), 0, w.zero_bytes, s));
-    Shape sh = resolve_plain(default_shape());
+    Shape cs = default_shape();
+    cs.algo = 0;  // occupancy of the community-pass kernels
+    Shape sh = resolve_plain(cs);
     const int L = launch_compare(dt, df, n, ka, kb, w, sh, num_sms_of(dev), s, trace_begin());
     if (L < 0) return cuda_fail(cudaGetLastError(), "launch_compare");
     g_launches += L;
@@ -889,6 +896,7 @@ qm_status qm_get_tuning(const qm_graph *gc, int32_t K, qm_tuning *t)
     t->smem_bytes = s.smem_bytes;
     t->big_community = s.big_community;
     t->blocks_per_sm = s.blocks_per_sm;
+    t->algorithm = s.algo;
     return QM_OK;
 }
 
@@ -901,6 +909,7 @@ qm_status qm_set_tuning(const qm_graph *gc, int32_t K, const qm_tuning *t)
     s.smem_bytes = t->smem_bytes;
     s.big_community = t->big_community;
     s.blocks_per_sm = 0;
+    s.algo = t->algorithm;
     std::lock_guard<std::mutex> lk(g->mu);
     g->tuning[bucket_of(g->n, g->n_arcs, K)] = s;
     return QM_OK;
@@ -929,15 +938,18 @@ qm_status qm_autotune(const qm_graph *gc, const int32_t *labels, int32_t K, qm_m
     float best_ms = 1e30f;
     Shape best = default_shape();
     qm_quality q;
+    for (int al : {1, 0})
     for (int th : threads_c)
         for (int sm : smem_c)
             for (int bg : big_c) {
+                if (al == 1 && bg != big_c[0]) continue;  // the two-phase path has no size split
                 Shape sh;
                 sh.threads = th;
                 sh.smem_bytes = sm;
                 sh.big_community = bg;
                 sh.blocks_per_sm = 0;
-                qm_tuning tt{th, sm, bg, 0};
+                sh.algo = al;
+                qm_tuning tt{th, sm, bg, 0, al};
                 if (!shape_ok(&tt)) continue;
                 sh = resolve_plain(sh);
                 if (sh.blocks_per_sm < 1) continue;
@@ -970,6 +982,7 @@ qm_status qm_autotune(const qm_graph *gc, const int32_t *labels, int32_t K, qm_m
         chosen->smem_bytes = best.smem_bytes;
         chosen->big_community = best.big_community;
         chosen->blocks_per_sm = best.blocks_per_sm;
+        chosen->algorithm = best.algo;
     }
     return QM_OK;
 }

@@ -22,7 +22,8 @@ __host__ __device__ static inline size_t al(size_t x) { return (x + 255) / 256 *
 size_t batch_scratch_bytes(long long n_max, int k_max, int kt_max, int slots)
 {
     const size_t per = al((size_t)n_max * 4) + al((size_t)(k_max + 1) * 4) + al((size_t)kt_max * 4) * 2 +
-                       al((size_t)kt_max * 8) + al((size_t)k_max * 4) * 3 + al((size_t)k_max * 4);
+                       al((size_t)kt_max * 8) + al((size_t)k_max * 4) * 3 + al((size_t)k_max * 4) +
+                       al((size_t)k_max * 8);
     return per * (size_t)slots;
 }
 
@@ -47,6 +48,8 @@ BatchScratch carve_batch_scratch(void *base, long long n_max, int k_max, int kt_
     b.big_list = (int *)p;          // three lists of k_max per slot
     p += al((size_t)k_max * 4) * 3 * slots;
     b.size = (int *)p;
+    p += al((size_t)k_max * 4) * slots;
+    b.recip = (unsigned long long *)p;
     return b;
 }
 
@@ -83,6 +86,7 @@ __global__ void __launch_bounds__(1024) k_batched(BatchKArgs a)
     int *big_cmp = big_score + al((size_t)bs.k_max * 4) / 4;
     int *ovf = big_cmp + al((size_t)bs.k_max * 4) / 4;
     int *gsize = (int *)((char *)bs.size + sl * al((size_t)bs.k_max * 4));
+    unsigned long long *recip = (unsigned long long *)((char *)bs.recip + sl * al((size_t)bs.k_max * 8));
 
     for (int i = tid; i < p.cap; i += T) slot[i] = 0ull;
     for (int i = tid; i < 2 * (W + 1); i += T) ctl[i] = 0;
@@ -90,8 +94,6 @@ __global__ void __launch_bounds__(1024) k_batched(BatchKArgs a)
     const SmemTable tb{slot, used, &ctl[0], &ctl[1], p.cap, p.max_used};
     const SmemTable tw{slot + wid * p.cap_w, used + wid * p.max_used_w, &ctl[2 + 2 * wid], &ctl[3 + 2 * wid],
                        p.cap_w, p.max_used_w};
-    unsigned *offw = offs + wid * 33;
-    long long *rsw = rs + wid * 32;
 
     for (;;) {
         if (tid == 0) s_item = atomicAdd(a.queue, 1);
@@ -155,6 +157,7 @@ __global__ void __launch_bounds__(1024) k_batched(BatchKArgs a)
             if (c < K) {
                 start[c] = (int)(carry + excl);
                 cnt[c] = (int)(carry + excl);
+                recip[c] = size_recip(s);
                 if (do_score && s > a.big_thr) {
                     const int k = atomicAdd(&s_nbig, 1);
                     if (QM_CHK(k, bs.k_max, 12)) big_score[k] = c;
@@ -203,6 +206,7 @@ __global__ void __launch_bounds__(1024) k_batched(BatchKArgs a)
             x.labels = I.labels;
             x.members = members;
             x.start = start;
+            x.recip = recip;
             x.E = I.n_arcs / 2;
             x.n = n;
             x.n_arcs = I.n_arcs;
@@ -237,7 +241,7 @@ __global__ void __launch_bounds__(1024) k_batched(BatchKArgs a)
                 while (mask) {
                     const int j = __ffs(mask) - 1;
                     mask &= mask - 1;
-                    if (!score_community(x, base + j, tw, offw, rsw, &sacc[wid], lane, 32, red))
+                    if (!score_community(x, base + j, tw, offs, rs, &sacc[wid], lane, 32, red))
                         if (lane == 0) {
                             const int k = atomicAdd(&s_novf, 1);
                             if (QM_CHK(k, bs.k_max, 13)) ovf[k] = base + j;

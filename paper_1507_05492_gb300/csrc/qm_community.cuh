@@ -30,6 +30,7 @@ struct ScoreCtx {
     const int *labels;
     const int *members;   // node ids grouped by label: members[start[c] .. start[c+1])
     const int *start;     // int[K + 1]
+    const unsigned long long *recip;  // per community: size_recip(|c|)
     long long E;          // |E|
     long long n, n_arcs;  // graph size (bounds of the arrays above)
     int K;
@@ -170,40 +171,102 @@ __device__ __forceinline__ void tab_wipe(const SmemTable &t, int gtid, int gsize
     for (int i = gtid; i < t.cap; i += gsize) t.slot[i] = 0ull;
 }
 
-// Score community c with a group.  Returns false only for a warp group whose
-// table overflowed (nothing was accumulated; the caller re-queues c for a block).
-// A block group handles overflow itself by splitting the neighbour ids into R
-// hash classes and walking the rows once per class.
-//   offs: group-shared unsigned[gsize + 1]; rs: group-shared long long[gsize]
-//   ctl:  group-shared int[2] (n_used, overflow) already wired into `tab`
+__device__ __forceinline__ u128 shfl_down_u128(u128 v, int d)
+{
+    unsigned long long lo = __shfl_down_sync(0xffffffffu, (unsigned long long)v, d);
+    unsigned long long hi = __shfl_down_sync(0xffffffffu, (unsigned long long)(v >> 64), d);
+    return ((u128)hi << 64) | lo;
+}
+
+__device__ __forceinline__ double u128_to_double(u128 v)
+{
+    return __dadd_rn(__dmul_rn((double)(unsigned long long)(v >> 64), 18446744073709551616.0),
+                     (double)(unsigned long long)v);
+}
+
+// Group totals of NW 64-bit words per thread, delivered to the group leader
+// (group thread 0): a warp reduction, then for a block group one exchange
+// through `red` (>= 32 * NW words) and one barrier.  Only the leader's result
+// is meaningful.  Words are added as unsigned integers, so a 128-bit value can
+// travel as two words and be recombined with carry by the caller (see sum128).
+template <int NW>
+__device__ __forceinline__ void group_words_to_leader(unsigned long long (&v)[NW], int gsize,
+                                                      unsigned long long *red)
+{
+#pragma unroll
+    for (int k = 0; k < NW; ++k) v[k] = warp_sum_u64(v[k]);
+    if (gsize == 32) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NW; ++k) red[wid * NW + k] = v[k];
+    block_sync();
+    if (threadIdx.x == 0)
+        for (int w = 1; w < nw; ++w)
+#pragma unroll
+            for (int k = 0; k < NW; ++k) v[k] += red[w * NW + k];
+}
+
+// A 128-bit group total, summed exactly (warp shuffles of both halves, then the
+// warps' totals through `red` at word offset `at`).  Valid in the leader only.
+__device__ __forceinline__ u128 group_u128_to_leader(u128 v, int gsize, unsigned long long *red, int at)
+{
+    for (int d = 16; d > 0; d >>= 1) v += shfl_down_u128(v, d);
+    if (gsize == 32) return v;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) {
+        red[at + 2 * wid] = (unsigned long long)v;
+        red[at + 2 * wid + 1] = (unsigned long long)(v >> 64);
+    }
+    block_sync();
+    if (threadIdx.x == 0)
+        for (int w = 1; w < nw; ++w) v += ((u128)red[at + 2 * w + 1] << 64) | red[at + 2 * w];
+    return v;
+}
+
+// Per-community reciprocal used by the pair sums: floor((2^64 - 1) / s) for
+// s >= 2, 0 for s = 1.
+__device__ __forceinline__ unsigned long long size_recip(long long s)
+{
+    return s >= 2 ? 0xFFFFFFFFFFFFFFFFull / (unsigned long long)s : 0ull;
+}
+
+// Score community c with a group (one warp, or a whole block).  Returns false
+// only for a warp whose table overflowed (nothing was accumulated; the caller
+// re-queues c for a block).  A block handles overflow itself by splitting the
+// neighbour ids into R hash classes and walking the rows once per class.
+//
+// Each warp of the group takes its own chunks of 32 members (a warp-local
+// prefix sum of their degrees in `offs`/`rs`, the warp's slices of shared
+// staging), so the arc walk needs no block-wide barrier; all warps insert into
+// the group's shared table.  The split penalty of Eq. (9) for community i is
+//   sum_j |E_ij|^2 / (2|E| |c_i| |c_j|) = (sum_j |E_ij|^2 R_j) 2^-64 / (2|E| |c_i|)
+// with R_j = floor(2^64 / |c_j|) (x.recip): the inner sum is an exact 128-bit
+// integer, so only one division per community is done in FP64.  For
+// |c_j| > 2^20 (R_j < 2^44) the term is formed in FP64 instead, keeping every
+// term's relative error below 2^-43.
 __device__ __forceinline__ bool score_community(const ScoreCtx &x, int c, const SmemTable &tab,
                                                 unsigned *offs, long long *rs, ScoreAcc *acc,
                                                 int gtid, int gsize, unsigned long long *red)
 {
+    const int lane = threadIdx.x & 31;
+    const int wrank = gtid >> 5;
+    unsigned *offw = offs + (threadIdx.x >> 5) * 33;
+    long long *rsw = rs + (threadIdx.x >> 5) * 32;
     const int mb = __ldcg(&x.start[c]), me = __ldcg(&x.start[c + 1]);
     const long long size = me - mb;
 #ifdef QM_DBG_VERIFY_AGREE
-    if (gsize == 32) {
-        QM_CHK(c == __shfl_sync(0xffffffffu, c, 0) && mb == __shfl_sync(0xffffffffu, mb, 0) &&
-               me == __shfl_sync(0xffffffffu, me, 0) ? 0 : 1, 1, 28);
-    } else {
-        __shared__ int dbg_agree[3];
-        block_sync();
-        if (gtid == 0) { dbg_agree[0] = c; dbg_agree[1] = mb; dbg_agree[2] = me; }
-        block_sync();
-        QM_CHK(c == dbg_agree[0] && mb == dbg_agree[1] && me == dbg_agree[2] ? 0 : 1, 1, 27);
-        block_sync();
-    }
+    if (gsize == 32)
+        QM_CHK(c == __shfl_sync(0xffffffffu, c, 0) && mb == __shfl_sync(0xffffffffu, mb, 0) ? 0 : 1, 1, 28);
 #endif
     unsigned R = 1;
     for (;;) {
-        unsigned long long same = 0, vol = 0;
-        i128 pair_fp = 0;
-        unsigned long long slots = 0, cnt2 = 0;
+        unsigned long long same = 0, vol = 0, slots = 0, cnt2 = 0;
+        u128 inner = 0;
         bool ok = true;
         for (unsigned r = 0; r < R && ok; ++r) {
-            for (int cb = mb; cb < me; cb += gsize) {
-                const int i = cb + gtid;
+            for (int cb = mb + wrank * 32; cb < me; cb += gsize) {
+                const int i = cb + lane;
                 unsigned d = 0;
                 long long rsi = 0;
                 if (i < me && QM_CHK(i, x.n, 1)) {
@@ -214,29 +277,29 @@ __device__ __forceinline__ bool score_community(const ScoreCtx &x, int c, const 
                     }
                 }
                 if (r == 0) vol += d;
-                unsigned excl;
-                const int nm = min(gsize, me - cb);
-                const unsigned total = group_exclusive_scan(d, excl, gsize, red);
-                if (gtid < nm) { offs[gtid] = excl; rs[gtid] = rsi; }
-                group_sync(gsize);
+                unsigned inc = d;
+#pragma unroll
+                for (int s2 = 1; s2 < 32; s2 <<= 1) {
+                    const unsigned t = __shfl_up_sync(0xffffffffu, inc, s2);
+                    if (lane >= s2) inc += t;
+                }
+                const unsigned total = __shfl_sync(0xffffffffu, inc, 31);
+                const int nm = min(32, me - cb);
+                if (lane < nm) { offw[lane] = inc - d; rsw[lane] = rsi; }
+                __syncwarp();
 #ifdef QM_DBG_VERIFY_OFFS
-                if (gtid < nm)
-                    QM_CHKX(offs[gtid] + d == (gtid + 1 < nm ? offs[gtid + 1] : total) ? 0 : 1, 1,
-                            23 + 100 * (gsize == 32 ? 1 : 2) + 1000 * (gtid + 1 < nm ? 1 : 2),
-                            c, gtid, ((long long)nm << 32) | (unsigned)(me - mb),
-                            ((long long)total << 32) | (unsigned)(offs[gtid] + d));
-                if (gtid == 0) QM_CHK(gsize == 32 || gsize == (int)blockDim.x ? 0 : 1, 1, 26);
+                if (lane < nm) QM_CHK(inc == (lane + 1 < nm ? offw[lane + 1] : total) ? 0 : 1, 1, 23);
 #endif
-                for (unsigned e0 = gtid; e0 < total; e0 += 4u * gsize) {
+                for (unsigned e0 = lane; e0 < total; e0 += 128u) {
                     int v[4], lv[4];
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        const unsigned e = e0 + k * gsize;
+                        const unsigned e = e0 + 32u * k;
                         v[k] = -1;
                         if (e < total) {
-                            const int o = upper_bound_smem(offs, nm, e) - 1;
-                            if (QM_CHK(o, nm, 4) && QM_CHK(rs[o] + (e - offs[o]), x.n_arcs, 3))
-                                v[k] = __ldg(&x.col[rs[o] + (e - offs[o])]);
+                            const int o = upper_bound_smem(offw, nm, e) - 1;
+                            if (QM_CHK(o, nm, 4) && QM_CHK(rsw[o] + (e - offw[o]), x.n_arcs, 3))
+                                v[k] = __ldg(&x.col[rsw[o] + (e - offw[o])]);
                             if (!QM_CHK(v[k], x.n, 5)) v[k] = -1;
                         }
                     }
@@ -253,18 +316,27 @@ __device__ __forceinline__ bool score_community(const ScoreCtx &x, int c, const 
                         }
                     }
                 }
-                group_sync(gsize);
+                __syncwarp();
             }
-            if (*tab.overflow) {
+            group_sync(gsize);
+            if (*(volatile int *)tab.overflow) {
                 ok = false;
                 break;
             }
             tab_drain(tab, gtid, gsize, [&](int key, long long cnt) {
                 if (!QM_CHK(key, x.K, 7)) return;
-                const long long sj = __ldcg(&x.start[key + 1]) - __ldcg(&x.start[key]);
-                pair_fp += fp_from_double(pair_term(cnt, size, sj, x.E), SC_QDS);
+                const unsigned long long q = (unsigned long long)cnt * (unsigned long long)cnt;
+                const unsigned long long rj = __ldcg(&x.recip[key]);
+                if (rj >= (1ull << 44)) {
+                    inner += (u128)q * (u128)rj;
+                } else if (rj == 0ull) {
+                    inner += (u128)q << 64;
+                } else {
+                    const long long sj = __ldcg(&x.start[key + 1]) - __ldcg(&x.start[key]);
+                    inner += (u128)fp_from_double(__ddiv_rn((double)q, (double)sj), 64);
+                }
                 ++slots;
-                cnt2 += (unsigned long long)(cnt * cnt);
+                cnt2 += q;
             });
             group_sync(gsize);
             if (gtid == 0) *tab.n_used = 0;
@@ -276,11 +348,18 @@ __device__ __forceinline__ bool score_community(const ScoreCtx &x, int c, const 
             if (gtid == 0) { *tab.n_used = 0; *tab.overflow = 0; }
             group_sync(gsize);
             if (gsize == 32) return false;
-            // Pass 0 completed, so the boundary arc count E_out (an upper bound of
-            // the distinct neighbour communities) is known: size R from it.
-            const unsigned long long eout = group_sum_u64(vol, gsize, red) - group_sum_u64(same, gsize, red);
-            const unsigned long long need = (eout * 4 + 3ull * tab.max_used - 1) / (3ull * tab.max_used);
-            unsigned long long nr = max((unsigned long long)R * 2ull, need);
+            // Pass 0 completed, so the exact boundary arc count E_out (an upper
+            // bound of the distinct neighbour communities) sizes R.
+            unsigned long long w2[2] = {vol, same};
+            group_words_to_leader<2>(w2, gsize, red);
+            if (gtid == 0) {
+                const unsigned long long eout = w2[0] - w2[1];
+                const unsigned long long need = (eout * 4 + 3ull * tab.max_used - 1) / (3ull * tab.max_used);
+                red[255] = max((unsigned long long)R * 2ull, need);
+            }
+            group_sync(gsize);
+            const unsigned long long nr = red[255];
+            group_sync(gsize);
             if (nr > R_MAX) {
                 if (gtid == 0) atomicOr(x.err, 2);
                 return true;
@@ -288,20 +367,22 @@ __device__ __forceinline__ bool score_community(const ScoreCtx &x, int c, const 
             R = (unsigned)nr;
             continue;
         }
-        // commit: group totals, then the group leader adds them to the group's
-        // shared accumulator
-        same = group_sum_u64(same, gsize, red);
-        vol = group_sum_u64(vol, gsize, red);
-        slots = group_sum_u64(slots, gsize, red);
-        cnt2 = group_sum_u64(cnt2, gsize, red);
-        const i128 pc_pair = group_sum_i128(pair_fp, gsize, red);
+        // commit: the group leader receives the totals and adds the community's
+        // terms to the group's shared accumulator
+        unsigned long long w4[4] = {same, vol, slots, cnt2};
+        group_words_to_leader<4>(w4, gsize, red);
+        const u128 inner_t = group_u128_to_leader(inner, gsize, red, 128);
         if (gtid == 0) {
+            same = w4[0];
+            vol = w4[1];
             const long long ein = (long long)(same / 2), eout = (long long)(vol - same);
             double qs, dens, contr, expn, cond;
             community_terms(ein, eout, size, x.E, qs, dens, contr, expn, cond);
-            acc->qds_pair += pc_pair;
-            acc->slots += slots;
-            acc->cnt2 += cnt2;
+            const double pen = __ddiv_rn(ldexp(u128_to_double(inner_t), -64),
+                                         __dmul_rn(__dmul_rn(2.0, (double)x.E), (double)size));
+            acc->qds_pair += fp_from_double(pen, SC_QDS);
+            acc->slots += w4[2];
+            acc->cnt2 += w4[3];
             acc->qds_self += fp_from_double(qs, SC_QDS);
             acc->dens += fp_from_double(dens, SC_MEAN);
             acc->contr += fp_from_double(contr, SC_MEAN);
@@ -318,7 +399,7 @@ __device__ __forceinline__ bool score_community(const ScoreCtx &x, int c, const 
             if (x.pc_contr) x.pc_contr[c] = contr;
             if (x.pc_expn) x.pc_expn[c] = expn;
             if (x.pc_cond) x.pc_cond[c] = cond;
-            if (x.pc_qds) x.pc_qds[c] = __dsub_rn(qs, fp_to_double(pc_pair, SC_QDS));
+            if (x.pc_qds) x.pc_qds[c] = __dsub_rn(qs, pen);
         }
         return true;
     }
@@ -351,7 +432,7 @@ __device__ __forceinline__ void compare_community(const CompareCtx &x, int b, co
                 if (R == 1 || tab_split((unsigned)a, R) == r) tab_insert(tab, (unsigned)a);
             }
             group_sync(gsize);
-            if (*tab.overflow) { ok = false; break; }
+            if (*(volatile int *)tab.overflow) { ok = false; break; }
             tab_drain(tab, gtid, gsize, [&](int a, long long n) {
                 const long long na = __ldcg(&x.size_a[a]);
                 a11 += (unsigned long long)(n * (n - 1) / 2);
@@ -374,16 +455,23 @@ __device__ __forceinline__ void compare_community(const CompareCtx &x, int b, co
             R *= 2;
             continue;
         }
-        colmax = group_max_u32(colmax, gsize, red);
-        a11 = group_sum_u64(a11, gsize, red);
-        cells = group_sum_u64(cells, gsize, red);
-        vi = group_sum_i128(vi, gsize, red);
-        hn = group_sum_i128(hn, gsize, red);
+        for (int d = 16; d > 0; d >>= 1) colmax = max(colmax, __shfl_down_sync(0xffffffffu, colmax, d));
+        unsigned long long w[3] = {a11, cells, 0ull};
+        // the column maximum travels through the same exchange: the warps'
+        // maxima are combined by the leader below
+        if (gsize != 32) {
+            if ((threadIdx.x & 31) == 0) red[96 + (threadIdx.x >> 5)] = colmax;
+        }
+        group_words_to_leader<3>(w, gsize, red);
+        const u128 vi_t = group_u128_to_leader((u128)vi, gsize, red, 128);
+        const u128 hn_t = group_u128_to_leader((u128)hn, gsize, red, 192);
         if (gtid == 0) {
-            acc->a11 += a11;
-            acc->cells += cells;
-            acc->vi += vi;
-            acc->hnum += hn;
+            if (gsize != 32)
+                for (int k = 1; k < (int)(blockDim.x >> 5); ++k) colmax = max(colmax, (unsigned)red[96 + k]);
+            acc->a11 += w[0];
+            acc->cells += w[1];
+            acc->vi += (i128)vi_t;
+            acc->hnum += (i128)hn_t;
             acc->nvd += colmax;
             acc->sb += (unsigned long long)(nb * (nb - 1) / 2);
             acc->hden += fp_from_double(entropy_term(nb, x.N), SC_H);
@@ -391,6 +479,154 @@ __device__ __forceinline__ void compare_community(const CompareCtx &x, int b, co
         }
         return;
     }
+}
+
+// ---------------------------------------------------------------- two-phase scoring
+//
+// Phase A (k_expand) writes, for every member of every community in member
+// order, the labels of its neighbours: community c's arcs occupy the contiguous
+// segment nbr[aoff[start[c]] .. aoff[start[c+1]]).  Phase B (count_community)
+// reads that segment with coalesced loads and counts it.  Phase B leaves one
+// integer record per community; the FP64 terms are formed afterwards for all
+// communities in parallel (k_score_terms).
+
+// Per-community record written by phase B (unsigned 64-bit words).
+enum { REC_SAME = 0, REC_VOL = 1, REC_SLOTS = 2, REC_CNT2 = 3, REC_INNER_LO = 4, REC_INNER_HI = 5, REC_WORDS = 6 };
+
+struct CountCtx {
+    const int *nbr;                   // neighbour labels in community order
+    const unsigned *aoff;             // [n + 1] arc offset of each member position
+    const int *start;                 // [K + 1] member offsets
+    const unsigned long long *recip;  // size_recip(|c|)
+    unsigned long long *rec;          // [K][REC_WORDS]
+    int K;
+    int *err;
+};
+
+// Counts community c's segment with a group.  A warp group is only given
+// communities whose segment fits its table (distinct keys <= segment length),
+// so only a block splits its keys into R classes on overflow.
+__device__ __forceinline__ void count_community(const CountCtx &x, int c, const SmemTable &tab, int gtid,
+                                                int gsize, unsigned long long *red)
+{
+    const unsigned a0 = __ldg(&x.aoff[__ldg(&x.start[c])]);
+    const unsigned a1 = __ldg(&x.aoff[__ldg(&x.start[c + 1])]);
+    unsigned R = 1;
+    for (;;) {
+        unsigned long long same = 0, slots = 0, cnt2 = 0;
+        u128 inner = 0;
+        bool ok = true;
+        for (unsigned r = 0; r < R && ok; ++r) {
+            for (unsigned e0 = a0 + gtid; e0 < a1; e0 += 4u * gsize) {
+                int lv[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const unsigned e = e0 + k * gsize;
+                    lv[k] = e < a1 ? __ldg(&x.nbr[e]) : -1;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (lv[k] < 0 || !QM_CHK(lv[k], x.K, 6)) continue;
+                    if (lv[k] == c) {
+                        if (r == 0) ++same;
+                    } else if (R == 1 || tab_split((unsigned)lv[k], R) == r) {
+                        tab_insert(tab, (unsigned)lv[k]);
+                    }
+                }
+            }
+            group_sync(gsize);
+            if (*(volatile int *)tab.overflow) {
+                ok = false;
+                break;
+            }
+            tab_drain(tab, gtid, gsize, [&](int key, long long cnt) {
+                if (!QM_CHK(key, x.K, 7)) return;
+                const unsigned long long q = (unsigned long long)cnt * (unsigned long long)cnt;
+                const unsigned long long rj = __ldg(&x.recip[key]);
+                if (rj >= (1ull << 44)) {
+                    inner += (u128)q * (u128)rj;
+                } else if (rj == 0ull) {
+                    inner += (u128)q << 64;
+                } else {
+                    const long long sj = __ldg(&x.start[key + 1]) - __ldg(&x.start[key]);
+                    inner += (u128)fp_from_double(__ddiv_rn((double)q, (double)sj), 64);
+                }
+                ++slots;
+                cnt2 += q;
+            });
+            group_sync(gsize);
+            if (gtid == 0) *tab.n_used = 0;
+            group_sync(gsize);
+        }
+        if (!ok) {
+            tab_wipe(tab, gtid, gsize);
+            group_sync(gsize);
+            if (gtid == 0) { *tab.n_used = 0; *tab.overflow = 0; }
+            group_sync(gsize);
+            unsigned long long w1[1] = {same};
+            group_words_to_leader<1>(w1, gsize, red);
+            if (gtid == 0) {
+                const unsigned long long eout = (unsigned long long)(a1 - a0) - w1[0];
+                const unsigned long long need = (eout * 4 + 3ull * tab.max_used - 1) / (3ull * tab.max_used);
+                red[255] = max((unsigned long long)R * 2ull, need);
+            }
+            group_sync(gsize);
+            const unsigned long long nr = red[255];
+            group_sync(gsize);
+            if (nr > R_MAX) {
+                if (gtid == 0) atomicOr(x.err, 2);
+                return;
+            }
+            R = (unsigned)nr;
+            continue;
+        }
+        unsigned long long w3[3] = {same, slots, cnt2};
+        group_words_to_leader<3>(w3, gsize, red);
+        const u128 inner_t = group_u128_to_leader(inner, gsize, red, 128);
+        if (gtid == 0) {
+            unsigned long long *rc = x.rec + (size_t)c * REC_WORDS;
+            rc[REC_SAME] = w3[0];
+            rc[REC_VOL] = (unsigned long long)(a1 - a0);
+            rc[REC_SLOTS] = w3[1];
+            rc[REC_CNT2] = w3[2];
+            rc[REC_INNER_LO] = (unsigned long long)inner_t;
+            rc[REC_INNER_HI] = (unsigned long long)(inner_t >> 64);
+        }
+        return;
+    }
+}
+
+// Eq. (9), Sec. II-B.3 and the Eq. (8) integers of community c from its record.
+__device__ __forceinline__ void terms_from_record(const unsigned long long *rc, long long size, long long E,
+                                                  ScoreAcc &acc, double *pen_out, double *qs_out,
+                                                  double *dens_o, double *contr_o, double *expn_o,
+                                                  double *cond_o)
+{
+    const unsigned long long same = rc[REC_SAME], vol = rc[REC_VOL];
+    const long long ein = (long long)(same / 2), eout = (long long)(vol - same);
+    double qs, dens, contr, expn, cond;
+    community_terms(ein, eout, size, E, qs, dens, contr, expn, cond);
+    const u128 inner = ((u128)rc[REC_INNER_HI] << 64) | rc[REC_INNER_LO];
+    const double pen = __ddiv_rn(ldexp(u128_to_double(inner), -64),
+                                 __dmul_rn(__dmul_rn(2.0, (double)E), (double)size));
+    acc.qds_pair += fp_from_double(pen, SC_QDS);
+    acc.slots += rc[REC_SLOTS];
+    acc.cnt2 += rc[REC_CNT2];
+    acc.qds_self += fp_from_double(qs, SC_QDS);
+    acc.dens += fp_from_double(dens, SC_MEAN);
+    acc.contr += fp_from_double(contr, SC_MEAN);
+    acc.expn += fp_from_double(expn, SC_MEAN);
+    acc.cond += fp_from_double(cond, SC_MEAN);
+    acc.vol2 += (u128)vol * (u128)vol;
+    acc.ein += (unsigned long long)ein;
+    acc.eout += (unsigned long long)eout;
+    acc.nonempty += 1;
+    *pen_out = pen;
+    *qs_out = qs;
+    *dens_o = dens;
+    *contr_o = contr;
+    *expn_o = expn;
+    *cond_o = cond;
 }
 
 // Row side of the contingency table for truth community a (Eqs. 2-4).

@@ -24,6 +24,7 @@ struct Shape {
     int smem_bytes;     // dynamic shared memory per block
     int big_community;  // communities with more members are scored by a whole block
     int blocks_per_sm;  // resident blocks per SM (filled in from occupancy)
+    int algo = 0;       // 0: one-kernel community pass, 1: expand + count (two phases)
 };
 
 // Carving of the dynamic shared memory of a community-major block.
@@ -43,11 +44,15 @@ struct ScoreWs {
     qm_quality *result;         // [1]
     int *size;                  // [K]
     int *start;                 // [K + 1]
+    unsigned long long *recip;  // [K] size_recip(|c|)
     int *cursor;                // [K]
     int *big_list;              // [K]
     int *ovf_list;              // [K]
     int *members;               // [n]
     int *scan_tmp;              // [scan tiles + 1]
+    unsigned *aoff;             // two-phase only: [n + 1] arc offsets of member positions
+    int *nbr;                   // two-phase only: [n_arcs] neighbour labels in community order
+    unsigned long long *rec;    // two-phase only: [K][6] per-community records
     size_t zero_bytes;          // bytes from `status` that must start at zero
 };
 
@@ -69,6 +74,8 @@ struct CompareWs {
 };
 
 size_t score_ws_bytes(long long n, int K);
+size_t score2_ws_bytes(long long n, long long n_arcs, int K);
+ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K);
 size_t compare_ws_bytes(long long n, int ka, int kb);
 ScoreWs carve_score_ws(void *base, long long n, int K);
 CompareWs carve_compare_ws(void *base, long long n, int ka, int kb);
@@ -87,8 +94,11 @@ typedef void (*TraceFn)(const char *name, cudaStream_t s);
 // number of kernels it launched, or -1 on a launch error.
 int launch_score(const GraphDev &g, const int *labels, int K, const ScoreWs &ws, const Shape &sh,
                  const PerCommDev *pc, int num_sms, cudaStream_t s, TraceFn tr);
+int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws, const Shape &sh,
+                  const PerCommDev *pc, int num_sms, cudaStream_t s, TraceFn tr);
 int launch_compare(const int *truth, const int *found, long long n, int ka, int kb,
                    const CompareWs &ws, const Shape &sh, int num_sms, cudaStream_t s, TraceFn tr);
+int count_blocks_per_sm(const Shape &sh);
 
 // Largest dynamic shared memory a community-major block may request.
 constexpr int MAX_DYN_SMEM = 220 * 1024;
@@ -127,7 +137,8 @@ struct BatchScratch {
     int *size_a;             // [slots][kt_max]
     unsigned *rowmax_n;      // [slots][kt_max]
     unsigned long long *rowmax_r; // [slots][kt_max]
-    int *big_list;           // [slots][k_max]
+    int *big_list;           // [slots][3 k_max]
+    unsigned long long *recip; // [slots][k_max]
     long long n_max;
     int k_max, kt_max;
     int slots;

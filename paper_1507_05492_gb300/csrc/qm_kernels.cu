@@ -31,7 +31,7 @@ SmemPlan plan_smem(int T, int S)
     const int W = T / 32;
     int off = 0;
     p.red_off = off;
-    off += 72 * 8;
+    off += 256 * 8;   // reduction exchange: 32 warps x 4 words, two 128-bit slots, a broadcast word
     p.ctl_off = off;
     off += ((2 * (W + 1) * 4 + 15) / 16) * 16;
     p.acc_off = off;    // one ScoreAcc / CompareAcc per warp
@@ -69,6 +69,7 @@ size_t score_ws_bytes(long long n, int K)
     b += align_up(sizeof(qm_quality), 256);     // result
     b += align_up((size_t)K * 4, 256);          // size (zeroed)
     b += align_up((size_t)(K + 1) * 4, 256);    // start
+    b += align_up((size_t)K * 8, 256);          // recip
     b += align_up((size_t)K * 4, 256) * 3;      // cursor, big_list, ovf_list
     b += align_up((size_t)n * 4, 256);          // members
     b += align_up((size_t)(scan_tiles(K) + 1) * 4, 256);
@@ -91,6 +92,8 @@ ScoreWs carve_score_ws(void *base, long long n, int K)
     w.zero_bytes = (size_t)(p - (char *)base);
     w.start = (int *)p;
     p += align_up((size_t)(K + 1) * 4, 256);
+    w.recip = (unsigned long long *)p;
+    p += align_up((size_t)K * 8, 256);
     w.cursor = (int *)p;
     p += align_up((size_t)K * 4, 256);
     w.big_list = (int *)p;
@@ -192,8 +195,8 @@ __global__ void k_hist(const int *__restrict__ a, int ka, int *size_a, const int
 
 // Exclusive prefix of size[0..K) by one block.  Writes start[0..K], optionally
 // cursor = start, and appends ids with size > big_thr to big_list.
-__global__ void k_scan_single(const int *size, int K, int *start, int *cursor, int big_thr,
-                              int *big_list, int *counters, const int *status)
+__global__ void k_scan_single(const int *size, int K, int *start, int *cursor, unsigned long long *recip,
+                              int big_thr, int *big_list, int *counters, const int *status)
 {
     __shared__ unsigned long long red[72];
     if (*status) return;
@@ -209,6 +212,7 @@ __global__ void k_scan_single(const int *size, int K, int *start, int *cursor, i
         const int s = size[i];
         start[i] = (int)run;
         if (cursor) cursor[i] = (int)run;
+        if (recip) recip[i] = size_recip(s);
         if (s > big_thr) big_list[atomicAdd(&counters[C_BIG_COUNT], 1)] = (int)i;
         run += (unsigned)s;
     }
@@ -230,7 +234,8 @@ __global__ void k_scan_tiles(const int *size, int K, int *tile_sum, const int *s
 }
 
 __global__ void k_scan_apply(const int *size, int K, const int *tile_off, int *start, int *cursor,
-                             int big_thr, int *big_list, int *counters, const int *status)
+                             unsigned long long *recip, int big_thr, int *big_list, int *counters,
+                             const int *status)
 {
     __shared__ unsigned long long red[72];
     if (*status) return;
@@ -247,7 +252,8 @@ __global__ void k_scan_apply(const int *size, int K, const int *tile_off, int *s
         if (i >= K) break;
         const int s = size[i];
         start[i] = (int)run;
-        cursor[i] = (int)run;
+        if (cursor) cursor[i] = (int)run;
+        if (recip) recip[i] = size_recip(s);
         if (s > big_thr) big_list[atomicAdd(&counters[C_BIG_COUNT], 1)] = (int)i;
         run += (unsigned)s;
     }
@@ -340,8 +346,6 @@ __global__ void __launch_bounds__(1024) k_score_cm(ScoreKArgs a)
     if (a.phase == 0) {
         const SmemTable tw{slot + wid * p.cap_w, used + wid * p.max_used_w, &ctl[2 + 2 * wid],
                            &ctl[3 + 2 * wid], p.cap_w, p.max_used_w};
-        unsigned *offw = offs + wid * 33;
-        long long *rsw = rs + wid * 32;
         for (;;) {
             int base = 0;
             if (lane == 0) base = atomicAdd(&a.counters[C_SMALL_NEXT], 32);
@@ -354,7 +358,7 @@ __global__ void __launch_bounds__(1024) k_score_cm(ScoreKArgs a)
             while (mask) {
                 const int j = __ffs(mask) - 1;
                 mask &= mask - 1;
-                if (!score_community(a.x, base + j, tw, offw, rsw, &sacc[wid], lane, 32, red)) {
+                if (!score_community(a.x, base + j, tw, offs, rs, &sacc[wid], lane, 32, red)) {
                     if (lane == 0) a.ovf_out[atomicAdd(&a.counters[C_OVF_COUNT], 1)] = base + j;
                 }
             }
@@ -566,10 +570,205 @@ static int grid_for(long long n, int threads, int num_sms, int per_sm)
     return (int)g;
 }
 
+// ------------------------------------------------------------------ two-phase scoring
+
+// Counting sort of the nodes by label (as k_scatter) that also records the
+// degree of the node placed at each member position (read in node order, so
+// the row-offset reads are coalesced).
+__global__ void k_scatter_deg(const int *__restrict__ labels, const long long *__restrict__ row_ptr, long long n,
+                              int *cursor, int *members, int *degm, const int *status)
+{
+    if (*status) return;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int l = __ldg(&labels[i]);
+        const int pos = atomicAdd(&cursor[l], 1);
+        members[pos] = (int)i;
+        degm[pos] = (int)(__ldg(&row_ptr[i + 1]) - __ldg(&row_ptr[i]));
+    }
+}
+
+// Phase A: for each member position p (community order), the labels of the
+// neighbours of members[p] go to nbr[aoff[p] .. aoff[p+1]).  A warp takes 32
+// consecutive member positions, spreads their arcs over its lanes (a search
+// over the 32 arc offsets) and writes the labels coalesced.  No shared-memory
+// table is needed, so the kernel runs at full occupancy.
+constexpr int EXPAND_THREADS = 256;
+__global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__restrict__ row_ptr,
+                                                           const int *__restrict__ col,
+                                                           const int *__restrict__ labels,
+                                                           const int *__restrict__ members,
+                                                           const unsigned *__restrict__ aoff, long long n,
+                                                           int *__restrict__ nbr, const int *status)
+{
+    __shared__ unsigned offs_s[EXPAND_THREADS / 32][33];
+    __shared__ long long rs_s[EXPAND_THREADS / 32][32];
+    if (*status) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned *offw = offs_s[w];
+    long long *rsw = rs_s[w];
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long p0 = ((long long)blockIdx.x * (blockDim.x >> 5) + w) * 32; p0 < n; p0 += nwarps * 32) {
+        const int nm = (int)min(32LL, n - p0);
+        const unsigned base = __ldg(&aoff[p0]);
+        const unsigned total = __ldg(&aoff[p0 + nm]) - base;
+        if (lane < nm) {
+            const int u = __ldg(&members[p0 + lane]);
+            offw[lane] = __ldg(&aoff[p0 + lane]) - base;
+            rsw[lane] = __ldg(&row_ptr[u]);
+        }
+        __syncwarp();
+        for (unsigned e0 = lane; e0 < total; e0 += 256u) {
+            int v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const unsigned e = e0 + 32u * k;
+                v[k] = -1;
+                if (e < total) {
+                    const int o = upper_bound_smem(offw, nm, e) - 1;
+                    v[k] = __ldg(&col[rsw[o] + (e - offw[o])]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const unsigned e = e0 + 32u * k;
+                if (e < total) nbr[(size_t)base + e] = __ldg(&labels[v[k]]);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Communities whose arc segment exceeds a warp table go to blocks in phase B.
+__global__ void k_classify(const int *start, const unsigned *aoff, int K, int warp_thr, int *big_list,
+                           int *counters, const int *status)
+{
+    if (*status) return;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < K; c += gridDim.x * blockDim.x) {
+        const int b = start[c], e = start[c + 1];
+        if (e > b && aoff[e] - aoff[b] > (unsigned)warp_thr)
+            big_list[atomicAdd(&counters[C_BIG_COUNT], 1)] = c;
+    }
+}
+
+struct CountKArgs {
+    CountCtx x;
+    const int *big_list;
+    int *counters;
+    const int *status;
+    int warp_thr;
+    SmemPlan plan;
+};
+
+// Phase B: large segments by whole blocks (a queue), the rest by single warps.
+__global__ void __launch_bounds__(1024) k_count(CountKArgs a)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ int s_item;
+    if (*a.status) return;
+    const SmemPlan &p = a.plan;
+    unsigned long long *red = (unsigned long long *)(sm + p.red_off);
+    int *ctl = (int *)(sm + p.ctl_off);
+    unsigned long long *slot = (unsigned long long *)(sm + p.slot_off);
+    int *used = (int *)(sm + p.used_off);
+    const int T = blockDim.x, W = T >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < p.cap; i += T) slot[i] = 0ull;
+    for (int i = threadIdx.x; i < 2 * (W + 1); i += T) ctl[i] = 0;
+    block_sync();
+    const SmemTable tb{slot, used, &ctl[0], &ctl[1], p.cap, p.max_used};
+    const int count = a.counters[C_BIG_COUNT];
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int i = atomicAdd(&a.counters[C_BIG_NEXT], 1);
+            s_item = i < count ? a.big_list[i] : -1;
+        }
+        block_sync();
+        const int c = s_item;
+        block_sync();
+        if (c < 0) break;
+        count_community(a.x, c, tb, threadIdx.x, T, red);
+    }
+    const SmemTable tw{slot + wid * p.cap_w, used + wid * p.max_used_w, &ctl[2 + 2 * wid], &ctl[3 + 2 * wid],
+                       p.cap_w, p.max_used_w};
+    for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&a.counters[C_SMALL_NEXT], 32);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= a.x.K) break;
+        const int c = base + lane;
+        bool take = false;
+        if (c < a.x.K) {
+            const int b = __ldg(&a.x.start[c]), e = __ldg(&a.x.start[c + 1]);
+            take = e > b && __ldg(&a.x.aoff[e]) - __ldg(&a.x.aoff[b]) <= (unsigned)a.warp_thr;
+        }
+        unsigned mask = __ballot_sync(0xffffffffu, take);
+        while (mask) {
+            const int j = __ffs(mask) - 1;
+            mask &= mask - 1;
+            count_community(a.x, base + j, tw, lane, 32, red);
+        }
+    }
+}
+
+// Block reduction of per-thread sums into the partition's global limbs.
+__device__ __forceinline__ void flush_score_threads(const ScoreAcc &acc, unsigned long long *g,
+                                                    unsigned long long *red)
+{
+    const int T = blockDim.x;
+    const i128 v[7] = {acc.qds_self, acc.qds_pair, acc.dens, acc.contr, acc.expn, acc.cond, (i128)acc.vol2};
+    const int at[7] = {GS_QDS_SELF, GS_QDS_PAIR, GS_DENS, GS_CONTR, GS_EXPN, GS_COND, GS_VOL2};
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        const i128 t = group_sum_i128(v[k], T, red);
+        if (threadIdx.x == 0) limbs_add(g + at[k], t);
+    }
+    const unsigned long long u[5] = {acc.ein, acc.eout, acc.nonempty, acc.slots, acc.cnt2};
+    const int au[5] = {GS_EIN, GS_EOUT, GS_NONEMPTY, GS_SLOTS, GS_CNT2};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const unsigned long long t = group_sum_u64(u[k], T, red);
+        if (threadIdx.x == 0 && t) atomicAdd(g + au[k], t);
+    }
+}
+
+// FP64 terms of every community from the phase-B records, all in parallel.
+__global__ void k_score_terms(const int *start, const unsigned long long *rec, int K, long long E, PerCommDev pc,
+                              unsigned long long *g, const int *status)
+{
+    __shared__ unsigned long long red[72];
+    if (*status) return;
+    ScoreAcc acc;
+    score_acc_zero(acc);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < K; c += gridDim.x * blockDim.x) {
+        const long long size = start[c + 1] - start[c];
+        if (size == 0) continue;
+        double pen, qs, dens, contr, expn, cond;
+        const unsigned long long *rc = rec + (size_t)c * REC_WORDS;
+        terms_from_record(rc, size, E, acc, &pen, &qs, &dens, &contr, &expn, &cond);
+        if (pc.size) pc.size[c] = size;
+        if (pc.ein) pc.ein[c] = (long long)(rc[REC_SAME] / 2);
+        if (pc.eout) pc.eout[c] = (long long)(rc[REC_VOL] - rc[REC_SAME]);
+        if (pc.dens) pc.dens[c] = dens;
+        if (pc.contr) pc.contr[c] = contr;
+        if (pc.expn) pc.expn[c] = expn;
+        if (pc.cond) pc.cond[c] = cond;
+        if (pc.qds) pc.qds[c] = __dsub_rn(qs, pen);
+    }
+    flush_score_threads(acc, g, red);
+}
+
 void prepare_kernels()
 {
     cudaFuncSetAttribute(k_score_cm, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     cudaFuncSetAttribute(k_compare_cm, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+    cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+}
+
+int count_blocks_per_sm(const Shape &sh)
+{
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_count, sh.threads, sh.smem_bytes);
+    return nb;
 }
 
 int score_blocks_per_sm(const Shape &sh)
@@ -584,12 +783,12 @@ int score_blocks_per_sm(const Shape &sh)
         if (tr) tr(name, s); \
     } while (0)
 
-static int launch_scan(const int *size, int K, int *start, int *cursor, int big_thr, int *big_list,
-                       int *counters, int *tmp, const int *status, cudaStream_t s, TraceFn tr)
+static int launch_scan(const int *size, int K, int *start, int *cursor, unsigned long long *recip, int big_thr,
+                       int *big_list, int *counters, int *tmp, const int *status, cudaStream_t s, TraceFn tr)
 {
     if (K <= SCAN_SINGLE_MAX) {
         TRACE("k_scan_single");
-        k_scan_single<<<1, 1024, 0, s>>>(size, K, start, cursor, big_thr, big_list, counters, status);
+        k_scan_single<<<1, 1024, 0, s>>>(size, K, start, cursor, recip, big_thr, big_list, counters, status);
         return 1;
     }
     const int tiles = scan_tiles(K);
@@ -597,9 +796,9 @@ static int launch_scan(const int *size, int K, int *start, int *cursor, int big_
     k_scan_tiles<<<tiles, 1024, 0, s>>>(size, K, tmp, status);
     // exclusive prefix of the tile sums, in place into tmp[0..tiles] (tmp[tiles] = total)
     TRACE("k_scan_single");
-    k_scan_single<<<1, 1024, 0, s>>>(tmp, tiles, tmp, nullptr, INT_MAX, nullptr, counters, status);
+    k_scan_single<<<1, 1024, 0, s>>>(tmp, tiles, tmp, nullptr, nullptr, INT_MAX, nullptr, counters, status);
     TRACE("k_scan_apply");
-    k_scan_apply<<<tiles, 1024, 0, s>>>(size, K, tmp, start, cursor, big_thr, big_list, counters, status);
+    k_scan_apply<<<tiles, 1024, 0, s>>>(size, K, tmp, start, cursor, recip, big_thr, big_list, counters, status);
     return 3;
 }
 
@@ -613,8 +812,8 @@ int launch_score(const GraphDev &g, const int *labels, int K, const ScoreWs &ws,
     k_hist<<<grid_for(n, 512, num_sms, 4), 512, hist_smem, s>>>(labels, K, ws.size, nullptr, 0, nullptr, n,
                                                                 ws.status, hist_smem ? 1 : 0);
     ++launches;
-    launches += launch_scan(ws.size, K, ws.start, ws.cursor, sh.big_community, ws.big_list, ws.counters,
-                            ws.scan_tmp, ws.status, s, tr);
+    launches += launch_scan(ws.size, K, ws.start, ws.cursor, ws.recip, sh.big_community, ws.big_list,
+                            ws.counters, ws.scan_tmp, ws.status, s, tr);
     TRACE("k_scatter");
     k_scatter<<<grid_for(n, 512, num_sms, 8), 512, 0, s>>>(labels, n, ws.cursor, ws.members, ws.status);
     ++launches;
@@ -625,6 +824,7 @@ int launch_score(const GraphDev &g, const int *labels, int K, const ScoreWs &ws,
     a.x.labels = labels;
     a.x.members = ws.members;
     a.x.start = ws.start;
+    a.x.recip = ws.recip;
     a.x.E = g.n_arcs / 2;
     a.x.n = g.n;
     a.x.n_arcs = g.n_arcs;
@@ -660,6 +860,131 @@ int launch_score(const GraphDev &g, const int *labels, int K, const ScoreWs &ws,
     return cudaGetLastError() == cudaSuccess ? launches : -1;
 }
 
+size_t score2_ws_bytes(long long n, long long n_arcs, int K)
+{
+    const int tiles = scan_tiles((int)std::max<long long>(n, K));
+    size_t b = 0;
+    b += 256 + align_up(32 * 8, 256) + align_up(sizeof(qm_quality), 256);
+    b += align_up((size_t)K * 4, 256);              // size (zeroed)
+    b += align_up((size_t)(K + 1) * 4, 256);        // start
+    b += align_up((size_t)K * 8, 256);              // recip
+    b += align_up((size_t)K * 4, 256) * 2;          // cursor, big_list
+    b += align_up((size_t)n * 4, 256);              // members
+    b += align_up((size_t)(n + 1) * 4, 256);        // member degrees -> arc offsets
+    b += align_up((size_t)n_arcs * 4, 256);         // neighbour labels in community order
+    b += align_up((size_t)K * 8 * REC_WORDS, 256);  // per-community records
+    b += align_up((size_t)(tiles + 1) * 4, 256);    // scan tiles
+    return b;
+}
+
+ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K)
+{
+    ScoreWs w;
+    const int tiles = scan_tiles((int)std::max<long long>(n, K));
+    char *p = (char *)base;
+    w.status = (int *)p;
+    w.counters = (int *)(p + 16);
+    p += 256;
+    w.gacc = (unsigned long long *)p;
+    p += align_up(32 * 8, 256);
+    w.result = (qm_quality *)p;
+    p += align_up(sizeof(qm_quality), 256);
+    w.size = (int *)p;
+    p += align_up((size_t)K * 4, 256);
+    w.zero_bytes = (size_t)(p - (char *)base);
+    w.start = (int *)p;
+    p += align_up((size_t)(K + 1) * 4, 256);
+    w.recip = (unsigned long long *)p;
+    p += align_up((size_t)K * 8, 256);
+    w.cursor = (int *)p;
+    p += align_up((size_t)K * 4, 256);
+    w.big_list = (int *)p;
+    p += align_up((size_t)K * 4, 256);
+    w.ovf_list = nullptr;
+    w.members = (int *)p;
+    p += align_up((size_t)n * 4, 256);
+    w.aoff = (unsigned *)p;
+    p += align_up((size_t)(n + 1) * 4, 256);
+    w.nbr = (int *)p;
+    p += align_up((size_t)n_arcs * 4, 256);
+    w.rec = (unsigned long long *)p;
+    p += align_up((size_t)K * 8 * REC_WORDS, 256);
+    w.scan_tmp = (int *)p;
+    (void)tiles;
+    return w;
+}
+
+// The two-phase plain scoring pipeline (see k_expand / count_community):
+//   k_hist -> scan (sizes) -> k_scatter_deg -> scan (member degrees = arc offsets)
+//   -> k_expand -> k_classify -> k_count -> k_score_terms -> k_score_fin
+int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws, const Shape &sh,
+                  const PerCommDev *pc, int num_sms, cudaStream_t s, TraceFn tr)
+{
+    int launches = 0;
+    const long long n = g.n;
+    const int hist_smem = (K <= 12288) ? K * 4 : 0;
+    TRACE("k_hist");
+    k_hist<<<grid_for(n, 512, num_sms, 4), 512, hist_smem, s>>>(labels, K, ws.size, nullptr, 0, nullptr, n,
+                                                                ws.status, hist_smem ? 1 : 0);
+    ++launches;
+    launches += launch_scan(ws.size, K, ws.start, ws.cursor, ws.recip, INT_MAX, nullptr, ws.counters,
+                            ws.scan_tmp, ws.status, s, tr);
+    TRACE("k_scatter_deg");
+    k_scatter_deg<<<grid_for(n, 512, num_sms, 8), 512, 0, s>>>(labels, g.row_ptr, n, ws.cursor, ws.members,
+                                                               (int *)ws.aoff, ws.status);
+    ++launches;
+    // exclusive prefix of the member degrees, in place: aoff[p] = arcs before member position p
+    launches += launch_scan((const int *)ws.aoff, (int)n, (int *)ws.aoff, nullptr, nullptr, INT_MAX, nullptr,
+                            ws.counters, ws.scan_tmp, ws.status, s, tr);
+    TRACE("k_expand");
+    k_expand<<<num_sms * 8, EXPAND_THREADS, 0, s>>>(g.row_ptr, g.col, labels, ws.members, ws.aoff, n, ws.nbr,
+                                                    ws.status);
+    ++launches;
+    const SmemPlan plan = plan_smem(sh.threads, sh.smem_bytes);
+    TRACE("k_classify");
+    k_classify<<<grid_for(K, 256, num_sms, 4), 256, 0, s>>>(ws.start, ws.aoff, K, plan.max_used_w, ws.big_list,
+                                                            ws.counters, ws.status);
+    ++launches;
+    CountKArgs a;
+    a.x.nbr = ws.nbr;
+    a.x.aoff = ws.aoff;
+    a.x.start = ws.start;
+    a.x.recip = ws.recip;
+    a.x.rec = ws.rec;
+    a.x.K = K;
+    a.x.err = ws.status;
+    a.big_list = ws.big_list;
+    a.counters = ws.counters;
+    a.status = ws.status;
+    a.warp_thr = plan.max_used_w;
+    a.plan = plan;
+    static int occ_cache[4][8] = {};
+    int nb = 0;
+    {
+        // occupancy of k_count for this shape (host-side query, cached per shape)
+        const int ti = sh.threads / 256 - 1, si = sh.smem_bytes / (32 * 1024);
+        if (ti >= 0 && ti < 4 && si >= 0 && si < 8 && occ_cache[ti][si] > 0) nb = occ_cache[ti][si];
+        else {
+            nb = count_blocks_per_sm(sh);
+            if (ti >= 0 && ti < 4 && si >= 0 && si < 8) occ_cache[ti][si] = nb;
+        }
+        if (nb < 1) nb = 1;
+    }
+    TRACE("k_count");
+    k_count<<<num_sms * nb, sh.threads, sh.smem_bytes, s>>>(a);
+    ++launches;
+    PerCommDev pcd{};
+    if (pc) pcd = *pc;
+    TRACE("k_score_terms");
+    k_score_terms<<<grid_for(K, 256, num_sms, 2), 256, 0, s>>>(ws.start, ws.rec, K, g.n_arcs / 2, pcd, ws.gacc,
+                                                               ws.status);
+    TRACE("k_score_fin");
+    k_score_fin<<<1, 32, 0, s>>>(ws.gacc, ws.status, n, g.n_arcs / 2, ws.result);
+    TRACE(nullptr);
+    launches += 2;
+    return cudaGetLastError() == cudaSuccess ? launches : -1;
+}
+
 int launch_compare(const int *truth, const int *found, long long n, int ka, int kb,
                    const CompareWs &ws, const Shape &sh, int num_sms, cudaStream_t s, TraceFn tr)
 {
@@ -670,8 +995,8 @@ int launch_compare(const int *truth, const int *found, long long n, int ka, int 
                                                                 ws.status, hist_smem ? 1 : 0);
     ++launches;
     const SmemPlan plan = plan_smem(sh.threads, sh.smem_bytes);
-    launches += launch_scan(ws.size_b, kb, ws.start, ws.cursor, plan.max_used_w, ws.big_list, ws.counters,
-                            ws.scan_tmp, ws.status, s, tr);
+    launches += launch_scan(ws.size_b, kb, ws.start, ws.cursor, nullptr, plan.max_used_w, ws.big_list,
+                            ws.counters, ws.scan_tmp, ws.status, s, tr);
     TRACE("k_scatter");
     k_scatter<<<grid_for(n, 512, num_sms, 8), 512, 0, s>>>(found, n, ws.cursor, ws.members, ws.status);
     ++launches;

@@ -61,7 +61,8 @@ class QmTraceEvent(ctypes.Structure):
 
 
 class QmTuning(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_int32) for n in ("threads", "smem_bytes", "big_community", "blocks_per_sm")]
+    _fields_ = [(n, ctypes.c_int32) for n in ("threads", "smem_bytes", "big_community", "blocks_per_sm",
+                                                    "algorithm")]
 
 
 _lib = None
@@ -335,8 +336,9 @@ def get_tuning(graph: Graph, K: int) -> dict:
     return _struct_dict(t)
 
 
-def set_tuning(graph: Graph, K: int, threads: int, smem_bytes: int, big_community: int):
-    t = QmTuning(threads, smem_bytes, big_community, 0)
+def set_tuning(graph: Graph, K: int, threads: int, smem_bytes: int, big_community: int, algorithm: int = 1):
+    """algorithm 0: one-kernel community pass; 1: expand + count (two phases)."""
+    t = QmTuning(threads, smem_bytes, big_community, 0, algorithm)
     _check(lib().qm_set_tuning(graph.handle, int(K), ctypes.byref(t)), "qm_set_tuning")
 
 

@@ -1,0 +1,82 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py
+times (default launch shape, graph and labels resident on the device).
+
+* 10M nodes (|E| ~ 9.6e7): every output against the whole-graph oracle.
+* 100M nodes (|E| ~ 9.6e8): the whole oracle is too slow here, so sampled
+  communities are checked one by one against the oracle's per-community routine
+  (sizes, |E_c^in|, |E_c^out| bit-exact, Qds terms within tolerance), and the
+  totals against identities that hold at any size."""
+import numpy as np
+import pytest
+import torch
+
+from helpers import check_quality, close
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qm():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1507_05492_gb300 import qm as q
+    return q
+
+
+def test_ten_million_nodes_against_whole_oracle(qm, oracle_mod):
+    from paper_1507_05492_gb300 import gen
+    g = gen.lfr_graph(gen.config_params("lfr10m"), device="cuda")
+    graph = qm.Graph(g.row_ptr, g.col)
+    q = qm.score(graph, g.labels, g.K, per_community=True)
+    rp, col, lab = g.row_ptr.cpu().numpy(), g.col.cpu().numpy(), g.labels.cpu().numpy()
+    o = oracle_mod.score(rp, col, lab, g.K, per_community=True)
+    check_quality(q, o, "lfr10m")
+    for k in ("size", "intra_edges", "inter_edges"):
+        assert np.array_equal(q["per_community"][k].cpu().numpy(), o["per_community"][k]), k
+    a, b = q["per_community"]["qds_term"].cpu().numpy(), o["per_community"]["qds_term"]
+    assert np.all(np.abs(a - b) <= 1e-12 * np.maximum(np.abs(b), 1e-6))
+    # a perturbed partition and the comparison with the planted one, also at full size
+    p = gen.perturb(g.labels, g.K, 0.2, seed=9)
+    q2 = qm.score(graph, p, g.K)
+    check_quality(q2, oracle_mod.score(rp, col, p.cpu().numpy(), g.K), "lfr10m perturbed")
+    from helpers import check_compare
+    c = qm.compare(g.labels, p, g.K, g.K)
+    check_compare(c, oracle_mod.compare(lab, p.cpu().numpy(), g.K, g.K), "lfr10m compare")
+
+
+def test_hundred_million_nodes_sampled(qm, oracle_mod):
+    from paper_1507_05492_gb300 import gen
+    g = gen.lfr_graph(gen.config_params("lfr100m"), device="cuda")
+    graph = qm.Graph(g.row_ptr, g.col)
+    q = qm.score(graph, g.labels, g.K, per_community=True)
+    pc = {k: v.cpu().numpy() for k, v in q["per_community"].items()}
+    n, E = g.n, g.n_edges
+    # identities at any size
+    assert q["n_nodes"] == n and q["n_edges"] == E
+    assert pc["size"].sum() == n
+    assert pc["intra_edges"].sum() == q["intra_edges_total"]
+    assert pc["inter_edges"].sum() == 2 * q["cut_edges_total"]
+    assert q["intra_edges_total"] + q["cut_edges_total"] == E
+    assert q["n_communities_nonempty"] == int((pc["size"] > 0).sum())
+    assert q["pair_count_sq_sum"] >= q["n_community_pairs"]
+    assert -0.5 <= q["modularity"] <= 1.0
+    # Q from the per-community integers (Eq. 8), summed exactly in Python
+    vol = 2 * pc["intra_edges"].astype(object) + pc["inter_edges"].astype(object)
+    num = 4 * E * int(pc["intra_edges"].sum()) - int(sum(v * v for v in vol))
+    assert close(q["modularity"], num / (4 * E * E), 1.0)
+    # sampled communities against the oracle, one by one
+    rng = np.random.default_rng(5)
+    nonempty = np.flatnonzero(pc["size"] > 0)
+    big = nonempty[np.argsort(pc["size"][nonempty])[-3:]]
+    ids = np.concatenate([rng.choice(nonempty, 13, replace=False), big]).astype(np.int32)
+    rp, col, lab = g.row_ptr.cpu().numpy(), g.col.cpu().numpy(), g.labels.cpu().numpy()
+    s = oracle_mod.score_communities(rp, col, lab, g.K, ids)
+    for j, c in enumerate(ids):
+        assert s["size"][j] == pc["size"][c]
+        assert s["intra_edges"][j] == pc["intra_edges"][c]
+        assert s["inter_edges"][j] == pc["inter_edges"][c]
+        assert close(pc["qds_term"][c], s["qds_term"][j], abs(s["qds_term"][j]) + s["split"][j]), c
+    # the mean measures are the means of the per-community arrays
+    ne = q["n_communities_nonempty"]
+    assert close(q["mean_conductance"], float(pc["conductance"].sum()) / ne, rel=1e-11)
+    assert close(q["mean_intra_edges"], float(pc["intra_edges"].sum()) / ne)

@@ -159,14 +159,16 @@ def test_every_launch_shape_gives_identical_bits(qm, gen, oracle_mod):
     lab = g.labels.cuda()
     o = oracle_mod.score(g.row_ptr.numpy(), g.col.numpy(), g.labels.numpy(), g.K)
     ref = None
-    for threads, smem, big in ((512, 96 * 1024, 48), (256, 48 * 1024, 16), (1024, 200 * 1024, 400),
-                               (128, 16 * 1024, 1), (512, 20 * 1024, 100_000)):
-        qm.set_tuning(graph, g.K, threads, smem, big)
-        q = qm.score(graph, lab, g.K)
-        check_quality(q, o, f"shape {threads}/{smem}/{big}")
-        if ref is None:
-            ref = q
-        assert q == ref, (threads, smem, big)
+    for algo in (1, 0):
+        for threads, smem, big in ((512, 96 * 1024, 48), (256, 48 * 1024, 16), (1024, 200 * 1024, 400),
+                                   (128, 16 * 1024, 1), (512, 20 * 1024, 100_000)):
+            qm.set_tuning(graph, g.K, threads, smem, big, algo)
+            assert qm.get_tuning(graph, g.K)["algorithm"] == algo
+            q = qm.score(graph, lab, g.K)
+            check_quality(q, o, f"algorithm {algo} shape {threads}/{smem}/{big}")
+            if ref is None:
+                ref = q
+            assert q == ref, (algo, threads, smem, big)
 
 
 def test_deterministic_and_host_inputs(qm, gen):

@@ -351,3 +351,26 @@ def test_invalid_inputs_rejected(oracle_mod):
     assert not oracle_mod.validate_graph(np.array([0, 1, 1], np.int64), np.array([1], np.int32))
     assert not oracle_mod.validate_graph(np.array([0, 1], np.int64), np.array([0], np.int32))
     assert oracle_mod.validate_graph(rp, col)
+
+
+def test_sampled_community_form_matches_whole_graph_oracle(oracle_mod):
+    """The per-community routine used on very large inputs agrees with the
+    whole-graph oracle's per-community arrays."""
+    rng = np.random.default_rng(19)
+    for _ in range(5):
+        n = int(rng.integers(50, 400))
+        rp, col, _ = random_graph(rng, n, 0.08)
+        K = int(rng.integers(2, 30))
+        lab = rng.integers(0, K, n).astype(np.int32)
+        full = oracle_mod.score(rp, col, lab, K, per_community=True)["per_community"]
+        ids = rng.integers(0, K, 12).astype(np.int32)
+        s = oracle_mod.score_communities(rp, col, lab, K, ids)
+        for j, c in enumerate(ids):
+            assert s["size"][j] == full["size"][c]
+            assert s["intra_edges"][j] == full["intra_edges"][c]
+            assert s["inter_edges"][j] == full["inter_edges"][c]
+            assert close(s["qds_term"][j], full["qds_term"][c], 1.0, 1e-13)
+    rp, col, _ = two_cliques()
+    s = oracle_mod.score_communities(rp, col, np.array([0] * 5 + [1] * 5, np.int32), 2, [0, 1])
+    assert list(s["distinct_neighbours"]) == [1, 1]
+    assert close(s["split"][0], 1 / 42 / 25)
