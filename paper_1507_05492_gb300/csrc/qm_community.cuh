@@ -483,10 +483,13 @@ __device__ __forceinline__ void compare_community(const CompareCtx &x, int b, co
 
 // ---------------------------------------------------------------- two-phase scoring
 //
-// Phase A (k_expand) writes, for every member of every community in member
-// order, the labels of its neighbours: community c's arcs occupy the contiguous
-// segment nbr[aoff[start[c]] .. aoff[start[c+1]]).  Phase B (count_community)
-// reads that segment with coalesced loads and counts it.  Phase B leaves one
+// Phase A (k_expand) visits every member of every community in member order
+// and looks up the labels of its neighbours.  Arcs to the member's own
+// community are only counted; the labels of the other arcs are packed densely
+// at the front of the community's arc segment, nbr[aoff[start[c]] ..
+// aoff[start[c]] + inter[c]), in no particular order.  Phase B
+// (count_community) reads that packed run with coalesced loads and counts
+// |E_cj| for every j != c in a shared-memory table.  Phase B leaves one
 // integer record per community; the FP64 terms are formed afterwards for all
 // communities in parallel (k_score_terms).
 
@@ -494,26 +497,86 @@ __device__ __forceinline__ void compare_community(const CompareCtx &x, int b, co
 enum { REC_SAME = 0, REC_VOL = 1, REC_SLOTS = 2, REC_CNT2 = 3, REC_INNER_LO = 4, REC_INNER_HI = 5, REC_WORDS = 6 };
 
 struct CountCtx {
-    const int *nbr;                   // neighbour labels in community order
+    const int *nbr;                   // packed inter-community neighbour labels
     const unsigned *aoff;             // [n + 1] arc offset of each member position
     const int *start;                 // [K + 1] member offsets
+    const int *inter;                 // [K] packed entries of each community (its cut arcs)
     const unsigned long long *recip;  // size_recip(|c|)
     unsigned long long *rec;          // [K][REC_WORDS]
     int K;
     int *err;
 };
 
-// Counts community c's segment with a group.  A warp group is only given
-// communities whose segment fits its table (distinct keys <= segment length),
-// so only a block splits its keys into R classes on overflow.
+// L2 eviction-priority hints (PTX createpolicy / ld.global.L2::cache_hint):
+// the label array is gathered at random and should stay resident, while the
+// adjacency and the packed labels stream through once.
+__device__ __forceinline__ unsigned long long l2_policy_evict_last()
+{
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ int ld_hint(const int *ptr, unsigned long long pol)
+{
+    int v;
+    asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(ptr), "l"(pol));
+    return v;
+}
+
+// Inserts one key: claim an empty slot with its first count in one CAS, or add
+// to the slot already holding the key.  Same table format as tab_insert.
+__device__ __forceinline__ void tab_insert_cas(const SmemTable &t, unsigned key)
+{
+    const unsigned long long tag = (unsigned long long)(key + 1u) << 32;
+    unsigned h = tab_hash(key, t.cap);
+    for (int probe = 0; probe < t.cap; ++probe) {
+        if (!QM_CHK(h, t.cap, 8)) return;
+        const unsigned long long prev = atomicCAS(&t.slot[h], 0ull, tag | 1ull);
+        if (prev == 0ull) {
+            const int idx = atomicAdd(t.n_used, 1);
+            if (idx < t.max_used) t.used[idx] = (int)h;
+            else *t.overflow = 1;
+            return;
+        }
+        if ((prev & 0xFFFFFFFF00000000ull) == tag) {
+            atomicAdd(&t.slot[h], 1ull);
+            return;
+        }
+        if ((probe & 15) == 15 && *(volatile int *)t.overflow) return;
+        h = (h + 1u == (unsigned)t.cap) ? 0u : h + 1u;
+    }
+    *t.overflow = 1;
+}
+
+// Eq. (9) split penalty numerator of one key j: |E_cj|^2 * floor((2^64-1)/|c_j|)
+// as 64.64 fixed point (the reciprocal is exact enough for |c_j| <= 2^20,
+// larger communities divide in FP64).
+__device__ __forceinline__ u128 pair_inner(unsigned long long q, unsigned long long rj, const int *start, int key)
+{
+    if (rj >= (1ull << 44)) return (u128)q * (u128)rj;
+    if (rj == 0ull) return (u128)q << 64;
+    const long long sj = __ldg(&start[key + 1]) - __ldg(&start[key]);
+    return (u128)fp_from_double(__ddiv_rn((double)q, (double)sj), 64);
+}
+
+// Counts community c's packed run with a group (a warp, or the whole block).
+// Every entry is a label j != c and the run has inter[c] entries, which bounds
+// the distinct keys; when that exceeds the table the keys are split into R
+// hash classes and the run is read once per class.  A block group passes two
+// barriers per community (after the inserts, and in the final exchange) and
+// must hand in a table whose n_used counter alternates between communities.
 __device__ __forceinline__ void count_community(const CountCtx &x, int c, const SmemTable &tab, int gtid,
                                                 int gsize, unsigned long long *red)
 {
     const unsigned a0 = __ldg(&x.aoff[__ldg(&x.start[c])]);
-    const unsigned a1 = __ldg(&x.aoff[__ldg(&x.start[c + 1])]);
-    unsigned R = 1;
+    const unsigned vol = __ldg(&x.aoff[__ldg(&x.start[c + 1])]) - a0;
+    const unsigned m = (unsigned)__ldcg(&x.inter[c]);
+    const unsigned a1 = a0 + m;
+    const unsigned cap_keys = (unsigned)tab.max_used;
+    unsigned R = m <= cap_keys ? 1u : (unsigned)min((unsigned long long)R_MAX, (5ull * m + 4ull * cap_keys - 1) / (4ull * cap_keys));
     for (;;) {
-        unsigned long long same = 0, slots = 0, cnt2 = 0;
+        unsigned long long slots = 0, cnt2 = 0;
         u128 inner = 0;
         bool ok = true;
         for (unsigned r = 0; r < R && ok; ++r) {
@@ -522,16 +585,12 @@ __device__ __forceinline__ void count_community(const CountCtx &x, int c, const 
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const unsigned e = e0 + k * gsize;
-                    lv[k] = e < a1 ? __ldg(&x.nbr[e]) : -1;
+                    lv[k] = e < a1 ? __ldcs(&x.nbr[e]) : -1;
                 }
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     if (lv[k] < 0 || !QM_CHK(lv[k], x.K, 6)) continue;
-                    if (lv[k] == c) {
-                        if (r == 0) ++same;
-                    } else if (R == 1 || tab_split((unsigned)lv[k], R) == r) {
-                        tab_insert(tab, (unsigned)lv[k]);
-                    }
+                    if (R == 1 || tab_split((unsigned)lv[k], R) == r) tab_insert_cas(tab, (unsigned)lv[k]);
                 }
             }
             group_sync(gsize);
@@ -539,59 +598,84 @@ __device__ __forceinline__ void count_community(const CountCtx &x, int c, const 
                 ok = false;
                 break;
             }
-            tab_drain(tab, gtid, gsize, [&](int key, long long cnt) {
-                if (!QM_CHK(key, x.K, 7)) return;
-                const unsigned long long q = (unsigned long long)cnt * (unsigned long long)cnt;
-                const unsigned long long rj = __ldg(&x.recip[key]);
-                if (rj >= (1ull << 44)) {
-                    inner += (u128)q * (u128)rj;
-                } else if (rj == 0ull) {
-                    inner += (u128)q << 64;
-                } else {
-                    const long long sj = __ldg(&x.start[key + 1]) - __ldg(&x.start[key]);
-                    inner += (u128)fp_from_double(__ddiv_rn((double)q, (double)sj), 64);
+            // drain, four entries at a time so their reciprocal loads overlap
+            const int nu = min(*tab.n_used, tab.max_used);
+            for (int i0 = gtid; i0 < nu; i0 += 4 * gsize) {
+                unsigned long long s[4], rj[4];
+                int hh[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int i = i0 + k * gsize;
+                    hh[k] = i < nu ? tab.used[i] : -1;
+                    s[k] = hh[k] >= 0 && QM_CHK(hh[k], tab.cap, 9) ? tab.slot[hh[k]] : 0ull;
+                    const int key = (int)(s[k] >> 32) - 1;
+                    rj[k] = s[k] && QM_CHK(key, x.K, 7) ? __ldg(&x.recip[key]) : 0ull;
                 }
-                ++slots;
-                cnt2 += q;
-            });
-            group_sync(gsize);
-            if (gtid == 0) *tab.n_used = 0;
-            group_sync(gsize);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (!s[k]) continue;
+                    const int key = (int)(s[k] >> 32) - 1;
+                    const unsigned long long cnt = s[k] & 0xFFFFFFFFull;
+                    const unsigned long long q = cnt * cnt;
+                    inner += pair_inner(q, rj[k], x.start, key);
+                    ++slots;
+                    cnt2 += q;
+                    tab.slot[hh[k]] = 0ull;
+                }
+            }
+            if (r + 1 < R) {  // another class follows: the table must be empty first
+                group_sync(gsize);
+                if (gtid == 0) *tab.n_used = 0;
+                group_sync(gsize);
+            }
         }
         if (!ok) {
             tab_wipe(tab, gtid, gsize);
             group_sync(gsize);
             if (gtid == 0) { *tab.n_used = 0; *tab.overflow = 0; }
             group_sync(gsize);
-            unsigned long long w1[1] = {same};
-            group_words_to_leader<1>(w1, gsize, red);
-            if (gtid == 0) {
-                const unsigned long long eout = (unsigned long long)(a1 - a0) - w1[0];
-                const unsigned long long need = (eout * 4 + 3ull * tab.max_used - 1) / (3ull * tab.max_used);
-                red[255] = max((unsigned long long)R * 2ull, need);
-            }
-            group_sync(gsize);
-            const unsigned long long nr = red[255];
-            group_sync(gsize);
+            const unsigned nr = R * 2u;
             if (nr > R_MAX) {
                 if (gtid == 0) atomicOr(x.err, 2);
                 return;
             }
-            R = (unsigned)nr;
+            R = nr;
             continue;
         }
-        unsigned long long w3[3] = {same, slots, cnt2};
-        group_words_to_leader<3>(w3, gsize, red);
-        const u128 inner_t = group_u128_to_leader(inner, gsize, red, 128);
+        // one exchange of (slots, cnt2, inner) per warp; its barrier also
+        // orders this community's drain before the next community's inserts
+        slots = warp_sum_u64(slots);
+        cnt2 = warp_sum_u64(cnt2);
+        for (int d = 16; d > 0; d >>= 1) inner += shfl_down_u128(inner, d);
+        if (gsize > 32) {
+            const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+            if (lane == 0) {
+                red[4 * wid] = slots;
+                red[4 * wid + 1] = cnt2;
+                red[4 * wid + 2] = (unsigned long long)inner;
+                red[4 * wid + 3] = (unsigned long long)(inner >> 64);
+            }
+            block_sync();
+            if (gtid == 0)
+                for (int w = 1; w < nw; ++w) {
+                    slots += red[4 * w];
+                    cnt2 += red[4 * w + 1];
+                    inner += ((u128)red[4 * w + 3] << 64) | red[4 * w + 2];
+                }
+        }
         if (gtid == 0) {
             unsigned long long *rc = x.rec + (size_t)c * REC_WORDS;
-            rc[REC_SAME] = w3[0];
-            rc[REC_VOL] = (unsigned long long)(a1 - a0);
-            rc[REC_SLOTS] = w3[1];
-            rc[REC_CNT2] = w3[2];
-            rc[REC_INNER_LO] = (unsigned long long)inner_t;
-            rc[REC_INNER_HI] = (unsigned long long)(inner_t >> 64);
+            rc[REC_SAME] = (unsigned long long)(vol - m);
+            rc[REC_VOL] = (unsigned long long)vol;
+            rc[REC_SLOTS] = slots;
+            rc[REC_CNT2] = cnt2;
+            rc[REC_INNER_LO] = (unsigned long long)inner;
+            rc[REC_INNER_HI] = (unsigned long long)(inner >> 64);
+            // a block caller alternates two counters, so this reset cannot
+            // race with the next community's inserts
+            *tab.n_used = 0;
         }
+        if (gsize == 32) __syncwarp();
         return;
     }
 }

@@ -51,6 +51,7 @@ struct ScoreWs {
     int *members;               // [n]
     int *scan_tmp;              // [scan tiles + 1]
     unsigned *aoff;             // two-phase only: [n + 1] arc offsets of member positions
+    int *inter;                 // two-phase only: [K] cut arcs of each community (zeroed)
     int *nbr;                   // two-phase only: [n_arcs] neighbour labels in community order
     unsigned long long *rec;    // two-phase only: [K][6] per-community records
     size_t zero_bytes;          // bytes from `status` that must start at zero

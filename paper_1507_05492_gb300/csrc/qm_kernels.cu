@@ -78,7 +78,7 @@ size_t score_ws_bytes(long long n, int K)
 
 ScoreWs carve_score_ws(void *base, long long n, int K)
 {
-    ScoreWs w;
+    ScoreWs w{};
     char *p = (char *)base;
     w.status = (int *)p;
     w.counters = (int *)(p + 16);
@@ -88,6 +88,8 @@ ScoreWs carve_score_ws(void *base, long long n, int K)
     w.result = (qm_quality *)p;
     p += align_up(sizeof(qm_quality), 256);
     w.size = (int *)p;
+    p += align_up((size_t)K * 4, 256);
+    w.inter = (int *)p;
     p += align_up((size_t)K * 4, 256);
     w.zero_bytes = (size_t)(p - (char *)base);
     w.start = (int *)p;
@@ -588,65 +590,103 @@ __global__ void k_scatter_deg(const int *__restrict__ labels, const long long *_
     }
 }
 
-// Phase A: for each member position p (community order), the labels of the
-// neighbours of members[p] go to nbr[aoff[p] .. aoff[p+1]).  A warp takes 32
-// consecutive member positions, spreads their arcs over its lanes (a search
-// over the 32 arc offsets) and writes the labels coalesced.  No shared-memory
+// Phase A: for each member position p (community order) the labels of the
+// neighbours of members[p] are looked up.  A warp takes 32 consecutive member
+// positions; they hold one or more runs of members of one community each.  For
+// a run of community c the warp spreads the run's arcs over its lanes (a
+// search over the run's arc offsets), gathers the neighbour labels, and packs
+// those != c at the front of c's arc segment: a ballot gives each lane its
+// place and one atomic on inter[c] reserves the room.  inter[c] ends as the
+// number of cut arcs of c, |E_c^out| (Sec. II-B.3), and the packed run never
+// outgrows the segment, whose length is the volume of c.  No shared-memory
 // table is needed, so the kernel runs at full occupancy.
 constexpr int EXPAND_THREADS = 256;
+constexpr int EXPAND_UNROLL = 8;
 __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__restrict__ row_ptr,
                                                            const int *__restrict__ col,
                                                            const int *__restrict__ labels,
                                                            const int *__restrict__ members,
-                                                           const unsigned *__restrict__ aoff, long long n,
-                                                           int *__restrict__ nbr, const int *status)
+                                                           const unsigned *__restrict__ aoff,
+                                                           const int *__restrict__ start, long long n,
+                                                           int *inter, int *__restrict__ nbr, const int *status)
 {
     __shared__ unsigned offs_s[EXPAND_THREADS / 32][33];
     __shared__ long long rs_s[EXPAND_THREADS / 32][32];
+    __shared__ int cw_s[EXPAND_THREADS / 32][32];
     if (*status) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
     unsigned *offw = offs_s[w];
     long long *rsw = rs_s[w];
+    int *cw = cw_s[w];
+    const unsigned long long keep = l2_policy_evict_last();
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
     for (long long p0 = ((long long)blockIdx.x * (blockDim.x >> 5) + w) * 32; p0 < n; p0 += nwarps * 32) {
         const int nm = (int)min(32LL, n - p0);
         const unsigned base = __ldg(&aoff[p0]);
-        const unsigned total = __ldg(&aoff[p0 + nm]) - base;
         if (lane < nm) {
-            const int u = __ldg(&members[p0 + lane]);
+            const int u = __ldcs(&members[p0 + lane]);
             offw[lane] = __ldg(&aoff[p0 + lane]) - base;
             rsw[lane] = __ldg(&row_ptr[u]);
+            cw[lane] = ld_hint(&labels[u], keep);
         }
+        if (lane == 0) offw[nm] = __ldg(&aoff[p0 + nm]) - base;
         __syncwarp();
-        for (unsigned e0 = lane; e0 < total; e0 += 256u) {
-            int v[8];
+        unsigned runs = __ballot_sync(0xffffffffu, lane < nm && (lane == 0 || cw[lane] != cw[lane - 1]));
+        while (runs) {
+            const int m_lo = __ffs(runs) - 1;
+            runs &= runs - 1;
+            const int m_hi = runs ? __ffs(runs) - 1 : nm;
+            const unsigned e_lo = offw[m_lo], e_hi = offw[m_hi];
+            if (e_lo == e_hi) continue;
+            const int c = cw[m_lo];
+            unsigned cbase = 0;
+            if (lane == 0) cbase = __ldg(&aoff[__ldg(&start[c])]);
+            cbase = __shfl_sync(0xffffffffu, cbase, 0);
+            for (unsigned e0 = e_lo; e0 < e_hi; e0 += 32u * EXPAND_UNROLL) {
+                int lab[EXPAND_UNROLL];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const unsigned e = e0 + 32u * k;
-                v[k] = -1;
-                if (e < total) {
-                    const int o = upper_bound_smem(offw, nm, e) - 1;
-                    v[k] = __ldg(&col[rsw[o] + (e - offw[o])]);
+                for (int k = 0; k < EXPAND_UNROLL; ++k) {
+                    const unsigned e = e0 + lane + 32u * k;
+                    lab[k] = -1;
+                    if (e < e_hi) {
+                        const int o = m_lo + upper_bound_smem(offw + m_lo, m_hi - m_lo, e) - 1;
+                        lab[k] = __ldcs(&col[rsw[o] + (e - offw[o])]);
+                    }
                 }
-            }
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const unsigned e = e0 + 32u * k;
-                if (e < total) nbr[(size_t)base + e] = __ldg(&labels[v[k]]);
+                for (int k = 0; k < EXPAND_UNROLL; ++k)
+                    if (lab[k] >= 0) lab[k] = ld_hint(&labels[lab[k]], keep);
+                unsigned msk[EXPAND_UNROLL];
+                int tot = 0;
+#pragma unroll
+                for (int k = 0; k < EXPAND_UNROLL; ++k) {
+                    msk[k] = __ballot_sync(0xffffffffu, lab[k] >= 0 && lab[k] != c);
+                    tot += __popc(msk[k]);
+                }
+                if (tot == 0) continue;
+                int pos = 0;
+                if (lane == 0) pos = atomicAdd(&inter[c], tot);
+                unsigned at = cbase + (unsigned)__shfl_sync(0xffffffffu, pos, 0);
+#pragma unroll
+                for (int k = 0; k < EXPAND_UNROLL; ++k) {
+                    if ((msk[k] >> lane) & 1u) __stcs(&nbr[at + __popc(msk[k] & lt)], lab[k]);
+                    at += __popc(msk[k]);
+                }
             }
         }
         __syncwarp();
     }
 }
 
-// Communities whose arc segment exceeds a warp table go to blocks in phase B.
-__global__ void k_classify(const int *start, const unsigned *aoff, int K, int warp_thr, int *big_list,
-                           int *counters, const int *status)
+// Communities whose cut arcs (an upper bound on their distinct neighbour
+// communities) exceed a warp table go to whole blocks in phase B.
+__global__ void k_classify(const int *start, const int *inter, int K, int warp_thr, int *big_list, int *counters,
+                           const int *status)
 {
     if (*status) return;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < K; c += gridDim.x * blockDim.x) {
-        const int b = start[c], e = start[c + 1];
-        if (e > b && aoff[e] - aoff[b] > (unsigned)warp_thr)
+        if (start[c + 1] > start[c] && inter[c] > warp_thr)
             big_list[atomicAdd(&counters[C_BIG_COUNT], 1)] = c;
     }
 }
@@ -660,11 +700,13 @@ struct CountKArgs {
     SmemPlan plan;
 };
 
-// Phase B: large segments by whole blocks (a queue), the rest by single warps.
+// Phase B: large runs by whole blocks (a queue whose next item is fetched while
+// the current one is counted), the rest by single warps.
 __global__ void __launch_bounds__(1024) k_count(CountKArgs a)
 {
     extern __shared__ __align__(16) unsigned char sm[];
-    __shared__ int s_item;
+    __shared__ int s_item[2];
+    __shared__ int s_nused_alt;
     if (*a.status) return;
     const SmemPlan &p = a.plan;
     unsigned long long *red = (unsigned long long *)(sm + p.red_off);
@@ -674,18 +716,23 @@ __global__ void __launch_bounds__(1024) k_count(CountKArgs a)
     const int T = blockDim.x, W = T >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < p.cap; i += T) slot[i] = 0ull;
     for (int i = threadIdx.x; i < 2 * (W + 1); i += T) ctl[i] = 0;
-    block_sync();
-    const SmemTable tb{slot, used, &ctl[0], &ctl[1], p.cap, p.max_used};
     const int count = a.counters[C_BIG_COUNT];
-    for (;;) {
+    if (threadIdx.x == 0) {
+        s_nused_alt = 0;
+        const int i = atomicAdd(&a.counters[C_BIG_NEXT], 1);
+        s_item[0] = i < count ? a.big_list[i] : -1;
+    }
+    block_sync();
+    for (int it = 0;; ++it) {
+        const int c = s_item[it & 1];
+        if (c < 0) break;
+        // the next item lands in the other slot; count_community's barriers
+        // publish it before the next iteration reads it
         if (threadIdx.x == 0) {
             const int i = atomicAdd(&a.counters[C_BIG_NEXT], 1);
-            s_item = i < count ? a.big_list[i] : -1;
+            s_item[(it + 1) & 1] = i < count ? a.big_list[i] : -1;
         }
-        block_sync();
-        const int c = s_item;
-        block_sync();
-        if (c < 0) break;
+        const SmemTable tb{slot, used, (it & 1) ? &s_nused_alt : &ctl[0], &ctl[1], p.cap, p.max_used};
         count_community(a.x, c, tb, threadIdx.x, T, red);
     }
     const SmemTable tw{slot + wid * p.cap_w, used + wid * p.max_used_w, &ctl[2 + 2 * wid], &ctl[3 + 2 * wid],
@@ -698,8 +745,7 @@ __global__ void __launch_bounds__(1024) k_count(CountKArgs a)
         const int c = base + lane;
         bool take = false;
         if (c < a.x.K) {
-            const int b = __ldg(&a.x.start[c]), e = __ldg(&a.x.start[c + 1]);
-            take = e > b && __ldg(&a.x.aoff[e]) - __ldg(&a.x.aoff[b]) <= (unsigned)a.warp_thr;
+            take = __ldg(&a.x.start[c + 1]) > __ldg(&a.x.start[c]) && __ldcg(&a.x.inter[c]) <= a.warp_thr;
         }
         unsigned mask = __ballot_sync(0xffffffffu, take);
         while (mask) {
@@ -865,7 +911,7 @@ size_t score2_ws_bytes(long long n, long long n_arcs, int K)
     const int tiles = scan_tiles((int)std::max<long long>(n, K));
     size_t b = 0;
     b += 256 + align_up(32 * 8, 256) + align_up(sizeof(qm_quality), 256);
-    b += align_up((size_t)K * 4, 256);              // size (zeroed)
+    b += align_up((size_t)K * 4, 256) * 2;          // size, inter (zeroed)
     b += align_up((size_t)(K + 1) * 4, 256);        // start
     b += align_up((size_t)K * 8, 256);              // recip
     b += align_up((size_t)K * 4, 256) * 2;          // cursor, big_list
@@ -879,7 +925,7 @@ size_t score2_ws_bytes(long long n, long long n_arcs, int K)
 
 ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K)
 {
-    ScoreWs w;
+    ScoreWs w{};
     const int tiles = scan_tiles((int)std::max<long long>(n, K));
     char *p = (char *)base;
     w.status = (int *)p;
@@ -890,6 +936,8 @@ ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K)
     w.result = (qm_quality *)p;
     p += align_up(sizeof(qm_quality), 256);
     w.size = (int *)p;
+    p += align_up((size_t)K * 4, 256);
+    w.inter = (int *)p;
     p += align_up((size_t)K * 4, 256);
     w.zero_bytes = (size_t)(p - (char *)base);
     w.start = (int *)p;
@@ -937,18 +985,19 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
     launches += launch_scan((const int *)ws.aoff, (int)n, (int *)ws.aoff, nullptr, nullptr, INT_MAX, nullptr,
                             ws.counters, ws.scan_tmp, ws.status, s, tr);
     TRACE("k_expand");
-    k_expand<<<num_sms * 8, EXPAND_THREADS, 0, s>>>(g.row_ptr, g.col, labels, ws.members, ws.aoff, n, ws.nbr,
-                                                    ws.status);
+    k_expand<<<num_sms * 8, EXPAND_THREADS, 0, s>>>(g.row_ptr, g.col, labels, ws.members, ws.aoff, ws.start, n,
+                                                    ws.inter, ws.nbr, ws.status);
     ++launches;
     const SmemPlan plan = plan_smem(sh.threads, sh.smem_bytes);
     TRACE("k_classify");
-    k_classify<<<grid_for(K, 256, num_sms, 4), 256, 0, s>>>(ws.start, ws.aoff, K, plan.max_used_w, ws.big_list,
+    k_classify<<<grid_for(K, 256, num_sms, 4), 256, 0, s>>>(ws.start, ws.inter, K, plan.max_used_w, ws.big_list,
                                                             ws.counters, ws.status);
     ++launches;
     CountKArgs a;
     a.x.nbr = ws.nbr;
     a.x.aoff = ws.aoff;
     a.x.start = ws.start;
+    a.x.inter = ws.inter;
     a.x.recip = ws.recip;
     a.x.rec = ws.rec;
     a.x.K = K;
