@@ -568,6 +568,8 @@ static qm_status score_impl(qm_graph *g, const int32_t *labels, int32_t K, qm_me
     const int st = *(int *)pin.ptr();
     if (st & 1) return fail(QM_EINVAL, "a label lies outside [0, K)");
     if (st & 2) return fail(QM_EOVERFLOW, "a community borders too many distinct communities");
+    if (st & 4) return fail(QM_ETIMEOUT, "a staging copy did not complete within its wait limit");
+    if (st) return fail(QM_ECUDA, "device status word set");
     std::memcpy(out, pin.ptr() + 256, sizeof(qm_quality));
     return QM_OK;
 }

@@ -23,7 +23,7 @@ size_t batch_scratch_bytes(long long n_max, int k_max, int kt_max, int slots)
 {
     const size_t per = al((size_t)n_max * 4) + al((size_t)(k_max + 1) * 4) + al((size_t)kt_max * 4) * 2 +
                        al((size_t)kt_max * 8) + al((size_t)k_max * 4) * 3 + al((size_t)k_max * 4) +
-                       al((size_t)k_max * 8);
+                       al((size_t)k_max * 16);
     return per * (size_t)slots;
 }
 
@@ -49,7 +49,7 @@ BatchScratch carve_batch_scratch(void *base, long long n_max, int k_max, int kt_
     p += al((size_t)k_max * 4) * 3 * slots;
     b.size = (int *)p;
     p += al((size_t)k_max * 4) * slots;
-    b.recip = (unsigned long long *)p;
+    b.recip = (Rcp *)p;
     return b;
 }
 
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(1024) k_batched(BatchKArgs a)
     int *big_cmp = big_score + al((size_t)bs.k_max * 4) / 4;
     int *ovf = big_cmp + al((size_t)bs.k_max * 4) / 4;
     int *gsize = (int *)((char *)bs.size + sl * al((size_t)bs.k_max * 4));
-    unsigned long long *recip = (unsigned long long *)((char *)bs.recip + sl * al((size_t)bs.k_max * 8));
+    Rcp *recip = (Rcp *)((char *)bs.recip + sl * al((size_t)bs.k_max * 16));
 
     for (int i = tid; i < p.cap; i += T) slot[i] = 0ull;
     for (int i = tid; i < 2 * (W + 1); i += T) ctl[i] = 0;
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(1024) k_batched(BatchKArgs a)
             if (c < K) {
                 start[c] = (int)(carry + excl);
                 cnt[c] = (int)(carry + excl);
-                recip[c] = size_recip(s);
+                if (s > 0) recip[c] = rcp_of(s);
                 if (do_score && s > a.big_thr) {
                     const int k = atomicAdd(&s_nbig, 1);
                     if (QM_CHK(k, bs.k_max, 12)) big_score[k] = c;

@@ -30,7 +30,7 @@ struct ScoreCtx {
     const int *labels;
     const int *members;   // node ids grouped by label: members[start[c] .. start[c+1])
     const int *start;     // int[K + 1]
-    const unsigned long long *recip;  // per community: size_recip(|c|)
+    const Rcp *recip;     // per community: rcp_of(|c|)
     long long E;          // |E|
     long long n, n_arcs;  // graph size (bounds of the arrays above)
     int K;
@@ -224,11 +224,26 @@ __device__ __forceinline__ u128 group_u128_to_leader(u128 v, int gsize, unsigned
     return v;
 }
 
-// Per-community reciprocal used by the pair sums: floor((2^64 - 1) / s) for
-// s >= 2, 0 for s = 1.
-__device__ __forceinline__ unsigned long long size_recip(long long s)
+
+// A 192-bit group total (valid in the leader only); the warps' totals travel
+// through `red` at word offset `at` (3 words per warp).
+__device__ __forceinline__ U192 group_u192_to_leader(U192 v, int gsize, unsigned long long *red, int at)
 {
-    return s >= 2 ? 0xFFFFFFFFFFFFFFFFull / (unsigned long long)s : 0ull;
+    v = u192_warp_sum(v);
+    if (gsize == 32) return v;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) {
+        red[at + 3 * wid] = v.w0;
+        red[at + 3 * wid + 1] = v.w1;
+        red[at + 3 * wid + 2] = v.w2;
+    }
+    block_sync();
+    if (threadIdx.x == 0)
+        for (int w = 1; w < nw; ++w) {
+            const U192 o{red[at + 3 * w], red[at + 3 * w + 1], red[at + 3 * w + 2]};
+            u192_add(v, o);
+        }
+    return v;
 }
 
 // Score community c with a group (one warp, or a whole block).  Returns false
@@ -240,11 +255,9 @@ __device__ __forceinline__ unsigned long long size_recip(long long s)
 // prefix sum of their degrees in `offs`/`rs`, the warp's slices of shared
 // staging), so the arc walk needs no block-wide barrier; all warps insert into
 // the group's shared table.  The split penalty of Eq. (9) for community i is
-//   sum_j |E_ij|^2 / (2|E| |c_i| |c_j|) = (sum_j |E_ij|^2 R_j) 2^-64 / (2|E| |c_i|)
-// with R_j = floor(2^64 / |c_j|) (x.recip): the inner sum is an exact 128-bit
-// integer, so only one division per community is done in FP64.  For
-// |c_j| > 2^20 (R_j < 2^44) the term is formed in FP64 instead, keeping every
-// term's relative error below 2^-43.
+//   sum_j |E_ij|^2 / (2|E| |c_i| |c_j|) = S_i / (2|E| |c_i|)
+// with S_i = sum_j |E_ij|^2 / |c_j| summed exactly with 128-bit reciprocals
+// (x.recip, see rcp_of): only one division per community is done in FP64.
 __device__ __forceinline__ bool score_community(const ScoreCtx &x, int c, const SmemTable &tab,
                                                 unsigned *offs, long long *rs, ScoreAcc *acc,
                                                 int gtid, int gsize, unsigned long long *red)
@@ -262,7 +275,8 @@ __device__ __forceinline__ bool score_community(const ScoreCtx &x, int c, const 
     unsigned R = 1;
     for (;;) {
         unsigned long long same = 0, vol = 0, slots = 0, cnt2 = 0;
-        u128 inner = 0;
+        U192 inner;
+        u192_zero(inner);
         bool ok = true;
         for (unsigned r = 0; r < R && ok; ++r) {
             for (int cb = mb + wrank * 32; cb < me; cb += gsize) {
@@ -326,15 +340,8 @@ __device__ __forceinline__ bool score_community(const ScoreCtx &x, int c, const 
             tab_drain(tab, gtid, gsize, [&](int key, long long cnt) {
                 if (!QM_CHK(key, x.K, 7)) return;
                 const unsigned long long q = (unsigned long long)cnt * (unsigned long long)cnt;
-                const unsigned long long rj = __ldcg(&x.recip[key]);
-                if (rj >= (1ull << 44)) {
-                    inner += (u128)q * (u128)rj;
-                } else if (rj == 0ull) {
-                    inner += (u128)q << 64;
-                } else {
-                    const long long sj = __ldcg(&x.start[key + 1]) - __ldcg(&x.start[key]);
-                    inner += (u128)fp_from_double(__ddiv_rn((double)q, (double)sj), 64);
-                }
+                const Rcp rj = ld_rcp_cg(&x.recip[key]);
+                u192_mac(inner, q, rj);
                 ++slots;
                 cnt2 += q;
             });
@@ -371,7 +378,7 @@ __device__ __forceinline__ bool score_community(const ScoreCtx &x, int c, const 
         // terms to the group's shared accumulator
         unsigned long long w4[4] = {same, vol, slots, cnt2};
         group_words_to_leader<4>(w4, gsize, red);
-        const u128 inner_t = group_u128_to_leader(inner, gsize, red, 128);
+        const u128 inner_t = u192_shr64(group_u192_to_leader(inner, gsize, red, 128));
         if (gtid == 0) {
             same = w4[0];
             vol = w4[1];
@@ -501,7 +508,7 @@ struct CountCtx {
     const unsigned *aoff;             // [n + 1] arc offset of each member position
     const int *start;                 // [K + 1] member offsets
     const int *inter;                 // [K] packed entries of each community (its cut arcs)
-    const unsigned long long *recip;  // size_recip(|c|)
+    const Rcp *recip;                 // rcp_of(|c|)
     unsigned long long *rec;          // [K][REC_WORDS]
     int K;
     int *err;
@@ -524,110 +531,309 @@ __device__ __forceinline__ int ld_hint(const int *ptr, unsigned long long pol)
     return v;
 }
 
-// Inserts one key: claim an empty slot with its first count in one CAS, or add
-// to the slot already holding the key.  Same table format as tab_insert.
-__device__ __forceinline__ void tab_insert_cas(const SmemTable &t, unsigned key)
-{
-    const unsigned long long tag = (unsigned long long)(key + 1u) << 32;
-    unsigned h = tab_hash(key, t.cap);
-    for (int probe = 0; probe < t.cap; ++probe) {
-        if (!QM_CHK(h, t.cap, 8)) return;
-        const unsigned long long prev = atomicCAS(&t.slot[h], 0ull, tag | 1ull);
-        if (prev == 0ull) {
-            const int idx = atomicAdd(t.n_used, 1);
-            if (idx < t.max_used) t.used[idx] = (int)h;
-            else *t.overflow = 1;
-            return;
+// Epoch-tagged counting tables (phase B).  A group's table is reused for
+// community after community: every slot carries the epoch it was written in
+// and counts as empty unless that is the group's current epoch, so a new
+// community (or hash class) only advances the epoch instead of clearing the
+// table; epoch 0 marks a slot never used.  After 255 epochs the group wipes
+// its table and starts again at 1.  Both layouts take `bytes_per_slot` = 8
+// bytes of shared memory per slot and expose the same calls:
+//   add(key, epoch)  adds one occurrence and returns how many came before it
+//                    in this epoch, or -1 when the table is full;
+//   wipe(gtid, gsize).
+// Runs never exceed 2^24 entries here (longer ones take the general path), so
+// every count fits the fields below.
+constexpr unsigned ET_MAX_RUN = 1u << 24;
+
+// 64-bit slots [63:56] epoch [55:25] key + 1 [24:0] occurrences, for any K.
+struct EpochTable {
+    unsigned long long *slot;
+    int cap;
+    int *overflow;   // shared flag: a key found no free slot
+
+    static constexpr int CNT_BITS = 25;
+    static constexpr unsigned long long CNT_MASK = (1ull << CNT_BITS) - 1ull;
+
+    __device__ __forceinline__ int add(unsigned key, unsigned epoch) const
+    {
+        const unsigned long long tag = ((unsigned long long)epoch << 56) | ((unsigned long long)(key + 1u) << CNT_BITS);
+        unsigned h = tab_hash(key, cap);
+        unsigned long long cur = ((volatile unsigned long long *)slot)[h];
+        const int limit = 2 * cap + 64;
+        for (int step = 0; step < limit; ++step) {
+            if (!QM_CHK(h, cap, 8)) return -1;
+            if ((unsigned)(cur >> 56) != epoch) {
+                const unsigned long long prev = atomicCAS(&slot[h], cur, tag | 1ull);
+                if (prev == cur) return 0;
+                cur = prev;  // the slot changed under us: look at it again
+                continue;
+            }
+            if ((cur & ~CNT_MASK) == tag) return (int)(atomicAdd(&slot[h], 1ull) & CNT_MASK);
+            if ((step & 15) == 15 && *(volatile int *)overflow) return -1;
+            h = (h + 1u == (unsigned)cap) ? 0u : h + 1u;
+            cur = ((volatile unsigned long long *)slot)[h];
         }
-        if ((prev & 0xFFFFFFFF00000000ull) == tag) {
-            atomicAdd(&t.slot[h], 1ull);
-            return;
-        }
-        if ((probe & 15) == 15 && *(volatile int *)t.overflow) return;
-        h = (h + 1u == (unsigned)t.cap) ? 0u : h + 1u;
+        *overflow = 1;
+        return -1;
     }
-    *t.overflow = 1;
+
+    __device__ __forceinline__ void wipe(int gtid, int gsize) const
+    {
+        for (int i = gtid; i < cap; i += gsize) slot[i] = 0ull;
+    }
+};
+
+// Two 32-bit words per slot, for K < 2^24: key[h] = [31:24] epoch [23:0]
+// key + 1, claimed with a 32-bit CAS (half the shared-memory atomic work of
+// a 64-bit one), and rep[h] = [31:24] epoch [23:0] repeats, touched only by
+// second and later occurrences of a key.  The first occurrence leaves rep[h]
+// alone: a word of an older epoch reads as no repeats.
+struct EpochTable32 {
+    unsigned *key;   // [cap]
+    unsigned *rep;   // [cap], right after key
+    int cap;
+    int *overflow;
+
+    __device__ __forceinline__ int add(unsigned k, unsigned epoch) const
+    {
+        const unsigned tag = (epoch << 24) | (k + 1u);
+        unsigned h = tab_hash(k, cap);
+        unsigned cur = ((volatile unsigned *)key)[h];
+        const int limit = 2 * cap + 64;
+        for (int step = 0; step < limit; ++step) {
+            if (!QM_CHK(h, cap, 8)) return -1;
+            if ((cur >> 24) != epoch) {
+                const unsigned prev = atomicCAS(&key[h], cur, tag);
+                if (prev == cur) return 0;
+                cur = prev;  // the slot changed under us: look at it again
+                continue;
+            }
+            if (cur == tag) {
+                unsigned w = ((volatile unsigned *)rep)[h];
+                for (int r = 0; r < limit; ++r) {
+                    const bool same = (w >> 24) == epoch;
+                    const unsigned prev = atomicCAS(&rep[h], w, same ? w + 1u : ((epoch << 24) | 1u));
+                    if (prev == w) return 1 + (same ? (int)(w & 0xFFFFFFu) : 0);
+                    w = prev;
+                }
+                break;
+            }
+            if ((step & 15) == 15 && *(volatile int *)overflow) return -1;
+            h = (h + 1u == (unsigned)cap) ? 0u : h + 1u;
+            cur = ((volatile unsigned *)key)[h];
+        }
+        *overflow = 1;
+        return -1;
+    }
+
+    __device__ __forceinline__ void wipe(int gtid, int gsize) const
+    {
+        for (int i = gtid; i < 2 * cap; i += gsize) key[i] = 0u;  // key and rep are contiguous
+    }
+};
+
+// Table over `cap` slots at `base` (8 bytes each).
+template <class TAB>
+__device__ __forceinline__ TAB make_table(unsigned long long *base, int cap, int *overflow);
+template <>
+__device__ __forceinline__ EpochTable make_table<EpochTable>(unsigned long long *base, int cap, int *overflow)
+{
+    return EpochTable{base, cap, overflow};
+}
+template <>
+__device__ __forceinline__ EpochTable32 make_table<EpochTable32>(unsigned long long *base, int cap, int *overflow)
+{
+    return EpochTable32{(unsigned *)base, (unsigned *)base + cap, cap, overflow};
 }
 
-// Eq. (9) split penalty numerator of one key j: |E_cj|^2 * floor((2^64-1)/|c_j|)
-// as 64.64 fixed point (the reciprocal is exact enough for |c_j| <= 2^20,
-// larger communities divide in FP64).
-__device__ __forceinline__ u128 pair_inner(unsigned long long q, unsigned long long rj, const int *start, int key)
+// Next epoch of a group (all its threads hold the same value); wipes the
+// table when the 8-bit epoch wraps.  The caller has passed a group barrier
+// since the table's last use.
+template <class TAB>
+__device__ __forceinline__ unsigned etab_next_epoch(const TAB &t, unsigned epoch, int gtid, int gsize)
 {
-    if (rj >= (1ull << 44)) return (u128)q * (u128)rj;
-    if (rj == 0ull) return (u128)q << 64;
-    const long long sj = __ldg(&start[key + 1]) - __ldg(&start[key]);
-    return (u128)fp_from_double(__ddiv_rn((double)q, (double)sj), 64);
+    if (epoch < 255u) return epoch + 1u;
+    t.wipe(gtid, gsize);
+    group_sync(gsize);
+    return 1u;
 }
 
-// Counts community c's packed run with a group (a warp, or the whole block).
-// Every entry is a label j != c and the run has inter[c] entries, which bounds
-// the distinct keys; when that exceeds the table the keys are split into R
-// hash classes and the run is read once per class.  A block group passes two
-// barriers per community (after the inserts, and in the final exchange) and
-// must hand in a table whose n_used counter alternates between communities.
-__device__ __forceinline__ void count_community(const CountCtx &x, int c, const SmemTable &tab, int gtid,
-                                                int gsize, unsigned long long *red)
+// Writes community c's record from the group totals (leader only).
+__device__ __forceinline__ void put_record(const CountCtx &x, int c, unsigned vol, unsigned m,
+                                           unsigned long long slots, unsigned long long cnt2, const U192 &inner)
 {
-    const unsigned a0 = __ldg(&x.aoff[__ldg(&x.start[c])]);
-    const unsigned vol = __ldg(&x.aoff[__ldg(&x.start[c + 1])]) - a0;
-    const unsigned m = (unsigned)__ldcg(&x.inter[c]);
-    const unsigned a1 = a0 + m;
-    const unsigned cap_keys = (unsigned)tab.max_used;
-    unsigned R = m <= cap_keys ? 1u : (unsigned)min((unsigned long long)R_MAX, (5ull * m + 4ull * cap_keys - 1) / (4ull * cap_keys));
+    const u128 in = u192_shr64(inner);
+    unsigned long long *rc = x.rec + (size_t)c * REC_WORDS;
+    rc[REC_SAME] = (unsigned long long)(vol - m);
+    rc[REC_VOL] = (unsigned long long)vol;
+    rc[REC_SLOTS] = slots;
+    rc[REC_CNT2] = cnt2;
+    rc[REC_INNER_LO] = (unsigned long long)in;
+    rc[REC_INNER_HI] = (unsigned long long)(in >> 64);
+}
+
+// Group totals of (slots, cnt2, inner) delivered to the leader with one
+// exchange (5 words per warp in `red`); for a block its barrier also orders
+// this community's inserts before the next community's.
+__device__ __forceinline__ void group_totals(unsigned long long &slots, unsigned long long &cnt2, U192 &inner,
+                                             int gsize, unsigned long long *red)
+{
+    slots = warp_sum_u64(slots);
+    cnt2 = warp_sum_u64(cnt2);
+    inner = u192_warp_sum(inner);
+    if (gsize == 32) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) {
+        red[5 * wid] = slots;
+        red[5 * wid + 1] = cnt2;
+        red[5 * wid + 2] = inner.w0;
+        red[5 * wid + 3] = inner.w1;
+        red[5 * wid + 4] = inner.w2;
+    }
+    block_sync();
+    if (threadIdx.x == 0)
+        for (int w = 1; w < nw; ++w) {
+            slots += red[5 * w];
+            cnt2 += red[5 * w + 1];
+            const U192 o{red[5 * w + 2], red[5 * w + 3], red[5 * w + 4]};
+            u192_add(inner, o);
+        }
+}
+
+// Header of one community's packed run, written by k_classify: the run is
+// nbr[a0 .. a0 + m), the community's volume is vol (2|E_c^in| + |E_c^out|).
+struct __align__(16) RunHdr {
+    int c;
+    unsigned a0, m, vol;
+};
+
+// Counts the m entries of community h.c's run, read from `src` (shared-memory
+// staging when SMEM, else the packed array in global memory), with a group (a
+// warp, or the whole block).  Every entry is a label j != c, so m bounds the
+// distinct keys.  Each entry adds its own share of the Eq. (9) pair sum: the
+// k-th occurrence of key j adds (2k - 1) Rcp_j, so no pass over the table is
+// needed afterwards.  When m exceeds what the table holds at 3/4 load the
+// keys are split into R hash classes and the run is read once per class.
+// `epoch` is the group's table epoch (updated).
+template <bool SMEM, class TAB>
+__device__ __forceinline__ void count_run(const CountCtx &x, const RunHdr &h, const int *src, const TAB &tab,
+                                          unsigned &epoch, int gtid, int gsize, unsigned long long *red)
+{
+    const unsigned m = h.m;
+    const unsigned fill = (unsigned)(3 * tab.cap / 4);
+    unsigned R = m <= fill ? 1u : (unsigned)min((unsigned long long)R_MAX, ((unsigned long long)m + fill - 1) / fill);
     for (;;) {
         unsigned long long slots = 0, cnt2 = 0;
-        u128 inner = 0;
+        U192 inner;
+        u192_zero(inner);
         bool ok = true;
         for (unsigned r = 0; r < R && ok; ++r) {
-            for (unsigned e0 = a0 + gtid; e0 < a1; e0 += 4u * gsize) {
+            epoch = etab_next_epoch(tab, epoch, gtid, gsize);
+            for (unsigned e0 = gtid; e0 < m; e0 += 4u * gsize) {
                 int lv[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const unsigned e = e0 + k * gsize;
-                    lv[k] = e < a1 ? __ldcs(&x.nbr[e]) : -1;
+                    lv[k] = -1;
+                    if (e < m) lv[k] = SMEM ? src[e] : __ldcs(&src[e]);
+                    if (lv[k] >= 0 && (!QM_CHK(lv[k], x.K, 6) || (R > 1 && tab_split((unsigned)lv[k], R) != r)))
+                        lv[k] = -1;
                 }
+                Rcp rj[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (lv[k] >= 0) rj[k] = ld_rcp(&x.recip[lv[k]]);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    if (lv[k] < 0 || !QM_CHK(lv[k], x.K, 6)) continue;
-                    if (R == 1 || tab_split((unsigned)lv[k], R) == r) tab_insert_cas(tab, (unsigned)lv[k]);
+                    if (lv[k] < 0) continue;
+                    const int prev = tab.add((unsigned)lv[k], epoch);
+                    if (prev < 0) continue;  // overflow: this pass is discarded
+                    if (prev == 0) {  // first occurrence (the common case): q = 1
+                        u192_add_rcp(inner, rj[k]);
+                        cnt2 += 1ull;
+                        slots += 1ull;
+                    } else {
+                        const unsigned long long q = 2ull * (unsigned long long)prev + 1ull;
+                        u192_mac(inner, q, rj[k]);
+                        cnt2 += q;
+                    }
                 }
+            }
+            group_sync(gsize);
+            if (*(volatile int *)tab.overflow) ok = false;
+        }
+        if (!ok) {
+            group_sync(gsize);
+            if (gtid == 0) *tab.overflow = 0;
+            group_sync(gsize);
+            const unsigned nr = R * 2u;
+            if (nr > R_MAX) {
+                if (gtid == 0) atomicOr(x.err, 2);
+                return;
+            }
+            R = nr;
+            continue;
+        }
+        group_totals(slots, cnt2, inner, gsize, red);
+        if (gtid == 0) put_record(x, h.c, h.vol, m, slots, cnt2, inner);
+        if (gsize == 32) __syncwarp();
+        return;
+    }
+}
+
+// Adds one entry's share of the pair sum: the k-th occurrence (prev = k - 1)
+// of a key with reciprocal r adds (2k - 1) r.
+__device__ __forceinline__ void add_share(U192 &inner, unsigned long long &slots, unsigned long long &cnt2, int prev,
+                                          const Rcp &r)
+{
+    if (prev == 0) {  // first occurrence (the common case): q = 1
+        u192_add_rcp(inner, r);
+        cnt2 += 1ull;
+        slots += 1ull;
+    } else {
+        const unsigned long long q = 2ull * (unsigned long long)prev + 1ull;
+        u192_mac(inner, q, r);
+        cnt2 += q;
+    }
+}
+
+// The same count for runs too long for the staged block path, including runs
+// of 2^24 entries or more (a key may then occur 2^25 times or more): 64-bit
+// counts in the tab_insert table, one pass over the used slots per class.
+// Block groups only; the table must be empty on entry and is left empty.
+__device__ __forceinline__ void count_run_general(const CountCtx &x, const RunHdr &h, const SmemTable &tab, int gtid,
+                                                  int gsize, unsigned long long *red)
+{
+    const unsigned m = h.m;
+    const int *src = x.nbr + h.a0;
+    const unsigned cap_keys = (unsigned)tab.max_used;
+    unsigned R = m <= cap_keys ? 1u : (unsigned)min((unsigned long long)R_MAX, (5ull * m + 4ull * cap_keys - 1) / (4ull * cap_keys));
+    for (;;) {
+        unsigned long long slots = 0, cnt2 = 0;
+        U192 inner;
+        u192_zero(inner);
+        bool ok = true;
+        for (unsigned r = 0; r < R && ok; ++r) {
+            for (unsigned e = gtid; e < m; e += gsize) {
+                const int lv = __ldcs(&src[e]);
+                if (!QM_CHK(lv, x.K, 6)) continue;
+                if (R == 1 || tab_split((unsigned)lv, R) == r) tab_insert(tab, (unsigned)lv);
             }
             group_sync(gsize);
             if (*(volatile int *)tab.overflow) {
                 ok = false;
                 break;
             }
-            // drain, four entries at a time so their reciprocal loads overlap
-            const int nu = min(*tab.n_used, tab.max_used);
-            for (int i0 = gtid; i0 < nu; i0 += 4 * gsize) {
-                unsigned long long s[4], rj[4];
-                int hh[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int i = i0 + k * gsize;
-                    hh[k] = i < nu ? tab.used[i] : -1;
-                    s[k] = hh[k] >= 0 && QM_CHK(hh[k], tab.cap, 9) ? tab.slot[hh[k]] : 0ull;
-                    const int key = (int)(s[k] >> 32) - 1;
-                    rj[k] = s[k] && QM_CHK(key, x.K, 7) ? __ldg(&x.recip[key]) : 0ull;
-                }
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if (!s[k]) continue;
-                    const int key = (int)(s[k] >> 32) - 1;
-                    const unsigned long long cnt = s[k] & 0xFFFFFFFFull;
-                    const unsigned long long q = cnt * cnt;
-                    inner += pair_inner(q, rj[k], x.start, key);
-                    ++slots;
-                    cnt2 += q;
-                    tab.slot[hh[k]] = 0ull;
-                }
-            }
-            if (r + 1 < R) {  // another class follows: the table must be empty first
-                group_sync(gsize);
-                if (gtid == 0) *tab.n_used = 0;
-                group_sync(gsize);
-            }
+            tab_drain(tab, gtid, gsize, [&](int key, long long cnt) {
+                if (!QM_CHK(key, x.K, 7)) return;
+                const unsigned long long q = (unsigned long long)cnt * (unsigned long long)cnt;
+                u192_mac(inner, q, ld_rcp(&x.recip[key]));
+                ++slots;
+                cnt2 += q;
+            });
+            group_sync(gsize);
+            if (gtid == 0) *tab.n_used = 0;
+            group_sync(gsize);
         }
         if (!ok) {
             tab_wipe(tab, gtid, gsize);
@@ -642,40 +848,9 @@ __device__ __forceinline__ void count_community(const CountCtx &x, int c, const 
             R = nr;
             continue;
         }
-        // one exchange of (slots, cnt2, inner) per warp; its barrier also
-        // orders this community's drain before the next community's inserts
-        slots = warp_sum_u64(slots);
-        cnt2 = warp_sum_u64(cnt2);
-        for (int d = 16; d > 0; d >>= 1) inner += shfl_down_u128(inner, d);
-        if (gsize > 32) {
-            const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-            if (lane == 0) {
-                red[4 * wid] = slots;
-                red[4 * wid + 1] = cnt2;
-                red[4 * wid + 2] = (unsigned long long)inner;
-                red[4 * wid + 3] = (unsigned long long)(inner >> 64);
-            }
-            block_sync();
-            if (gtid == 0)
-                for (int w = 1; w < nw; ++w) {
-                    slots += red[4 * w];
-                    cnt2 += red[4 * w + 1];
-                    inner += ((u128)red[4 * w + 3] << 64) | red[4 * w + 2];
-                }
-        }
-        if (gtid == 0) {
-            unsigned long long *rc = x.rec + (size_t)c * REC_WORDS;
-            rc[REC_SAME] = (unsigned long long)(vol - m);
-            rc[REC_VOL] = (unsigned long long)vol;
-            rc[REC_SLOTS] = slots;
-            rc[REC_CNT2] = cnt2;
-            rc[REC_INNER_LO] = (unsigned long long)inner;
-            rc[REC_INNER_HI] = (unsigned long long)(inner >> 64);
-            // a block caller alternates two counters, so this reset cannot
-            // race with the next community's inserts
-            *tab.n_used = 0;
-        }
-        if (gsize == 32) __syncwarp();
+        group_totals(slots, cnt2, inner, gsize, red);
+        if (gtid == 0) put_record(x, h.c, h.vol, m, slots, cnt2, inner);
+        group_sync(gsize);
         return;
     }
 }

@@ -140,6 +140,106 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
     return v;
 }
 
+// ---------------------------------------------------------------- exact pair sums
+//
+// The split penalty of Eq. (9) for community i needs S_i = sum_j |E_ij|^2 / |c_j|
+// over the neighbouring communities j.  Each 1/|c_j| is held as the 128-bit
+// integer Rcp_j = floor((2^128 - 1) / |c_j|) (relative error below 2^-97 for
+// any size below 2^31), and sum_j |E_ij|^2 Rcp_j is accumulated exactly in 192
+// bits; S_i is that sum / 2^128.  Integer sums do not depend on the order or
+// grouping of their terms, so a pass that adds |E_ij|^2 per key and one that
+// adds (2k - 1) Rcp_j for the k-th occurrence of key j (sum over k of 2k - 1
+// is |E_ij|^2) give identical bits.
+
+struct __align__(16) Rcp {
+    unsigned long long lo, hi;
+};
+
+// floor((2^128 - 1) / s) for 1 <= s < 2^31, by long division in 32-bit digits.
+__device__ __forceinline__ Rcp rcp_of(long long s)
+{
+    const unsigned long long d = (unsigned long long)s;
+    unsigned long long rem = 0, q[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const unsigned long long cur = (rem << 32) | 0xFFFFFFFFull;
+        q[k] = cur / d;
+        rem = cur % d;
+    }
+    Rcp r;
+    r.hi = (q[0] << 32) | q[1];
+    r.lo = (q[2] << 32) | q[3];
+    return r;
+}
+
+// Loads through L2 only (data written earlier in the same launch) / through
+// the read-only path.
+__device__ __forceinline__ Rcp ld_rcp_cg(const Rcp *p)
+{
+    const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2 *>(p));
+    return Rcp{v.x, v.y};
+}
+
+__device__ __forceinline__ Rcp ld_rcp(const Rcp *p)
+{
+    const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(p));
+    return Rcp{v.x, v.y};
+}
+
+struct U192 {
+    unsigned long long w0, w1, w2;
+};
+
+__device__ __forceinline__ void u192_zero(U192 &a) { a.w0 = a.w1 = a.w2 = 0ull; }
+
+// a += q * r
+__device__ __forceinline__ void u192_mac(U192 &a, unsigned long long q, const Rcp &r)
+{
+    const u128 p0 = (u128)q * r.lo;
+    const u128 p1 = (u128)q * r.hi;
+    const u128 t = (((u128)a.w1 << 64) | a.w0) + p0;
+    const unsigned long long c = t < p0 ? 1ull : 0ull;
+    a.w0 = (unsigned long long)t;
+    const u128 t2 = (((u128)(a.w2 + c) << 64) | (unsigned long long)(t >> 64)) + p1;
+    a.w1 = (unsigned long long)t2;
+    a.w2 = (unsigned long long)(t2 >> 64);
+}
+
+// a += r (u192_mac with q = 1)
+__device__ __forceinline__ void u192_add_rcp(U192 &a, const Rcp &r)
+{
+    const u128 r128 = ((u128)r.hi << 64) | r.lo;
+    const u128 t = (((u128)a.w1 << 64) | a.w0) + r128;
+    a.w2 += t < r128 ? 1ull : 0ull;
+    a.w0 = (unsigned long long)t;
+    a.w1 = (unsigned long long)(t >> 64);
+}
+
+__device__ __forceinline__ void u192_add(U192 &a, const U192 &b)
+{
+    const u128 lb = ((u128)b.w1 << 64) | b.w0;
+    const u128 t = (((u128)a.w1 << 64) | a.w0) + lb;
+    a.w2 += b.w2 + (t < lb ? 1ull : 0ull);
+    a.w0 = (unsigned long long)t;
+    a.w1 = (unsigned long long)(t >> 64);
+}
+
+// Warp total (valid in lane 0).
+__device__ __forceinline__ U192 u192_warp_sum(U192 a)
+{
+    for (int d = 16; d > 0; d >>= 1) {
+        U192 o;
+        o.w0 = __shfl_down_sync(0xffffffffu, a.w0, d);
+        o.w1 = __shfl_down_sync(0xffffffffu, a.w1, d);
+        o.w2 = __shfl_down_sync(0xffffffffu, a.w2, d);
+        u192_add(a, o);
+    }
+    return a;
+}
+
+// S * 2^64 as a 64.64 fixed-point number: the sum shifted right by 64 bits.
+__device__ __forceinline__ u128 u192_shr64(const U192 &a) { return ((u128)a.w2 << 64) | a.w1; }
+
 // ---------------------------------------------------------------- accumulators
 
 // Per-thread partial sums of one partition's no-ground-truth metrics.
@@ -343,6 +443,52 @@ __device__ __forceinline__ void tab_insert(const SmemTable &t, unsigned key)
     *t.overflow = 1;
 }
 
+// ---------------------------------------------------------------- bulk copies
+//
+// One-dimensional TMA bulk copy global -> shared memory completing on an
+// mbarrier (PTX cp.async.bulk / mbarrier.*).  Both addresses must be 16-byte
+// aligned and the size a multiple of 16 bytes.
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// Orders this thread's earlier shared-memory accesses (and barrier inits)
+// before later accesses by the async proxy (bulk copies).
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_load_smem(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Waits for the phase with the given parity to complete; gives up after
+// `limit` polls (each poll may itself suspend briefly) and returns false.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, unsigned limit)
+{
+    for (unsigned i = 0; i < limit; ++i) {
+        unsigned done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(smem_u32(bar)), "r"(parity)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 // ---------------------------------------------------------------- misc
 
 // Number of entries of the sorted prefix a[0..n) that are <= x.
@@ -361,10 +507,14 @@ __device__ __forceinline__ int upper_bound_smem(const unsigned *a, int n, unsign
 // routines reach their barriers straight from data-dependent loops (hash-table
 // probing, ragged arc loops), so the warp may arrive in several pieces.  The
 // non-aligned barrier counts threads, not converged warps, and orders memory
-// like __syncthreads().
+// like __syncthreads().  Every lane of every warp has arrived once it returns,
+// so a warp sync then merges the pieces again: without it a warp can stay
+// split and issue each later instruction once per piece.  (No caller lets a
+// lane exit while others of its warp still reach a block barrier.)
 __device__ __forceinline__ void block_sync()
 {
     asm volatile("barrier.sync 0;" ::: "memory");
+    __syncwarp();
 }
 
 __device__ __forceinline__ void group_sync(int group)

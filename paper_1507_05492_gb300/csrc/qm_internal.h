@@ -7,6 +7,11 @@
 
 #include "../../include/qm.h"
 
+namespace qmk {
+struct Rcp;     // 128-bit reciprocal of a community size (qm_device.cuh)
+struct RunHdr;  // header of one community's packed run (qm_community.cuh)
+}
+
 namespace qm {
 
 // Device copy of a symmetric CSR (library-owned).
@@ -36,6 +41,19 @@ struct SmemPlan {
 };
 SmemPlan plan_smem(int threads, int smem_bytes);
 
+// Shared-memory layout of the two-phase count kernel: reduction exchange,
+// table control words, two mbarriers, two staging buffers for bulk-copied
+// runs, and the counting table (a block table of `cap` slots, or W warp
+// slices of cap_w).  Runs of up to `fill` entries (3/4 of the table) are
+// staged; warps take runs of up to fill_w.
+struct CountPlan {
+    int red_off, ctl_off, bar_off, stage_off, slot_off;
+    int stage_elems;
+    int cap, fill, cap_w, fill_w;
+    int bytes;
+};
+CountPlan plan_count(int threads, int smem_bytes);
+
 // Device scratch of one plain scoring call (carved from one allocation).
 struct ScoreWs {
     int *status;                // [1] bit 0: label out of range
@@ -44,7 +62,7 @@ struct ScoreWs {
     qm_quality *result;         // [1]
     int *size;                  // [K]
     int *start;                 // [K + 1]
-    unsigned long long *recip;  // [K] size_recip(|c|)
+    qmk::Rcp *recip;            // [K] rcp_of(|c|)
     int *cursor;                // [K]
     int *big_list;              // [K]
     int *ovf_list;              // [K]
@@ -52,6 +70,9 @@ struct ScoreWs {
     int *scan_tmp;              // [scan tiles + 1]
     unsigned *aoff;             // two-phase only: [n + 1] arc offsets of member positions
     int *inter;                 // two-phase only: [K] cut arcs of each community (zeroed)
+    qmk::RunHdr *hdr_big;       // two-phase only: [K] run headers for whole blocks
+    qmk::RunHdr *hdr_small;     // two-phase only: [K] run headers for single warps
+    qmk::RunHdr *hdr_long;      // two-phase only: [K] run headers for k_count_long
     int *nbr;                   // two-phase only: [n_arcs] neighbour labels in community order
     unsigned long long *rec;    // two-phase only: [K][6] per-community records
     size_t zero_bytes;          // bytes from `status` that must start at zero
@@ -139,7 +160,7 @@ struct BatchScratch {
     unsigned *rowmax_n;      // [slots][kt_max]
     unsigned long long *rowmax_r; // [slots][kt_max]
     int *big_list;           // [slots][3 k_max]
-    unsigned long long *recip; // [slots][k_max]
+    qmk::Rcp *recip;           // [slots][k_max]
     long long n_max;
     int k_max, kt_max;
     int slots;

@@ -20,7 +20,8 @@
 namespace qm {
 using namespace qmk;
 
-enum { C_BIG_COUNT = 0, C_BIG_NEXT = 1, C_SMALL_NEXT = 2, C_OVF_COUNT = 3, C_OVF_NEXT = 4 };
+enum { C_BIG_COUNT = 0, C_BIG_NEXT = 1, C_SMALL_NEXT = 2, C_OVF_COUNT = 3, C_OVF_NEXT = 4, C_SMALL_COUNT = 5,
+       C_LONG_COUNT = 6 };
 
 constexpr int SCAN_TILE = 4096;   // elements per block in the multi-block scan
 constexpr int SCAN_SINGLE_MAX = 1 << 16;
@@ -59,6 +60,34 @@ SmemPlan plan_smem(int T, int S)
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+CountPlan plan_count(int T, int S)
+{
+    CountPlan p;
+    const int W = T / 32;
+    int off = 0;
+    p.red_off = off;
+    off += 256 * 8;
+    p.ctl_off = off;
+    off += ((2 * (W + 1) * 4 + 15) / 16) * 16;
+    p.bar_off = off;
+    off += 16;
+    p.stage_off = off;
+    // 8 bytes per slot plus two staging buffers of 3/4 of the slots (4 bytes each, + 8 entries of slack)
+    const int rest = S - off;
+    int cap = (rest - 2 * 4 * 12) / 14;
+    cap = (cap / W) * W;
+    p.cap = cap;
+    p.fill = 3 * cap / 4;
+    p.stage_elems = (p.fill + 8 + 3) & ~3;
+    off += 2 * p.stage_elems * 4;
+    p.slot_off = off;
+    off += cap * 8;
+    p.cap_w = cap / W;
+    p.fill_w = 3 * p.cap_w / 4;
+    p.bytes = off;
+    return p;
+}
+
 static int scan_tiles(int K) { return (K + SCAN_TILE - 1) / SCAN_TILE; }
 
 size_t score_ws_bytes(long long n, int K)
@@ -69,7 +98,7 @@ size_t score_ws_bytes(long long n, int K)
     b += align_up(sizeof(qm_quality), 256);     // result
     b += align_up((size_t)K * 4, 256);          // size (zeroed)
     b += align_up((size_t)(K + 1) * 4, 256);    // start
-    b += align_up((size_t)K * 8, 256);          // recip
+    b += align_up((size_t)K * 16, 256);         // recip
     b += align_up((size_t)K * 4, 256) * 3;      // cursor, big_list, ovf_list
     b += align_up((size_t)n * 4, 256);          // members
     b += align_up((size_t)(scan_tiles(K) + 1) * 4, 256);
@@ -94,8 +123,8 @@ ScoreWs carve_score_ws(void *base, long long n, int K)
     w.zero_bytes = (size_t)(p - (char *)base);
     w.start = (int *)p;
     p += align_up((size_t)(K + 1) * 4, 256);
-    w.recip = (unsigned long long *)p;
-    p += align_up((size_t)K * 8, 256);
+    w.recip = (Rcp *)p;
+    p += align_up((size_t)K * 16, 256);
     w.cursor = (int *)p;
     p += align_up((size_t)K * 4, 256);
     w.big_list = (int *)p;
@@ -197,7 +226,7 @@ __global__ void k_hist(const int *__restrict__ a, int ka, int *size_a, const int
 
 // Exclusive prefix of size[0..K) by one block.  Writes start[0..K], optionally
 // cursor = start, and appends ids with size > big_thr to big_list.
-__global__ void k_scan_single(const int *size, int K, int *start, int *cursor, unsigned long long *recip,
+__global__ void k_scan_single(const int *size, int K, int *start, int *cursor, Rcp *recip,
                               int big_thr, int *big_list, int *counters, const int *status)
 {
     __shared__ unsigned long long red[72];
@@ -214,7 +243,7 @@ __global__ void k_scan_single(const int *size, int K, int *start, int *cursor, u
         const int s = size[i];
         start[i] = (int)run;
         if (cursor) cursor[i] = (int)run;
-        if (recip) recip[i] = size_recip(s);
+        if (recip && s > 0) recip[i] = rcp_of(s);
         if (s > big_thr) big_list[atomicAdd(&counters[C_BIG_COUNT], 1)] = (int)i;
         run += (unsigned)s;
     }
@@ -236,7 +265,7 @@ __global__ void k_scan_tiles(const int *size, int K, int *tile_sum, const int *s
 }
 
 __global__ void k_scan_apply(const int *size, int K, const int *tile_off, int *start, int *cursor,
-                             unsigned long long *recip, int big_thr, int *big_list, int *counters,
+                             Rcp *recip, int big_thr, int *big_list, int *counters,
                              const int *status)
 {
     __shared__ unsigned long long red[72];
@@ -255,7 +284,7 @@ __global__ void k_scan_apply(const int *size, int K, const int *tile_off, int *s
         const int s = size[i];
         start[i] = (int)run;
         if (cursor) cursor[i] = (int)run;
-        if (recip) recip[i] = size_recip(s);
+        if (recip && s > 0) recip[i] = rcp_of(s);
         if (s > big_thr) big_list[atomicAdd(&counters[C_BIG_COUNT], 1)] = (int)i;
         run += (unsigned)s;
     }
@@ -679,81 +708,188 @@ __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__re
     }
 }
 
-// Communities whose cut arcs (an upper bound on their distinct neighbour
-// communities) exceed a warp table go to whole blocks in phase B.
-__global__ void k_classify(const int *start, const int *inter, int K, int warp_thr, int *big_list, int *counters,
+// One header per non-empty community, sorted into three lists by run length
+// m (the community's cut arcs, an upper bound on its distinct neighbouring
+// communities): m <= warp_fill for single warps, warp_fill < m <= block_fill
+// for whole blocks of k_count, longer runs for k_count_long.  Appends are
+// warp-aggregated.
+__global__ void k_classify(const int *start, const unsigned *aoff, const int *inter, int K, int warp_fill,
+                           int block_fill, RunHdr *big, RunHdr *small, RunHdr *lng, int *counters,
                            const int *status)
 {
     if (*status) return;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < K; c += gridDim.x * blockDim.x) {
-        if (start[c + 1] > start[c] && inter[c] > warp_thr)
-            big_list[atomicAdd(&counters[C_BIG_COUNT], 1)] = c;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    for (long long c0 = (long long)blockIdx.x * blockDim.x; c0 < K; c0 += (long long)gridDim.x * blockDim.x) {
+        const long long cl = c0 + threadIdx.x;
+        int cls = -1;
+        RunHdr h{-1, 0u, 0u, 0u};
+        if (cl < K) {
+            const int c = (int)cl;
+            const int s0 = start[c], s1 = start[c + 1];
+            if (s1 > s0) {
+                const unsigned a0 = aoff[s0];
+                h = RunHdr{c, a0, (unsigned)inter[c], aoff[s1] - a0};
+                cls = h.m > (unsigned)block_fill ? 2 : (h.m > (unsigned)warp_fill ? 0 : 1);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const unsigned mask = __ballot_sync(0xffffffffu, cls == k);
+            if (!mask) continue;
+            const int leader = __ffs(mask) - 1;
+            int base = 0;
+            if (lane == leader)
+                base = atomicAdd(&counters[k == 0 ? C_BIG_COUNT : (k == 1 ? C_SMALL_COUNT : C_LONG_COUNT)],
+                                 __popc(mask));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (cls == k) (k == 0 ? big : (k == 1 ? small : lng))[base + __popc(mask & lt)] = h;
+        }
     }
 }
 
 struct CountKArgs {
     CountCtx x;
-    const int *big_list;
+    const RunHdr *big;
+    const RunHdr *small;
     int *counters;
     const int *status;
-    int warp_thr;
-    SmemPlan plan;
+    CountPlan plan;
 };
 
-// Phase B: large runs by whole blocks (a queue whose next item is fetched while
-// the current one is counted), the rest by single warps.
+constexpr unsigned STAGE_WAIT_LIMIT = 1u << 22;
+
+// Phase B.  Runs longer than a warp table takes go to whole blocks in a static
+// round-robin; while a block counts one run, the next run is already on its
+// way into shared memory (a TMA bulk copy into the other of two staging
+// buffers, completing on an mbarrier) and the header after that is being
+// loaded.  Short runs then go to single warps, 32 headers at a time.  Each
+// group has its own epoch-tagged table (see count_run).  Runs longer than the
+// staging buffers go to k_count_long.
+template <class TAB>
 __global__ void __launch_bounds__(1024) k_count(CountKArgs a)
 {
     extern __shared__ __align__(16) unsigned char sm[];
-    __shared__ int s_item[2];
-    __shared__ int s_nused_alt;
+    __shared__ RunHdr ring[3];
+    __shared__ int s_timeout;
     if (*a.status) return;
-    const SmemPlan &p = a.plan;
+    const CountPlan &p = a.plan;
     unsigned long long *red = (unsigned long long *)(sm + p.red_off);
     int *ctl = (int *)(sm + p.ctl_off);
+    unsigned long long *bars = (unsigned long long *)(sm + p.bar_off);
+    int *stage = (int *)(sm + p.stage_off);
     unsigned long long *slot = (unsigned long long *)(sm + p.slot_off);
-    int *used = (int *)(sm + p.used_off);
-    const int T = blockDim.x, W = T >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < p.cap; i += T) slot[i] = 0ull;
-    for (int i = threadIdx.x; i < 2 * (W + 1); i += T) ctl[i] = 0;
-    const int count = a.counters[C_BIG_COUNT];
-    if (threadIdx.x == 0) {
-        s_nused_alt = 0;
-        const int i = atomicAdd(&a.counters[C_BIG_NEXT], 1);
-        s_item[0] = i < count ? a.big_list[i] : -1;
+    const int T = blockDim.x, tid = threadIdx.x, wid = tid >> 5, lane = tid & 31, W = T >> 5;
+    for (int i = tid; i < p.cap; i += T) slot[i] = 0ull;
+    for (int i = tid; i < 2 * (W + 1); i += T) ctl[i] = 0;
+    const int nbig = a.counters[C_BIG_COUNT];
+    const long long G = gridDim.x, b = blockIdx.x;
+    const RunHdr none{-1, 0u, 0u, 0u};
+    // thread 0's bookkeeping of the staging buffers: copies issued and
+    // consumed per buffer, packed as issued0 | issued1 << 16 ... (wrapping
+    // 16-bit counters; only their difference and low bit are used)
+    unsigned issued = 0u, used = 0u;
+    auto cnt_of = [](unsigned v, int k) { return (v >> (16 * k)) & 0xFFFFu; };
+    auto issue = [&](const RunHdr &h, int k) {
+        const unsigned lo = h.a0 & ~3u;
+        const unsigned bytes = ((h.a0 - lo) + h.m + 3u) / 4u * 16u;
+        bulk_load_smem(stage + k * p.stage_elems, a.x.nbr + lo, bytes, &bars[k]);
+        issued = (issued & ~(0xFFFFu << (16 * k))) | (((cnt_of(issued, k) + 1u) & 0xFFFFu) << (16 * k));
+    };
+    auto consume = [&](int k) {
+        used = (used & ~(0xFFFFu << (16 * k))) | (((cnt_of(used, k) + 1u) & 0xFFFFu) << (16 * k));
+    };
+    if (tid == 0) {
+        s_timeout = 0;
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_proxy_async_smem();
+        ring[0] = b < nbig ? a.big[b] : none;
+        ring[1] = b + G < nbig ? a.big[b + G] : none;
+        if (ring[0].c >= 0) issue(ring[0], 0);
     }
     block_sync();
+    const TAB eb = make_table<TAB>(slot, p.cap, &ctl[1]);
+    unsigned epoch = 0;
+    bool aborted = false;
     for (int it = 0;; ++it) {
-        const int c = s_item[it & 1];
-        if (c < 0) break;
-        // the next item lands in the other slot; count_community's barriers
-        // publish it before the next iteration reads it
-        if (threadIdx.x == 0) {
-            const int i = atomicAdd(&a.counters[C_BIG_NEXT], 1);
-            s_item[(it + 1) & 1] = i < count ? a.big_list[i] : -1;
+        const RunHdr h = ring[it % 3];
+        if (h.c < 0) break;
+        const int k = it & 1;
+        RunHdr nn = none;
+        if (tid == 0) {
+            const RunHdr hn = ring[(it + 1) % 3];
+            if (hn.c >= 0) {
+                fence_proxy_async_smem();
+                issue(hn, k ^ 1);
+            }
+            const long long idx = b + (long long)(it + 2) * G;
+            if (idx < nbig) nn = a.big[idx];
+            if (mbar_wait(&bars[k], cnt_of(used, k) & 1u, STAGE_WAIT_LIMIT)) consume(k);
+            else s_timeout = 1;
         }
-        const SmemTable tb{slot, used, (it & 1) ? &s_nused_alt : &ctl[0], &ctl[1], p.cap, p.max_used};
-        count_community(a.x, c, tb, threadIdx.x, T, red);
+        block_sync();
+        if (s_timeout) {
+            aborted = true;
+            break;
+        }
+        count_run<true>(a.x, h, stage + k * p.stage_elems + (h.a0 & 3u), eb, epoch, tid, T, red);
+        if (tid == 0) ring[(it + 2) % 3] = nn;
     }
-    const SmemTable tw{slot + wid * p.cap_w, used + wid * p.max_used_w, &ctl[2 + 2 * wid], &ctl[3 + 2 * wid],
-                       p.cap_w, p.max_used_w};
+    if (aborted) {
+        // report, and let the copies still in flight land before the block exits
+        if (tid == 0) {
+            atomicOr(a.x.err, 4);
+            for (int q = 0; q < 2; ++q)
+                while (cnt_of(used, q) != cnt_of(issued, q) && mbar_wait(&bars[q], cnt_of(used, q) & 1u, STAGE_WAIT_LIMIT))
+                    consume(q);
+        }
+        return;
+    }
+    // the warps' tables are slices of the block's: start them empty
+    block_sync();
+    for (int i = tid; i < p.cap; i += T) slot[i] = 0ull;
+    block_sync();
+    const TAB ew = make_table<TAB>(slot + wid * p.cap_w, p.cap_w, &ctl[3 + 2 * wid]);
+    unsigned wepoch = 0;
+    const int nsmall = a.counters[C_SMALL_COUNT];
     for (;;) {
         int base = 0;
         if (lane == 0) base = atomicAdd(&a.counters[C_SMALL_NEXT], 32);
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= a.x.K) break;
-        const int c = base + lane;
-        bool take = false;
-        if (c < a.x.K) {
-            take = __ldg(&a.x.start[c + 1]) > __ldg(&a.x.start[c]) && __ldcg(&a.x.inter[c]) <= a.warp_thr;
-        }
-        unsigned mask = __ballot_sync(0xffffffffu, take);
-        while (mask) {
-            const int j = __ffs(mask) - 1;
-            mask &= mask - 1;
-            count_community(a.x, base + j, tw, lane, 32, red);
+        if (base >= nsmall) break;
+        const RunHdr mine = base + lane < nsmall ? a.small[base + lane] : none;
+        const int cnt = min(32, nsmall - base);
+        for (int j = 0; j < cnt; ++j) {
+            RunHdr h;
+            h.c = __shfl_sync(0xffffffffu, mine.c, j);
+            h.a0 = __shfl_sync(0xffffffffu, mine.a0, j);
+            h.m = __shfl_sync(0xffffffffu, mine.m, j);
+            h.vol = __shfl_sync(0xffffffffu, mine.vol, j);
+            count_run<false>(a.x, h, a.x.nbr + h.a0, ew, wepoch, lane, 32, red);
         }
     }
+}
+
+// Runs longer than the block tables of k_count hold at 3/4 load (and any run
+// of 2^24 entries or more), one block each, with 64-bit counts
+// (count_run_general).
+__global__ void __launch_bounds__(1024) k_count_long(CountCtx x, const RunHdr *lng, const int *counters,
+                                                      SmemPlan p, const int *status)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    if (*status) return;
+    const int n = counters[C_LONG_COUNT];
+    if ((int)blockIdx.x >= n) return;
+    unsigned long long *red = (unsigned long long *)(sm + p.red_off);
+    int *ctl = (int *)(sm + p.ctl_off);
+    unsigned long long *slot = (unsigned long long *)(sm + p.slot_off);
+    int *used = (int *)(sm + p.used_off);
+    for (int i = threadIdx.x; i < p.cap; i += blockDim.x) slot[i] = 0ull;
+    if (threadIdx.x < 2) ctl[threadIdx.x] = 0;
+    block_sync();
+    const SmemTable tb{slot, used, &ctl[0], &ctl[1], p.cap, p.max_used};
+    for (int i = blockIdx.x; i < n; i += gridDim.x) count_run_general(x, lng[i], tb, threadIdx.x, blockDim.x, red);
 }
 
 // Block reduction of per-thread sums into the partition's global limbs.
@@ -807,13 +943,15 @@ void prepare_kernels()
 {
     cudaFuncSetAttribute(k_score_cm, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     cudaFuncSetAttribute(k_compare_cm, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
-    cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+    cudaFuncSetAttribute(k_count<EpochTable>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+    cudaFuncSetAttribute(k_count<EpochTable32>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+    cudaFuncSetAttribute(k_count_long, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
 }
 
 int count_blocks_per_sm(const Shape &sh)
 {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_count, sh.threads, sh.smem_bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_count<EpochTable32>, sh.threads, sh.smem_bytes);
     return nb;
 }
 
@@ -829,7 +967,7 @@ int score_blocks_per_sm(const Shape &sh)
         if (tr) tr(name, s); \
     } while (0)
 
-static int launch_scan(const int *size, int K, int *start, int *cursor, unsigned long long *recip, int big_thr,
+static int launch_scan(const int *size, int K, int *start, int *cursor, Rcp *recip, int big_thr,
                        int *big_list, int *counters, int *tmp, const int *status, cudaStream_t s, TraceFn tr)
 {
     if (K <= SCAN_SINGLE_MAX) {
@@ -913,12 +1051,13 @@ size_t score2_ws_bytes(long long n, long long n_arcs, int K)
     b += 256 + align_up(32 * 8, 256) + align_up(sizeof(qm_quality), 256);
     b += align_up((size_t)K * 4, 256) * 2;          // size, inter (zeroed)
     b += align_up((size_t)(K + 1) * 4, 256);        // start
-    b += align_up((size_t)K * 8, 256);              // recip
+    b += align_up((size_t)K * 16, 256);             // recip
     b += align_up((size_t)K * 4, 256) * 2;          // cursor, big_list
     b += align_up((size_t)n * 4, 256);              // members
     b += align_up((size_t)(n + 1) * 4, 256);        // member degrees -> arc offsets
-    b += align_up((size_t)n_arcs * 4, 256);         // neighbour labels in community order
+    b += align_up((size_t)n_arcs * 4, 256) + 256;   // packed neighbour labels (+ slack for 16-byte copies)
     b += align_up((size_t)K * 8 * REC_WORDS, 256);  // per-community records
+    b += align_up((size_t)K * sizeof(RunHdr), 256) * 3;  // run headers: block, warp and general lists
     b += align_up((size_t)(tiles + 1) * 4, 256);    // scan tiles
     return b;
 }
@@ -942,8 +1081,8 @@ ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K)
     w.zero_bytes = (size_t)(p - (char *)base);
     w.start = (int *)p;
     p += align_up((size_t)(K + 1) * 4, 256);
-    w.recip = (unsigned long long *)p;
-    p += align_up((size_t)K * 8, 256);
+    w.recip = (Rcp *)p;
+    p += align_up((size_t)K * 16, 256);
     w.cursor = (int *)p;
     p += align_up((size_t)K * 4, 256);
     w.big_list = (int *)p;
@@ -954,9 +1093,15 @@ ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K)
     w.aoff = (unsigned *)p;
     p += align_up((size_t)(n + 1) * 4, 256);
     w.nbr = (int *)p;
-    p += align_up((size_t)n_arcs * 4, 256);
+    p += align_up((size_t)n_arcs * 4, 256) + 256;
     w.rec = (unsigned long long *)p;
     p += align_up((size_t)K * 8 * REC_WORDS, 256);
+    w.hdr_big = (RunHdr *)p;
+    p += align_up((size_t)K * sizeof(RunHdr), 256);
+    w.hdr_small = (RunHdr *)p;
+    p += align_up((size_t)K * sizeof(RunHdr), 256);
+    w.hdr_long = (RunHdr *)p;
+    p += align_up((size_t)K * sizeof(RunHdr), 256);
     w.scan_tmp = (int *)p;
     (void)tiles;
     return w;
@@ -988,10 +1133,11 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
     k_expand<<<num_sms * 8, EXPAND_THREADS, 0, s>>>(g.row_ptr, g.col, labels, ws.members, ws.aoff, ws.start, n,
                                                     ws.inter, ws.nbr, ws.status);
     ++launches;
-    const SmemPlan plan = plan_smem(sh.threads, sh.smem_bytes);
+    const CountPlan cp = plan_count(sh.threads, sh.smem_bytes);
     TRACE("k_classify");
-    k_classify<<<grid_for(K, 256, num_sms, 4), 256, 0, s>>>(ws.start, ws.inter, K, plan.max_used_w, ws.big_list,
-                                                            ws.counters, ws.status);
+    k_classify<<<grid_for(K, 256, num_sms, 4), 256, 0, s>>>(ws.start, ws.aoff, ws.inter, K, cp.fill_w, cp.fill,
+                                                            ws.hdr_big, ws.hdr_small, ws.hdr_long, ws.counters,
+                                                            ws.status);
     ++launches;
     CountKArgs a;
     a.x.nbr = ws.nbr;
@@ -1002,26 +1148,19 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
     a.x.rec = ws.rec;
     a.x.K = K;
     a.x.err = ws.status;
-    a.big_list = ws.big_list;
+    a.big = ws.hdr_big;
+    a.small = ws.hdr_small;
     a.counters = ws.counters;
     a.status = ws.status;
-    a.warp_thr = plan.max_used_w;
-    a.plan = plan;
-    static int occ_cache[4][8] = {};
-    int nb = 0;
-    {
-        // occupancy of k_count for this shape (host-side query, cached per shape)
-        const int ti = sh.threads / 256 - 1, si = sh.smem_bytes / (32 * 1024);
-        if (ti >= 0 && ti < 4 && si >= 0 && si < 8 && occ_cache[ti][si] > 0) nb = occ_cache[ti][si];
-        else {
-            nb = count_blocks_per_sm(sh);
-            if (ti >= 0 && ti < 4 && si >= 0 && si < 8) occ_cache[ti][si] = nb;
-        }
-        if (nb < 1) nb = 1;
-    }
+    a.plan = cp;
+    const int nb = sh.blocks_per_sm > 0 ? sh.blocks_per_sm : 1;  // occupancy of k_count (resolved by the caller)
     TRACE("k_count");
-    k_count<<<num_sms * nb, sh.threads, sh.smem_bytes, s>>>(a);
-    ++launches;
+    if (K < (1 << 24) - 1) k_count<EpochTable32><<<num_sms * nb, sh.threads, sh.smem_bytes, s>>>(a);
+    else k_count<EpochTable><<<num_sms * nb, sh.threads, sh.smem_bytes, s>>>(a);
+    TRACE("k_count_long");
+    k_count_long<<<num_sms, 1024, MAX_DYN_SMEM, s>>>(a.x, ws.hdr_long, ws.counters, plan_smem(1024, MAX_DYN_SMEM),
+                                                      ws.status);
+    launches += 2;
     PerCommDev pcd{};
     if (pc) pcd = *pc;
     TRACE("k_score_terms");

@@ -126,6 +126,22 @@ def test_empty_label_ids_and_max_label(qm, oracle_mod):
     check_compare(c, oracle_mod.compare(truth, lab, 7, K))
 
 
+def test_label_space_beyond_24_bits(qm, gen, oracle_mod):
+    """K >= 2^24 - 1 takes the count tables with 31-bit keys; the result must
+    equal, bit for bit, the one for the same partition with compact ids (the
+    metrics ignore empty communities and the names of the others)."""
+    g = gen.lfr_graph(gen.LfrParams(n=30_000, seed=12))
+    graph = qm.Graph(*to_dev(g.row_ptr, g.col))
+    K_big = (1 << 24) + 5
+    ids = np.random.default_rng(12).choice(K_big, g.K, replace=False).astype(np.int32)
+    ids[0] = K_big - 1
+    lab = g.labels.numpy()
+    q_big = qm.score(graph, torch.from_numpy(ids[lab]).cuda(), K_big)
+    q_small = qm.score(graph, g.labels.cuda(), g.K)
+    assert q_big == q_small
+    check_quality(q_small, oracle_mod.score(g.row_ptr.numpy(), g.col.numpy(), lab, g.K), "compact ids")
+
+
 def test_star_hub_forces_multipass(qm, oracle_mod):
     """A hub whose community borders 30k other communities overflows every
     shared-memory table; the block path splits its neighbour ids into classes."""
