@@ -62,6 +62,10 @@ typedef enum { QM_HOST = 0, QM_DEVICE = 1 } qm_mem;
 
 /* qm_load_graph flags */
 #define QM_VALIDATE 1u /* check symmetry, no self-loops, no repeated arcs, ids in range */
+#define QM_REORDER 2u  /* store the graph renumbered for locality (see qm_load_graph) */
+
+/* Label-propagation rounds of the QM_REORDER clustering. */
+#define QM_REORDER_ROUNDS 6
 
 /* batched-compare flags */
 #define QM_SHARED_TRUTH 1u /* one truth labelling [n] shared by all P candidates */
@@ -75,7 +79,17 @@ typedef struct qm_graph qm_graph; /* opaque; owns a device copy of the CSR */
  *   row_ptr  int64[n_nodes + 1], row_ptr[0] = 0, non-decreasing, row_ptr[n] = n_arcs
  *   col      int32[n_arcs], neighbour ids in [0, n_nodes)
  *   where    QM_HOST or QM_DEVICE for row_ptr and col
- *   flags    QM_VALIDATE runs a device check of the CSR (untimed set-up work)
+ *   flags    QM_VALIDATE runs a device check of the CSR (untimed set-up work);
+ *            QM_REORDER stores the graph renumbered so that nodes of one
+ *            cluster are adjacent: QM_REORDER_ROUNDS synchronous
+ *            label-propagation rounds on the graph alone (each node takes the
+ *            most frequent label of up to 32 evenly spaced neighbours), then
+ *            the nodes are renumbered cluster by cluster.  Every call still
+ *            takes labels in the caller's node order (they are gathered
+ *            through the permutation on the device) and returns the same bits
+ *            as without the flag; the gathers of neighbour labels then mostly
+ *            hit nearby memory.  Costs one pass per round over the arcs and
+ *            4 bytes per node, at load time only.
  *   out      receives the handle; free it with qm_free_graph
  * The arrays are copied: the caller may free them when the call returns.
  * Errors: QM_EINVAL (n_nodes < 1, n_arcs odd or 0, bad CSR with QM_VALIDATE),

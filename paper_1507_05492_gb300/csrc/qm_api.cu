@@ -278,6 +278,7 @@ struct qm_graph {
     GraphDev d;
     long long *row_ptr;
     int *col;
+    int *inv = nullptr;  // QM_REORDER: new node id -> caller's node id (else null)
     long long n, n_arcs, max_degree;
     size_t bytes;
     std::mutex mu;
@@ -482,6 +483,25 @@ qm_status qm_load_graph(const int64_t *row_ptr, const int32_t *col, int64_t n_no
     g->max_degree = (long long)*(unsigned long long *)(pin.ptr() + 64);
     g->d.max_degree = g->max_degree;
     g->bytes = (size_t)(n_nodes + 1) * 8 + (size_t)n_arcs * 4;
+    if (flags & QM_REORDER) {
+        long long *row2 = nullptr;
+        int *col2 = nullptr, *inv = nullptr, L = 0;
+        const int r = reorder_graph(g->d, QM_REORDER_ROUNDS, num_sms_of(dev), s, &row2, &col2, &inv, &L);
+        if (r != 0) {
+            cleanup();
+            return cuda_fail((cudaError_t)(-r), "graph reorder");
+        }
+        g_launches += L;
+        cudaFree(g->row_ptr);
+        cudaFree(g->col);
+        g->row_ptr = row2;
+        g->col = col2;
+        g->inv = inv;
+        g->d.row_ptr = row2;
+        g->d.col = col2;
+        g->d.inv = inv;
+        g->bytes += (size_t)n_nodes * 4;
+    }
     *out = g.release();
     return QM_OK;
 }
@@ -492,6 +512,7 @@ qm_status qm_free_graph(qm_graph *g)
     DeviceGuard dg(g->device);
     cudaFree(g->row_ptr);
     cudaFree(g->col);
+    cudaFree(g->inv);
     delete g;
     return QM_OK;
 }
@@ -513,6 +534,7 @@ qm_status qm_workspace_bytes(const qm_graph *g, int32_t K, int32_t with_compare,
 {
     if (!g || !bytes || K < 1 || (with_compare && k_truth < 1)) return fail(QM_EINVAL, "bad argument");
     size_t b = std::max(score_ws_bytes(g->n, K), score2_ws_bytes(g->n, g->n_arcs, K)) + al256((size_t)g->n * 4);
+    if (g->inv) b += al256((size_t)g->n * 4);
     if (with_compare) b += compare_ws_bytes(g->n, k_truth, K) + al256((size_t)g->n * 4);
     *bytes = b;
     return QM_OK;
@@ -526,6 +548,8 @@ static qm_status score_impl(qm_graph *g, const int32_t *labels, int32_t K, qm_me
     size_t need = sh.algo ? score2_ws_bytes(n, g->n_arcs, K) : score_ws_bytes(n, K);
     const size_t lab_off = need;
     if (where == QM_HOST) need += al256((size_t)n * 4);
+    const size_t perm_off = need;
+    if (g->inv) need += al256((size_t)n * 4);
     const size_t pc_off = need;
     const bool pc_host = pc && where == QM_HOST;
     if (pc_host) need += al256((size_t)K * 8) * 8;
@@ -537,6 +561,15 @@ static qm_status score_impl(qm_graph *g, const int32_t *labels, int32_t K, qm_me
     if (where == QM_HOST) {
         dl = (const int32_t *)(ws.ptr() + lab_off);
         CK(cudaMemcpyAsync((void *)dl, labels, (size_t)n * 4, cudaMemcpyHostToDevice, s));
+    }
+    const TraceFn tr = trace_begin();
+    if (g->inv) {  // the graph is stored renumbered: gather the labels into its order
+        int32_t *pl = (int32_t *)(ws.ptr() + perm_off);
+        if (tr) tr("k_permute_labels", s);
+        if (launch_permute_labels(dl, g->inv, n, 1, pl, num_sms_of(g->device), s) < 0)
+            return cuda_fail(cudaGetLastError(), "label permutation");
+        g_launches += 1;
+        dl = pl;
     }
     CK(cudaMemsetAsync(ws.ptr(), 0, w.zero_bytes, s));
     PerCommDev pcd{};
@@ -550,10 +583,8 @@ static qm_status score_impl(qm_graph *g, const int32_t *labels, int32_t K, qm_me
             CK(cudaMemsetAsync(dp[k], 0, (size_t)K * 8, s));
         }
     }
-    const int L = sh.algo ? launch_score2(g->d, dl, K, w, sh, pc ? &pcd : nullptr, num_sms_of(g->device), s,
-                                          trace_begin())
-                          : launch_score(g->d, dl, K, w, sh, pc ? &pcd : nullptr, num_sms_of(g->device), s,
-                                         trace_begin());
+    const int L = sh.algo ? launch_score2(g->d, dl, K, w, sh, pc ? &pcd : nullptr, num_sms_of(g->device), s, tr)
+                          : launch_score(g->d, dl, K, w, sh, pc ? &pcd : nullptr, num_sms_of(g->device), s, tr);
     if (L < 0) return cuda_fail(cudaGetLastError(), "launch_score");
     g_launches += L;
     CK(cudaMemcpyAsync(pin.ptr(), w.status, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -756,6 +787,22 @@ static qm_status evaluate_batched(qm_graph *g, const int32_t *labels, int32_t P,
         st = stage_labels(g->device, truth, (size_t)g->n, where, s, tru, &dt);
         if (st != QM_OK) return st;
     }
+    Lease plab;
+    if (g->inv) {  // renumbered graph: candidates and truth follow its node order
+        const size_t rows = (size_t)P + ((flags & 2) ? 1 : 0);
+        plab.b = g_pool.acquire(rows * (size_t)g->n * 4, g->device, false);
+        if (!plab.b) return fail(QM_ENOMEM, "label permutation allocation failed");
+        int32_t *pl = (int32_t *)plab.ptr();
+        if (launch_permute_labels(dl, g->inv, g->n, P, pl, num_sms_of(g->device), s) < 0)
+            return cuda_fail(cudaGetLastError(), "label permutation");
+        dl = pl;
+        if (flags & 2) {
+            if (launch_permute_labels(dt, g->inv, g->n, 1, pl + (size_t)P * g->n, num_sms_of(g->device), s) < 0)
+                return cuda_fail(cudaGetLastError(), "label permutation");
+            dt = pl + (size_t)P * g->n;
+        }
+        g_launches += (flags & 2) ? 2 : 1;
+    }
     d.n_max = g->n;
     d.k_max = kmax;
     d.kt_max = (flags & 2) ? kt : 1;
@@ -861,6 +908,24 @@ qm_status qm_score_graphs_batched(const qm_graph *const *graphs, const int32_t *
         }
     } else {
         for (int i = 0; i < count; ++i) dl[i] = labels[i];
+    }
+    size_t perm_total = 0;
+    for (int i = 0; i < count; ++i)
+        if (graphs[i]->inv) perm_total += al256((size_t)graphs[i]->n * 4);
+    Lease plab;
+    if (perm_total) {  // renumbered graphs: gather their labels into the graph's node order
+        plab.b = g_pool.acquire(perm_total, dev, false);
+        if (!plab.b) return fail(QM_ENOMEM, "label permutation allocation failed");
+        size_t off = 0;
+        for (int i = 0; i < count; ++i) {
+            if (!graphs[i]->inv) continue;
+            int32_t *pl = (int32_t *)(plab.ptr() + off);
+            if (launch_permute_labels(dl[i], graphs[i]->inv, graphs[i]->n, 1, pl, num_sms_of(dev), s) < 0)
+                return cuda_fail(cudaGetLastError(), "label permutation");
+            g_launches += 1;
+            dl[i] = pl;
+            off += al256((size_t)graphs[i]->n * 4);
+        }
     }
     d.items.resize(count);
     for (int i = 0; i < count; ++i) {

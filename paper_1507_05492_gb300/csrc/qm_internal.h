@@ -21,6 +21,7 @@ struct GraphDev {
     long long n;
     long long n_arcs;
     long long max_degree;
+    const int *inv = nullptr;  // loaded with QM_REORDER: new node id -> caller's node id
 };
 
 // Launch shape of the community-major kernels.
@@ -76,6 +77,7 @@ struct ScoreWs {
     int *nbr;                   // two-phase only: [n_arcs] neighbour labels in community order
     unsigned long long *rec;    // two-phase only: [K][6] per-community records
     size_t zero_bytes;          // bytes from `status` that must start at zero
+    size_t bytes;               // total bytes carved (the *_ws_bytes size)
 };
 
 struct CompareWs {
@@ -93,6 +95,7 @@ struct CompareWs {
     int *members;               // [n]
     int *scan_tmp;
     size_t zero_bytes;
+    size_t bytes;  // total bytes carved (compare_ws_bytes)
 };
 
 size_t score_ws_bytes(long long n, int K);
@@ -121,6 +124,17 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
 int launch_compare(const int *truth, const int *found, long long n, int ka, int kb,
                    const CompareWs &ws, const Shape &sh, int num_sms, cudaStream_t s, TraceFn tr);
 int count_blocks_per_sm(const Shape &sh);
+
+// Generic exclusive scan (qm_kernels.cu) and the graph reorder (qm_reorder.cu).
+size_t scan_tmp_elems(long long n);
+int scan_offsets(const int *in, int n, int *out, int *tmp, int *counters, const int *status, cudaStream_t s);
+int launch_permute_labels(const int *labels, const int *inv, long long n, int P, int *out, int num_sms,
+                          cudaStream_t s);
+// Builds the renumbered CSR (row_ptr, col: new device allocations) and inv
+// (new id -> old id) of g from `rounds` label-propagation rounds.  Returns 0,
+// or minus a CUDA error code (nothing allocated then).
+int reorder_graph(const GraphDev &g, int rounds, int num_sms, cudaStream_t s, long long **row_ptr_out, int **col_out,
+                  int **inv_out, int *launches);
 
 // Largest dynamic shared memory a community-major block may request.
 constexpr int MAX_DYN_SMEM = 220 * 1024;

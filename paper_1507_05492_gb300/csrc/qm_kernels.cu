@@ -90,20 +90,7 @@ CountPlan plan_count(int T, int S)
 
 static int scan_tiles(int K) { return (K + SCAN_TILE - 1) / SCAN_TILE; }
 
-size_t score_ws_bytes(long long n, int K)
-{
-    size_t b = 0;
-    b += 256;                                   // status + counters
-    b += align_up(32 * 8, 256);                 // gacc
-    b += align_up(sizeof(qm_quality), 256);     // result
-    b += align_up((size_t)K * 4, 256);          // size (zeroed)
-    b += align_up((size_t)(K + 1) * 4, 256);    // start
-    b += align_up((size_t)K * 16, 256);         // recip
-    b += align_up((size_t)K * 4, 256) * 3;      // cursor, big_list, ovf_list
-    b += align_up((size_t)n * 4, 256);          // members
-    b += align_up((size_t)(scan_tiles(K) + 1) * 4, 256);
-    return b;
-}
+size_t score_ws_bytes(long long n, int K) { return carve_score_ws(reinterpret_cast<void *>(4096), n, K).bytes; }
 
 ScoreWs carve_score_ws(void *base, long long n, int K)
 {
@@ -117,8 +104,6 @@ ScoreWs carve_score_ws(void *base, long long n, int K)
     w.result = (qm_quality *)p;
     p += align_up(sizeof(qm_quality), 256);
     w.size = (int *)p;
-    p += align_up((size_t)K * 4, 256);
-    w.inter = (int *)p;
     p += align_up((size_t)K * 4, 256);
     w.zero_bytes = (size_t)(p - (char *)base);
     w.start = (int *)p;
@@ -134,28 +119,19 @@ ScoreWs carve_score_ws(void *base, long long n, int K)
     w.members = (int *)p;
     p += align_up((size_t)n * 4, 256);
     w.scan_tmp = (int *)p;
+    p += align_up((size_t)(scan_tiles(K) + 1) * 4, 256);
+    w.bytes = (size_t)(p - (char *)base);
     return w;
 }
 
 size_t compare_ws_bytes(long long n, int ka, int kb)
 {
-    size_t b = 0;
-    b += 256;
-    b += align_up(32 * 8, 256);
-    b += align_up(sizeof(qm_compare), 256);
-    b += align_up((size_t)ka * 4, 256) * 2;     // size_a, rowmax_n
-    b += align_up((size_t)kb * 4, 256);         // size_b
-    b += align_up((size_t)ka * 8, 256);         // rowmax_r
-    b += align_up((size_t)(kb + 1) * 4, 256);   // start
-    b += align_up((size_t)kb * 4, 256) * 2;     // cursor, big_list
-    b += align_up((size_t)n * 4, 256);          // members
-    b += align_up((size_t)(scan_tiles(kb) + 1) * 4, 256);
-    return b;
+    return carve_compare_ws(reinterpret_cast<void *>(4096), n, ka, kb).bytes;
 }
 
 CompareWs carve_compare_ws(void *base, long long n, int ka, int kb)
 {
-    CompareWs w;
+    CompareWs w{};
     char *p = (char *)base;
     w.status = (int *)p;
     w.counters = (int *)(p + 16);
@@ -182,6 +158,8 @@ CompareWs carve_compare_ws(void *base, long long n, int ka, int kb)
     w.members = (int *)p;
     p += align_up((size_t)n * 4, 256);
     w.scan_tmp = (int *)p;
+    p += align_up((size_t)(scan_tiles(kb) + 1) * 4, 256);
+    w.bytes = (size_t)(p - (char *)base);
     return w;
 }
 
@@ -986,6 +964,15 @@ static int launch_scan(const int *size, int K, int *start, int *cursor, Rcp *rec
     return 3;
 }
 
+// Exclusive prefix of in[0..n) into out[0..n] (out may alias in); tmp holds
+// scan_tmp_elems(n) ints.  Returns the number of launches, or -1.
+size_t scan_tmp_elems(long long n) { return (size_t)scan_tiles((int)n) + 1; }
+
+int scan_offsets(const int *in, int n, int *out, int *tmp, int *counters, const int *status, cudaStream_t s)
+{
+    return launch_scan(in, n, out, nullptr, nullptr, INT_MAX, nullptr, counters, tmp, status, s, nullptr);
+}
+
 int launch_score(const GraphDev &g, const int *labels, int K, const ScoreWs &ws, const Shape &sh,
                  const PerCommDev *pc, int num_sms, cudaStream_t s, TraceFn tr)
 {
@@ -1046,20 +1033,7 @@ int launch_score(const GraphDev &g, const int *labels, int K, const ScoreWs &ws,
 
 size_t score2_ws_bytes(long long n, long long n_arcs, int K)
 {
-    const int tiles = scan_tiles((int)std::max<long long>(n, K));
-    size_t b = 0;
-    b += 256 + align_up(32 * 8, 256) + align_up(sizeof(qm_quality), 256);
-    b += align_up((size_t)K * 4, 256) * 2;          // size, inter (zeroed)
-    b += align_up((size_t)(K + 1) * 4, 256);        // start
-    b += align_up((size_t)K * 16, 256);             // recip
-    b += align_up((size_t)K * 4, 256) * 2;          // cursor, big_list
-    b += align_up((size_t)n * 4, 256);              // members
-    b += align_up((size_t)(n + 1) * 4, 256);        // member degrees -> arc offsets
-    b += align_up((size_t)n_arcs * 4, 256) + 256;   // packed neighbour labels (+ slack for 16-byte copies)
-    b += align_up((size_t)K * 8 * REC_WORDS, 256);  // per-community records
-    b += align_up((size_t)K * sizeof(RunHdr), 256) * 3;  // run headers: block, warp and general lists
-    b += align_up((size_t)(tiles + 1) * 4, 256);    // scan tiles
-    return b;
+    return carve_score2_ws(reinterpret_cast<void *>(4096), n, n_arcs, K).bytes;
 }
 
 ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K)
@@ -1103,7 +1077,8 @@ ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K)
     w.hdr_long = (RunHdr *)p;
     p += align_up((size_t)K * sizeof(RunHdr), 256);
     w.scan_tmp = (int *)p;
-    (void)tiles;
+    p += align_up((size_t)(tiles + 1) * 4, 256);
+    w.bytes = (size_t)(p - (char *)base);
     return w;
 }
 

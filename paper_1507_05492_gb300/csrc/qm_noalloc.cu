@@ -82,11 +82,13 @@ extern "C" qm_status qm_score_partition_noalloc(const qm_graph *g, const int32_t
     if (!g || !labels || !out) return noalloc_fail(QM_EINVAL, "null argument");
     if (K < 1) return noalloc_fail(QM_EINVAL, "K must be >= 1");
     if (qm::graph_device_view(g, &gd, &dev) != QM_OK) return noalloc_fail(QM_EINVAL, "bad graph handle");
-    const size_t need = qm::score_ws_bytes(gd.n, K);
+    const size_t ws_bytes = qm::score_ws_bytes(gd.n, K);
+    // a renumbered graph (QM_REORDER) also needs room for the gathered labels
+    const size_t need = ws_bytes + (gd.inv ? ((size_t)gd.n * 4 + 255) / 256 * 256 : 0);
     if (need > kScratchBytes)
         return noalloc_fail(QM_EOVERFLOW, "graph and label count need " + std::to_string(need) +
                                               " bytes of scratch; the allocation-free call has " +
-                                              std::to_string(kScratchBytes) + " (about 4 n + 20 K bytes fit)");
+                                              std::to_string(kScratchBytes) + " (about 4 n + 36 K bytes fit, 8 n + 36 K for a graph loaded with QM_REORDER)");
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != dev) cudaSetDevice(dev);
@@ -112,7 +114,16 @@ extern "C" qm_status qm_score_partition_noalloc(const qm_graph *g, const int32_t
     // rest of the array is fully written before it is read
     cudaError_t e = cudaMemsetAsync(s.scratch, 0, w.zero_bytes, cs);
     if (e != cudaSuccess) return noalloc_fail(QM_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
-    if (qm::launch_score(gd, labels, K, w, s.shape, nullptr, s.num_sms, cs, nullptr) < 0) {
+    const int32_t *dl = labels;
+    if (gd.inv) {
+        int32_t *pl = (int32_t *)((char *)s.scratch + ws_bytes);
+        if (qm::launch_permute_labels(labels, gd.inv, gd.n, 1, pl, s.num_sms, cs) < 0) {
+            e = cudaGetLastError();
+            return noalloc_fail(QM_ECUDA, std::string("label permutation: ") + cudaGetErrorString(e));
+        }
+        dl = pl;
+    }
+    if (qm::launch_score(gd, dl, K, w, s.shape, nullptr, s.num_sms, cs, nullptr) < 0) {
         e = cudaGetLastError();
         return noalloc_fail(QM_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
     }

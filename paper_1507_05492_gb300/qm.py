@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libqm.so")
 QM_OK, QM_EINVAL, QM_ENOMEM, QM_ECUDA, QM_ETIMEOUT, QM_EOVERFLOW, QM_EBUSY = range(7)
 QM_HOST, QM_DEVICE = 0, 1
 QM_VALIDATE = 1
+QM_REORDER = 2
 QM_SHARED_TRUTH = 1
 
 
@@ -165,7 +166,10 @@ def _struct_dict(s) -> dict:
 class Graph:
     """A symmetric CSR graph resident on the current CUDA device."""
 
-    def __init__(self, row_ptr, col, validate: bool = False, stream=None):
+    def __init__(self, row_ptr, col, validate: bool = False, reorder: bool = False, stream=None):
+        """reorder=True stores the graph renumbered for locality (QM_REORDER):
+        calls still take labels in the caller's node order and give the same
+        results."""
         if isinstance(row_ptr, torch.Tensor):
             rp = row_ptr.contiguous().to(torch.int64)
             cl = col.contiguous().to(torch.int32)
@@ -183,13 +187,15 @@ class Graph:
             where = QM_HOST
             n, arcs = len(rp) - 1, len(cl)
         h = ctypes.c_void_p()
-        _check(lib().qm_load_graph(prp, pcl, n, arcs, where, QM_VALIDATE if validate else 0,
-                                   _stream_ptr(stream), ctypes.byref(h)), "qm_load_graph")
+        flags = (QM_VALIDATE if validate else 0) | (QM_REORDER if reorder else 0)
+        _check(lib().qm_load_graph(prp, pcl, n, arcs, where, flags, _stream_ptr(stream), ctypes.byref(h)),
+               "qm_load_graph")
         del keep
         self.handle = h
         self.n = n
         self.n_arcs = arcs
         self.n_edges = arcs // 2
+        self.reordered = reorder
 
     def info(self) -> dict:
         vals = [ctypes.c_int64() for _ in range(3)]
