@@ -91,19 +91,25 @@ def recorded_traffic(kernel: str, workload: str):
     return None
 
 
-def algorithmic_bytes(kernel: str, n: int, E: int, K: int) -> float:
+def algorithmic_bytes(kernel: str, n: int, E: int, K: int, q: dict) -> float:
     """Bytes a launch of `kernel` must move at minimum (each input read once,
-    each output written once; 4-byte ids and labels, 8-byte row offsets)."""
+    each output written once; 4-byte ids and labels, 8-byte row offsets,
+    16-byte reciprocals).  cut = 2 x cut_edges_total is the number of packed
+    inter-community entries of the two-phase pipeline."""
+    cut = 2.0 * q["cut_edges_total"]
     table = {
         # one-kernel pass: adjacency 2|E| x 4 B, row offsets 8 B, labels + members 4 B each
         "k_score_cm": 8.0 * E + 12.0 * n,
-        # expand: adjacency read + neighbour-label write (2|E| x 4 B each), row offsets,
-        # labels, members, arc offsets
-        "k_expand": 16.0 * E + 20.0 * n,
-        # count: neighbour labels read once, member offsets + reciprocals + 48-byte record per community
-        "k_count": 8.0 * E + 60.0 * K,
+        # expand: adjacency, row offsets, labels, members and arc offsets read once;
+        # the packed inter-community labels written once
+        "k_expand": 8.0 * E + 20.0 * n + 4.0 * cut,
+        # count: the packed labels and one 16-byte reciprocal per entry read once,
+        # a 16-byte header read and a 48-byte record written per community
+        "k_count": 20.0 * cut + 64.0 * K,
         # counting sort with degrees: labels, row offsets read; members, degrees written
         "k_scatter_deg": 20.0 * n,
+        # label gather through the reorder permutation: labels, permutation read, result written
+        "k_permute_labels": 12.0 * n,
     }
     return table.get(kernel, 0.0)
 
@@ -252,6 +258,26 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ our arm
 
+def _timed_steps(qm, graph, labels, K, steps, stream, torch):
+    """steps scoring calls on resident inputs, CUDA events on the launching
+    stream; returns (ms, last result, per-step kernel traces, launches)."""
+    qm.trace_enable(True)
+    l0 = qm.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    traces = []
+    q = None
+    for _ in range(steps):
+        q = qm.score(graph, labels, K)
+        traces.append(qm.trace_read())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = qm.kernel_launches() - l0
+    qm.trace_enable(False)
+    return e0.elapsed_time(e1), q, traces, launches
+
+
 def bench_headline(args, world, rank, local):
     import torch
     from paper_1507_05492_gb300 import gen, qm
@@ -262,10 +288,14 @@ def bench_headline(args, world, rank, local):
     g = gen.lfr_graph(p, device=dev)
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
-    graph = qm.Graph(g.row_ptr, g.col)
+    t_load = time.perf_counter()
+    graph = qm.Graph(g.row_ptr, g.col, reorder=not args.no_reorder)
+    torch.cuda.synchronize()
+    t_load = time.perf_counter() - t_load
     n, E, K = g.n, g.n_edges, g.K
     max_deg = graph.info()["max_degree"]
     labels = g.labels
+    keep_csr = (g.row_ptr, g.col) if (not args.no_reorder and not args.no_extras and world == 1) else None
     del g
     torch.cuda.empty_cache()
     stream = torch.cuda.current_stream()
@@ -278,28 +308,16 @@ def bench_headline(args, world, rank, local):
 
     clocks = Clocks(local)
     clocks.start()
-    qm.trace_enable(True)
-    l0 = qm.kernel_launches()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(world)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    step_kernels = []
-    for _ in range(args.steps):
-        q = qm.score(graph, labels, K)
-        step_kernels.append(qm.trace_read())
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms, q, step_kernels, launches = _timed_steps(qm, graph, labels, K, args.steps, stream, torch)
     barrier(world)
-    launches = qm.kernel_launches() - l0
-    qm.trace_enable(False)
-    ms = e0.elapsed_time(e1)
     clk = clocks.stop()
     ms_max = max_over_ranks(ms, world)
     edges_all = sum_over_ranks(float(E) * args.steps, world)
     value = edges_all / (ms_max / 1e3)
 
     # end to end through the C ABI with host buffers
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     lab_h = labels.cpu().pin_memory()
     for _ in range(2):
         qm.score(graph, lab_h, K)
@@ -317,6 +335,23 @@ def bench_headline(args, world, rank, local):
     assert qe == q, "host-buffer path differs from the device path"
     e2e_value = edges_all / (e2e_ms / 1e3)
 
+    # the same workload on the graph as given (no reorder), for comparison
+    unordered = None
+    if keep_csr is not None:
+        g2 = qm.Graph(*keep_csr)
+        for _ in range(2):
+            qm.score(g2, labels, K)
+        ms2, q2, tr2, _ = _timed_steps(qm, g2, labels, K, max(1, args.steps // 2), stream, torch)
+        assert q2 == q, "reordered and unordered graphs disagree"
+        st2 = max(1, args.steps // 2)
+        unordered = {"value": E * st2 / (ms2 / 1e3), "unit": UNIT, "ms_per_step": ms2 / st2,
+                     "kernel_ms": {k: round(sum(t for nm, t in tr if nm == k) / st2, 3)
+                                   for k in sorted({nm for tr in tr2 for nm, _ in tr})
+                                   for tr in [sum(tr2, [])]}}
+        g2.close()
+        del keep_csr, g2
+        torch.cuda.empty_cache()
+
     peak, peak_kind = hbm_peak()
     kernel_shares = {}
     for tr in step_kernels:
@@ -326,7 +361,7 @@ def bench_headline(args, world, rank, local):
     # the dominant kernel: largest share of the step's kernel time (one launch per step)
     top = max(kernel_shares, key=kernel_shares.get)
     top_avg = kernel_shares[top] / args.steps
-    b_alg = algorithmic_bytes(top, n, E, K)
+    b_alg = algorithmic_bytes(top, n, E, K, q)
     achieved = b_alg / (top_avg / 1e3) / 1e9
     b_step = 8.0 * E + 12.0 * n
     res = dict(
@@ -343,11 +378,15 @@ def bench_headline(args, world, rank, local):
         config={"workload": f"{args.workload}: LFR-style, n={n}, |E|={E}, K={K}, max degree {max_deg}, "
                             f"mean degree 20 target, mu=0.3, communities 20-1000, planted partition",
                 "n_nodes": n, "n_edges": E, "n_communities": K, "seed": p.seed,
+                "graph_load": ("QM_REORDER: label-propagation renumbering at load, "
+                               f"{t_load:.2f} s incl. copy (not in the timed region)") if not args.no_reorder
+                              else f"as given, {t_load:.2f} s",
                 "l2": "inputs (CSR 8 GB + labels 0.4 GB) far larger than the 129 MB L2",
                 "generation_s": round(t_gen, 1)},
         kernel_share={k: round(v / total_k, 4) for k, v in sorted(kernel_shares.items(), key=lambda x: -x[1])},
         result={k: q[k] for k in ("modularity", "modularity_density", "mean_conductance",
                                   "n_community_pairs", "cut_edges_total")},
+        unordered=unordered,
     )
     graph.close()
     del labels, lab_h
@@ -439,7 +478,8 @@ def run_ours(args):
             "config": res["config"] | {"parallelism": f"replicas x{world}"},
             "roofline": res["roofline"], "cpu_baseline": cpu, "e2e": res["e2e"],
             "gpu_launches": res["launches"], "clocks": res["clocks"],
-            "kernel_share": res["kernel_share"], "result": res["result"], "extras": extras,
+            "kernel_share": res["kernel_share"], "result": res["result"],
+            "extras": extras | ({"graph_as_given": res["unordered"]} if res["unordered"] else {}),
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -455,9 +495,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="lfr100m")
-    ap.add_argument("--cpu-sample-nodes", type=int, default=2_000_000)
+    ap.add_argument("--cpu-sample-nodes", type=int, default=16_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-reorder", action="store_true",
+                    help="load the graph as given instead of with QM_REORDER")
     ap.add_argument("--batch", type=int, default=1024)
     ap.add_argument("--plain-sample", type=int, default=256)
     ap.add_argument("--serve-seconds", type=float, default=10.0)

@@ -729,34 +729,33 @@ __device__ __forceinline__ void count_run(const CountCtx &x, const RunHdr &h, co
         bool ok = true;
         for (unsigned r = 0; r < R && ok; ++r) {
             epoch = etab_next_epoch(tab, epoch, gtid, gsize);
-            for (unsigned e0 = gtid; e0 < m; e0 += 4u * gsize) {
-                int lv[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const unsigned e = e0 + k * gsize;
-                    lv[k] = -1;
-                    if (e < m) lv[k] = SMEM ? src[e] : __ldcs(&src[e]);
-                    if (lv[k] >= 0 && (!QM_CHK(lv[k], x.K, 6) || (R > 1 && tab_split((unsigned)lv[k], R) != r)))
-                        lv[k] = -1;
-                }
-                Rcp rj[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (lv[k] >= 0) rj[k] = ld_rcp(&x.recip[lv[k]]);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if (lv[k] < 0) continue;
-                    const int prev = tab.add((unsigned)lv[k], epoch);
-                    if (prev < 0) continue;  // overflow: this pass is discarded
-                    if (prev == 0) {  // first occurrence (the common case): q = 1
-                        u192_add_rcp(inner, rj[k]);
-                        cnt2 += 1ull;
-                        slots += 1ull;
-                    } else {
-                        const unsigned long long q = 2ull * (unsigned long long)prev + 1ull;
-                        u192_mac(inner, q, rj[k]);
-                        cnt2 += q;
-                    }
+            // one entry per thread per step (several table probes in flight per
+            // thread serialise worse than more warps do); the next entry's label
+            // and reciprocal are fetched before this entry's table update
+            auto fetch = [&](unsigned e, int &lv, Rcp &rj) {
+                lv = -1;
+                if (e < m) lv = SMEM ? src[e] : __ldcs(&src[e]);
+                if (lv >= 0 && (!QM_CHK(lv, x.K, 6) || (R > 1 && tab_split((unsigned)lv, R) != r))) lv = -1;
+                if (lv >= 0) rj = ld_rcp(&x.recip[lv]);
+            };
+            int lv_n;
+            Rcp rj_n;
+            fetch((unsigned)gtid, lv_n, rj_n);
+            for (unsigned e = gtid; e < m; e += gsize) {
+                const int lv = lv_n;
+                const Rcp rj = rj_n;
+                fetch(e + gsize, lv_n, rj_n);
+                if (lv < 0) continue;
+                const int prev = tab.add((unsigned)lv, epoch);
+                if (prev < 0) continue;  // overflow: this pass is discarded
+                if (prev == 0) {  // first occurrence (the common case): q = 1
+                    u192_add_rcp(inner, rj);
+                    cnt2 += 1ull;
+                    slots += 1ull;
+                } else {
+                    const unsigned long long q = 2ull * (unsigned long long)prev + 1ull;
+                    u192_mac(inner, q, rj);
+                    cnt2 += q;
                 }
             }
             group_sync(gsize);

@@ -583,15 +583,27 @@ static int grid_for(long long n, int threads, int num_sms, int per_sm)
 
 // Counting sort of the nodes by label (as k_scatter) that also records the
 // degree of the node placed at each member position (read in node order, so
-// the row-offset reads are coalesced).
+// the row-offset reads are coalesced).  The lanes of a warp that hold one label
+// take their places with a single atomic, in node order: on a graph whose nodes
+// are numbered cluster by cluster (QM_REORDER) consecutive member positions
+// are then mostly consecutive nodes, whose rows are adjacent (see k_expand).
 __global__ void k_scatter_deg(const int *__restrict__ labels, const long long *__restrict__ row_ptr, long long n,
                               int *cursor, int *members, int *degm, const int *status)
 {
     if (*status) return;
+    const int lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    for (long long i0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < n; i0 += stride) {
+        const long long i = i0 + lane;
+        const unsigned act = __ballot_sync(0xffffffffu, i < n);
+        if (i >= n) continue;
         const int l = __ldg(&labels[i]);
-        const int pos = atomicAdd(&cursor[l], 1);
+        const unsigned peers = __match_any_sync(act, l);
+        const int leader = __ffs(peers) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&cursor[l], __popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        const int pos = base + __popc(peers & ((1u << lane) - 1u));
         members[pos] = (int)i;
         degm[pos] = (int)(__ldg(&row_ptr[i + 1]) - __ldg(&row_ptr[i]));
     }
@@ -600,15 +612,60 @@ __global__ void k_scatter_deg(const int *__restrict__ labels, const long long *_
 // Phase A: for each member position p (community order) the labels of the
 // neighbours of members[p] are looked up.  A warp takes 32 consecutive member
 // positions; they hold one or more runs of members of one community each.  For
-// a run of community c the warp spreads the run's arcs over its lanes (a
-// search over the run's arc offsets), gathers the neighbour labels, and packs
-// those != c at the front of c's arc segment: a ballot gives each lane its
-// place and one atomic on inter[c] reserves the room.  inter[c] ends as the
-// number of cut arcs of c, |E_c^out| (Sec. II-B.3), and the packed run never
-// outgrows the segment, whose length is the volume of c.  No shared-memory
-// table is needed, so the kernel runs at full occupancy.
+// a run of community c the warp spreads the run's arcs over its lanes,
+// gathers the neighbour labels, and packs those != c at the front of c's arc
+// segment: a ballot gives each lane its place and one atomic on inter[c]
+// reserves the room.  inter[c] ends as the number of cut arcs of c,
+// |E_c^out| (Sec. II-B.3), and the packed run never outgrows the segment,
+// whose length is the volume of c.  No shared-memory table is needed, so the
+// kernel runs at full occupancy.
+//
+// Locating the CSR entry of the e-th arc of a run: when the 32 members form a
+// few segments of consecutive node ids (the common case on a graph loaded
+// with QM_REORDER), a segment's rows are adjacent in the CSR and its arcs are
+// one contiguous range; otherwise a search over the members' arc offsets
+// finds the member of each arc.
 constexpr int EXPAND_THREADS = 256;
 constexpr int EXPAND_UNROLL = 8;
+constexpr int EXPAND_MAX_SEGS = 6;
+
+// Gathers the labels of arcs [e_lo, e_hi) of a run of community c (loc(e) is
+// the CSR index of arc e) and packs those != c into c's segment at cbase.
+template <class LOC>
+__device__ __forceinline__ void expand_range(unsigned e_lo, unsigned e_hi, int c, unsigned cbase, LOC loc,
+                                             const int *__restrict__ col, const int *__restrict__ labels,
+                                             int *inter, int *__restrict__ nbr, unsigned long long keep, int lane)
+{
+    const unsigned lt = (1u << lane) - 1u;
+    for (unsigned e0 = e_lo; e0 < e_hi; e0 += 32u * EXPAND_UNROLL) {
+        int lab[EXPAND_UNROLL];
+#pragma unroll
+        for (int k = 0; k < EXPAND_UNROLL; ++k) {
+            const unsigned e = e0 + lane + 32u * k;
+            lab[k] = e < e_hi ? __ldcs(&col[loc(e)]) : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < EXPAND_UNROLL; ++k)
+            if (lab[k] >= 0) lab[k] = ld_hint(&labels[lab[k]], keep);
+        unsigned msk[EXPAND_UNROLL];
+        int tot = 0;
+#pragma unroll
+        for (int k = 0; k < EXPAND_UNROLL; ++k) {
+            msk[k] = __ballot_sync(0xffffffffu, lab[k] >= 0 && lab[k] != c);
+            tot += __popc(msk[k]);
+        }
+        if (tot == 0) continue;
+        int pos = 0;
+        if (lane == 0) pos = atomicAdd(&inter[c], tot);
+        unsigned at = cbase + (unsigned)__shfl_sync(0xffffffffu, pos, 0);
+#pragma unroll
+        for (int k = 0; k < EXPAND_UNROLL; ++k) {
+            if ((msk[k] >> lane) & 1u) __stcs(&nbr[at + __popc(msk[k] & lt)], lab[k]);
+            at += __popc(msk[k]);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__restrict__ row_ptr,
                                                            const int *__restrict__ col,
                                                            const int *__restrict__ labels,
@@ -622,7 +679,6 @@ __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__re
     __shared__ int cw_s[EXPAND_THREADS / 32][32];
     if (*status) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const unsigned lt = (1u << lane) - 1u;
     unsigned *offw = offs_s[w];
     long long *rsw = rs_s[w];
     int *cw = cw_s[w];
@@ -631,55 +687,57 @@ __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__re
     for (long long p0 = ((long long)blockIdx.x * (blockDim.x >> 5) + w) * 32; p0 < n; p0 += nwarps * 32) {
         const int nm = (int)min(32LL, n - p0);
         const unsigned base = __ldg(&aoff[p0]);
+        int u = -2;
         if (lane < nm) {
-            const int u = __ldcs(&members[p0 + lane]);
+            u = __ldcs(&members[p0 + lane]);
             offw[lane] = __ldg(&aoff[p0 + lane]) - base;
             rsw[lane] = __ldg(&row_ptr[u]);
             cw[lane] = ld_hint(&labels[u], keep);
         }
         if (lane == 0) offw[nm] = __ldg(&aoff[p0 + nm]) - base;
         __syncwarp();
-        unsigned runs = __ballot_sync(0xffffffffu, lane < nm && (lane == 0 || cw[lane] != cw[lane - 1]));
-        while (runs) {
-            const int m_lo = __ffs(runs) - 1;
-            runs &= runs - 1;
-            const int m_hi = runs ? __ffs(runs) - 1 : nm;
-            const unsigned e_lo = offw[m_lo], e_hi = offw[m_hi];
-            if (e_lo == e_hi) continue;
-            const int c = cw[m_lo];
-            unsigned cbase = 0;
-            if (lane == 0) cbase = __ldg(&aoff[__ldg(&start[c])]);
-            cbase = __shfl_sync(0xffffffffu, cbase, 0);
-            for (unsigned e0 = e_lo; e0 < e_hi; e0 += 32u * EXPAND_UNROLL) {
-                int lab[EXPAND_UNROLL];
-#pragma unroll
-                for (int k = 0; k < EXPAND_UNROLL; ++k) {
-                    const unsigned e = e0 + lane + 32u * k;
-                    lab[k] = -1;
-                    if (e < e_hi) {
+        const int u_prev = __shfl_up_sync(0xffffffffu, u, 1);
+        const bool valid = lane < nm;
+        const bool newrun = valid && (lane == 0 || cw[lane] != cw[lane - 1]);
+        unsigned runs = __ballot_sync(0xffffffffu, newrun);
+        const unsigned segs = __ballot_sync(0xffffffffu, newrun || (valid && u != u_prev + 1));
+        int cur_c = -1;
+        unsigned cbase = 0;
+        if (__popc(segs) <= EXPAND_MAX_SEGS) {
+            unsigned rem = segs;
+            while (rem) {
+                const int lo = __ffs(rem) - 1;
+                rem &= rem - 1;
+                const int hi = rem ? __ffs(rem) - 1 : nm;
+                const unsigned e_lo = offw[lo], e_hi = offw[hi];
+                if (e_lo == e_hi) continue;
+                const int c = cw[lo];
+                if (c != cur_c) {
+                    cur_c = c;
+                    if (lane == 0) cbase = __ldg(&aoff[__ldg(&start[c])]);
+                    cbase = __shfl_sync(0xffffffffu, cbase, 0);
+                }
+                const long long cs = rsw[lo] - (long long)e_lo;  // CSR index of arc e is cs + e
+                expand_range(e_lo, e_hi, c, cbase, [cs](unsigned e) { return cs + (long long)e; }, col, labels,
+                             inter, nbr, keep, lane);
+            }
+        } else {
+            while (runs) {
+                const int m_lo = __ffs(runs) - 1;
+                runs &= runs - 1;
+                const int m_hi = runs ? __ffs(runs) - 1 : nm;
+                const unsigned e_lo = offw[m_lo], e_hi = offw[m_hi];
+                if (e_lo == e_hi) continue;
+                const int c = cw[m_lo];
+                if (lane == 0) cbase = __ldg(&aoff[__ldg(&start[c])]);
+                cbase = __shfl_sync(0xffffffffu, cbase, 0);
+                expand_range(
+                    e_lo, e_hi, c, cbase,
+                    [=](unsigned e) {
                         const int o = m_lo + upper_bound_smem(offw + m_lo, m_hi - m_lo, e) - 1;
-                        lab[k] = __ldcs(&col[rsw[o] + (e - offw[o])]);
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < EXPAND_UNROLL; ++k)
-                    if (lab[k] >= 0) lab[k] = ld_hint(&labels[lab[k]], keep);
-                unsigned msk[EXPAND_UNROLL];
-                int tot = 0;
-#pragma unroll
-                for (int k = 0; k < EXPAND_UNROLL; ++k) {
-                    msk[k] = __ballot_sync(0xffffffffu, lab[k] >= 0 && lab[k] != c);
-                    tot += __popc(msk[k]);
-                }
-                if (tot == 0) continue;
-                int pos = 0;
-                if (lane == 0) pos = atomicAdd(&inter[c], tot);
-                unsigned at = cbase + (unsigned)__shfl_sync(0xffffffffu, pos, 0);
-#pragma unroll
-                for (int k = 0; k < EXPAND_UNROLL; ++k) {
-                    if ((msk[k] >> lane) & 1u) __stcs(&nbr[at + __popc(msk[k] & lt)], lab[k]);
-                    at += __popc(msk[k]);
-                }
+                        return rsw[o] + (long long)(e - offw[o]);
+                    },
+                    col, labels, inter, nbr, keep, lane);
             }
         }
         __syncwarp();
