@@ -19,7 +19,7 @@
  *   Sec. II-B.2  Eq. (9) modularity density Qds    -> oq_score
  *   Sec. II-B.3  six per-community measures        -> oq_score
  *
- * Readings where the paper is silent (each also listed in the design doc):
+ * Readings taken where the paper is silent:
  *   - log is the natural log (Eq. 1);
  *   - d_c = 0 for a one-node community (Eq. 9, 0/0);
  *   - label ids with no member are absent communities, skipped everywhere;

@@ -168,6 +168,15 @@ CompareWs carve_compare_ws(void *base, long long n, int ka, int kb)
 // |c| for every label id (and the ground-truth sizes when `b` is given).
 // Labels outside [0, K) set bit 0 of *status and are skipped.  When the ids fit,
 // each block counts in shared memory first and adds its non-zero bins once.
+// Community sizes of one or two labellings.  With few label ids the counts
+// are privatised in shared memory; otherwise the lanes of a warp that share a
+// label add their count with one global atomic.
+__device__ __forceinline__ void hist_add_warp(int *size, int l, unsigned act)
+{
+    const unsigned peers = __match_any_sync(act, l);
+    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&size[l], __popc(peers));
+}
+
 __global__ void k_hist(const int *__restrict__ a, int ka, int *size_a, const int *__restrict__ b,
                        int kb, int *size_b, long long n, int *status, int use_smem)
 {
@@ -177,17 +186,30 @@ __global__ void k_hist(const int *__restrict__ a, int ka, int *size_a, const int
         block_sync();
     }
     bool bad = false;
+    const int lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int la = __ldcs(&a[i]);
-        if ((unsigned)la >= (unsigned)ka) bad = true;
-        else if (use_smem) atomicAdd(&sh[la], 1);
-        else atomicAdd(&size_a[la], 1);
+    for (long long i0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < n; i0 += stride) {
+        const long long i = i0 + lane;
+        const bool in = i < n;
+        const int la = in ? __ldcs(&a[i]) : 0;
+        const bool oka = in && (unsigned)la < (unsigned)ka;
+        if (in && !oka) bad = true;
+        if (use_smem) {
+            if (oka) atomicAdd(&sh[la], 1);
+        } else {
+            const unsigned act = __ballot_sync(0xffffffffu, oka);
+            if (oka) hist_add_warp(size_a, la, act);
+        }
         if (b) {
-            const int lb = __ldcs(&b[i]);
-            if ((unsigned)lb >= (unsigned)kb) bad = true;
-            else if (use_smem) atomicAdd(&sh[ka + lb], 1);
-            else atomicAdd(&size_b[lb], 1);
+            const int lb = in ? __ldcs(&b[i]) : 0;
+            const bool okb = in && (unsigned)lb < (unsigned)kb;
+            if (in && !okb) bad = true;
+            if (use_smem) {
+                if (okb) atomicAdd(&sh[ka + lb], 1);
+            } else {
+                const unsigned act = __ballot_sync(0xffffffffu, okb);
+                if (okb) hist_add_warp(size_b, lb, act);
+            }
         }
     }
     if (bad) atomicOr(status, 1);
