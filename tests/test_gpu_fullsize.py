@@ -80,3 +80,21 @@ def test_hundred_million_nodes_sampled(qm, oracle_mod):
     ne = q["n_communities_nonempty"]
     assert close(q["mean_conductance"], float(pc["conductance"].sum()) / ne, rel=1e-11)
     assert close(q["mean_intra_edges"], float(pc["intra_edges"].sum()) / ne)
+
+
+def test_giant_runs_and_counts_beyond_2_25(qm, oracle_mod):
+    """A random 2-way and 3-way split of the 10M-node graph: every community
+    has ~5e7 cut arcs (runs far beyond 2^24 entries) and its few keys occur far
+    more than 2^25 times, which takes the 64-bit-count general path."""
+    from paper_1507_05492_gb300 import gen
+    g = gen.lfr_graph(gen.config_params("lfr10m"), device="cuda")
+    graph = qm.Graph(g.row_ptr, g.col)
+    rp, col = g.row_ptr.cpu().numpy(), g.col.cpu().numpy()
+    rng = np.random.default_rng(31)
+    for K in (2, 3):
+        lab = rng.integers(0, K, g.n).astype(np.int32)
+        o = oracle_mod.score(rp, col, lab, K)
+        for algo in (1, 0):
+            qm.set_tuning(graph, K, 512, 96 * 1024, 48, algo)
+            q = qm.score(graph, torch.from_numpy(lab).cuda(), K)
+            check_quality(q, o, f"random {K}-way split, algorithm {algo}")

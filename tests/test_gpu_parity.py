@@ -240,3 +240,23 @@ def test_graph_validation(qm):
     oob[5] = 10_000
     with pytest.raises(qm.QmError):
         qm.Graph(*to_dev(rp, oob))  # ids out of range are always rejected
+
+
+def test_epoch_wraparound_in_block_tables(qm, oracle_mod):
+    """With a small launch shape almost every community goes to a block, and
+    each block counts hundreds of communities, so its table epochs wrap (and
+    the table is wiped) several times; the results must not change."""
+    rp, col = random_graph(400_000, 8_000_000, seed=41)
+    rng = np.random.default_rng(41)
+    K = 160_000  # ~2.5 nodes and ~100 cut arcs per community
+    lab = rng.integers(0, K, 400_000).astype(np.int32)
+    graph = qm.Graph(*to_dev(rp, col))
+    o = oracle_mod.score(rp, col, lab, K)
+    ref = None
+    for threads, smem in ((512, 20 * 1024), (128, 16 * 1024), (512, 96 * 1024)):
+        qm.set_tuning(graph, K, threads, smem, 48, 1)
+        q = qm.score(graph, torch.from_numpy(lab).cuda(), K)
+        check_quality(q, o, f"shape {threads}/{smem}")
+        if ref is None:
+            ref = q
+        assert q == ref
