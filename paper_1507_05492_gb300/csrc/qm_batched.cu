@@ -277,6 +277,7 @@ __global__ void __launch_bounds__(1024) k_batched(BatchKArgs a)
         if (do_cmp) {
             CompareCtx x;
             x.truth = I.truth;
+            x.tl = nullptr;
             x.members = members;
             x.start = start;
             x.size_a = size_a;

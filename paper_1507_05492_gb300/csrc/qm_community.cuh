@@ -42,7 +42,8 @@ struct ScoreCtx {
 
 struct CompareCtx {
     const int *truth;        // labels of C (ground truth)
-    const int *members;      // nodes grouped by found label
+    const int *tl;           // truth label of each member position, or null: truth[members[i]]
+    const int *members;      // nodes grouped by found label (used when tl is null)
     const int *start;        // int[k_found + 1]
     const int *size_a;       // |c| for c in C
     unsigned *rowmax_n;      // per truth community: max_c' |c n c'|
@@ -435,7 +436,7 @@ __device__ __forceinline__ void compare_community(const CompareCtx &x, int b, co
         bool ok = true;
         for (unsigned r = 0; r < R; ++r) {
             for (int i = mb + gtid; i < me; i += gsize) {
-                const int a = __ldg(&x.truth[__ldcg(&x.members[i])]);
+                const int a = x.tl ? __ldcg(&x.tl[i]) : __ldg(&x.truth[__ldcg(&x.members[i])]);
                 if (R == 1 || tab_split((unsigned)a, R) == r) tab_insert(tab, (unsigned)a);
             }
             group_sync(gsize);
@@ -486,6 +487,77 @@ __device__ __forceinline__ void compare_community(const CompareCtx &x, int b, co
         }
         return;
     }
+}
+
+// One contingency cell |c_a n c'_b| = n (Eqs. 1-4), written by the counting
+// pass of the comparison and turned into terms by a parallel pass.
+struct __align__(16) Cell {
+    int a, b;
+    unsigned n, pad;
+};
+
+// Counts the truth labels of found community b's members (x.tl, in member
+// order) and appends one Cell per distinct truth label to cells[*ncells ..].
+// Only the integer column maximum (NVD, Eq. 4) and the cell count are kept
+// here; every term that needs the cell sizes is formed later, in parallel.
+// The hash classes are chosen up front with room to spare (distinct labels
+// are at most min(|b|, ka)), because cells of a finished class are already
+// out; a class that still overflows is reported, never silently dropped.
+__device__ __forceinline__ void compare_cells_community(const CompareCtx &x, int b, const SmemTable &tab,
+                                                        CompareAcc *acc, int gtid, int gsize,
+                                                        unsigned long long *red, Cell *cells, int *ncells)
+{
+    const int mb = __ldcg(&x.start[b]), me = __ldcg(&x.start[b + 1]);
+    const long long nb = me - mb;
+    const long long distinct = min(nb, (long long)x.ka);
+    unsigned R = 1;
+    if (distinct > tab.max_used) R = (unsigned)((2 * distinct + tab.max_used - 1) / tab.max_used);
+    if (R > R_MAX) {
+        if (gtid == 0) atomicOr(x.err, 2);
+        return;
+    }
+    unsigned colmax = 0;
+    unsigned long long ncell = 0;
+    for (unsigned r = 0; r < R; ++r) {
+        for (int i = mb + gtid; i < me; i += gsize) {
+            const int a = x.tl ? __ldcg(&x.tl[i]) : __ldg(&x.truth[__ldcg(&x.members[i])]);
+            if (R == 1 || tab_split((unsigned)a, R) == r) tab_insert(tab, (unsigned)a);
+        }
+        group_sync(gsize);
+        if (*(volatile int *)tab.overflow) {
+            if (gtid == 0) atomicOr(x.err, 2);
+            return;
+        }
+        const int nu = min(*tab.n_used, tab.max_used);
+        int base = 0;
+        if (gtid == 0 && nu > 0) base = atomicAdd(ncells, nu);
+        if (gsize == 32) {
+            base = __shfl_sync(0xffffffffu, base, 0);
+        } else {
+            if (gtid == 0) red[255] = (unsigned long long)base;
+            group_sync(gsize);
+            base = (int)red[255];
+        }
+        for (int i = gtid; i < nu; i += gsize) {
+            const int h = tab.used[i];
+            if (!QM_CHK(h, tab.cap, 9)) continue;
+            const unsigned long long sv = tab.slot[h];
+            const unsigned n = (unsigned)(sv & 0xFFFFFFFFull);
+            cells[base + i] = Cell{(int)(sv >> 32) - 1, b, n, 0u};
+            colmax = max(colmax, n);
+            tab.slot[h] = 0ull;
+        }
+        ncell += (unsigned long long)nu;
+        group_sync(gsize);
+        if (gtid == 0) *tab.n_used = 0;
+        group_sync(gsize);
+    }
+    colmax = (unsigned)group_max_u32(colmax, gsize, red);
+    if (gtid == 0) {
+        acc->nvd += colmax;
+        acc->cells += ncell;
+    }
+    if (gsize != 32) group_sync(gsize);
 }
 
 // ---------------------------------------------------------------- two-phase scoring

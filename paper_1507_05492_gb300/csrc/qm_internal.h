@@ -8,6 +8,7 @@
 #include "../../include/qm.h"
 
 namespace qmk {
+struct Cell;    // one contingency cell (qm_community.cuh)
 struct Rcp;     // 128-bit reciprocal of a community size (qm_device.cuh)
 struct RunHdr;  // header of one community's packed run (qm_community.cuh)
 }
@@ -93,6 +94,7 @@ struct CompareWs {
     int *cursor;                // [kb]
     int *big_list;              // [kb]
     int *members;               // [n]
+    qmk::Cell *cells;  // contingency cells of the counting pass ([n])
     int *scan_tmp;
     size_t zero_bytes;
     size_t bytes;  // total bytes carved (compare_ws_bytes)

@@ -21,7 +21,7 @@ namespace qm {
 using namespace qmk;
 
 enum { C_BIG_COUNT = 0, C_BIG_NEXT = 1, C_SMALL_NEXT = 2, C_OVF_COUNT = 3, C_OVF_NEXT = 4, C_SMALL_COUNT = 5,
-       C_LONG_COUNT = 6 };
+       C_LONG_COUNT = 6, C_NCELLS = 7 };
 
 constexpr int SCAN_TILE = 4096;   // elements per block in the multi-block scan
 constexpr int SCAN_SINGLE_MAX = 1 << 16;
@@ -157,6 +157,8 @@ CompareWs carve_compare_ws(void *base, long long n, int ka, int kb)
     p += align_up((size_t)kb * 4, 256);
     w.members = (int *)p;
     p += align_up((size_t)n * 4, 256);
+    w.cells = (Cell *)p;  // at most one new cell per node
+    p += align_up((size_t)n * sizeof(Cell), 256);
     w.scan_tmp = (int *)p;
     p += align_up((size_t)(scan_tiles(kb) + 1) * 4, 256);
     w.bytes = (size_t)(p - (char *)base);
@@ -293,15 +295,18 @@ __global__ void k_scan_apply(const int *size, int K, const int *tile_off, int *s
 
 // ------------------------------------------------------------------ scatter
 
-__global__ void k_scatter(const int *__restrict__ labels, long long n, int *cursor, int *members,
-                          const int *status)
+// Counting sort of the nodes by label: members[pos] receives the node id, or
+// vals[node] when vals is given (the comparison places each node's truth
+// label straight into its detected community's run, read in node order).
+__global__ void k_scatter(const int *__restrict__ labels, const int *__restrict__ vals, long long n, int *cursor,
+                          int *members, const int *status)
 {
     if (*status) return;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const int l = __ldg(&labels[i]);
         const int pos = atomicAdd(&cursor[l], 1);
-        members[pos] = (int)i;
+        members[pos] = vals ? __ldcs(&vals[i]) : (int)i;
     }
 }
 
@@ -425,6 +430,7 @@ struct CompareKArgs {
     CompareCtx x;
     const int *big_list;
     int *counters;
+    Cell *cells;
     unsigned long long *gacc;
     const int *status;
     SmemPlan plan;
@@ -494,7 +500,7 @@ __global__ void __launch_bounds__(1024) k_compare_cm(CompareKArgs a)
         const int b = s_item;
         block_sync();
         if (b < 0) break;
-        compare_community(a.x, b, tb, &cacc[0], threadIdx.x, T, red);
+        compare_cells_community(a.x, b, tb, &cacc[0], threadIdx.x, T, red, a.cells, &a.counters[C_NCELLS]);
     }
     const SmemTable tw{slot + wid * p.cap_w, used + wid * p.max_used_w, &ctl[2 + 2 * wid],
                        &ctl[3 + 2 * wid], p.cap_w, p.max_used_w};
@@ -510,7 +516,8 @@ __global__ void __launch_bounds__(1024) k_compare_cm(CompareKArgs a)
         while (mask) {
             const int j = __ffs(mask) - 1;
             mask &= mask - 1;
-            compare_community(a.x, base + j, tw, &cacc[wid], lane, 32, red);
+            compare_cells_community(a.x, base + j, tw, &cacc[wid], lane, 32, red, a.cells,
+                                    &a.counters[C_NCELLS]);
         }
     }
     block_sync();
@@ -529,6 +536,47 @@ __global__ void k_compare_rows(CompareCtx x, unsigned long long *g, const int *s
     compare_acc_zero(acc);
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < x.ka; a += gridDim.x * blockDim.x)
         compare_row(x, a, acc);
+    flush_compare(acc, g, red);
+}
+
+// Terms of every contingency cell (Eqs. 1-4), in parallel over the cell list:
+// the pair count, the VI and NMI-numerator terms, and the row maxima of the
+// F-measure and NVD (Eqs. 3-4) through atomicMax per truth community.
+__global__ void k_compare_cells(CompareCtx x, const Cell *cells, const int *counters, const int *size_b,
+                                unsigned long long *g, const int *status)
+{
+    __shared__ unsigned long long red[72];
+    if (*status) return;
+    CompareAcc acc;
+    compare_acc_zero(acc);
+    const int nc = counters[C_NCELLS];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+        const Cell c = cells[i];
+        if (!QM_CHK(c.a, x.ka, 30) || !QM_CHK(c.b, x.kb, 31)) continue;
+        const long long n = c.n, na = __ldg(&x.size_a[c.a]), nb = __ldg(&size_b[c.b]);
+        acc.a11 += (unsigned long long)(n * (n - 1) / 2);
+        atomicMax(&x.rowmax_n[c.a], (unsigned)n);
+        atomicMax(&x.rowmax_r[c.a], (unsigned long long)__double_as_longlong(f_ratio(n, na, nb)));
+        acc.vi += fp_from_double(vi_term(n, na, nb), SC_VI);
+        acc.hnum += fp_from_double(nmi_num_term(n, na, nb, x.N), SC_H);
+    }
+    flush_compare(acc, g, red);
+}
+
+// Column side of every found community b: C(|b|, 2), its entropy term, the count.
+__global__ void k_compare_cols(const int *size_b, int kb, long long N, unsigned long long *g, const int *status)
+{
+    __shared__ unsigned long long red[72];
+    if (*status) return;
+    CompareAcc acc;
+    compare_acc_zero(acc);
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < kb; b += gridDim.x * blockDim.x) {
+        const long long nb = size_b[b];
+        if (nb == 0) continue;
+        acc.sb += (unsigned long long)(nb * (nb - 1) / 2);
+        acc.hden += fp_from_double(entropy_term(nb, N), SC_H);
+        acc.kb += 1;
+    }
     flush_compare(acc, g, red);
 }
 
@@ -1066,7 +1114,7 @@ int launch_score(const GraphDev &g, const int *labels, int K, const ScoreWs &ws,
     launches += launch_scan(ws.size, K, ws.start, ws.cursor, ws.recip, sh.big_community, ws.big_list,
                             ws.counters, ws.scan_tmp, ws.status, s, tr);
     TRACE("k_scatter");
-    k_scatter<<<grid_for(n, 512, num_sms, 8), 512, 0, s>>>(labels, n, ws.cursor, ws.members, ws.status);
+    k_scatter<<<grid_for(n, 512, num_sms, 8), 512, 0, s>>>(labels, nullptr, n, ws.cursor, ws.members, ws.status);
     ++launches;
 
     ScoreKArgs a;
@@ -1241,11 +1289,12 @@ int launch_compare(const int *truth, const int *found, long long n, int ka, int 
     launches += launch_scan(ws.size_b, kb, ws.start, ws.cursor, nullptr, plan.max_used_w, ws.big_list,
                             ws.counters, ws.scan_tmp, ws.status, s, tr);
     TRACE("k_scatter");
-    k_scatter<<<grid_for(n, 512, num_sms, 8), 512, 0, s>>>(found, n, ws.cursor, ws.members, ws.status);
+    k_scatter<<<grid_for(n, 512, num_sms, 8), 512, 0, s>>>(found, truth, n, ws.cursor, ws.members, ws.status);
     ++launches;
     CompareKArgs a;
     a.x.truth = truth;
-    a.x.members = ws.members;
+    a.x.tl = ws.members;  // truth labels in detected-community order (k_scatter with vals)
+    a.x.members = nullptr;
     a.x.start = ws.start;
     a.x.size_a = ws.size_a;
     a.x.rowmax_n = ws.rowmax_n;
@@ -1256,6 +1305,7 @@ int launch_compare(const int *truth, const int *found, long long n, int ka, int 
     a.x.err = ws.status;
     a.big_list = ws.big_list;
     a.counters = ws.counters;
+    a.cells = ws.cells;
     a.gacc = ws.gacc;
     a.status = ws.status;
     a.plan = plan;
@@ -1264,12 +1314,17 @@ int launch_compare(const int *truth, const int *found, long long n, int ka, int 
     if (nb < 1) nb = 1;
     TRACE("k_compare_cm");
     k_compare_cm<<<num_sms * nb, sh.threads, sh.smem_bytes, s>>>(a);
+    TRACE("k_compare_cells");
+    k_compare_cells<<<grid_for(n, 256, num_sms, 8), 256, 0, s>>>(a.x, ws.cells, ws.counters, ws.size_b, ws.gacc,
+                                                                 ws.status);
+    TRACE("k_compare_cols");
+    k_compare_cols<<<grid_for(kb, 256, num_sms, 2), 256, 0, s>>>(ws.size_b, kb, n, ws.gacc, ws.status);
     TRACE("k_compare_rows");
     k_compare_rows<<<grid_for(ka, 256, num_sms, 2), 256, 0, s>>>(a.x, ws.gacc, ws.status);
     TRACE("k_compare_fin");
     k_compare_fin<<<1, 32, 0, s>>>(ws.gacc, ws.status, n, ws.result);
     TRACE(nullptr);
-    launches += 3;
+    launches += 5;
     return cudaGetLastError() == cudaSuccess ? launches : -1;
 }
 
