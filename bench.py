@@ -335,6 +335,25 @@ def bench_headline(args, world, rank, local):
     assert qe == q, "host-buffer path differs from the device path"
     e2e_value = edges_all / (e2e_ms / 1e3)
 
+    # metrics with ground truth at the same size: the planted partition as the
+    # truth against a copy with 20% of the nodes moved (Eqs. 1-7)
+    cmp = None
+    if not args.no_extras and world == 1:
+        found = gen.perturb(labels, K, 0.2, seed=9)
+        for _ in range(2):
+            qm.compare(labels, found, K, K)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        csteps = max(1, args.steps // 2)
+        for _ in range(csteps):
+            c = qm.compare(labels, found, K, K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        cms = e0.elapsed_time(e1) / csteps
+        cmp = {"what": "planted partition (truth) vs 20% of nodes moved (found), all seven indices",
+               "ms_per_call": cms, "nodes_per_s": n / (cms / 1e3), "nmi": c["nmi"], "ari": c["ari"]}
+        del found
+
     # the same workload on the graph as given (no reorder), for comparison
     unordered = None
     if keep_csr is not None:
@@ -387,6 +406,7 @@ def bench_headline(args, world, rank, local):
         result={k: q[k] for k in ("modularity", "modularity_density", "mean_conductance",
                                   "n_community_pairs", "cut_edges_total")},
         unordered=unordered,
+        compare=cmp,
     )
     graph.close()
     del labels, lab_h
@@ -479,7 +499,8 @@ def run_ours(args):
             "roofline": res["roofline"], "cpu_baseline": cpu, "e2e": res["e2e"],
             "gpu_launches": res["launches"], "clocks": res["clocks"],
             "kernel_share": res["kernel_share"], "result": res["result"],
-            "extras": extras | ({"graph_as_given": res["unordered"]} if res["unordered"] else {}),
+            "extras": extras | ({"graph_as_given": res["unordered"]} if res["unordered"] else {})
+                      | ({"compare": res["compare"]} if res["compare"] else {}),
         }
         print(json.dumps(line), flush=True)
     if world > 1:

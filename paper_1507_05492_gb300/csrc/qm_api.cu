@@ -642,8 +642,13 @@ qm_status qm_compare_partitions(const int32_t *truth, const int32_t *found, int6
         CK(cudaMemcpyAsync((void *)df, found, (size_t)n * 4, cudaMemcpyHostToDevice, s));
     }
     CK(cudaMemsetAsync(ws.ptr(), 0, w.zero_bytes, s));
+    // Comparison runs are the detected communities' member lists (a few hundred
+    // entries with few distinct truth labels): small blocks with large warp
+    // tables keep almost all of them in warp mode.
     Shape cs = default_shape();
-    cs.algo = 0;  // occupancy of the community-pass kernels
+    cs.algo = 0;
+    cs.threads = 128;
+    cs.smem_bytes = 48 * 1024;
     Shape sh = resolve_plain(cs);
     const int L = launch_compare(dt, df, n, ka, kb, w, sh, num_sms_of(dev), s, trace_begin());
     if (L < 0) return cuda_fail(cudaGetLastError(), "launch_compare");
