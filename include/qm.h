@@ -24,9 +24,12 @@
  *     ids with no member are absent communities and are skipped in every sum and
  *     mean.  A label outside [0, K) makes the call return QM_EINVAL.
  *   - Counts are exact int64.  Floating-point results are FP64; every sum of
- *     per-community or per-cell terms is accumulated in 128-bit fixed point, so a
- *     result does not depend on thread scheduling and is bit-identical whether a
- *     partition is scored alone or inside a batch.
+ *     per-community or per-cell terms is accumulated in 128-bit fixed point, and
+ *     the Eq. (9) split penalty's inner sum over neighbouring communities
+ *     (sum_j |E_ij|^2 / |c_j|) exactly in 192-bit integers with 128-bit
+ *     reciprocals, so a result does not depend on thread scheduling, node order
+ *     or pipeline, and is bit-identical whether a partition is scored alone,
+ *     inside a batch, or on a graph loaded with QM_REORDER.
  *   - Limits: n_nodes < 2^31, n_arcs <= 2^32 - 2^20.
  *   - Calls on different streams may run concurrently from different threads;
  *     each call takes its own scratch memory from an internal pool.
@@ -170,7 +173,13 @@ typedef struct {
  * qm_compare_partitions -- Eqs. (1)-(7) from the contingency table of two
  * partitions of the same n_nodes nodes.  truth = C (ground truth), found = C'.
  *   truth  int32[n_nodes] in [0, k_truth); found int32[n_nodes] in [0, k_found)
- * Errors: QM_EINVAL (n_nodes < 2, bad label), QM_ENOMEM, QM_ECUDA.
+ * The cells are counted per detected community in shared-memory hash tables
+ * (a community with more distinct truth labels than a table holds is split
+ * into hash classes sized with room to spare) and the terms of every cell are
+ * then formed in parallel.
+ * Errors: QM_EINVAL (n_nodes < 2, bad label), QM_ENOMEM, QM_ECUDA, QM_EOVERFLOW
+ * (a hash class still overflowed: reported rather than dropped; not expected
+ * for any real labelling).
  */
 qm_status qm_compare_partitions(const int32_t *truth, const int32_t *found, int64_t n_nodes,
                                 int32_t k_truth, int32_t k_found, qm_mem where,
@@ -270,7 +279,7 @@ qm_status qm_set_tuning(const qm_graph *g, int32_t K, const qm_tuning *t);
  * Some hosts hand a plugin no allocator (all GPU memory is budgeted up front),
  * and some latency-critical loops must not pay for the device-wide
  * synchronisation that cudaMalloc / cudaFree can cause.  This call computes the
- * same result as qm_score_partition (same kernels, bit-identical output) but
+ * same result as qm_score_partition (bit-identical output) but
  * allocates nothing: its scratch memory is one fixed device array of
  * QM_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads the
  * library keeps until the process exits, and the result is copied straight
@@ -279,9 +288,11 @@ qm_status qm_set_tuning(const qm_graph *g, int32_t K, const qm_tuning *t);
  *   labels  device int32[n_nodes], labels in [0, K)
  *   out     host struct, written on success
  * Limits and rules:
- *   - The workspace of the call must fit the array: about 4 * n_nodes + 20 * K
- *     bytes (for example 10,000,000 nodes with 100,000 label ids).  Larger
- *     calls return QM_EOVERFLOW with the required size in qm_last_error().
+ *   - The call runs the one-kernel pipeline (tuning algorithm 0).  Its
+ *     workspace must fit the array: about 4 * n_nodes + 36 * K bytes, plus
+ *     4 * n_nodes for a graph loaded with QM_REORDER (for example 10,000,000
+ *     nodes with 100,000 label ids).  Larger calls return QM_EOVERFLOW with the
+ *     required size in qm_last_error().
  *   - labels must be device memory (QM_EINVAL otherwise); no per-community
  *     outputs.
  *   - All calls share the one array, and each call clears what must start at
