@@ -273,6 +273,22 @@ qm_status qm_get_tuning(const qm_graph *g, int32_t K, qm_tuning *t);
 qm_status qm_set_tuning(const qm_graph *g, int32_t K, const qm_tuning *t);
 
 /*
+ * The same for the batched kernel (qm_score_partitions_batched,
+ * qm_evaluate_partitions_batched), keyed by the batch's largest K.
+ * qm_autotune_batched times candidate shapes (threads, shared memory, the
+ * block/warp community-size split) on the caller's batch, exactly as
+ * qm_evaluate_partitions_batched (truth != NULL) or
+ * qm_score_partitions_batched (truth == NULL) would run it, and caches the
+ * fastest; the batch's results are the same bits for every shape.  The
+ * algorithm field is ignored (the batched kernel has one pipeline).
+ */
+qm_status qm_autotune_batched(const qm_graph *g, const int32_t *labels, int32_t P, const int32_t *K,
+                              const int32_t *truth, int32_t k_truth, qm_mem where, void *stream,
+                              qm_tuning *chosen);
+qm_status qm_get_batch_tuning(const qm_graph *g, int32_t K, qm_tuning *t);
+qm_status qm_set_batch_tuning(const qm_graph *g, int32_t K, const qm_tuning *t);
+
+/*
  * qm_score_partition_noalloc -- qm_score_partition for callers that cannot let
  * a library allocate memory while it runs (no counterpart in the paper).
  *

@@ -317,6 +317,19 @@ static Shape default_shape()
     return s;
 }
 
+// Batched kernel: one block per item; communities up to 128 members counted by
+// single warps (the autotuner's usual choice on 10^5-node graphs).
+static Shape default_batch_shape()
+{
+    Shape s;
+    s.threads = 256;
+    s.smem_bytes = 96 * 1024;
+    s.big_community = 128;
+    s.blocks_per_sm = 0;
+    s.algo = 0;
+    return s;
+}
+
 static Shape resolve_plain(Shape s)
 {
     int dev = 0;
@@ -353,7 +366,7 @@ static Shape shape_for(qm_graph *g, int K, bool batched)
     std::lock_guard<std::mutex> lk(g->mu);
     auto &m = batched ? g->tuning_batch : g->tuning;
     auto it = m.find(bucket_of(g->n, g->n_arcs, K));
-    Shape s = it != m.end() ? it->second : default_shape();
+    Shape s = it != m.end() ? it->second : (batched ? default_batch_shape() : default_shape());
     return batched ? resolve_batched(s) : resolve_plain(s);
 }
 
@@ -772,7 +785,7 @@ static qm_status stage_labels(int dev, const int32_t *labels, size_t n_labels, q
 
 static qm_status evaluate_batched(qm_graph *g, const int32_t *labels, int32_t P, const int32_t *K,
                                   const int32_t *truth, int32_t kt, int flags, qm_mem where, qm_quality *out_q,
-                                  qm_compare *out_c, cudaStream_t s)
+                                  qm_compare *out_c, cudaStream_t s, const Shape *force = nullptr)
 {
     if (!g || !labels || !K || P < 1) return fail(QM_EINVAL, "bad argument");
     if ((flags & 2) && (!truth || kt < 1)) return fail(QM_EINVAL, "truth labels required");
@@ -825,7 +838,7 @@ static qm_status evaluate_batched(qm_graph *g, const int32_t *labels, int32_t P,
         it.k_truth = (flags & 2) ? kt : 0;
         it.flags = flags;
     }
-    return run_batched(g->device, d, shape_for(g, kmax, true), out_q, out_c, s, nullptr);
+    return run_batched(g->device, d, force ? *force : shape_for(g, kmax, true), out_q, out_c, s, nullptr);
 }
 
 qm_status qm_score_partitions_batched(const qm_graph *g, const int32_t *labels, int32_t P, const int32_t *K,
@@ -880,7 +893,7 @@ qm_status qm_compare_partitions_batched(const int32_t *truth, const int32_t *fou
         it.k_truth = kt;
         it.flags = 2;
     }
-    return run_batched(dev, d, default_shape(), nullptr, out, s, nullptr);
+    return run_batched(dev, d, default_batch_shape(), nullptr, out, s, nullptr);
 }
 
 qm_status qm_score_graphs_batched(const qm_graph *const *graphs, const int32_t *const *labels, const int32_t *K,
@@ -944,7 +957,7 @@ qm_status qm_score_graphs_batched(const qm_graph *const *graphs, const int32_t *
         it.K = K[i];
         it.flags = 1;
     }
-    return run_batched(dev, d, default_shape(), out, nullptr, s, nullptr);
+    return run_batched(dev, d, default_batch_shape(), out, nullptr, s, nullptr);
 }
 
 qm_status qm_release_cache(void)
@@ -984,6 +997,108 @@ qm_status qm_set_tuning(const qm_graph *gc, int32_t K, const qm_tuning *t)
     s.algo = t->algorithm;
     std::lock_guard<std::mutex> lk(g->mu);
     g->tuning[bucket_of(g->n, g->n_arcs, K)] = s;
+    return QM_OK;
+}
+
+qm_status qm_get_batch_tuning(const qm_graph *gc, int32_t K, qm_tuning *t)
+{
+    qm_graph *g = const_cast<qm_graph *>(gc);
+    if (!g || !t || K < 1) return fail(QM_EINVAL, "bad argument");
+    DeviceGuard dg(g->device);
+    const Shape s = shape_for(g, K, true);
+    t->threads = s.threads;
+    t->smem_bytes = s.smem_bytes;
+    t->big_community = s.big_community;
+    t->blocks_per_sm = s.blocks_per_sm;
+    t->algorithm = 0;
+    return QM_OK;
+}
+
+qm_status qm_set_batch_tuning(const qm_graph *gc, int32_t K, const qm_tuning *t)
+{
+    qm_graph *g = const_cast<qm_graph *>(gc);
+    if (!g || K < 1 || !shape_ok(t)) return fail(QM_EINVAL, "bad tuning");
+    Shape s;
+    s.threads = t->threads;
+    s.smem_bytes = t->smem_bytes;
+    s.big_community = t->big_community;
+    s.blocks_per_sm = 0;
+    s.algo = 0;
+    std::lock_guard<std::mutex> lk(g->mu);
+    g->tuning_batch[bucket_of(g->n, g->n_arcs, K)] = s;
+    return QM_OK;
+}
+
+// Times candidate shapes of the batched kernel on the caller's batch (the
+// median of 3 launches each, CUDA events on the call's stream) and caches the
+// fastest for the batch's size bucket (its largest K).
+qm_status qm_autotune_batched(const qm_graph *gc, const int32_t *labels, int32_t P, const int32_t *K,
+                              const int32_t *truth, int32_t k_truth, qm_mem where, void *stream,
+                              qm_tuning *chosen)
+{
+    qm_graph *g = const_cast<qm_graph *>(gc);
+    if (!g || !labels || !K || P < 1) return fail(QM_EINVAL, "bad argument");
+    if (truth && k_truth < 1) return fail(QM_EINVAL, "k_truth must be >= 1");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int kmax = 1;
+    for (int p = 0; p < P; ++p) kmax = std::max(kmax, K[p]);
+    const int flags = truth ? 3 : 1;
+    std::vector<qm_quality> oq(P);
+    std::vector<qm_compare> oc(P);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    num_sms_of(g->device);
+    float best_ms = 1e30f;
+    Shape best = default_shape();
+    best.algo = 0;
+    for (int th : {256, 512})
+        for (int sm : {64 * 1024, 96 * 1024, 160 * 1024})
+            for (int bg : {48, 128, 256}) {
+                qm_tuning tt{th, sm, bg, 0, 0};
+                if (!shape_ok(&tt)) continue;
+                Shape sh;
+                sh.threads = th;
+                sh.smem_bytes = sm;
+                sh.big_community = bg;
+                sh.blocks_per_sm = 0;
+                sh.algo = 0;
+                if (resolve_batched(sh).blocks_per_sm < 1) continue;
+                float times[3];
+                bool ok = true;
+                for (int r = 0; r < 3 && ok; ++r) {
+                    cudaEventRecord(e0, s);
+                    if (evaluate_batched(g, labels, P, K, truth, k_truth, flags, where, oq.data(),
+                                         truth ? oc.data() : nullptr, s, &sh) != QM_OK)
+                        ok = false;
+                    cudaEventRecord(e1, s);
+                    cudaEventSynchronize(e1);
+                    cudaEventElapsedTime(&times[r], e0, e1);
+                }
+                if (!ok) continue;
+                std::sort(times, times + 3);
+                if (times[1] < best_ms) {
+                    best_ms = times[1];
+                    best = sh;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    {
+        std::lock_guard<std::mutex> lk(g->mu);
+        Shape b = best;
+        b.blocks_per_sm = 0;
+        g->tuning_batch[bucket_of(g->n, g->n_arcs, kmax)] = b;
+    }
+    if (chosen) {
+        const Shape r = resolve_batched(best);
+        chosen->threads = r.threads;
+        chosen->smem_bytes = r.smem_bytes;
+        chosen->big_community = r.big_community;
+        chosen->blocks_per_sm = r.blocks_per_sm;
+        chosen->algorithm = 0;
+    }
     return QM_OK;
 }
 

@@ -90,6 +90,9 @@ def _signatures(lib):
         "qm_autotune": [_P, _P, _I32, S, _P, _P],
         "qm_get_tuning": [_P, _I32, _P],
         "qm_set_tuning": [_P, _I32, _P],
+        "qm_autotune_batched": [_P, _P, _I32, _P, _P, _I32, S, _P, _P],
+        "qm_get_batch_tuning": [_P, _I32, _P],
+        "qm_set_batch_tuning": [_P, _I32, _P],
         "qm_last_error": [_P, ctypes.c_size_t],
         "qm_trace_enable": [_I32],
         "qm_trace_read": [_P, _I32, _P],
@@ -346,6 +349,33 @@ def set_tuning(graph: Graph, K: int, threads: int, smem_bytes: int, big_communit
     """algorithm 0: one-kernel community pass; 1: expand + count (two phases)."""
     t = QmTuning(threads, smem_bytes, big_community, 0, algorithm)
     _check(lib().qm_set_tuning(graph.handle, int(K), ctypes.byref(t)), "qm_set_tuning")
+
+
+def autotune_batched(graph: Graph, labels, K, truth=None, k_truth: int = 0, stream=None) -> dict:
+    """qm_autotune_batched over a [P, n] label matrix (and an optional truth)."""
+    ptr, where, keep = _labels_arg(labels)
+    pt = None
+    if truth is not None:
+        pt, wt, keep_t = _labels_arg(truth, "truth")
+        if wt != where:
+            raise ValueError("labels and truth must live in the same memory")
+    P = labels.shape[0]
+    k = _k_array(K, P)
+    t = QmTuning()
+    _check(lib().qm_autotune_batched(graph.handle, ptr, P, k.ctypes.data, pt, int(k_truth), where,
+                                     _stream_ptr(stream), ctypes.byref(t)), "qm_autotune_batched")
+    return _struct_dict(t)
+
+
+def get_batch_tuning(graph: Graph, K: int) -> dict:
+    t = QmTuning()
+    _check(lib().qm_get_batch_tuning(graph.handle, int(K), ctypes.byref(t)), "qm_get_batch_tuning")
+    return _struct_dict(t)
+
+
+def set_batch_tuning(graph: Graph, K: int, threads: int, smem_bytes: int, big_community: int):
+    t = QmTuning(threads, smem_bytes, big_community, 0, 0)
+    _check(lib().qm_set_batch_tuning(graph.handle, int(K), ctypes.byref(t)), "qm_set_batch_tuning")
 
 
 def trace_enable(on: bool = True):

@@ -94,3 +94,22 @@ def test_batched_rejects_bad_item(qm, setup):
     assert e.value.status == qm.QM_EINVAL
     out = qm.score_batched(graph, L.cuda(), Ks)  # still usable
     assert out[0] == qm.score(graph, L[0].cuda(), Ks[0])
+
+
+def test_autotune_batched_keeps_results(qm, setup):
+    """qm_autotune_batched tries several launch shapes of the batched kernel and
+    caches the fastest; every shape gives the same bits."""
+    g, graph, L, Ks = setup
+    truth = g.labels.cuda()
+    ref_q, ref_c = qm.evaluate_batched(graph, L.cuda(), Ks, truth, g.K)
+    t = qm.autotune_batched(graph, L.cuda(), Ks, truth, g.K)
+    assert t["threads"] in (256, 512) and t["blocks_per_sm"] >= 1
+    got = qm.get_batch_tuning(graph, max(Ks))
+    assert (got["threads"], got["smem_bytes"], got["big_community"]) == \
+        (t["threads"], t["smem_bytes"], t["big_community"])
+    oq, oc = qm.evaluate_batched(graph, L.cuda(), Ks, truth, g.K)
+    assert oq == ref_q and oc == ref_c
+    for shape in ((256, 64 * 1024, 128), (512, 160 * 1024, 48)):
+        qm.set_batch_tuning(graph, max(Ks), *shape)
+        oq, oc = qm.evaluate_batched(graph, L.cuda(), Ks, truth, g.K)
+        assert oq == ref_q and oc == ref_c, shape
