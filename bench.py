@@ -354,6 +354,30 @@ def bench_headline(args, world, rank, local):
                "ms_per_call": cms, "nodes_per_s": n / (cms / 1e3), "nmi": c["nmi"], "ari": c["ari"]}
         del found
 
+    # the paper's detected-vs-truth workload at this size: detect C' with the
+    # device label propagation, then score C' and compare it with the truth
+    detect = None
+    if not args.no_extras and world == 1:
+        rounds = 10
+        qm.label_propagation(graph, 1)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        found, k_found = qm.label_propagation(graph, rounds)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_lpa = e0.elapsed_time(e1)
+        e0.record(stream)
+        qd = qm.score(graph, found, k_found)
+        cd = qm.compare(labels, found, K, k_found)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        detect = {"what": f"label propagation ({rounds} rounds) on the graph, then all metrics of C' "
+                          "with and without the planted truth",
+                  "lpa_ms": t_lpa, "lpa_ms_per_round": t_lpa / rounds, "score_and_compare_ms": e0.elapsed_time(e1),
+                  "k_found": k_found, "nmi": cd["nmi"], "ari": cd["ari"], "f_measure": cd["f_measure"],
+                  "modularity": qd["modularity"]}
+        del found
+
     # the same workload on the graph as given (no reorder), for comparison
     unordered = None
     if keep_csr is not None:
@@ -407,6 +431,7 @@ def bench_headline(args, world, rank, local):
                                   "n_community_pairs", "cut_edges_total")},
         unordered=unordered,
         compare=cmp,
+        detect=detect,
     )
     graph.close()
     del labels, lab_h
@@ -465,6 +490,52 @@ def bench_batched(args):
     return out
 
 
+def bench_configs(args):
+    """The smaller configurations, one plain call each: 10k nodes (scoring of
+    the planted partition and its comparison with a 10% perturbed copy; latency
+    bound, so microseconds per call) and 10M nodes (scoring of the planted
+    partition; ms per call and edges/s).  CUDA events on the current stream,
+    median of the timed calls."""
+    import torch
+    from paper_1507_05492_gb300 import gen, qm
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    out = {}
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    g = gen.lfr_graph(gen.config_params("lfr10k"), device=dev)
+    graph = qm.Graph(g.row_ptr, g.col)
+    b = gen.perturb(g.labels, g.K, 0.1, seed=101)
+    t_s = timed(lambda: qm.score(graph, g.labels, g.K), 20)
+    t_c = timed(lambda: qm.compare(g.labels, b, g.K, g.K), 20)
+    out["lfr10k"] = {"score_us_per_call": 1e3 * t_s, "compare_us_per_call": 1e3 * t_c,
+                     "n_edges": g.n_edges}
+    graph.close()
+    g = gen.lfr_graph(gen.config_params("lfr10m"), device=dev)
+    for reorder in (True, False):
+        graph = qm.Graph(g.row_ptr, g.col, reorder=reorder)
+        t = timed(lambda: qm.score(graph, g.labels, g.K), 10)
+        out["lfr10m" + ("" if reorder else "_graph_as_given")] = {
+            "score_ms_per_call": t, "edges_per_s": g.n_edges / (t / 1e3)}
+        graph.close()
+    del g
+    torch.cuda.empty_cache()
+    return out
+
+
 def bench_serving(args):
     from paper_1507_05492_gb300 import server
     return server.run_benchmark(duration_s=args.serve_seconds, rate=args.serve_rate, seed=11)
@@ -491,6 +562,10 @@ def run_ours(args):
         except Exception as e:  # reported, never silently dropped
             extras["batched"] = {"error": repr(e)}
         try:
+            extras["configs"] = bench_configs(args)
+        except Exception as e:
+            extras["configs"] = {"error": repr(e)}
+        try:
             extras["serving"] = bench_serving(args)
         except Exception as e:
             extras["serving"] = {"error": repr(e)}
@@ -505,7 +580,8 @@ def run_ours(args):
             "gpu_launches": res["launches"], "clocks": res["clocks"],
             "kernel_share": res["kernel_share"], "result": res["result"],
             "extras": extras | ({"graph_as_given": res["unordered"]} if res["unordered"] else {})
-                      | ({"compare": res["compare"]} if res["compare"] else {}),
+                      | ({"compare": res["compare"]} if res["compare"] else {})
+                      | ({"detect": res["detect"]} if res["detect"] else {}),
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -322,6 +322,24 @@ qm_status qm_set_batch_tuning(const qm_graph *g, int32_t K, const qm_tuning *t);
 qm_status qm_score_partition_noalloc(const qm_graph *g, const int32_t *labels, int32_t K,
                                      qm_quality *out, void *stream);
 
+/*
+ * qm_label_propagation -- a detected partition C' of the graph by synchronous
+ * label propagation (the O(|E|) detector family the paper scores, Sec. I and
+ * Sec. IV-C; not SLPA itself).  Labels start as the node ids; in each round
+ * every node takes the label found most often among its neighbours (among up
+ * to 32 evenly spaced ones: positions floor(i * deg / 32), i < 32, when
+ * deg > 32), keeps its own label when that is among the most frequent, and
+ * otherwise takes the smallest of the most frequent.  Afterwards the labels
+ * present are renumbered in increasing order to [0, K').  Deterministic, and
+ * the same for a graph loaded with QM_REORDER.
+ *   rounds      number of rounds, 0..1000
+ *   labels_out  int32[n_nodes] (host or device memory as `where` says)
+ *   k_out       host int32, receives K'
+ * Errors: QM_EINVAL, QM_ENOMEM, QM_ECUDA.
+ */
+qm_status qm_label_propagation(const qm_graph *g, int32_t rounds, int32_t *labels_out, qm_mem where,
+                               int32_t *k_out, void *stream);
+
 /* Number of this library's kernel launches issued since load (for accounting). */
 int64_t qm_kernel_launches(void);
 

@@ -62,8 +62,10 @@ def _load():
     lib.oq_compare_bruteforce.argtypes = [p, p, i64, i32, i32, p]
     lib.oq_score_bruteforce.argtypes = [p, p, i64, p, i32, p]
     lib.oq_score_communities.argtypes = [p, p, i64, p, i32, p, i64, p, p]
+    lib.oq_label_propagation.argtypes = [p, p, i64, i32, p, p]
     for f in (lib.oq_validate_graph, lib.oq_score, lib.oq_compare, lib.oq_pairs_bruteforce,
-              lib.oq_compare_bruteforce, lib.oq_score_bruteforce, lib.oq_score_communities):
+              lib.oq_compare_bruteforce, lib.oq_score_bruteforce, lib.oq_score_communities,
+              lib.oq_label_propagation):
         f.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -177,6 +179,19 @@ def score_communities(row_ptr, col, labels, K: int, ids) -> dict:
                                         _ptr(ids), m, _ptr(i64), _ptr(dbl)), "score_communities")
     return dict(size=i64[:, 0], intra_edges=i64[:, 1], inter_edges=i64[:, 2], distinct_neighbours=i64[:, 3],
                 qds_term=dbl[:, 0], split=dbl[:, 1])
+
+
+def label_propagation(row_ptr, col, rounds: int):
+    """Synchronous label propagation (the detector family of Sec. I and IV-C):
+    (labels renumbered to [0, K'), K')."""
+    row_ptr = _as(row_ptr, np.int64)
+    col = _as(col, np.int32)
+    n = len(row_ptr) - 1
+    out = np.zeros(n, np.int32)
+    k = np.zeros(1, np.int32)
+    _check(_load().oq_label_propagation(_ptr(row_ptr), _ptr(col), n, int(rounds), _ptr(out), _ptr(k)),
+           "label_propagation")
+    return out, int(k[0])
 
 
 def within(gpu: float, ref: float, cond: float = 0.0, rel: float = 1e-12) -> bool:

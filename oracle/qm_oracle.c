@@ -633,3 +633,73 @@ int oq_score_communities(const int64_t *row_ptr, const int32_t *col, int64_t n,
     free(size);
     return rc;
 }
+
+/*
+ * oq_label_propagation -- plain synchronous label propagation, the O(|E|)
+ * detector family whose output C' the paper scores (Sec. I, Sec. IV-C); not
+ * SLPA itself, whose exact rules the paper leaves to its cited source (parity
+ * against SLPA unpinned).  Rules, applied to every node at once in each round:
+ *   - labels start as the node ids;
+ *   - a node looks at its neighbours' labels; when deg > 32 it looks only at
+ *     the neighbours in row positions floor(i * deg / 32), i = 0..31;
+ *   - it takes the label seen most often; it keeps its own label when that is
+ *     among the most frequent, else it takes the smallest of them; a node with
+ *     no neighbours keeps its label.
+ * Afterwards the labels present are renumbered in increasing order of value
+ * to 0..K'-1.  The counting is a plain double loop over the (at most 32)
+ * labels seen.
+ *   out[n]   final labels in [0, K'),  *k_out = K'
+ */
+int oq_label_propagation(const int64_t *row_ptr, const int32_t *col, int64_t n, int32_t rounds,
+                         int32_t *out, int32_t *k_out)
+{
+    if (n < 1 || rounds < 0)
+        return OQ_EINVAL;
+    int32_t *cur = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *nxt = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *rank = (int32_t *)calloc((size_t)n, sizeof(int32_t));
+    if (!cur || !nxt || !rank) { free(cur); free(nxt); free(rank); return OQ_ENOMEM; }
+    for (int64_t u = 0; u < n; u++)
+        cur[u] = (int32_t)u;
+    for (int32_t r = 0; r < rounds; r++) {
+        for (int64_t u = 0; u < n; u++) {
+            const int64_t deg = row_ptr[u + 1] - row_ptr[u];
+            int32_t seen[32];
+            int m = 0;
+            for (int64_t i = 0; i < (deg < 32 ? deg : 32); i++) {
+                const int64_t pos = deg <= 32 ? i : i * deg / 32;
+                seen[m++] = cur[col[row_ptr[u] + pos]];
+            }
+            int32_t best = cur[u];
+            int best_count = 0, own_count = 0;
+            for (int a = 0; a < m; a++) {
+                int count = 0;
+                for (int b = 0; b < m; b++)
+                    count += seen[b] == seen[a];
+                if (seen[a] == cur[u])
+                    own_count = count;
+                if (count > best_count || (count == best_count && seen[a] < best)) {
+                    best_count = count;
+                    best = seen[a];
+                }
+            }
+            if (m > 0 && own_count == best_count)
+                best = cur[u];
+            nxt[u] = m > 0 ? best : cur[u];
+        }
+        int32_t *t = cur; cur = nxt; nxt = t;
+    }
+    for (int64_t u = 0; u < n; u++)
+        rank[cur[u]] = 1;
+    int32_t k = 0;
+    for (int64_t c = 0; c < n; c++) {
+        const int32_t present = rank[c];
+        rank[c] = k;
+        k += present;
+    }
+    for (int64_t u = 0; u < n; u++)
+        out[u] = rank[cur[u]];
+    *k_out = k;
+    free(cur); free(nxt); free(rank);
+    return OQ_OK;
+}

@@ -1000,6 +1000,37 @@ qm_status qm_set_tuning(const qm_graph *gc, int32_t K, const qm_tuning *t)
     return QM_OK;
 }
 
+qm_status qm_label_propagation(const qm_graph *gc, int32_t rounds, int32_t *labels_out, qm_mem where,
+                               int32_t *k_out, void *stream)
+{
+    qm_graph *g = const_cast<qm_graph *>(gc);
+    if (!g || !labels_out || !k_out) return fail(QM_EINVAL, "null argument");
+    if (rounds < 0 || rounds > 1000) return fail(QM_EINVAL, "rounds must be in [0, 1000]");
+    if (where != QM_HOST && where != QM_DEVICE) return fail(QM_EINVAL, "bad memory kind");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long n = g->n;
+    const size_t tmp_elems = scan_tmp_elems(n + 1) + 64;
+    const size_t b_lab = al256((size_t)n * 4), b_hist = al256((size_t)(n + 1) * 4);
+    const size_t need = 2 * b_lab + b_hist + al256(tmp_elems * 4) + (where == QM_HOST ? b_lab : 0);
+    Lease ws(g_pool.acquire(need, g->device, false));
+    Lease pin(g_pool.acquire(256, g->device, true));
+    if (!ws.b || !pin.b) return fail(QM_ENOMEM, "scratch allocation failed");
+    char *p = ws.ptr();
+    int *lab0 = (int *)p, *lab1 = (int *)(p + b_lab), *hist = (int *)(p + 2 * b_lab);
+    int *tmp = (int *)(p + 2 * b_lab + b_hist);
+    int *out = where == QM_HOST ? (int *)(p + 2 * b_lab + b_hist + al256(tmp_elems * 4)) : labels_out;
+    const int L = launch_label_propagation(g->d, rounds, num_sms_of(g->device), s, lab0, lab1, hist, tmp,
+                                           tmp_elems, out);
+    if (L < 0) return cuda_fail(cudaGetLastError(), "label propagation launch");
+    g_launches += L;
+    CK(cudaMemcpyAsync(pin.ptr(), hist + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (where == QM_HOST) CK(cudaMemcpyAsync(labels_out, out, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *k_out = *(int *)pin.ptr();
+    return QM_OK;
+}
+
 qm_status qm_get_batch_tuning(const qm_graph *gc, int32_t K, qm_tuning *t)
 {
     qm_graph *g = const_cast<qm_graph *>(gc);

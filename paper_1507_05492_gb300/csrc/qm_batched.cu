@@ -106,11 +106,7 @@ __global__ void __launch_bounds__(1024) k_batched(BatchKArgs a)
         const bool do_score = (I.flags & 1) != 0;
         const bool do_cmp = (I.flags & 2) != 0 && I.truth != nullptr;
         const int kt = do_cmp ? I.k_truth : 0;
-#ifdef QM_DBG_NO_SMEM_HIST
-        const bool smem_hist = false;
-#else
         const bool smem_hist = (long long)K + kt <= 2LL * p.cap;
-#endif
         int *cnt = smem_hist ? (int *)slot : gsize;       // label counts, then cursors
         int *cnt_a = smem_hist ? (int *)slot + K : size_a;
         if (tid == 0) { s_bad = 0; s_nbig = 0; s_ncmp = 0; s_next = 0; s_novf = 0; s_next2 = 0; }
@@ -182,17 +178,6 @@ __global__ void __launch_bounds__(1024) k_batched(BatchKArgs a)
         }
         __threadfence();  // members[] is read by every warp below
         block_sync();
-#ifdef QM_DBG_VERIFY_MEMBERS
-        // diagnostic: members[start[c] .. start[c+1]) must hold exactly the nodes labelled c
-        for (int c = tid; c < K; c += T) {
-            if (!QM_CHK(start[c], start[c + 1] + 1, 22)) continue;
-            for (int i = start[c]; i < start[c + 1]; ++i) {
-                const int m = members[i];
-                if (QM_CHK(m, n, 24)) QM_CHK(I.labels[m] == c ? 0 : 1, 1, 21);
-            }
-        }
-        if (tid == 0) QM_CHK(start[K] == n ? 0 : 1, 1, 25);
-#endif
         if (smem_hist) {
             for (int i = tid; i < K + kt; i += T) ((int *)slot)[i] = 0;
             block_sync();
@@ -219,24 +204,16 @@ __global__ void __launch_bounds__(1024) k_batched(BatchKArgs a)
             block_sync();
             const int nbig = s_nbig;
             for (int i = 0; i < nbig; ++i) {
-#ifdef QM_DBG_SYNC_F
-                block_sync();
-#endif
                 score_community(x, __ldcg(&big_score[i]), tb, offs, rs, &sacc[0], tid, T, red);
-#ifdef QM_DBG_SYNC_F
-                block_sync();
-#endif
             }
-#ifdef QM_DBG_SYNC_G
-            block_sync();
-#endif
+            const int chunk = claim_chunk(K, W);
             for (;;) {
                 int base = 0;
-                if (lane == 0) base = atomicAdd(&s_next, 32);
+                if (lane == 0) base = atomicAdd(&s_next, chunk);
                 base = __shfl_sync(0xffffffffu, base, 0);
                 if (base >= K) break;
                 const int c = base + lane;
-                const int sz = c < K ? __ldcg(&start[c + 1]) - __ldcg(&start[c]) : 0;
+                const int sz = lane < chunk && c < K ? __ldcg(&start[c + 1]) - __ldcg(&start[c]) : 0;
                 unsigned mask = __ballot_sync(0xffffffffu, sz > 0 && sz <= a.big_thr);
                 while (mask) {
                     const int j = __ffs(mask) - 1;
@@ -293,13 +270,14 @@ __global__ void __launch_bounds__(1024) k_batched(BatchKArgs a)
             block_sync();
             const int ncmp = s_ncmp;
             for (int i = 0; i < ncmp; ++i) compare_community(x, __ldcg(&big_cmp[i]), tb, &cacc[0], tid, T, red);
+            const int chunk2 = claim_chunk(K, W);
             for (;;) {
                 int base = 0;
-                if (lane == 0) base = atomicAdd(&s_next2, 32);
+                if (lane == 0) base = atomicAdd(&s_next2, chunk2);
                 base = __shfl_sync(0xffffffffu, base, 0);
                 if (base >= K) break;
                 const int b = base + lane;
-                const int sz = b < K ? __ldcg(&start[b + 1]) - __ldcg(&start[b]) : 0;
+                const int sz = lane < chunk2 && b < K ? __ldcg(&start[b + 1]) - __ldcg(&start[b]) : 0;
                 unsigned mask = __ballot_sync(0xffffffffu, sz > 0 && sz <= p.max_used_w);
                 while (mask) {
                     const int j = __ffs(mask) - 1;

@@ -269,10 +269,6 @@ __device__ __forceinline__ bool score_community(const ScoreCtx &x, int c, const 
     long long *rsw = rs + (threadIdx.x >> 5) * 32;
     const int mb = __ldcg(&x.start[c]), me = __ldcg(&x.start[c + 1]);
     const long long size = me - mb;
-#ifdef QM_DBG_VERIFY_AGREE
-    if (gsize == 32)
-        QM_CHK(c == __shfl_sync(0xffffffffu, c, 0) && mb == __shfl_sync(0xffffffffu, mb, 0) ? 0 : 1, 1, 28);
-#endif
     unsigned R = 1;
     for (;;) {
         unsigned long long same = 0, vol = 0, slots = 0, cnt2 = 0;
@@ -302,9 +298,6 @@ __device__ __forceinline__ bool score_community(const ScoreCtx &x, int c, const 
                 const int nm = min(32, me - cb);
                 if (lane < nm) { offw[lane] = inc - d; rsw[lane] = rsi; }
                 __syncwarp();
-#ifdef QM_DBG_VERIFY_OFFS
-                if (lane < nm) QM_CHK(inc == (lane + 1 < nm ? offw[lane + 1] : total) ? 0 : 1, 1, 23);
-#endif
                 for (unsigned e0 = lane; e0 < total; e0 += 128u) {
                     int v[4], lv[4];
 #pragma unroll

@@ -491,6 +491,16 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
 
 // ---------------------------------------------------------------- misc
 
+// How many items a warp claims at a time from a shared list of n items when
+// `warps` warps draw from it: about a quarter of an even share, between 1 and
+// 32.  Few items (a small graph) then spread over all warps instead of
+// queueing behind a few, and many items still take few atomics per warp.
+__device__ __forceinline__ int claim_chunk(long long n, long long warps)
+{
+    const long long c = n / (4 * (warps > 0 ? warps : 1));
+    return c < 1 ? 1 : (c > 32 ? 32 : (int)c);
+}
+
 // Number of entries of the sorted prefix a[0..n) that are <= x.
 __device__ __forceinline__ int upper_bound_smem(const unsigned *a, int n, unsigned x)
 {

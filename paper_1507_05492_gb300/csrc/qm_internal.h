@@ -137,6 +137,12 @@ int launch_permute_labels(const int *labels, const int *inv, long long n, int P,
 // or minus a CUDA error code (nothing allocated then).
 int reorder_graph(const GraphDev &g, int rounds, int num_sms, cudaStream_t s, long long **row_ptr_out, int **col_out,
                   int **inv_out, int *launches);
+// qm_label_propagation on the device: `rounds` rounds from the caller's node
+// ids, then the labels present are ranked into [0, K'): out (caller order,
+// n entries) and hist[n] = K' (device).  lab0, lab1: n ints; hist: n + 1;
+// tmp: tmp_elems >= scan_tmp_elems(n + 1) + 64.  Returns launches or -1.
+int launch_label_propagation(const GraphDev &g, int rounds, int num_sms, cudaStream_t s, int *lab0, int *lab1,
+                             int *hist, int *tmp, size_t tmp_elems, int *out);
 
 // Largest dynamic shared memory a community-major block may request.
 constexpr int MAX_DYN_SMEM = 220 * 1024;

@@ -382,14 +382,15 @@ __global__ void __launch_bounds__(1024) k_score_cm(ScoreKArgs a)
     if (a.phase == 0) {
         const SmemTable tw{slot + wid * p.cap_w, used + wid * p.max_used_w, &ctl[2 + 2 * wid],
                            &ctl[3 + 2 * wid], p.cap_w, p.max_used_w};
+        const int chunk = claim_chunk(a.x.K, (long long)gridDim.x * W);
         for (;;) {
             int base = 0;
-            if (lane == 0) base = atomicAdd(&a.counters[C_SMALL_NEXT], 32);
+            if (lane == 0) base = atomicAdd(&a.counters[C_SMALL_NEXT], chunk);
             base = __shfl_sync(0xffffffffu, base, 0);
             if (base >= a.x.K) break;
             const int c = base + lane;
             int sz = 0;
-            if (c < a.x.K) sz = a.x.start[c + 1] - a.x.start[c];
+            if (lane < chunk && c < a.x.K) sz = a.x.start[c + 1] - a.x.start[c];
             unsigned mask = __ballot_sync(0xffffffffu, sz > 0 && sz <= a.big_thr);
             while (mask) {
                 const int j = __ffs(mask) - 1;
@@ -504,14 +505,15 @@ __global__ void __launch_bounds__(1024) k_compare_cm(CompareKArgs a)
     }
     const SmemTable tw{slot + wid * p.cap_w, used + wid * p.max_used_w, &ctl[2 + 2 * wid],
                        &ctl[3 + 2 * wid], p.cap_w, p.max_used_w};
+    const int chunk = claim_chunk(a.x.kb, (long long)gridDim.x * W);
     for (;;) {
         int base = 0;
-        if (lane == 0) base = atomicAdd(&a.counters[C_SMALL_NEXT], 32);
+        if (lane == 0) base = atomicAdd(&a.counters[C_SMALL_NEXT], chunk);
         base = __shfl_sync(0xffffffffu, base, 0);
         if (base >= a.x.kb) break;
         const int b = base + lane;
         int sz = 0;
-        if (b < a.x.kb) sz = a.x.start[b + 1] - a.x.start[b];
+        if (lane < chunk && b < a.x.kb) sz = a.x.start[b + 1] - a.x.start[b];
         unsigned mask = __ballot_sync(0xffffffffu, sz > 0 && sz <= p.max_used_w);
         while (mask) {
             const int j = __ffs(mask) - 1;
@@ -959,13 +961,14 @@ __global__ void __launch_bounds__(1024) k_count(CountKArgs a)
     const TAB ew = make_table<TAB>(slot + wid * p.cap_w, p.cap_w, &ctl[3 + 2 * wid]);
     unsigned wepoch = 0;
     const int nsmall = a.counters[C_SMALL_COUNT];
+    const int chunk = claim_chunk(nsmall, G * W);
     for (;;) {
         int base = 0;
-        if (lane == 0) base = atomicAdd(&a.counters[C_SMALL_NEXT], 32);
+        if (lane == 0) base = atomicAdd(&a.counters[C_SMALL_NEXT], chunk);
         base = __shfl_sync(0xffffffffu, base, 0);
         if (base >= nsmall) break;
-        const RunHdr mine = base + lane < nsmall ? a.small[base + lane] : none;
-        const int cnt = min(32, nsmall - base);
+        const RunHdr mine = lane < chunk && base + lane < nsmall ? a.small[base + lane] : none;
+        const int cnt = min(chunk, nsmall - base);
         for (int j = 0; j < cnt; ++j) {
             RunHdr h;
             h.c = __shfl_sync(0xffffffffu, mine.c, j);

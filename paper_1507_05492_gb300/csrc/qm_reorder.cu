@@ -119,6 +119,29 @@ __global__ void k_permute_labels(const int *__restrict__ labels, const int *__re
     }
 }
 
+// Label propagation as a detector (qm_label_propagation): labels start as the
+// caller's node ids, so a renumbered graph gives the same partition.
+__global__ void k_lpa_init_ids(int *lab, const int *__restrict__ inv, long long n)
+{
+    for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x)
+        lab[u] = inv ? inv[u] : (int)u;
+}
+
+// flag[c] = 1 when some node carries label c (c in [0, n)).
+__global__ void k_present(int *hist, long long n)
+{
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+        hist[c] = hist[c] > 0 ? 1 : 0;
+}
+
+// out[caller id] = rank of the node's final label among the labels present.
+__global__ void k_write_ranks(const int *__restrict__ lab, const int *__restrict__ rank, const int *__restrict__ inv,
+                              long long n, int *__restrict__ out)
+{
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x)
+        out[inv ? inv[j] : j] = rank[lab[j]];
+}
+
 static int grid_of(long long work, int threads, int num_sms, int per_sm)
 {
     long long g = (work + threads - 1) / threads;
@@ -131,6 +154,33 @@ int launch_permute_labels(const int *labels, const int *inv, long long n, int P,
 {
     k_permute_labels<<<grid_of(n * (long long)P, 512, num_sms, 8), 512, 0, s>>>(labels, inv, n, P, out);
     return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_label_propagation(const GraphDev &g, int rounds, int num_sms, cudaStream_t s, int *lab0, int *lab1,
+                             int *hist, int *tmp, size_t tmp_elems, int *out)
+{
+    const long long n = g.n;
+    const int g1 = grid_of(n, 512, num_sms, 8), gw = grid_of(n * 32, 256, num_sms, 8);
+    int L = 0;
+    k_lpa_init_ids<<<g1, 512, 0, s>>>(lab0, g.inv, n);
+    ++L;
+    for (int r = 0; r < rounds; ++r) {
+        k_lpa_round<<<gw, 256, 0, s>>>(g.row_ptr, g.col, n, lab0, lab1);
+        std::swap(lab0, lab1);
+        ++L;
+    }
+    if (cudaMemsetAsync(hist, 0, (size_t)(n + 1) * 4, s) != cudaSuccess) return -1;
+    if (cudaMemsetAsync(tmp, 0, tmp_elems * 4, s) != cudaSuccess) return -1;
+    k_count_ids<<<g1, 512, 0, s>>>(lab0, n, hist);
+    k_present<<<g1, 512, 0, s>>>(hist, n);
+    L += 2;
+    int *status = tmp + tmp_elems - 32, *counters = tmp + tmp_elems - 16;
+    const int l2 = scan_offsets(hist, (int)n, hist, tmp, counters, status, s);  // hist[n] = number of labels
+    if (l2 < 0) return -1;
+    L += l2;
+    k_write_ranks<<<g1, 512, 0, s>>>(lab0, hist, g.inv, n, out);
+    ++L;
+    return cudaGetLastError() == cudaSuccess ? L : -1;
 }
 
 int reorder_graph(const GraphDev &g, int rounds, int num_sms, cudaStream_t s, long long **row_ptr_out, int **col_out,

@@ -91,6 +91,7 @@ def _signatures(lib):
         "qm_get_tuning": [_P, _I32, _P],
         "qm_set_tuning": [_P, _I32, _P],
         "qm_autotune_batched": [_P, _P, _I32, _P, _P, _I32, S, _P, _P],
+        "qm_label_propagation": [_P, _I32, _P, S, _P, _P],
         "qm_get_batch_tuning": [_P, _I32, _P],
         "qm_set_batch_tuning": [_P, _I32, _P],
         "qm_last_error": [_P, ctypes.c_size_t],
@@ -349,6 +350,21 @@ def set_tuning(graph: Graph, K: int, threads: int, smem_bytes: int, big_communit
     """algorithm 0: one-kernel community pass; 1: expand + count (two phases)."""
     t = QmTuning(threads, smem_bytes, big_community, 0, algorithm)
     _check(lib().qm_set_tuning(graph.handle, int(K), ctypes.byref(t)), "qm_set_tuning")
+
+
+def label_propagation(graph: Graph, rounds: int = 10, device: bool = True, stream=None):
+    """qm_label_propagation: (labels int32[n] (cuda tensor, or numpy when
+    device=False), K')."""
+    if device:
+        out = torch.empty(graph.n, dtype=torch.int32, device="cuda")
+        ptr, where = out.data_ptr(), QM_DEVICE
+    else:
+        out = np.empty(graph.n, dtype=np.int32)
+        ptr, where = out.ctypes.data, QM_HOST
+    k = ctypes.c_int32()
+    _check(lib().qm_label_propagation(graph.handle, int(rounds), ptr, where, ctypes.byref(k),
+                                      _stream_ptr(stream)), "qm_label_propagation")
+    return out, int(k.value)
 
 
 def autotune_batched(graph: Graph, labels, K, truth=None, k_truth: int = 0, stream=None) -> dict:
