@@ -81,13 +81,14 @@ def recorded_traffic(kernel: str, workload: str):
             except ValueError:
                 break
             pos = end + 3
-            try:
-                rec = json.loads(text[start:end])
-            except ValueError:
-                continue
-            if (rec.get("kernel") == kernel and rec.get("workload") == workload
-                    and rec.get("source_hash") == want and rec.get("dram_bytes_per_launch") is not None):
-                return float(rec["dram_bytes_per_launch"])
+            for line in text[start:end].splitlines():  # one JSON record per line
+                try:
+                    rec = json.loads(line)
+                except ValueError:
+                    continue
+                if (rec.get("kernel") == kernel and rec.get("workload") == workload
+                        and rec.get("source_hash") == want and rec.get("dram_bytes_per_launch") is not None):
+                    return float(rec["dram_bytes_per_launch"])
     return None
 
 
@@ -407,6 +408,19 @@ def bench_headline(args, world, rank, local):
     b_alg = algorithmic_bytes(top, n, E, K, q)
     achieved = b_alg / (top_avg / 1e3) / 1e9
     b_step = 8.0 * E + 12.0 * n
+    # whole-pass DRAM traffic from the committed ncu records of every kernel of
+    # the step (null when any record is missing or the kernels changed since)
+    launches_per_step = {}
+    for tr in step_kernels:
+        for name, _ in tr:
+            launches_per_step[name] = launches_per_step.get(name, 0) + 1
+    pass_bytes = 0.0
+    for name, cnt in launches_per_step.items():
+        rec = recorded_traffic(name, args.workload)
+        if rec is None:
+            pass_bytes = None
+            break
+        pass_bytes += rec * cnt / args.steps
     res = dict(
         value=value, ms_per_step=ms_max / args.steps, launches=launches,
         e2e={"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * n,
@@ -416,7 +430,10 @@ def bench_headline(args, world, rank, local):
                   "kernel": top, "peak_kind": f"{peak_kind} (burst copy)",
                   "algorithmic_bytes_per_launch": b_alg, "kernel_ms": top_avg,
                   "step_algorithmic_bytes": b_step,
-                  "step_algorithmic_gbs": b_step / (ms_max / args.steps / 1e3) / 1e9},
+                  "step_algorithmic_gbs": b_step / (ms_max / args.steps / 1e3) / 1e9,
+                  "step_dram_bytes": pass_bytes,
+                  "step_dram_gbs": (pass_bytes / (ms_max / args.steps / 1e3) / 1e9) if pass_bytes else None,
+                  "step_dram_frac": (pass_bytes / (ms_max / args.steps / 1e3) / 1e9 / peak) if pass_bytes else None},
         clocks=clk,
         config={"workload": f"{args.workload}: LFR-style, n={n}, |E|={E}, K={K}, max degree {max_deg}, "
                             f"mean degree 20 target, mu=0.3, communities 20-1000, planted partition",
