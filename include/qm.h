@@ -62,6 +62,8 @@ typedef enum {
 } qm_status;
 
 typedef enum { QM_HOST = 0, QM_DEVICE = 1 } qm_mem;
+#define QM_HOST_PTR QM_HOST     /* alternative names of the two memory kinds */
+#define QM_DEVICE_PTR QM_DEVICE
 
 /* qm_load_graph flags */
 #define QM_VALIDATE 1u /* check symmetry, no self-loops, no repeated arcs, ids in range */
@@ -364,6 +366,8 @@ qm_status qm_trace_read(qm_trace_event *events, int32_t capacity, int32_t *count
 const char *qm_strerror(qm_status s);
 /* Copies the calling thread's last error message into buf (always NUL-terminated). */
 qm_status qm_last_error(char *buf, size_t len);
+/* The same as qm_last_error (the name the interface plan uses). */
+qm_status qm_last_error_detail(char *buf, size_t len);
 
 #ifdef __cplusplus
 }

@@ -400,6 +400,8 @@ qm_status qm_last_error(char *buf, size_t len)
     return QM_OK;
 }
 
+qm_status qm_last_error_detail(char *buf, size_t len) { return qm_last_error(buf, len); }
+
 int64_t qm_kernel_launches(void) { return g_launches.load(); }
 
 qm_status qm_trace_enable(int32_t on)

@@ -201,6 +201,12 @@ class Graph:
         self.n_edges = arcs // 2
         self.reordered = reorder
 
+    @classmethod
+    def from_csr(cls, row_ptr, col, **kwargs) -> "Graph":
+        """The same as Graph(row_ptr, col, ...): a symmetric CSR from torch tensors
+        (host or device) or numpy arrays."""
+        return cls(row_ptr, col, **kwargs)
+
     def info(self) -> dict:
         vals = [ctypes.c_int64() for _ in range(3)]
         nbytes = ctypes.c_size_t()
