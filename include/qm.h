@@ -291,6 +291,41 @@ qm_status qm_get_batch_tuning(const qm_graph *g, int32_t K, qm_tuning *t);
 qm_status qm_set_batch_tuning(const qm_graph *g, int32_t K, const qm_tuning *t);
 
 /*
+ * Sharded scoring -- the paper's decomposition of the no-ground-truth metrics
+ * by community (Sec. III-A): community c belongs to shard c mod P, each shard
+ * sums the terms of its own communities, and one sum over the shards gives
+ * the partition's values (the single reduction of the paper's processes).
+ * Each shard needs the whole graph and all labels (neighbours' communities
+ * and all community sizes enter the sums).  The partial sums are exact
+ * integers, so any split gives the bits of qm_score_partition.
+ *
+ *   qm_score_partition_part   shard `rank` of `nranks` (1..64) of one call of
+ *                             qm_score_partition (same arguments, no
+ *                             per-community output); fills *out.
+ *   qm_partials_combine       exact sum of `count` partials of the same graph
+ *                             and shard count, each shard at most once;
+ *                             host-only, touches no GPU.
+ *   qm_partial_finalize       the metrics from a partial that covers every
+ *                             shard (one small kernel on the current device).
+ * Errors: QM_EINVAL (ranks out of range, partials of different graphs or
+ * shard counts, a shard repeated or missing), plus those of
+ * qm_score_partition.
+ */
+#define QM_PARTIAL_WORDS 32
+typedef struct {
+    int64_t n_nodes, n_edges;
+    int32_t nranks;                   /* number of shards of the call */
+    int32_t reserved;
+    uint64_t ranks_mask;              /* shards summed into this partial: bit r = shard r */
+    uint64_t words[QM_PARTIAL_WORDS]; /* exact integer sums (opaque) */
+} qm_partial;
+
+qm_status qm_score_partition_part(const qm_graph *g, const int32_t *labels, int32_t K, qm_mem where,
+                                  int32_t rank, int32_t nranks, qm_partial *out, void *stream);
+qm_status qm_partials_combine(const qm_partial *parts, int32_t count, qm_partial *out);
+qm_status qm_partial_finalize(const qm_partial *p, qm_quality *out, void *stream);
+
+/*
  * qm_score_partition_noalloc -- qm_score_partition for callers that cannot let
  * a library allocate memory while it runs (no counterpart in the paper).
  *

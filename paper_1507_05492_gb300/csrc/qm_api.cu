@@ -556,8 +556,12 @@ qm_status qm_workspace_bytes(const qm_graph *g, int32_t K, int32_t with_compare,
 }
 
 // One plain scoring call on an already-leased workspace.
+// One scoring call.  A shard (shard_p > 1, two-phase pipeline only) scores the
+// communities c with c mod shard_p == shard_r and returns its exact partial
+// sums in gacc_out (QM_PARTIAL_WORDS words) instead of a result.
 static qm_status score_impl(qm_graph *g, const int32_t *labels, int32_t K, qm_mem where, qm_quality *out,
-                            const qm_percomm *pc, cudaStream_t s, const Shape &sh)
+                            const qm_percomm *pc, cudaStream_t s, const Shape &sh, int shard_r = 0,
+                            int shard_p = 1, uint64_t *gacc_out = nullptr)
 {
     const long long n = g->n;
     size_t need = sh.algo ? score2_ws_bytes(n, g->n_arcs, K) : score_ws_bytes(n, K);
@@ -569,7 +573,8 @@ static qm_status score_impl(qm_graph *g, const int32_t *labels, int32_t K, qm_me
     const bool pc_host = pc && where == QM_HOST;
     if (pc_host) need += al256((size_t)K * 8) * 8;
     Lease ws(g_pool.acquire(need, g->device, false));
-    Lease pin(g_pool.acquire(al256(sizeof(qm_quality)) + 256, g->device, true));
+    Lease pin(g_pool.acquire(al256(std::max(sizeof(qm_quality), (size_t)QM_PARTIAL_WORDS * 8)) + 256, g->device,
+                             true));
     if (!ws.b || !pin.b) return fail(QM_ENOMEM, "scratch allocation failed");
     ScoreWs w = sh.algo ? carve_score2_ws(ws.ptr(), n, g->n_arcs, K) : carve_score_ws(ws.ptr(), n, K);
     const int32_t *dl = labels;
@@ -598,12 +603,16 @@ static qm_status score_impl(qm_graph *g, const int32_t *labels, int32_t K, qm_me
             CK(cudaMemsetAsync(dp[k], 0, (size_t)K * 8, s));
         }
     }
-    const int L = sh.algo ? launch_score2(g->d, dl, K, w, sh, pc ? &pcd : nullptr, num_sms_of(g->device), s, tr)
+    const int L = sh.algo ? launch_score2(g->d, dl, K, w, sh, pc ? &pcd : nullptr, num_sms_of(g->device), s, tr,
+                                          shard_r, shard_p)
                           : launch_score(g->d, dl, K, w, sh, pc ? &pcd : nullptr, num_sms_of(g->device), s, tr);
     if (L < 0) return cuda_fail(cudaGetLastError(), "launch_score");
     g_launches += L;
     CK(cudaMemcpyAsync(pin.ptr(), w.status, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(pin.ptr() + 256, w.result, sizeof(qm_quality), cudaMemcpyDeviceToHost, s));
+    if (gacc_out)
+        CK(cudaMemcpyAsync(pin.ptr() + 256, w.gacc, QM_PARTIAL_WORDS * 8, cudaMemcpyDeviceToHost, s));
+    else
+        CK(cudaMemcpyAsync(pin.ptr() + 256, w.result, sizeof(qm_quality), cudaMemcpyDeviceToHost, s));
     if (pc_host) {
         void **dp = (void **)&pcd;
         for (int k = 0; k < 8; ++k)
@@ -616,7 +625,97 @@ static qm_status score_impl(qm_graph *g, const int32_t *labels, int32_t K, qm_me
     if (st & 2) return fail(QM_EOVERFLOW, "a community borders too many distinct communities");
     if (st & 4) return fail(QM_ETIMEOUT, "a staging copy did not complete within its wait limit");
     if (st) return fail(QM_ECUDA, "device status word set");
-    std::memcpy(out, pin.ptr() + 256, sizeof(qm_quality));
+    if (gacc_out) std::memcpy(gacc_out, pin.ptr() + 256, QM_PARTIAL_WORDS * 8);
+    else std::memcpy(out, pin.ptr() + 256, sizeof(qm_quality));
+    return QM_OK;
+}
+
+// ---------------------------------------------------------------- sharded scoring
+
+// The accumulator words: 7 sums of three limbs (value = L2 * 2^86 + L1 * 2^43 +
+// L0, L0 and L1 unsigned, L2 signed), then 5 unsigned 64-bit counters.
+static constexpr int PART_TRIPLES = 7, PART_U64_FIRST = 21, PART_U64_COUNT = 5;
+
+static __int128 part_limbs_get(const uint64_t *L)
+{
+    return (__int128)(int64_t)L[2] * ((__int128)1 << 86) + (__int128)L[1] * ((__int128)1 << 43) + (__int128)L[0];
+}
+
+static void part_limbs_put(uint64_t *L, __int128 v)
+{
+    const unsigned __int128 mask = (((unsigned __int128)1) << 43) - 1;
+    const unsigned __int128 u = (unsigned __int128)v;
+    L[0] = (uint64_t)(u & mask);
+    L[1] = (uint64_t)((u >> 43) & mask);
+    L[2] = (uint64_t)(int64_t)(v >> 86);
+}
+
+static uint64_t full_mask(int nranks) { return nranks >= 64 ? ~0ull : ((1ull << nranks) - 1ull); }
+
+qm_status qm_score_partition_part(const qm_graph *gc, const int32_t *labels, int32_t K, qm_mem where,
+                                  int32_t rank, int32_t nranks, qm_partial *out, void *stream)
+{
+    qm_graph *g = const_cast<qm_graph *>(gc);
+    if (!g || !labels || !out) return fail(QM_EINVAL, "null argument");
+    if (K < 1) return fail(QM_EINVAL, "K must be >= 1");
+    if (nranks < 1 || nranks > 64 || rank < 0 || rank >= nranks)
+        return fail(QM_EINVAL, "need 1 <= nranks <= 64 and 0 <= rank < nranks");
+    if (where != QM_HOST && where != QM_DEVICE) return fail(QM_EINVAL, "bad memory kind");
+    DeviceGuard dg(g->device);
+    Shape sh = shape_for(g, K, false);
+    if (sh.algo != 1) sh = resolve_plain(default_shape());  // shards run the two-phase pipeline
+    std::memset(out, 0, sizeof(*out));
+    const qm_status st = score_impl(g, labels, K, where, nullptr, nullptr, (cudaStream_t)stream, sh, rank, nranks,
+                                    out->words);
+    if (st != QM_OK) return st;
+    out->n_nodes = g->n;
+    out->n_edges = g->n_arcs / 2;
+    out->nranks = nranks;
+    out->ranks_mask = 1ull << rank;
+    return QM_OK;
+}
+
+qm_status qm_partials_combine(const qm_partial *parts, int32_t count, qm_partial *out)
+{
+    if (!parts || !out || count < 1) return fail(QM_EINVAL, "need count >= 1 partials and an output");
+    qm_partial r = parts[0];
+    for (int k = 0; k < PART_TRIPLES; ++k) part_limbs_put(r.words + 3 * k, part_limbs_get(r.words + 3 * k));
+    for (int i = 1; i < count; ++i) {
+        const qm_partial &p = parts[i];
+        if (p.n_nodes != r.n_nodes || p.n_edges != r.n_edges || p.nranks != r.nranks)
+            return fail(QM_EINVAL, "partials of different graphs or shard counts");
+        if (p.ranks_mask & r.ranks_mask) return fail(QM_EINVAL, "a shard is present twice");
+        for (int k = 0; k < PART_TRIPLES; ++k)
+            part_limbs_put(r.words + 3 * k, part_limbs_get(r.words + 3 * k) + part_limbs_get(p.words + 3 * k));
+        for (int k = 0; k < PART_U64_COUNT; ++k) r.words[PART_U64_FIRST + k] += p.words[PART_U64_FIRST + k];
+        r.ranks_mask |= p.ranks_mask;
+    }
+    *out = r;
+    return QM_OK;
+}
+
+qm_status qm_partial_finalize(const qm_partial *p, qm_quality *out, void *stream)
+{
+    if (!p || !out) return fail(QM_EINVAL, "null argument");
+    if (p->nranks < 1 || p->nranks > 64 || p->ranks_mask != full_mask(p->nranks))
+        return fail(QM_EINVAL, "the partial does not cover every shard");
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    cudaStream_t s = (cudaStream_t)stream;
+    Lease ws(g_pool.acquire(1024, dev, false));
+    Lease pin(g_pool.acquire(1024, dev, true));
+    if (!ws.b || !pin.b) return fail(QM_ENOMEM, "scratch allocation failed");
+    char *d = ws.ptr();
+    std::memcpy(pin.ptr(), p->words, QM_PARTIAL_WORDS * 8);
+    CK(cudaMemcpyAsync(d, pin.ptr(), QM_PARTIAL_WORDS * 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(d + 256, 0, 16, s));
+    if (launch_score_fin((const unsigned long long *)d, (const int *)(d + 256), p->n_nodes, p->n_edges,
+                         (qm_quality *)(d + 512), s) < 0)
+        return cuda_fail(cudaGetLastError(), "finalize launch");
+    g_launches += 1;
+    CK(cudaMemcpyAsync(pin.ptr() + 512, d + 512, sizeof(qm_quality), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::memcpy(out, pin.ptr() + 512, sizeof(qm_quality));
     return QM_OK;
 }
 

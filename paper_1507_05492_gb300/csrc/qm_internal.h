@@ -122,7 +122,12 @@ typedef void (*TraceFn)(const char *name, cudaStream_t s);
 int launch_score(const GraphDev &g, const int *labels, int K, const ScoreWs &ws, const Shape &sh,
                  const PerCommDev *pc, int num_sms, cudaStream_t s, TraceFn tr);
 int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws, const Shape &sh,
-                  const PerCommDev *pc, int num_sms, cudaStream_t s, TraceFn tr);
+                  const PerCommDev *pc, int num_sms, cudaStream_t s, TraceFn tr, int shard_r = 0,
+                  int shard_p = 1);
+// k_score_fin on an accumulator array of GS_COUNT words (a combined set of shard
+// partials): status must point at a zero int.  Returns 1 (launches) or -1.
+int launch_score_fin(const unsigned long long *gacc, const int *status, long long n, long long E, qm_quality *out,
+                     cudaStream_t s);
 int launch_compare(const int *truth, const int *found, long long n, int ka, int kb,
                    const CompareWs &ws, const Shape &sh, int num_sms, cudaStream_t s, TraceFn tr);
 int count_blocks_per_sm(const Shape &sh);

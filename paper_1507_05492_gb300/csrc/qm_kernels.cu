@@ -698,6 +698,14 @@ __global__ void k_scatter_deg(const int *__restrict__ labels, const long long *_
 // one contiguous range; otherwise a search over the members' arc offsets
 // finds the member of each arc.
 constexpr int EXPAND_THREADS = 256;
+
+// Community ownership of a sharded call (the decomposition of Sec. III-A:
+// community c belongs to process c mod P).  Unsharded calls pass P = 1.
+struct Shard {
+    int r;  // this shard
+    int p;  // number of shards
+    __device__ __forceinline__ bool owns(int c) const { return p == 1 || c % p == r; }
+};
 constexpr int EXPAND_UNROLL = 8;
 constexpr int EXPAND_MAX_SEGS = 6;
 
@@ -744,7 +752,8 @@ __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__re
                                                            const int *__restrict__ members,
                                                            const unsigned *__restrict__ aoff,
                                                            const int *__restrict__ start, long long n,
-                                                           int *inter, int *__restrict__ nbr, const int *status)
+                                                           int *inter, int *__restrict__ nbr, const int *status,
+                                                           Shard own)
 {
     __shared__ unsigned offs_s[EXPAND_THREADS / 32][33];
     __shared__ long long rs_s[EXPAND_THREADS / 32][32];
@@ -784,6 +793,7 @@ __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__re
                 const unsigned e_lo = offw[lo], e_hi = offw[hi];
                 if (e_lo == e_hi) continue;
                 const int c = cw[lo];
+                if (!own.owns(c)) continue;
                 if (c != cur_c) {
                     cur_c = c;
                     if (lane == 0) cbase = __ldg(&aoff[__ldg(&start[c])]);
@@ -801,6 +811,7 @@ __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__re
                 const unsigned e_lo = offw[m_lo], e_hi = offw[m_hi];
                 if (e_lo == e_hi) continue;
                 const int c = cw[m_lo];
+                if (!own.owns(c)) continue;
                 if (lane == 0) cbase = __ldg(&aoff[__ldg(&start[c])]);
                 cbase = __shfl_sync(0xffffffffu, cbase, 0);
                 expand_range(
@@ -823,7 +834,7 @@ __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__re
 // warp-aggregated.
 __global__ void k_classify(const int *start, const unsigned *aoff, const int *inter, int K, int warp_fill,
                            int block_fill, RunHdr *big, RunHdr *small, RunHdr *lng, int *counters,
-                           const int *status)
+                           const int *status, Shard own)
 {
     if (*status) return;
     const int lane = threadIdx.x & 31;
@@ -835,7 +846,7 @@ __global__ void k_classify(const int *start, const unsigned *aoff, const int *in
         if (cl < K) {
             const int c = (int)cl;
             const int s0 = start[c], s1 = start[c + 1];
-            if (s1 > s0) {
+            if (s1 > s0 && own.owns(c)) {
                 const unsigned a0 = aoff[s0];
                 h = RunHdr{c, a0, (unsigned)inter[c], aoff[s1] - a0};
                 cls = h.m > (unsigned)block_fill ? 2 : (h.m > (unsigned)warp_fill ? 0 : 1);
@@ -1024,7 +1035,7 @@ __device__ __forceinline__ void flush_score_threads(const ScoreAcc &acc, unsigne
 
 // FP64 terms of every community from the phase-B records, all in parallel.
 __global__ void k_score_terms(const int *start, const unsigned long long *rec, int K, long long E, PerCommDev pc,
-                              unsigned long long *g, const int *status)
+                              unsigned long long *g, const int *status, Shard own)
 {
     __shared__ unsigned long long red[72];
     if (*status) return;
@@ -1032,7 +1043,7 @@ __global__ void k_score_terms(const int *start, const unsigned long long *rec, i
     score_acc_zero(acc);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < K; c += gridDim.x * blockDim.x) {
         const long long size = start[c + 1] - start[c];
-        if (size == 0) continue;
+        if (size == 0 || !own.owns(c)) continue;
         double pen, qs, dens, contr, expn, cond;
         const unsigned long long *rc = rec + (size_t)c * REC_WORDS;
         terms_from_record(rc, size, E, acc, &pen, &qs, &dens, &contr, &expn, &cond);
@@ -1217,9 +1228,10 @@ ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K)
 //   k_hist -> scan (sizes) -> k_scatter_deg -> scan (member degrees = arc offsets)
 //   -> k_expand -> k_classify -> k_count -> k_score_terms -> k_score_fin
 int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws, const Shape &sh,
-                  const PerCommDev *pc, int num_sms, cudaStream_t s, TraceFn tr)
+                  const PerCommDev *pc, int num_sms, cudaStream_t s, TraceFn tr, int shard_r, int shard_p)
 {
     int launches = 0;
+    const Shard own{shard_r, shard_p};
     const long long n = g.n;
     const int hist_smem = (K <= 12288) ? K * 4 : 0;
     TRACE("k_hist");
@@ -1237,13 +1249,13 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
                             ws.counters, ws.scan_tmp, ws.status, s, tr);
     TRACE("k_expand");
     k_expand<<<num_sms * 8, EXPAND_THREADS, 0, s>>>(g.row_ptr, g.col, labels, ws.members, ws.aoff, ws.start, n,
-                                                    ws.inter, ws.nbr, ws.status);
+                                                    ws.inter, ws.nbr, ws.status, own);
     ++launches;
     const CountPlan cp = plan_count(sh.threads, sh.smem_bytes);
     TRACE("k_classify");
     k_classify<<<grid_for(K, 256, num_sms, 4), 256, 0, s>>>(ws.start, ws.aoff, ws.inter, K, cp.fill_w, cp.fill,
                                                             ws.hdr_big, ws.hdr_small, ws.hdr_long, ws.counters,
-                                                            ws.status);
+                                                            ws.status, own);
     ++launches;
     CountKArgs a;
     a.x.nbr = ws.nbr;
@@ -1271,12 +1283,22 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
     if (pc) pcd = *pc;
     TRACE("k_score_terms");
     k_score_terms<<<grid_for(K, 256, num_sms, 2), 256, 0, s>>>(ws.start, ws.rec, K, g.n_arcs / 2, pcd, ws.gacc,
-                                                               ws.status);
-    TRACE("k_score_fin");
-    k_score_fin<<<1, 32, 0, s>>>(ws.gacc, ws.status, n, g.n_arcs / 2, ws.result);
+                                                               ws.status, own);
+    ++launches;
+    if (shard_p == 1) {  // a shard's caller reads the partial sums instead
+        TRACE("k_score_fin");
+        k_score_fin<<<1, 32, 0, s>>>(ws.gacc, ws.status, n, g.n_arcs / 2, ws.result);
+        ++launches;
+    }
     TRACE(nullptr);
-    launches += 2;
     return cudaGetLastError() == cudaSuccess ? launches : -1;
+}
+
+int launch_score_fin(const unsigned long long *gacc, const int *status, long long n, long long E, qm_quality *out,
+                     cudaStream_t s)
+{
+    k_score_fin<<<1, 32, 0, s>>>(gacc, status, n, E, out);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
 int launch_compare(const int *truth, const int *found, long long n, int ka, int kb,

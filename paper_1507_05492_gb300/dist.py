@@ -80,3 +80,25 @@ def score_sharded(score_unit, units: int) -> list | None:
     ws, rank = world()
     local = {i: score_unit(i) for i in shard(units, ws, rank)}
     return gather_sharded(local, units)
+
+
+def score_partition_sharded(graph, labels, K: int, stream=None, part_fn=None, finalize_fn=None):
+    """One scoring call split over the ranks by community ownership, the
+    paper's own decomposition (Sec. III-A): rank r scores the communities
+    c with c mod world_size == r, the ranks exchange their exact partial sums
+    (one all-gather of 36 int64 words each, the single reduction of the
+    paper's processes), and every rank finalises the same total.  Every rank
+    holds the whole graph and all labels.  Bit-identical to qm.score.
+
+    part_fn(graph, labels, K, rank, world_size) and finalize_fn(partial) default
+    to the library calls; tests pass stand-ins to run the exchange on CPU."""
+    from . import qm
+    ws, rank = world()
+    part = (part_fn or qm.score_part)(graph, labels, K, rank, ws)
+    if ws > 1:
+        a = torch.from_numpy(qm.part_to_array(part)).to(_device())
+        bufs = [torch.empty_like(a) for _ in range(ws)]
+        dist.all_gather(bufs, a)
+        part = qm.combine_parts([qm.part_from_array(b.cpu().numpy()) for b in bufs])
+    return (finalize_fn or (lambda p: qm.finalize_part(p, stream)))(part)
+

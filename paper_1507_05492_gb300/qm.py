@@ -51,6 +51,15 @@ class QmCompare(ctypes.Structure):
         (n, ctypes.c_double) for n in ("vi", "nmi", "f_measure", "nvd", "ri", "ari", "ji")]
 
 
+PARTIAL_WORDS = 32
+
+
+class QmPartial(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int64), ("n_edges", ctypes.c_int64), ("nranks", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("ranks_mask", ctypes.c_uint64),
+                ("words", ctypes.c_uint64 * PARTIAL_WORDS)]
+
+
 class QmPercomm(ctypes.Structure):
     _fields_ = [(n, ctypes.c_void_p) for n in (
         "size", "intra_edges", "inter_edges", "intra_density", "contraction", "expansion",
@@ -92,6 +101,9 @@ def _signatures(lib):
         "qm_set_tuning": [_P, _I32, _P],
         "qm_autotune_batched": [_P, _P, _I32, _P, _P, _I32, S, _P, _P],
         "qm_label_propagation": [_P, _I32, _P, S, _P, _P],
+        "qm_score_partition_part": [_P, _P, _I32, S, _I32, _I32, _P, _P],
+        "qm_partials_combine": [_P, _I32, _P],
+        "qm_partial_finalize": [_P, _P, _P],
         "qm_get_batch_tuning": [_P, _I32, _P],
         "qm_set_batch_tuning": [_P, _I32, _P],
         "qm_last_error": [_P, ctypes.c_size_t],
@@ -356,6 +368,52 @@ def set_tuning(graph: Graph, K: int, threads: int, smem_bytes: int, big_communit
     """algorithm 0: one-kernel community pass; 1: expand + count (two phases)."""
     t = QmTuning(threads, smem_bytes, big_community, 0, algorithm)
     _check(lib().qm_set_tuning(graph.handle, int(K), ctypes.byref(t)), "qm_set_tuning")
+
+
+def score_part(graph: Graph, labels, K: int, rank: int, nranks: int, stream=None) -> QmPartial:
+    """qm_score_partition_part: the exact partial sums of shard `rank` of
+    `nranks` (communities c with c mod nranks == rank, Sec. III-A)."""
+    ptr, where, keep = _labels_arg(labels)
+    out = QmPartial()
+    rc = lib().qm_score_partition_part(graph.handle, ptr, int(K), where, int(rank), int(nranks),
+                                       ctypes.byref(out), _stream_ptr(stream))
+    del keep
+    _check(rc, "qm_score_partition_part")
+    return out
+
+
+def combine_parts(parts) -> QmPartial:
+    """qm_partials_combine: exact sum of partials (host only, no GPU needed)."""
+    parts = list(parts)
+    arr = (QmPartial * len(parts))(*parts)
+    out = QmPartial()
+    _check(lib().qm_partials_combine(arr, len(parts), ctypes.byref(out)), "qm_partials_combine")
+    return out
+
+
+def finalize_part(part: QmPartial, stream=None) -> dict:
+    """qm_partial_finalize: the metrics of a partial that covers every shard."""
+    out = QmQuality()
+    _check(lib().qm_partial_finalize(ctypes.byref(part), ctypes.byref(out), _stream_ptr(stream)),
+           "qm_partial_finalize")
+    return _struct_dict(out)
+
+
+def part_to_array(part: QmPartial) -> np.ndarray:
+    """The partial as int64[4 + PARTIAL_WORDS] (for transport between processes)."""
+    head = np.array([part.n_nodes, part.n_edges, part.nranks, 0], np.int64)
+    head[3] = np.array([part.ranks_mask], np.uint64).view(np.int64)[0]
+    words = np.frombuffer(bytes(part.words), dtype=np.uint64).view(np.int64)
+    return np.concatenate([head, words])
+
+
+def part_from_array(a) -> QmPartial:
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.int64))
+    p = QmPartial()
+    p.n_nodes, p.n_edges, p.nranks = int(a[0]), int(a[1]), int(a[2])
+    p.ranks_mask = int(a[3:4].view(np.uint64)[0])
+    ctypes.memmove(p.words, a[4:4 + PARTIAL_WORDS].view(np.uint64).tobytes(), 8 * PARTIAL_WORDS)
+    return p
 
 
 def label_propagation(graph: Graph, rounds: int = 10, device: bool = True, stream=None):
