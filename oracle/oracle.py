@@ -63,9 +63,10 @@ def _load():
     lib.oq_score_bruteforce.argtypes = [p, p, i64, p, i32, p]
     lib.oq_score_communities.argtypes = [p, p, i64, p, i32, p, i64, p, p]
     lib.oq_label_propagation.argtypes = [p, p, i64, i32, p, p]
+    lib.oq_score_weighted.argtypes = [p, p, p, i64, p, i32, p]
     for f in (lib.oq_validate_graph, lib.oq_score, lib.oq_compare, lib.oq_pairs_bruteforce,
               lib.oq_compare_bruteforce, lib.oq_score_bruteforce, lib.oq_score_communities,
-              lib.oq_label_propagation):
+              lib.oq_label_propagation, lib.oq_score_weighted):
         f.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -179,6 +180,20 @@ def score_communities(row_ptr, col, labels, K: int, ids) -> dict:
                                         _ptr(ids), m, _ptr(i64), _ptr(dbl)), "score_communities")
     return dict(size=i64[:, 0], intra_edges=i64[:, 1], inter_edges=i64[:, 2], distinct_neighbours=i64[:, 3],
                 qds_term=dbl[:, 0], split=dbl[:, 1])
+
+
+def score_weighted(row_ptr, col, weight, labels, K: int) -> dict:
+    """Eqs. (8)-(9) on a weighted graph: edge amounts weighted, densities
+    unweighted (the paper's note on the weighted case)."""
+    row_ptr = _as(row_ptr, np.int64)
+    col = _as(col, np.int32)
+    weight = _as(weight, np.float64)
+    labels = _as(labels, np.int32)
+    dbl = np.zeros(5, np.float64)
+    _check(_load().oq_score_weighted(_ptr(row_ptr), _ptr(col), _ptr(weight), len(row_ptr) - 1, _ptr(labels),
+                                     int(K), _ptr(dbl)), "score_weighted")
+    return dict(modularity=float(dbl[0]), modularity_density=float(dbl[1]), cond_modularity=float(dbl[2]),
+                cond_modularity_density=float(dbl[3]), total_weight=float(dbl[4]))
 
 
 def label_propagation(row_ptr, col, rounds: int):

@@ -18,6 +18,8 @@
  *   Sec. II-B.1  Eq. (8) modularity Q              -> oq_score
  *   Sec. II-B.2  Eq. (9) modularity density Qds    -> oq_score
  *   Sec. II-B.3  six per-community measures        -> oq_score
+ *   weighted graphs (the note beside Eq. 9)        -> oq_score_weighted
+ *   label propagation (the detector family of Sec. I, IV-C) -> oq_label_propagation
  *
  * Readings taken where the paper is silent:
  *   - log is the natural log (Eq. 1);
@@ -702,4 +704,120 @@ int oq_label_propagation(const int64_t *row_ptr, const int32_t *col, int64_t n, 
     *k_out = k;
     free(cur); free(nxt); free(rank);
     return OQ_OK;
+}
+
+/*
+ * oq_score_weighted -- Eq. (8) and Eq. (9) on a weighted undirected graph, in
+ * the reading the paper's note on the weighted case gives: every edge count
+ * that measures amount (|E|, |E_c^in|, |E_c^out|, |E_ci,cj| outside the
+ * densities) becomes a sum of edge weights, while the densities d_c and
+ * d_ci,cj keep the unweighted counts, so that they stay at most 1:
+ *   Q_w   = sum_c [ W_c^in / W - ((2 W_c^in + W_c^out) / (2W))^2 ]
+ *   Qds_w = sum_ci [ W_ci^in / W d_ci - ((2 W_ci^in + W_ci^out) / (2W) d_ci)^2
+ *                    - sum_{cj != ci} W_ci,cj / (2W) d_ci,cj ]
+ * with W the total edge weight, d_c = 2|E_c^in| / (|c|(|c|-1)) and
+ * d_ci,cj = |E_ci,cj| / (|ci||cj|).  Edges are visited once (v > u) with the
+ * weight stored on arc (u, v); weight[] runs parallel to col[].
+ *   dbl[0] Q_w, dbl[1] Qds_w, dbl[2] sum |terms| of Q_w, dbl[3] sum |terms| of Qds_w,
+ *   dbl[4] W
+ * Returns OQ_EINVAL for a non-positive total weight or a bad label.
+ */
+typedef struct {
+    uint64_t key;
+    long double w;
+} oq_wkey;
+
+static int cmp_wkey(const void *a, const void *b)
+{
+    uint64_t x = ((const oq_wkey *)a)->key, y = ((const oq_wkey *)b)->key;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+int oq_score_weighted(const int64_t *row_ptr, const int32_t *col, const double *weight, int64_t n,
+                      const int32_t *label, int32_t K, double *dbl)
+{
+    if (n < 1 || K < 1)
+        return OQ_EINVAL;
+    for (int64_t u = 0; u < n; u++)
+        if (label[u] < 0 || label[u] >= K)
+            return OQ_EINVAL;
+    const int64_t nnz = row_ptr[n];
+    if (nnz <= 0 || (nnz & 1))
+        return OQ_EINVAL;
+    const int64_t E = nnz / 2;
+    int64_t *size = (int64_t *)calloc((size_t)K, sizeof(int64_t));
+    int64_t *ein = (int64_t *)calloc((size_t)K, sizeof(int64_t));
+    long double *win = (long double *)calloc((size_t)K, sizeof(long double));
+    long double *wout = (long double *)calloc((size_t)K, sizeof(long double));
+    long double *split = (long double *)calloc((size_t)K, sizeof(long double));
+    oq_wkey *keys = (oq_wkey *)malloc((size_t)E * sizeof(oq_wkey));
+    if (!size || !ein || !win || !wout || !split || !keys) {
+        free(size); free(ein); free(win); free(wout); free(split); free(keys);
+        return OQ_ENOMEM;
+    }
+    for (int64_t u = 0; u < n; u++)
+        size[label[u]]++;
+    long double W = 0.0L;
+    int64_t nkeys = 0;
+    for (int64_t u = 0; u < n; u++) {
+        const int32_t lu = label[u];
+        for (int64_t k = row_ptr[u]; k < row_ptr[u + 1]; k++) {
+            const int32_t v = col[k];
+            if (v <= u)
+                continue;
+            const long double w = (long double)weight[k];
+            W += w;
+            const int32_t lv = label[v];
+            if (lu == lv) {
+                ein[lu]++;
+                win[lu] += w;
+            } else {
+                wout[lu] += w;
+                wout[lv] += w;
+                const uint64_t a = (uint64_t)(lu < lv ? lu : lv), b = (uint64_t)(lu < lv ? lv : lu);
+                keys[nkeys].key = (a << 32) | b;
+                keys[nkeys].w = w;
+                nkeys++;
+            }
+        }
+    }
+    int rc = W > 0.0L ? OQ_OK : OQ_EINVAL;
+    /* per unordered pair: the count |E_ci,cj| and the weight W_ci,cj */
+    qsort(keys, (size_t)nkeys, sizeof(oq_wkey), cmp_wkey);
+    for (int64_t s = 0; s < nkeys && rc == OQ_OK;) {
+        int64_t t = s;
+        long double wij = 0.0L;
+        while (t < nkeys && keys[t].key == keys[s].key) {
+            wij += keys[t].w;
+            t++;
+        }
+        const long double cnt = (long double)(t - s);
+        const int32_t ci = (int32_t)(keys[s].key >> 32), cj = (int32_t)(keys[s].key & 0xffffffffu);
+        const long double term = (wij / (2.0L * W)) * (cnt / ((long double)size[ci] * (long double)size[cj]));
+        split[ci] += term;
+        split[cj] += term;
+        s = t;
+    }
+    oq_sum q = {0, 0}, qabs = {0, 0}, qds = {0, 0}, qdsabs = {0, 0};
+    for (int32_t c = 0; c < K && rc == OQ_OK; c++) {
+        if (size[c] == 0)
+            continue;
+        const long double s = (long double)size[c];
+        const long double fin = win[c] / W, fvol = (2.0L * win[c] + wout[c]) / (2.0L * W);
+        sum_add(&q, fin - fvol * fvol);
+        sum_add(&qabs, fabsl(fin) + fvol * fvol);
+        const long double d = size[c] > 1 ? (2.0L * (long double)ein[c]) / (s * (s - 1.0L)) : 0.0L;
+        const long double t1 = fin * d, t2 = fvol * d;
+        sum_add(&qds, t1 - t2 * t2 - split[c]);
+        sum_add(&qdsabs, fabsl(t1) + t2 * t2 + split[c]);
+    }
+    if (rc == OQ_OK) {
+        dbl[0] = (double)sum_get(&q);
+        dbl[1] = (double)sum_get(&qds);
+        dbl[2] = (double)sum_get(&qabs);
+        dbl[3] = (double)sum_get(&qdsabs);
+        dbl[4] = (double)W;
+    }
+    free(size); free(ein); free(win); free(wout); free(split); free(keys);
+    return rc;
 }
