@@ -104,6 +104,27 @@ qm_status qm_load_graph(const int64_t *row_ptr, const int32_t *col, int64_t n_no
                         int64_t n_arcs, qm_mem where, unsigned flags, void *stream,
                         qm_graph **out);
 
+/*
+ * qm_load_graph_weighted -- qm_load_graph for a weighted undirected graph:
+ * weight[k] (float32, parallel to col, same memory kind) is the weight of arc
+ * k; arcs (u,v) and (v,u) must carry the same weight (checked with
+ * QM_VALIDATE).  Every weight must be 0 or in [2^-20, 2^20), so that it is an
+ * exact fixed-point integer w * 2^43 and every weight sum is exact; the total
+ * weight W must be positive.  qm_score_partition (and the sharded calls) then
+ * return Q and Qds in the paper's weighted reading (the note beside Eq. 9):
+ *   Q_w   = sum_c [ W_c^in / W - ((2 W_c^in + W_c^out) / (2W))^2 ]
+ *   Qds_w = sum_ci [ W_ci^in / W d_ci - ((2 W_ci^in + W_ci^out) / (2W) d_ci)^2
+ *                    - sum_{cj != ci} W_ci,cj / (2W) d_ci,cj ]
+ * with the densities d_ci and d_ci,cj and the six measures of Sec. II-B.3
+ * still counting edges (unweighted).  The batched calls, the one-kernel
+ * pipeline and qm_score_partition_noalloc refuse weighted graphs (QM_EINVAL);
+ * qm_label_propagation ignores the weights.  QM_REORDER is supported.
+ * Costs 4 bytes per arc more on the device.
+ * Errors: those of qm_load_graph, and QM_EINVAL for a weight out of range,
+ * asymmetric weights or a zero total.
+ */
+qm_status qm_load_graph_weighted(const int64_t *row_ptr, const int32_t *col, const float *weight, int64_t n_nodes,
+                                 int64_t n_arcs, qm_mem where, unsigned flags, void *stream, qm_graph **out);
 qm_status qm_free_graph(qm_graph *g);
 
 /* Sizes of a loaded graph; any output pointer may be NULL. */
@@ -315,7 +336,7 @@ qm_status qm_set_batch_tuning(const qm_graph *g, int32_t K, const qm_tuning *t);
 typedef struct {
     int64_t n_nodes, n_edges;
     int32_t nranks;                   /* number of shards of the call */
-    int32_t reserved;
+    int32_t flags;                    /* bit 0: a weighted graph's partial */
     uint64_t ranks_mask;              /* shards summed into this partial: bit r = shard r */
     uint64_t words[QM_PARTIAL_WORDS]; /* exact integer sums (opaque) */
 } qm_partial;

@@ -279,6 +279,7 @@ struct qm_graph {
     long long *row_ptr;
     int *col;
     int *inv = nullptr;  // QM_REORDER: new node id -> caller's node id (else null)
+    float *wt = nullptr; // weighted graph: edge weights parallel to col (else null)
     long long n, n_arcs, max_degree;
     size_t bytes;
     std::mutex mu;
@@ -367,6 +368,7 @@ static Shape shape_for(qm_graph *g, int K, bool batched)
     auto &m = batched ? g->tuning_batch : g->tuning;
     auto it = m.find(bucket_of(g->n, g->n_arcs, K));
     Shape s = it != m.end() ? it->second : (batched ? default_batch_shape() : default_shape());
+    if (!batched && g->wt && s.algo == 0) s = default_shape();  // weighted graphs: two-phase pipeline only
     return batched ? resolve_batched(s) : resolve_plain(s);
 }
 
@@ -424,8 +426,8 @@ qm_status qm_trace_read(qm_trace_event *events, int32_t capacity, int32_t *count
     return QM_OK;
 }
 
-qm_status qm_load_graph(const int64_t *row_ptr, const int32_t *col, int64_t n_nodes, int64_t n_arcs,
-                        qm_mem where, unsigned flags, void *stream, qm_graph **out)
+static qm_status load_impl(const int64_t *row_ptr, const int32_t *col, const float *weight, int64_t n_nodes,
+                           int64_t n_arcs, qm_mem where, unsigned flags, void *stream, qm_graph **out)
 {
     if (!out || !row_ptr || !col) return fail(QM_EINVAL, "null argument");
     *out = nullptr;
@@ -455,6 +457,7 @@ qm_status qm_load_graph(const int64_t *row_ptr, const int32_t *col, int64_t n_no
     auto cleanup = [&]() {
         cudaFree(g->row_ptr);
         cudaFree(g->col);
+        cudaFree(g->wt);
     };
     const cudaMemcpyKind kind = where == QM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     e = cudaMemcpyAsync(g->row_ptr, row_ptr, (size_t)(n_nodes + 1) * 8, kind, s);
@@ -498,10 +501,48 @@ qm_status qm_load_graph(const int64_t *row_ptr, const int32_t *col, int64_t n_no
     g->max_degree = (long long)*(unsigned long long *)(pin.ptr() + 64);
     g->d.max_degree = g->max_degree;
     g->bytes = (size_t)(n_nodes + 1) * 8 + (size_t)n_arcs * 4;
+    if (weight) {
+        e = cudaMalloc(&g->wt, (size_t)n_arcs * 4);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g->wt, weight, (size_t)n_arcs * 4, kind, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ws.ptr(), 0, 256, s);
+        if (e != cudaSuccess) {
+            cleanup();
+            return cuda_fail(e, "weights");
+        }
+        unsigned long long *lim = (unsigned long long *)(ws.ptr() + 128);
+        const int LW = launch_weight_check(g->d, g->wt, (flags & QM_VALIDATE) ? 1 : 0, status, lim,
+                                           num_sms_of(dev), s);
+        e = LW < 0 ? cudaGetLastError() : cudaMemcpyAsync(pin.ptr(), ws.ptr(), 256, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            cleanup();
+            return cuda_fail(e, "weight check");
+        }
+        g_launches += LW;
+        const int wst = *(int *)pin.ptr();
+        const uint64_t *L = (const uint64_t *)(pin.ptr() + 128);
+        const __int128 two_w = (__int128)(int64_t)L[2] * ((__int128)1 << 86) + (__int128)L[1] * ((__int128)1 << 43) +
+                               (__int128)L[0];
+        const char *why = (wst & 2)   ? "edge weights must be 0 or in [2^-20, 2^20)"
+                          : (wst & 4) ? "edge weights must be symmetric (arc (u,v) and arc (v,u) equal)"
+                          : two_w <= 0 ? "the total edge weight must be positive"
+                          : (two_w & 1) ? "edge weights must be symmetric (odd fixed-point total)"
+                                        : nullptr;
+        if (why) {
+            cleanup();
+            return fail(QM_EINVAL, why);
+        }
+        const unsigned __int128 w_fx = (unsigned __int128)(two_w / 2);
+        g->d.wt = g->wt;
+        g->d.w_lo = (unsigned long long)w_fx;
+        g->d.w_hi = (unsigned long long)(w_fx >> 64);
+        g->bytes += (size_t)n_arcs * 4;
+    }
     if (flags & QM_REORDER) {
         long long *row2 = nullptr;
         int *col2 = nullptr, *inv = nullptr, L = 0;
-        const int r = reorder_graph(g->d, QM_REORDER_ROUNDS, num_sms_of(dev), s, &row2, &col2, &inv, &L);
+        float *wt2 = nullptr;
+        const int r = reorder_graph(g->d, QM_REORDER_ROUNDS, num_sms_of(dev), s, &row2, &col2, &inv, &L, &wt2);
         if (r != 0) {
             cleanup();
             return cuda_fail((cudaError_t)(-r), "graph reorder");
@@ -515,10 +556,28 @@ qm_status qm_load_graph(const int64_t *row_ptr, const int32_t *col, int64_t n_no
         g->d.row_ptr = row2;
         g->d.col = col2;
         g->d.inv = inv;
+        if (g->wt) {
+            cudaFree(g->wt);
+            g->wt = wt2;
+            g->d.wt = wt2;
+        }
         g->bytes += (size_t)n_nodes * 4;
     }
     *out = g.release();
     return QM_OK;
+}
+
+qm_status qm_load_graph(const int64_t *row_ptr, const int32_t *col, int64_t n_nodes, int64_t n_arcs,
+                        qm_mem where, unsigned flags, void *stream, qm_graph **out)
+{
+    return load_impl(row_ptr, col, nullptr, n_nodes, n_arcs, where, flags, stream, out);
+}
+
+qm_status qm_load_graph_weighted(const int64_t *row_ptr, const int32_t *col, const float *weight, int64_t n_nodes,
+                                 int64_t n_arcs, qm_mem where, unsigned flags, void *stream, qm_graph **out)
+{
+    if (!weight) return fail(QM_EINVAL, "null weights");
+    return load_impl(row_ptr, col, weight, n_nodes, n_arcs, where, flags, stream, out);
 }
 
 qm_status qm_free_graph(qm_graph *g)
@@ -528,6 +587,7 @@ qm_status qm_free_graph(qm_graph *g)
     cudaFree(g->row_ptr);
     cudaFree(g->col);
     cudaFree(g->inv);
+    cudaFree(g->wt);
     delete g;
     return QM_OK;
 }
@@ -548,7 +608,8 @@ static size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 qm_status qm_workspace_bytes(const qm_graph *g, int32_t K, int32_t with_compare, int32_t k_truth, size_t *bytes)
 {
     if (!g || !bytes || K < 1 || (with_compare && k_truth < 1)) return fail(QM_EINVAL, "bad argument");
-    size_t b = std::max(score_ws_bytes(g->n, K), score2_ws_bytes(g->n, g->n_arcs, K)) + al256((size_t)g->n * 4);
+    size_t b = std::max(score_ws_bytes(g->n, K), score2_ws_bytes(g->n, g->n_arcs, K, g->wt != nullptr)) +
+               al256((size_t)g->n * 4);
     if (g->inv) b += al256((size_t)g->n * 4);
     if (with_compare) b += compare_ws_bytes(g->n, k_truth, K) + al256((size_t)g->n * 4);
     *bytes = b;
@@ -564,7 +625,8 @@ static qm_status score_impl(qm_graph *g, const int32_t *labels, int32_t K, qm_me
                             int shard_p = 1, uint64_t *gacc_out = nullptr)
 {
     const long long n = g->n;
-    size_t need = sh.algo ? score2_ws_bytes(n, g->n_arcs, K) : score_ws_bytes(n, K);
+    const bool weighted = g->wt != nullptr;
+    size_t need = sh.algo ? score2_ws_bytes(n, g->n_arcs, K, weighted) : score_ws_bytes(n, K);
     const size_t lab_off = need;
     if (where == QM_HOST) need += al256((size_t)n * 4);
     const size_t perm_off = need;
@@ -576,7 +638,7 @@ static qm_status score_impl(qm_graph *g, const int32_t *labels, int32_t K, qm_me
     Lease pin(g_pool.acquire(al256(std::max(sizeof(qm_quality), (size_t)QM_PARTIAL_WORDS * 8)) + 256, g->device,
                              true));
     if (!ws.b || !pin.b) return fail(QM_ENOMEM, "scratch allocation failed");
-    ScoreWs w = sh.algo ? carve_score2_ws(ws.ptr(), n, g->n_arcs, K) : carve_score_ws(ws.ptr(), n, K);
+    ScoreWs w = sh.algo ? carve_score2_ws(ws.ptr(), n, g->n_arcs, K, weighted) : carve_score_ws(ws.ptr(), n, K);
     const int32_t *dl = labels;
     if (where == QM_HOST) {
         dl = (const int32_t *)(ws.ptr() + lab_off);
@@ -633,8 +695,11 @@ static qm_status score_impl(qm_graph *g, const int32_t *labels, int32_t K, qm_me
 // ---------------------------------------------------------------- sharded scoring
 
 // The accumulator words: 7 sums of three limbs (value = L2 * 2^86 + L1 * 2^43 +
-// L0, L0 and L1 unsigned, L2 signed), then 5 unsigned 64-bit counters.
-static constexpr int PART_TRIPLES = 7, PART_U64_FIRST = 21, PART_U64_COUNT = 5;
+// L0, L0 and L1 unsigned, L2 signed) at words 0..20, 5 unsigned 64-bit
+// counters at 21..25, and one more three-limb sum (Q of a weighted graph) at
+// 26..28.
+static constexpr int PART_TRIPLE_AT[] = {0, 3, 6, 9, 12, 15, 18, 26};
+static constexpr int PART_U64_FIRST = 21, PART_U64_COUNT = 5;
 
 static __int128 part_limbs_get(const uint64_t *L)
 {
@@ -671,6 +736,7 @@ qm_status qm_score_partition_part(const qm_graph *gc, const int32_t *labels, int
     out->n_nodes = g->n;
     out->n_edges = g->n_arcs / 2;
     out->nranks = nranks;
+    out->flags = g->wt ? 1 : 0;
     out->ranks_mask = 1ull << rank;
     return QM_OK;
 }
@@ -679,14 +745,14 @@ qm_status qm_partials_combine(const qm_partial *parts, int32_t count, qm_partial
 {
     if (!parts || !out || count < 1) return fail(QM_EINVAL, "need count >= 1 partials and an output");
     qm_partial r = parts[0];
-    for (int k = 0; k < PART_TRIPLES; ++k) part_limbs_put(r.words + 3 * k, part_limbs_get(r.words + 3 * k));
+    for (int t : PART_TRIPLE_AT) part_limbs_put(r.words + t, part_limbs_get(r.words + t));
     for (int i = 1; i < count; ++i) {
         const qm_partial &p = parts[i];
-        if (p.n_nodes != r.n_nodes || p.n_edges != r.n_edges || p.nranks != r.nranks)
+        if (p.n_nodes != r.n_nodes || p.n_edges != r.n_edges || p.nranks != r.nranks || p.flags != r.flags)
             return fail(QM_EINVAL, "partials of different graphs or shard counts");
         if (p.ranks_mask & r.ranks_mask) return fail(QM_EINVAL, "a shard is present twice");
-        for (int k = 0; k < PART_TRIPLES; ++k)
-            part_limbs_put(r.words + 3 * k, part_limbs_get(r.words + 3 * k) + part_limbs_get(p.words + 3 * k));
+        for (int t : PART_TRIPLE_AT)
+            part_limbs_put(r.words + t, part_limbs_get(r.words + t) + part_limbs_get(p.words + t));
         for (int k = 0; k < PART_U64_COUNT; ++k) r.words[PART_U64_FIRST + k] += p.words[PART_U64_FIRST + k];
         r.ranks_mask |= p.ranks_mask;
     }
@@ -710,7 +776,7 @@ qm_status qm_partial_finalize(const qm_partial *p, qm_quality *out, void *stream
     CK(cudaMemcpyAsync(d, pin.ptr(), QM_PARTIAL_WORDS * 8, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(d + 256, 0, 16, s));
     if (launch_score_fin((const unsigned long long *)d, (const int *)(d + 256), p->n_nodes, p->n_edges,
-                         (qm_quality *)(d + 512), s) < 0)
+                         (qm_quality *)(d + 512), p->flags & 1, s) < 0)
         return cuda_fail(cudaGetLastError(), "finalize launch");
     g_launches += 1;
     CK(cudaMemcpyAsync(pin.ptr() + 512, d + 512, sizeof(qm_quality), cudaMemcpyDeviceToHost, s));
@@ -889,6 +955,7 @@ static qm_status evaluate_batched(qm_graph *g, const int32_t *labels, int32_t P,
                                   qm_compare *out_c, cudaStream_t s, const Shape *force = nullptr)
 {
     if (!g || !labels || !K || P < 1) return fail(QM_EINVAL, "bad argument");
+    if (g->wt) return fail(QM_EINVAL, "weighted graphs are scored by qm_score_partition and the sharded calls");
     if ((flags & 2) && (!truth || kt < 1)) return fail(QM_EINVAL, "truth labels required");
     if (where != QM_HOST && where != QM_DEVICE) return fail(QM_EINVAL, "bad memory kind");
     DeviceGuard dg(g->device);
@@ -1007,6 +1074,7 @@ qm_status qm_score_graphs_batched(const qm_graph *const *graphs, const int32_t *
     size_t total_labels = 0;
     for (int i = 0; i < count; ++i) {
         if (!graphs[i] || !labels[i] || K[i] < 1) return fail(QM_EINVAL, "bad graph, labels or K");
+        if (graphs[i]->wt) return fail(QM_EINVAL, "weighted graphs are scored by qm_score_partition and the sharded calls");
         if (graphs[i]->device != dev) return fail(QM_EINVAL, "all graphs must live on one device");
         d.n_max = std::max(d.n_max, graphs[i]->n);
         d.k_max = std::max(d.k_max, K[i]);
@@ -1170,6 +1238,7 @@ qm_status qm_autotune_batched(const qm_graph *gc, const int32_t *labels, int32_t
 {
     qm_graph *g = const_cast<qm_graph *>(gc);
     if (!g || !labels || !K || P < 1) return fail(QM_EINVAL, "bad argument");
+    if (g->wt) return fail(QM_EINVAL, "weighted graphs are scored by qm_score_partition and the sharded calls");
     if (truth && k_truth < 1) return fail(QM_EINVAL, "k_truth must be >= 1");
     DeviceGuard dg(g->device);
     cudaStream_t s = (cudaStream_t)stream;
@@ -1262,6 +1331,7 @@ qm_status qm_autotune(const qm_graph *gc, const int32_t *labels, int32_t K, qm_m
         for (int sm : smem_c)
             for (int bg : big_c) {
                 if (al == 1 && bg != big_c[0]) continue;  // the two-phase path has no size split
+                if (al == 0 && g->wt) continue;           // weighted graphs: two-phase pipeline only
                 Shape sh;
                 sh.threads = th;
                 sh.smem_bytes = sm;

@@ -285,7 +285,8 @@ __device__ __forceinline__ void score_acc_add(ScoreAcc &d, const ScoreAcc &s)
 enum {
     GS_QDS_SELF = 0, GS_QDS_PAIR = 3, GS_DENS = 6, GS_CONTR = 9, GS_EXPN = 12, GS_COND = 15,
     GS_VOL2 = 18, GS_EIN = 21, GS_EOUT = 22, GS_NONEMPTY = 23, GS_SLOTS = 24, GS_CNT2 = 25,
-    GS_COUNT = 26
+    GS_QW = 26,  // weighted graphs: sum_c of the Q_w term (SC_QDS), three limbs
+    GS_COUNT = 29
 };
 
 // Per-thread partial sums of one comparison (contingency table).

@@ -23,6 +23,8 @@ struct GraphDev {
     long long n_arcs;
     long long max_degree;
     const int *inv = nullptr;  // loaded with QM_REORDER: new node id -> caller's node id
+    const float *wt = nullptr; // weighted graph: [n_arcs] edge weights parallel to col
+    unsigned long long w_lo = 0, w_hi = 0;  // weighted graph: total weight W * 2^43 (128-bit)
 };
 
 // Launch shape of the community-major kernels.
@@ -77,6 +79,9 @@ struct ScoreWs {
     qmk::RunHdr *hdr_long;      // two-phase only: [K] run headers for k_count_long
     int *nbr;                   // two-phase only: [n_arcs] neighbour labels in community order
     unsigned long long *rec;    // two-phase only: [K][6] per-community records
+    float *nbrw = nullptr;      // weighted graphs: [n_arcs] weights of the packed cut arcs
+    unsigned long long *wl = nullptr;    // weighted graphs: [K][6] intra / cut weight limbs (zeroed)
+    unsigned long long *recw = nullptr;  // weighted graphs: [K][4] 256-bit weighted pair sums
     size_t zero_bytes;          // bytes from `status` that must start at zero
     size_t bytes;               // total bytes carved (the *_ws_bytes size)
 };
@@ -101,8 +106,8 @@ struct CompareWs {
 };
 
 size_t score_ws_bytes(long long n, int K);
-size_t score2_ws_bytes(long long n, long long n_arcs, int K);
-ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K);
+size_t score2_ws_bytes(long long n, long long n_arcs, int K, bool weighted = false);
+ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K, bool weighted = false);
 size_t compare_ws_bytes(long long n, int ka, int kb);
 ScoreWs carve_score_ws(void *base, long long n, int K);
 CompareWs carve_compare_ws(void *base, long long n, int ka, int kb);
@@ -127,7 +132,12 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
 // k_score_fin on an accumulator array of GS_COUNT words (a combined set of shard
 // partials): status must point at a zero int.  Returns 1 (launches) or -1.
 int launch_score_fin(const unsigned long long *gacc, const int *status, long long n, long long E, qm_quality *out,
-                     cudaStream_t s);
+                     int weighted, cudaStream_t s);
+// Load-time checks of a weighted graph's weights (range, and symmetry when
+// `full`) and its total weight 2W * 2^43 in three limbs at lim (zeroed by the
+// caller); status bit 1: weight out of range, bit 2: asymmetric.
+int launch_weight_check(const GraphDev &g, const float *wt, int full, int *status, unsigned long long *lim,
+                        int num_sms, cudaStream_t s);
 int launch_compare(const int *truth, const int *found, long long n, int ka, int kb,
                    const CompareWs &ws, const Shape &sh, int num_sms, cudaStream_t s, TraceFn tr);
 int count_blocks_per_sm(const Shape &sh);
@@ -141,7 +151,7 @@ int launch_permute_labels(const int *labels, const int *inv, long long n, int P,
 // (new id -> old id) of g from `rounds` label-propagation rounds.  Returns 0,
 // or minus a CUDA error code (nothing allocated then).
 int reorder_graph(const GraphDev &g, int rounds, int num_sms, cudaStream_t s, long long **row_ptr_out, int **col_out,
-                  int **inv_out, int *launches);
+                  int **inv_out, int *launches, float **wt_out = nullptr);
 // qm_label_propagation on the device: `rounds` rounds from the caller's node
 // ids, then the labels present are ranked into [0, K'): out (caller order,
 // n entries) and hist[n] = K' (device).  lab0, lab1: n ints; hist: n + 1;

@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(1024) k_score_cm(ScoreKArgs a)
 }
 
 __global__ void k_score_fin(const unsigned long long *g, const int *status, long long n, long long E,
-                            qm_quality *out)
+                            qm_quality *out, int weighted)
 {
     if (threadIdx.x != 0 || *status) return;
     ScoreTotals t;
@@ -423,6 +423,7 @@ __global__ void k_score_fin(const unsigned long long *g, const int *status, long
     t.slots = g[GS_SLOTS];
     t.cnt2 = g[GS_CNT2];
     make_quality(t, n, E, out);
+    if (weighted) out->modularity = fp_to_double(limbs_get(g + GS_QW), SC_QDS);
 }
 
 // ------------------------------------------------------------------ compare
@@ -709,24 +710,42 @@ struct Shard {
 constexpr int EXPAND_UNROLL = 8;
 constexpr int EXPAND_MAX_SEGS = 6;
 
+// Edge weights of a weighted graph (float32, 0 or in [2^-20, 2^20)) as exact
+// fixed-point integers: w * 2^43 (an integer below 2^63).
+__device__ __forceinline__ unsigned long long w_fixed(float w) { return __float2ull_rn(w * 8796093022208.0f); }
+
 // Gathers the labels of arcs [e_lo, e_hi) of a run of community c (loc(e) is
-// the CSR index of arc e) and packs those != c into c's segment at cbase.
-template <class LOC>
+// the CSR index of arc e) and packs those != c into c's segment at cbase.  On
+// a weighted graph (WT) the arc weights travel with the packed labels (nbrw)
+// and each lane sums the fixed-point weights of its intra and cut arcs.
+template <bool WT, class LOC>
 __device__ __forceinline__ void expand_range(unsigned e_lo, unsigned e_hi, int c, unsigned cbase, LOC loc,
                                              const int *__restrict__ col, const int *__restrict__ labels,
-                                             int *inter, int *__restrict__ nbr, unsigned long long keep, int lane)
+                                             int *inter, int *__restrict__ nbr, unsigned long long keep, int lane,
+                                             const float *__restrict__ wt, float *__restrict__ nbrw, u128 &w_in,
+                                             u128 &w_out)
 {
     const unsigned lt = (1u << lane) - 1u;
     for (unsigned e0 = e_lo; e0 < e_hi; e0 += 32u * EXPAND_UNROLL) {
         int lab[EXPAND_UNROLL];
+        float wv[EXPAND_UNROLL];
 #pragma unroll
         for (int k = 0; k < EXPAND_UNROLL; ++k) {
             const unsigned e = e0 + lane + 32u * k;
             lab[k] = e < e_hi ? __ldcs(&col[loc(e)]) : -1;
+            if (WT) wv[k] = e < e_hi ? __ldcs(&wt[loc(e)]) : 0.0f;
         }
 #pragma unroll
         for (int k = 0; k < EXPAND_UNROLL; ++k)
             if (lab[k] >= 0) lab[k] = ld_hint(&labels[lab[k]], keep);
+        if (WT) {
+#pragma unroll
+            for (int k = 0; k < EXPAND_UNROLL; ++k)
+                if (lab[k] >= 0) {
+                    const unsigned long long f = w_fixed(wv[k]);
+                    if (lab[k] == c) w_in += f; else w_out += f;
+                }
+        }
         unsigned msk[EXPAND_UNROLL];
         int tot = 0;
 #pragma unroll
@@ -740,12 +759,30 @@ __device__ __forceinline__ void expand_range(unsigned e_lo, unsigned e_hi, int c
         unsigned at = cbase + (unsigned)__shfl_sync(0xffffffffu, pos, 0);
 #pragma unroll
         for (int k = 0; k < EXPAND_UNROLL; ++k) {
-            if ((msk[k] >> lane) & 1u) __stcs(&nbr[at + __popc(msk[k] & lt)], lab[k]);
+            if ((msk[k] >> lane) & 1u) {
+                __stcs(&nbr[at + __popc(msk[k] & lt)], lab[k]);
+                if (WT) __stcs(&nbrw[at + __popc(msk[k] & lt)], wv[k]);
+            }
             at += __popc(msk[k]);
         }
     }
 }
 
+// Adds a warp's intra and cut weight sums of community c to its limbs (wl:
+// six words per community, intra then cut).
+__device__ __forceinline__ void flush_weights(unsigned long long *wl, int c, u128 w_in, u128 w_out, int lane)
+{
+    for (int d = 16; d > 0; d >>= 1) {
+        w_in += shfl_down_u128(w_in, d);
+        w_out += shfl_down_u128(w_out, d);
+    }
+    if (lane == 0) {
+        if (w_in) limbs_add(wl + (size_t)c * 6, (i128)w_in);
+        if (w_out) limbs_add(wl + (size_t)c * 6 + 3, (i128)w_out);
+    }
+}
+
+template <bool WT>
 __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__restrict__ row_ptr,
                                                            const int *__restrict__ col,
                                                            const int *__restrict__ labels,
@@ -753,7 +790,8 @@ __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__re
                                                            const unsigned *__restrict__ aoff,
                                                            const int *__restrict__ start, long long n,
                                                            int *inter, int *__restrict__ nbr, const int *status,
-                                                           Shard own)
+                                                           Shard own, const float *__restrict__ wt,
+                                                           float *__restrict__ nbrw, unsigned long long *wl)
 {
     __shared__ unsigned offs_s[EXPAND_THREADS / 32][33];
     __shared__ long long rs_s[EXPAND_THREADS / 32][32];
@@ -800,8 +838,10 @@ __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__re
                     cbase = __shfl_sync(0xffffffffu, cbase, 0);
                 }
                 const long long cs = rsw[lo] - (long long)e_lo;  // CSR index of arc e is cs + e
-                expand_range(e_lo, e_hi, c, cbase, [cs](unsigned e) { return cs + (long long)e; }, col, labels,
-                             inter, nbr, keep, lane);
+                u128 w_in = 0, w_out = 0;
+                expand_range<WT>(e_lo, e_hi, c, cbase, [cs](unsigned e) { return cs + (long long)e; }, col, labels,
+                                 inter, nbr, keep, lane, wt, nbrw, w_in, w_out);
+                if (WT) flush_weights(wl, c, w_in, w_out, lane);
             }
         } else {
             while (runs) {
@@ -814,13 +854,15 @@ __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__re
                 if (!own.owns(c)) continue;
                 if (lane == 0) cbase = __ldg(&aoff[__ldg(&start[c])]);
                 cbase = __shfl_sync(0xffffffffu, cbase, 0);
-                expand_range(
+                u128 w_in = 0, w_out = 0;
+                expand_range<WT>(
                     e_lo, e_hi, c, cbase,
                     [=](unsigned e) {
                         const int o = m_lo + upper_bound_smem(offw + m_lo, m_hi - m_lo, e) - 1;
                         return rsw[o] + (long long)(e - offw[o]);
                     },
-                    col, labels, inter, nbr, keep, lane);
+                    col, labels, inter, nbr, keep, lane, wt, nbrw, w_in, w_out);
+                if (WT) flush_weights(wl, c, w_in, w_out, lane);
             }
         }
         __syncwarp();
@@ -1059,6 +1101,8 @@ __global__ void k_score_terms(const int *start, const unsigned long long *rec, i
     flush_score_threads(acc, g, red);
 }
 
+#include "qm_weighted.cuh"
+
 void prepare_kernels()
 {
     cudaFuncSetAttribute(k_score_cm, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
@@ -1066,6 +1110,7 @@ void prepare_kernels()
     cudaFuncSetAttribute(k_count<EpochTable>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     cudaFuncSetAttribute(k_count<EpochTable32>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     cudaFuncSetAttribute(k_count_long, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+    cudaFuncSetAttribute(k_count_w, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
 }
 
 int count_blocks_per_sm(const Shape &sh)
@@ -1167,18 +1212,18 @@ int launch_score(const GraphDev &g, const int *labels, int K, const ScoreWs &ws,
     TRACE("k_score_cm_overflow");
     k_score_cm<<<blocks, sh.threads, sh.smem_bytes, s>>>(a);
     TRACE("k_score_fin");
-    k_score_fin<<<1, 32, 0, s>>>(ws.gacc, ws.status, n, g.n_arcs / 2, ws.result);
+    k_score_fin<<<1, 32, 0, s>>>(ws.gacc, ws.status, n, g.n_arcs / 2, ws.result, 0);
     TRACE(nullptr);
     launches += 3;
     return cudaGetLastError() == cudaSuccess ? launches : -1;
 }
 
-size_t score2_ws_bytes(long long n, long long n_arcs, int K)
+size_t score2_ws_bytes(long long n, long long n_arcs, int K, bool weighted)
 {
-    return carve_score2_ws(reinterpret_cast<void *>(4096), n, n_arcs, K).bytes;
+    return carve_score2_ws(reinterpret_cast<void *>(4096), n, n_arcs, K, weighted).bytes;
 }
 
-ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K)
+ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K, bool weighted)
 {
     ScoreWs w{};
     const int tiles = scan_tiles((int)std::max<long long>(n, K));
@@ -1194,7 +1239,17 @@ ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K)
     p += align_up((size_t)K * 4, 256);
     w.inter = (int *)p;
     p += align_up((size_t)K * 4, 256);
+    if (weighted) {
+        w.wl = (unsigned long long *)p;
+        p += align_up((size_t)K * 6 * 8, 256);
+    }
     w.zero_bytes = (size_t)(p - (char *)base);
+    if (weighted) {
+        w.nbrw = (float *)p;
+        p += align_up((size_t)n_arcs * 4, 256) + 256;
+        w.recw = (unsigned long long *)p;
+        p += align_up((size_t)K * 4 * 8, 256);
+    }
     w.start = (int *)p;
     p += align_up((size_t)(K + 1) * 4, 256);
     w.recip = (Rcp *)p;
@@ -1224,6 +1279,46 @@ ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K)
     return w;
 }
 
+// Weighted graphs after k_expand<true>: one block per community counts and
+// forms the weighted pair sums, then the weighted terms and the result.
+constexpr int COUNT_W_THREADS = 256, COUNT_W_SMEM = 48 * 1024;
+
+static int launch_weighted_tail(const GraphDev &g, int K, const ScoreWs &ws, const PerCommDev *pc, int num_sms,
+                                cudaStream_t s, TraceFn tr, Shard own, int launches)
+{
+    CountCtx x;
+    x.nbr = ws.nbr;
+    x.aoff = ws.aoff;
+    x.start = ws.start;
+    x.inter = ws.inter;
+    x.recip = ws.recip;
+    x.rec = ws.rec;
+    x.K = K;
+    x.err = ws.status;
+    static int blocks_per_sm = 0;
+    if (blocks_per_sm == 0) {
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_count_w, COUNT_W_THREADS, COUNT_W_SMEM);
+        blocks_per_sm = nb > 0 ? nb : 1;
+    }
+    TRACE("k_count_w");
+    k_count_w<<<num_sms * blocks_per_sm, COUNT_W_THREADS, COUNT_W_SMEM, s>>>(
+        x, ws.nbrw, ws.recw, plan_smem(COUNT_W_THREADS, COUNT_W_SMEM), ws.status, own);
+    PerCommDev pcd{};
+    if (pc) pcd = *pc;
+    TRACE("k_score_terms_w");
+    k_score_terms_w<<<grid_for(K, 256, num_sms, 2), 256, 0, s>>>(ws.start, ws.rec, ws.recw, ws.wl, K, g.n_arcs / 2,
+                                                                 g.w_lo, g.w_hi, pcd, ws.gacc, ws.status, own);
+    launches += 2;
+    if (own.p == 1) {
+        TRACE("k_score_fin");
+        k_score_fin<<<1, 32, 0, s>>>(ws.gacc, ws.status, g.n, g.n_arcs / 2, ws.result, 1);
+        ++launches;
+    }
+    TRACE(nullptr);
+    return cudaGetLastError() == cudaSuccess ? launches : -1;
+}
+
 // The two-phase plain scoring pipeline (see k_expand / count_community):
 //   k_hist -> scan (sizes) -> k_scatter_deg -> scan (member degrees = arc offsets)
 //   -> k_expand -> k_classify -> k_count -> k_score_terms -> k_score_fin
@@ -1248,8 +1343,16 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
     launches += launch_scan((const int *)ws.aoff, (int)n, (int *)ws.aoff, nullptr, nullptr, INT_MAX, nullptr,
                             ws.counters, ws.scan_tmp, ws.status, s, tr);
     TRACE("k_expand");
-    k_expand<<<num_sms * 8, EXPAND_THREADS, 0, s>>>(g.row_ptr, g.col, labels, ws.members, ws.aoff, ws.start, n,
-                                                    ws.inter, ws.nbr, ws.status, own);
+    if (g.wt) {
+        k_expand<true><<<num_sms * 8, EXPAND_THREADS, 0, s>>>(g.row_ptr, g.col, labels, ws.members, ws.aoff,
+                                                              ws.start, n, ws.inter, ws.nbr, ws.status, own, g.wt,
+                                                              ws.nbrw, ws.wl);
+        ++launches;
+        return launch_weighted_tail(g, K, ws, pc, num_sms, s, tr, own, launches);
+    }
+    k_expand<false><<<num_sms * 8, EXPAND_THREADS, 0, s>>>(g.row_ptr, g.col, labels, ws.members, ws.aoff, ws.start,
+                                                           n, ws.inter, ws.nbr, ws.status, own, nullptr, nullptr,
+                                                           nullptr);
     ++launches;
     const CountPlan cp = plan_count(sh.threads, sh.smem_bytes);
     TRACE("k_classify");
@@ -1287,7 +1390,7 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
     ++launches;
     if (shard_p == 1) {  // a shard's caller reads the partial sums instead
         TRACE("k_score_fin");
-        k_score_fin<<<1, 32, 0, s>>>(ws.gacc, ws.status, n, g.n_arcs / 2, ws.result);
+        k_score_fin<<<1, 32, 0, s>>>(ws.gacc, ws.status, n, g.n_arcs / 2, ws.result, 0);
         ++launches;
     }
     TRACE(nullptr);
@@ -1295,10 +1398,18 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
 }
 
 int launch_score_fin(const unsigned long long *gacc, const int *status, long long n, long long E, qm_quality *out,
-                     cudaStream_t s)
+                     int weighted, cudaStream_t s)
 {
-    k_score_fin<<<1, 32, 0, s>>>(gacc, status, n, E, out);
+    k_score_fin<<<1, 32, 0, s>>>(gacc, status, n, E, out, weighted);
     return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_weight_check(const GraphDev &g, const float *wt, int full, int *status, unsigned long long *lim,
+                        int num_sms, cudaStream_t s)
+{
+    k_wcheck<<<grid_for(g.n_arcs, 256, num_sms, 8), 256, 0, s>>>(wt, g.n_arcs, status, lim);
+    if (full) k_wsym<<<grid_for(g.n, 256, num_sms, 8), 256, 0, s>>>(g.row_ptr, g.col, wt, g.n, status);
+    return cudaGetLastError() == cudaSuccess ? (full ? 2 : 1) : -1;
 }
 
 int launch_compare(const int *truth, const int *found, long long n, int ka, int kb,

@@ -82,6 +82,7 @@ extern "C" qm_status qm_score_partition_noalloc(const qm_graph *g, const int32_t
     if (!g || !labels || !out) return noalloc_fail(QM_EINVAL, "null argument");
     if (K < 1) return noalloc_fail(QM_EINVAL, "K must be >= 1");
     if (qm::graph_device_view(g, &gd, &dev) != QM_OK) return noalloc_fail(QM_EINVAL, "bad graph handle");
+    if (gd.wt) return noalloc_fail(QM_EINVAL, "weighted graphs are scored by qm_score_partition and the sharded calls");
     const size_t ws_bytes = qm::score_ws_bytes(gd.n, K);
     // a renumbered graph (QM_REORDER) also needs room for the gathered labels
     const size_t need = ws_bytes + (gd.inv ? ((size_t)gd.n * 4 + 255) / 256 * 256 : 0);

@@ -92,10 +92,11 @@ __global__ void k_widen(const unsigned *__restrict__ off, long long n, long long
 }
 
 // Row j of the new CSR is row inv[j] of the old one with every neighbour
-// renamed; one warp per row.
+// renamed (and its weights, on a weighted graph); one warp per row.
 __global__ void k_fill_rows(const long long *__restrict__ row_ptr, const int *__restrict__ col,
                             const int *__restrict__ inv, const int *__restrict__ perm, long long n,
-                            const long long *__restrict__ row_ptr2, int *__restrict__ col2)
+                            const long long *__restrict__ row_ptr2, int *__restrict__ col2,
+                            const float *__restrict__ wt, float *__restrict__ wt2)
 {
     const int lane = threadIdx.x & 31;
     const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
@@ -103,7 +104,10 @@ __global__ void k_fill_rows(const long long *__restrict__ row_ptr, const int *__
         const int u = __ldg(&inv[j]);
         const long long rs = __ldg(&row_ptr[u]), deg = __ldg(&row_ptr[u + 1]) - rs;
         const long long ws = __ldg(&row_ptr2[j]);
-        for (long long e = lane; e < deg; e += 32) col2[ws + e] = __ldg(&perm[__ldg(&col[rs + e])]);
+        for (long long e = lane; e < deg; e += 32) {
+            col2[ws + e] = __ldg(&perm[__ldg(&col[rs + e])]);
+            if (wt) wt2[ws + e] = __ldg(&wt[rs + e]);
+        }
     }
 }
 
@@ -184,12 +188,13 @@ int launch_label_propagation(const GraphDev &g, int rounds, int num_sms, cudaStr
 }
 
 int reorder_graph(const GraphDev &g, int rounds, int num_sms, cudaStream_t s, long long **row_ptr_out, int **col_out,
-                  int **inv_out, int *launches)
+                  int **inv_out, int *launches, float **wt_out)
 {
     const long long n = g.n;
     int *lab0 = nullptr, *lab1 = nullptr, *hist = nullptr, *perm = nullptr, *inv = nullptr, *tmp = nullptr;
     long long *row2 = nullptr;
     int *col2 = nullptr;
+    float *wt2 = nullptr;
     int L = 0;
     auto bad = [&](cudaError_t e) {
         cudaFree(lab0);
@@ -200,6 +205,7 @@ int reorder_graph(const GraphDev &g, int rounds, int num_sms, cudaStream_t s, lo
         cudaFree(tmp);
         cudaFree(row2);
         cudaFree(col2);
+        cudaFree(wt2);
         return e == cudaSuccess ? (int)cudaErrorUnknown : (int)e;
     };
     cudaError_t e = cudaSuccess;
@@ -237,8 +243,9 @@ int reorder_graph(const GraphDev &g, int rounds, int num_sms, cudaStream_t s, lo
     L += l2;
     if ((e = cudaMalloc(&row2, (size_t)(n + 1) * 8)) != cudaSuccess) return -bad(e);
     if ((e = cudaMalloc(&col2, (size_t)g.n_arcs * 4)) != cudaSuccess) return -bad(e);
+    if (g.wt && (e = cudaMalloc(&wt2, (size_t)g.n_arcs * 4)) != cudaSuccess) return -bad(e);
     k_widen<<<g1, 512, 0, s>>>((const unsigned *)hist, n, row2);
-    k_fill_rows<<<gw, 256, 0, s>>>(g.row_ptr, g.col, inv, perm, n, row2, col2);
+    k_fill_rows<<<gw, 256, 0, s>>>(g.row_ptr, g.col, inv, perm, n, row2, col2, g.wt, wt2);
     L += 2;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return -bad(e);
     if ((e = cudaGetLastError()) != cudaSuccess) return -bad(e);
@@ -250,6 +257,7 @@ int reorder_graph(const GraphDev &g, int rounds, int num_sms, cudaStream_t s, lo
     *row_ptr_out = row2;
     *col_out = col2;
     *inv_out = inv;
+    if (wt_out) *wt_out = wt2;
     if (launches) *launches = L;
     return 0;
 }

@@ -56,7 +56,7 @@ PARTIAL_WORDS = 32
 
 class QmPartial(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int64), ("n_edges", ctypes.c_int64), ("nranks", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("ranks_mask", ctypes.c_uint64),
+                ("flags", ctypes.c_int32), ("ranks_mask", ctypes.c_uint64),
                 ("words", ctypes.c_uint64 * PARTIAL_WORDS)]
 
 
@@ -101,6 +101,7 @@ def _signatures(lib):
         "qm_set_tuning": [_P, _I32, _P],
         "qm_autotune_batched": [_P, _P, _I32, _P, _P, _I32, S, _P, _P],
         "qm_label_propagation": [_P, _I32, _P, S, _P, _P],
+        "qm_load_graph_weighted": [_P, _P, _P, _I64, _I64, S, ctypes.c_uint, _P, ctypes.POINTER(_P)],
         "qm_score_partition_part": [_P, _P, _I32, S, _I32, _I32, _P, _P],
         "qm_partials_combine": [_P, _I32, _P],
         "qm_partial_finalize": [_P, _P, _P],
@@ -182,10 +183,11 @@ def _struct_dict(s) -> dict:
 class Graph:
     """A symmetric CSR graph resident on the current CUDA device."""
 
-    def __init__(self, row_ptr, col, validate: bool = False, reorder: bool = False, stream=None):
+    def __init__(self, row_ptr, col, validate: bool = False, reorder: bool = False, stream=None, weights=None):
         """reorder=True stores the graph renumbered for locality (QM_REORDER):
         calls still take labels in the caller's node order and give the same
-        results."""
+        results.  weights (float32 per arc, in the memory of col) loads a
+        weighted graph (qm_load_graph_weighted)."""
         if isinstance(row_ptr, torch.Tensor):
             rp = row_ptr.contiguous().to(torch.int64)
             cl = col.contiguous().to(torch.int32)
@@ -195,6 +197,10 @@ class Graph:
             keep = (rp, cl)
             prp, pcl = rp.data_ptr(), cl.data_ptr()
             n, arcs = rp.numel() - 1, cl.numel()
+            if weights is not None:
+                wt = torch.as_tensor(weights).to(device=cl.device, dtype=torch.float32).contiguous()
+                keep = keep + (wt,)
+                pwt = wt.data_ptr()
         else:
             rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
             cl = np.ascontiguousarray(col, dtype=np.int32)
@@ -202,16 +208,25 @@ class Graph:
             prp, pcl = rp.ctypes.data, cl.ctypes.data
             where = QM_HOST
             n, arcs = len(rp) - 1, len(cl)
+            if weights is not None:
+                wt = np.ascontiguousarray(np.asarray(weights), dtype=np.float32)
+                keep = keep + (wt,)
+                pwt = wt.ctypes.data
         h = ctypes.c_void_p()
         flags = (QM_VALIDATE if validate else 0) | (QM_REORDER if reorder else 0)
-        _check(lib().qm_load_graph(prp, pcl, n, arcs, where, flags, _stream_ptr(stream), ctypes.byref(h)),
-               "qm_load_graph")
+        if weights is None:
+            _check(lib().qm_load_graph(prp, pcl, n, arcs, where, flags, _stream_ptr(stream), ctypes.byref(h)),
+                   "qm_load_graph")
+        else:
+            _check(lib().qm_load_graph_weighted(prp, pcl, pwt, n, arcs, where, flags, _stream_ptr(stream),
+                                                ctypes.byref(h)), "qm_load_graph_weighted")
         del keep
         self.handle = h
         self.n = n
         self.n_arcs = arcs
         self.n_edges = arcs // 2
         self.reordered = reorder
+        self.weighted = weights is not None
 
     @classmethod
     def from_csr(cls, row_ptr, col, **kwargs) -> "Graph":
@@ -401,7 +416,7 @@ def finalize_part(part: QmPartial, stream=None) -> dict:
 
 def part_to_array(part: QmPartial) -> np.ndarray:
     """The partial as int64[4 + PARTIAL_WORDS] (for transport between processes)."""
-    head = np.array([part.n_nodes, part.n_edges, part.nranks, 0], np.int64)
+    head = np.array([part.n_nodes, part.n_edges, part.nranks | (part.flags << 32), 0], np.int64)
     head[3] = np.array([part.ranks_mask], np.uint64).view(np.int64)[0]
     words = np.frombuffer(bytes(part.words), dtype=np.uint64).view(np.int64)
     return np.concatenate([head, words])
@@ -410,7 +425,8 @@ def part_to_array(part: QmPartial) -> np.ndarray:
 def part_from_array(a) -> QmPartial:
     a = np.ascontiguousarray(np.asarray(a, dtype=np.int64))
     p = QmPartial()
-    p.n_nodes, p.n_edges, p.nranks = int(a[0]), int(a[1]), int(a[2])
+    p.n_nodes, p.n_edges = int(a[0]), int(a[1])
+    p.nranks, p.flags = int(a[2]) & 0xFFFFFFFF, int(a[2]) >> 32
     p.ranks_mask = int(a[3:4].view(np.uint64)[0])
     ctypes.memmove(p.words, a[4:4 + PARTIAL_WORDS].view(np.uint64).tobytes(), 8 * PARTIAL_WORDS)
     return p
