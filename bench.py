@@ -548,6 +548,19 @@ def bench_configs(args):
         out["lfr10m" + ("" if reorder else "_graph_as_given")] = {
             "score_ms_per_call": t, "edges_per_s": g.n_edges / (t / 1e3)}
         graph.close()
+    # the same graph with a float32 weight per edge (a hash of the pair, in [0.05, 5))
+    u = torch.repeat_interleave(torch.arange(g.n, device=dev), g.row_ptr[1:] - g.row_ptr[:-1])
+    v = g.col.to(torch.int64)
+    a, b = torch.minimum(u, v), torch.maximum(u, v)
+    h = (a * 2654435761 + b * 40503 + 12345) % (1 << 32)
+    w = (0.05 + h.to(torch.float64) / float(1 << 32) * 4.95).to(torch.float32)
+    del u, v, a, b, h
+    graph = qm.Graph(g.row_ptr, g.col, reorder=True, weights=w)
+    t = timed(lambda: qm.score(graph, g.labels, g.K), 5)
+    out["lfr10m_weighted"] = {"score_ms_per_call": t, "edges_per_s": g.n_edges / (t / 1e3),
+                              "what": "weighted Q and Qds (edge weights, unweighted densities), graph reordered"}
+    graph.close()
+    del w
     del g
     torch.cuda.empty_cache()
     return out
