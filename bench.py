@@ -111,6 +111,7 @@ def algorithmic_bytes(kernel: str, n: int, E: int, K: int, q: dict) -> float:
         "k_scatter_deg": 20.0 * n,
         # label gather through the reorder permutation: labels, permutation read, result written
         "k_permute_labels": 12.0 * n,
+        "k_permute_hist": 12.0 * n,
     }
     return table.get(kernel, 0.0)
 

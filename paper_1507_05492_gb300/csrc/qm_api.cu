@@ -645,15 +645,23 @@ static qm_status score_impl(qm_graph *g, const int32_t *labels, int32_t K, qm_me
         CK(cudaMemcpyAsync((void *)dl, labels, (size_t)n * 4, cudaMemcpyHostToDevice, s));
     }
     const TraceFn tr = trace_begin();
+    CK(cudaMemsetAsync(ws.ptr(), 0, w.zero_bytes, s));
+    bool sizes_ready = false;
     if (g->inv) {  // the graph is stored renumbered: gather the labels into its order
         int32_t *pl = (int32_t *)(ws.ptr() + perm_off);
-        if (tr) tr("k_permute_labels", s);
-        if (launch_permute_labels(dl, g->inv, n, 1, pl, num_sms_of(g->device), s) < 0)
-            return cuda_fail(cudaGetLastError(), "label permutation");
+        if (sh.algo) {  // the two-phase pipeline takes the community sizes from the gather
+            if (tr) tr("k_permute_hist", s);
+            if (launch_permute_hist(dl, g->inv, n, pl, K, w, num_sms_of(g->device), s) < 0)
+                return cuda_fail(cudaGetLastError(), "label permutation");
+            sizes_ready = true;
+        } else {
+            if (tr) tr("k_permute_labels", s);
+            if (launch_permute_labels(dl, g->inv, n, 1, pl, num_sms_of(g->device), s) < 0)
+                return cuda_fail(cudaGetLastError(), "label permutation");
+        }
         g_launches += 1;
         dl = pl;
     }
-    CK(cudaMemsetAsync(ws.ptr(), 0, w.zero_bytes, s));
     PerCommDev pcd{};
     void *const *hp = nullptr;
     if (pc) {
@@ -666,7 +674,7 @@ static qm_status score_impl(qm_graph *g, const int32_t *labels, int32_t K, qm_me
         }
     }
     const int L = sh.algo ? launch_score2(g->d, dl, K, w, sh, pc ? &pcd : nullptr, num_sms_of(g->device), s, tr,
-                                          shard_r, shard_p)
+                                          shard_r, shard_p, sizes_ready)
                           : launch_score(g->d, dl, K, w, sh, pc ? &pcd : nullptr, num_sms_of(g->device), s, tr);
     if (L < 0) return cuda_fail(cudaGetLastError(), "launch_score");
     g_launches += L;

@@ -128,7 +128,11 @@ int launch_score(const GraphDev &g, const int *labels, int K, const ScoreWs &ws,
                  const PerCommDev *pc, int num_sms, cudaStream_t s, TraceFn tr);
 int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws, const Shape &sh,
                   const PerCommDev *pc, int num_sms, cudaStream_t s, TraceFn tr, int shard_r = 0,
-                  int shard_p = 1);
+                  int shard_p = 1, bool sizes_ready = false);
+// For a renumbered graph: out[j] = labels[inv[j]] and the community sizes into
+// ws.size (zeroed), with the label range check of k_hist.  Returns 1 or -1.
+int launch_permute_hist(const int *labels, const int *inv, long long n, int *out, int K, const ScoreWs &ws,
+                        int num_sms, cudaStream_t s);
 // k_score_fin on an accumulator array of GS_COUNT words (a combined set of shard
 // partials): status must point at a zero int.  Returns 1 (launches) or -1.
 int launch_score_fin(const unsigned long long *gacc, const int *status, long long n, long long E, qm_quality *out,

@@ -224,6 +224,44 @@ __global__ void k_hist(const int *__restrict__ a, int ka, int *size_a, const int
     }
 }
 
+// Labels of a graph stored renumbered (QM_REORDER) gathered into its order,
+// out[j] = labels[inv[j]], with the community sizes of k_hist counted on the
+// way (the histogram does not depend on the order; in the new order a warp's
+// labels mostly agree, so the warp-aggregated atomics merge well).
+__global__ void k_permute_hist(const int *__restrict__ labels, const int *__restrict__ inv, long long n,
+                               int *__restrict__ out, int K, int *size, int *status, int use_smem)
+{
+    extern __shared__ int sh[];
+    if (use_smem) {
+        for (int i = threadIdx.x; i < K; i += blockDim.x) sh[i] = 0;
+        block_sync();
+    }
+    bool bad = false;
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); j0 < n; j0 += stride) {
+        const long long j = j0 + lane;
+        const bool in = j < n;
+        const int l = in ? __ldg(&labels[__ldg(&inv[j])]) : 0;
+        if (in) out[j] = l;
+        const bool ok = in && (unsigned)l < (unsigned)K;
+        if (in && !ok) bad = true;
+        if (use_smem) {
+            if (ok) atomicAdd(&sh[l], 1);
+        } else {
+            const unsigned act = __ballot_sync(0xffffffffu, ok);
+            if (ok) hist_add_warp(size, l, act);
+        }
+    }
+    if (bad) atomicOr(status, 1);
+    if (use_smem) {
+        block_sync();
+        for (int i = threadIdx.x; i < K; i += blockDim.x)
+            if (sh[i]) atomicAdd(&size[i], sh[i]);
+    }
+}
+
+
 // ------------------------------------------------------------------ scan
 
 // Exclusive prefix of size[0..K) by one block.  Writes start[0..K], optionally
@@ -1279,6 +1317,15 @@ ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K, bool w
     return w;
 }
 
+int launch_permute_hist(const int *labels, const int *inv, long long n, int *out, int K, const ScoreWs &ws,
+                        int num_sms, cudaStream_t s)
+{
+    const int hist_smem = (K <= 12288) ? K * 4 : 0;
+    k_permute_hist<<<grid_for(n, 512, num_sms, 8), 512, hist_smem, s>>>(labels, inv, n, out, K, ws.size, ws.status,
+                                                                       hist_smem ? 1 : 0);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
 // Weighted graphs after k_expand<true>: one block per community counts and
 // forms the weighted pair sums, then the weighted terms and the result.
 constexpr int COUNT_W_THREADS = 256, COUNT_W_SMEM = 48 * 1024;
@@ -1323,16 +1370,19 @@ static int launch_weighted_tail(const GraphDev &g, int K, const ScoreWs &ws, con
 //   k_hist -> scan (sizes) -> k_scatter_deg -> scan (member degrees = arc offsets)
 //   -> k_expand -> k_classify -> k_count -> k_score_terms -> k_score_fin
 int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws, const Shape &sh,
-                  const PerCommDev *pc, int num_sms, cudaStream_t s, TraceFn tr, int shard_r, int shard_p)
+                  const PerCommDev *pc, int num_sms, cudaStream_t s, TraceFn tr, int shard_r, int shard_p,
+                  bool sizes_ready)
 {
     int launches = 0;
     const Shard own{shard_r, shard_p};
     const long long n = g.n;
-    const int hist_smem = (K <= 12288) ? K * 4 : 0;
-    TRACE("k_hist");
-    k_hist<<<grid_for(n, 512, num_sms, 4), 512, hist_smem, s>>>(labels, K, ws.size, nullptr, 0, nullptr, n,
-                                                                ws.status, hist_smem ? 1 : 0);
-    ++launches;
+    if (!sizes_ready) {
+        const int hist_smem = (K <= 12288) ? K * 4 : 0;
+        TRACE("k_hist");
+        k_hist<<<grid_for(n, 512, num_sms, 4), 512, hist_smem, s>>>(labels, K, ws.size, nullptr, 0, nullptr, n,
+                                                                    ws.status, hist_smem ? 1 : 0);
+        ++launches;
+    }
     launches += launch_scan(ws.size, K, ws.start, ws.cursor, ws.recip, INT_MAX, nullptr, ws.counters,
                             ws.scan_tmp, ws.status, s, tr);
     TRACE("k_scatter_deg");

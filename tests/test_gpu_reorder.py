@@ -88,3 +88,16 @@ def test_allocation_free_call_identical(qm, setup):
     torch.cuda.synchronize()
     got = {name: getattr(out, name) for name, _ in out._fields_}
     assert got == qm.score(plain, lab, K)
+
+
+@pytest.mark.parametrize("algo", [1, 0])
+def test_out_of_range_label_rejected(qm, setup, algo):
+    g, plain, reord, parts = setup
+    labels, K = parts[0]
+    bad = labels.clone()
+    bad[12345] = K                                   # one label past the end
+    qm.set_tuning(reord, K, 512, 96 * 1024, 48, algo)
+    with pytest.raises(RuntimeError):
+        qm.score(reord, bad.cuda(), K)
+    assert qm.score(reord, labels.cuda(), K) == qm.score(plain, labels.cuda(), K)
+
