@@ -245,6 +245,24 @@ struct GraphKey {
 static std::mutex g_graph_mu;
 static std::map<GraphKey, cudaGraphExec_t> g_graphs;
 
+// A captured CUDA graph of one plain scoring call on a small graph (see
+// score_impl), valid for the scratch blocks and the graph it was captured with.
+struct PlainKey {
+    const void *dev, *pin;
+    const qm_graph *g;
+    int K, threads, smem, big, algo, shard_r, shard_p, partial;
+    bool operator<(const PlainKey &o) const
+    {
+        return std::tie(dev, pin, g, K, threads, smem, big, algo, shard_r, shard_p, partial) <
+               std::tie(o.dev, o.pin, o.g, o.K, o.threads, o.smem, o.big, o.algo, o.shard_r, o.shard_p, o.partial);
+    }
+};
+struct PlainGraph {
+    cudaGraphExec_t exec;
+    int launches;
+};
+static std::map<PlainKey, PlainGraph> g_plain_graphs;
+
 void Pool::on_free(PoolBlock *b)
 {
     std::lock_guard<std::mutex> lk(g_graph_mu);
@@ -252,6 +270,28 @@ void Pool::on_free(PoolBlock *b)
         if (it->first.dev == b->ptr || it->first.pin == b->ptr) {
             cudaGraphExecDestroy(it->second);
             it = g_graphs.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    for (auto it = g_plain_graphs.begin(); it != g_plain_graphs.end();) {
+        if (it->first.dev == b->ptr || it->first.pin == b->ptr) {
+            cudaGraphExecDestroy(it->second.exec);
+            it = g_plain_graphs.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+// Drops the captured plain-call graphs of a graph that is being freed.
+static void drop_plain_graphs(const qm_graph *g)
+{
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (auto it = g_plain_graphs.begin(); it != g_plain_graphs.end();) {
+        if (it->first.g == g) {
+            cudaGraphExecDestroy(it->second.exec);
+            it = g_plain_graphs.erase(it);
         } else {
             ++it;
         }
@@ -584,6 +624,7 @@ qm_status qm_free_graph(qm_graph *g)
 {
     if (!g) return fail(QM_EINVAL, "null graph");
     DeviceGuard dg(g->device);
+    drop_plain_graphs(g);
     cudaFree(g->row_ptr);
     cudaFree(g->col);
     cudaFree(g->inv);
@@ -620,15 +661,24 @@ qm_status qm_workspace_bytes(const qm_graph *g, int32_t K, int32_t with_compare,
 // One scoring call.  A shard (shard_p > 1, two-phase pipeline only) scores the
 // communities c with c mod shard_p == shard_r and returns its exact partial
 // sums in gacc_out (QM_PARTIAL_WORDS words) instead of a result.
+//
+// On graphs of up to kPlainGraphMaxN nodes the launch overhead outweighs the
+// work, so the call's device work after the label copy (zeroing, kernels,
+// read-back) is captured once into a CUDA graph per (scratch blocks, graph,
+// K, launch shape) and replayed; the labels go to a fixed place in the
+// scratch first.  Calls with per-community output or tracing run directly.
+static constexpr long long kPlainGraphMaxN = 1LL << 21;
+
 static qm_status score_impl(qm_graph *g, const int32_t *labels, int32_t K, qm_mem where, qm_quality *out,
                             const qm_percomm *pc, cudaStream_t s, const Shape &sh, int shard_r = 0,
                             int shard_p = 1, uint64_t *gacc_out = nullptr)
 {
     const long long n = g->n;
     const bool weighted = g->wt != nullptr;
+    const bool graphed = !pc && !t_trace.on && n <= kPlainGraphMaxN;
     size_t need = sh.algo ? score2_ws_bytes(n, g->n_arcs, K, weighted) : score_ws_bytes(n, K);
     const size_t lab_off = need;
-    if (where == QM_HOST) need += al256((size_t)n * 4);
+    if (where == QM_HOST || graphed) need += al256((size_t)n * 4);
     const size_t perm_off = need;
     if (g->inv) need += al256((size_t)n * 4);
     const size_t pc_off = need;
@@ -640,53 +690,96 @@ static qm_status score_impl(qm_graph *g, const int32_t *labels, int32_t K, qm_me
     if (!ws.b || !pin.b) return fail(QM_ENOMEM, "scratch allocation failed");
     ScoreWs w = sh.algo ? carve_score2_ws(ws.ptr(), n, g->n_arcs, K, weighted) : carve_score_ws(ws.ptr(), n, K);
     const int32_t *dl = labels;
-    if (where == QM_HOST) {
+    if (where == QM_HOST || graphed) {
         dl = (const int32_t *)(ws.ptr() + lab_off);
-        CK(cudaMemcpyAsync((void *)dl, labels, (size_t)n * 4, cudaMemcpyHostToDevice, s));
-    }
-    const TraceFn tr = trace_begin();
-    CK(cudaMemsetAsync(ws.ptr(), 0, w.zero_bytes, s));
-    bool sizes_ready = false;
-    if (g->inv) {  // the graph is stored renumbered: gather the labels into its order
-        int32_t *pl = (int32_t *)(ws.ptr() + perm_off);
-        if (sh.algo) {  // the two-phase pipeline takes the community sizes from the gather
-            if (tr) tr("k_permute_hist", s);
-            if (launch_permute_hist(dl, g->inv, n, pl, K, w, num_sms_of(g->device), s) < 0)
-                return cuda_fail(cudaGetLastError(), "label permutation");
-            sizes_ready = true;
-        } else {
-            if (tr) tr("k_permute_labels", s);
-            if (launch_permute_labels(dl, g->inv, n, 1, pl, num_sms_of(g->device), s) < 0)
-                return cuda_fail(cudaGetLastError(), "label permutation");
-        }
-        g_launches += 1;
-        dl = pl;
+        CK(cudaMemcpyAsync((void *)dl, labels, (size_t)n * 4,
+                           where == QM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
     }
     PerCommDev pcd{};
-    void *const *hp = nullptr;
-    if (pc) {
-        hp = (void *const *)pc;
-        void **dp = (void **)&pcd;
-        for (int k = 0; k < 8; ++k) {
-            if (!hp[k]) { dp[k] = nullptr; continue; }
-            dp[k] = pc_host ? (void *)(ws.ptr() + pc_off + al256((size_t)K * 8) * k) : hp[k];
-            CK(cudaMemsetAsync(dp[k], 0, (size_t)K * 8, s));
+    void *const *hp = pc ? (void *const *)pc : nullptr;
+    const int nsm = num_sms_of(g->device);
+    // the call's device work on stream st; returns its kernel launches, or -1
+    auto enqueue = [&](cudaStream_t st, TraceFn tr) -> int {
+        int L = 0;
+        if (cudaMemsetAsync(ws.ptr(), 0, w.zero_bytes, st) != cudaSuccess) return -1;
+        const int32_t *src = dl;
+        bool sizes_ready = false;
+        if (g->inv) {  // the graph is stored renumbered: gather the labels into its order
+            int32_t *pl = (int32_t *)(ws.ptr() + perm_off);
+            if (sh.algo) {  // the two-phase pipeline takes the community sizes from the gather
+                if (tr) tr("k_permute_hist", st);
+                if (launch_permute_hist(dl, g->inv, n, pl, K, w, nsm, st) < 0) return -1;
+                sizes_ready = true;
+            } else {
+                if (tr) tr("k_permute_labels", st);
+                if (launch_permute_labels(dl, g->inv, n, 1, pl, nsm, st) < 0) return -1;
+            }
+            L += 1;
+            src = pl;
+        }
+        if (pc) {
+            void **dp = (void **)&pcd;
+            for (int k = 0; k < 8; ++k) {
+                if (!hp[k]) { dp[k] = nullptr; continue; }
+                dp[k] = pc_host ? (void *)(ws.ptr() + pc_off + al256((size_t)K * 8) * k) : hp[k];
+                if (cudaMemsetAsync(dp[k], 0, (size_t)K * 8, st) != cudaSuccess) return -1;
+            }
+        }
+        const int L2 = sh.algo ? launch_score2(g->d, src, K, w, sh, pc ? &pcd : nullptr, nsm, st, tr, shard_r,
+                                               shard_p, sizes_ready)
+                               : launch_score(g->d, src, K, w, sh, pc ? &pcd : nullptr, nsm, st, tr);
+        if (L2 < 0) return -1;
+        L += L2;
+        if (cudaMemcpyAsync(pin.ptr(), w.status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return -1;
+        const cudaError_t e = gacc_out
+            ? cudaMemcpyAsync(pin.ptr() + 256, w.gacc, QM_PARTIAL_WORDS * 8, cudaMemcpyDeviceToHost, st)
+            : cudaMemcpyAsync(pin.ptr() + 256, w.result, sizeof(qm_quality), cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return -1;
+        if (pc_host) {
+            void **dp = (void **)&pcd;
+            for (int k = 0; k < 8; ++k)
+                if (hp[k] && cudaMemcpyAsync(hp[k], dp[k], (size_t)K * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+                    return -1;
+        }
+        return L;
+    };
+    cudaGraphExec_t exec = nullptr;
+    int L = -1;
+    if (graphed) {
+        const PlainKey key{ws.ptr(), pin.ptr(), g, K, sh.threads, sh.smem_bytes, sh.big_community, sh.algo,
+                           shard_r, shard_p, gacc_out ? 1 : 0};
+        {
+            std::lock_guard<std::mutex> lk(g_graph_mu);
+            auto it = g_plain_graphs.find(key);
+            if (it != g_plain_graphs.end()) {
+                exec = it->second.exec;
+                L = it->second.launches;
+            }
+        }
+        if (!exec) {
+            cudaStream_t cs = capture_stream(g->device);
+            CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            const int Lc = enqueue(cs, nullptr);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+            if (e == cudaSuccess && Lc >= 0 && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+                L = Lc;
+                std::lock_guard<std::mutex> lk(g_graph_mu);
+                g_plain_graphs[key] = PlainGraph{exec, L};
+            } else {
+                exec = nullptr;
+                cudaGetLastError();  // the call runs without a graph instead
+            }
+            if (graph) cudaGraphDestroy(graph);
         }
     }
-    const int L = sh.algo ? launch_score2(g->d, dl, K, w, sh, pc ? &pcd : nullptr, num_sms_of(g->device), s, tr,
-                                          shard_r, shard_p, sizes_ready)
-                          : launch_score(g->d, dl, K, w, sh, pc ? &pcd : nullptr, num_sms_of(g->device), s, tr);
-    if (L < 0) return cuda_fail(cudaGetLastError(), "launch_score");
-    g_launches += L;
-    CK(cudaMemcpyAsync(pin.ptr(), w.status, sizeof(int), cudaMemcpyDeviceToHost, s));
-    if (gacc_out)
-        CK(cudaMemcpyAsync(pin.ptr() + 256, w.gacc, QM_PARTIAL_WORDS * 8, cudaMemcpyDeviceToHost, s));
-    else
-        CK(cudaMemcpyAsync(pin.ptr() + 256, w.result, sizeof(qm_quality), cudaMemcpyDeviceToHost, s));
-    if (pc_host) {
-        void **dp = (void **)&pcd;
-        for (int k = 0; k < 8; ++k)
-            if (hp[k]) CK(cudaMemcpyAsync(hp[k], dp[k], (size_t)K * 8, cudaMemcpyDeviceToHost, s));
+    if (exec) {
+        CK(cudaGraphLaunch(exec, s));
+        g_launches += L;
+    } else {
+        L = enqueue(s, trace_begin());
+        if (L < 0) return cuda_fail(cudaGetLastError(), "launch_score");
+        g_launches += L;
     }
     CK(cudaStreamSynchronize(s));
     trace_collect();

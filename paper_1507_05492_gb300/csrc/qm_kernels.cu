@@ -681,6 +681,12 @@ __global__ void k_validate(const long long *row_ptr, const int *col, long long n
 
 // ------------------------------------------------------------------ launchers
 
+// Grid of a community-major kernel: one block per SM and resident slot, but
+// no more blocks than there are communities (any of which may need a whole
+// block), so that a small graph does not start blocks that find no work.
+struct Shape;
+static int community_grid(long long K, int num_sms, const Shape &sh);
+
 static int grid_for(long long n, int threads, int num_sms, int per_sm)
 {
     long long g = (n + threads - 1) / threads;
@@ -1141,6 +1147,10 @@ __global__ void k_score_terms(const int *start, const unsigned long long *rec, i
 
 #include "qm_weighted.cuh"
 
+// Launch shape of k_count_w (weighted graphs) and its occupancy.
+constexpr int COUNT_W_THREADS = 256, COUNT_W_SMEM = 48 * 1024;
+static int g_count_w_blocks_per_sm = 1;  // set by prepare_kernels
+
 void prepare_kernels()
 {
     cudaFuncSetAttribute(k_score_cm, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
@@ -1149,6 +1159,9 @@ void prepare_kernels()
     cudaFuncSetAttribute(k_count<EpochTable32>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     cudaFuncSetAttribute(k_count_long, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     cudaFuncSetAttribute(k_count_w, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_count_w, COUNT_W_THREADS, COUNT_W_SMEM);
+    g_count_w_blocks_per_sm = nb > 0 ? nb : 1;
 }
 
 int count_blocks_per_sm(const Shape &sh)
@@ -1242,7 +1255,7 @@ int launch_score(const GraphDev &g, const int *labels, int K, const ScoreWs &ws,
     a.status = ws.status;
     a.big_thr = sh.big_community;
     a.plan = plan_smem(sh.threads, sh.smem_bytes);
-    const int blocks = num_sms * (sh.blocks_per_sm > 0 ? sh.blocks_per_sm : 1);
+    const int blocks = community_grid(K, num_sms, sh);
     a.phase = 0;
     TRACE("k_score_cm");
     k_score_cm<<<blocks, sh.threads, sh.smem_bytes, s>>>(a);
@@ -1326,9 +1339,22 @@ int launch_permute_hist(const int *labels, const int *inv, long long n, int *out
     return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
+static int community_grid(long long K, int num_sms, const Shape &sh)
+{
+    const long long resident = (long long)num_sms * (sh.blocks_per_sm > 0 ? sh.blocks_per_sm : 1);
+    return (int)std::max<long long>(1, std::min<long long>(resident, K));
+}
+
+// k_expand: 8 blocks per SM, or fewer when the graph has fewer member chunks
+// (32 member positions per warp, EXPAND_THREADS / 32 warps per block).
+static int expand_grid(long long n, int num_sms)
+{
+    const long long per_block = 32LL * (EXPAND_THREADS / 32);
+    return (int)std::max<long long>(1, std::min<long long>((long long)num_sms * 8, (n + per_block - 1) / per_block));
+}
+
 // Weighted graphs after k_expand<true>: one block per community counts and
 // forms the weighted pair sums, then the weighted terms and the result.
-constexpr int COUNT_W_THREADS = 256, COUNT_W_SMEM = 48 * 1024;
 
 static int launch_weighted_tail(const GraphDev &g, int K, const ScoreWs &ws, const PerCommDev *pc, int num_sms,
                                 cudaStream_t s, TraceFn tr, Shard own, int launches)
@@ -1342,14 +1368,9 @@ static int launch_weighted_tail(const GraphDev &g, int K, const ScoreWs &ws, con
     x.rec = ws.rec;
     x.K = K;
     x.err = ws.status;
-    static int blocks_per_sm = 0;
-    if (blocks_per_sm == 0) {
-        int nb = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_count_w, COUNT_W_THREADS, COUNT_W_SMEM);
-        blocks_per_sm = nb > 0 ? nb : 1;
-    }
     TRACE("k_count_w");
-    k_count_w<<<num_sms * blocks_per_sm, COUNT_W_THREADS, COUNT_W_SMEM, s>>>(
+    k_count_w<<<(int)std::min<long long>((long long)num_sms * g_count_w_blocks_per_sm, K), COUNT_W_THREADS,
+                COUNT_W_SMEM, s>>>(
         x, ws.nbrw, ws.recw, plan_smem(COUNT_W_THREADS, COUNT_W_SMEM), ws.status, own);
     PerCommDev pcd{};
     if (pc) pcd = *pc;
@@ -1394,13 +1415,13 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
                             ws.counters, ws.scan_tmp, ws.status, s, tr);
     TRACE("k_expand");
     if (g.wt) {
-        k_expand<true><<<num_sms * 8, EXPAND_THREADS, 0, s>>>(g.row_ptr, g.col, labels, ws.members, ws.aoff,
+        k_expand<true><<<expand_grid(n, num_sms), EXPAND_THREADS, 0, s>>>(g.row_ptr, g.col, labels, ws.members, ws.aoff,
                                                               ws.start, n, ws.inter, ws.nbr, ws.status, own, g.wt,
                                                               ws.nbrw, ws.wl);
         ++launches;
         return launch_weighted_tail(g, K, ws, pc, num_sms, s, tr, own, launches);
     }
-    k_expand<false><<<num_sms * 8, EXPAND_THREADS, 0, s>>>(g.row_ptr, g.col, labels, ws.members, ws.aoff, ws.start,
+    k_expand<false><<<expand_grid(n, num_sms), EXPAND_THREADS, 0, s>>>(g.row_ptr, g.col, labels, ws.members, ws.aoff, ws.start,
                                                            n, ws.inter, ws.nbr, ws.status, own, nullptr, nullptr,
                                                            nullptr);
     ++launches;
@@ -1424,12 +1445,12 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
     a.counters = ws.counters;
     a.status = ws.status;
     a.plan = cp;
-    const int nb = sh.blocks_per_sm > 0 ? sh.blocks_per_sm : 1;  // occupancy of k_count (resolved by the caller)
     TRACE("k_count");
-    if (K < (1 << 24) - 1) k_count<EpochTable32><<<num_sms * nb, sh.threads, sh.smem_bytes, s>>>(a);
-    else k_count<EpochTable><<<num_sms * nb, sh.threads, sh.smem_bytes, s>>>(a);
+    const int count_grid = community_grid(K, num_sms, sh);  // sh.blocks_per_sm: occupancy resolved by the caller
+    if (K < (1 << 24) - 1) k_count<EpochTable32><<<count_grid, sh.threads, sh.smem_bytes, s>>>(a);
+    else k_count<EpochTable><<<count_grid, sh.threads, sh.smem_bytes, s>>>(a);
     TRACE("k_count_long");
-    k_count_long<<<num_sms, 1024, MAX_DYN_SMEM, s>>>(a.x, ws.hdr_long, ws.counters, plan_smem(1024, MAX_DYN_SMEM),
+    k_count_long<<<std::min(num_sms, K), 1024, MAX_DYN_SMEM, s>>>(a.x, ws.hdr_long, ws.counters, plan_smem(1024, MAX_DYN_SMEM),
                                                       ws.status);
     launches += 2;
     PerCommDev pcd{};
@@ -1499,7 +1520,7 @@ int launch_compare(const int *truth, const int *found, long long n, int ka, int 
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_compare_cm, sh.threads, sh.smem_bytes);
     if (nb < 1) nb = 1;
     TRACE("k_compare_cm");
-    k_compare_cm<<<num_sms * nb, sh.threads, sh.smem_bytes, s>>>(a);
+    k_compare_cm<<<community_grid(kb, num_sms, sh), sh.threads, sh.smem_bytes, s>>>(a);
     TRACE("k_compare_cells");
     k_compare_cells<<<grid_for(n, 256, num_sms, 8), 256, 0, s>>>(a.x, ws.cells, ws.counters, ws.size_b, ws.gacc,
                                                                  ws.status);
