@@ -298,16 +298,27 @@ static void drop_plain_graphs(const qm_graph *g)
     }
 }
 
+// A stream to capture graphs on, one per calling thread and device (captures
+// of concurrent calls must not share a stream).
+struct CaptureStreams {
+    std::map<int, cudaStream_t> by_device;
+    ~CaptureStreams()
+    {
+        for (auto &kv : by_device) cudaStreamDestroy(kv.second);  // errors at process exit are ignored
+    }
+};
+
 static cudaStream_t capture_stream(int dev)
 {
-    static std::mutex mu;
-    static std::map<int, cudaStream_t> streams;
-    std::lock_guard<std::mutex> lk(mu);
-    auto it = streams.find(dev);
-    if (it != streams.end()) return it->second;
+    static thread_local CaptureStreams streams;
+    auto it = streams.by_device.find(dev);
+    if (it != streams.by_device.end()) return it->second;
     cudaStream_t s = nullptr;
-    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-    streams[dev] = s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    streams.by_device[dev] = s;
     return s;
 }
 
@@ -758,10 +769,13 @@ static qm_status score_impl(qm_graph *g, const int32_t *labels, int32_t K, qm_me
         }
         if (!exec) {
             cudaStream_t cs = capture_stream(g->device);
-            CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-            const int Lc = enqueue(cs, nullptr);
             cudaGraph_t graph = nullptr;
-            const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+            int Lc = -1;
+            cudaError_t e = cs ? cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) : cudaErrorInvalidValue;
+            if (e == cudaSuccess) {
+                Lc = enqueue(cs, nullptr);
+                e = cudaStreamEndCapture(cs, &graph);
+            }
             if (e == cudaSuccess && Lc >= 0 && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
                 L = Lc;
                 std::lock_guard<std::mutex> lk(g_graph_mu);
@@ -998,6 +1012,7 @@ static qm_status run_batched(int dev, BatchDesc &d, const Shape &sh0, qm_quality
     }
     if (!exec) {
         cudaStream_t cs = capture_stream(dev);
+        if (!cs) return fail(QM_ECUDA, "no capture stream");
         CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         cudaMemcpyAsync(items_dev, items_h, (size_t)count * sizeof(BatchItem), cudaMemcpyHostToDevice, cs);
         cudaMemsetAsync(st_dev, 0, (size_t)count * sizeof(int) + 256, cs);

@@ -93,3 +93,33 @@ def test_sharded_replays(qm, lfr):
     for _ in range(2):
         parts = [qm.score_part(graph, lab, lfr.K, r, 3) for r in range(3)]
         assert qm.finalize_part(qm.combine_parts(parts)) == ref
+
+
+def test_concurrent_threads(qm, lfr):
+    """Calls from several host threads at once (each on its own stream) take
+    their own scratch and capture streams and give the serial results."""
+    import threading
+    from paper_1507_05492_gb300 import gen
+    graph = qm.Graph(*to_dev(lfr.row_ptr, lfr.col))
+    labs = [gen.perturb(lfr.labels, lfr.K, 0.04 * i, seed=40 + i).cuda() for i in range(8)]
+    ref = [direct(qm, graph, lab, lfr.K) for lab in labs]
+    errors = []
+
+    def worker(t):
+        st = torch.cuda.Stream()
+        try:
+            for r in range(12):
+                i = (t + r) % len(labs)
+                with torch.cuda.stream(st):
+                    got = qm.score(graph, labs[i], lfr.K, stream=st)
+                if got != ref[i]:
+                    errors.append((t, r, i))
+        except Exception as e:  # reported below
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=worker, args=(t,)) for t in range(4)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert not errors, errors[:3]
