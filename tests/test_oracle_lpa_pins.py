@@ -40,8 +40,8 @@ def test_matching_swaps_labels_every_round(oracle_mod, rounds):
 
 @pytest.mark.parametrize("m", [4, 9, 32])
 def test_complete_graph(oracle_mod, m):
-    # round 1: every label is seen once and the node's own is not among them,
-    # so node 0 takes 1 and every other node takes 0; round 2: all take 0
+    # first propagation round: every label is seen once and the node's own is not among them,
+    # so node 0 takes 1 and every other node takes 0; second round: all take 0
     rp, col = csr(m, undirected(m, [(i, j) for i in range(m) for j in range(i + 1, m)]))
     out, k = oracle_mod.label_propagation(rp, col, 1)
     assert k == 2 and out[0] == 1 and np.all(out[1:] == 0)
@@ -61,8 +61,8 @@ def test_disjoint_cliques_and_isolated_nodes(oracle_mod):
 
 def test_keeps_own_label_on_a_tie(oracle_mod):
     # s=0, b=1, a=2, x=3; edges x-a, x-b, a-b, b-s.
-    # round 1: x -> 1, a -> 1, b -> 0, s -> 1   (each node sees distinct ids)
-    # round 2: x sees {1, 0}: own label 1 is tied for most frequent -> keeps 1
+    # first propagation round: x -> 1, a -> 1, b -> 0, s -> 1   (each node sees distinct ids)
+    # second round: x sees {1, 0}: own label 1 is tied for most frequent -> keeps 1
     #          a sees {1, 0}: keeps 1;  b sees {1, 1, 1} -> 1;  s sees {0} -> 0
     rp, col = csr(4, undirected(4, [(3, 2), (3, 1), (2, 1), (1, 0)]))
     out, k = oracle_mod.label_propagation(rp, col, 1)
@@ -82,7 +82,7 @@ def test_path_oscillates(oracle_mod):
 @pytest.mark.parametrize("deg", [33, 40, 64, 100])
 def test_high_degree_node_samples_evenly_spaced_neighbours(oracle_mod, deg):
     # Centre 0 joined to leaves 1..deg; leaf l also has a pendant node deg + l.
-    # Round 1: each pendant takes its leaf's id, each leaf takes 0 (the centre
+    # First propagation round: each pendant takes its leaf's id, each leaf takes 0 (the centre
     # is its smallest neighbour id), and the centre takes the smallest leaf id
     # among the row positions it looks at.  The centre's row is ordered so that
     # the positions skipped by the even spacing floor(i * deg / 32) hold the
