@@ -51,7 +51,11 @@ struct CompareCtx {
     long long N;
     int ka, kb;
     int *err;
+    const double *logt = nullptr;  // log(N / n) for 1 <= n <= LOGT_MAX (plain comparison), or null
 };
+
+// Largest n whose log(N / n) the plain comparison tabulates per call.
+constexpr int LOGT_MAX = 8192;
 
 // Upper bound of the number of hash classes a block splits one community's
 // neighbour ids into.  A community with more than R_MAX * max_used distinct
@@ -428,9 +432,10 @@ __device__ __forceinline__ void compare_community(const CompareCtx &x, int b, co
         i128 vi = 0, hn = 0;
         bool ok = true;
         for (unsigned r = 0; r < R; ++r) {
-            for (int i = mb + gtid; i < me; i += gsize) {
-                const int a = x.tl ? __ldcg(&x.tl[i]) : __ldg(&x.truth[__ldcg(&x.members[i])]);
-                if (R == 1 || tab_split((unsigned)a, R) == r) tab_insert(tab, (unsigned)a);
+            for (int i0 = mb + (gtid & ~31); i0 < me; i0 += gsize) {  // warp-uniform trips
+                const int i = i0 + (gtid & 31);
+                const int a = i < me ? (x.tl ? __ldcg(&x.tl[i]) : __ldg(&x.truth[__ldcg(&x.members[i])])) : 0;
+                tab_insert_warp(tab, (unsigned)a, i < me && (R == 1 || tab_split((unsigned)a, R) == r));
             }
             group_sync(gsize);
             if (*(volatile int *)tab.overflow) { ok = false; break; }
@@ -441,8 +446,9 @@ __device__ __forceinline__ void compare_community(const CompareCtx &x, int b, co
                 colmax = max(colmax, (unsigned)n);
                 atomicMax(&x.rowmax_n[a], (unsigned)n);
                 atomicMax(&x.rowmax_r[a], (unsigned long long)__double_as_longlong(f_ratio(n, na, nb)));
-                vi += fp_from_double(vi_term(n, na, nb), SC_VI);
-                hn += fp_from_double(nmi_num_term(n, na, nb, x.N), SC_H);
+                const double l1 = cell_log(n, na, nb);
+                vi += fp_from_double(vi_term_l(n, l1), SC_VI);
+                hn += fp_from_double(nmi_num_term_l(n, x.N, l1, log_ratio(x.N, n)), SC_H);
             });
             group_sync(gsize);
             if (gtid == 0) *tab.n_used = 0;
@@ -512,9 +518,10 @@ __device__ __forceinline__ void compare_cells_community(const CompareCtx &x, int
     unsigned colmax = 0;
     unsigned long long ncell = 0;
     for (unsigned r = 0; r < R; ++r) {
-        for (int i = mb + gtid; i < me; i += gsize) {
-            const int a = x.tl ? __ldcg(&x.tl[i]) : __ldg(&x.truth[__ldcg(&x.members[i])]);
-            if (R == 1 || tab_split((unsigned)a, R) == r) tab_insert(tab, (unsigned)a);
+        for (int i0 = mb + (gtid & ~31); i0 < me; i0 += gsize) {  // warp-uniform trips
+            const int i = i0 + (gtid & 31);
+            const int a = i < me ? (x.tl ? __ldcg(&x.tl[i]) : __ldg(&x.truth[__ldcg(&x.members[i])])) : 0;
+            tab_insert_warp(tab, (unsigned)a, i < me && (R == 1 || tab_split((unsigned)a, R) == r));
         }
         group_sync(gsize);
         if (*(volatile int *)tab.overflow) {

@@ -359,18 +359,28 @@ __device__ __forceinline__ double pair_term(long long cnt, long long si, long lo
     return __dmul_rn(a, b);
 }
 
-// Eq. (1) term n log(n^2 / (n_a n_b)) of one contingency cell.
-__device__ __forceinline__ double vi_term(long long n, long long na, long long nb)
+// log(n^2 / (n_a n_b)) of one contingency cell: the logarithm of its Eq. (1)
+// term, and (with log(N/n)) of its Eq. (2) term.
+__device__ __forceinline__ double cell_log(long long n, long long na, long long nb)
 {
     const double x = (double)n;
-    return __dmul_rn(x, log(__ddiv_rn(__dmul_rn(x, x), __dmul_rn((double)na, (double)nb))));
+    return log(__ddiv_rn(__dmul_rn(x, x), __dmul_rn((double)na, (double)nb)));
 }
 
-// Eq. (2) numerator term (n/N) log(n N / (n_a n_b)) of one cell.
-__device__ __forceinline__ double nmi_num_term(long long n, long long na, long long nb, long long N)
+// log(N / n); every caller evaluates this same expression (directly, or via
+// a table of it for small n), so all paths give the same bits.
+__device__ __forceinline__ double log_ratio(long long N, long long n)
 {
-    const double x = (double)n, nn = (double)N;
-    return __dmul_rn(__ddiv_rn(x, nn), log(__ddiv_rn(__dmul_rn(x, nn), __dmul_rn((double)na, (double)nb))));
+    return log(__ddiv_rn((double)N, (double)n));
+}
+
+// Eq. (1) term n log(n^2 / (n_a n_b)) from the cell's logarithm l1.
+__device__ __forceinline__ double vi_term_l(long long n, double l1) { return __dmul_rn((double)n, l1); }
+
+// Eq. (2) numerator term (n/N) log(n N / (n_a n_b)) = (n/N) (l1 + log(N/n)).
+__device__ __forceinline__ double nmi_num_term_l(long long n, long long N, double l1, double log_n_over)
+{
+    return __dmul_rn(__ddiv_rn((double)n, (double)N), __dadd_rn(l1, log_n_over));
 }
 
 // Eq. (2) denominator term (n_c/N) log(n_c/N) of one community.
@@ -415,7 +425,8 @@ __device__ __forceinline__ unsigned tab_split(unsigned key, unsigned R)
     return h % R;
 }
 
-__device__ __forceinline__ void tab_insert(const SmemTable &t, unsigned key)
+// Adds inc (>= 1) occurrences of key.
+__device__ __forceinline__ void tab_insert_n(const SmemTable &t, unsigned key, unsigned inc)
 {
     const unsigned long long tag = (unsigned long long)(key + 1u) << 32;
     unsigned h = tab_hash(key, t.cap);
@@ -426,7 +437,7 @@ __device__ __forceinline__ void tab_insert(const SmemTable &t, unsigned key)
         if ((probe & 15) == 15 && *(volatile int *)t.overflow) return;
         unsigned long long cur = ((volatile unsigned long long *)t.slot)[h];
         if (cur == 0ull) {
-            unsigned long long prev = atomicCAS(&t.slot[h], 0ull, tag | 1ull);
+            unsigned long long prev = atomicCAS(&t.slot[h], 0ull, tag | (unsigned long long)inc);
             if (prev == 0ull) {
                 int idx = atomicAdd(t.n_used, 1);
                 if (idx < t.max_used) t.used[idx] = (int)h;
@@ -436,12 +447,24 @@ __device__ __forceinline__ void tab_insert(const SmemTable &t, unsigned key)
             cur = prev;
         }
         if ((cur & 0xFFFFFFFF00000000ull) == tag) {
-            atomicAdd(&t.slot[h], 1ull);
+            atomicAdd(&t.slot[h], (unsigned long long)inc);
             return;
         }
         h = (h + 1u == (unsigned)t.cap) ? 0u : h + 1u;
     }
     *t.overflow = 1;
+}
+
+__device__ __forceinline__ void tab_insert(const SmemTable &t, unsigned key) { tab_insert_n(t, key, 1u); }
+
+// Warp-aggregated insert: the lanes with `valid` set insert their keys, equal
+// keys merged into one update of their count (all 32 lanes call this).
+__device__ __forceinline__ void tab_insert_warp(const SmemTable &t, unsigned key, bool valid)
+{
+    const unsigned act = __ballot_sync(0xffffffffu, valid);
+    if (!valid) return;
+    const unsigned peers = __match_any_sync(act, key);
+    if ((threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1)) tab_insert_n(t, key, (unsigned)__popc(peers));
 }
 
 // ---------------------------------------------------------------- bulk copies

@@ -101,6 +101,7 @@ struct CompareWs {
     int *members;               // [n]
     qmk::Cell *cells;  // contingency cells of the counting pass ([n])
     int *scan_tmp;
+    double *logt;               // [LOGT_MAX + 1] log(N / n)
     size_t zero_bytes;
     size_t bytes;  // total bytes carved (compare_ws_bytes)
 };

@@ -161,6 +161,8 @@ CompareWs carve_compare_ws(void *base, long long n, int ka, int kb)
     p += align_up((size_t)n * sizeof(Cell), 256);
     w.scan_tmp = (int *)p;
     p += align_up((size_t)(scan_tiles(kb) + 1) * 4, 256);
+    w.logt = (double *)p;
+    p += align_up((size_t)(LOGT_MAX + 1) * 8, 256);
     w.bytes = (size_t)(p - (char *)base);
     return w;
 }
@@ -598,10 +600,20 @@ __global__ void k_compare_cells(CompareCtx x, const Cell *cells, const int *coun
         acc.a11 += (unsigned long long)(n * (n - 1) / 2);
         atomicMax(&x.rowmax_n[c.a], (unsigned)n);
         atomicMax(&x.rowmax_r[c.a], (unsigned long long)__double_as_longlong(f_ratio(n, na, nb)));
-        acc.vi += fp_from_double(vi_term(n, na, nb), SC_VI);
-        acc.hnum += fp_from_double(nmi_num_term(n, na, nb, x.N), SC_H);
+        const double l1 = cell_log(n, na, nb);
+        acc.vi += fp_from_double(vi_term_l(n, l1), SC_VI);
+        acc.hnum += fp_from_double(nmi_num_term_l(n, x.N, l1, n <= LOGT_MAX ? __ldg(&x.logt[n]) : log_ratio(x.N, n)),
+                                   SC_H);
     }
     flush_compare(acc, g, red);
+}
+
+// log(N / n) for n = 1 .. LOGT_MAX (contingency cells and community sizes are
+// mostly small, so k_compare_cells then takes one logarithm per cell).
+__global__ void k_log_table(double *logt, long long N)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= LOGT_MAX; i += gridDim.x * blockDim.x)
+        logt[i] = i == 0 ? 0.0 : log_ratio(N, i);
 }
 
 // Column side of every found community b: C(|b|, 2), its entropy term, the count.
@@ -1516,10 +1528,11 @@ int launch_compare(const int *truth, const int *found, long long n, int ka, int 
     a.gacc = ws.gacc;
     a.status = ws.status;
     a.plan = plan;
-    int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_compare_cm, sh.threads, sh.smem_bytes);
-    if (nb < 1) nb = 1;
-    TRACE("k_compare_cm");
+    a.x.logt = ws.logt;
+    TRACE("k_log_table");
+    k_log_table<<<(LOGT_MAX + 256) / 256, 256, 0, s>>>(ws.logt, n);
+    ++launches;
+    TRACE("k_compare_cm");  // sh.blocks_per_sm: occupancy resolved by the caller
     k_compare_cm<<<community_grid(kb, num_sms, sh), sh.threads, sh.smem_bytes, s>>>(a);
     TRACE("k_compare_cells");
     k_compare_cells<<<grid_for(n, 256, num_sms, 8), 256, 0, s>>>(a.x, ws.cells, ws.counters, ws.size_b, ws.gacc,
