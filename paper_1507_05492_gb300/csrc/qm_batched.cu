@@ -320,6 +320,8 @@ __global__ void __launch_bounds__(1024) k_batched(BatchKArgs a)
 void prepare_batched_kernel()
 {
     cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+    k_fill_log_int<<<(LOGT_MAX + 256) / 256, 256>>>();  // this unit's copy of the log table
+    cudaDeviceSynchronize();
 }
 
 int batched_blocks_per_sm(const Shape &sh)

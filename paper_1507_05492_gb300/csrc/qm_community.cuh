@@ -54,8 +54,6 @@ struct CompareCtx {
     const double *logt = nullptr;  // log(N / n) for 1 <= n <= LOGT_MAX (plain comparison), or null
 };
 
-// Largest n whose log(N / n) the plain comparison tabulates per call.
-constexpr int LOGT_MAX = 8192;
 
 // Upper bound of the number of hash classes a block splits one community's
 // neighbour ids into.  A community with more than R_MAX * max_used distinct

@@ -1174,6 +1174,8 @@ void prepare_kernels()
     int nb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_count_w, COUNT_W_THREADS, COUNT_W_SMEM);
     g_count_w_blocks_per_sm = nb > 0 ? nb : 1;
+    k_fill_log_int<<<(LOGT_MAX + 256) / 256, 256>>>();
+    cudaDeviceSynchronize();
 }
 
 int count_blocks_per_sm(const Shape &sh)
