@@ -52,6 +52,7 @@ struct CompareCtx {
     int ka, kb;
     int *err;
     const double *logt = nullptr;  // log(N / n) for 1 <= n <= LOGT_MAX (plain comparison), or null
+    int *size_a_acc = nullptr;     // plain comparison: |c| summed from the cells (zeroed), or null
 };
 
 
@@ -542,6 +543,7 @@ __device__ __forceinline__ void compare_cells_community(const CompareCtx &x, int
             const unsigned long long sv = tab.slot[h];
             const unsigned n = (unsigned)(sv & 0xFFFFFFFFull);
             cells[base + i] = Cell{(int)(sv >> 32) - 1, b, n, 0u};
+            if (x.size_a_acc) atomicAdd(&x.size_a_acc[(int)(sv >> 32) - 1], (int)n);
             colmax = max(colmax, n);
             tab.slot[h] = 0ull;
         }

@@ -338,16 +338,22 @@ __global__ void k_scan_apply(const int *size, int K, const int *tile_off, int *s
 // Counting sort of the nodes by label: members[pos] receives the node id, or
 // vals[node] when vals is given (the comparison places each node's truth
 // label straight into its detected community's run, read in node order).
+// (When vals are given and kv > 0, a value outside [0, kv) sets bit 0 of
+// *status, as a label outside its range does in k_hist.)
 __global__ void k_scatter(const int *__restrict__ labels, const int *__restrict__ vals, long long n, int *cursor,
-                          int *members, const int *status)
+                          int *members, int *status, int kv)
 {
     if (*status) return;
+    bool bad = false;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const int l = __ldg(&labels[i]);
         const int pos = atomicAdd(&cursor[l], 1);
-        members[pos] = vals ? __ldcs(&vals[i]) : (int)i;
+        const int v = vals ? __ldcs(&vals[i]) : (int)i;
+        if (vals && kv > 0 && (unsigned)v >= (unsigned)kv) bad = true;
+        members[pos] = v;
     }
+    if (bad) atomicOr(status, 1);
 }
 
 // ------------------------------------------------------------------ community pass
@@ -1238,7 +1244,7 @@ int launch_score(const GraphDev &g, const int *labels, int K, const ScoreWs &ws,
     launches += launch_scan(ws.size, K, ws.start, ws.cursor, ws.recip, sh.big_community, ws.big_list,
                             ws.counters, ws.scan_tmp, ws.status, s, tr);
     TRACE("k_scatter");
-    k_scatter<<<grid_for(n, 512, num_sms, 8), 512, 0, s>>>(labels, nullptr, n, ws.cursor, ws.members, ws.status);
+    k_scatter<<<grid_for(n, 512, num_sms, 8), 512, 0, s>>>(labels, nullptr, n, ws.cursor, ws.members, ws.status, 0);
     ++launches;
 
     ScoreKArgs a;
@@ -1501,16 +1507,18 @@ int launch_compare(const int *truth, const int *found, long long n, int ka, int 
                    const CompareWs &ws, const Shape &sh, int num_sms, cudaStream_t s, TraceFn tr)
 {
     int launches = 0;
-    const int hist_smem = (ka + kb <= 12288) ? (ka + kb) * 4 : 0;
-    TRACE("k_hist2");
-    k_hist<<<grid_for(n, 512, num_sms, 4), 512, hist_smem, s>>>(truth, ka, ws.size_a, found, kb, ws.size_b, n,
+    // sizes of the detected communities (the truth sizes are summed from the
+    // contingency cells by k_compare_cm, far fewer updates than one per node)
+    const int hist_smem = (kb <= 12288) ? kb * 4 : 0;
+    TRACE("k_hist");
+    k_hist<<<grid_for(n, 512, num_sms, 4), 512, hist_smem, s>>>(found, kb, ws.size_b, nullptr, 0, nullptr, n,
                                                                 ws.status, hist_smem ? 1 : 0);
     ++launches;
     const SmemPlan plan = plan_smem(sh.threads, sh.smem_bytes);
     launches += launch_scan(ws.size_b, kb, ws.start, ws.cursor, nullptr, plan.max_used_w, ws.big_list,
                             ws.counters, ws.scan_tmp, ws.status, s, tr);
     TRACE("k_scatter");
-    k_scatter<<<grid_for(n, 512, num_sms, 8), 512, 0, s>>>(found, truth, n, ws.cursor, ws.members, ws.status);
+    k_scatter<<<grid_for(n, 512, num_sms, 8), 512, 0, s>>>(found, truth, n, ws.cursor, ws.members, ws.status, ka);
     ++launches;
     CompareKArgs a;
     a.x.truth = truth;
@@ -1518,6 +1526,7 @@ int launch_compare(const int *truth, const int *found, long long n, int ka, int 
     a.x.members = nullptr;
     a.x.start = ws.start;
     a.x.size_a = ws.size_a;
+    a.x.size_a_acc = ws.size_a;  // summed from the cells by k_compare_cm
     a.x.rowmax_n = ws.rowmax_n;
     a.x.rowmax_r = ws.rowmax_r;
     a.x.N = n;

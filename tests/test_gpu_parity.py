@@ -223,6 +223,11 @@ def test_invalid_labels_rejected(qm, gen):
         assert e.value.status == qm.QM_EINVAL
         with pytest.raises(qm.QmError):
             qm.compare(g.labels.cuda(), lab.cuda(), g.K, g.K)
+        for truth in (lab.cuda(), lab.numpy()):          # a ground-truth label out of range
+            found = g.labels.cuda() if isinstance(truth, torch.Tensor) else g.labels.numpy()
+            with pytest.raises(qm.QmError) as e:
+                qm.compare(truth, found, g.K, g.K)
+            assert e.value.status == qm.QM_EINVAL
     # the library stays usable after a rejected call
     q = qm.score(graph, g.labels.cuda(), g.K)
     assert q["n_nodes"] == 2000
