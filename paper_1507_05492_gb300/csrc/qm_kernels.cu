@@ -986,7 +986,7 @@ constexpr unsigned STAGE_WAIT_LIMIT = 1u << 22;
 // round-robin; while a block counts one run, the next run is already on its
 // way into shared memory (a TMA bulk copy into the other of two staging
 // buffers, completing on an mbarrier) and the header after that is being
-// loaded.  Short runs then go to single warps, 32 headers at a time.  Each
+// loaded.  Short runs then go to single warps, claim_chunk headers at a time.  Each
 // group has its own epoch-tagged table (see count_run).  Runs longer than the
 // staging buffers go to k_count_long.
 template <class TAB>
