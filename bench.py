@@ -572,6 +572,36 @@ def bench_serving(args):
     return server.run_benchmark(duration_s=args.serve_seconds, rate=args.serve_rate, seed=11)
 
 
+def run_compare_only(args):
+    """Metrics with ground truth alone on the workload (Eqs. 1-7): the planted
+    partition against a copy with 20% of the nodes moved, and against itself;
+    one JSON line with ms per call (CUDA events on the current stream)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1507_05492_gb300 import gen, qm
+    dev = torch.device("cuda", torch.cuda.current_device())
+    g = gen.lfr_graph(gen.config_params(args.workload), device=dev)
+    stream = torch.cuda.current_stream()
+    out = {"workload": args.workload, "n_nodes": g.n, "k": g.K}
+    found = gen.perturb(g.labels, g.K, 0.2, seed=9)
+    for name, f in (("vs_20pct_moved", found), ("vs_itself", g.labels)):
+        for _ in range(args.warmup):
+            qm.compare(g.labels, f, g.K, g.K)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            c = qm.compare(g.labels, f, g.K, g.K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        out[name] = {"ms_per_call": ms, "nodes_per_s": g.n / (ms / 1e3), "n_cells": c["n_cells"],
+                     "nmi": c["nmi"], "ari": c["ari"]}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_setup(args.gpus)
@@ -637,11 +667,15 @@ def main():
     ap.add_argument("--plain-sample", type=int, default=256)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--only-compare", action="store_true",
+                    help="time only the metrics with ground truth (Eqs. 1-7) on the workload")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.only_compare:
+        return run_compare_only(args)
     return run_ours(args)
 
 
