@@ -303,7 +303,9 @@ qm_status qm_set_tuning(const qm_graph *g, int32_t K, const qm_tuning *t);
  * qm_evaluate_partitions_batched (truth != NULL) or
  * qm_score_partitions_batched (truth == NULL) would run it, and caches the
  * fastest; the batch's results are the same bits for every shape.  The
- * algorithm field is ignored (the batched kernel has one pipeline).
+ * algorithm field is ignored (the batched kernel has one pipeline), and the
+ * batched kernel takes at most 512 threads a block (qm_set_batch_tuning
+ * returns QM_EINVAL for more).
  */
 qm_status qm_autotune_batched(const qm_graph *g, const int32_t *labels, int32_t P, const int32_t *K,
                               const int32_t *truth, int32_t k_truth, qm_mem where, void *stream,

@@ -1334,6 +1334,7 @@ qm_status qm_set_batch_tuning(const qm_graph *gc, int32_t K, const qm_tuning *t)
 {
     qm_graph *g = const_cast<qm_graph *>(gc);
     if (!g || K < 1 || !shape_ok(t)) return fail(QM_EINVAL, "bad tuning");
+    if (t->threads > BATCH_MAX_THREADS) return fail(QM_EINVAL, "the batched kernel takes at most 512 threads a block");
     Shape s;
     s.threads = t->threads;
     s.smem_bytes = t->smem_bytes;

@@ -62,7 +62,7 @@ struct BatchKArgs {
     int big_thr;
 };
 
-__global__ void __launch_bounds__(1024) k_batched(BatchKArgs a)
+__global__ void __launch_bounds__(BATCH_MAX_THREADS) k_batched(BatchKArgs a)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int s_item, s_bad, s_nbig, s_ncmp, s_next, s_novf, s_next2;

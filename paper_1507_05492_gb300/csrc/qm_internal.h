@@ -167,6 +167,11 @@ int launch_label_propagation(const GraphDev &g, int rounds, int num_sms, cudaStr
 // Largest dynamic shared memory a community-major block may request.
 constexpr int MAX_DYN_SMEM = 220 * 1024;
 
+// Largest block of the batched kernel (its launch bound: at most 512 threads
+// leaves it 128 registers a thread, so that its per-item state stays in
+// registers).
+constexpr int BATCH_MAX_THREADS = 512;
+
 // Raises the dynamic shared-memory limit of the kernels to MAX_DYN_SMEM (once
 // per device, before any launch or capture).
 void prepare_kernels();

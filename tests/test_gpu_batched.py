@@ -113,3 +113,5 @@ def test_autotune_batched_keeps_results(qm, setup):
         qm.set_batch_tuning(graph, max(Ks), *shape)
         oq, oc = qm.evaluate_batched(graph, L.cuda(), Ks, truth, g.K)
         assert oq == ref_q and oc == ref_c, shape
+    with pytest.raises(qm.QmError):                      # more threads than the kernel's launch bound
+        qm.set_batch_tuning(graph, max(Ks), 1024, 96 * 1024, 128)

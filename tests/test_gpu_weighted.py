@@ -152,3 +152,10 @@ def test_one_million_nodes_against_oracle(qm, oracle_mod):
     q = qm.score(wg, labels.cuda(), g.K)
     assert close(q["modularity"], o["modularity"], o["cond_modularity"])
     assert close(q["modularity_density"], o["modularity_density"], o["cond_modularity_density"])
+
+
+def test_host_and_device_loads_agree(qm, setup):
+    g, w, _, wg, _, parts = setup
+    host = qm.Graph(g.row_ptr.numpy(), g.col.numpy(), weights=w, validate=True)
+    labels, K = parts["perturbed"]
+    assert qm.score(host, labels.cuda(), K) == qm.score(wg, labels.cuda(), K)
