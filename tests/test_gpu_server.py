@@ -86,3 +86,22 @@ def test_admission_respects_budget(env):
     with pytest.raises(MemoryError):
         f.result(timeout=5)
     tiny.close()
+
+
+def test_requests_made_just_before_submission(env):
+    """Labels produced by device kernels on the submitter's stream and submitted
+    at once (before those kernels finish) are read only when complete."""
+    from paper_1507_05492_gb300 import gen
+    from paper_1507_05492_gb300.server import Server
+    qm, graphs, truths, pools = env
+    srv = Server(graphs, budget_bytes=2 << 30, max_batch=64, n_streams=3)
+    futs = []
+    for i in range(24):
+        gid = ("small", "mid", "large")[i % 3]
+        labels, K = truths[gid]
+        lab = gen.perturb(labels, K, 0.3, seed=500 + i)      # queued on the current stream
+        futs.append((gid, lab, K, srv.submit(gid, lab, K)))
+    results = [(gid, lab, K, f.result(timeout=120)) for gid, lab, K, f in futs]
+    srv.close()
+    for gid, lab, K, res in results:
+        assert res["quality"] == qm.score(graphs[gid], lab, K)
