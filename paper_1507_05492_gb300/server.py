@@ -43,14 +43,19 @@ class Request:
 class Server:
     """graphs: {graph_id: qm.Graph}.  budget_bytes bounds the scratch memory of
     the launches in flight.  Graphs with at most `batch_max_nodes` nodes are
-    scored by the batched persistent kernel, larger ones call by call."""
+    scored by the batched persistent kernel, larger ones call by call.  Work on
+    graphs of more than `exclusive_min_nodes` nodes (one call fills the GPU)
+    runs one batch at a time, so that such requests do not slow each other
+    down; requests on smaller graphs keep running beside it."""
 
     def __init__(self, graphs: dict, budget_bytes: int, max_batch: int = 512, n_streams: int = 4,
-                 batch_max_nodes: int = 300_000, device=None):
+                 batch_max_nodes: int = 300_000, exclusive_min_nodes: int = 2_000_000, device=None):
         self.graphs = graphs
         self.budget = int(budget_bytes)
         self.max_batch = max_batch
         self.batch_max_nodes = batch_max_nodes
+        self.exclusive_min_nodes = exclusive_min_nodes
+        self.exclusive_busy = False
         self.device = device if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.pending = collections.deque()
         self.cv = threading.Condition()
@@ -100,10 +105,20 @@ class Server:
 
     # ---------------------------------------------------------------- worker side
 
-    def _take_batch(self):
-        """Oldest pending request's graph; then every pending request of that graph
+    def _exclusive(self, gid) -> bool:
+        return self.graphs[gid].n > self.exclusive_min_nodes
+
+    def _head(self):
+        """The oldest pending request that may start now (None if none): its graph
+        is not one whose work runs one batch at a time while such a batch runs."""
+        for r in self.pending:
+            if not (self.exclusive_busy and self._exclusive(r.graph_id)):
+                return r
+        return None
+
+    def _take_batch(self, head):
+        """The head request's graph; then every pending request of that graph
         (FIFO) while the batch limit and the memory budget allow."""
-        head = self.pending[0]
         gid = head.graph_id
         batch, total = [], 0
         rest = collections.deque()
@@ -120,20 +135,28 @@ class Server:
         self.pending = rest
         return batch, total
 
+    def _ready(self):
+        head = self._head() if self.pending else None
+        return head if head is not None and self.in_flight + head.bytes <= self.budget else None
+
     def _worker(self, stream):
         torch.cuda.set_device(self.device)
         while True:
             with self.cv:
-                while not self.closed and (not self.pending or
-                                           self.in_flight + self.pending[0].bytes > self.budget):
+                while not self.closed and self._ready() is None:
                     self.cv.wait(timeout=0.05)
-                if self.closed and not self.pending:
-                    return
-                if not self.pending:
+                head = self._ready()
+                if head is None:
+                    if self.closed and not self.pending:
+                        return
+                    self.cv.wait(timeout=0.05)  # closing: wait for the batches in flight
                     continue
-                batch, total = self._take_batch()
+                batch, total = self._take_batch(head)
                 if not batch:
                     continue
+                exclusive = self._exclusive(head.graph_id)
+                if exclusive:
+                    self.exclusive_busy = True
                 self.in_flight += total
                 self.launches += 1
                 self.batch_sizes.append(len(batch))
@@ -147,6 +170,8 @@ class Server:
             finally:
                 with self.cv:
                     self.in_flight -= total
+                    if exclusive:
+                        self.exclusive_busy = False
                     self.cv.notify_all()
 
     def _run(self, batch, stream):

@@ -70,8 +70,8 @@ def test_admission_respects_budget(env):
     peak = [0]
     orig = srv._take_batch
 
-    def take():
-        b, total = orig()
+    def take(head):
+        b, total = orig(head)
         peak[0] = max(peak[0], srv.in_flight + total)
         return b, total
     srv._take_batch = take
@@ -105,3 +105,38 @@ def test_requests_made_just_before_submission(env):
     srv.close()
     for gid, lab, K, res in results:
         assert res["quality"] == qm.score(graphs[gid], lab, K)
+
+
+def test_large_graph_batches_run_one_at_a_time(env):
+    """Batches on graphs above exclusive_min_nodes never overlap; smaller
+    graphs' requests keep running beside them."""
+    from paper_1507_05492_gb300.server import Server
+    qm, graphs, truths, pools = env
+    srv = Server(graphs, budget_bytes=4 << 30, max_batch=4, n_streams=4, exclusive_min_nodes=100_000)
+    running, peak = [0], [0]
+    lock = threading.Lock()
+    orig = srv._run
+
+    def run(batch, stream):
+        big = graphs[batch[0].graph_id].n > 100_000
+        if big:
+            with lock:
+                running[0] += 1
+                peak[0] = max(peak[0], running[0])
+        try:
+            orig(batch, stream)
+        finally:
+            if big:
+                with lock:
+                    running[0] -= 1
+    srv._run = run
+    futs = []
+    for i in range(24):
+        gid = ("large", "small")[i % 2]
+        futs.append((gid, pools[gid][i % 12], srv.submit(gid, pools[gid][i % 12], truths[gid][1])))
+    results = [(gid, lab, f.result(timeout=120)) for gid, lab, f in futs]
+    srv.close()
+    assert peak[0] == 1
+    for gid, lab, res in results:
+        assert res["quality"] == qm.score(graphs[gid], lab, truths[gid][1])
+
