@@ -121,3 +121,22 @@ def test_merge_split_reaches_target():
         assert len(np.unique(lab.numpy())) == K
     lab, K, f = gen.candidate_partition(g.labels, seed=10001)
     assert 0 <= f <= 0.5 and K == int(lab.max()) + 1
+
+
+def test_bench_reads_traffic_records(tmp_path, monkeypatch):
+    """bench.py takes roofline.traffic from ```json blocks of profiles/*.md (one
+    record per line) and only for the current kernel sources."""
+    import bench
+    (tmp_path / "k.md").write_text(
+        "# summary\n\n```json\n"
+        '{"kernel": "k_expand", "workload": "w", "source_hash": "abc", "dram_bytes_per_launch": 123}\n'
+        '{"kernel": "k_count", "workload": "w", "source_hash": "abc", "dram_bytes_per_launch": 45}\n'
+        '{"kernel": "k_count", "workload": "w", "source_hash": "old", "dram_bytes_per_launch": 99}\n'
+        "```\n")
+    monkeypatch.setattr(bench, "PROFILE_DIR", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "abc")
+    assert bench.recorded_traffic("k_expand", "w") == 123.0
+    assert bench.recorded_traffic("k_count", "w") == 45.0
+    assert bench.recorded_traffic("k_count", "other") is None
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "new")
+    assert bench.recorded_traffic("k_expand", "w") is None
