@@ -208,7 +208,7 @@ def lfr_graph(p: LfrParams, device="cpu") -> Graph:
     slot_size = sizes[slot_comm]
     free = torch.ones(n, dtype=torch.bool, device=dev)
     node_comm = torch.full((n,), -1, dtype=torch.int64, device=dev)
-    order = torch.argsort(((p.k_max - k_in) << 40) | rng.key40(3, n))
+    order = torch.argsort(((p.k_max - k_in) << 40) | rng.key40(3, n), stable=True)
     kin_sorted = k_in[order]
     s_small = int(sizes.min())
     values, counts = torch.unique_consecutive(kin_sorted, return_counts=True)
@@ -223,7 +223,7 @@ def lfr_graph(p: LfrParams, device="cpu") -> Graph:
         cand = torch.nonzero(free & (slot_size > t)).flatten()
         take = min(c, cand.numel())
         if take > 0:
-            pick = cand[torch.argsort(rng.bits_at(4 + t, cand))[:take]]
+            pick = cand[torch.argsort(rng.bits_at(4 + t, cand), stable=True)[:take]]
             node_comm[seg[:take]] = slot_comm[pick]
             free[pick] = False
         if take < c:
@@ -231,7 +231,7 @@ def lfr_graph(p: LfrParams, device="cpu") -> Graph:
     if pending:
         rest = torch.cat(pending)
         cand = torch.nonzero(free).flatten()
-        pick = cand[torch.argsort(rng.bits_at(200, cand))]
+        pick = cand[torch.argsort(rng.bits_at(200, cand), stable=True)]
         node_comm[rest] = slot_comm[pick[: rest.numel()]]
     cap = sizes[node_comm] - 1
     excess = (k_in - cap).clamp_(min=0)
@@ -242,7 +242,7 @@ def lfr_graph(p: LfrParams, device="cpu") -> Graph:
     nodes = torch.arange(n, device=dev)
     s_node = torch.repeat_interleave(nodes, k_in)
     s_comm = node_comm[s_node]
-    perm = torch.argsort((s_comm << 40) | rng.key40(5, s_node.numel()))
+    perm = torch.argsort((s_comm << 40) | rng.key40(5, s_node.numel()), stable=True)
     s_node = s_node[perm]
     s_comm = s_comm[perm]
     del perm
@@ -256,7 +256,7 @@ def lfr_graph(p: LfrParams, device="cpu") -> Graph:
 
     # 5b. inter stubs, paired at random across the graph
     o_node = torch.repeat_interleave(nodes, k_out)
-    o_node = o_node[torch.argsort(rng.key40(6, o_node.numel()))]
+    o_node = o_node[torch.argsort(rng.key40(6, o_node.numel()), stable=True)]
     half = o_node.numel() // 2
     ou = o_node[0:2 * half:2]
     ov = o_node[1:2 * half:2]
@@ -278,7 +278,7 @@ def lfr_graph(p: LfrParams, device="cpu") -> Graph:
     # 6. seeded node permutation and symmetric CSR
     if p.permute:
         new_id = torch.empty(n, dtype=torch.int64, device=dev)
-        new_id[torch.argsort(rng.key40(7, n))] = nodes
+        new_id[torch.argsort(rng.key40(7, n), stable=True)] = nodes
     else:
         new_id = nodes
     a = new_id[ekey // n]
@@ -329,7 +329,7 @@ def perturb(labels: torch.Tensor, K: int, frac: float, seed: int, stream: int = 
     out = labels.clone()
     if m == 0 or K < 2:
         return out
-    chosen = torch.argsort(rng.key40(stream, n))[:m]
+    chosen = torch.argsort(rng.key40(stream, n), stable=True)[:m]
     shift = 1 + (rng.uniform(stream + 1, m) * (K - 1)).to(torch.int64).clamp_(max=K - 2)
     out[chosen] = ((labels[chosen].to(torch.int64) + shift) % K).to(torch.int32)
     return out
@@ -347,7 +347,7 @@ def merge_split(labels: torch.Tensor, k_target: int, seed: int, stream: int = 30
         rnd += 1
         if K > k_target:
             d = min(K - k_target, K // 2)
-            order = torch.argsort(rng.key40(stream + 2 * rnd, K))
+            order = torch.argsort(rng.key40(stream + 2 * rnd, K), stable=True)
             target = torch.arange(K, device=dev)
             target[order[1:2 * d:2]] = order[0:2 * d:2]
             lab, K = compact(target[lab])
@@ -358,12 +358,12 @@ def merge_split(labels: torch.Tensor, k_target: int, seed: int, stream: int = 30
             if splittable.numel() == 0:
                 break
             d = min(k_target - K, splittable.numel())
-            pick = splittable[torch.argsort(rng.bits_at(stream + 2 * rnd, splittable))[:d]]
+            pick = splittable[torch.argsort(rng.bits_at(stream + 2 * rnd, splittable), stable=True)[:d]]
             new_id = torch.full((K,), -1, dtype=torch.int64, device=dev)
             new_id[pick] = K + torch.arange(d, device=dev)
             n = lab.numel()
             key = (lab << 40) | rng.key40(stream + 2 * rnd + 1, n)
-            order = torch.argsort(key)
+            order = torch.argsort(key, stable=True)
             sl = lab[order]
             seg_start = torch.cumsum(sizes, 0) - sizes
             pos = torch.arange(n, device=dev) - seg_start[sl]
