@@ -602,6 +602,35 @@ def run_compare_only(args):
     return 0
 
 
+def run_batched_only(args):
+    """The batched launch alone (all metrics with and without ground truth of
+    --batch candidates of the 100k-node, mu = 0.3 graph) with the default
+    launch shape; one JSON line with partitions/s (CUDA events)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1507_05492_gb300 import gen, qm
+    dev = torch.device("cuda", torch.cuda.current_device())
+    g = gen.lfr_graph(gen.config_params("lfr100k_mu03"), device=dev)
+    graph = qm.Graph(g.row_ptr, g.col)
+    labs, Ks = gen.candidate_batch(g.labels, args.batch, seed=10_000)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        qm.evaluate_batched(graph, labs, Ks, g.labels, g.K)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        qm.evaluate_batched(graph, labs, Ks, g.labels, g.K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"workload": "lfr100k_mu03", "candidates": args.batch, "ms_per_launch": ms,
+                      "partitions_per_s": args.batch / (ms / 1e3), "tuning": qm.get_batch_tuning(graph, max(Ks))}),
+          flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_setup(args.gpus)
@@ -669,6 +698,8 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--only-compare", action="store_true",
                     help="time only the metrics with ground truth (Eqs. 1-7) on the workload")
+    ap.add_argument("--only-batched", action="store_true",
+                    help="time only the batched launch (--batch candidates, default launch shape)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -676,6 +707,8 @@ def main():
         return run_reference(args)
     if args.only_compare:
         return run_compare_only(args)
+    if args.only_batched:
+        return run_batched_only(args)
     return run_ours(args)
 
 
