@@ -174,6 +174,17 @@ def _labels_arg(x, name="labels"):
     return a.ctypes.data, QM_HOST, a
 
 
+def _shape(x) -> tuple:
+    return tuple(x.shape)
+
+
+def _need(ok: bool, where: str, detail: str):
+    """Lengths the C ABI cannot see (it takes plain pointers) are checked here,
+    before any device work: a short buffer would otherwise be read past its end."""
+    if not ok:
+        raise QmError(QM_EINVAL, where, detail)
+
+
 def _struct_dict(s) -> dict:
     return {name: getattr(s, name) for name, _ in s._fields_}
 
@@ -199,6 +210,7 @@ class Graph:
             n, arcs = rp.numel() - 1, cl.numel()
             if weights is not None:
                 wt = torch.as_tensor(weights).to(device=cl.device, dtype=torch.float32).contiguous()
+                _need(wt.numel() == arcs, "qm_load_graph_weighted", f"{wt.numel()} weights for {arcs} arcs")
                 keep = keep + (wt,)
                 pwt = wt.data_ptr()
         else:
@@ -210,6 +222,7 @@ class Graph:
             n, arcs = len(rp) - 1, len(cl)
             if weights is not None:
                 wt = np.ascontiguousarray(np.asarray(weights), dtype=np.float32)
+                _need(wt.size == arcs, "qm_load_graph_weighted", f"{wt.size} weights for {arcs} arcs")
                 keep = keep + (wt,)
                 pwt = wt.ctypes.data
         h = ctypes.c_void_p()
@@ -259,6 +272,7 @@ class Graph:
 def score(graph: Graph, labels, K: int, per_community: bool = False, stream=None) -> dict:
     """qm_score_partition: Q, Qds and the six measures of one partition."""
     ptr, where, keep = _labels_arg(labels)
+    _need(_shape(keep) == (graph.n,), "qm_score_partition", f"labels of shape {_shape(keep)} for {graph.n} nodes")
     out = QmQuality()
     pc = None
     arrays = None
@@ -288,6 +302,8 @@ def compare(truth, found, k_truth: int, k_found: int, stream=None) -> dict:
     if wt != wf:
         raise ValueError("truth and found must live in the same memory")
     n = kt_.numel() if isinstance(kt_, torch.Tensor) else len(kt_)
+    _need(_shape(kt_) == (n,) and _shape(kf_) == (n,), "qm_compare_partitions",
+          f"truth of shape {_shape(kt_)} and found of shape {_shape(kf_)}")
     out = QmCompare()
     rc = lib().qm_compare_partitions(pt, pf, n, int(k_truth), int(k_found), wt, ctypes.byref(out),
                                      _stream_ptr(stream))
@@ -303,7 +319,9 @@ def _k_array(K, P):
 def score_batched(graph: Graph, labels, K, stream=None) -> list[dict]:
     """qm_score_partitions_batched over a [P, n] int32 label matrix."""
     ptr, where, keep = _labels_arg(labels)
-    P = labels.shape[0]
+    _need(len(_shape(keep)) == 2 and _shape(keep)[1] == graph.n, "qm_score_partitions_batched",
+          f"labels of shape {_shape(keep)} for {graph.n} nodes")
+    P = _shape(keep)[0]
     k = _k_array(K, P)
     out = (QmQuality * P)()
     _check(lib().qm_score_partitions_batched(graph.handle, ptr, P, k.ctypes.data, where, out,
@@ -317,7 +335,10 @@ def evaluate_batched(graph: Graph, labels, K, truth, k_truth: int, stream=None):
     pt, wt, keep_t = _labels_arg(truth, "truth")
     if wt != where:
         raise ValueError("labels and truth must live in the same memory")
-    P = labels.shape[0]
+    _need(len(_shape(keep)) == 2 and _shape(keep)[1] == graph.n and _shape(keep_t) == (graph.n,),
+          "qm_evaluate_partitions_batched",
+          f"labels of shape {_shape(keep)} and truth of shape {_shape(keep_t)} for {graph.n} nodes")
+    P = _shape(keep)[0]
     k = _k_array(K, P)
     oq = (QmQuality * P)()
     oc = (QmCompare * P)()
@@ -332,7 +353,10 @@ def compare_batched(truth, found, k_truth, k_found, shared_truth: bool = True, s
     pt, wt, keep_t = _labels_arg(truth, "truth")
     if wt != wf:
         raise ValueError("truth and found must live in the same memory")
-    P, n = found.shape[0], found.shape[1]
+    _need(len(_shape(keep_f)) == 2, "qm_compare_partitions_batched", f"found of shape {_shape(keep_f)}")
+    P, n = _shape(keep_f)
+    _need(_shape(keep_t) == ((n,) if shared_truth else (P, n)), "qm_compare_partitions_batched",
+          f"truth of shape {_shape(keep_t)} for found of shape {(P, n)}")
     kt = _k_array(k_truth, 1 if shared_truth else P)
     kf = _k_array(k_found, P)
     out = (QmCompare * P)()
@@ -345,7 +369,12 @@ def compare_batched(truth, found, k_truth, k_found, shared_truth: bool = True, s
 def score_graphs_batched(graphs: list[Graph], labels: list, K: list[int], stream=None) -> list[dict]:
     """qm_score_graphs_batched: one partition on each of several graphs."""
     count = len(graphs)
+    _need(len(labels) == count and len(K) == count, "qm_score_graphs_batched",
+          f"{count} graphs, {len(labels)} label arrays, {len(K)} label counts")
     args = [_labels_arg(l) for l in labels]
+    for i, (g, a) in enumerate(zip(graphs, args)):
+        _need(_shape(a[2]) == (g.n,), "qm_score_graphs_batched",
+              f"labels {i} of shape {_shape(a[2])} for {g.n} nodes")
     kinds = {a[1] for a in args}
     if len(kinds) != 1:
         raise ValueError("all label arrays must live in the same memory")
@@ -367,6 +396,7 @@ def workspace_bytes(graph: Graph, K: int, k_truth: int | None = None) -> int:
 
 def autotune(graph: Graph, labels, K: int, stream=None) -> dict:
     ptr, where, keep = _labels_arg(labels)
+    _need(_shape(keep) == (graph.n,), "qm_autotune", f"labels of shape {_shape(keep)} for {graph.n} nodes")
     t = QmTuning()
     _check(lib().qm_autotune(graph.handle, ptr, int(K), where, _stream_ptr(stream), ctypes.byref(t)),
            "qm_autotune")
@@ -389,6 +419,7 @@ def score_part(graph: Graph, labels, K: int, rank: int, nranks: int, stream=None
     """qm_score_partition_part: the exact partial sums of shard `rank` of
     `nranks` (communities c with c mod nranks == rank, Sec. III-A)."""
     ptr, where, keep = _labels_arg(labels)
+    _need(_shape(keep) == (graph.n,), "qm_score_partition_part", f"labels of shape {_shape(keep)} for {graph.n} nodes")
     out = QmPartial()
     rc = lib().qm_score_partition_part(graph.handle, ptr, int(K), where, int(rank), int(nranks),
                                        ctypes.byref(out), _stream_ptr(stream))
@@ -450,12 +481,15 @@ def label_propagation(graph: Graph, rounds: int = 10, device: bool = True, strea
 def autotune_batched(graph: Graph, labels, K, truth=None, k_truth: int = 0, stream=None) -> dict:
     """qm_autotune_batched over a [P, n] label matrix (and an optional truth)."""
     ptr, where, keep = _labels_arg(labels)
+    _need(len(_shape(keep)) == 2 and _shape(keep)[1] == graph.n, "qm_autotune_batched",
+          f"labels of shape {_shape(keep)} for {graph.n} nodes")
     pt = None
     if truth is not None:
         pt, wt, keep_t = _labels_arg(truth, "truth")
         if wt != where:
             raise ValueError("labels and truth must live in the same memory")
-    P = labels.shape[0]
+        _need(_shape(keep_t) == (graph.n,), "qm_autotune_batched", f"truth of shape {_shape(keep_t)}")
+    P = _shape(keep)[0]
     k = _k_array(K, P)
     t = QmTuning()
     _check(lib().qm_autotune_batched(graph.handle, ptr, P, k.ctypes.data, pt, int(k_truth), where,

@@ -56,7 +56,8 @@ class Server:
         self.batch_max_nodes = batch_max_nodes
         self.exclusive_min_nodes = exclusive_min_nodes
         self.exclusive_busy = False
-        self.device = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        dev = torch.device(device if device is not None else "cuda")
+        self.device = dev if dev.index is not None else torch.device("cuda", torch.cuda.current_device())
         self.pending = collections.deque()
         self.cv = threading.Condition()
         self.in_flight = 0
@@ -78,6 +79,15 @@ class Server:
 
     def submit(self, graph_id, labels: torch.Tensor, K: int, truth: torch.Tensor | None = None,
                k_truth: int | None = None) -> cf.Future:
+        # a malformed request is refused here: inside a batch it would fail the
+        # launch for every request batched with it
+        n = self.graphs[graph_id].n
+        for name, t in (("labels", labels), ("truth", truth)):
+            if t is not None and (not isinstance(t, torch.Tensor) or t.dtype != torch.int32 or
+                                  tuple(t.shape) != (n,) or not t.is_contiguous() or t.device != self.device):
+                raise ValueError(f"{name} must be a contiguous int32 tensor of shape ({n},) on {self.device}")
+        if truth is not None and k_truth is None:
+            raise ValueError("a ground truth needs its label count k_truth")
         nbytes = self.request_bytes(graph_id, K, k_truth if truth is not None else None)
         if nbytes > self.budget:
             f = cf.Future()

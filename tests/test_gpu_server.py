@@ -140,3 +140,22 @@ def test_large_graph_batches_run_one_at_a_time(env):
     for gid, lab, res in results:
         assert res["quality"] == qm.score(graphs[gid], lab, truths[gid][1])
 
+
+
+def test_malformed_requests_are_refused_at_submit(env):
+    """A request whose tensors do not fit its graph is refused at once; it never
+    joins a batch, where it would fail the launch for the others."""
+    from paper_1507_05492_gb300.server import Server
+    qm, graphs, truths, pools = env
+    srv = Server(graphs, budget_bytes=2 << 30, max_batch=64, n_streams=2)
+    lab, K = truths["mid"]
+    for bad in (lab[:-1], lab.cpu(), lab.to(torch.int64), lab.view(2, -1)):
+        with pytest.raises(ValueError):
+            srv.submit("mid", bad, K)
+    with pytest.raises(ValueError):
+        srv.submit("mid", lab, K, truths["small"][0], truths["small"][1])   # truth of another graph
+    with pytest.raises(ValueError):
+        srv.submit("mid", lab, K, lab)                                        # truth without k_truth
+    good = srv.submit("mid", pools["mid"][0], K)
+    assert good.result(timeout=60)["quality"] == qm.score(graphs["mid"], pools["mid"][0], K)
+    srv.close()

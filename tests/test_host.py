@@ -140,3 +140,34 @@ def test_bench_reads_traffic_records(tmp_path, monkeypatch):
     assert bench.recorded_traffic("k_count", "other") is None
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "new")
     assert bench.recorded_traffic("k_expand", "w") is None
+
+
+def test_binding_checks_lengths_before_any_device_work():
+    """The C ABI takes plain pointers and cannot see lengths; the binding refuses
+    arrays whose shape does not match the graph (or each other) with QM_EINVAL
+    before the library is called, so no kernel reads past a short buffer."""
+    import types
+    from paper_1507_05492_gb300 import qm
+    G = types.SimpleNamespace(n=10, handle=None)     # never reaches the library
+    i32 = lambda *s: np.zeros(s, np.int32)
+    bad_calls = [
+        (qm.score, (G, i32(9), 3)),
+        (qm.score, (G, torch.zeros(1, 10, dtype=torch.int32), 3)),
+        (qm.compare, (i32(5), i32(4), 1, 1)),
+        (qm.score_batched, (G, i32(2, 9), 3)),
+        (qm.score_batched, (G, i32(10), 3)),
+        (qm.evaluate_batched, (G, i32(2, 10), 3, i32(9), 2)),
+        (qm.compare_batched, (i32(10), i32(2, 9), 2, 3)),
+        (qm.compare_batched, (i32(3, 9), i32(2, 9), 2, 3, False)),
+        (qm.score_graphs_batched, ([G, G], [i32(10)], [3, 3])),
+        (qm.score_graphs_batched, ([G, G], [i32(10), i32(11)], [3, 3])),
+        (qm.score_part, (G, i32(11), 3, 0, 2)),
+        (qm.autotune, (G, i32(11), 3)),
+        (qm.autotune_batched, (G, i32(2, 10), 3, i32(9), 2)),
+    ]
+    for fn, args in bad_calls:
+        with pytest.raises(qm.QmError) as e:
+            fn(*args)
+        assert e.value.status == qm.QM_EINVAL, fn.__name__
+    with pytest.raises(qm.QmError):
+        qm.Graph(np.array([0, 1, 2]), np.array([1, 0]), weights=np.ones(3, np.float32))
