@@ -94,7 +94,10 @@ def score_partition_sharded(graph, labels, K: int, stream=None, part_fn=None, fi
     to the library calls; tests pass stand-ins to run the exchange on CPU."""
     from . import qm
     ws, rank = world()
-    part = (part_fn or qm.score_part)(graph, labels, K, rank, ws)
+    if part_fn is None:
+        part = qm.score_part(graph, labels, K, rank, ws, stream=stream)
+    else:
+        part = part_fn(graph, labels, K, rank, ws)
     if ws > 1:
         a = torch.from_numpy(qm.part_to_array(part)).to(_device())
         bufs = [torch.empty_like(a) for _ in range(ws)]

@@ -99,3 +99,18 @@ def test_ten_million_nodes_four_shards(qm):
     graph = qm.Graph(g.row_ptr, g.col, reorder=True)
     ref = qm.score(graph, g.labels, g.K)
     assert sharded(qm, graph, g.labels, g.K, 4) == ref
+
+
+def test_single_process_sharded_call_on_a_side_stream(qm, setup):
+    """dist.score_partition_sharded without a process group (one rank) runs the
+    library's shard call and finalisation on the stream it is given."""
+    from paper_1507_05492_gb300 import dist as qd
+    g, plain, _, parts = setup
+    labels, K = parts["perturbed"]
+    lab = labels.cuda()
+    ref = qm.score(plain, lab, K)
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        got = qd.score_partition_sharded(plain, lab, K, stream=st)
+    assert got == ref
