@@ -374,3 +374,53 @@ def test_sampled_community_form_matches_whole_graph_oracle(oracle_mod):
     s = oracle_mod.score_communities(rp, col, np.array([0] * 5 + [1] * 5, np.int32), 2, [0, 1])
     assert list(s["distinct_neighbours"]) == [1, 1]
     assert close(s["split"][0], 1 / 42 / 25)
+
+
+def test_six_measures_and_pair_counts_by_brute_force(oracle_mod):
+    """The six measures of Sec. II-B.3 per community and their means over the
+    non-empty communities, and the integer pair summaries (distinct unordered
+    community pairs joined by an edge, and the sum of |E_ci,cj|^2 over them),
+    from adjacency sets in exact rationals.  Label spaces leave ids unused, so
+    a mean taken over all K ids instead of the non-empty ones fails."""
+    rng = np.random.default_rng(20)
+    for trial in range(30):
+        n = int(rng.integers(2, 40))
+        rp, col, adj = random_graph(rng, n, float(rng.uniform(0.05, 0.6)))
+        used = int(rng.integers(1, n + 1))
+        K = used + int(rng.integers(1, 6))                 # ids used..K-1 (and gaps) stay empty
+        lab = (rng.integers(0, used, n) * (1 + trial % 2)).astype(np.int32)
+        K = max(K, int(lab.max()) + 1)
+        r = oracle_mod.score(rp, col, lab, K, per_community=True)
+        pc = r["per_community"]
+        comms = sorted(set(lab.tolist()))
+        members = {c: [u for u in range(n) if lab[u] == c] for c in comms}
+        means = {k: Fraction(0) for k in ("ie", "id", "co", "oe", "ex", "cd")}
+        pairs = {}
+        for c in comms:
+            s = len(members[c])
+            ein = sum(1 for u in members[c] for v in adj[u] if lab[v] == c) // 2
+            eout = sum(1 for u in members[c] for v in adj[u] if lab[v] != c)
+            for u in members[c]:
+                for v in adj[u]:
+                    if lab[v] > c:
+                        pairs[c, int(lab[v])] = pairs.get((c, int(lab[v])), 0) + 1
+            dens = Fraction(2 * ein, s * (s - 1)) if s > 1 else Fraction(0)
+            cond = Fraction(eout, 2 * ein + eout) if 2 * ein + eout > 0 else Fraction(0)
+            vals = {"ie": Fraction(ein), "id": dens, "co": Fraction(2 * ein, s), "oe": Fraction(eout),
+                    "ex": Fraction(eout, s), "cd": cond}
+            for k, v in vals.items():
+                means[k] += v
+            assert pc["size"][c] == s and pc["intra_edges"][c] == ein and pc["inter_edges"][c] == eout
+            for key, k in (("intra_density", "id"), ("contraction", "co"), ("expansion", "ex"),
+                           ("conductance", "cd")):
+                assert close(pc[key][c], float(vals[k])), (trial, key, c)
+        for c in set(range(K)) - set(comms):
+            assert pc["size"][c] == 0 and pc["intra_edges"][c] == 0 and pc["inter_edges"][c] == 0
+        nc = len(comms)
+        assert r["n_communities_nonempty"] == nc
+        for key, k in (("mean_intra_edges", "ie"), ("mean_intra_density", "id"), ("mean_contraction", "co"),
+                       ("mean_inter_edges", "oe"), ("mean_expansion", "ex"), ("mean_conductance", "cd")):
+            assert close(r[key], float(means[k] / nc)), (trial, key)
+        assert r["n_community_pairs"] == len(pairs)
+        assert r["pair_count_sq_sum"] == sum(e * e for e in pairs.values())
+        assert r["cut_edges_total"] == sum(pairs.values())
