@@ -227,6 +227,17 @@ def time_oracle(rp, col, lab, K, reps=1):
 
 # ------------------------------------------------------------------ reference arm
 
+REFERENCE_BUDGET_S = 150.0      # oracle time of a whole --impl reference run (warm-up + steps)
+ORACLE_S_PER_NODE = 0.8e-6      # one oracle scoring on the workload's graph family, per node
+
+
+def reference_sample_nodes(steps: int, warmup: int) -> int:
+    """Sample size so that warm-up + steps oracle scorings take about
+    REFERENCE_BUDGET_S: at most 16M nodes, at least 1M, whole millions."""
+    n = int(REFERENCE_BUDGET_S / max(1, steps + warmup) / ORACLE_S_PER_NODE)
+    return max(1_000_000, min(16_000_000, n // 1_000_000 * 1_000_000))
+
+
 def run_reference(args):
     """The oracle as it stands, timed on the host cores, on a bounded sample of
     the workload (each step one oracle scoring of the sample)."""
@@ -236,6 +247,9 @@ def run_reference(args):
         return 0
     import torch
     dev = "cuda" if torch.cuda.is_available() else "cpu"
+    sized = args.cpu_sample_nodes is None
+    if sized:
+        args.cpu_sample_nodes = reference_sample_nodes(args.steps, args.warmup)
     rp, col, lab, K = oracle_sample(args.cpu_sample_nodes, dev)
     E = len(col) // 2
     for _ in range(args.warmup):
@@ -244,7 +258,9 @@ def run_reference(args):
     total = sum(ts)
     value = E * args.steps / total
     sample = (f"LFR-style graph with the 100M-node workload's parameters at {args.cpu_sample_nodes} nodes "
-              f"(|E| = {E}), planted partition; one oracle scoring per step")
+              f"(|E| = {E}), planted partition; one oracle scoring per step"
+              + (f", the sample sized so that warm-up and steps take about {REFERENCE_BUDGET_S:.0f} s" if sized
+                 else ""))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
@@ -639,6 +655,8 @@ def run_ours(args):
     res = bench_headline(args, world, rank, local)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        if args.cpu_sample_nodes is None:
+            args.cpu_sample_nodes = 16_000_000   # one oracle scoring, about 12 s
         rp, col, lab, K = oracle_sample(args.cpu_sample_nodes, torch.device("cuda", local))
         t = time_oracle(rp, col, lab, K, reps=1)
         E = len(col) // 2
@@ -687,7 +705,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="lfr100m")
-    ap.add_argument("--cpu-sample-nodes", type=int, default=16_000_000)
+    ap.add_argument("--cpu-sample-nodes", type=int, default=None,
+                    help="nodes of the oracle's sample (default: 16M for cpu_baseline; for --impl reference, "
+                         "sized so that warm-up + steps take about 150 s)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-reorder", action="store_true",

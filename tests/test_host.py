@@ -171,3 +171,15 @@ def test_binding_checks_lengths_before_any_device_work():
         assert e.value.status == qm.QM_EINVAL, fn.__name__
     with pytest.raises(qm.QmError):
         qm.Graph(np.array([0, 1, 2]), np.array([1, 0]), weights=np.ones(3, np.float32))
+
+
+def test_reference_arm_sample_is_bounded():
+    """--impl reference sizes its oracle sample so that warm-up plus steps stay
+    within a few minutes at any step count, and never above 16M nodes."""
+    import bench
+    sizes = [bench.reference_sample_nodes(k, w) for k, w in ((1, 0), (2, 3), (10, 3), (50, 5), (500, 10))]
+    assert sizes == sorted(sizes, reverse=True)
+    assert all(1_000_000 <= n <= 16_000_000 and n % 1_000_000 == 0 for n in sizes)
+    for k, w in ((10, 3), (50, 5), (100, 3)):
+        n = bench.reference_sample_nodes(k, w)
+        assert (k + w) * n * bench.ORACLE_S_PER_NODE <= bench.REFERENCE_BUDGET_S * 1.01
