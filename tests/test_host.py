@@ -183,3 +183,43 @@ def test_reference_arm_sample_is_bounded():
     for k, w in ((10, 3), (50, 5), (100, 3)):
         n = bench.reference_sample_nodes(k, w)
         assert (k + w) * n * bench.ORACLE_S_PER_NODE <= bench.REFERENCE_BUDGET_S * 1.01
+
+
+C_PROGRAM = r"""
+#include "qm.h"
+#include <stdio.h>
+#include <string.h>
+int main(void) {
+    int32_t a[1] = {0};
+    qm_compare out;
+    qm_graph *g = NULL;
+    char buf[256];
+    if (strcmp(qm_strerror(QM_OK), "ok") != 0) return 1;
+    /* argument errors are reported before any device work */
+    if (qm_compare_partitions(a, a, 1, 1, 1, QM_HOST, &out, NULL) != QM_EINVAL) return 2;
+    if (qm_last_error(buf, sizeof buf) != QM_OK || strstr(buf, "n_nodes") == NULL) return 3;
+    if (qm_free_graph(g) != QM_EINVAL) return 4;            /* a null handle is refused */
+    printf("%lld\n", (long long)qm_kernel_launches());
+    return 0;
+}
+"""
+
+
+def test_header_is_plain_c(libpath, tmp_path):
+    """include/qm.h compiles as strict C99 (no C++ in the interface), and a C
+    program links against libqm.so and gets its argument errors."""
+    import shutil
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not found")
+    src = tmp_path / "t.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "t"
+    libdir = os.path.dirname(libpath)
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-I", os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lqm",
+                        f"-Wl,-rpath,{libdir}", "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    assert r.stdout.strip() == "0"
