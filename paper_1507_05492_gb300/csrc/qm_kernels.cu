@@ -107,7 +107,7 @@ ScoreWs carve_score_ws(void *base, long long n, int K)
     p += align_up((size_t)K * 4, 256);
     w.zero_bytes = (size_t)(p - (char *)base);
     w.start = (int *)p;
-    p += align_up((size_t)(K + 1) * 4, 256);
+    p += align_up(((size_t)K + 1) * 4, 256);
     w.recip = (Rcp *)p;
     p += align_up((size_t)K * 16, 256);
     w.cursor = (int *)p;
@@ -150,7 +150,7 @@ CompareWs carve_compare_ws(void *base, long long n, int ka, int kb)
     p += align_up((size_t)ka * 8, 256);
     w.zero_bytes = (size_t)(p - (char *)base);
     w.start = (int *)p;
-    p += align_up((size_t)(kb + 1) * 4, 256);
+    p += align_up(((size_t)kb + 1) * 4, 256);
     w.cursor = (int *)p;
     p += align_up((size_t)kb * 4, 256);
     w.big_list = (int *)p;
@@ -1322,7 +1322,7 @@ ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K, bool w
         p += align_up((size_t)K * 4 * 8, 256);
     }
     w.start = (int *)p;
-    p += align_up((size_t)(K + 1) * 4, 256);
+    p += align_up(((size_t)K + 1) * 4, 256);
     w.recip = (Rcp *)p;
     p += align_up((size_t)K * 16, 256);
     w.cursor = (int *)p;

@@ -105,6 +105,10 @@ extern "C" qm_status qm_score_partition_noalloc(const qm_graph *g, const int32_t
         cudaGetLastError();
         return noalloc_fail(QM_EINVAL, "labels must be device memory for the allocation-free call");
     }
+    // the kernels read the labels directly: they must live on the graph's GPU
+    if (pa.device != dev)
+        return noalloc_fail(QM_EINVAL, "labels must be on the graph's GPU (device " + std::to_string(dev) +
+                                           ", labels on device " + std::to_string(pa.device) + ")");
     DeviceSetup s;
     qm_status st = device_setup(dev, &s);
     if (st != QM_OK) return st;
@@ -136,6 +140,8 @@ extern "C" qm_status qm_score_partition_noalloc(const qm_graph *g, const int32_t
     if (e != cudaSuccess) return noalloc_fail(QM_ECUDA, std::string("result copy: ") + cudaGetErrorString(e));
     if (status & 1) return noalloc_fail(QM_EINVAL, "a label lies outside [0, K)");
     if (status & 2) return noalloc_fail(QM_EOVERFLOW, "a community borders too many distinct communities");
+    if (status & 4) return noalloc_fail(QM_ETIMEOUT, "a bounded device wait expired");
+    if (status) return noalloc_fail(QM_ECUDA, "device status " + std::to_string(status));
     std::memcpy(out, &result, sizeof(qm_quality));
     return QM_OK;
 }

@@ -351,6 +351,18 @@ def test_invalid_inputs_rejected(oracle_mod):
     assert not oracle_mod.validate_graph(np.array([0, 1, 1], np.int64), np.array([1], np.int32))
     assert not oracle_mod.validate_graph(np.array([0, 1], np.int64), np.array([0], np.int32))
     assert oracle_mod.validate_graph(rp, col)
+    # a repeated arc: edge {0,1} stored twice in both rows is a multi-edge, which
+    # the unweighted simple-graph setting of Sec. II-B.1 excludes, though the
+    # CSR is symmetric and has no self-loop
+    assert oracle_mod.validate_graph(np.array([0, 1, 2], np.int64), np.array([1, 0], np.int32))
+    assert not oracle_mod.validate_graph(np.array([0, 2, 4], np.int64), np.array([1, 1, 0, 0], np.int32))
+    # the same repeat inside a larger valid graph (one extra 0-1 arc each way)
+    rows = [list(col[rp[u]:rp[u + 1]]) for u in range(len(rp) - 1)]
+    rows[0].append(1)
+    rows[1].append(0)
+    rp2 = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int64)
+    col2 = np.array([v for r in rows for v in r], np.int32)
+    assert not oracle_mod.validate_graph(rp2, col2)
 
 
 def test_sampled_community_form_matches_whole_graph_oracle(oracle_mod):

@@ -1,10 +1,10 @@
 """qm_score_partition_noalloc: the scoring call for hosts that cannot let a
 library allocate memory at call time (no counterpart in the paper).
 
-The call must return what qm_score_partition returns, within the parity
-tolerance of the other tests, on two calls in a row (the scratch array is shared
-and reused), and must refuse a call whose workspace exceeds the fixed array.
-This file is named to be collected last."""
+The call must return exactly what qm_score_partition returns (every field,
+bit for bit: both sum the same integer terms exactly), on two calls in a row (the
+scratch array is shared and reused), and must refuse a call whose workspace
+exceeds the fixed array.  This file is named to be collected last."""
 import ctypes
 
 import pytest
@@ -53,10 +53,14 @@ def test_two_calls_match_the_allocating_entry_point(qm):
         assert rc == qm.QM_OK, qm.last_error()
         got = {name: getattr(out, name) for name, _ in out._fields_}
         check_quality(got, as_oracle_like(ref), "noalloc")
+        assert got == {k: ref[k] for k in got}, "noalloc differs from qm_score_partition"
     # the same partition again: the reused array leaves nothing behind
     rc, out2 = noalloc(qm, graph, parts[0][0], parts[0][1])
     assert rc == qm.QM_OK
-    assert close(out2.modularity, qm.score(graph, parts[0][0], parts[0][1])["modularity"], 1.0)
+    again = {name: getattr(out2, name) for name, _ in out2._fields_}
+    ref0 = qm.score(graph, parts[0][0], parts[0][1])
+    assert again == {k: ref0[k] for k in again}
+    assert close(out2.modularity, ref0["modularity"], 1.0)
 
 
 def test_sizes_beyond_the_array_are_refused(qm):
