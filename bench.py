@@ -92,28 +92,59 @@ def recorded_traffic(kernel: str, workload: str):
     return None
 
 
+def method_bytes(n: int, E: int) -> float:
+    """The method's own bytes for one pass of all metrics without ground truth:
+    per undirected edge one 4-byte endpoint id and one 4-byte label gather, per
+    node an 8-byte row offset and its 4-byte label (8|E| + 12|V|).  Anything a
+    pipeline writes and reads back (member lists, arc offsets, packed labels,
+    keys) is overhead, not method bytes."""
+    return 8.0 * E + 12.0 * n
+
+
 def algorithmic_bytes(kernel: str, n: int, E: int, K: int, q: dict) -> float:
-    """Bytes a launch of `kernel` must move at minimum (each input read once,
-    each output written once; 4-byte ids and labels, 8-byte row offsets,
-    16-byte reciprocals).  cut = 2 x cut_edges_total is the number of packed
-    inter-community entries of the two-phase pipeline."""
+    """A kernel's share of the method bytes (method_bytes): the kernels that
+    stream the adjacency with its label gathers carry all of them (they read
+    every arc, every row offset and every node's label); the others carry none
+    (pair counting and finalisation add no method bytes)."""
+    if kernel in ("k_expand", "k_score_cm", "k_expand_half"):
+        return method_bytes(n, E)
+    return 0.0
+
+
+def pipeline_bytes(kernel: str, n: int, E: int, K: int, q: dict) -> float:
+    """Bytes a launch of `kernel` moves at minimum in this pipeline, counting
+    its own intermediates (each input read once, each output written once; 4-byte
+    ids and labels, 8-byte row offsets, 16-byte reciprocals).  cut = 2 x
+    cut_edges_total is the number of packed inter-community entries."""
     cut = 2.0 * q["cut_edges_total"]
     table = {
-        # one-kernel pass: adjacency 2|E| x 4 B, row offsets 8 B, labels + members 4 B each
         "k_score_cm": 8.0 * E + 12.0 * n,
-        # expand: adjacency, row offsets, labels, members and arc offsets read once;
-        # the packed inter-community labels written once
         "k_expand": 8.0 * E + 20.0 * n + 4.0 * cut,
-        # count: the packed labels and one 16-byte reciprocal per entry read once,
-        # a 16-byte header read and a 48-byte record written per community
         "k_count": 20.0 * cut + 64.0 * K,
-        # counting sort with degrees: labels, row offsets read; members, degrees written
         "k_scatter_deg": 20.0 * n,
-        # label gather through the reorder permutation: labels, permutation read, result written
         "k_permute_labels": 12.0 * n,
         "k_permute_hist": 12.0 * n,
     }
     return table.get(kernel, 0.0)
+
+
+def host_cpu() -> dict:
+    """The host's logical CPU count and model (lscpu), recorded at run time."""
+    info = {"cpu_count": os.cpu_count()}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            k, v = k.strip(), v.strip()
+            if k in ("Model name", "Architecture", "Socket(s)", "Core(s) per socket", "Thread(s) per core"):
+                info[k.lower().replace("(s)", "s").replace(" ", "_")] = v
+    except Exception:
+        pass
+    try:
+        info["affinity"] = len(os.sched_getaffinity(0))
+    except Exception:
+        pass
+    return info
 
 
 class Clocks:
@@ -267,7 +298,8 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64",
         "data": "synthetic", "config": {"workload": "lfr100m (bounded sample, see cpu_baseline)",
                                         "sample_nodes": args.cpu_sample_nodes, "n_edges": E},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "host": host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -313,7 +345,7 @@ def bench_headline(args, world, rank, local):
     n, E, K = g.n, g.n_edges, g.K
     max_deg = graph.info()["max_degree"]
     labels = g.labels
-    keep_csr = (g.row_ptr, g.col) if (not args.no_reorder and not args.no_extras and world == 1) else None
+    keep_csr = (g.row_ptr, g.col) if (not args.no_reorder and world == 1) else None
     del g
     torch.cuda.empty_cache()
     stream = torch.cuda.current_stream()
@@ -424,7 +456,8 @@ def bench_headline(args, world, rank, local):
     top_avg = kernel_shares[top] / args.steps
     b_alg = algorithmic_bytes(top, n, E, K, q)
     achieved = b_alg / (top_avg / 1e3) / 1e9
-    b_step = 8.0 * E + 12.0 * n
+    b_step = method_bytes(n, E)
+    top_traffic = recorded_traffic(top, args.workload)
     # whole-pass DRAM traffic from the committed ncu records of every kernel of
     # the step (null when any record is missing or the kernels changed since)
     launches_per_step = {}
@@ -443,14 +476,22 @@ def bench_headline(args, world, rank, local):
         e2e={"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * n,
              "d2h_bytes_per_step": 4 + 120},
         roofline={"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                  "frac": achieved / peak, "traffic": recorded_traffic(top, args.workload),
+                  "frac": achieved / peak, "traffic": top_traffic,
                   "kernel": top, "peak_kind": f"{peak_kind} (burst copy)",
                   "algorithmic_bytes_per_launch": b_alg, "kernel_ms": top_avg,
+                  "bytes_rule": "method bytes 8|E| + 12|V| per pass, carried by the kernel that streams "
+                                "the adjacency with its label gathers",
+                  "overfetch": (top_traffic / b_alg) if (top_traffic and b_alg) else None,
+                  "pipeline_bytes_per_launch": pipeline_bytes(top, n, E, K, q),
+                  "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum per launch from the committed "
+                                    "ncu record of this kernel and workload (profiles/), null unless its "
+                                    "source hash matches the current kernel sources",
                   "step_algorithmic_bytes": b_step,
                   "step_algorithmic_gbs": b_step / (ms_max / args.steps / 1e3) / 1e9,
                   "step_dram_bytes": pass_bytes,
                   "step_dram_gbs": (pass_bytes / (ms_max / args.steps / 1e3) / 1e9) if pass_bytes else None,
-                  "step_dram_frac": (pass_bytes / (ms_max / args.steps / 1e3) / 1e9 / peak) if pass_bytes else None},
+                  "step_dram_frac": (pass_bytes / (ms_max / args.steps / 1e3) / 1e9 / peak) if pass_bytes else None,
+                  "step_algorithmic_frac": b_step / (ms_max / args.steps / 1e3) / 1e9 / peak},
         clocks=clk,
         config={"workload": f"{args.workload}: LFR-style, n={n}, |E|={E}, K={K}, max degree {max_deg}, "
                             f"mean degree 20 target, mu=0.3, communities 20-1000, planted partition",
@@ -662,7 +703,8 @@ def run_ours(args):
         E = len(col) // 2
         cpu = {"value": E / t, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"LFR-style graph with the workload's parameters at {args.cpu_sample_nodes} nodes "
-                         f"(|E| = {E}), planted partition, single-threaded oracle, {t:.1f} s"}
+                         f"(|E| = {E}), planted partition, single-threaded oracle, {t:.1f} s",
+               "host": host_cpu()}
     extras = {}
     if rank == 0 and world == 1 and not args.no_extras:
         try:
@@ -687,8 +729,10 @@ def run_ours(args):
             "roofline": res["roofline"], "cpu_baseline": cpu, "e2e": res["e2e"],
             "gpu_launches": res["launches"], "clocks": res["clocks"],
             "kernel_share": res["kernel_share"], "result": res["result"],
-            "extras": extras | ({"graph_as_given": res["unordered"]} if res["unordered"] else {})
-                      | ({"compare": res["compare"]} if res["compare"] else {})
+            "orders": {"reordered" if not args.no_reorder else "as_given":
+                       {"value": res["value"], "unit": UNIT, "ms_per_step": res["ms_per_step"]}}
+                      | ({"as_given": res["unordered"]} if res["unordered"] else {}),
+            "extras": extras | ({"compare": res["compare"]} if res["compare"] else {})
                       | ({"detect": res["detect"]} if res["detect"] else {}),
         }
         print(json.dumps(line), flush=True)

@@ -268,6 +268,22 @@ qm_status qm_workspace_bytes(const qm_graph *g, int32_t K, int32_t with_compare,
 qm_status qm_release_cache(void);
 
 /*
+ * qm_debug_set_stage_wait -- test hook for the bounded device wait (no
+ * counterpart in the paper).  The pair-count kernel stages each long run of
+ * packed labels into shared memory with an asynchronous bulk copy and waits for
+ * it on an mbarrier for at most `polls` polls (default 2^22); when the wait
+ * expires the kernel stops issuing copies, lets the one copy in flight land
+ * (a second wait, bounded by the default), sets a status bit and returns, and
+ * the call returns QM_ETIMEOUT with the context still usable.  Setting polls to
+ * 0 makes every such wait expire at its first check, without withholding any
+ * copy, so that a test can drive this path; a negative value restores the
+ * default.  Applies to all later calls in the process (captured calls are
+ * dropped, as by qm_release_cache).  Only the two-phase scoring pipeline
+ * stages copies.
+ */
+qm_status qm_debug_set_stage_wait(int64_t polls);
+
+/*
  * Tuning.  qm_autotune times the candidate launch shapes of the scoring and
  * batched kernels on the given inputs and caches the fastest per size bucket
  * (log2 n_nodes, log2 n_arcs, log2 K).  qm_get_tuning reports the shape the

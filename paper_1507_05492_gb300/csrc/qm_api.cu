@@ -1254,6 +1254,12 @@ qm_status qm_release_cache(void)
     return QM_OK;
 }
 
+qm_status qm_debug_set_stage_wait(int64_t polls)
+{
+    qm::set_stage_wait_polls((long long)polls);
+    return qm_release_cache();  // captured calls hold the old limit in their kernel arguments
+}
+
 // ------------------------------------------------------------------ tuning
 
 qm_status qm_get_tuning(const qm_graph *gc, int32_t K, qm_tuning *t)

@@ -180,6 +180,10 @@ void prepare_batched_kernel();
 // Occupancy of the community-major kernels for a shape.
 int score_blocks_per_sm(const Shape &sh);
 
+// Poll limit of k_count's pipelined staging wait for later launches (negative:
+// the default).
+void set_stage_wait_polls(long long polls);
+
 // ---- batched persistent kernel
 
 // One work item of the batched kernel: score and/or compare one partition.

@@ -11,6 +11,7 @@
 // qm_compare_partitions runs the same counting sort on the detected labels,
 // hashes the ground-truth labels of each detected community's members into the
 // contingency cells, then walks the ground-truth communities for the row maxima.
+#include <atomic>
 #include <climits>
 
 #include "qm_internal.h"
@@ -978,9 +979,20 @@ struct CountKArgs {
     int *counters;
     const int *status;
     CountPlan plan;
+    unsigned stage_wait;  // polls of each pipelined staging wait before the block gives up
 };
 
 constexpr unsigned STAGE_WAIT_LIMIT = 1u << 22;
+
+// Poll limit of the pipelined staging wait of k_count for later launches
+// (qm_debug_set_stage_wait).  The wait that drains a block's copies after an
+// expiry always keeps STAGE_WAIT_LIMIT.
+static std::atomic<unsigned> g_stage_wait{STAGE_WAIT_LIMIT};
+
+void set_stage_wait_polls(long long polls)
+{
+    g_stage_wait.store(polls < 0 ? STAGE_WAIT_LIMIT : (unsigned)std::min(polls, (long long)INT_MAX));
+}
 
 // Phase B.  Runs longer than a warp table takes go to whole blocks in a static
 // round-robin; while a block counts one run, the next run is already on its
@@ -1041,15 +1053,20 @@ __global__ void __launch_bounds__(1024) k_count(CountKArgs a)
         const int k = it & 1;
         RunHdr nn = none;
         if (tid == 0) {
-            const RunHdr hn = ring[(it + 1) % 3];
-            if (hn.c >= 0) {
-                fence_proxy_async_smem();
-                issue(hn, k ^ 1);
+            // wait for this run's copy first and issue the next one only then, so
+            // that at most one copy is in flight whenever a wait can expire
+            if (mbar_wait(&bars[k], cnt_of(used, k) & 1u, a.stage_wait)) {
+                consume(k);
+                const RunHdr hn = ring[(it + 1) % 3];
+                if (hn.c >= 0) {
+                    fence_proxy_async_smem();
+                    issue(hn, k ^ 1);
+                }
+                const long long idx = b + (long long)(it + 2) * G;
+                if (idx < nbig) nn = a.big[idx];
+            } else {
+                s_timeout = 1;
             }
-            const long long idx = b + (long long)(it + 2) * G;
-            if (idx < nbig) nn = a.big[idx];
-            if (mbar_wait(&bars[k], cnt_of(used, k) & 1u, STAGE_WAIT_LIMIT)) consume(k);
-            else s_timeout = 1;
         }
         block_sync();
         if (s_timeout) {
@@ -1060,7 +1077,9 @@ __global__ void __launch_bounds__(1024) k_count(CountKArgs a)
         if (tid == 0) ring[(it + 2) % 3] = nn;
     }
     if (aborted) {
-        // report, and let the copies still in flight land before the block exits
+        // report, and let the one copy still in flight land before the block
+        // exits (thread 0 keeps the block, and so its shared memory, alive
+        // while it waits; the wait is bounded like every other)
         if (tid == 0) {
             atomicOr(a.x.err, 4);
             for (int q = 0; q < 2; ++q)
@@ -1465,6 +1484,7 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
     a.counters = ws.counters;
     a.status = ws.status;
     a.plan = cp;
+    a.stage_wait = g_stage_wait.load();
     TRACE("k_count");
     const int count_grid = community_grid(K, num_sms, sh);  // sh.blocks_per_sm: occupancy resolved by the caller
     if (K < (1 << 24) - 1) k_count<EpochTable32><<<count_grid, sh.threads, sh.smem_bytes, s>>>(a);

@@ -96,6 +96,7 @@ def _signatures(lib):
         "qm_score_graphs_batched": [_P, _P, _P, _I32, S, _P, _P],
         "qm_workspace_bytes": [_P, _I32, _I32, _I32, _P],
         "qm_release_cache": [],
+        "qm_debug_set_stage_wait": [_I64],
         "qm_autotune": [_P, _P, _I32, S, _P, _P],
         "qm_get_tuning": [_P, _I32, _P],
         "qm_set_tuning": [_P, _I32, _P],
@@ -524,3 +525,10 @@ def trace_read() -> list[tuple[str, float]]:
 
 def release_cache():
     _check(lib().qm_release_cache(), "qm_release_cache")
+
+
+def debug_set_stage_wait(polls: int):
+    """qm_debug_set_stage_wait: poll limit of the pair-count kernel's staging
+    wait for later calls (0: every such wait expires at once; negative: the
+    default).  A test hook for the QM_ETIMEOUT path."""
+    _check(lib().qm_debug_set_stage_wait(int(polls)), "qm_debug_set_stage_wait")

@@ -1,5 +1,10 @@
 """The batched persistent launch: every result must equal, bit for bit, the
-plain one-partition call on the same inputs (which itself matches the oracle)."""
+plain one-partition call on the same inputs (which itself matches the oracle),
+and at the benchmark's batched shape (1,024 candidates per launch on 100,000-node
+graphs with mixing 0.1, 0.3 and 0.5) every item matches the oracle."""
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 import pytest
 import torch
@@ -115,3 +120,26 @@ def test_autotune_batched_keeps_results(qm, setup):
         assert oq == ref_q and oc == ref_c, shape
     with pytest.raises(qm.QmError):                      # more threads than the kernel's launch bound
         qm.set_batch_tuning(graph, max(Ks), 1024, 96 * 1024, 128)
+
+
+@pytest.mark.parametrize("workload", ["lfr100k_mu01", "lfr100k_mu03", "lfr100k_mu05"])
+def test_full_batch_against_oracle(qm, oracle_mod, workload):
+    """One launch of 1,024 candidates (community counts 500-5,000, up to half of
+    the nodes moved), scored and compared with the planted partition, exactly as
+    bench.py times it; every item of both families against the oracle."""
+    from paper_1507_05492_gb300 import gen
+    g = gen.lfr_graph(gen.config_params(workload), device="cuda")
+    graph = qm.Graph(g.row_ptr, g.col)
+    labs, Ks = gen.candidate_batch(g.labels, 1024, seed=10_000)
+    oq, oc = qm.evaluate_batched(graph, labs, Ks, g.labels, g.K)
+    rp, col, truth = g.row_ptr.cpu().numpy(), g.col.cpu().numpy(), g.labels.cpu().numpy()
+    L = labs.cpu().numpy()
+
+    def both(p):
+        return (oracle_mod.score(rp, col, L[p], Ks[p]), oracle_mod.compare(truth, L[p], g.K, Ks[p]))
+
+    with ThreadPoolExecutor(max(1, os.cpu_count() or 1)) as ex:
+        ref = list(ex.map(both, range(len(Ks))))
+    for p, (o_s, o_c) in enumerate(ref):
+        check_quality(oq[p], o_s, f"{workload} candidate {p}")
+        check_compare(oc[p], o_c, f"{workload} candidate {p}")

@@ -2,10 +2,16 @@
 times (default launch shape, graph and labels resident on the device).
 
 * 10M nodes (|E| ~ 9.6e7): every output against the whole-graph oracle.
-* 100M nodes (|E| ~ 9.6e8): the whole oracle is too slow here, so sampled
-  communities are checked one by one against the oracle's per-community routine
-  (sizes, |E_c^in|, |E_c^out| bit-exact, Qds terms within tolerance), and the
-  totals against identities that hold at any size."""
+* 100M nodes (|E| ~ 9.6e8): every output against the whole-graph oracle, on
+  the graph loaded with QM_REORDER (the order bench.py times) and on the graph
+  as given, plus the comparison of the planted partition with a copy with 20%
+  of the nodes moved (Eqs. 1-7) against the oracle.  The oracle runs in worker
+  threads while the GPU calls are made.
+* 100M nodes, sampled: communities checked one by one against the oracle's
+  per-community routine, and the totals against identities that hold at any
+  size."""
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 import pytest
 import torch
@@ -42,6 +48,45 @@ def test_ten_million_nodes_against_whole_oracle(qm, oracle_mod):
     from helpers import check_compare
     c = qm.compare(g.labels, p, g.K, g.K)
     check_compare(c, oracle_mod.compare(lab, p.cpu().numpy(), g.K, g.K), "lfr10m compare")
+
+
+def test_hundred_million_nodes_against_whole_oracle(qm, oracle_mod):
+    from helpers import check_compare
+    from paper_1507_05492_gb300 import gen
+    g = gen.lfr_graph(gen.config_params("lfr100m"), device="cuda")
+    found = gen.perturb(g.labels, g.K, 0.2, seed=9)
+    rp, col, lab = g.row_ptr.cpu().numpy(), g.col.cpu().numpy(), g.labels.cpu().numpy()
+    found_np = found.cpu().numpy()
+    with ThreadPoolExecutor(2) as ex:
+        fut_score = ex.submit(oracle_mod.score, rp, col, lab, g.K, True)
+        fut_cmp = ex.submit(oracle_mod.compare, lab, found_np, g.K, g.K)
+        results = {}
+        for reorder in (True, False):
+            graph = qm.Graph(g.row_ptr, g.col, reorder=reorder)
+            q = qm.score(graph, g.labels, g.K, per_community=True)
+            q["per_community"] = {k: v.cpu().numpy() for k, v in q["per_community"].items()}
+            q_plain = qm.score(graph, g.labels, g.K)      # the call bench.py times (no per-community output)
+            results[reorder] = (q, q_plain)
+            graph.close()
+            del graph
+        c = qm.compare(g.labels, found, g.K, g.K)
+        o = fut_score.result()
+        oc = fut_cmp.result()
+    opc = o["per_community"]
+    for reorder, (q, q_plain) in results.items():
+        ctx = f"lfr100m reorder={reorder}"
+        check_quality(q, o, ctx)
+        check_quality(q_plain, o, ctx + " (no per-community output)")
+        pc = q["per_community"]
+        for k in ("size", "intra_edges", "inter_edges"):
+            assert np.array_equal(pc[k], opc[k]), (ctx, k)
+        a, b = pc["qds_term"], opc["qds_term"]
+        assert np.all(np.abs(a - b) <= 1e-12 * np.maximum(np.abs(b), 1e-6)), ctx
+        for k in ("intra_density", "contraction", "expansion", "conductance"):
+            assert np.all(np.abs(pc[k] - opc[k]) <= 1e-12 * np.abs(opc[k])), (ctx, k)
+    # both node orders give the same bits
+    assert {k: v for k, v in results[True][1].items()} == results[False][1]
+    check_compare(c, oc, "lfr100m planted vs 20% moved")
 
 
 def test_hundred_million_nodes_sampled(qm, oracle_mod):

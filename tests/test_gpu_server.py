@@ -1,14 +1,17 @@
 """The serving loop: requests of different graph sizes admitted by a memory
 budget and batched as they arrive; each result in the mix must equal the
-result of the same request scored alone."""
+result of the same request scored alone, and, on the serving workload's own
+graphs (10k, 1M and 10M nodes), the oracle's result for that request."""
+import os
 import threading
+from concurrent.futures import ThreadPoolExecutor
 import time
 
 import numpy as np
 import pytest
 import torch
 
-from helpers import to_dev
+from helpers import check_compare, check_quality, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -159,3 +162,56 @@ def test_malformed_requests_are_refused_at_submit(env):
     good = srv.submit("mid", pools["mid"][0], K)
     assert good.result(timeout=60)["quality"] == qm.score(graphs["mid"], pools["mid"][0], K)
     srv.close()
+
+
+def test_serving_workload_graphs_against_oracle():
+    """Poisson-like arrivals over resident 10k-, 1M- and 10M-node graphs (the
+    serving configuration), each request a partition with up to half of the
+    nodes moved and half of them with a comparison against the planted
+    partition; every served result against the oracle."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from oracle import oracle
+    from paper_1507_05492_gb300 import gen, qm
+    from paper_1507_05492_gb300.server import Server
+    graphs, host, pools = {}, {}, {}
+    for gid in ("lfr10k", "lfr1m", "lfr10m"):
+        g = gen.lfr_graph(gen.config_params(gid), device="cuda")
+        graphs[gid] = qm.Graph(g.row_ptr, g.col, reorder=(g.n >= 1_000_000))
+        host[gid] = (g.row_ptr.cpu().numpy(), g.col.cpu().numpy(), g.labels.cpu().numpy(), g.K, g.labels)
+        pools[gid] = [gen.perturb(g.labels, g.K, 0.5 * i / 5, seed=700 + i) for i in range(6)]
+    rng = np.random.default_rng(11)
+    srv = Server(graphs, budget_bytes=8 << 30, max_batch=64, n_streams=3)
+    futs = []
+    for i in range(90):
+        gid = ("lfr10k", "lfr1m", "lfr10m")[rng.integers(3)]
+        j = int(rng.integers(len(pools[gid])))
+        with_truth = bool(rng.random() < 0.5)
+        K = host[gid][3]
+        truth = host[gid][4] if with_truth else None
+        futs.append((gid, j, with_truth, srv.submit(gid, pools[gid][j], K, truth, K if with_truth else None)))
+        time.sleep(float(rng.exponential(1 / 400)))
+    served = [(gid, j, wt, f.result(timeout=300)) for gid, j, wt, f in futs]
+    srv.close()
+    need = sorted({(gid, j) for gid, j, _, _ in served})
+    need_c = sorted({(gid, j) for gid, j, wt, _ in served if wt})
+
+    def o_score(key):
+        gid, j = key
+        rp, col, _, K, _ = host[gid]
+        return key, oracle.score(rp, col, pools[gid][j].cpu().numpy(), K)
+
+    def o_cmp(key):
+        gid, j = key
+        _, _, lab, K, _ = host[gid]
+        return key, oracle.compare(lab, pools[gid][j].cpu().numpy(), K, K)
+
+    with ThreadPoolExecutor(max(1, min(8, os.cpu_count() or 1))) as ex:
+        os_ = dict(ex.map(o_score, need))
+        oc_ = dict(ex.map(o_cmp, need_c))
+    for gid, j, wt, res in served:
+        check_quality(res["quality"], os_[(gid, j)], f"served {gid} partition {j}")
+        if wt:
+            check_compare(res["compare"], oc_[(gid, j)], f"served {gid} partition {j} vs planted")
+    for gr in graphs.values():
+        gr.close()
