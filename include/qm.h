@@ -292,11 +292,18 @@ qm_status qm_debug_set_stage_wait(int64_t polls);
  * community (used by algorithm 0 only).  algorithm selects the scoring pipeline:
  *   0  one kernel visits every community's members and gathers their
  *      neighbours' labels itself;
- *   1  (default) the neighbour labels are first written out in community order
- *      (one streaming pass over the arcs), then a second kernel counts each
+ *   1  the neighbour labels are first written out in community order (one
+ *      streaming pass over the arcs), then a second kernel counts each
  *      community's contiguous segment and a third forms the FP64 terms of all
- *      communities in parallel.
- * Both give bit-identical results.
+ *      communities in parallel (the default up to 2^24 nodes);
+ *   2  as 1, but an arc whose far end is not close to its near end in node-id
+ *      order has its label gathered later, through bins by windows of the
+ *      node ids, so that those gathers hit one L2-sized window of the label
+ *      array at a time (the default above 2^24 nodes, unweighted graphs);
+ *   3  as 2 with every arc binned and about four windows (for tests and
+ *      comparisons on small graphs).
+ * All give bit-identical results.  Weighted graphs take algorithm 1 whatever
+ * is set.
  */
 typedef struct {
     int32_t threads;

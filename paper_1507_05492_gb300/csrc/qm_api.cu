@@ -419,14 +419,17 @@ static Shape shape_for(qm_graph *g, int K, bool batched)
     auto &m = batched ? g->tuning_batch : g->tuning;
     auto it = m.find(bucket_of(g->n, g->n_arcs, K));
     Shape s = it != m.end() ? it->second : (batched ? default_batch_shape() : default_shape());
-    if (!batched && g->wt && s.algo == 0) s = default_shape();  // weighted graphs: two-phase pipeline only
+    // graphs whose label array is beyond what L2 serves at random gather the far
+    // labels through destination-window bins
+    if (!batched && it == m.end() && !g->wt && g->n > BIN_DEFAULT_MIN_NODES) s.algo = 2;
+    if (!batched && g->wt && s.algo != 1) s = default_shape();  // weighted graphs: two-phase pipeline, direct gathers
     return batched ? resolve_batched(s) : resolve_plain(s);
 }
 
 static bool shape_ok(const qm_tuning *t)
 {
     return t && t->threads >= 64 && t->threads <= 1024 && t->threads % 32 == 0 && t->smem_bytes >= 16384 &&
-           t->smem_bytes <= MAX_DYN_SMEM && t->big_community >= 1 && (t->algorithm == 0 || t->algorithm == 1) &&
+           t->smem_bytes <= MAX_DYN_SMEM && t->big_community >= 1 && (t->algorithm >= 0 && t->algorithm <= 3) &&
            plan_smem(t->threads, t->smem_bytes).max_used_w >= 32;
 }
 
@@ -660,8 +663,10 @@ static size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 qm_status qm_workspace_bytes(const qm_graph *g, int32_t K, int32_t with_compare, int32_t k_truth, size_t *bytes)
 {
     if (!g || !bytes || K < 1 || (with_compare && k_truth < 1)) return fail(QM_EINVAL, "bad argument");
-    size_t b = std::max(score_ws_bytes(g->n, K), score2_ws_bytes(g->n, g->n_arcs, K, g->wt != nullptr)) +
-               al256((size_t)g->n * 4);
+    const bool wt = g->wt != nullptr;
+    size_t b = std::max(score_ws_bytes(g->n, K), score2_ws_bytes(g->n, g->n_arcs, K, wt)) + al256((size_t)g->n * 4);
+    if (!wt && g->n > BIN_DEFAULT_MIN_NODES)  // the default two-phase call of such a graph bins its far gathers
+        b = std::max(b, score2_ws_bytes(g->n, g->n_arcs, K, wt, 2) + al256((size_t)g->n * 4));
     if (g->inv) b += al256((size_t)g->n * 4);
     if (with_compare) b += compare_ws_bytes(g->n, k_truth, K) + al256((size_t)g->n * 4);
     *bytes = b;
@@ -687,7 +692,8 @@ static qm_status score_impl(qm_graph *g, const int32_t *labels, int32_t K, qm_me
     const long long n = g->n;
     const bool weighted = g->wt != nullptr;
     const bool graphed = !pc && !t_trace.on && n <= kPlainGraphMaxN;
-    size_t need = sh.algo ? score2_ws_bytes(n, g->n_arcs, K, weighted) : score_ws_bytes(n, K);
+    const int bmode = bin_mode_of(sh.algo, weighted);
+    size_t need = sh.algo ? score2_ws_bytes(n, g->n_arcs, K, weighted, bmode) : score_ws_bytes(n, K);
     const size_t lab_off = need;
     if (where == QM_HOST || graphed) need += al256((size_t)n * 4);
     const size_t perm_off = need;
@@ -699,7 +705,7 @@ static qm_status score_impl(qm_graph *g, const int32_t *labels, int32_t K, qm_me
     Lease pin(g_pool.acquire(al256(std::max(sizeof(qm_quality), (size_t)QM_PARTIAL_WORDS * 8)) + 256, g->device,
                              true));
     if (!ws.b || !pin.b) return fail(QM_ENOMEM, "scratch allocation failed");
-    ScoreWs w = sh.algo ? carve_score2_ws(ws.ptr(), n, g->n_arcs, K, weighted) : carve_score_ws(ws.ptr(), n, K);
+    ScoreWs w = sh.algo ? carve_score2_ws(ws.ptr(), n, g->n_arcs, K, weighted, bmode) : carve_score_ws(ws.ptr(), n, K);
     const int32_t *dl = labels;
     if (where == QM_HOST || graphed) {
         dl = (const int32_t *)(ws.ptr() + lab_off);
@@ -843,7 +849,11 @@ qm_status qm_score_partition_part(const qm_graph *gc, const int32_t *labels, int
     if (where != QM_HOST && where != QM_DEVICE) return fail(QM_EINVAL, "bad memory kind");
     DeviceGuard dg(g->device);
     Shape sh = shape_for(g, K, false);
-    if (sh.algo != 1) sh = resolve_plain(default_shape());  // shards run the two-phase pipeline
+    if (sh.algo == 0) {  // shards run the two-phase pipeline
+        Shape d = default_shape();
+        if (!g->wt && g->n > BIN_DEFAULT_MIN_NODES) d.algo = 2;
+        sh = resolve_plain(d);
+    }
     std::memset(out, 0, sizeof(*out));
     const qm_status st = score_impl(g, labels, K, where, nullptr, nullptr, (cudaStream_t)stream, sh, rank, nranks,
                                     out->words);
@@ -1251,6 +1261,8 @@ qm_status qm_release_cache(void)
     std::lock_guard<std::mutex> lk(g_graph_mu);
     for (auto &kv : g_graphs) cudaGraphExecDestroy(kv.second);
     g_graphs.clear();
+    for (auto &kv : g_plain_graphs) cudaGraphExecDestroy(kv.second.exec);
+    g_plain_graphs.clear();
     return QM_OK;
 }
 
@@ -1449,12 +1461,13 @@ qm_status qm_autotune(const qm_graph *gc, const int32_t *labels, int32_t K, qm_m
     float best_ms = 1e30f;
     Shape best = default_shape();
     qm_quality q;
-    for (int al : {1, 0})
+    for (int al : {2, 1, 0})
     for (int th : threads_c)
         for (int sm : smem_c)
             for (int bg : big_c) {
-                if (al == 1 && bg != big_c[0]) continue;  // the two-phase path has no size split
+                if (al >= 1 && bg != big_c[0]) continue;  // the two-phase path has no size split
                 if (al == 0 && g->wt) continue;           // weighted graphs: two-phase pipeline only
+                if (al == 2 && (g->wt || g->n <= BIN_DEFAULT_MIN_NODES)) continue;  // binning pays beyond L2 only
                 Shape sh;
                 sh.threads = th;
                 sh.smem_bytes = sm;

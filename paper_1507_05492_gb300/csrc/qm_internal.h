@@ -82,6 +82,12 @@ struct ScoreWs {
     float *nbrw = nullptr;      // weighted graphs: [n_arcs] weights of the packed cut arcs
     unsigned long long *wl = nullptr;    // weighted graphs: [K][6] intra / cut weight limbs (zeroed)
     unsigned long long *recw = nullptr;  // weighted graphs: [K][4] 256-bit weighted pair sums
+    // far-end gathers through destination-window bins (algorithms 2 and 3; qm_binned.cuh)
+    unsigned long long *bin_pool = nullptr, *bin_list = nullptr, *bin_sorted = nullptr;
+    int *bin_ctr = nullptr;     // [64] counters (zeroed)
+    int *bin_seg = nullptr;     // [K]
+    long long bin_chunks = 0;   // pool capacity in chunks
+    int bin_shift = 0, bin_nbins = 0, bin_near = 0;
     size_t zero_bytes;          // bytes from `status` that must start at zero
     size_t bytes;               // total bytes carved (the *_ws_bytes size)
 };
@@ -107,8 +113,18 @@ struct CompareWs {
 };
 
 size_t score_ws_bytes(long long n, int K);
-size_t score2_ws_bytes(long long n, long long n_arcs, int K, bool weighted = false);
-ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K, bool weighted = false);
+// bin_mode (two-phase pipeline): 0 gathers every label directly; 2 bins the
+// arcs whose far end is not close in node-id order, by windows of at least 2^23
+// node ids; 3 bins every arc, by about four windows (tests and comparisons).
+// Weighted graphs take mode 0.
+size_t score2_ws_bytes(long long n, long long n_arcs, int K, bool weighted = false, int bin_mode = 0);
+ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K, bool weighted = false, int bin_mode = 0);
+// The binning mode of a two-phase launch shape on a graph (algorithm 2 or 3
+// on an unweighted graph; 0 otherwise).
+inline int bin_mode_of(int algo, bool weighted) { return (!weighted && (algo == 2 || algo == 3)) ? algo : 0; }
+// Graphs with more nodes than this take the binned gathers by default: their
+// label array (4 bytes a node) is beyond what L2 serves at random.
+constexpr long long BIN_DEFAULT_MIN_NODES = 1LL << 24;
 size_t compare_ws_bytes(long long n, int ka, int kb);
 ScoreWs carve_score_ws(void *base, long long n, int K);
 CompareWs carve_compare_ws(void *base, long long n, int ka, int kb);

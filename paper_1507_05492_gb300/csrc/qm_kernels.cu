@@ -932,6 +932,8 @@ __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__re
     }
 }
 
+#include "qm_binned.cuh"
+
 // One header per non-empty community, sorted into three lists by run length
 // m (the community's cut arcs, an upper bound on its distinct neighbouring
 // communities): m <= warp_fill for single warps, warp_fill < m <= block_fill
@@ -1196,6 +1198,8 @@ void prepare_kernels()
     cudaFuncSetAttribute(k_count<EpochTable32>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     cudaFuncSetAttribute(k_count_long, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     cudaFuncSetAttribute(k_count_w, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+    cudaFuncSetAttribute(k_expand_bin, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         bin_smem_bytes_per_warp(BIN_MAX) * (EXPAND_THREADS / 32));
     int nb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_count_w, COUNT_W_THREADS, COUNT_W_SMEM);
     g_count_w_blocks_per_sm = nb > 0 ? nb : 1;
@@ -1308,14 +1312,30 @@ int launch_score(const GraphDev &g, const int *labels, int K, const ScoreWs &ws,
     return cudaGetLastError() == cudaSuccess ? launches : -1;
 }
 
-size_t score2_ws_bytes(long long n, long long n_arcs, int K, bool weighted)
+size_t score2_ws_bytes(long long n, long long n_arcs, int K, bool weighted, int bin_mode)
 {
-    return carve_score2_ws(reinterpret_cast<void *>(4096), n, n_arcs, K, weighted).bytes;
+    return carve_score2_ws(reinterpret_cast<void *>(4096), n, n_arcs, K, weighted, bin_mode).bytes;
 }
 
-ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K, bool weighted)
+// Window size, window count and nearness distance of the binned gathers.
+static void bin_geometry(long long n, int mode, int *shift, int *nbins, int *near)
+{
+    int lg = 0;
+    while ((1LL << lg) < n) ++lg;  // ceil(log2 n)
+    if (mode == 2) {
+        *shift = std::max(23, lg - 4);
+        *near = 1 << 14;
+    } else {
+        *shift = std::max(4, lg - 2);
+        *near = 0;
+    }
+    *nbins = (int)(((std::max(n, 1LL) - 1) >> *shift) + 1);
+}
+
+ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K, bool weighted, int bin_mode)
 {
     ScoreWs w{};
+    if (weighted) bin_mode = 0;
     const int tiles = scan_tiles((int)std::max<long long>(n, K));
     char *p = (char *)base;
     w.status = (int *)p;
@@ -1333,7 +1353,24 @@ ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K, bool w
         w.wl = (unsigned long long *)p;
         p += align_up((size_t)K * 6 * 8, 256);
     }
+    if (bin_mode) {
+        w.bin_ctr = (int *)p;
+        p += align_up(BC_WORDS * 4, 256);
+    }
     w.zero_bytes = (size_t)(p - (char *)base);
+    if (bin_mode) {
+        bin_geometry(n, bin_mode, &w.bin_shift, &w.bin_nbins, &w.bin_near);
+        const long long warps = std::min<long long>((n + 255) / 256, BIN_MAX_BLOCKS) * (EXPAND_THREADS / 32);
+        w.bin_chunks = n_arcs / BIN_CHUNK + 1 + warps * w.bin_nbins;
+        w.bin_seg = (int *)p;
+        p += align_up((size_t)K * 4, 256);
+        w.bin_list = (unsigned long long *)p;
+        p += align_up((size_t)w.bin_chunks * 8, 256);
+        w.bin_sorted = (unsigned long long *)p;
+        p += align_up((size_t)w.bin_chunks * 8, 256);
+        w.bin_pool = (unsigned long long *)p;
+        p += align_up((size_t)w.bin_chunks * BIN_CHUNK * 8, 256);
+    }
     if (weighted) {
         w.nbrw = (float *)p;
         p += align_up((size_t)n_arcs * 4, 256) + 256;
@@ -1460,10 +1497,32 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
         ++launches;
         return launch_weighted_tail(g, K, ws, pc, num_sms, s, tr, own, launches);
     }
-    k_expand<false><<<expand_grid(n, num_sms), EXPAND_THREADS, 0, s>>>(g.row_ptr, g.col, labels, ws.members, ws.aoff, ws.start,
-                                                           n, ws.inter, ws.nbr, ws.status, own, nullptr, nullptr,
-                                                           nullptr);
-    ++launches;
+    if (ws.bin_pool) {
+        BinArgs ba;
+        ba.pool = ws.bin_pool;
+        ba.list = ws.bin_list;
+        ba.sorted = ws.bin_sorted;
+        ba.ctr = ws.bin_ctr;
+        ba.seg = ws.bin_seg;
+        ba.pool_chunks = ws.bin_chunks;
+        ba.shift = ws.bin_shift;
+        ba.nbins = ws.bin_nbins;
+        ba.near = ws.bin_near;
+        const int smem = bin_smem_bytes_per_warp(ba.nbins) * (EXPAND_THREADS / 32);
+        TRACE("k_expand_bin");
+        k_expand_bin<<<std::min(expand_grid(n, num_sms), BIN_MAX_BLOCKS), EXPAND_THREADS, smem, s>>>(
+            g.row_ptr, g.col, labels, ws.members, ws.aoff, ws.start, n, ws.inter, ws.nbr, ws.status, own, ba);
+        TRACE("k_bin_order");
+        k_bin_order<<<num_sms * 2, 256, 0, s>>>(ba, ws.aoff, ws.start, K, ws.status);
+        TRACE("k_resolve");
+        k_resolve<<<num_sms * 8, RESOLVE_THREADS, 0, s>>>(ba, labels, ws.inter, ws.nbr, ws.status);
+        launches += 3;
+    } else {
+        k_expand<false><<<expand_grid(n, num_sms), EXPAND_THREADS, 0, s>>>(g.row_ptr, g.col, labels, ws.members,
+                                                                          ws.aoff, ws.start, n, ws.inter, ws.nbr,
+                                                                          ws.status, own, nullptr, nullptr, nullptr);
+        ++launches;
+    }
     const CountPlan cp = plan_count(sh.threads, sh.smem_bytes);
     TRACE("k_classify");
     k_classify<<<grid_for(K, 256, num_sms, 4), 256, 0, s>>>(ws.start, ws.aoff, ws.inter, K, cp.fill_w, cp.fill,

@@ -1,0 +1,133 @@
+"""The far-end label gathers through destination-window bins (algorithms 2
+and 3 of the two-phase pipeline): the packed runs hold the same multisets as
+with direct gathers, so every result must equal the direct pipeline's bit for
+bit and match the oracle, on LFR-style graphs with several windows and a
+ragged last window, the degenerate partitions, a hub whose run takes the long
+path, isolated nodes, label ids beyond 24 bits, reordered graphs, sharded
+calls and per-community output."""
+import numpy as np
+import pytest
+import torch
+
+from helpers import check_quality, random_graph, star, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qm():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1507_05492_gb300 import qm as q
+    return q
+
+
+@pytest.fixture(scope="module")
+def gen():
+    from paper_1507_05492_gb300 import gen as g
+    return g
+
+
+def by_algo(qm, graph, lab, K, algos=(1, 2, 3), per_community=False):
+    out = {}
+    for a in algos:
+        qm.set_tuning(graph, K, 512, 96 * 1024, 48, a)
+        out[a] = qm.score(graph, lab, K, per_community=per_community)
+    return out
+
+
+@pytest.mark.parametrize("n,seed", [(1000, 1), (100_003, 3), (300_000, 4)])
+def test_lfr_all_algorithms_identical_and_oracle(qm, gen, oracle_mod, n, seed):
+    g = gen.lfr_graph(gen.LfrParams(n=n, k_max=100, s_max=1000, seed=seed))
+    graph = qm.Graph(*to_dev(g.row_ptr, g.col))
+    rp, col = g.row_ptr.numpy(), g.col.numpy()
+    for name, lab in (("planted", g.labels), ("perturbed", gen.perturb(g.labels, g.K, 0.4, seed=seed + 7))):
+        o = oracle_mod.score(rp, col, lab.numpy(), g.K)
+        res = by_algo(qm, graph, lab.cuda(), g.K)
+        for a, q in res.items():
+            check_quality(q, o, f"n={n} {name} algorithm {a}")
+            assert q == res[1], (n, name, a)
+
+
+def test_per_community_output(qm, gen, oracle_mod):
+    g = gen.lfr_graph(gen.LfrParams(n=80_000, k_max=100, s_max=1000, seed=5))
+    graph = qm.Graph(*to_dev(g.row_ptr, g.col))
+    res = by_algo(qm, graph, g.labels.cuda(), g.K, per_community=True)
+    o = oracle_mod.score(g.row_ptr.numpy(), g.col.numpy(), g.labels.numpy(), g.K, per_community=True)
+    for a, q in res.items():
+        for k in ("size", "intra_edges", "inter_edges"):
+            assert np.array_equal(q["per_community"][k].cpu().numpy(), o["per_community"][k]), (a, k)
+        for k in ("intra_density", "contraction", "expansion", "conductance", "qds_term"):
+            assert torch.equal(q["per_community"][k], res[1]["per_community"][k]), (a, k)
+
+
+def test_degenerate_partitions_and_graphs(qm, gen, oracle_mod):
+    g = gen.lfr_graph(gen.LfrParams(n=20_000, seed=6))
+    graph = qm.Graph(*to_dev(g.row_ptr, g.col))
+    n = g.n
+    for lab, K in ((np.zeros(n, np.int32), 1), (np.arange(n, dtype=np.int32), n)):
+        o = oracle_mod.score(g.row_ptr.numpy(), g.col.numpy(), lab, K)
+        res = by_algo(qm, graph, torch.from_numpy(lab).cuda(), K)
+        for a, q in res.items():
+            check_quality(q, o, f"K={K} algorithm {a}")
+            assert q == res[1]
+    # a hub bordering 30k communities (its run takes the long path)
+    rp, col = star(30_000)
+    lab = np.arange(30_001, dtype=np.int32)
+    lab[1:100] = 0
+    graph = qm.Graph(*to_dev(rp, col))
+    o = oracle_mod.score(rp, col, lab, 30_001)
+    res = by_algo(qm, graph, torch.from_numpy(lab).cuda(), 30_001)
+    for a, q in res.items():
+        check_quality(q, o, f"star algorithm {a}")
+        assert q == res[1]
+    # isolated nodes and sparse label ids
+    rp, col = random_graph(5000, 30_000, seed=9)
+    rp = np.concatenate([rp, np.full(700, rp[-1])])
+    lab = np.random.default_rng(9).integers(0, 20_000, 5700).astype(np.int32)
+    graph = qm.Graph(*to_dev(rp, col))
+    o = oracle_mod.score(rp, col, lab, 20_000)
+    res = by_algo(qm, graph, torch.from_numpy(lab).cuda(), 20_000)
+    for a, q in res.items():
+        check_quality(q, o, f"random graph algorithm {a}")
+        assert q == res[1]
+
+
+def test_label_ids_beyond_24_bits(qm, gen):
+    g = gen.lfr_graph(gen.LfrParams(n=30_000, seed=12))
+    graph = qm.Graph(*to_dev(g.row_ptr, g.col))
+    K_big = (1 << 24) + 5
+    ids = np.random.default_rng(12).choice(K_big, g.K, replace=False).astype(np.int32)
+    ids[0] = K_big - 1
+    lab_big = torch.from_numpy(ids[g.labels.numpy()]).cuda()
+    ref = by_algo(qm, graph, g.labels.cuda(), g.K, algos=(1,))[1]
+    for a, q in by_algo(qm, graph, lab_big, K_big).items():
+        assert q == ref, a
+
+
+def test_reordered_sharded_and_host_labels(qm, gen):
+    g = gen.lfr_graph(gen.LfrParams(n=120_000, k_max=100, s_max=1000, seed=13))
+    plain = qm.Graph(*to_dev(g.row_ptr, g.col))
+    reord = qm.Graph(*to_dev(g.row_ptr, g.col), reorder=True)
+    lab = gen.perturb(g.labels, g.K, 0.2, seed=14)
+    ref = by_algo(qm, plain, lab.cuda(), g.K, algos=(1,))[1]
+    for a in (2, 3):
+        for graph in (plain, reord):
+            qm.set_tuning(graph, g.K, 512, 96 * 1024, 48, a)
+            assert qm.score(graph, lab.cuda(), g.K) == ref
+            assert qm.score(graph, lab.numpy(), g.K) == ref
+            parts = [qm.score_part(graph, lab.cuda(), g.K, r, 3) for r in range(3)]
+            assert qm.finalize_part(qm.combine_parts(parts)) == ref
+
+
+def test_weighted_graph_ignores_binning(qm, gen):
+    g = gen.lfr_graph(gen.LfrParams(n=20_000, seed=15))
+    w = torch.rand(g.col.numel(), generator=torch.Generator().manual_seed(3)) + 0.5
+    # symmetric weights: the weight of (u, v) from the unordered pair
+    u = torch.repeat_interleave(torch.arange(g.n), g.row_ptr[1:] - g.row_ptr[:-1])
+    v = g.col.to(torch.int64)
+    key = torch.minimum(u, v) * g.n + torch.maximum(u, v)
+    w = ((key * 2654435761) % 1000).to(torch.float32) / 100.0 + 0.25
+    graph = qm.Graph(*to_dev(g.row_ptr, g.col), weights=w.cuda())
+    res = by_algo(qm, graph, g.labels.cuda(), g.K)
+    assert res[2] == res[1] and res[3] == res[1]

@@ -37,6 +37,12 @@ def test_ten_million_nodes_against_whole_oracle(qm, oracle_mod):
     rp, col, lab = g.row_ptr.cpu().numpy(), g.col.cpu().numpy(), g.labels.cpu().numpy()
     o = oracle_mod.score(rp, col, lab, g.K, per_community=True)
     check_quality(q, o, "lfr10m")
+    # the binned far-end gathers give the same bits
+    q_plain = qm.score(graph, g.labels, g.K)
+    for algo in (2, 3):
+        qm.set_tuning(graph, g.K, 512, 96 * 1024, 48, algo)
+        assert qm.score(graph, g.labels, g.K) == q_plain, algo
+    qm.set_tuning(graph, g.K, 512, 96 * 1024, 48, 1)
     for k in ("size", "intra_edges", "inter_edges"):
         assert np.array_equal(q["per_community"][k].cpu().numpy(), o["per_community"][k]), k
     a, b = q["per_community"]["qds_term"].cpu().numpy(), o["per_community"]["qds_term"]
