@@ -292,16 +292,24 @@ qm_status qm_debug_set_stage_wait(int64_t polls);
  * community (used by algorithm 0 only).  algorithm selects the scoring pipeline:
  *   0  one kernel visits every community's members and gathers their
  *      neighbours' labels itself;
- *   1  the neighbour labels are first written out in community order (one
- *      streaming pass over the arcs), then a second kernel counts each
- *      community's contiguous segment and a third forms the FP64 terms of all
- *      communities in parallel (the default up to 2^24 nodes);
+ *   1  (default) the neighbour labels are first written out in community
+ *      order (one streaming pass over the arcs), then a second kernel counts
+ *      each community's contiguous segment and a third forms the FP64 terms of
+ *      all communities in parallel;
  *   2  as 1, but an arc whose far end is not close to its near end in node-id
  *      order has its label gathered later, through bins by windows of the
  *      node ids, so that those gathers hit one L2-sized window of the label
- *      array at a time (the default above 2^24 nodes, unweighted graphs);
+ *      array at a time (measured slower than 1 on the LFR-style graphs of
+ *      10^8 nodes, in either node order; the autotuner tries it above 2^24
+ *      nodes);
  *   3  as 2 with every arc binned and about four windows (for tests and
- *      comparisons on small graphs).
+ *      comparisons on small graphs);
+ *   4  as 1, with the far-end labels always gathered from a copy packed three
+ *      21-bit ids to a 64-bit word (8/3 bytes a node instead of 4, so a larger
+ *      share of it stays in L2); algorithm 1 does this on graphs of more than
+ *      2^22 nodes;
+ *   5  as 1, never packed.
+ * Packing needs K <= 2^21; with more label ids the 32-bit labels are gathered.
  * All give bit-identical results.  Weighted graphs take algorithm 1 whatever
  * is set.
  */

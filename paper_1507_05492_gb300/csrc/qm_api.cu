@@ -419,9 +419,6 @@ static Shape shape_for(qm_graph *g, int K, bool batched)
     auto &m = batched ? g->tuning_batch : g->tuning;
     auto it = m.find(bucket_of(g->n, g->n_arcs, K));
     Shape s = it != m.end() ? it->second : (batched ? default_batch_shape() : default_shape());
-    // graphs whose label array is beyond what L2 serves at random gather the far
-    // labels through destination-window bins
-    if (!batched && it == m.end() && !g->wt && g->n > BIN_DEFAULT_MIN_NODES) s.algo = 2;
     if (!batched && g->wt && s.algo != 1) s = default_shape();  // weighted graphs: two-phase pipeline, direct gathers
     return batched ? resolve_batched(s) : resolve_plain(s);
 }
@@ -429,7 +426,7 @@ static Shape shape_for(qm_graph *g, int K, bool batched)
 static bool shape_ok(const qm_tuning *t)
 {
     return t && t->threads >= 64 && t->threads <= 1024 && t->threads % 32 == 0 && t->smem_bytes >= 16384 &&
-           t->smem_bytes <= MAX_DYN_SMEM && t->big_community >= 1 && (t->algorithm >= 0 && t->algorithm <= 3) &&
+           t->smem_bytes <= MAX_DYN_SMEM && t->big_community >= 1 && (t->algorithm >= 0 && t->algorithm <= 5) &&
            plan_smem(t->threads, t->smem_bytes).max_used_w >= 32;
 }
 
@@ -664,9 +661,9 @@ qm_status qm_workspace_bytes(const qm_graph *g, int32_t K, int32_t with_compare,
 {
     if (!g || !bytes || K < 1 || (with_compare && k_truth < 1)) return fail(QM_EINVAL, "bad argument");
     const bool wt = g->wt != nullptr;
-    size_t b = std::max(score_ws_bytes(g->n, K), score2_ws_bytes(g->n, g->n_arcs, K, wt)) + al256((size_t)g->n * 4);
-    if (!wt && g->n > BIN_DEFAULT_MIN_NODES)  // the default two-phase call of such a graph bins its far gathers
-        b = std::max(b, score2_ws_bytes(g->n, g->n_arcs, K, wt, 2) + al256((size_t)g->n * 4));
+    size_t b = std::max(score_ws_bytes(g->n, K),
+                        score2_ws_bytes(g->n, g->n_arcs, K, wt, 0, packs_labels(1, wt, g->n, K))) +
+               al256((size_t)g->n * 4);
     if (g->inv) b += al256((size_t)g->n * 4);
     if (with_compare) b += compare_ws_bytes(g->n, k_truth, K) + al256((size_t)g->n * 4);
     *bytes = b;
@@ -693,7 +690,8 @@ static qm_status score_impl(qm_graph *g, const int32_t *labels, int32_t K, qm_me
     const bool weighted = g->wt != nullptr;
     const bool graphed = !pc && !t_trace.on && n <= kPlainGraphMaxN;
     const int bmode = bin_mode_of(sh.algo, weighted);
-    size_t need = sh.algo ? score2_ws_bytes(n, g->n_arcs, K, weighted, bmode) : score_ws_bytes(n, K);
+    const bool pack = packs_labels(sh.algo, weighted, n, K);
+    size_t need = sh.algo ? score2_ws_bytes(n, g->n_arcs, K, weighted, bmode, pack) : score_ws_bytes(n, K);
     const size_t lab_off = need;
     if (where == QM_HOST || graphed) need += al256((size_t)n * 4);
     const size_t perm_off = need;
@@ -705,7 +703,8 @@ static qm_status score_impl(qm_graph *g, const int32_t *labels, int32_t K, qm_me
     Lease pin(g_pool.acquire(al256(std::max(sizeof(qm_quality), (size_t)QM_PARTIAL_WORDS * 8)) + 256, g->device,
                              true));
     if (!ws.b || !pin.b) return fail(QM_ENOMEM, "scratch allocation failed");
-    ScoreWs w = sh.algo ? carve_score2_ws(ws.ptr(), n, g->n_arcs, K, weighted, bmode) : carve_score_ws(ws.ptr(), n, K);
+    ScoreWs w = sh.algo ? carve_score2_ws(ws.ptr(), n, g->n_arcs, K, weighted, bmode, pack)
+                        : carve_score_ws(ws.ptr(), n, K);
     const int32_t *dl = labels;
     if (where == QM_HOST || graphed) {
         dl = (const int32_t *)(ws.ptr() + lab_off);
@@ -849,11 +848,7 @@ qm_status qm_score_partition_part(const qm_graph *gc, const int32_t *labels, int
     if (where != QM_HOST && where != QM_DEVICE) return fail(QM_EINVAL, "bad memory kind");
     DeviceGuard dg(g->device);
     Shape sh = shape_for(g, K, false);
-    if (sh.algo == 0) {  // shards run the two-phase pipeline
-        Shape d = default_shape();
-        if (!g->wt && g->n > BIN_DEFAULT_MIN_NODES) d.algo = 2;
-        sh = resolve_plain(d);
-    }
+    if (sh.algo == 0) sh = resolve_plain(default_shape());  // shards run the two-phase pipeline
     std::memset(out, 0, sizeof(*out));
     const qm_status st = score_impl(g, labels, K, where, nullptr, nullptr, (cudaStream_t)stream, sh, rank, nranks,
                                     out->words);
@@ -1461,13 +1456,14 @@ qm_status qm_autotune(const qm_graph *gc, const int32_t *labels, int32_t K, qm_m
     float best_ms = 1e30f;
     Shape best = default_shape();
     qm_quality q;
-    for (int al : {2, 1, 0})
+    for (int al : {2, 5, 1, 0})
     for (int th : threads_c)
         for (int sm : smem_c)
             for (int bg : big_c) {
                 if (al >= 1 && bg != big_c[0]) continue;  // the two-phase path has no size split
                 if (al == 0 && g->wt) continue;           // weighted graphs: two-phase pipeline only
-                if (al == 2 && (g->wt || g->n <= BIN_DEFAULT_MIN_NODES)) continue;  // binning pays beyond L2 only
+                if (al == 2 && (g->wt || g->n <= BIN_MIN_NODES)) continue;  // binning can pay beyond L2 only
+                if (al == 5 && (g->wt || !packs_labels(1, false, g->n, K))) continue;  // 1 is 5 there
                 Shape sh;
                 sh.threads = th;
                 sh.smem_bytes = sm;

@@ -88,6 +88,7 @@ struct ScoreWs {
     int *bin_seg = nullptr;     // [K]
     long long bin_chunks = 0;   // pool capacity in chunks
     int bin_shift = 0, bin_nbins = 0, bin_near = 0;
+    unsigned long long *plab = nullptr;  // packed labels (three 21-bit ids a word), [(n + 2) / 3]
     size_t zero_bytes;          // bytes from `status` that must start at zero
     size_t bytes;               // total bytes carved (the *_ws_bytes size)
 };
@@ -117,14 +118,28 @@ size_t score_ws_bytes(long long n, int K);
 // arcs whose far end is not close in node-id order, by windows of at least 2^23
 // node ids; 3 bins every arc, by about four windows (tests and comparisons).
 // Weighted graphs take mode 0.
-size_t score2_ws_bytes(long long n, long long n_arcs, int K, bool weighted = false, int bin_mode = 0);
-ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K, bool weighted = false, int bin_mode = 0);
+// pack (two-phase pipeline, direct gathers, K <= 2^21): the far-end gathers
+// read a copy of the labels packed three to a 64-bit word.
+size_t score2_ws_bytes(long long n, long long n_arcs, int K, bool weighted = false, int bin_mode = 0,
+                       bool pack = false);
+ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K, bool weighted = false, int bin_mode = 0,
+                        bool pack = false);
 // The binning mode of a two-phase launch shape on a graph (algorithm 2 or 3
 // on an unweighted graph; 0 otherwise).
 inline int bin_mode_of(int algo, bool weighted) { return (!weighted && (algo == 2 || algo == 3)) ? algo : 0; }
-// Graphs with more nodes than this take the binned gathers by default: their
-// label array (4 bytes a node) is beyond what L2 serves at random.
-constexpr long long BIN_DEFAULT_MIN_NODES = 1LL << 24;
+// Graphs with more nodes than this gather packed labels by default (algorithm
+// 1): their label array is well beyond what L2 keeps.
+constexpr long long PACK_MIN_NODES = 1LL << 22;
+// Whether a two-phase call gathers from the packed copy: algorithm 4 always,
+// algorithm 1 on graphs above PACK_MIN_NODES; unweighted graphs and label ids
+// below 2^21 only.
+inline bool packs_labels(int algo, bool weighted, long long n, int K)
+{
+    return !weighted && K <= (1 << 21) && (algo == 4 || (algo == 1 && n > PACK_MIN_NODES));
+}
+// The autotuner tries the binned gathers on graphs with more nodes than this:
+// their label array (4 bytes a node) is beyond what L2 serves at random.
+constexpr long long BIN_MIN_NODES = 1LL << 24;
 size_t compare_ws_bytes(long long n, int ka, int kb);
 ScoreWs carve_score_ws(void *base, long long n, int K);
 CompareWs carve_compare_ws(void *base, long long n, int ka, int kb);

@@ -777,13 +777,45 @@ constexpr int EXPAND_MAX_SEGS = 6;
 // fixed-point integers: w * 2^43 (an integer below 2^63).
 __device__ __forceinline__ unsigned long long w_fixed(float w) { return __float2ull_rn(w * 8796093022208.0f); }
 
+// Packed copy of the labels for the far-end gathers: three 21-bit labels per
+// 64-bit word (label ids below 2^21), 8/3 bytes a node instead of 4.  The
+// gathers of the expand phase land at random in the label array; a smaller
+// array leaves a larger share of it in L2.
+constexpr int PACK_BITS = 21;
+constexpr long long PACK_MAX_K = 1LL << PACK_BITS;
+
+__global__ void k_pack3(const int *__restrict__ labels, long long n, unsigned long long *__restrict__ plab,
+                        const int *status)
+{
+    if (*status) return;
+    const long long words = (n + 2) / 3;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < words;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long i = 3 * t;
+        unsigned long long w = (unsigned long long)(__ldcs(&labels[i]) & 0x1FFFFF);
+        if (i + 1 < n) w |= (unsigned long long)(__ldcs(&labels[i + 1]) & 0x1FFFFF) << PACK_BITS;
+        if (i + 2 < n) w |= (unsigned long long)(__ldcs(&labels[i + 2]) & 0x1FFFFF) << (2 * PACK_BITS);
+        plab[t] = w;
+    }
+}
+
+__device__ __forceinline__ int ld_label3(const unsigned long long *plab, int v, unsigned long long pol)
+{
+    const unsigned q = (unsigned)v / 3u;
+    const unsigned r = (unsigned)v - 3u * q;
+    unsigned long long w;
+    asm("ld.global.nc.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(w) : "l"(plab + q), "l"(pol));
+    return (int)((w >> (PACK_BITS * r)) & 0x1FFFFFull);
+}
+
 // Gathers the labels of arcs [e_lo, e_hi) of a run of community c (loc(e) is
 // the CSR index of arc e) and packs those != c into c's segment at cbase.  On
 // a weighted graph (WT) the arc weights travel with the packed labels (nbrw)
 // and each lane sums the fixed-point weights of its intra and cut arcs.
-template <bool WT, class LOC>
+template <bool WT, bool PACK, class LOC>
 __device__ __forceinline__ void expand_range(unsigned e_lo, unsigned e_hi, int c, unsigned cbase, LOC loc,
                                              const int *__restrict__ col, const int *__restrict__ labels,
+                                             const unsigned long long *__restrict__ plab,
                                              int *inter, int *__restrict__ nbr, unsigned long long keep, int lane,
                                              const float *__restrict__ wt, float *__restrict__ nbrw, u128 &w_in,
                                              u128 &w_out)
@@ -800,7 +832,7 @@ __device__ __forceinline__ void expand_range(unsigned e_lo, unsigned e_hi, int c
         }
 #pragma unroll
         for (int k = 0; k < EXPAND_UNROLL; ++k)
-            if (lab[k] >= 0) lab[k] = ld_hint(&labels[lab[k]], keep);
+            if (lab[k] >= 0) lab[k] = PACK ? ld_label3(plab, lab[k], keep) : ld_hint(&labels[lab[k]], keep);
         if (WT) {
 #pragma unroll
             for (int k = 0; k < EXPAND_UNROLL; ++k)
@@ -845,10 +877,11 @@ __device__ __forceinline__ void flush_weights(unsigned long long *wl, int c, u12
     }
 }
 
-template <bool WT>
+template <bool WT, bool PACK>
 __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__restrict__ row_ptr,
                                                            const int *__restrict__ col,
                                                            const int *__restrict__ labels,
+                                                           const unsigned long long *__restrict__ plab,
                                                            const int *__restrict__ members,
                                                            const unsigned *__restrict__ aoff,
                                                            const int *__restrict__ start, long long n,
@@ -902,8 +935,8 @@ __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__re
                 }
                 const long long cs = rsw[lo] - (long long)e_lo;  // CSR index of arc e is cs + e
                 u128 w_in = 0, w_out = 0;
-                expand_range<WT>(e_lo, e_hi, c, cbase, [cs](unsigned e) { return cs + (long long)e; }, col, labels,
-                                 inter, nbr, keep, lane, wt, nbrw, w_in, w_out);
+                expand_range<WT, PACK>(e_lo, e_hi, c, cbase, [cs](unsigned e) { return cs + (long long)e; }, col,
+                                       labels, plab, inter, nbr, keep, lane, wt, nbrw, w_in, w_out);
                 if (WT) flush_weights(wl, c, w_in, w_out, lane);
             }
         } else {
@@ -918,13 +951,13 @@ __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__re
                 if (lane == 0) cbase = __ldg(&aoff[__ldg(&start[c])]);
                 cbase = __shfl_sync(0xffffffffu, cbase, 0);
                 u128 w_in = 0, w_out = 0;
-                expand_range<WT>(
+                expand_range<WT, PACK>(
                     e_lo, e_hi, c, cbase,
                     [=](unsigned e) {
                         const int o = m_lo + upper_bound_smem(offw + m_lo, m_hi - m_lo, e) - 1;
                         return rsw[o] + (long long)(e - offw[o]);
                     },
-                    col, labels, inter, nbr, keep, lane, wt, nbrw, w_in, w_out);
+                    col, labels, plab, inter, nbr, keep, lane, wt, nbrw, w_in, w_out);
                 if (WT) flush_weights(wl, c, w_in, w_out, lane);
             }
         }
@@ -1312,9 +1345,9 @@ int launch_score(const GraphDev &g, const int *labels, int K, const ScoreWs &ws,
     return cudaGetLastError() == cudaSuccess ? launches : -1;
 }
 
-size_t score2_ws_bytes(long long n, long long n_arcs, int K, bool weighted, int bin_mode)
+size_t score2_ws_bytes(long long n, long long n_arcs, int K, bool weighted, int bin_mode, bool pack)
 {
-    return carve_score2_ws(reinterpret_cast<void *>(4096), n, n_arcs, K, weighted, bin_mode).bytes;
+    return carve_score2_ws(reinterpret_cast<void *>(4096), n, n_arcs, K, weighted, bin_mode, pack).bytes;
 }
 
 // Window size, window count and nearness distance of the binned gathers.
@@ -1332,10 +1365,11 @@ static void bin_geometry(long long n, int mode, int *shift, int *nbins, int *nea
     *nbins = (int)(((std::max(n, 1LL) - 1) >> *shift) + 1);
 }
 
-ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K, bool weighted, int bin_mode)
+ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K, bool weighted, int bin_mode, bool pack)
 {
     ScoreWs w{};
     if (weighted) bin_mode = 0;
+    if (weighted || bin_mode || K > PACK_MAX_K) pack = false;
     const int tiles = scan_tiles((int)std::max<long long>(n, K));
     char *p = (char *)base;
     w.status = (int *)p;
@@ -1370,6 +1404,10 @@ ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K, bool w
         p += align_up((size_t)w.bin_chunks * 8, 256);
         w.bin_pool = (unsigned long long *)p;
         p += align_up((size_t)w.bin_chunks * BIN_CHUNK * 8, 256);
+    }
+    if (pack) {
+        w.plab = (unsigned long long *)p;
+        p += align_up((size_t)((n + 2) / 3) * 8, 256);
     }
     if (weighted) {
         w.nbrw = (float *)p;
@@ -1489,9 +1527,9 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
     // exclusive prefix of the member degrees, in place: aoff[p] = arcs before member position p
     launches += launch_scan((const int *)ws.aoff, (int)n, (int *)ws.aoff, nullptr, nullptr, INT_MAX, nullptr,
                             ws.counters, ws.scan_tmp, ws.status, s, tr);
-    TRACE("k_expand");
     if (g.wt) {
-        k_expand<true><<<expand_grid(n, num_sms), EXPAND_THREADS, 0, s>>>(g.row_ptr, g.col, labels, ws.members, ws.aoff,
+        TRACE("k_expand");
+        k_expand<true, false><<<expand_grid(n, num_sms), EXPAND_THREADS, 0, s>>>(g.row_ptr, g.col, labels, nullptr, ws.members, ws.aoff,
                                                               ws.start, n, ws.inter, ws.nbr, ws.status, own, g.wt,
                                                               ws.nbrw, ws.wl);
         ++launches;
@@ -1517,10 +1555,19 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
         TRACE("k_resolve");
         k_resolve<<<num_sms * 8, RESOLVE_THREADS, 0, s>>>(ba, labels, ws.inter, ws.nbr, ws.status);
         launches += 3;
+    } else if (ws.plab) {
+        TRACE("k_pack3");
+        k_pack3<<<grid_for((n + 2) / 3, 256, num_sms, 8), 256, 0, s>>>(labels, n, ws.plab, ws.status);
+        TRACE("k_expand");
+        k_expand<false, true><<<expand_grid(n, num_sms), EXPAND_THREADS, 0, s>>>(
+            g.row_ptr, g.col, labels, ws.plab, ws.members, ws.aoff, ws.start, n, ws.inter, ws.nbr, ws.status, own,
+            nullptr, nullptr, nullptr);
+        launches += 2;
     } else {
-        k_expand<false><<<expand_grid(n, num_sms), EXPAND_THREADS, 0, s>>>(g.row_ptr, g.col, labels, ws.members,
-                                                                          ws.aoff, ws.start, n, ws.inter, ws.nbr,
-                                                                          ws.status, own, nullptr, nullptr, nullptr);
+        TRACE("k_expand");
+        k_expand<false, false><<<expand_grid(n, num_sms), EXPAND_THREADS, 0, s>>>(
+            g.row_ptr, g.col, labels, nullptr, ws.members, ws.aoff, ws.start, n, ws.inter, ws.nbr, ws.status, own,
+            nullptr, nullptr, nullptr);
         ++launches;
     }
     const CountPlan cp = plan_count(sh.threads, sh.smem_bytes);

@@ -1,7 +1,8 @@
-"""The far-end label gathers through destination-window bins (algorithms 2
-and 3 of the two-phase pipeline): the packed runs hold the same multisets as
-with direct gathers, so every result must equal the direct pipeline's bit for
-bit and match the oracle, on LFR-style graphs with several windows and a
+"""The variants of the far-end label gathers of the two-phase pipeline:
+through destination-window bins (algorithms 2 and 3) and from the copy of the
+labels packed three to a word (algorithm 4; algorithm 5 never packs).  The
+packed runs hold the same multisets whatever the gathers, so every result must
+equal the direct pipeline's bit for bit and match the oracle, on LFR-style graphs with several windows and a
 ragged last window, the degenerate partitions, a hub whose run takes the long
 path, isolated nodes, label ids beyond 24 bits, reordered graphs, sharded
 calls and per-community output."""
@@ -28,7 +29,7 @@ def gen():
     return g
 
 
-def by_algo(qm, graph, lab, K, algos=(1, 2, 3), per_community=False):
+def by_algo(qm, graph, lab, K, algos=(1, 2, 3, 4, 5), per_community=False):
     out = {}
     for a in algos:
         qm.set_tuning(graph, K, 512, 96 * 1024, 48, a)
@@ -111,7 +112,7 @@ def test_reordered_sharded_and_host_labels(qm, gen):
     reord = qm.Graph(*to_dev(g.row_ptr, g.col), reorder=True)
     lab = gen.perturb(g.labels, g.K, 0.2, seed=14)
     ref = by_algo(qm, plain, lab.cuda(), g.K, algos=(1,))[1]
-    for a in (2, 3):
+    for a in (2, 3, 4, 5):
         for graph in (plain, reord):
             qm.set_tuning(graph, g.K, 512, 96 * 1024, 48, a)
             assert qm.score(graph, lab.cuda(), g.K) == ref
@@ -130,4 +131,4 @@ def test_weighted_graph_ignores_binning(qm, gen):
     w = ((key * 2654435761) % 1000).to(torch.float32) / 100.0 + 0.25
     graph = qm.Graph(*to_dev(g.row_ptr, g.col), weights=w.cuda())
     res = by_algo(qm, graph, g.labels.cuda(), g.K)
-    assert res[2] == res[1] and res[3] == res[1]
+    assert all(res[a] == res[1] for a in (2, 3, 4, 5))

@@ -39,7 +39,7 @@ def test_ten_million_nodes_against_whole_oracle(qm, oracle_mod):
     check_quality(q, o, "lfr10m")
     # the binned far-end gathers give the same bits
     q_plain = qm.score(graph, g.labels, g.K)
-    for algo in (2, 3):
+    for algo in (2, 3, 5):
         qm.set_tuning(graph, g.K, 512, 96 * 1024, 48, algo)
         assert qm.score(graph, g.labels, g.K) == q_plain, algo
     qm.set_tuning(graph, g.K, 512, 96 * 1024, 48, 1)

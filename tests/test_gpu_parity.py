@@ -175,7 +175,7 @@ def test_every_launch_shape_gives_identical_bits(qm, gen, oracle_mod):
     lab = g.labels.cuda()
     o = oracle_mod.score(g.row_ptr.numpy(), g.col.numpy(), g.labels.numpy(), g.K)
     ref = None
-    for algo in (1, 0, 2, 3):
+    for algo in (1, 0, 2, 3, 4, 5):
         for threads, smem, big in ((512, 96 * 1024, 48), (256, 48 * 1024, 16), (1024, 200 * 1024, 400),
                                    (128, 16 * 1024, 1), (512, 20 * 1024, 100_000)):
             qm.set_tuning(graph, g.K, threads, smem, big, algo)

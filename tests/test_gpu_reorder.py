@@ -44,7 +44,7 @@ def test_reorder_keeps_graph_info(qm, setup):
     assert b["device_bytes"] == a["device_bytes"] + 4 * g.n
 
 
-@pytest.mark.parametrize("algo", [1, 0, 2, 3])
+@pytest.mark.parametrize("algo", [1, 0, 2, 3, 4])
 def test_plain_scoring_identical(qm, setup, oracle_mod, algo):
     g, plain, reord, parts = setup
     for labels, K in parts:
@@ -90,7 +90,7 @@ def test_allocation_free_call_identical(qm, setup):
     assert got == qm.score(plain, lab, K)
 
 
-@pytest.mark.parametrize("algo", [1, 0, 2, 3])
+@pytest.mark.parametrize("algo", [1, 0, 2, 3, 4])
 def test_out_of_range_label_rejected(qm, setup, algo):
     g, plain, reord, parts = setup
     labels, K = parts[0]
