@@ -188,6 +188,22 @@ __device__ __forceinline__ double u128_to_double(u128 v)
                      (double)(unsigned long long)v);
 }
 
+// Community c's share of the Eq. (9) split penalty when each unordered pair
+// of communities is charged once, to its smaller id: T_c / (|E| |c|), T_c in
+// 64.64 fixed point (see score_community).
+__device__ __forceinline__ double pair_penalty_once(u128 t, long long size, long long E)
+{
+    return __ddiv_rn(ldexp(u128_to_double(t), -64), __dmul_rn((double)E, (double)size));
+}
+
+// Community c's own split penalty of Eq. (9), S_c / (2|E| |c|) (the
+// per-community Qds term), S_c in 64.64 fixed point.
+__device__ __forceinline__ double pair_penalty_own(u128 s, long long size, long long E)
+{
+    return __ddiv_rn(ldexp(u128_to_double(s), -64), __dmul_rn(__dmul_rn(2.0, (double)E), (double)size));
+}
+
+
 // Group totals of NW 64-bit words per thread, delivered to the group leader
 // (group thread 0): a warp reduction, then for a block group one exchange
 // through `red` (>= 32 * NW words) and one barrier.  Only the leader's result
@@ -258,10 +274,16 @@ __device__ __forceinline__ U192 group_u192_to_leader(U192 v, int gsize, unsigned
 // Each warp of the group takes its own chunks of 32 members (a warp-local
 // prefix sum of their degrees in `offs`/`rs`, the warp's slices of shared
 // staging), so the arc walk needs no block-wide barrier; all warps insert into
-// the group's shared table.  The split penalty of Eq. (9) for community i is
-//   sum_j |E_ij|^2 / (2|E| |c_i| |c_j|) = S_i / (2|E| |c_i|)
-// with S_i = sum_j |E_ij|^2 / |c_j| summed exactly with 128-bit reciprocals
-// (x.recip, see rcp_of): only one division per community is done in FP64.
+// the group's shared table.  The split penalty of Eq. (9) summed over all
+// communities is
+//   sum_i sum_{j != i} |E_ij|^2 / (2|E| |c_i| |c_j|) = sum_i T_i / (|E| |c_i|)
+// with T_i = sum_{j > i} |E_ij|^2 / |c_j|: the ordered sum counts every
+// unordered pair twice with the same value, so each pair is charged once, to
+// its smaller id, and only neighbour ids above i are counted.  T_i is summed
+// exactly with 128-bit reciprocals (x.recip, see rcp_of): one division per
+// community is done in FP64.  A per-community Qds term needs i's own penalty
+// S_i / (2|E| |c_i|) with S_i = sum_{j != i} |E_ij|^2 / |c_j|, which is then
+// summed as well.
 __device__ __forceinline__ bool score_community(const ScoreCtx &x, int c, const SmemTable &tab,
                                                 unsigned *offs, long long *rs, ScoreAcc *acc,
                                                 int gtid, int gsize, unsigned long long *red)
@@ -273,10 +295,12 @@ __device__ __forceinline__ bool score_community(const ScoreCtx &x, int c, const 
     const int mb = __ldcg(&x.start[c]), me = __ldcg(&x.start[c + 1]);
     const long long size = me - mb;
     unsigned R = 1;
+    const bool full = x.pc_qds != nullptr;
     for (;;) {
         unsigned long long same = 0, vol = 0, slots = 0, cnt2 = 0;
-        U192 inner;
+        U192 inner, inner_full;
         u192_zero(inner);
+        u192_zero(inner_full);
         bool ok = true;
         for (unsigned r = 0; r < R && ok; ++r) {
             for (int cb = mb + wrank * 32; cb < me; cb += gsize) {
@@ -322,7 +346,7 @@ __device__ __forceinline__ bool score_community(const ScoreCtx &x, int c, const 
                         if (!QM_CHK(lv[k], x.K, 6)) continue;
                         if (lv[k] == c) {
                             if (r == 0) ++same;
-                        } else if (R == 1 || tab_split((unsigned)lv[k], R) == r) {
+                        } else if ((full || lv[k] > c) && (R == 1 || tab_split((unsigned)lv[k], R) == r)) {
                             tab_insert(tab, (unsigned)lv[k]);
                         }
                     }
@@ -338,9 +362,12 @@ __device__ __forceinline__ bool score_community(const ScoreCtx &x, int c, const 
                 if (!QM_CHK(key, x.K, 7)) return;
                 const unsigned long long q = (unsigned long long)cnt * (unsigned long long)cnt;
                 const Rcp rj = ld_rcp_cg(&x.recip[key]);
-                u192_mac(inner, q, rj);
-                ++slots;
-                cnt2 += q;
+                if (full) u192_mac(inner_full, q, rj);
+                if (key > c) {
+                    u192_mac(inner, q, rj);
+                    ++slots;
+                    cnt2 += q;
+                }
             });
             group_sync(gsize);
             if (gtid == 0) *tab.n_used = 0;
@@ -376,14 +403,15 @@ __device__ __forceinline__ bool score_community(const ScoreCtx &x, int c, const 
         unsigned long long w4[4] = {same, vol, slots, cnt2};
         group_words_to_leader<4>(w4, gsize, red);
         const u128 inner_t = u192_shr64(group_u192_to_leader(inner, gsize, red, 128));
+        u128 full_t = 0;
+        if (full) full_t = u192_shr64(group_u192_to_leader(inner_full, gsize, red, 128));
         if (gtid == 0) {
             same = w4[0];
             vol = w4[1];
             const long long ein = (long long)(same / 2), eout = (long long)(vol - same);
             double qs, dens, contr, expn, cond;
             community_terms(ein, eout, size, x.E, qs, dens, contr, expn, cond);
-            const double pen = __ddiv_rn(ldexp(u128_to_double(inner_t), -64),
-                                         __dmul_rn(__dmul_rn(2.0, (double)x.E), (double)size));
+            const double pen = pair_penalty_once(inner_t, size, x.E);
             acc->qds_pair += fp_from_double(pen, SC_QDS);
             acc->slots += w4[2];
             acc->cnt2 += w4[3];
@@ -403,7 +431,7 @@ __device__ __forceinline__ bool score_community(const ScoreCtx &x, int c, const 
             if (x.pc_contr) x.pc_contr[c] = contr;
             if (x.pc_expn) x.pc_expn[c] = expn;
             if (x.pc_cond) x.pc_cond[c] = cond;
-            if (x.pc_qds) x.pc_qds[c] = __dsub_rn(qs, pen);
+            if (x.pc_qds) x.pc_qds[c] = __dsub_rn(qs, pair_penalty_own(full_t, size, x.E));
         }
         return true;
     }
@@ -572,8 +600,14 @@ __device__ __forceinline__ void compare_cells_community(const CompareCtx &x, int
 // integer record per community; the FP64 terms are formed afterwards for all
 // communities in parallel (k_score_terms).
 
-// Per-community record written by phase B (unsigned 64-bit words).
-enum { REC_SAME = 0, REC_VOL = 1, REC_SLOTS = 2, REC_CNT2 = 3, REC_INNER_LO = 4, REC_INNER_HI = 5, REC_WORDS = 6 };
+// Per-community record written by phase B (unsigned 64-bit words).  INNER is
+// T_c = sum_{j > c} |E_cj|^2 / |c_j| (64.64 fixed point), the community's share
+// of the Eq. (9) split penalty when every unordered pair {c, j} is charged once
+// (to its smaller id); SLOTS and CNT2 count those pairs and sum |E_cj|^2.  FULL
+// is S_c = sum_{j != c} |E_cj|^2 / |c_j|, the community's own penalty sum,
+// formed only when the per-community Qds terms are asked for.
+enum { REC_SAME = 0, REC_VOL = 1, REC_SLOTS = 2, REC_CNT2 = 3, REC_INNER_LO = 4, REC_INNER_HI = 5,
+       REC_FULL_LO = 6, REC_FULL_HI = 7, REC_WORDS = 8 };
 
 struct CountCtx {
     const int *nbr;                   // packed inter-community neighbour labels
@@ -584,6 +618,7 @@ struct CountCtx {
     unsigned long long *rec;          // [K][REC_WORDS]
     int K;
     int *err;
+    int full;                         // also form S_c (per-community Qds terms asked for)
 };
 
 // L2 eviction-priority hints (PTX createpolicy / ld.global.L2::cache_hint):
@@ -732,9 +767,10 @@ __device__ __forceinline__ unsigned etab_next_epoch(const TAB &t, unsigned epoch
 
 // Writes community c's record from the group totals (leader only).
 __device__ __forceinline__ void put_record(const CountCtx &x, int c, unsigned vol, unsigned m,
-                                           unsigned long long slots, unsigned long long cnt2, const U192 &inner)
+                                           unsigned long long slots, unsigned long long cnt2, const U192 &inner,
+                                           const U192 &inner_full)
 {
-    const u128 in = u192_shr64(inner);
+    const u128 in = u192_shr64(inner), fu = u192_shr64(inner_full);
     unsigned long long *rc = x.rec + (size_t)c * REC_WORDS;
     rc[REC_SAME] = (unsigned long long)(vol - m);
     rc[REC_VOL] = (unsigned long long)vol;
@@ -742,33 +778,47 @@ __device__ __forceinline__ void put_record(const CountCtx &x, int c, unsigned vo
     rc[REC_CNT2] = cnt2;
     rc[REC_INNER_LO] = (unsigned long long)in;
     rc[REC_INNER_HI] = (unsigned long long)(in >> 64);
+    rc[REC_FULL_LO] = (unsigned long long)fu;
+    rc[REC_FULL_HI] = (unsigned long long)(fu >> 64);
 }
 
-// Group totals of (slots, cnt2, inner) delivered to the leader with one
-// exchange (5 words per warp in `red`); for a block its barrier also orders
-// this community's inserts before the next community's.
+// Group totals of (slots, cnt2, inner[, inner_full]) delivered to the leader
+// with one exchange (5 or 8 words per warp in `red`); for a block its barrier
+// also orders this community's inserts before the next community's.
+template <bool FULL>
 __device__ __forceinline__ void group_totals(unsigned long long &slots, unsigned long long &cnt2, U192 &inner,
-                                             int gsize, unsigned long long *red)
+                                             U192 &inner_full, int gsize, unsigned long long *red)
 {
     slots = warp_sum_u64(slots);
     cnt2 = warp_sum_u64(cnt2);
     inner = u192_warp_sum(inner);
+    if (FULL) inner_full = u192_warp_sum(inner_full);
     if (gsize == 32) return;
+    constexpr int WW = FULL ? 8 : 5;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (lane == 0) {
-        red[5 * wid] = slots;
-        red[5 * wid + 1] = cnt2;
-        red[5 * wid + 2] = inner.w0;
-        red[5 * wid + 3] = inner.w1;
-        red[5 * wid + 4] = inner.w2;
+        red[WW * wid] = slots;
+        red[WW * wid + 1] = cnt2;
+        red[WW * wid + 2] = inner.w0;
+        red[WW * wid + 3] = inner.w1;
+        red[WW * wid + 4] = inner.w2;
+        if (FULL) {
+            red[WW * wid + 5] = inner_full.w0;
+            red[WW * wid + 6] = inner_full.w1;
+            red[WW * wid + 7] = inner_full.w2;
+        }
     }
     block_sync();
     if (threadIdx.x == 0)
         for (int w = 1; w < nw; ++w) {
-            slots += red[5 * w];
-            cnt2 += red[5 * w + 1];
-            const U192 o{red[5 * w + 2], red[5 * w + 3], red[5 * w + 4]};
+            slots += red[WW * w];
+            cnt2 += red[WW * w + 1];
+            const U192 o{red[WW * w + 2], red[WW * w + 3], red[WW * w + 4]};
             u192_add(inner, o);
+            if (FULL) {
+                const U192 f{red[WW * w + 5], red[WW * w + 6], red[WW * w + 7]};
+                u192_add(inner_full, f);
+            }
         }
 }
 
@@ -778,79 +828,6 @@ struct __align__(16) RunHdr {
     int c;
     unsigned a0, m, vol;
 };
-
-// Counts the m entries of community h.c's run, read from `src` (shared-memory
-// staging when SMEM, else the packed array in global memory), with a group (a
-// warp, or the whole block).  Every entry is a label j != c, so m bounds the
-// distinct keys.  Each entry adds its own share of the Eq. (9) pair sum: the
-// k-th occurrence of key j adds (2k - 1) Rcp_j, so no pass over the table is
-// needed afterwards.  When m exceeds what the table holds at 3/4 load the
-// keys are split into R hash classes and the run is read once per class.
-// `epoch` is the group's table epoch (updated).
-template <bool SMEM, class TAB>
-__device__ __forceinline__ void count_run(const CountCtx &x, const RunHdr &h, const int *src, const TAB &tab,
-                                          unsigned &epoch, int gtid, int gsize, unsigned long long *red)
-{
-    const unsigned m = h.m;
-    const unsigned fill = (unsigned)(3 * tab.cap / 4);
-    unsigned R = m <= fill ? 1u : (unsigned)min((unsigned long long)R_MAX, ((unsigned long long)m + fill - 1) / fill);
-    for (;;) {
-        unsigned long long slots = 0, cnt2 = 0;
-        U192 inner;
-        u192_zero(inner);
-        bool ok = true;
-        for (unsigned r = 0; r < R && ok; ++r) {
-            epoch = etab_next_epoch(tab, epoch, gtid, gsize);
-            // one entry per thread per step (several table probes in flight per
-            // thread serialise worse than more warps do); the next entry's label
-            // and reciprocal are fetched before this entry's table update
-            auto fetch = [&](unsigned e, int &lv, Rcp &rj) {
-                lv = -1;
-                if (e < m) lv = SMEM ? src[e] : __ldcs(&src[e]);
-                if (lv >= 0 && (!QM_CHK(lv, x.K, 6) || (R > 1 && tab_split((unsigned)lv, R) != r))) lv = -1;
-                if (lv >= 0) rj = ld_rcp(&x.recip[lv]);
-            };
-            int lv_n;
-            Rcp rj_n;
-            fetch((unsigned)gtid, lv_n, rj_n);
-            for (unsigned e = gtid; e < m; e += gsize) {
-                const int lv = lv_n;
-                const Rcp rj = rj_n;
-                fetch(e + gsize, lv_n, rj_n);
-                if (lv < 0) continue;
-                const int prev = tab.add((unsigned)lv, epoch);
-                if (prev < 0) continue;  // overflow: this pass is discarded
-                if (prev == 0) {  // first occurrence (the common case): q = 1
-                    u192_add_rcp(inner, rj);
-                    cnt2 += 1ull;
-                    slots += 1ull;
-                } else {
-                    const unsigned long long q = 2ull * (unsigned long long)prev + 1ull;
-                    u192_mac(inner, q, rj);
-                    cnt2 += q;
-                }
-            }
-            group_sync(gsize);
-            if (*(volatile int *)tab.overflow) ok = false;
-        }
-        if (!ok) {
-            group_sync(gsize);
-            if (gtid == 0) *tab.overflow = 0;
-            group_sync(gsize);
-            const unsigned nr = R * 2u;
-            if (nr > R_MAX) {
-                if (gtid == 0) atomicOr(x.err, 2);
-                return;
-            }
-            R = nr;
-            continue;
-        }
-        group_totals(slots, cnt2, inner, gsize, red);
-        if (gtid == 0) put_record(x, h.c, h.vol, m, slots, cnt2, inner);
-        if (gsize == 32) __syncwarp();
-        return;
-    }
-}
 
 // Adds one entry's share of the pair sum: the k-th occurrence (prev = k - 1)
 // of a key with reciprocal r adds (2k - 1) r.
@@ -868,6 +845,78 @@ __device__ __forceinline__ void add_share(U192 &inner, unsigned long long &slots
     }
 }
 
+// Counts the m entries of community h.c's run, read from `src` (shared-memory
+// staging when SMEM, else the packed array in global memory), with a group (a
+// warp, or the whole block).  Every entry is a label j != c, so m bounds the
+// distinct keys.  Only labels j > c are counted (each unordered pair is
+// charged to its smaller id, see score_community), unless FULL, when every
+// label is counted and S_c formed too.  Each counted entry adds its own share
+// of the Eq. (9) pair sum: the k-th occurrence of key j adds (2k - 1) Rcp_j, so
+// no pass over the table is needed afterwards.  When m exceeds what the table
+// holds at 3/4 load the keys are split into R hash classes and the run is read
+// once per class.  `epoch` is the group's table epoch (updated).
+template <bool SMEM, bool FULL, class TAB>
+__device__ __forceinline__ void count_run(const CountCtx &x, const RunHdr &h, const int *src, const TAB &tab,
+                                          unsigned &epoch, int gtid, int gsize, unsigned long long *red)
+{
+    const unsigned m = h.m;
+    const unsigned fill = (unsigned)(3 * tab.cap / 4);
+    unsigned R = m <= fill ? 1u : (unsigned)min((unsigned long long)R_MAX, ((unsigned long long)m + fill - 1) / fill);
+    const int c = h.c;
+    for (;;) {
+        unsigned long long slots = 0, cnt2 = 0, s_dummy = 0, c_dummy = 0;
+        U192 inner, inner_full;
+        u192_zero(inner);
+        u192_zero(inner_full);
+        bool ok = true;
+        for (unsigned r = 0; r < R && ok; ++r) {
+            epoch = etab_next_epoch(tab, epoch, gtid, gsize);
+            // one entry per thread per step (several table probes in flight per
+            // thread serialise worse than more warps do); the next entry's label
+            // and reciprocal are fetched before this entry's table update
+            auto fetch = [&](unsigned e, int &lv, Rcp &rj) {
+                lv = -1;
+                if (e < m) lv = SMEM ? src[e] : __ldcs(&src[e]);
+                if (lv >= 0 && (!QM_CHK(lv, x.K, 6) || (!FULL && lv < c) ||
+                                (R > 1 && tab_split((unsigned)lv, R) != r)))
+                    lv = -1;
+                if (lv >= 0) rj = ld_rcp(&x.recip[lv]);
+            };
+            int lv_n;
+            Rcp rj_n;
+            fetch((unsigned)gtid, lv_n, rj_n);
+            for (unsigned e = gtid; e < m; e += gsize) {
+                const int lv = lv_n;
+                const Rcp rj = rj_n;
+                fetch(e + gsize, lv_n, rj_n);
+                if (lv < 0) continue;
+                const int prev = tab.add((unsigned)lv, epoch);
+                if (prev < 0) continue;  // overflow: this pass is discarded
+                if (!FULL || lv > c) add_share(inner, slots, cnt2, prev, rj);
+                if (FULL) add_share(inner_full, s_dummy, c_dummy, prev, rj);
+            }
+            group_sync(gsize);
+            if (*(volatile int *)tab.overflow) ok = false;
+        }
+        if (!ok) {
+            group_sync(gsize);
+            if (gtid == 0) *tab.overflow = 0;
+            group_sync(gsize);
+            const unsigned nr = R * 2u;
+            if (nr > R_MAX) {
+                if (gtid == 0) atomicOr(x.err, 2);
+                return;
+            }
+            R = nr;
+            continue;
+        }
+        group_totals<FULL>(slots, cnt2, inner, inner_full, gsize, red);
+        if (gtid == 0) put_record(x, h.c, h.vol, m, slots, cnt2, inner, inner_full);
+        if (gsize == 32) __syncwarp();
+        return;
+    }
+}
+
 // The same count for runs too long for the staged block path, including runs
 // of 2^24 entries or more (a key may then occur 2^25 times or more): 64-bit
 // counts in the tab_insert table, one pass over the used slots per class.
@@ -876,18 +925,21 @@ __device__ __forceinline__ void count_run_general(const CountCtx &x, const RunHd
                                                   int gsize, unsigned long long *red)
 {
     const unsigned m = h.m;
+    const int c = h.c;
+    const bool full = x.full != 0;
     const int *src = x.nbr + h.a0;
     const unsigned cap_keys = (unsigned)tab.max_used;
     unsigned R = m <= cap_keys ? 1u : (unsigned)min((unsigned long long)R_MAX, (5ull * m + 4ull * cap_keys - 1) / (4ull * cap_keys));
     for (;;) {
         unsigned long long slots = 0, cnt2 = 0;
-        U192 inner;
+        U192 inner, inner_full;
         u192_zero(inner);
+        u192_zero(inner_full);
         bool ok = true;
         for (unsigned r = 0; r < R && ok; ++r) {
             for (unsigned e = gtid; e < m; e += gsize) {
                 const int lv = __ldcs(&src[e]);
-                if (!QM_CHK(lv, x.K, 6)) continue;
+                if (!QM_CHK(lv, x.K, 6) || (!full && lv < c)) continue;
                 if (R == 1 || tab_split((unsigned)lv, R) == r) tab_insert(tab, (unsigned)lv);
             }
             group_sync(gsize);
@@ -898,9 +950,13 @@ __device__ __forceinline__ void count_run_general(const CountCtx &x, const RunHd
             tab_drain(tab, gtid, gsize, [&](int key, long long cnt) {
                 if (!QM_CHK(key, x.K, 7)) return;
                 const unsigned long long q = (unsigned long long)cnt * (unsigned long long)cnt;
-                u192_mac(inner, q, ld_rcp(&x.recip[key]));
-                ++slots;
-                cnt2 += q;
+                const Rcp rj = ld_rcp(&x.recip[key]);
+                if (full) u192_mac(inner_full, q, rj);
+                if (key > c) {
+                    u192_mac(inner, q, rj);
+                    ++slots;
+                    cnt2 += q;
+                }
             });
             group_sync(gsize);
             if (gtid == 0) *tab.n_used = 0;
@@ -919,14 +975,16 @@ __device__ __forceinline__ void count_run_general(const CountCtx &x, const RunHd
             R = nr;
             continue;
         }
-        group_totals(slots, cnt2, inner, gsize, red);
-        if (gtid == 0) put_record(x, h.c, h.vol, m, slots, cnt2, inner);
+        group_totals<true>(slots, cnt2, inner, inner_full, gsize, red);
+        if (gtid == 0) put_record(x, h.c, h.vol, m, slots, cnt2, inner, inner_full);
         group_sync(gsize);
         return;
     }
 }
 
-// Eq. (9), Sec. II-B.3 and the Eq. (8) integers of community c from its record.
+// Eq. (9), Sec. II-B.3 and the Eq. (8) integers of community c from its
+// record.  pen_out receives c's own split penalty (valid when the record holds
+// S_c, i.e. the count ran with per-community terms asked for).
 __device__ __forceinline__ void terms_from_record(const unsigned long long *rc, long long size, long long E,
                                                   ScoreAcc &acc, double *pen_out, double *qs_out,
                                                   double *dens_o, double *contr_o, double *expn_o,
@@ -937,8 +995,8 @@ __device__ __forceinline__ void terms_from_record(const unsigned long long *rc, 
     double qs, dens, contr, expn, cond;
     community_terms(ein, eout, size, E, qs, dens, contr, expn, cond);
     const u128 inner = ((u128)rc[REC_INNER_HI] << 64) | rc[REC_INNER_LO];
-    const double pen = __ddiv_rn(ldexp(u128_to_double(inner), -64),
-                                 __dmul_rn(__dmul_rn(2.0, (double)E), (double)size));
+    const u128 full = ((u128)rc[REC_FULL_HI] << 64) | rc[REC_FULL_LO];
+    const double pen = pair_penalty_once(inner, size, E);
     acc.qds_pair += fp_from_double(pen, SC_QDS);
     acc.slots += rc[REC_SLOTS];
     acc.cnt2 += rc[REC_CNT2];
@@ -951,7 +1009,7 @@ __device__ __forceinline__ void terms_from_record(const unsigned long long *rc, 
     acc.ein += (unsigned long long)ein;
     acc.eout += (unsigned long long)eout;
     acc.nonempty += 1;
-    *pen_out = pen;
+    *pen_out = pair_penalty_own(full, size, E);
     *qs_out = qs;
     *dens_o = dens;
     *contr_o = contr;

@@ -31,8 +31,8 @@ __device__ __forceinline__ void make_quality(const ScoreTotals &t, long long n, 
     r.n_communities_nonempty = (long long)t.nonempty;
     r.intra_edges_total = (long long)t.ein;
     r.cut_edges_total = (long long)(t.eout / 2);
-    r.n_community_pairs = (long long)(t.slots / 2);
-    r.pair_count_sq_sum = (long long)(t.cnt2 / 2);
+    r.n_community_pairs = (long long)t.slots;  // each unordered pair counted once
+    r.pair_count_sq_sum = (long long)t.cnt2;
     const i128 num = (i128)4 * (i128)E * (i128)t.ein - t.vol2;
     const i128 den = (i128)4 * (i128)E * (i128)E;
     r.modularity = __ddiv_rn(i128_to_double(num), i128_to_double(den));

@@ -1036,7 +1036,7 @@ void set_stage_wait_polls(long long polls)
 // loaded.  Short runs then go to single warps, claim_chunk headers at a time.  Each
 // group has its own epoch-tagged table (see count_run).  Runs longer than the
 // staging buffers go to k_count_long.
-template <class TAB>
+template <class TAB, bool FULL>
 __global__ void __launch_bounds__(1024) k_count(CountKArgs a)
 {
     extern __shared__ __align__(16) unsigned char sm[];
@@ -1108,7 +1108,7 @@ __global__ void __launch_bounds__(1024) k_count(CountKArgs a)
             aborted = true;
             break;
         }
-        count_run<true>(a.x, h, stage + k * p.stage_elems + (h.a0 & 3u), eb, epoch, tid, T, red);
+        count_run<true, FULL>(a.x, h, stage + k * p.stage_elems + (h.a0 & 3u), eb, epoch, tid, T, red);
         if (tid == 0) ring[(it + 2) % 3] = nn;
     }
     if (aborted) {
@@ -1144,7 +1144,7 @@ __global__ void __launch_bounds__(1024) k_count(CountKArgs a)
             h.a0 = __shfl_sync(0xffffffffu, mine.a0, j);
             h.m = __shfl_sync(0xffffffffu, mine.m, j);
             h.vol = __shfl_sync(0xffffffffu, mine.vol, j);
-            count_run<false>(a.x, h, a.x.nbr + h.a0, ew, wepoch, lane, 32, red);
+            count_run<false, FULL>(a.x, h, a.x.nbr + h.a0, ew, wepoch, lane, 32, red);
         }
     }
 }
@@ -1227,8 +1227,10 @@ void prepare_kernels()
 {
     cudaFuncSetAttribute(k_score_cm, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     cudaFuncSetAttribute(k_compare_cm, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
-    cudaFuncSetAttribute(k_count<EpochTable>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
-    cudaFuncSetAttribute(k_count<EpochTable32>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+    cudaFuncSetAttribute(k_count<EpochTable, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+    cudaFuncSetAttribute(k_count<EpochTable32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+    cudaFuncSetAttribute(k_count<EpochTable, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+    cudaFuncSetAttribute(k_count<EpochTable32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     cudaFuncSetAttribute(k_count_long, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     cudaFuncSetAttribute(k_count_w, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     cudaFuncSetAttribute(k_expand_bin, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1243,7 +1245,7 @@ void prepare_kernels()
 int count_blocks_per_sm(const Shape &sh)
 {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_count<EpochTable32>, sh.threads, sh.smem_bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_count<EpochTable32, false>, sh.threads, sh.smem_bytes);
     return nb;
 }
 
@@ -1482,6 +1484,7 @@ static int launch_weighted_tail(const GraphDev &g, int K, const ScoreWs &ws, con
     x.rec = ws.rec;
     x.K = K;
     x.err = ws.status;
+    x.full = 0;
     TRACE("k_count_w");
     k_count_w<<<(int)std::min<long long>((long long)num_sms * g_count_w_blocks_per_sm, K), COUNT_W_THREADS,
                 COUNT_W_SMEM, s>>>(
@@ -1593,8 +1596,15 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
     a.stage_wait = g_stage_wait.load();
     TRACE("k_count");
     const int count_grid = community_grid(K, num_sms, sh);  // sh.blocks_per_sm: occupancy resolved by the caller
-    if (K < (1 << 24) - 1) k_count<EpochTable32><<<count_grid, sh.threads, sh.smem_bytes, s>>>(a);
-    else k_count<EpochTable><<<count_grid, sh.threads, sh.smem_bytes, s>>>(a);
+    // S_c of every community only when its per-community Qds term is asked for
+    a.x.full = (pc && pc->qds) ? 1 : 0;
+    if (K < (1 << 24) - 1) {
+        if (a.x.full) k_count<EpochTable32, true><<<count_grid, sh.threads, sh.smem_bytes, s>>>(a);
+        else k_count<EpochTable32, false><<<count_grid, sh.threads, sh.smem_bytes, s>>>(a);
+    } else {
+        if (a.x.full) k_count<EpochTable, true><<<count_grid, sh.threads, sh.smem_bytes, s>>>(a);
+        else k_count<EpochTable, false><<<count_grid, sh.threads, sh.smem_bytes, s>>>(a);
+    }
     TRACE("k_count_long");
     k_count_long<<<std::min(num_sms, K), 1024, MAX_DYN_SMEM, s>>>(a.x, ws.hdr_long, ws.counters, plan_smem(1024, MAX_DYN_SMEM),
                                                       ws.status);

@@ -156,7 +156,7 @@ __device__ __forceinline__ void count_run_weighted(const CountCtx &x, const floa
             }
             block_sync();
             tab_drain(tab, tid, T, [&](int key, long long cnt) {
-                (void)key;
+                if (key < c) return;  // each unordered pair counted once, by its smaller id
                 ++slots;
                 cnt2 += (unsigned long long)cnt * (unsigned long long)cnt;
             });
@@ -186,6 +186,8 @@ __device__ __forceinline__ void count_run_weighted(const CountCtx &x, const floa
             rc[REC_CNT2] = cnt2;
             rc[REC_INNER_LO] = 0ull;
             rc[REC_INNER_HI] = 0ull;
+            rc[REC_FULL_LO] = 0ull;
+            rc[REC_FULL_HI] = 0ull;
 #pragma unroll
             for (int k = 0; k < 4; ++k) recw[(size_t)c * 4 + k] = P.w[k];
         }
