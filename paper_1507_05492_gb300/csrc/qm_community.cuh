@@ -404,7 +404,10 @@ __device__ __forceinline__ bool score_community(const ScoreCtx &x, int c, const 
         group_words_to_leader<4>(w4, gsize, red);
         const u128 inner_t = u192_shr64(group_u192_to_leader(inner, gsize, red, 128));
         u128 full_t = 0;
-        if (full) full_t = u192_shr64(group_u192_to_leader(inner_full, gsize, red, 128));
+        if (full) {
+            group_sync(gsize);  // the leader has read inner's words from `red` before they are reused
+            full_t = u192_shr64(group_u192_to_leader(inner_full, gsize, red, 128));
+        }
         if (gtid == 0) {
             same = w4[0];
             vol = w4[1];
