@@ -758,7 +758,7 @@ def main():
                     help="load the graph as given instead of with QM_REORDER")
     ap.add_argument("--batch", type=int, default=1024)
     ap.add_argument("--plain-sample", type=int, default=256)
-    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--only-compare", action="store_true",
                     help="time only the metrics with ground truth (Eqs. 1-7) on the workload")

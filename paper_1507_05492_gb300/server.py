@@ -65,9 +65,13 @@ class Server:
         self.launches = 0
         self.batch_sizes = []
         self.workers = []
+        # each worker has a stream of normal priority and one of high priority;
+        # batches on the largest graphs take the high one, so that the small
+        # graphs' work running beside them does not stretch the latency tail
         for i in range(n_streams):
-            t = threading.Thread(target=self._worker, args=(torch.cuda.Stream(device=self.device),),
-                                 daemon=True, name=f"qm-server-{i}")
+            streams = (torch.cuda.Stream(device=self.device, priority=0),
+                       torch.cuda.Stream(device=self.device, priority=-1))
+            t = threading.Thread(target=self._worker, args=streams, daemon=True, name=f"qm-server-{i}")
             t.start()
             self.workers.append(t)
 
@@ -149,7 +153,7 @@ class Server:
         head = self._head() if self.pending else None
         return head if head is not None and self.in_flight + head.bytes <= self.budget else None
 
-    def _worker(self, stream):
+    def _worker(self, stream, stream_hi):
         torch.cuda.set_device(self.device)
         while True:
             with self.cv:
@@ -170,9 +174,10 @@ class Server:
                 self.in_flight += total
                 self.launches += 1
                 self.batch_sizes.append(len(batch))
+            st = stream_hi if exclusive else stream
             try:
-                with torch.cuda.stream(stream):
-                    self._run(batch, stream)
+                with torch.cuda.stream(st):
+                    self._run(batch, st)
             except Exception as e:  # every request of a failed launch sees the error
                 for r in batch:
                     if not r.future.done():
@@ -242,18 +247,26 @@ def _make_workload(duration_s, rate, seed, device, pool_per_graph=24):
     graphs, pools, truths = {}, {}, {}
     for gid, cfg in sizes.items():
         g = gen.lfr_graph(gen.config_params(cfg), device=device)
-        graphs[gid] = qm.Graph(g.row_ptr, g.col)
+        # resident graphs of a million nodes and more are renumbered for locality at load
+        graphs[gid] = qm.Graph(g.row_ptr, g.col, reorder=g.n >= 1_000_000)
         truths[gid] = (g.labels, g.K)
         rng = np.random.default_rng(seed)
         pools[gid] = [gen.perturb(g.labels, g.K, float(rng.uniform(0, 0.5)), seed=seed + i)
                       for i in range(pool_per_graph)]
         del g
+    return graphs, pools, truths
+
+
+def _arrivals(pools, truths, rate, seed, duration_s=None, count=None):
+    """Poisson arrivals at `rate` per second for duration_s seconds (or the
+    first `count` of them): each request a uniformly chosen graph, a partition
+    from its pool, and with probability 1/2 a comparison with the planted one."""
     rng = np.random.default_rng(seed)
     t, reqs = 0.0, []
-    gids = list(sizes)
+    gids = list(pools)
     while True:
         t += rng.exponential(1.0 / rate)
-        if t > duration_s:
+        if (duration_s is not None and t > duration_s) or (count is not None and len(reqs) >= count):
             break
         gid = gids[rng.integers(len(gids))]
         lab = pools[gid][rng.integers(len(pools[gid]))]
@@ -262,34 +275,16 @@ def _make_workload(duration_s, rate, seed, device, pool_per_graph=24):
             reqs.append((t, gid, lab, K, truths[gid][0], truths[gid][1]))
         else:
             reqs.append((t, gid, lab, K, None, None))
-    return graphs, reqs
+    return reqs
 
 
 def _pct(xs, q):
     return float(np.percentile(np.asarray(xs) * 1e3, q)) if xs else None
 
 
-def run_benchmark(duration_s=10.0, rate=200.0, seed=11, budget_bytes=8 << 30, n_streams=4):
-    """Poisson arrivals over three resident graphs (10k, 1M, 10M nodes), half of
-    the requests with a ground-truth comparison.  Returns p50/p99 latency and
-    partitions/s for the served loop and for the plain FIFO baseline, plus the
-    same for a burst where every request arrives at once."""
-    device = torch.device("cuda", torch.cuda.current_device())
-    graphs, reqs = _make_workload(duration_s, rate, seed, device)
-    torch.cuda.synchronize()
-    out = {"requests": len(reqs), "rate_per_s": rate, "duration_s": duration_s}
-
-    # warm both paths alike before timing either (scratch pools of the
-    # concurrent workers, captured graphs of the small calls): a burst of the
-    # first requests through a server and through the plain loop
-    warm = [(0.0,) + r[1:] for r in reqs[:min(len(reqs), 96)]]
-    srv = Server(graphs, budget_bytes, n_streams=n_streams)
-    _ = [f.result() for f in [srv.submit(gid, lab, K, truth, kt) for (_, gid, lab, K, truth, kt) in warm]]
-    srv.close()
-    serve_plain(graphs, warm)
-    torch.cuda.synchronize()
-
-    # served, Poisson arrivals
+def _serve(graphs, reqs, budget_bytes, n_streams):
+    """The requests through a Server at their arrival times: latencies
+    (arrival to result) and elapsed seconds, and the server's batch record."""
     srv = Server(graphs, budget_bytes, n_streams=n_streams)
     objs, t0 = [], time.perf_counter()
     for (ta, gid, lab, K, truth, kt) in reqs:
@@ -301,22 +296,59 @@ def run_benchmark(duration_s=10.0, rate=200.0, seed=11, budget_bytes=8 << 30, n_
     el = time.perf_counter() - t0
     srv.close()
     lat = [f.request.t_done - f.request.t_arrival for f in objs]
-    out["served"] = {"p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99), "partitions_per_s": len(reqs) / el,
-                     "launches": srv.launches, "mean_batch": float(np.mean(srv.batch_sizes))}
+    return lat, el, srv
+
+
+def _both(graphs, reqs, budget_bytes, n_streams):
+    lat, el, srv = _serve(graphs, reqs, budget_bytes, n_streams)
     lat_p, el_p = serve_plain(graphs, reqs)
-    out["plain"] = {"p50_ms": _pct(lat_p, 50), "p99_ms": _pct(lat_p, 99), "partitions_per_s": len(reqs) / el_p}
+    return {"requests": len(reqs),
+            "served": {"p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99), "partitions_per_s": len(reqs) / el,
+                       "launches": srv.launches, "mean_batch": float(np.mean(srv.batch_sizes)),
+                       "max_batch": int(max(srv.batch_sizes))},
+            "plain": {"p50_ms": _pct(lat_p, 50), "p99_ms": _pct(lat_p, 99), "partitions_per_s": len(reqs) / el_p}}
+
+
+def run_benchmark(duration_s=60.0, rate=200.0, seed=11, budget_bytes=8 << 30, n_streams=4,
+                  sweep_rates=(1000.0, 5000.0, 20000.0), sweep_requests=1500):
+    """Poisson arrivals over three resident graphs (10k, 1M, 10M nodes), half of
+    the requests with a ground-truth comparison.  Returns p50/p99 latency and
+    partitions/s of the served loop and of the plain FIFO baseline (one call per
+    request, one stream) on the same arrivals: for duration_s seconds at `rate`,
+    for `sweep_requests` requests at each of the sweep rates (where batching
+    starts to pay), and for a burst where every request arrives at once."""
+    device = torch.device("cuda", torch.cuda.current_device())
+    graphs, pools, truths = _make_workload(duration_s, rate, seed, device)
+    reqs = _arrivals(pools, truths, rate, seed, duration_s=duration_s)
+    torch.cuda.synchronize()
+
+    # warm both paths alike before timing either (scratch pools of the
+    # concurrent workers, captured graphs of the small calls): a burst of the
+    # first requests through a server and through the plain loop
+    warm = [(0.0,) + r[1:] for r in reqs[:min(len(reqs), 96)]]
+    srv = Server(graphs, budget_bytes, n_streams=n_streams)
+    _ = [f.result() for f in [srv.submit(gid, lab, K, truth, kt) for (_, gid, lab, K, truth, kt) in warm]]
+    srv.close()
+    serve_plain(graphs, warm)
+    torch.cuda.synchronize()
+
+    out = {"rate_per_s": rate, "duration_s": duration_s} | _both(graphs, reqs, budget_bytes, n_streams)
+    out["sweep"] = {}
+    for i, r in enumerate(sweep_rates):
+        rq = _arrivals(pools, truths, r, seed + 1 + i, count=sweep_requests)
+        out["sweep"][str(int(r))] = _both(graphs, rq, budget_bytes, n_streams)
     # burst: everything arrives at t = 0 (throughput)
-    burst = [(0.0,) + r[1:] for r in reqs]
+    burst = [(0.0,) + r[1:] for r in reqs[:sweep_requests]]
     srv = Server(graphs, budget_bytes, n_streams=n_streams)
     t0 = time.perf_counter()
     objs = [srv.submit(gid, lab, K, truth, kt) for (_, gid, lab, K, truth, kt) in burst]
     _ = [f.result() for f in objs]
     el = time.perf_counter() - t0
     srv.close()
-    out["burst_served_partitions_per_s"] = len(reqs) / el
+    out["burst_requests"] = len(burst)
+    out["burst_served_partitions_per_s"] = len(burst) / el
     _, el_p = serve_plain(graphs, burst)
-    out["burst_plain_partitions_per_s"] = len(reqs) / el_p
+    out["burst_plain_partitions_per_s"] = len(burst) / el_p
     for g in graphs.values():
         g.close()
     return out
-
