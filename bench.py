@@ -256,6 +256,26 @@ def time_oracle(rp, col, lab, K, reps=1):
     return statistics.median(ts)
 
 
+def time_oracle_all_cores(workload: str, device) -> dict:
+    """The oracle's OpenMP statement (the same source built with -fopenmp) on
+    the whole workload graph, all host cores, one run."""
+    from oracle import oracle
+    from paper_1507_05492_gb300 import gen
+    try:
+        oracle.build_omp()
+    except Exception as e:  # reported, never silently dropped
+        return {"unavailable": f"OpenMP build of the oracle failed: {e!r}"}
+    g = gen.lfr_graph(gen.config_params(workload), device=device)
+    rp, col, lab, K, E = g.row_ptr.cpu().numpy(), g.col.cpu().numpy(), g.labels.cpu().numpy(), g.K, g.n_edges
+    del g
+    t0 = time.perf_counter()
+    o = oracle.score_all_cores(rp, col, lab, K)
+    t = time.perf_counter() - t0
+    return {"value": E / t, "unit": UNIT, "cores": o["threads"], "kind": "oracle (OpenMP build, all host cores)",
+            "sample": f"the whole {workload} graph (|E| = {E}), planted partition, one run of {t:.1f} s",
+            "modularity": o["modularity"]}
+
+
 # ------------------------------------------------------------------ reference arm
 
 REFERENCE_BUDGET_S = 150.0      # oracle time of a whole --impl reference run (warm-up + steps)
@@ -705,6 +725,8 @@ def run_ours(args):
                "sample": f"LFR-style graph with the workload's parameters at {args.cpu_sample_nodes} nodes "
                          f"(|E| = {E}), planted partition, single-threaded oracle, {t:.1f} s",
                "host": host_cpu()}
+        del rp, col, lab
+        cpu["all_cores"] = time_oracle_all_cores(args.workload, torch.device("cuda", local))
     extras = {}
     if rank == 0 and world == 1 and not args.no_extras:
         try:

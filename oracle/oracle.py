@@ -20,8 +20,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "qm_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_OMP_PATH = os.path.join(_BUILD, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_omp = None
 
 SCORE_DBL = ["modularity", "modularity_density", "mean_intra_edges", "mean_intra_density",
              "mean_contraction", "mean_inter_edges", "mean_expansion", "mean_conductance",
@@ -45,6 +47,52 @@ def build(force: bool = False) -> str:
                         "-o", tmp, _SRC, "-lm"], check=True)
         os.replace(tmp, _LIB_PATH)
         return _LIB_PATH
+
+
+def build_omp(force: bool = False) -> str:
+    """The same source built with OpenMP (-fopenmp) for the all-core timed
+    baseline (oq_score_omp); returns the .so path."""
+    with _lock:
+        if (not force and os.path.exists(_OMP_PATH)
+                and os.path.getmtime(_OMP_PATH) >= os.path.getmtime(_SRC)):
+            return _OMP_PATH
+        os.makedirs(_BUILD, exist_ok=True)
+        tmp = _OMP_PATH + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
+                        "-o", tmp, _SRC, "-lm"], check=True)
+        os.replace(tmp, _OMP_PATH)
+        return _OMP_PATH
+
+
+def _load_omp():
+    global _omp
+    if _omp is None:
+        lib = ctypes.CDLL(build_omp())
+        p = ctypes.c_void_p
+        lib.oq_score_omp.argtypes = [p, p, ctypes.c_int64, p, ctypes.c_int32, p, p, p]
+        lib.oq_score_omp.restype = ctypes.c_int
+        _omp = lib
+    return _omp
+
+
+def score_all_cores(row_ptr, col, labels, K: int) -> dict:
+    """Eqs. (8)-(9) and the six measures with OpenMP threads over the host cores
+    (the same quantities as score() without per-community arrays); the result
+    carries the thread count in "threads"."""
+    row_ptr = _as(row_ptr, np.int64)
+    col = _as(col, np.int32)
+    labels = _as(labels, np.int32)
+    n = len(row_ptr) - 1
+    assert len(labels) == n
+    dbl = np.zeros(16, np.float64)
+    i64 = np.zeros(8, np.int64)
+    th = np.zeros(1, np.int32)
+    _check(_load_omp().oq_score_omp(_ptr(row_ptr), _ptr(col), n, _ptr(labels), int(K), _ptr(dbl), _ptr(i64),
+                                    _ptr(th)), "score_all_cores")
+    out = {k: float(dbl[i]) for i, k in enumerate(SCORE_DBL)}
+    out.update({k: int(i64[i]) for i, k in enumerate(SCORE_I64)})
+    out["threads"] = int(th[0])
+    return out
 
 
 def _load():

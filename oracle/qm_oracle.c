@@ -821,3 +821,257 @@ int oq_score_weighted(const int64_t *row_ptr, const int32_t *col, const double *
     free(size); free(ein); free(win); free(wout); free(split); free(keys);
     return rc;
 }
+
+/* ------------------------------------------------------------------------
+ * All-core statement of oq_score for the timed CPU baseline.
+ *
+ * oq_score_omp computes oq_score's quantities (same dbl[0..9], i64[0..6]
+ * layout, no per-community arrays) with OpenMP threads over the host cores,
+ * in the same steps: community sizes; each undirected edge classified once
+ * (v > u) into |E_c^in|, |E_c^out| and an unordered pair key; the keys sorted
+ * and counted by runs into |E_ci,cj| and the Eq. (9) split penalty of both
+ * communities; then Eqs. (8)-(9) and the Sec. II-B.3 measures community by
+ * community, summed on one thread.  Threads take static node chunks with
+ * private counters and key buffers (merged afterwards); the sort buckets the
+ * keys by ranges of their smaller community id and sorts each bucket on its
+ * own; split penalties go to per-thread arrays added in thread order.  It
+ * differs from oq_score only in the order of the long double additions of the
+ * split penalties.  Built without -fopenmp it runs on one thread.
+ * *threads receives the number of threads used.
+ * ------------------------------------------------------------------------ */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+static int oq_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+static int oq_thread_id(void)
+{
+#ifdef _OPENMP
+    return omp_get_thread_num();
+#else
+    return 0;
+#endif
+}
+
+int oq_score_omp(const int64_t *row_ptr, const int32_t *col, int64_t n, const int32_t *label, int32_t K,
+                 double *dbl, int64_t *i64, int32_t *threads)
+{
+    if (n < 1 || K < 1)
+        return OQ_EINVAL;
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+    for (int64_t u = 0; u < n; u++)
+        if (label[u] < 0 || label[u] >= K)
+            bad = 1;
+    if (bad)
+        return OQ_EINVAL;
+    const int64_t nnz = row_ptr[n];
+    if (nnz <= 0 || (nnz & 1))
+        return OQ_EINVAL;
+    const int64_t E = nnz / 2;
+    const int T = oq_max_threads();
+    const size_t TK = (size_t)T * (size_t)K;
+    const int B = 4 * T; /* key buckets by ranges of the smaller community id */
+    int64_t *tsize = (int64_t *)calloc(TK, sizeof(int64_t));
+    int64_t *tein = (int64_t *)calloc(TK, sizeof(int64_t));
+    int64_t *teout = (int64_t *)calloc(TK, sizeof(int64_t));
+    uint64_t **tkeys = (uint64_t **)calloc((size_t)T, sizeof(uint64_t *));
+    int64_t *tn = (int64_t *)calloc((size_t)T, sizeof(int64_t));
+    int64_t *tb = (int64_t *)calloc((size_t)T * (size_t)B, sizeof(int64_t)); /* keys per (thread, bucket) */
+    int64_t *boff = (int64_t *)calloc((size_t)B + 1, sizeof(int64_t));
+    int64_t *size = (int64_t *)calloc((size_t)K, sizeof(int64_t));
+    int64_t *ein = (int64_t *)calloc((size_t)K, sizeof(int64_t));
+    int64_t *eout = (int64_t *)calloc((size_t)K, sizeof(int64_t));
+    if (!tsize || !tein || !teout || !tkeys || !tn || !tb || !boff || !size || !ein || !eout) {
+        free(tsize); free(tein); free(teout); free(tkeys); free(tn); free(tb); free(boff);
+        free(size); free(ein); free(eout);
+        return OQ_ENOMEM;
+    }
+    int nomem = 0;
+#pragma omp parallel reduction(| : nomem)
+    {
+        const int t = oq_thread_id();
+        int64_t *ls = tsize + (size_t)t * K, *li = tein + (size_t)t * K, *lo = teout + (size_t)t * K;
+        int64_t cap = 1 << 16, cnt = 0;
+        uint64_t *buf = (uint64_t *)malloc((size_t)cap * sizeof(uint64_t));
+        if (!buf) nomem = 1;
+#pragma omp for schedule(static)
+        for (int64_t u = 0; u < n; u++) {
+            const int32_t lu = label[u];
+            ls[lu]++;
+            for (int64_t k = row_ptr[u]; k < row_ptr[u + 1]; k++) {
+                const int32_t v = col[k];
+                if (v <= u) continue;
+                const int32_t lv = label[v];
+                if (lu == lv) {
+                    li[lu]++;
+                    continue;
+                }
+                lo[lu]++;
+                lo[lv]++;
+                if (!buf) continue;
+                if (cnt == cap) {
+                    uint64_t *nb = (uint64_t *)realloc(buf, (size_t)cap * 2 * sizeof(uint64_t));
+                    if (!nb) { free(buf); buf = NULL; nomem = 1; continue; }
+                    buf = nb;
+                    cap *= 2;
+                }
+                const uint64_t a = (uint64_t)(lu < lv ? lu : lv), b = (uint64_t)(lu < lv ? lv : lu);
+                buf[cnt++] = (a << 32) | b;
+            }
+        }
+        tkeys[t] = buf;
+        tn[t] = cnt;
+        if (buf)
+            for (int64_t i = 0; i < cnt; i++)
+                tb[(size_t)t * B + (int)((buf[i] >> 32) * (uint64_t)B / (uint64_t)K)]++;
+    }
+    int rc = nomem ? OQ_ENOMEM : OQ_OK;
+    /* merged counters */
+#pragma omp parallel for schedule(static)
+    for (int32_t c = 0; c < K; c++)
+        for (int t = 0; t < T; t++) {
+            size[c] += tsize[(size_t)t * K + c];
+            ein[c] += tein[(size_t)t * K + c];
+            eout[c] += teout[(size_t)t * K + c];
+        }
+    free(tsize); free(tein); free(teout);
+    int64_t s_in = 0, s_out = 0, nkeys = 0;
+    for (int32_t c = 0; c < K; c++) { s_in += ein[c]; s_out += eout[c]; }
+    for (int t = 0; t < T; t++) nkeys += tn[t];
+    if (rc == OQ_OK && (2 * s_in + s_out != nnz || s_in + s_out / 2 != E || (s_out & 1) || s_out / 2 != nkeys))
+        rc = OQ_ECHECK;
+    uint64_t *keys = rc == OQ_OK ? (uint64_t *)malloc((size_t)(nkeys > 0 ? nkeys : 1) * sizeof(uint64_t)) : NULL;
+    if (rc == OQ_OK && !keys) rc = OQ_ENOMEM;
+    long double *tsplit = NULL;
+    int64_t *tpair = NULL;
+    int64_t npairs = 0, sq_check = 0;
+    if (rc == OQ_OK) {
+        /* bucket offsets, then every thread scatters its keys into its slice of each bucket */
+        int64_t *at = (int64_t *)malloc((size_t)T * (size_t)B * sizeof(int64_t));
+        if (!at) rc = OQ_ENOMEM;
+        if (rc == OQ_OK) {
+            int64_t acc = 0;
+            for (int b = 0; b < B; b++) {
+                boff[b] = acc;
+                for (int t = 0; t < T; t++) {
+                    at[(size_t)t * B + b] = acc;
+                    acc += tb[(size_t)t * B + b];
+                }
+            }
+            boff[B] = acc;
+#pragma omp parallel for schedule(static)
+            for (int t = 0; t < T; t++) {
+                int64_t *pos = at + (size_t)t * B;
+                for (int64_t i = 0; i < tn[t]; i++) {
+                    const uint64_t key = tkeys[t][i];
+                    keys[pos[(int)((key >> 32) * (uint64_t)B / (uint64_t)K)]++] = key;
+                }
+            }
+#pragma omp parallel for schedule(dynamic, 1)
+            for (int b = 0; b < B; b++)
+                qsort(keys + boff[b], (size_t)(boff[b + 1] - boff[b]), sizeof(uint64_t), cmp_u64);
+        }
+        free(at);
+        tsplit = (long double *)calloc(TK, sizeof(long double));
+        tpair = (int64_t *)calloc(TK, sizeof(int64_t));
+        if (rc == OQ_OK && (!tsplit || !tpair)) rc = OQ_ENOMEM;
+    }
+    for (int t = 0; t < T; t++) free(tkeys[t]);
+    free(tkeys); free(tn); free(tb);
+    if (rc == OQ_OK) {
+        /* |E_ci,cj| by runs; the Eq. (9) split term goes to both communities */
+#pragma omp parallel for schedule(static) reduction(+ : npairs, sq_check)
+        for (int b = 0; b < B; b++) {
+            const int t = oq_thread_id();
+            long double *sp = tsplit + (size_t)t * K;
+            int64_t *ps = tpair + (size_t)t * K;
+            for (int64_t s = boff[b]; s < boff[b + 1];) {
+                int64_t u = s;
+                while (u < boff[b + 1] && keys[u] == keys[s]) u++;
+                const int64_t cnt = u - s;
+                const int32_t ci = (int32_t)(keys[s] >> 32), cj = (int32_t)(keys[s] & 0xffffffffu);
+                npairs++;
+                sq_check += cnt * cnt;
+                ps[ci] += cnt;
+                ps[cj] += cnt;
+                const long double eij = (long double)cnt;
+                const long double term = (eij / (2.0L * (long double)E)) *
+                                         (eij / ((long double)size[ci] * (long double)size[cj]));
+                sp[ci] += term;
+                sp[cj] += term;
+                s = u;
+            }
+        }
+    }
+    free(keys);
+    long double *split = tsplit ? (long double *)calloc((size_t)K, sizeof(long double)) : NULL;
+    if (rc == OQ_OK && !split) rc = OQ_ENOMEM;
+    if (rc == OQ_OK) {
+#pragma omp parallel for schedule(static) reduction(| : bad)
+        for (int32_t c = 0; c < K; c++) {
+            int64_t p = 0;
+            for (int t = 0; t < T; t++) {
+                split[c] += tsplit[(size_t)t * K + c];
+                p += tpair[(size_t)t * K + c];
+            }
+            if (p != eout[c]) bad = 1; /* sum_j |E_ij| = |E_i^out| */
+        }
+        if (bad) rc = OQ_ECHECK;
+    }
+    free(tsplit); free(tpair);
+    if (rc == OQ_OK) {
+        oq_sum q = {0, 0}, qabs = {0, 0}, qds = {0, 0}, qdsabs = {0, 0};
+        oq_sum m_in = {0, 0}, m_dens = {0, 0}, m_contr = {0, 0}, m_out = {0, 0}, m_exp = {0, 0}, m_cond = {0, 0};
+        int64_t nonempty = 0;
+        const long double LE = (long double)E;
+        for (int32_t c = 0; c < K; c++) {
+            if (size[c] == 0) continue;
+            nonempty++;
+            const long double s = (long double)size[c], in = (long double)ein[c], out = (long double)eout[c];
+            const long double frac_in = in / LE, frac_vol = (2.0L * in + out) / (2.0L * LE);
+            sum_add(&q, frac_in - frac_vol * frac_vol);
+            sum_add(&qabs, fabsl(frac_in) + frac_vol * frac_vol);
+            const long double d = size[c] > 1 ? (2.0L * in) / (s * (s - 1.0L)) : 0.0L;
+            const long double t1 = in / LE * d, t2 = (2.0L * in + out) / (2.0L * LE) * d;
+            sum_add(&qds, t1 - t2 * t2 - split[c]);
+            sum_add(&qdsabs, fabsl(t1) + t2 * t2 + split[c]);
+            const long double vol = 2.0L * in + out;
+            sum_add(&m_in, in);
+            sum_add(&m_dens, d);
+            sum_add(&m_contr, 2.0L * in / s);
+            sum_add(&m_out, out);
+            sum_add(&m_exp, out / s);
+            sum_add(&m_cond, vol > 0 ? out / vol : 0.0L);
+        }
+        const long double ne = (long double)nonempty;
+        dbl[0] = (double)sum_get(&q);
+        dbl[1] = (double)sum_get(&qds);
+        dbl[2] = (double)(sum_get(&m_in) / ne);
+        dbl[3] = (double)(sum_get(&m_dens) / ne);
+        dbl[4] = (double)(sum_get(&m_contr) / ne);
+        dbl[5] = (double)(sum_get(&m_out) / ne);
+        dbl[6] = (double)(sum_get(&m_exp) / ne);
+        dbl[7] = (double)(sum_get(&m_cond) / ne);
+        dbl[8] = (double)sum_get(&qabs);
+        dbl[9] = (double)sum_get(&qdsabs);
+        i64[0] = n;
+        i64[1] = E;
+        i64[2] = nonempty;
+        i64[3] = s_in;
+        i64[4] = s_out / 2;
+        i64[5] = npairs;
+        i64[6] = sq_check;
+    }
+    free(split); free(size); free(ein); free(eout); free(boff);
+    if (threads) *threads = T;
+    return rc;
+}

@@ -436,3 +436,25 @@ def test_six_measures_and_pair_counts_by_brute_force(oracle_mod):
         assert r["n_community_pairs"] == len(pairs)
         assert r["pair_count_sq_sum"] == sum(e * e for e in pairs.values())
         assert r["cut_edges_total"] == sum(pairs.values())
+
+
+def test_all_core_build_matches_the_serial_oracle(oracle_mod):
+    """The OpenMP statement used for the all-core CPU baseline computes the
+    serial oracle's quantities: counts exact, sums within the tolerance (only
+    the order of the split-penalty additions differs)."""
+    rng = np.random.default_rng(77)
+    for trial in range(6):
+        n = int(rng.integers(30, 3000))
+        rp, col, _ = random_graph(rng, n, float(rng.uniform(0.002, 0.05)))
+        K = int(rng.integers(1, max(2, n // 3)))
+        lab = rng.integers(0, K, n).astype(np.int32)
+        a = oracle_mod.score(rp, col, lab, K)
+        b = oracle_mod.score_all_cores(rp, col, lab, K)
+        assert b["threads"] >= 1
+        for k in ("n_nodes", "n_edges", "n_communities_nonempty", "intra_edges_total", "cut_edges_total",
+                  "n_community_pairs", "pair_count_sq_sum"):
+            assert a[k] == b[k], (trial, k)
+        for k in ("modularity", "modularity_density", "mean_intra_edges", "mean_intra_density",
+                  "mean_contraction", "mean_inter_edges", "mean_expansion", "mean_conductance"):
+            cond = {"modularity": a["cond_modularity"], "modularity_density": a["cond_modularity_density"]}.get(k, 0.0)
+            assert close(b[k], a[k], cond), (trial, k, a[k], b[k])
