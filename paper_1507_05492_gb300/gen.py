@@ -401,6 +401,9 @@ def config_params(name: str, seed: int | None = None) -> LfrParams:
         "lfr100k_mu03": LfrParams(n=100_000, k_mean=20, k_max=50, s_min=20, s_max=100, mu=0.3, seed=5),
         "lfr100k_mu05": LfrParams(n=100_000, k_mean=20, k_max=50, s_min=20, s_max=100, mu=0.5, seed=6),
         "lfr1m": LfrParams(n=1_000_000, k_mean=20, k_max=100, s_min=20, s_max=1000, mu=0.3, seed=8),
+        # the 100M-node recipe at 32M nodes: its label array (128 MB) is about
+        # the L2's size, so profiler captures of a few GB still see DRAM behaviour
+        "lfr32m": LfrParams(n=32_000_000, k_mean=20, k_max=100, s_min=20, s_max=1000, mu=0.3, seed=10),
     }
     p = table[name]
     if seed is not None:
