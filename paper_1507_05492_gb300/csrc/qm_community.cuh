@@ -764,7 +764,7 @@ __device__ __forceinline__ unsigned etab_next_epoch(const TAB &t, unsigned epoch
 {
     if (epoch < 255u) return epoch + 1u;
     t.wipe(gtid, gsize);
-    group_sync(gsize);
+    group_sync_n(gsize);
     return 1u;
 }
 
@@ -798,7 +798,9 @@ __device__ __forceinline__ void group_totals(unsigned long long &slots, unsigned
     if (FULL) inner_full = u192_warp_sum(inner_full);
     if (gsize == 32) return;
     constexpr int WW = FULL ? 8 : 5;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // the group's warps are w0 .. w0 + nw - 1; its leader is its first thread
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = gsize >> 5;
+    const int w0 = ((int)threadIdx.x / gsize) * nw;
     if (lane == 0) {
         red[WW * wid] = slots;
         red[WW * wid + 1] = cnt2;
@@ -811,9 +813,9 @@ __device__ __forceinline__ void group_totals(unsigned long long &slots, unsigned
             red[WW * wid + 7] = inner_full.w2;
         }
     }
-    block_sync();
-    if (threadIdx.x == 0)
-        for (int w = 1; w < nw; ++w) {
+    group_sync_n(gsize);
+    if ((int)threadIdx.x % gsize == 0)
+        for (int w = w0 + 1; w < w0 + nw; ++w) {
             slots += red[WW * w];
             cnt2 += red[WW * w + 1];
             const U192 o{red[WW * w + 2], red[WW * w + 3], red[WW * w + 4]};
@@ -898,13 +900,13 @@ __device__ __forceinline__ void count_run(const CountCtx &x, const RunHdr &h, co
                 if (!FULL || lv > c) add_share(inner, slots, cnt2, prev, rj);
                 if (FULL) add_share(inner_full, s_dummy, c_dummy, prev, rj);
             }
-            group_sync(gsize);
+            group_sync_n(gsize);
             if (*(volatile int *)tab.overflow) ok = false;
         }
         if (!ok) {
-            group_sync(gsize);
+            group_sync_n(gsize);
             if (gtid == 0) *tab.overflow = 0;
-            group_sync(gsize);
+            group_sync_n(gsize);
             const unsigned nr = R * 2u;
             if (nr > R_MAX) {
                 if (gtid == 0) atomicOr(x.err, 2);

@@ -580,4 +580,19 @@ __device__ __forceinline__ void group_sync(int group)
     else block_sync();
 }
 
+// Barrier of a group of threads that may also be one of the block's equal
+// groups of `group` consecutive threads (a multiple of 32): such a group takes
+// named barrier 1 + its index (non-aligned, like block_sync).
+__device__ __forceinline__ void group_sync_n(int group)
+{
+    if (group == 32) {
+        __syncwarp();
+    } else if (group == (int)blockDim.x) {
+        block_sync();
+    } else {
+        asm volatile("barrier.sync %0, %1;" ::"r"(1 + (int)threadIdx.x / group), "r"(group) : "memory");
+        __syncwarp();
+    }
+}
+
 }  // namespace qmk

@@ -54,6 +54,7 @@ struct CountPlan {
     int red_off, ctl_off, bar_off, stage_off, slot_off;
     int stage_elems;
     int cap, fill, cap_w, fill_w;
+    int ng, cap_g, fill_g;  // ng groups of warps, each with a table of cap_g slots (ng = 1: none)
     int bytes;
 };
 CountPlan plan_count(int threads, int smem_bytes);
@@ -77,6 +78,7 @@ struct ScoreWs {
     qmk::RunHdr *hdr_big;       // two-phase only: [K] run headers for whole blocks
     qmk::RunHdr *hdr_small;     // two-phase only: [K] run headers for single warps
     qmk::RunHdr *hdr_long;      // two-phase only: [K] run headers for k_count_long
+    qmk::RunHdr *hdr_mid;       // two-phase only: [K] run headers for groups of warps
     int *nbr;                   // two-phase only: [n_arcs] neighbour labels in community order
     unsigned long long *rec;    // two-phase only: [K][6] per-community records
     float *nbrw = nullptr;      // weighted graphs: [n_arcs] weights of the packed cut arcs

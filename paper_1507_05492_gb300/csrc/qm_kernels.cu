@@ -22,7 +22,7 @@ namespace qm {
 using namespace qmk;
 
 enum { C_BIG_COUNT = 0, C_BIG_NEXT = 1, C_SMALL_NEXT = 2, C_OVF_COUNT = 3, C_OVF_NEXT = 4, C_SMALL_COUNT = 5,
-       C_LONG_COUNT = 6, C_NCELLS = 7 };
+       C_LONG_COUNT = 6, C_NCELLS = 7, C_MID_COUNT = 8 };
 
 constexpr int SCAN_TILE = 4096;   // elements per block in the multi-block scan
 constexpr int SCAN_SINGLE_MAX = 1 << 16;
@@ -85,6 +85,11 @@ CountPlan plan_count(int T, int S)
     off += cap * 8;
     p.cap_w = cap / W;
     p.fill_w = 3 * p.cap_w / 4;
+    // four groups of W/4 warps, each with a quarter of the table, take the
+    // runs between a warp's and the block's reach
+    p.ng = (W >= 8 && W % 4 == 0) ? 4 : 1;
+    p.cap_g = cap / p.ng;
+    p.fill_g = p.ng > 1 ? 3 * p.cap_g / 4 : p.fill_w;
     p.bytes = off;
     return p;
 }
@@ -967,14 +972,14 @@ __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__re
 
 #include "qm_binned.cuh"
 
-// One header per non-empty community, sorted into three lists by run length
+// One header per non-empty community, sorted into four lists by run length
 // m (the community's cut arcs, an upper bound on its distinct neighbouring
-// communities): m <= warp_fill for single warps, warp_fill < m <= block_fill
-// for whole blocks of k_count, longer runs for k_count_long.  Appends are
-// warp-aggregated.
+// communities): m <= warp_fill for single warps, up to group_fill for groups
+// of warps, up to block_fill for whole blocks of k_count, longer runs for
+// k_count_long.  Appends are warp-aggregated.
 __global__ void k_classify(const int *start, const unsigned *aoff, const int *inter, int K, int warp_fill,
-                           int block_fill, RunHdr *big, RunHdr *small, RunHdr *lng, int *counters,
-                           const int *status, Shard own)
+                           int group_fill, int block_fill, RunHdr *big, RunHdr *small, RunHdr *lng, RunHdr *mid,
+                           int *counters, const int *status, Shard own)
 {
     if (*status) return;
     const int lane = threadIdx.x & 31;
@@ -989,20 +994,22 @@ __global__ void k_classify(const int *start, const unsigned *aoff, const int *in
             if (s1 > s0 && own.owns(c)) {
                 const unsigned a0 = aoff[s0];
                 h = RunHdr{c, a0, (unsigned)inter[c], aoff[s1] - a0};
-                cls = h.m > (unsigned)block_fill ? 2 : (h.m > (unsigned)warp_fill ? 0 : 1);
+                cls = h.m > (unsigned)block_fill ? 2
+                      : h.m > (unsigned)group_fill ? 0
+                      : h.m > (unsigned)warp_fill ? 3 : 1;
             }
         }
+        const int ctr[4] = {C_BIG_COUNT, C_SMALL_COUNT, C_LONG_COUNT, C_MID_COUNT};
+        RunHdr *const lists[4] = {big, small, lng, mid};
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < 4; ++k) {
             const unsigned mask = __ballot_sync(0xffffffffu, cls == k);
             if (!mask) continue;
             const int leader = __ffs(mask) - 1;
             int base = 0;
-            if (lane == leader)
-                base = atomicAdd(&counters[k == 0 ? C_BIG_COUNT : (k == 1 ? C_SMALL_COUNT : C_LONG_COUNT)],
-                                 __popc(mask));
+            if (lane == leader) base = atomicAdd(&counters[ctr[k]], __popc(mask));
             base = __shfl_sync(0xffffffffu, base, leader);
-            if (cls == k) (k == 0 ? big : (k == 1 ? small : lng))[base + __popc(mask & lt)] = h;
+            if (cls == k) lists[k][base + __popc(mask & lt)] = h;
         }
     }
 }
@@ -1011,6 +1018,7 @@ struct CountKArgs {
     CountCtx x;
     const RunHdr *big;
     const RunHdr *small;
+    const RunHdr *mid;
     int *counters;
     const int *status;
     CountPlan plan;
@@ -1122,6 +1130,22 @@ __global__ void __launch_bounds__(1024) k_count(CountKArgs a)
                     consume(q);
         }
         return;
+    }
+    // runs between a warp's and the block's reach: groups of warps, each with
+    // a quarter of the table (started empty) and its own named barrier, take
+    // runs in a static round-robin
+    if (p.ng > 1) {
+        block_sync();
+        for (int i = tid; i < p.cap; i += T) slot[i] = 0ull;
+        block_sync();
+        const int GS = T / p.ng, g = tid / GS, gtid = tid % GS;
+        const TAB eg = make_table<TAB>(slot + (size_t)g * p.cap_g, p.cap_g, &ctl[3 + 2 * (g * (GS >> 5))]);
+        unsigned gepoch = 0;
+        const int nmid = a.counters[C_MID_COUNT];
+        for (long long i = b * p.ng + g; i < nmid; i += G * p.ng) {
+            const RunHdr h = a.mid[i];
+            count_run<false, FULL>(a.x, h, a.x.nbr + h.a0, eg, gepoch, gtid, GS, red);
+        }
     }
     // the warps' tables are slices of the block's: start them empty
     block_sync();
@@ -1440,6 +1464,8 @@ ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K, bool w
     p += align_up((size_t)K * sizeof(RunHdr), 256);
     w.hdr_long = (RunHdr *)p;
     p += align_up((size_t)K * sizeof(RunHdr), 256);
+    w.hdr_mid = (RunHdr *)p;
+    p += align_up((size_t)K * sizeof(RunHdr), 256);
     w.scan_tmp = (int *)p;
     p += align_up((size_t)(tiles + 1) * 4, 256);
     w.bytes = (size_t)(p - (char *)base);
@@ -1575,9 +1601,9 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
     }
     const CountPlan cp = plan_count(sh.threads, sh.smem_bytes);
     TRACE("k_classify");
-    k_classify<<<grid_for(K, 256, num_sms, 4), 256, 0, s>>>(ws.start, ws.aoff, ws.inter, K, cp.fill_w, cp.fill,
-                                                            ws.hdr_big, ws.hdr_small, ws.hdr_long, ws.counters,
-                                                            ws.status, own);
+    k_classify<<<grid_for(K, 256, num_sms, 4), 256, 0, s>>>(ws.start, ws.aoff, ws.inter, K, cp.fill_w, cp.fill_g,
+                                                            cp.fill, ws.hdr_big, ws.hdr_small, ws.hdr_long,
+                                                            ws.hdr_mid, ws.counters, ws.status, own);
     ++launches;
     CountKArgs a;
     a.x.nbr = ws.nbr;
@@ -1590,6 +1616,7 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
     a.x.err = ws.status;
     a.big = ws.hdr_big;
     a.small = ws.hdr_small;
+    a.mid = ws.hdr_mid;
     a.counters = ws.counters;
     a.status = ws.status;
     a.plan = cp;
