@@ -616,7 +616,7 @@ struct CountCtx {
     const int *nbr;                   // packed inter-community neighbour labels
     const unsigned *aoff;             // [n + 1] arc offset of each member position
     const int *start;                 // [K + 1] member offsets
-    const int *inter;                 // [K] packed entries of each community (its cut arcs)
+    const int *inter;                 // [K] cut arcs of each community (its packed run may hold only part)
     const Rcp *recip;                 // rcp_of(|c|)
     unsigned long long *rec;          // [K][REC_WORDS]
     int K;
@@ -775,7 +775,9 @@ __device__ __forceinline__ void put_record(const CountCtx &x, int c, unsigned vo
 {
     const u128 in = u192_shr64(inner), fu = u192_shr64(inner_full);
     unsigned long long *rc = x.rec + (size_t)c * REC_WORDS;
-    rc[REC_SAME] = (unsigned long long)(vol - m);
+    // |E_c^out| is the cut-arc count (the packed run may hold only part of it)
+    (void)m;
+    rc[REC_SAME] = (unsigned long long)(vol - (unsigned)x.inter[c]);
     rc[REC_VOL] = (unsigned long long)vol;
     rc[REC_SLOTS] = slots;
     rc[REC_CNT2] = cnt2;

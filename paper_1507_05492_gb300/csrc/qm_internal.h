@@ -75,6 +75,7 @@ struct ScoreWs {
     int *scan_tmp;              // [scan tiles + 1]
     unsigned *aoff;             // two-phase only: [n + 1] arc offsets of member positions
     int *inter;                 // two-phase only: [K] cut arcs of each community (zeroed)
+    int *inter_hi;              // two-phase only: [K] packed labels above c of each community (zeroed)
     qmk::RunHdr *hdr_big;       // two-phase only: [K] run headers for whole blocks
     qmk::RunHdr *hdr_small;     // two-phase only: [K] run headers for single warps
     qmk::RunHdr *hdr_long;      // two-phase only: [K] run headers for k_count_long

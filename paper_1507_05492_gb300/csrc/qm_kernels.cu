@@ -814,16 +814,19 @@ __device__ __forceinline__ int ld_label3(const unsigned long long *plab, int v, 
 }
 
 // Gathers the labels of arcs [e_lo, e_hi) of a run of community c (loc(e) is
-// the CSR index of arc e) and packs those != c into c's segment at cbase.  On
-// a weighted graph (WT) the arc weights travel with the packed labels (nbrw)
-// and each lane sums the fixed-point weights of its intra and cut arcs.
-template <bool WT, bool PACK, class LOC>
+// the CSR index of arc e), counts those != c in inter[c] (the cut arcs of c)
+// and packs them into c's segment at cbase; with HI only the labels above c are
+// packed (each unordered pair of communities is counted by its smaller id), and
+// hi[c] counts them.  On a weighted graph (WT) the arc weights travel with the
+// packed labels (nbrw) and each lane sums the fixed-point weights of its intra
+// and cut arcs.
+template <bool WT, bool PACK, bool HI, class LOC>
 __device__ __forceinline__ void expand_range(unsigned e_lo, unsigned e_hi, int c, unsigned cbase, LOC loc,
                                              const int *__restrict__ col, const int *__restrict__ labels,
                                              const unsigned long long *__restrict__ plab,
-                                             int *inter, int *__restrict__ nbr, unsigned long long keep, int lane,
-                                             const float *__restrict__ wt, float *__restrict__ nbrw, u128 &w_in,
-                                             u128 &w_out)
+                                             int *inter, int *hi, int *__restrict__ nbr, unsigned long long keep,
+                                             int lane, const float *__restrict__ wt, float *__restrict__ nbrw,
+                                             u128 &w_in, u128 &w_out)
 {
     const unsigned lt = (1u << lane) - 1u;
     for (unsigned e0 = e_lo; e0 < e_hi; e0 += 32u * EXPAND_UNROLL) {
@@ -847,15 +850,17 @@ __device__ __forceinline__ void expand_range(unsigned e_lo, unsigned e_hi, int c
                 }
         }
         unsigned msk[EXPAND_UNROLL];
-        int tot = 0;
+        int tot = 0, cut = 0;
 #pragma unroll
         for (int k = 0; k < EXPAND_UNROLL; ++k) {
-            msk[k] = __ballot_sync(0xffffffffu, lab[k] >= 0 && lab[k] != c);
+            if (HI) cut += __popc(__ballot_sync(0xffffffffu, lab[k] >= 0 && lab[k] != c));
+            msk[k] = __ballot_sync(0xffffffffu, HI ? lab[k] > c : (lab[k] >= 0 && lab[k] != c));
             tot += __popc(msk[k]);
         }
+        if (HI && cut && lane == 0) atomicAdd(&inter[c], cut);
         if (tot == 0) continue;
         int pos = 0;
-        if (lane == 0) pos = atomicAdd(&inter[c], tot);
+        if (lane == 0) pos = atomicAdd(HI ? &hi[c] : &inter[c], tot);
         unsigned at = cbase + (unsigned)__shfl_sync(0xffffffffu, pos, 0);
 #pragma unroll
         for (int k = 0; k < EXPAND_UNROLL; ++k) {
@@ -882,7 +887,7 @@ __device__ __forceinline__ void flush_weights(unsigned long long *wl, int c, u12
     }
 }
 
-template <bool WT, bool PACK>
+template <bool WT, bool PACK, bool HI>
 __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__restrict__ row_ptr,
                                                            const int *__restrict__ col,
                                                            const int *__restrict__ labels,
@@ -890,7 +895,8 @@ __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__re
                                                            const int *__restrict__ members,
                                                            const unsigned *__restrict__ aoff,
                                                            const int *__restrict__ start, long long n,
-                                                           int *inter, int *__restrict__ nbr, const int *status,
+                                                           int *inter, int *inter_hi, int *__restrict__ nbr,
+                                                           const int *status,
                                                            Shard own, const float *__restrict__ wt,
                                                            float *__restrict__ nbrw, unsigned long long *wl)
 {
@@ -940,8 +946,8 @@ __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__re
                 }
                 const long long cs = rsw[lo] - (long long)e_lo;  // CSR index of arc e is cs + e
                 u128 w_in = 0, w_out = 0;
-                expand_range<WT, PACK>(e_lo, e_hi, c, cbase, [cs](unsigned e) { return cs + (long long)e; }, col,
-                                       labels, plab, inter, nbr, keep, lane, wt, nbrw, w_in, w_out);
+                expand_range<WT, PACK, HI>(e_lo, e_hi, c, cbase, [cs](unsigned e) { return cs + (long long)e; }, col,
+                                           labels, plab, inter, inter_hi, nbr, keep, lane, wt, nbrw, w_in, w_out);
                 if (WT) flush_weights(wl, c, w_in, w_out, lane);
             }
         } else {
@@ -956,13 +962,13 @@ __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__re
                 if (lane == 0) cbase = __ldg(&aoff[__ldg(&start[c])]);
                 cbase = __shfl_sync(0xffffffffu, cbase, 0);
                 u128 w_in = 0, w_out = 0;
-                expand_range<WT, PACK>(
+                expand_range<WT, PACK, HI>(
                     e_lo, e_hi, c, cbase,
                     [=](unsigned e) {
                         const int o = m_lo + upper_bound_smem(offw + m_lo, m_hi - m_lo, e) - 1;
                         return rsw[o] + (long long)(e - offw[o]);
                     },
-                    col, labels, plab, inter, nbr, keep, lane, wt, nbrw, w_in, w_out);
+                    col, labels, plab, inter, inter_hi, nbr, keep, lane, wt, nbrw, w_in, w_out);
                 if (WT) flush_weights(wl, c, w_in, w_out, lane);
             }
         }
@@ -973,11 +979,11 @@ __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__re
 #include "qm_binned.cuh"
 
 // One header per non-empty community, sorted into four lists by run length
-// m (the community's cut arcs, an upper bound on its distinct neighbouring
-// communities): m <= warp_fill for single warps, up to group_fill for groups
+// m (the community's packed entries, an upper bound on the distinct keys its
+// count will see): m <= warp_fill for single warps, up to group_fill for groups
 // of warps, up to block_fill for whole blocks of k_count, longer runs for
 // k_count_long.  Appends are warp-aggregated.
-__global__ void k_classify(const int *start, const unsigned *aoff, const int *inter, int K, int warp_fill,
+__global__ void k_classify(const int *start, const unsigned *aoff, const int *mlen, int K, int warp_fill,
                            int group_fill, int block_fill, RunHdr *big, RunHdr *small, RunHdr *lng, RunHdr *mid,
                            int *counters, const int *status, Shard own)
 {
@@ -993,7 +999,7 @@ __global__ void k_classify(const int *start, const unsigned *aoff, const int *in
             const int s0 = start[c], s1 = start[c + 1];
             if (s1 > s0 && own.owns(c)) {
                 const unsigned a0 = aoff[s0];
-                h = RunHdr{c, a0, (unsigned)inter[c], aoff[s1] - a0};
+                h = RunHdr{c, a0, (unsigned)mlen[c], aoff[s1] - a0};
                 cls = h.m > (unsigned)block_fill ? 2
                       : h.m > (unsigned)group_fill ? 0
                       : h.m > (unsigned)warp_fill ? 3 : 1;
@@ -1409,6 +1415,8 @@ ScoreWs carve_score2_ws(void *base, long long n, long long n_arcs, int K, bool w
     p += align_up((size_t)K * 4, 256);
     w.inter = (int *)p;
     p += align_up((size_t)K * 4, 256);
+    w.inter_hi = (int *)p;
+    p += align_up((size_t)K * 4, 256);
     if (weighted) {
         w.wl = (unsigned long long *)p;
         p += align_up((size_t)K * 6 * 8, 256);
@@ -1558,12 +1566,13 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
                             ws.counters, ws.scan_tmp, ws.status, s, tr);
     if (g.wt) {
         TRACE("k_expand");
-        k_expand<true, false><<<expand_grid(n, num_sms), EXPAND_THREADS, 0, s>>>(g.row_ptr, g.col, labels, nullptr, ws.members, ws.aoff,
-                                                              ws.start, n, ws.inter, ws.nbr, ws.status, own, g.wt,
+        k_expand<true, false, false><<<expand_grid(n, num_sms), EXPAND_THREADS, 0, s>>>(g.row_ptr, g.col, labels, nullptr, ws.members, ws.aoff,
+                                                              ws.start, n, ws.inter, nullptr, ws.nbr, ws.status, own, g.wt,
                                                               ws.nbrw, ws.wl);
         ++launches;
         return launch_weighted_tail(g, K, ws, pc, num_sms, s, tr, own, launches);
     }
+    const int *packed_len = ws.inter;  // entries of each community's packed run
     if (ws.bin_pool) {
         BinArgs ba;
         ba.pool = ws.bin_pool;
@@ -1584,24 +1593,39 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
         TRACE("k_resolve");
         k_resolve<<<num_sms * 8, RESOLVE_THREADS, 0, s>>>(ba, labels, ws.inter, ws.nbr, ws.status);
         launches += 3;
-    } else if (ws.plab) {
-        TRACE("k_pack3");
-        k_pack3<<<grid_for((n + 2) / 3, 256, num_sms, 8), 256, 0, s>>>(labels, n, ws.plab, ws.status);
-        TRACE("k_expand");
-        k_expand<false, true><<<expand_grid(n, num_sms), EXPAND_THREADS, 0, s>>>(
-            g.row_ptr, g.col, labels, ws.plab, ws.members, ws.aoff, ws.start, n, ws.inter, ws.nbr, ws.status, own,
-            nullptr, nullptr, nullptr);
-        launches += 2;
     } else {
+        // without per-community Qds terms each unordered pair of communities is
+        // counted by its smaller id only, so only the labels above c are packed
+        const bool hi = !(pc && pc->qds);
+        const dim3 eg(expand_grid(n, num_sms)), eb(EXPAND_THREADS);
+        if (ws.plab) {
+            TRACE("k_pack3");
+            k_pack3<<<grid_for((n + 2) / 3, 256, num_sms, 8), 256, 0, s>>>(labels, n, ws.plab, ws.status);
+            ++launches;
+        }
         TRACE("k_expand");
-        k_expand<false, false><<<expand_grid(n, num_sms), EXPAND_THREADS, 0, s>>>(
-            g.row_ptr, g.col, labels, nullptr, ws.members, ws.aoff, ws.start, n, ws.inter, ws.nbr, ws.status, own,
-            nullptr, nullptr, nullptr);
+        if (ws.plab && hi)
+            k_expand<false, true, true><<<eg, eb, 0, s>>>(g.row_ptr, g.col, labels, ws.plab, ws.members, ws.aoff,
+                                                          ws.start, n, ws.inter, ws.inter_hi, ws.nbr, ws.status, own,
+                                                          nullptr, nullptr, nullptr);
+        else if (ws.plab)
+            k_expand<false, true, false><<<eg, eb, 0, s>>>(g.row_ptr, g.col, labels, ws.plab, ws.members, ws.aoff,
+                                                           ws.start, n, ws.inter, nullptr, ws.nbr, ws.status, own,
+                                                           nullptr, nullptr, nullptr);
+        else if (hi)
+            k_expand<false, false, true><<<eg, eb, 0, s>>>(g.row_ptr, g.col, labels, nullptr, ws.members, ws.aoff,
+                                                           ws.start, n, ws.inter, ws.inter_hi, ws.nbr, ws.status,
+                                                           own, nullptr, nullptr, nullptr);
+        else
+            k_expand<false, false, false><<<eg, eb, 0, s>>>(g.row_ptr, g.col, labels, nullptr, ws.members,
+                                                            ws.aoff, ws.start, n, ws.inter, nullptr, ws.nbr,
+                                                            ws.status, own, nullptr, nullptr, nullptr);
         ++launches;
+        packed_len = hi ? ws.inter_hi : ws.inter;
     }
     const CountPlan cp = plan_count(sh.threads, sh.smem_bytes);
     TRACE("k_classify");
-    k_classify<<<grid_for(K, 256, num_sms, 4), 256, 0, s>>>(ws.start, ws.aoff, ws.inter, K, cp.fill_w, cp.fill_g,
+    k_classify<<<grid_for(K, 256, num_sms, 4), 256, 0, s>>>(ws.start, ws.aoff, packed_len, K, cp.fill_w, cp.fill_g,
                                                             cp.fill, ws.hdr_big, ws.hdr_small, ws.hdr_long,
                                                             ws.hdr_mid, ws.counters, ws.status, own);
     ++launches;
