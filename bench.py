@@ -44,12 +44,17 @@ PROFILE_DIR = os.path.join(ROOT, "profiles")
 FALLBACK_HBM = 6800.0
 
 
+# The translation unit that defines the kernels of the scoring step, with the
+# headers it includes; the DRAM records under profiles/ name its hash.
+STEP_SOURCES = ("qm_kernels.cu", "qm_community.cuh", "qm_device.cuh", "qm_finalize.cuh", "qm_binned.cuh",
+                "qm_weighted.cuh", "qm_internal.h")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1507_05492_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in STEP_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
