@@ -631,6 +631,26 @@ def bench_configs(args):
         out["lfr10m" + ("" if reorder else "_graph_as_given")] = {
             "score_ms_per_call": t, "edges_per_s": g.n_edges / (t / 1e3)}
         graph.close()
+    # batched candidates at this size: 16 perturbed copies of the planted partition (0-50% of
+    # the nodes moved), each scored and compared with the planted one, in one batched call
+    # (above 2^21 nodes the plain pipelines of every item, captured into one launch) against
+    # the plain loop of one score and one compare call each
+    P = 16
+    cands = torch.stack([gen.perturb(g.labels, g.K, 0.5 * p / (P - 1), seed=900 + p) for p in range(P)])
+    Ks = [g.K] * P
+    graph = qm.Graph(g.row_ptr, g.col, reorder=True)
+
+    def plain_loop():
+        return [(qm.score(graph, cands[p], g.K), qm.compare(g.labels, cands[p], g.K, g.K)) for p in range(P)]
+    t_b = timed(lambda: qm.evaluate_batched(graph, cands, Ks, g.labels, g.K), 5)
+    t_p = timed(plain_loop, 5)
+    oq, oc = qm.evaluate_batched(graph, cands, Ks, g.labels, g.K)
+    same = all(oq[p] == a and oc[p] == b for p, (a, b) in enumerate(plain_loop()))
+    out["lfr10m_batched_candidates"] = {"candidates": P, "ms_per_batch": t_b, "partitions_per_s_batched": P / (t_b / 1e3),
+                                        "partitions_per_s_plain": P / (t_p / 1e3), "identical_to_plain": bool(same),
+                                        "what": "score + compare with the planted partition per candidate, graph reordered"}
+    graph.close()
+    del cands
     # the same graph with a float32 weight per edge (a hash of the pair, in [0.05, 5))
     u = torch.repeat_interleave(torch.arange(g.n, device=dev), g.row_ptr[1:] - g.row_ptr[:-1])
     v = g.col.to(torch.int64)

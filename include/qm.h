@@ -209,8 +209,15 @@ qm_status qm_compare_partitions(const int32_t *truth, const int32_t *found, int6
                                 qm_compare *out, void *stream);
 
 /*
+ * Batched calls.  On graphs of up to 2^21 nodes the items run in one
+ * persistent kernel, one block per item, replayed from a captured CUDA graph.
+ * On larger graphs one block per item would not fill the GPU, so every item
+ * runs the plain full-GPU pipelines one after another, all captured into one
+ * CUDA graph launched once, with one copy of all results at the end.  Either
+ * way each result is bit-identical to the plain call on that item.
+ *
  * qm_score_partitions_batched -- score P partitions of one graph in a single
- * persistent launch (replayed from a captured CUDA graph).
+ * launch.
  *   labels  int32[P][n_nodes] row-major
  *   K       host int32[P], label-id count of each partition
  *   out     host qm_quality[P]
@@ -222,7 +229,7 @@ qm_status qm_score_partitions_batched(const qm_graph *g, const int32_t *labels, 
 
 /*
  * qm_compare_partitions_batched -- compare P detected partitions with ground
- * truth in one persistent launch.
+ * truth in one launch.
  *   truth   int32[n] when flags has QM_SHARED_TRUTH, else int32[P][n]
  *   found   int32[P][n]
  *   k_truth host int32[1] with QM_SHARED_TRUTH, else int32[P]; k_found host int32[P]
@@ -235,7 +242,7 @@ qm_status qm_compare_partitions_batched(const int32_t *truth, const int32_t *fou
 
 /*
  * qm_evaluate_partitions_batched -- for each of P candidate partitions of one
- * graph, every metric with and without ground truth, in one persistent launch:
+ * graph, every metric with and without ground truth, in one launch:
  * out_q[p] as qm_score_partition(labels[p]) and out_c[p] as
  * qm_compare_partitions(truth, labels[p]).
  *   truth int32[n] shared by all candidates, k_truth its label-id count

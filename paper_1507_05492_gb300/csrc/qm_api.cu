@@ -1056,6 +1056,128 @@ static qm_status run_batched(int dev, BatchDesc &d, const Shape &sh0, qm_quality
     return QM_OK;
 }
 
+// Batched calls on graphs too large for one block per item: every item runs
+// the plain full-GPU pipelines (the kernels of qm_score_partition and
+// qm_compare_partitions, so the results are the same bits), one after another,
+// captured into one CUDA graph that is launched once; the results come back in
+// one copy at the end.  Labels (and truths) are device rows in the graph's
+// stored order.
+static constexpr long long kBatchBlockMaxN = 1LL << 21;
+
+struct LargeItem {
+    const int32_t *labels;
+    int K;
+    const int32_t *truth;
+    int kt;
+    int flags;  // 1: score, 2: compare with the truth
+};
+
+// Launch shape of the comparison pipeline (see qm_compare_partitions).
+static Shape compare_shape()
+{
+    Shape cs = default_shape();
+    cs.algo = 0;
+    cs.threads = 128;
+    cs.smem_bytes = 48 * 1024;
+    return resolve_plain(cs);
+}
+
+static qm_status run_large_batched(qm_graph *g, int dev, long long n, const std::vector<LargeItem> &items,
+                                   qm_quality *out_q, qm_compare *out_c, cudaStream_t s)
+{
+    const int P = (int)items.size();
+    const bool wt = g && g->wt;
+    std::vector<Shape> shapes(P);
+    size_t sb = 0, cb = 0;
+    for (int p = 0; p < P; ++p) {  // shapes and scratch sizes before any capture
+        const LargeItem &it = items[p];
+        if (it.flags & 1) {
+            shapes[p] = shape_for(g, it.K, false);
+            const Shape &sh = shapes[p];
+            sb = std::max(sb, sh.algo ? score2_ws_bytes(n, g->n_arcs, it.K, wt, bin_mode_of(sh.algo, wt),
+                                                        packs_labels(sh.algo, wt, n, it.K))
+                                      : score_ws_bytes(n, it.K));
+        }
+        if (it.flags & 2) cb = std::max(cb, compare_ws_bytes(n, it.kt, it.K));
+    }
+    const Shape csh = compare_shape();
+    const size_t q_b = al256((size_t)P * sizeof(qm_quality)), c_b = al256((size_t)P * sizeof(qm_compare));
+    const size_t st_b = al256((size_t)P * 2 * sizeof(int));
+    Lease ws(g_pool.acquire(al256(sb) + al256(cb) + q_b + c_b + st_b, dev, false));
+    Lease pin(g_pool.acquire(q_b + c_b + st_b, dev, true));
+    if (!ws.b || !pin.b) return fail(QM_ENOMEM, "batched scratch allocation failed");
+    char *S = ws.ptr(), *C = S + al256(sb), *R = C + al256(cb);
+    qm_quality *q_dev = (qm_quality *)R;
+    qm_compare *c_dev = (qm_compare *)(R + q_b);
+    int *st_dev = (int *)(R + q_b + c_b);
+    const int nsm = num_sms_of(dev);
+    cudaStream_t cs = capture_stream(dev);
+    if (!cs) return fail(QM_ECUDA, "no capture stream");
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    int L = 0;
+    bool ok = cudaMemsetAsync(st_dev, 0, st_b, cs) == cudaSuccess;
+    for (int p = 0; p < P && ok; ++p) {
+        const LargeItem &it = items[p];
+        if (it.flags & 1) {
+            const Shape &sh = shapes[p];
+            const ScoreWs w = sh.algo ? carve_score2_ws(S, n, g->n_arcs, it.K, wt, bin_mode_of(sh.algo, wt),
+                                                        packs_labels(sh.algo, wt, n, it.K))
+                                      : carve_score_ws(S, n, it.K);
+            ok = cudaMemsetAsync(S, 0, w.zero_bytes, cs) == cudaSuccess;
+            const int Li = !ok ? -1
+                         : sh.algo ? launch_score2(g->d, it.labels, it.K, w, sh, nullptr, nsm, cs, nullptr)
+                                   : launch_score(g->d, it.labels, it.K, w, sh, nullptr, nsm, cs, nullptr);
+            ok = Li >= 0 &&
+                 cudaMemcpyAsync(q_dev + p, w.result, sizeof(qm_quality), cudaMemcpyDeviceToDevice, cs) == cudaSuccess &&
+                 cudaMemcpyAsync(st_dev + 2 * p, w.status, sizeof(int), cudaMemcpyDeviceToDevice, cs) == cudaSuccess;
+            L += std::max(Li, 0);
+        }
+        if (ok && (it.flags & 2)) {
+            const CompareWs w = carve_compare_ws(C, n, it.kt, it.K);
+            ok = cudaMemsetAsync(C, 0, w.zero_bytes, cs) == cudaSuccess;
+            const int Li = ok ? launch_compare(it.truth, it.labels, n, it.kt, it.K, w, csh, nsm, cs, nullptr) : -1;
+            ok = Li >= 0 &&
+                 cudaMemcpyAsync(c_dev + p, w.result, sizeof(qm_compare), cudaMemcpyDeviceToDevice, cs) == cudaSuccess &&
+                 cudaMemcpyAsync(st_dev + 2 * p + 1, w.status, sizeof(int), cudaMemcpyDeviceToDevice, cs) == cudaSuccess;
+            L += std::max(Li, 0);
+        }
+    }
+    if (ok) ok = cudaMemcpyAsync(pin.ptr(), R, q_b + c_b + st_b, cudaMemcpyDeviceToHost, cs) == cudaSuccess;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess && ok) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess || !ok) {
+        if (exec) cudaGraphExecDestroy(exec);
+        return cuda_fail(e != cudaSuccess ? e : cudaErrorLaunchFailure, "batched capture of the plain pipelines");
+    }
+    TraceFn tr = trace_begin();
+    if (tr) tr("batched_plain", s);
+    e = cudaGraphLaunch(exec, s);
+    if (tr) tr(nullptr, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaGraphExecDestroy(exec);
+    if (e != cudaSuccess) return cuda_fail(e, "batched launch");
+    g_launches += L;
+    trace_collect();
+    const char *H = pin.ptr();
+    const int *st_h = (const int *)(H + q_b + c_b);
+    for (int p = 0; p < P; ++p)
+        for (int k = 0; k < 2; ++k) {
+            const int v = st_h[2 * p + k];
+            if (v & 1) return fail(QM_EINVAL, "item " + std::to_string(p) + ": a label lies outside its range");
+            if (v & 2) return fail(QM_EOVERFLOW, "item " + std::to_string(p) + ": a community borders too many communities");
+            if (v & 4) return fail(QM_ETIMEOUT, "item " + std::to_string(p) + ": a bounded device wait expired");
+            if (v) return fail(QM_ECUDA, "item " + std::to_string(p) + ": device status " + std::to_string(v));
+        }
+    for (int p = 0; p < P; ++p) {
+        if (out_q && (items[p].flags & 1)) out_q[p] = ((const qm_quality *)H)[p];
+        if (out_c && (items[p].flags & 2)) out_c[p] = ((const qm_compare *)(H + q_b))[p];
+    }
+    return QM_OK;
+}
+
 // Copies P label rows (and an optional truth) to the device when they are host memory.
 static qm_status stage_labels(int dev, const int32_t *labels, size_t n_labels, qm_mem where, cudaStream_t s,
                               Lease &lease, const int32_t **out)
@@ -1109,6 +1231,12 @@ static qm_status evaluate_batched(qm_graph *g, const int32_t *labels, int32_t P,
             dt = pl + (size_t)P * g->n;
         }
         g_launches += (flags & 2) ? 2 : 1;
+    }
+    if (g->n > kBatchBlockMaxN && !force) {  // one block per item would not fill the GPU: plain pipelines
+        std::vector<LargeItem> li(P);
+        for (int p = 0; p < P; ++p)
+            li[p] = LargeItem{dl + (size_t)p * g->n, K[p], (flags & 2) ? dt : nullptr, (flags & 2) ? kt : 0, flags};
+        return run_large_batched(g, g->device, g->n, li, out_q, out_c, s);
     }
     d.n_max = g->n;
     d.k_max = kmax;
@@ -1165,6 +1293,15 @@ qm_status qm_compare_partitions_batched(const int32_t *truth, const int32_t *fou
     if (st != QM_OK) return st;
     st = stage_labels(dev, truth, (size_t)(shared ? 1 : P) * n, where, s, tru, &dt);
     if (st != QM_OK) return st;
+    if (n > kBatchBlockMaxN) {  // one block per item would not fill the GPU: plain pipelines
+        std::vector<LargeItem> li(P);
+        for (int p = 0; p < P; ++p) {
+            const int kt = shared ? k_truth[0] : k_truth[p];
+            if (kt < 1 || k_found[p] < 1) return fail(QM_EINVAL, "label-id counts must be >= 1");
+            li[p] = LargeItem{df + (size_t)p * n, k_found[p], dt + (shared ? 0 : (size_t)p * n), kt, 2};
+        }
+        return run_large_batched(nullptr, dev, n, li, nullptr, out, s);
+    }
     BatchDesc d;
     d.n_max = n;
     d.items.resize(P);

@@ -143,3 +143,44 @@ def test_full_batch_against_oracle(qm, oracle_mod, workload):
     for p, (o_s, o_c) in enumerate(ref):
         check_quality(oq[p], o_s, f"{workload} candidate {p}")
         check_compare(oc[p], o_c, f"{workload} candidate {p}")
+
+
+def test_large_graph_batches_equal_plain(qm, oracle_mod):
+    """Above 2^21 nodes the batched calls run the plain pipelines of every item
+    in one captured launch: the same bits as the plain calls, for scoring,
+    evaluation against a shared truth, comparisons with shared and per-item
+    truths, host inputs and reordered graphs; an out-of-range label in one item
+    is reported for the whole call."""
+    from paper_1507_05492_gb300 import gen
+    g = gen.lfr_graph(gen.LfrParams(n=2_500_000, k_max=100, s_max=1000, seed=61), device="cuda")
+    plain = qm.Graph(g.row_ptr, g.col)
+    reord = qm.Graph(g.row_ptr, g.col, reorder=True)
+    labs, Ks = [], []
+    for p in range(5):
+        lab, K, _ = gen.candidate_partition(g.labels, seed=20_000 + p, k_range=(5_000, 20_000))
+        labs.append(lab)
+        Ks.append(K)
+    L = torch.stack(labs)
+    for graph in (plain, reord):
+        oq, oc = qm.evaluate_batched(graph, L, Ks, g.labels, g.K)
+        sq = qm.score_batched(graph, L, Ks)
+        for p in range(len(Ks)):
+            ref = qm.score(graph, L[p], Ks[p])
+            assert oq[p] == ref and sq[p] == ref, p
+            assert oc[p] == qm.compare(g.labels, L[p], g.K, Ks[p]), p
+        oq2, _ = qm.evaluate_batched(graph, L.cpu().numpy(), Ks, g.labels.cpu().numpy(), g.K)
+        assert oq2 == oq
+    shared = qm.compare_batched(g.labels, L, g.K, Ks, shared_truth=True)
+    per = qm.compare_batched(torch.roll(L, 1, 0).contiguous(), L, [Ks[-1]] + Ks[:-1], Ks, shared_truth=False)
+    for p in range(len(Ks)):
+        assert shared[p] == qm.compare(g.labels, L[p], g.K, Ks[p]), p
+        q = (p - 1) % len(Ks)
+        assert per[p] == qm.compare(L[q], L[p], Ks[q], Ks[p]), p
+    check_quality(oq[2], oracle_mod.score(g.row_ptr.cpu().numpy(), g.col.cpu().numpy(), L[2].cpu().numpy(), Ks[2]),
+                  "large batch item 2")
+    bad = L.clone()
+    bad[3, 17] = Ks[3]
+    with pytest.raises(qm.QmError) as e:
+        qm.score_batched(plain, bad, Ks)
+    assert e.value.status == qm.QM_EINVAL
+    assert qm.score_batched(plain, L, Ks)[0] == qm.score(plain, L[0], Ks[0])
