@@ -112,9 +112,14 @@ def _load():
     lib.oq_score_communities.argtypes = [p, p, i64, p, i32, p, i64, p, p]
     lib.oq_label_propagation.argtypes = [p, p, i64, i32, p, p]
     lib.oq_score_weighted.argtypes = [p, p, p, i64, p, i32, p]
+    lib.oq_validate_cover.argtypes = [p, p, i64, i32]
+    lib.oq_score_cover.argtypes = [p, p, i64, p, p, i32, p, p]
+    lib.oq_compare_cover.argtypes = [p, p, i32, p, p, i32, i64, p, p]
+    lib.oq_pairs_cover_bruteforce.argtypes = [p, p, p, p, i64, p]
     for f in (lib.oq_validate_graph, lib.oq_score, lib.oq_compare, lib.oq_pairs_bruteforce,
               lib.oq_compare_bruteforce, lib.oq_score_bruteforce, lib.oq_score_communities,
-              lib.oq_label_propagation, lib.oq_score_weighted):
+              lib.oq_label_propagation, lib.oq_score_weighted, lib.oq_validate_cover, lib.oq_score_cover,
+              lib.oq_compare_cover, lib.oq_pairs_cover_bruteforce):
         f.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -260,3 +265,63 @@ def label_propagation(row_ptr, col, rounds: int):
 def within(gpu: float, ref: float, cond: float = 0.0, rel: float = 1e-12) -> bool:
     """Tolerance rule: |g - o| <= rel * max(|o|, conditioning)."""
     return abs(gpu - ref) <= rel * max(abs(ref), abs(cond), 1e-300)
+
+
+# ------------------------------------------------------------------ covers (overlapping communities)
+
+def cover_from_lists(lists):
+    """(mptr int64[n+1], memb int32[...]) from one list of community ids per node
+    (each list sorted, without repeats)."""
+    mptr = np.zeros(len(lists) + 1, np.int64)
+    mptr[1:] = np.cumsum([len(x) for x in lists])
+    memb = np.array([c for x in lists for c in x], dtype=np.int32)
+    return mptr, memb
+
+
+def validate_cover(mptr, memb, K: int) -> bool:
+    mptr = _as(mptr, np.int64)
+    memb = _as(memb, np.int32) if len(memb) else np.zeros(1, np.int32)
+    return _load().oq_validate_cover(_ptr(mptr), _ptr(memb), len(mptr) - 1, int(K)) == 0
+
+
+def score_cover(row_ptr, col, mptr, memb, K: int) -> dict:
+    """Eqs. (8)-(9) and the six measures for a cover (the set formulas read
+    literally, see qm_oracle.c); cut_edges_total holds the sum over communities
+    of |E_c^out|."""
+    row_ptr = _as(row_ptr, np.int64)
+    col = _as(col, np.int32)
+    mptr = _as(mptr, np.int64)
+    memb = _as(memb, np.int32) if len(memb) else np.zeros(1, np.int32)
+    dbl = np.zeros(16, np.float64)
+    i64 = np.zeros(8, np.int64)
+    _check(_load().oq_score_cover(_ptr(row_ptr), _ptr(col), len(row_ptr) - 1, _ptr(mptr), _ptr(memb), int(K),
+                                  _ptr(dbl), _ptr(i64)), "score_cover")
+    out = {k: float(dbl[i]) for i, k in enumerate(SCORE_DBL)}
+    out.update({k: int(i64[i]) for i, k in enumerate(SCORE_I64)})
+    return out
+
+
+def compare_cover(aptr, amemb, ka: int, bptr, bmemb, kb: int) -> dict:
+    """Eqs. (1)-(7) for two covers (ground truth first)."""
+    aptr, bptr = _as(aptr, np.int64), _as(bptr, np.int64)
+    amemb = _as(amemb, np.int32) if len(amemb) else np.zeros(1, np.int32)
+    bmemb = _as(bmemb, np.int32) if len(bmemb) else np.zeros(1, np.int32)
+    assert len(aptr) == len(bptr)
+    dbl = np.zeros(16, np.float64)
+    i64 = np.zeros(16, np.int64)
+    _check(_load().oq_compare_cover(_ptr(aptr), _ptr(amemb), int(ka), _ptr(bptr), _ptr(bmemb), int(kb),
+                                    len(aptr) - 1, _ptr(dbl), _ptr(i64)), "compare_cover")
+    out = {k: float(dbl[i]) for i, k in enumerate(COMPARE_DBL)}
+    out.update({k: int(i64[i]) for i, k in enumerate(COMPARE_I64)})
+    return out
+
+
+def pairs_cover_bruteforce(aptr, amemb, bptr, bmemb) -> tuple[int, int, int, int]:
+    """(a11, a10, a01, a00) of two covers by visiting every node pair."""
+    aptr, bptr = _as(aptr, np.int64), _as(bptr, np.int64)
+    amemb = _as(amemb, np.int32) if len(amemb) else np.zeros(1, np.int32)
+    bmemb = _as(bmemb, np.int32) if len(bmemb) else np.zeros(1, np.int32)
+    out = np.zeros(4, np.int64)
+    _check(_load().oq_pairs_cover_bruteforce(_ptr(aptr), _ptr(amemb), _ptr(bptr), _ptr(bmemb), len(aptr) - 1,
+                                             _ptr(out)), "pairs_cover_bruteforce")
+    return tuple(int(x) for x in out)

@@ -1075,3 +1075,381 @@ int oq_score_omp(const int64_t *row_ptr, const int32_t *col, int64_t n, const in
     if (threads) *threads = T;
     return rc;
 }
+
+/* ------------------------------------------------------------------------
+ * Overlapping communities (covers).
+ *
+ * The paper defines its metrics for disjoint communities and names overlapping
+ * ones as future work (Sec. VI).  Every formula is written with node sets
+ * (|c|, |c n c'|, edges inside c, edges leaving c, edges between c_i and c_j),
+ * so a cover -- a family of node sets in which a node may belong to several
+ * communities or to none -- is scored here by reading each set formula
+ * literally:
+ *   |c|        the members of c;
+ *   |E_c^in|   edges with both ends in c;
+ *   |E_c^out|  edges with exactly one end in c;
+ *   |E_ci,cj|  edges {u, v} with u in c_i \ c_j and v in c_j \ c_i (an edge
+ *              that leaves c_i and enters c_j; symmetric in i and j);
+ *   |c n c'|   the nodes in both c and c' (one node can add to several cells);
+ *   a11 etc.   a pair of nodes is "in the same community" of a cover when the
+ *              two share at least one community.
+ * Q, Qds, the six measures and Eqs. (1)-(7) then follow their printed formulas
+ * unchanged.  For a cover in which every node has exactly one community every
+ * quantity equals the partition's.
+ *
+ * A cover is given node by node: the communities of node u are
+ * memb[mptr[u] .. mptr[u+1]), ids in [0, K), strictly increasing.
+ * ------------------------------------------------------------------------ */
+
+int oq_validate_cover(const int64_t *mptr, const int32_t *memb, int64_t n, int32_t K)
+{
+    if (n < 1 || K < 1 || mptr[0] != 0)
+        return OQ_EINVAL;
+    for (int64_t u = 0; u < n; u++) {
+        if (mptr[u + 1] < mptr[u])
+            return OQ_EINVAL;
+        for (int64_t k = mptr[u]; k < mptr[u + 1]; k++) {
+            if (memb[k] < 0 || memb[k] >= K)
+                return OQ_EINVAL;
+            if (k > mptr[u] && memb[k] <= memb[k - 1])
+                return OQ_EINVAL;
+        }
+    }
+    return OQ_OK;
+}
+
+/* is c among the sorted communities list[0 .. len) */
+static int in_list(const int32_t *list, int64_t len, int32_t c)
+{
+    for (int64_t k = 0; k < len; k++)
+        if (list[k] == c)
+            return 1;
+    return 0;
+}
+
+/*
+ * Eqs. (8)-(9) and the six measures of Sec. II-B.3 for a cover, in the layout
+ * of oq_score (dbl[0..9], i64[0..6]) except that i64[4] is the sum over
+ * communities of |E_c^out| (for a partition, twice the cut edges).  Every
+ * undirected edge is visited once (v > u) with its two communities lists A, B:
+ * it is inside each c in A n B, on the boundary of each c in A \ B and B \ A,
+ * and between every i in A \ B and j in B \ A.
+ */
+int oq_score_cover(const int64_t *row_ptr, const int32_t *col, int64_t n, const int64_t *mptr,
+                   const int32_t *memb, int32_t K, double *dbl, int64_t *i64)
+{
+    if (oq_validate_cover(mptr, memb, n, K) != OQ_OK)
+        return OQ_EINVAL;
+    const int64_t nnz = row_ptr[n];
+    if (nnz <= 0 || (nnz & 1))
+        return OQ_EINVAL;
+    const int64_t E = nnz / 2;
+    int64_t *size = (int64_t *)calloc((size_t)K, sizeof(int64_t));
+    int64_t *ein = (int64_t *)calloc((size_t)K, sizeof(int64_t));
+    int64_t *eout = (int64_t *)calloc((size_t)K, sizeof(int64_t));
+    long double *split = (long double *)calloc((size_t)K, sizeof(long double));
+    int64_t nkeys = 0, cap = 1024;
+    uint64_t *keys = (uint64_t *)malloc((size_t)cap * sizeof(uint64_t));
+    if (!size || !ein || !eout || !split || !keys) {
+        free(size); free(ein); free(eout); free(split); free(keys);
+        return OQ_ENOMEM;
+    }
+    int rc = OQ_OK;
+    for (int64_t u = 0; u < n; u++)
+        for (int64_t k = mptr[u]; k < mptr[u + 1]; k++)
+            size[memb[k]]++;
+    int64_t vol_check = 0;
+    for (int64_t u = 0; u < n && rc == OQ_OK; u++) {
+        const int32_t *A = memb + mptr[u];
+        const int64_t la = mptr[u + 1] - mptr[u];
+        vol_check += (row_ptr[u + 1] - row_ptr[u]) * la;
+        for (int64_t e = row_ptr[u]; e < row_ptr[u + 1] && rc == OQ_OK; e++) {
+            const int32_t v = col[e];
+            if (v <= u)
+                continue;
+            const int32_t *B = memb + mptr[v];
+            const int64_t lb = mptr[v + 1] - mptr[v];
+            for (int64_t x = 0; x < la; x++) {
+                if (in_list(B, lb, A[x])) ein[A[x]]++;
+                else eout[A[x]]++;
+            }
+            for (int64_t y = 0; y < lb; y++)
+                if (!in_list(A, la, B[y])) eout[B[y]]++;
+            for (int64_t x = 0; x < la; x++) {
+                if (in_list(B, lb, A[x])) continue;       /* i in A \ B */
+                for (int64_t y = 0; y < lb; y++) {
+                    if (in_list(A, la, B[y])) continue;   /* j in B \ A */
+                    if (nkeys == cap) {
+                        uint64_t *nk = (uint64_t *)realloc(keys, (size_t)cap * 2 * sizeof(uint64_t));
+                        if (!nk) { rc = OQ_ENOMEM; break; }
+                        keys = nk;
+                        cap *= 2;
+                    }
+                    const uint64_t a = (uint64_t)(A[x] < B[y] ? A[x] : B[y]);
+                    const uint64_t b = (uint64_t)(A[x] < B[y] ? B[y] : A[x]);
+                    keys[nkeys++] = (a << 32) | b;
+                }
+            }
+        }
+    }
+    /* identity: the volumes sum_c (2|E_c^in| + |E_c^out|) add up the degrees of all memberships */
+    int64_t s_in = 0, s_out = 0;
+    for (int32_t c = 0; c < K; c++) { s_in += ein[c]; s_out += eout[c]; }
+    if (rc == OQ_OK && 2 * s_in + s_out != vol_check)
+        rc = OQ_ECHECK;
+    qsort(keys, (size_t)nkeys, sizeof(uint64_t), cmp_u64);
+    int64_t npairs = 0, sq_check = 0;
+    for (int64_t s = 0; s < nkeys && rc == OQ_OK;) {
+        int64_t t = s;
+        while (t < nkeys && keys[t] == keys[s]) t++;
+        const int64_t cnt = t - s;
+        const int32_t ci = (int32_t)(keys[s] >> 32), cj = (int32_t)(keys[s] & 0xffffffffu);
+        npairs++;
+        sq_check += cnt * cnt;
+        /* Eq. (9): |E_ci,cj| / (2|E|) * |E_ci,cj| / (|ci||cj|), to both communities */
+        const long double eij = (long double)cnt;
+        const long double term = (eij / (2.0L * (long double)E)) * (eij / ((long double)size[ci] * (long double)size[cj]));
+        split[ci] += term;
+        split[cj] += term;
+        s = t;
+    }
+    if (rc == OQ_OK) {
+        oq_sum q = {0, 0}, qabs = {0, 0}, qds = {0, 0}, qdsabs = {0, 0};
+        oq_sum m_in = {0, 0}, m_dens = {0, 0}, m_contr = {0, 0}, m_out = {0, 0}, m_exp = {0, 0}, m_cond = {0, 0};
+        int64_t nonempty = 0;
+        const long double LE = (long double)E;
+        for (int32_t c = 0; c < K; c++) {
+            if (size[c] == 0) continue;
+            nonempty++;
+            const long double s = (long double)size[c], in = (long double)ein[c], out = (long double)eout[c];
+            const long double frac_in = in / LE, frac_vol = (2.0L * in + out) / (2.0L * LE);
+            sum_add(&q, frac_in - frac_vol * frac_vol);
+            sum_add(&qabs, fabsl(frac_in) + frac_vol * frac_vol);
+            const long double d = size[c] > 1 ? (2.0L * in) / (s * (s - 1.0L)) : 0.0L;
+            const long double t1 = in / LE * d, t2 = (2.0L * in + out) / (2.0L * LE) * d;
+            sum_add(&qds, t1 - t2 * t2 - split[c]);
+            sum_add(&qdsabs, fabsl(t1) + t2 * t2 + split[c]);
+            const long double vol = 2.0L * in + out;
+            sum_add(&m_in, in);
+            sum_add(&m_dens, d);
+            sum_add(&m_contr, 2.0L * in / s);
+            sum_add(&m_out, out);
+            sum_add(&m_exp, out / s);
+            sum_add(&m_cond, vol > 0 ? out / vol : 0.0L);
+        }
+        if (nonempty == 0) {
+            rc = OQ_EINVAL;  /* no community has a member */
+        } else {
+            const long double ne = (long double)nonempty;
+            dbl[0] = (double)sum_get(&q);
+            dbl[1] = (double)sum_get(&qds);
+            dbl[2] = (double)(sum_get(&m_in) / ne);
+            dbl[3] = (double)(sum_get(&m_dens) / ne);
+            dbl[4] = (double)(sum_get(&m_contr) / ne);
+            dbl[5] = (double)(sum_get(&m_out) / ne);
+            dbl[6] = (double)(sum_get(&m_exp) / ne);
+            dbl[7] = (double)(sum_get(&m_cond) / ne);
+            dbl[8] = (double)sum_get(&qabs);
+            dbl[9] = (double)sum_get(&qdsabs);
+            i64[0] = n;
+            i64[1] = E;
+            i64[2] = nonempty;
+            i64[3] = s_in;
+            i64[4] = s_out;
+            i64[5] = npairs;
+            i64[6] = sq_check;
+        }
+    }
+    free(size); free(ein); free(eout); free(split); free(keys);
+    return rc;
+}
+
+/* do two sorted lists share an element */
+static int lists_meet(const int32_t *a, int64_t la, const int32_t *b, int64_t lb)
+{
+    int64_t x = 0, y = 0;
+    while (x < la && y < lb) {
+        if (a[x] == b[y]) return 1;
+        if (a[x] < b[y]) x++; else y++;
+    }
+    return 0;
+}
+
+/*
+ * Eqs. (1)-(7) for two covers, C = (aptr, amemb, ka) the ground truth and
+ * C' = (bptr, bmemb, kb) the detected one, in the layout of oq_compare.  The
+ * cells |c n c'| come from every node's pairs (c, c') of its two lists, sorted
+ * and counted.  The pair counts follow their definition: a pair {i, j} is
+ * together in a cover when the two share a community; each pair sharing one
+ * in C is found once by walking, for every node i, the members j > i of its
+ * communities and marking j.
+ */
+int oq_compare_cover(const int64_t *aptr, const int32_t *amemb, int32_t ka, const int64_t *bptr,
+                     const int32_t *bmemb, int32_t kb, int64_t n, double *dbl, int64_t *i64)
+{
+    if (n < 2 || oq_validate_cover(aptr, amemb, n, ka) != OQ_OK || oq_validate_cover(bptr, bmemb, n, kb) != OQ_OK)
+        return OQ_EINVAL;
+    const int64_t ma = aptr[n], mb = bptr[n];
+    int64_t *na = (int64_t *)calloc((size_t)ka, sizeof(int64_t));
+    int64_t *nb = (int64_t *)calloc((size_t)kb, sizeof(int64_t));
+    int64_t *rowmax = (int64_t *)calloc((size_t)ka, sizeof(int64_t));
+    int64_t *colmax = (int64_t *)calloc((size_t)kb, sizeof(int64_t));
+    long double *rowbest = (long double *)calloc((size_t)ka, sizeof(long double));
+    int64_t ncell_cap = 0;
+    for (int64_t i = 0; i < n; i++) ncell_cap += (aptr[i + 1] - aptr[i]) * (bptr[i + 1] - bptr[i]);
+    uint64_t *keys = (uint64_t *)malloc((size_t)(ncell_cap > 0 ? ncell_cap : 1) * sizeof(uint64_t));
+    /* members of every community of both covers (transposes), and the pair marks */
+    int64_t *astart = (int64_t *)calloc((size_t)ka + 1, sizeof(int64_t));
+    int64_t *bstart = (int64_t *)calloc((size_t)kb + 1, sizeof(int64_t));
+    int32_t *amem = (int32_t *)malloc((size_t)(ma > 0 ? ma : 1) * sizeof(int32_t));
+    int32_t *bmem = (int32_t *)malloc((size_t)(mb > 0 ? mb : 1) * sizeof(int32_t));
+    int64_t *mark = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    if (!na || !nb || !rowmax || !colmax || !rowbest || !keys || !astart || !bstart || !amem || !bmem || !mark) {
+        free(na); free(nb); free(rowmax); free(colmax); free(rowbest); free(keys);
+        free(astart); free(bstart); free(amem); free(bmem); free(mark);
+        return OQ_ENOMEM;
+    }
+    int64_t nk = 0;
+    for (int64_t i = 0; i < n; i++) {
+        for (int64_t x = aptr[i]; x < aptr[i + 1]; x++) na[amemb[x]]++;
+        for (int64_t y = bptr[i]; y < bptr[i + 1]; y++) nb[bmemb[y]]++;
+        for (int64_t x = aptr[i]; x < aptr[i + 1]; x++)
+            for (int64_t y = bptr[i]; y < bptr[i + 1]; y++)
+                keys[nk++] = ((uint64_t)(uint32_t)amemb[x] << 32) | (uint64_t)(uint32_t)bmemb[y];
+    }
+    qsort(keys, (size_t)nk, sizeof(uint64_t), cmp_u64);
+    const long double N = (long double)n;
+    oq_sum vi = {0, 0}, viabs = {0, 0}, num = {0, 0}, numabs = {0, 0}, den = {0, 0};
+    int64_t ncells = 0;
+    for (int64_t s = 0; s < nk;) {
+        int64_t t = s;
+        while (t < nk && keys[t] == keys[s]) t++;
+        const int64_t cnt = t - s;
+        const int32_t ca = (int32_t)(keys[s] >> 32), cb = (int32_t)(keys[s] & 0xffffffffu);
+        ncells++;
+        const long double x = (long double)cnt, sa = (long double)na[ca], sb = (long double)nb[cb];
+        const long double tv = x * logl(x * x / (sa * sb));          /* Eq. (1) term */
+        sum_add(&vi, tv);
+        sum_add(&viabs, fabsl(tv));
+        const long double tn = x / N * logl(x * N / (sa * sb));       /* Eq. (2) numerator term */
+        sum_add(&num, tn);
+        sum_add(&numabs, fabsl(tn));
+        const long double r = 2.0L * x / (sa + sb);                  /* Eq. (3) */
+        if (r > rowbest[ca]) rowbest[ca] = r;
+        if (cnt > rowmax[ca]) rowmax[ca] = cnt;                       /* Eq. (4) */
+        if (cnt > colmax[cb]) colmax[cb] = cnt;
+        s = t;
+    }
+    int64_t nvdsum = 0, kan = 0, kbn = 0;
+    oq_sum f = {0, 0};
+    for (int32_t c = 0; c < ka; c++) {
+        if (na[c] == 0) continue;
+        kan++;
+        const long double p = (long double)na[c] / N;
+        sum_add(&den, p * logl(p));
+        nvdsum += rowmax[c];
+        sum_add(&f, (long double)na[c] * rowbest[c]);
+    }
+    for (int32_t c = 0; c < kb; c++) {
+        if (nb[c] == 0) continue;
+        kbn++;
+        const long double p = (long double)nb[c] / N;
+        sum_add(&den, p * logl(p));
+        nvdsum += colmax[c];
+    }
+    /* transposes */
+    for (int32_t c = 0; c < ka; c++) astart[c + 1] = astart[c] + na[c];
+    for (int32_t c = 0; c < kb; c++) bstart[c + 1] = bstart[c] + nb[c];
+    {
+        int64_t *fa = (int64_t *)malloc((size_t)ka * sizeof(int64_t)), *fb = (int64_t *)malloc((size_t)kb * sizeof(int64_t));
+        if (!fa || !fb) {
+            free(fa); free(fb);
+            free(na); free(nb); free(rowmax); free(colmax); free(rowbest); free(keys);
+            free(astart); free(bstart); free(amem); free(bmem); free(mark);
+            return OQ_ENOMEM;
+        }
+        memcpy(fa, astart, (size_t)ka * sizeof(int64_t));
+        memcpy(fb, bstart, (size_t)kb * sizeof(int64_t));
+        for (int64_t i = 0; i < n; i++) {
+            for (int64_t x = aptr[i]; x < aptr[i + 1]; x++) amem[fa[amemb[x]]++] = (int32_t)i;
+            for (int64_t y = bptr[i]; y < bptr[i + 1]; y++) bmem[fb[bmemb[y]]++] = (int32_t)i;
+        }
+        free(fa); free(fb);
+    }
+    /* pairs together in C (a11 when also together in C'), then pairs together in C' */
+    int64_t sameA = 0, sameB = 0, a11 = 0;
+    for (int64_t i = 0; i < n; i++) mark[i] = -1;
+    for (int64_t i = 0; i < n; i++)
+        for (int64_t x = aptr[i]; x < aptr[i + 1]; x++) {
+            const int32_t c = amemb[x];
+            for (int64_t p = astart[c]; p < astart[c + 1]; p++) {
+                const int64_t j = amem[p];
+                if (j <= i || mark[j] == i) continue;
+                mark[j] = i;
+                sameA++;
+                if (lists_meet(bmemb + bptr[i], bptr[i + 1] - bptr[i], bmemb + bptr[j], bptr[j + 1] - bptr[j]))
+                    a11++;
+            }
+        }
+    for (int64_t i = 0; i < n; i++) mark[i] = -1;
+    for (int64_t i = 0; i < n; i++)
+        for (int64_t y = bptr[i]; y < bptr[i + 1]; y++) {
+            const int32_t c = bmemb[y];
+            for (int64_t p = bstart[c]; p < bstart[c + 1]; p++) {
+                const int64_t j = bmem[p];
+                if (j <= i || mark[j] == i) continue;
+                mark[j] = i;
+                sameB++;
+            }
+        }
+    const int64_t A = n * (n - 1) / 2;
+    const int64_t a10 = sameA - a11, a01 = sameB - a11, a00 = A - a11 - a10 - a01;
+    int rc = (a10 < 0 || a01 < 0 || a00 < 0) ? OQ_ECHECK : OQ_OK;
+    if (rc == OQ_OK) {
+        const long double LA = (long double)A;
+        const long double l11 = (long double)a11, l10 = (long double)a10, l01 = (long double)a01, l00 = (long double)a00;
+        dbl[0] = (double)(-sum_get(&vi) / N);
+        const long double dd = sum_get(&den);
+        dbl[1] = dd != 0.0L ? (double)(-2.0L * sum_get(&num) / dd) : 1.0;
+        dbl[2] = (double)(sum_get(&f) / N);
+        dbl[3] = (double)(1.0L - (long double)nvdsum / (2.0L * N));
+        dbl[4] = (double)((l11 + l00) / LA);
+        const long double M = (l11 + l10) * (l11 + l01) / LA;  /* Eq. (6) */
+        const long double ari_den = 0.5L * ((l11 + l10) + (l11 + l01)) - M;
+        dbl[5] = ari_den != 0.0L ? (double)((l11 - M) / ari_den) : 1.0;
+        const long double ji_den = l11 + l10 + l01;
+        dbl[6] = ji_den != 0.0L ? (double)(l11 / ji_den) : 1.0;
+        dbl[7] = (double)(sum_get(&viabs) / N);
+        dbl[8] = (double)(2.0L * sum_get(&numabs));
+        dbl[9] = (double)fabsl(dd);
+        i64[0] = n; i64[1] = kan; i64[2] = kbn; i64[3] = ncells;
+        i64[4] = a11; i64[5] = a10; i64[6] = a01; i64[7] = a00; i64[8] = nvdsum;
+    }
+    free(na); free(nb); free(rowmax); free(colmax); free(rowbest); free(keys);
+    free(astart); free(bstart); free(amem); free(bmem); free(mark);
+    return rc;
+}
+
+/*
+ * Pair counts of two covers by visiting every node pair i < j (O(|V|^2),
+ * tiny inputs only): together in a cover = the two lists share an id.
+ * out[0..3] = a11, a10, a01, a00.
+ */
+int oq_pairs_cover_bruteforce(const int64_t *aptr, const int32_t *amemb, const int64_t *bptr,
+                              const int32_t *bmemb, int64_t n, int64_t *out)
+{
+    if (n < 2)
+        return OQ_EINVAL;
+    int64_t a11 = 0, a10 = 0, a01 = 0, a00 = 0;
+    for (int64_t i = 0; i < n; i++)
+        for (int64_t j = i + 1; j < n; j++) {
+            const int sa = lists_meet(amemb + aptr[i], aptr[i + 1] - aptr[i], amemb + aptr[j], aptr[j + 1] - aptr[j]);
+            const int sb = lists_meet(bmemb + bptr[i], bptr[i + 1] - bptr[i], bmemb + bptr[j], bptr[j + 1] - bptr[j]);
+            if (sa && sb) a11++;
+            else if (sa) a10++;
+            else if (sb) a01++;
+            else a00++;
+        }
+    out[0] = a11; out[1] = a10; out[2] = a01; out[3] = a00;
+    return OQ_OK;
+}
