@@ -209,6 +209,50 @@ qm_status qm_compare_partitions(const int32_t *truth, const int32_t *found, int6
                                 qm_compare *out, void *stream);
 
 /*
+ * Overlapping communities (covers).  The paper defines its metrics for
+ * disjoint communities and leaves overlapping ones to future work (Sec. VI);
+ * every formula is written with node sets, and a cover -- a family of node
+ * sets in which a node may belong to several communities or to none -- is
+ * scored by reading them literally:
+ *   |c|          the members of c;
+ *   |E_c^in|     edges with both ends in c;
+ *   |E_c^out|    edges with exactly one end in c;
+ *   |E_ci,cj|    edges {u, v} with u in c_i \ c_j and v in c_j \ c_i;
+ *   |c n c'|     nodes in both c and c' (one node may add to several cells);
+ *   a11 .. a00   a pair of nodes is together in a cover when the two share a
+ *                community.
+ * Q, Qds, the six measures and Eqs. (1)-(7) then follow their printed formulas
+ * (VI may be negative and F above 1 on covers).  For a cover with exactly one
+ * community per node every result equals the partition call's, bit for bit,
+ * except cut_edges_total (below).
+ *
+ * A cover is given node by node: the communities of node u are
+ * memb[mptr[u] .. mptr[u+1]), strictly increasing ids in [0, K); mptr is
+ * int64[n_nodes + 1] with mptr[0] = 0, memb int32[mptr[n_nodes]] (fewer than
+ * 2^31 memberships).  Both arrays live where `where` says.
+ *
+ * qm_score_cover -- Eqs. (8)-(9) and the Sec. II-B.3 measures of a cover on a
+ * loaded graph (any node order; the lists are in the caller's node order).
+ * out->cut_edges_total holds the sum over communities of |E_c^out| (an edge
+ * may leave several communities; for a partition it is twice the cut edges).
+ * Errors: QM_EINVAL (malformed lists, no non-empty community, weighted graph),
+ * QM_EOVERFLOW, QM_ENOMEM, QM_ECUDA.
+ */
+qm_status qm_score_cover(const qm_graph *g, const int64_t *mptr, const int32_t *memb, int32_t K,
+                         qm_mem where, qm_quality *out, void *stream);
+
+/*
+ * qm_compare_covers -- Eqs. (1)-(7) for two covers of the same n_nodes nodes,
+ * truth C = (truth_ptr, truth_memb, k_truth) and detected C' = (found_ptr,
+ * found_memb, k_found).  The pair counts follow their definition (pairs
+ * sharing a community); the cost beyond the cells grows with the pairs of
+ * nodes that both have two or more memberships within one community.
+ */
+qm_status qm_compare_covers(const int64_t *truth_ptr, const int32_t *truth_memb, int32_t k_truth,
+                            const int64_t *found_ptr, const int32_t *found_memb, int32_t k_found,
+                            int64_t n_nodes, qm_mem where, qm_compare *out, void *stream);
+
+/*
  * Batched calls.  On graphs of up to 2^21 nodes the items run in one
  * persistent kernel, one block per item, replayed from a captured CUDA graph.
  * On larger graphs one block per item would not fill the GPU, so every item

@@ -21,7 +21,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libqm.so")
-SOURCES = ["qm_kernels.cu", "qm_batched.cu", "qm_api.cu", "qm_noalloc.cu", "qm_reorder.cu"]
+SOURCES = ["qm_kernels.cu", "qm_batched.cu", "qm_api.cu", "qm_noalloc.cu", "qm_reorder.cu", "qm_cover.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "--fmad=false", "-std=c++17", "-Xcompiler", "-fPIC",
                 "-Xcompiler", "-O2", "--expt-relaxed-constexpr"]

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "qm_internal.h"
+#include "qm_cover.h"
 
 using namespace qm;
 
@@ -126,6 +127,7 @@ static int num_sms_of(int dev)
     if (prev != dev) cudaSetDevice(dev);
     prepare_kernels();
     prepare_batched_kernel();
+    prepare_cover_kernels();
     if (prev != dev) cudaSetDevice(prev);
     int v = 0;
     cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
@@ -1395,6 +1397,117 @@ qm_status qm_release_cache(void)
     g_graphs.clear();
     for (auto &kv : g_plain_graphs) cudaGraphExecDestroy(kv.second.exec);
     g_plain_graphs.clear();
+    return QM_OK;
+}
+
+// ------------------------------------------------------------------ covers (overlapping communities)
+
+// Device copies of a cover's arrays (host arrays are staged; device ones are
+// used as they are) and its membership count m = mptr[n].
+static qm_status stage_cover(int dev, const int64_t *mptr, const int32_t *memb, long long n, qm_mem where,
+                             cudaStream_t s, Lease &lease, const long long **dptr, const int **dmemb, long long *m)
+{
+    if (where == QM_HOST) {
+        *m = mptr[n];
+    } else {
+        long long v = 0;
+        CK(cudaMemcpyAsync(&v, mptr + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        *m = v;
+    }
+    if (*m < 0 || *m >= (1LL << 31)) return fail(QM_EOVERFLOW, "a cover must hold fewer than 2^31 memberships");
+    if (where == QM_DEVICE) {
+        *dptr = (const long long *)mptr;
+        *dmemb = memb;
+        return QM_OK;
+    }
+    const size_t pb = al256(((size_t)n + 1) * 8), mbytes = al256((size_t)std::max(*m, 1LL) * 4);
+    lease.b = g_pool.acquire(pb + mbytes, dev, false);
+    if (!lease.b) return fail(QM_ENOMEM, "cover staging allocation failed");
+    CK(cudaMemcpyAsync(lease.ptr(), mptr, ((size_t)n + 1) * 8, cudaMemcpyHostToDevice, s));
+    if (*m > 0) CK(cudaMemcpyAsync(lease.ptr() + pb, memb, (size_t)*m * 4, cudaMemcpyHostToDevice, s));
+    *dptr = (const long long *)lease.ptr();
+    *dmemb = (const int *)(lease.ptr() + pb);
+    return QM_OK;
+}
+
+static qm_status cover_status(int st)
+{
+    if (st & 1) return fail(QM_EINVAL, "a cover's offsets or lists are malformed (lists must be strictly increasing ids in [0, K))");
+    if (st & 2) return fail(QM_EOVERFLOW, "a community borders too many distinct communities");
+    if (st) return fail(QM_ECUDA, "device status " + std::to_string(st));
+    return QM_OK;
+}
+
+qm_status qm_score_cover(const qm_graph *gc, const int64_t *mptr, const int32_t *memb, int32_t K, qm_mem where,
+                         qm_quality *out, void *stream)
+{
+    qm_graph *g = const_cast<qm_graph *>(gc);
+    if (!g || !mptr || !out || (!memb && where == QM_DEVICE)) return fail(QM_EINVAL, "null argument");
+    if (K < 1) return fail(QM_EINVAL, "K must be >= 1");
+    if (where != QM_HOST && where != QM_DEVICE) return fail(QM_EINVAL, "bad memory kind");
+    if (g->wt) return fail(QM_EINVAL, "weighted graphs are scored by qm_score_partition and the sharded calls");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    Lease stage;
+    const long long *dptr = nullptr;
+    const int *dmemb = nullptr;
+    long long m = 0;
+    qm_status st = stage_cover(g->device, mptr, memb, g->n, where, s, stage, &dptr, &dmemb, &m);
+    if (st != QM_OK) return st;
+    Lease ws(g_pool.acquire(cover_score_ws_bytes(g->n, m, K), g->device, false));
+    Lease pin(g_pool.acquire(512, g->device, true));
+    if (!ws.b || !pin.b) return fail(QM_ENOMEM, "scratch allocation failed");
+    const CoverWs w = carve_cover_score_ws(ws.ptr(), g->n, m, K);
+    CK(cudaMemsetAsync(ws.ptr(), 0, w.zero_bytes, s));
+    const int L = launch_cover_score(g->d, dptr, dmemb, m, K, w, num_sms_of(g->device), s);
+    if (L < 0) return cuda_fail(cudaGetLastError(), "launch_cover_score");
+    g_launches += L;
+    CK(cudaMemcpyAsync(pin.ptr(), w.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(pin.ptr() + 256, w.result, sizeof(qm_quality), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    st = cover_status(*(int *)pin.ptr());
+    if (st != QM_OK) return st;
+    const qm_quality *q = (const qm_quality *)(pin.ptr() + 256);
+    if (q->n_communities_nonempty == 0) return fail(QM_EINVAL, "no community of the cover has a member");
+    std::memcpy(out, q, sizeof(qm_quality));
+    return QM_OK;
+}
+
+qm_status qm_compare_covers(const int64_t *truth_ptr, const int32_t *truth_memb, int32_t k_truth,
+                            const int64_t *found_ptr, const int32_t *found_memb, int32_t k_found, int64_t n,
+                            qm_mem where, qm_compare *out, void *stream)
+{
+    if (!truth_ptr || !found_ptr || !out) return fail(QM_EINVAL, "null argument");
+    if (n < 2) return fail(QM_EINVAL, "n_nodes must be >= 2 (no node pairs otherwise)");
+    if (n >= (1LL << 31)) return fail(QM_EOVERFLOW, "n_nodes must be < 2^31");
+    if (k_truth < 1 || k_found < 1) return fail(QM_EINVAL, "k_truth and k_found must be >= 1");
+    if (where != QM_HOST && where != QM_DEVICE) return fail(QM_EINVAL, "bad memory kind");
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    cudaStream_t s = (cudaStream_t)stream;
+    Lease sa, sb;
+    const long long *ap = nullptr, *bp = nullptr;
+    const int *am = nullptr, *bm = nullptr;
+    long long ma = 0, mb = 0;
+    qm_status st = stage_cover(dev, truth_ptr, truth_memb, n, where, s, sa, &ap, &am, &ma);
+    if (st != QM_OK) return st;
+    st = stage_cover(dev, found_ptr, found_memb, n, where, s, sb, &bp, &bm, &mb);
+    if (st != QM_OK) return st;
+    Lease ws(g_pool.acquire(cover_compare_ws_bytes(n, ma, k_truth, mb, k_found), dev, false));
+    Lease pin(g_pool.acquire(512, dev, true));
+    if (!ws.b || !pin.b) return fail(QM_ENOMEM, "scratch allocation failed");
+    const CoverWs w = carve_cover_compare_ws(ws.ptr(), n, ma, k_truth, mb, k_found);
+    CK(cudaMemsetAsync(ws.ptr(), 0, w.zero_bytes, s));
+    const int L = launch_cover_compare(ap, am, ma, k_truth, bp, bm, mb, k_found, n, w, num_sms_of(dev), s);
+    if (L < 0) return cuda_fail(cudaGetLastError(), "launch_cover_compare");
+    g_launches += L;
+    CK(cudaMemcpyAsync(pin.ptr(), w.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(pin.ptr() + 256, w.result, sizeof(qm_compare), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    st = cover_status(*(int *)pin.ptr());
+    if (st != QM_OK) return st;
+    std::memcpy(out, pin.ptr() + 256, sizeof(qm_compare));
     return QM_OK;
 }
 

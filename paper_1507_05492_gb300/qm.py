@@ -97,6 +97,8 @@ def _signatures(lib):
         "qm_workspace_bytes": [_P, _I32, _I32, _I32, _P],
         "qm_release_cache": [],
         "qm_debug_set_stage_wait": [_I64],
+        "qm_score_cover": [_P, _P, _P, _I32, S, _P, _P],
+        "qm_compare_covers": [_P, _P, _I32, _P, _P, _I32, _I64, S, _P, _P],
         "qm_autotune": [_P, _P, _I32, S, _P, _P],
         "qm_get_tuning": [_P, _I32, _P],
         "qm_set_tuning": [_P, _I32, _P],
@@ -173,6 +175,30 @@ def _labels_arg(x, name="labels"):
         return x.data_ptr(), (QM_DEVICE if x.is_cuda else QM_HOST), x
     a = np.ascontiguousarray(np.asarray(x), dtype=np.int32)
     return a.ctypes.data, QM_HOST, a
+
+
+def _cover_arg(cover, n, where_name):
+    """(mptr pointer, memb pointer, memory kind, keep-alive, m) of a cover given
+    as (mptr int64[n + 1], memb int32[m]), both torch tensors on one device or
+    both host arrays.  The lengths are checked here (the C ABI cannot see them)."""
+    mptr, memb = cover
+    if isinstance(mptr, torch.Tensor) or isinstance(memb, torch.Tensor):
+        _need(isinstance(mptr, torch.Tensor) and isinstance(memb, torch.Tensor) and mptr.device == memb.device,
+              where_name, "mptr and memb must both be tensors on one device, or both host arrays")
+        _need(mptr.dtype == torch.int64 and memb.dtype == torch.int32 and mptr.is_contiguous() and
+              memb.is_contiguous(), where_name, "mptr must be contiguous int64 and memb contiguous int32")
+        _need(tuple(mptr.shape) == (n + 1,), where_name, f"mptr of shape {tuple(mptr.shape)} for {n} nodes")
+        m = int(mptr[-1].item())
+        _need(memb.dim() == 1 and memb.numel() >= m, where_name, f"memb holds {memb.numel()} ids, mptr[n] = {m}")
+        return mptr.data_ptr(), memb.data_ptr(), (QM_DEVICE if mptr.is_cuda else QM_HOST), (mptr, memb), m
+    mp = np.ascontiguousarray(np.asarray(mptr), dtype=np.int64)
+    mb = np.ascontiguousarray(np.asarray(memb), dtype=np.int32)
+    _need(mp.shape == (n + 1,), where_name, f"mptr of shape {mp.shape} for {n} nodes")
+    m = int(mp[-1]) if n >= 0 else 0
+    _need(mb.ndim == 1 and mb.size >= m, where_name, f"memb holds {mb.size} ids, mptr[n] = {m}")
+    if mb.size == 0:
+        mb = np.zeros(1, np.int32)
+    return mp.ctypes.data, mb.ctypes.data, QM_HOST, (mp, mb), m
 
 
 def _shape(x) -> tuple:
@@ -294,6 +320,33 @@ def score(graph: Graph, labels, K: int, per_community: bool = False, stream=None
     if arrays is not None:
         d["per_community"] = arrays
     return d
+
+
+def score_cover(graph: "Graph", cover, K: int, stream=None) -> dict:
+    """qm_score_cover: Q, Qds and the six measures of a cover (overlapping
+    communities): cover = (mptr int64[n + 1], memb int32[m]), the communities of
+    node u being memb[mptr[u]:mptr[u + 1]] in increasing order.  The field
+    cut_edges_total holds the sum over communities of |E_c^out|."""
+    mp, mb, where, keep, _ = _cover_arg(cover, graph.n, "qm_score_cover")
+    out = QmQuality()
+    rc = lib().qm_score_cover(graph.handle, mp, mb, int(K), where, ctypes.byref(out), _stream_ptr(stream))
+    del keep
+    _check(rc, "qm_score_cover")
+    return _struct_dict(out)
+
+
+def compare_covers(truth, k_truth: int, found, k_found: int, n: int, stream=None) -> dict:
+    """qm_compare_covers: Eqs. (1)-(7) for two covers of n nodes, each given as
+    (mptr, memb) like score_cover; truth first."""
+    ap, am, wa, ka_keep, _ = _cover_arg(truth, n, "qm_compare_covers")
+    bp, bm, wb, kb_keep, _ = _cover_arg(found, n, "qm_compare_covers")
+    _need(wa == wb, "qm_compare_covers", "both covers must be in the same kind of memory")
+    out = QmCompare()
+    rc = lib().qm_compare_covers(ap, am, int(k_truth), bp, bm, int(k_found), int(n), wa, ctypes.byref(out),
+                                 _stream_ptr(stream))
+    del ka_keep, kb_keep
+    _check(rc, "qm_compare_covers")
+    return _struct_dict(out)
 
 
 def compare(truth, found, k_truth: int, k_found: int, stream=None) -> dict:
