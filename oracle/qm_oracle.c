@@ -20,6 +20,11 @@
  *   Sec. II-B.3  six per-community measures        -> oq_score
  *   weighted graphs (the note beside Eq. 9)        -> oq_score_weighted
  *   label propagation (the detector family of Sec. I, IV-C) -> oq_label_propagation
+ *   overlapping communities (covers; the paper's future work, Sec. VI),
+ *   the set formulas read literally -> oq_score_cover, oq_compare_cover,
+ *                oq_pairs_cover_bruteforce
+ *   the same quantities as oq_score with OpenMP threads (all-core CPU
+ *   baseline)                                        -> oq_score_omp
  *
  * Readings taken where the paper is silent:
  *   - log is the natural log (Eq. 1);
