@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "qm_internal.h"
+#include "qm_batched.h"
 #include "qm_cover.h"
 
 using namespace qm;
@@ -237,10 +238,12 @@ struct GraphKey {
     int count, slots, threads, smem, big;
     long long n_max;
     int k_max, kt_max;
+    long long extra = 0;  // two-phase batched graphs: node count of the log table
     bool operator<(const GraphKey &o) const
     {
-        return std::tie(dev, pin, count, slots, threads, smem, big, n_max, k_max, kt_max) <
-               std::tie(o.dev, o.pin, o.count, o.slots, o.threads, o.smem, o.big, o.n_max, o.k_max, o.kt_max);
+        return std::tie(dev, pin, count, slots, threads, smem, big, n_max, k_max, kt_max, extra) <
+               std::tie(o.dev, o.pin, o.count, o.slots, o.threads, o.smem, o.big, o.n_max, o.k_max, o.kt_max,
+                        o.extra);
     }
 };
 
@@ -411,6 +414,21 @@ static Shape resolve_batched(Shape s)
     auto key = std::make_tuple(s.threads, s.smem_bytes);
     auto it = occ.find(key);
     if (it == occ.end()) it = occ.emplace(key, std::max(1, batched_blocks_per_sm(s))).first;
+    s.blocks_per_sm = it->second;
+    return s;
+}
+
+static Shape resolve_batch_units(Shape s)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    num_sms_of(dev);
+    static std::mutex mu;
+    static std::map<std::tuple<int, int>, int> occ;
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_tuple(s.threads, s.smem_bytes);
+    auto it = occ.find(key);
+    if (it == occ.end()) it = occ.emplace(key, std::max(1, batch_units_blocks_per_sm(s))).first;
     s.blocks_per_sm = it->second;
     return s;
 }
@@ -972,13 +990,145 @@ struct BatchDesc {
     std::vector<BatchItem> items;   // device pointers filled except outputs/status
     long long n_max = 0;
     int k_max = 1, kt_max = 1;
-    bool any_score = false, any_cmp = false;
 };
 
-// Runs the persistent kernel over `d.items`.  Labels must already be on the device.
+// Runs the two-phase batched pipeline (qm_batched.h) over `d.items`, in waves
+// that keep the scratch within a quarter of free memory and the unit counts
+// within int range.  Labels must already be on the device and every item's arc
+// count at most BATCH_UNITS_MAX_ARCS.
+static qm_status run_batched_units(int dev, BatchDesc &d, const Shape &sh0, qm_quality *out_q, qm_compare *out_c,
+                                   cudaStream_t s)
+{
+    const int count = (int)d.items.size();
+    const int num_sms = num_sms_of(dev);
+    Shape sh = resolve_batch_units(sh0);
+    long long a_max = 1;
+    bool cells = false;
+    for (const BatchItem &it : d.items) {
+        a_max = std::max(a_max, it.n_arcs);
+        cells |= (it.flags & 2) && it.truth;
+    }
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    auto scratch = [&](int per) { return batch_units_bytes(per, d.n_max, a_max, d.k_max, d.kt_max, cells); };
+    int per = count;
+    while (per > 1 && ((long long)per * std::max<long long>(d.k_max, (d.n_max + 31) / 32) >= (1LL << 30) ||
+                       scratch(per) > free_b / 4))
+        per = (per + 1) / 2;
+    const int waves = (count + per - 1) / per;
+    const size_t items_b = al256((size_t)count * sizeof(BatchItem));
+    const size_t q_b = al256((size_t)count * sizeof(qm_quality));
+    const size_t c_b = al256((size_t)count * sizeof(qm_compare));
+    const size_t st_b = al256((size_t)count * sizeof(int) + 256);
+    const size_t pre_b = al256((size_t)(count + waves) * 3 * sizeof(int));
+    const size_t scratch_b = scratch(per);
+    Lease ws(g_pool.acquire(items_b + q_b + c_b + st_b + scratch_b, dev, false));
+    Lease pin(g_pool.acquire(items_b + q_b + c_b + st_b + pre_b, dev, true));
+    if (!ws.b || !pin.b) return fail(QM_ENOMEM, "batched scratch allocation failed");
+    char *D = ws.ptr(), *H = pin.ptr();
+    BatchItem *items_dev = (BatchItem *)D;
+    qm_quality *q_dev = (qm_quality *)(D + items_b);
+    qm_compare *c_dev = (qm_compare *)(D + items_b + q_b);
+    int *st_dev = (int *)(D + items_b + q_b + c_b);
+    BatchUnits bu = carve_batch_units(D + items_b + q_b + c_b + st_b, per, d.n_max, a_max, d.k_max, d.kt_max, cells);
+    BatchItem *items_h = (BatchItem *)H;
+    int *pre_h = (int *)(H + items_b + q_b + c_b + st_b);  // per wave: tpre, cpre, kpre (w1 - w0 + 1 each)
+    for (int i = 0; i < count; ++i) {
+        items_h[i] = d.items[i];
+        items_h[i].out_q = q_dev + i;
+        items_h[i].out_c = c_dev + i;
+        items_h[i].status = st_dev + i;
+    }
+    for (int w = 0; w < waves; ++w) {
+        const int w0 = w * per, w1 = std::min(count, w0 + per), m = w1 - w0;
+        int *tp = pre_h + 3 * (w0 + w), *cp = tp + m + 1, *kp = cp + m + 1;
+        tp[0] = cp[0] = kp[0] = 0;
+        for (int i = 0; i < m; ++i) {
+            const long long n = d.items[w0 + i].n;
+            tp[i + 1] = tp[i] + (int)((n + BATCH_UNITS_TILE - 1) / BATCH_UNITS_TILE);
+            cp[i + 1] = cp[i] + (int)((n + 31) / 32);
+            kp[i + 1] = kp[i] + d.items[w0 + i].K;
+        }
+    }
+    const long long logt_n = count ? d.items[0].n : 0;
+    // key: the leases, the wave size, the item bounds and the log table's node
+    // count fix everything the graph holds (prefixes and items are copied in at
+    // launch)
+    GraphKey key{D, H, count, -(2 * per + (cells ? 1 : 0)), sh.threads, sh.smem_bytes, (int)a_max, d.n_max,
+                 d.k_max, d.kt_max, logt_n};
+    cudaGraphExec_t exec = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        auto it = g_graphs.find(key);
+        if (it != g_graphs.end()) exec = it->second;
+    }
+    int L = 0;
+    if (!exec) {
+        cudaStream_t cs = capture_stream(dev);
+        if (!cs) return fail(QM_ECUDA, "no capture stream");
+        CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        cudaMemcpyAsync(items_dev, items_h, (size_t)count * sizeof(BatchItem), cudaMemcpyHostToDevice, cs);
+        cudaMemsetAsync(st_dev, 0, (size_t)count * sizeof(int), cs);
+        launch_batch_logt(bu.logt, logt_n, cs);
+        L = 1;
+        for (int w = 0; w < waves && L >= 0; ++w) {
+            const int w0 = w * per, w1 = std::min(count, w0 + per), m = w1 - w0;
+            const int *tp = pre_h + 3 * (w0 + w);
+            cudaMemcpyAsync(bu.tpre, tp, (size_t)(m + 1) * sizeof(int), cudaMemcpyHostToDevice, cs);
+            cudaMemcpyAsync(bu.cpre, tp + m + 1, (size_t)(m + 1) * sizeof(int), cudaMemcpyHostToDevice, cs);
+            cudaMemcpyAsync(bu.kpre, tp + 2 * (m + 1), (size_t)(m + 1) * sizeof(int), cudaMemcpyHostToDevice, cs);
+            cudaMemsetAsync(bu.zero, 0, bu.zero_bytes, cs);
+            BatchUnits bw = bu;
+            bw.count = m;
+            const int l = launch_batch_units(items_dev + w0, m, bw, logt_n, sh, num_sms, cs);
+            L = l < 0 ? -1 : L + l;
+        }
+        cudaMemcpyAsync(H + items_b, D + items_b, q_b + c_b + (size_t)count * sizeof(int), cudaMemcpyDeviceToHost, cs);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cs, &graph);
+        if (e != cudaSuccess || L < 0) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(e != cudaSuccess ? e : cudaErrorLaunchFailure, "batched graph capture");
+        }
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        g_graphs[key] = exec;
+    }
+    TraceFn tr = trace_begin();
+    if (tr) tr("k_bu", s);
+    CK(cudaGraphLaunch(exec, s));
+    if (tr) tr(nullptr, s);
+    g_launches += 1;
+    CK(cudaStreamSynchronize(s));
+    trace_collect();
+    const int *st_h = (const int *)(H + items_b + q_b + c_b);
+    for (int i = 0; i < count; ++i) {
+        if (st_h[i] & 1) return fail(QM_EINVAL, "item " + std::to_string(i) + ": a label lies outside its range");
+        if (st_h[i] & 2) return fail(QM_EOVERFLOW, "item " + std::to_string(i) + ": a community borders too many communities");
+        if (st_h[i]) return fail(QM_ECUDA, "item " + std::to_string(i) + ": device status " + std::to_string(st_h[i]));
+    }
+    const qm_quality *qh = (const qm_quality *)(H + items_b);
+    const qm_compare *ch = (const qm_compare *)(H + items_b + q_b);
+    for (int i = 0; i < count; ++i) {
+        if (out_q && (d.items[i].flags & 1)) out_q[i] = qh[i];
+        if (out_c && (d.items[i].flags & 2)) out_c[i] = ch[i];
+    }
+    return QM_OK;
+}
+
+// Runs the batched items: the two-phase pipeline when every item's runs fit
+// its limits, otherwise the persistent kernel k_batched (one block per item).
+// Labels must already be on the device.
 static qm_status run_batched(int dev, BatchDesc &d, const Shape &sh0, qm_quality *out_q, qm_compare *out_c,
                              cudaStream_t s, Lease *extra_dev)
 {
+    {
+        bool fits = true;
+        for (const BatchItem &it : d.items) fits &= it.n_arcs <= BATCH_UNITS_MAX_ARCS;
+        if (fits) return run_batched_units(dev, d, sh0, out_q, out_c, s);
+    }
     (void)extra_dev;
     const int count = (int)d.items.size();
     const int num_sms = num_sms_of(dev);
@@ -1634,9 +1784,15 @@ qm_status qm_autotune_batched(const qm_graph *gc, const int32_t *labels, int32_t
     float best_ms = 1e30f;
     Shape best = default_shape();
     best.algo = 0;
+    // the two-phase pipeline (graphs with at most BATCH_UNITS_MAX_ARCS arcs)
+    // has no large-community threshold; the one-block-per-item kernel does
+    const bool units = g->n_arcs <= BATCH_UNITS_MAX_ARCS;
+    const std::vector<int> smems = units ? std::vector<int>{32 * 1024, 48 * 1024, 64 * 1024, 96 * 1024, 160 * 1024}
+                                         : std::vector<int>{64 * 1024, 96 * 1024, 160 * 1024};
+    const std::vector<int> bigs = units ? std::vector<int>{128} : std::vector<int>{48, 128, 256};
     for (int th : {256, 512})
-        for (int sm : {64 * 1024, 96 * 1024, 160 * 1024})
-            for (int bg : {48, 128, 256}) {
+        for (int sm : smems)
+            for (int bg : bigs) {
                 qm_tuning tt{th, sm, bg, 0, 0};
                 if (!shape_ok(&tt)) continue;
                 Shape sh;
@@ -1645,7 +1801,7 @@ qm_status qm_autotune_batched(const qm_graph *gc, const int32_t *labels, int32_t
                 sh.big_community = bg;
                 sh.blocks_per_sm = 0;
                 sh.algo = 0;
-                if (resolve_batched(sh).blocks_per_sm < 1) continue;
+                if ((units ? resolve_batch_units(sh) : resolve_batched(sh)).blocks_per_sm < 1) continue;
                 float times[3];
                 bool ok = true;
                 for (int r = 0; r < 3 && ok; ++r) {
@@ -1673,7 +1829,7 @@ qm_status qm_autotune_batched(const qm_graph *gc, const int32_t *labels, int32_t
         g->tuning_batch[bucket_of(g->n, g->n_arcs, kmax)] = b;
     }
     if (chosen) {
-        const Shape r = resolve_batched(best);
+        const Shape r = units ? resolve_batch_units(best) : resolve_batched(best);
         chosen->threads = r.threads;
         chosen->smem_bytes = r.smem_bytes;
         chosen->big_community = r.big_community;

@@ -16,6 +16,7 @@
 
 #include "qm_internal.h"
 #include "qm_community.cuh"
+#include "qm_expand.cuh"
 #include "qm_finalize.cuh"
 
 namespace qm {
@@ -750,45 +751,8 @@ __global__ void k_scatter_deg(const int *__restrict__ labels, const long long *_
     }
 }
 
-// Phase A: for each member position p (community order) the labels of the
-// neighbours of members[p] are looked up.  A warp takes 32 consecutive member
-// positions; they hold one or more runs of members of one community each.  For
-// a run of community c the warp spreads the run's arcs over its lanes,
-// gathers the neighbour labels, and packs those != c at the front of c's arc
-// segment: a ballot gives each lane its place and one atomic on inter[c]
-// reserves the room.  inter[c] ends as the number of cut arcs of c,
-// |E_c^out| (Sec. II-B.3), and the packed run never outgrows the segment,
-// whose length is the volume of c.  No shared-memory table is needed, so the
-// kernel runs at full occupancy.
-//
-// Locating the CSR entry of the e-th arc of a run: when the 32 members form a
-// few segments of consecutive node ids (the common case on a graph loaded
-// with QM_REORDER), a segment's rows are adjacent in the CSR and its arcs are
-// one contiguous range; otherwise a search over the members' arc offsets
-// finds the member of each arc.
-constexpr int EXPAND_THREADS = 256;
-
-// Community ownership of a sharded call (the decomposition of Sec. III-A:
-// community c belongs to process c mod P).  Unsharded calls pass P = 1.
-struct Shard {
-    int r;  // this shard
-    int p;  // number of shards
-    __device__ __forceinline__ bool owns(int c) const { return p == 1 || c % p == r; }
-};
-constexpr int EXPAND_UNROLL = 8;
-constexpr int EXPAND_MAX_SEGS = 6;
-
-// Edge weights of a weighted graph (float32, 0 or in [2^-20, 2^20)) as exact
-// fixed-point integers: w * 2^43 (an integer below 2^63).
-__device__ __forceinline__ unsigned long long w_fixed(float w) { return __float2ull_rn(w * 8796093022208.0f); }
-
-// Packed copy of the labels for the far-end gathers: three 21-bit labels per
-// 64-bit word (label ids below 2^21), 8/3 bytes a node instead of 4.  The
-// gathers of the expand phase land at random in the label array; a smaller
-// array leaves a larger share of it in L2.
-constexpr int PACK_BITS = 21;
-constexpr long long PACK_MAX_K = 1LL << PACK_BITS;
-
+// The packed label copy read by the far-end gathers (PACK_BITS-bit ids, three
+// to a word; see qm_expand.cuh).
 __global__ void k_pack3(const int *__restrict__ labels, long long n, unsigned long long *__restrict__ plab,
                         const int *status)
 {
@@ -804,88 +768,8 @@ __global__ void k_pack3(const int *__restrict__ labels, long long n, unsigned lo
     }
 }
 
-__device__ __forceinline__ int ld_label3(const unsigned long long *plab, int v, unsigned long long pol)
-{
-    const unsigned q = (unsigned)v / 3u;
-    const unsigned r = (unsigned)v - 3u * q;
-    unsigned long long w;
-    asm("ld.global.nc.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(w) : "l"(plab + q), "l"(pol));
-    return (int)((w >> (PACK_BITS * r)) & 0x1FFFFFull);
-}
-
-// Gathers the labels of arcs [e_lo, e_hi) of a run of community c (loc(e) is
-// the CSR index of arc e), counts those != c in inter[c] (the cut arcs of c)
-// and packs them into c's segment at cbase; with HI only the labels above c are
-// packed (each unordered pair of communities is counted by its smaller id), and
-// hi[c] counts them.  On a weighted graph (WT) the arc weights travel with the
-// packed labels (nbrw) and each lane sums the fixed-point weights of its intra
-// and cut arcs.
-template <bool WT, bool PACK, bool HI, class LOC>
-__device__ __forceinline__ void expand_range(unsigned e_lo, unsigned e_hi, int c, unsigned cbase, LOC loc,
-                                             const int *__restrict__ col, const int *__restrict__ labels,
-                                             const unsigned long long *__restrict__ plab,
-                                             int *inter, int *hi, int *__restrict__ nbr, unsigned long long keep,
-                                             int lane, const float *__restrict__ wt, float *__restrict__ nbrw,
-                                             u128 &w_in, u128 &w_out)
-{
-    const unsigned lt = (1u << lane) - 1u;
-    for (unsigned e0 = e_lo; e0 < e_hi; e0 += 32u * EXPAND_UNROLL) {
-        int lab[EXPAND_UNROLL];
-        float wv[EXPAND_UNROLL];
-#pragma unroll
-        for (int k = 0; k < EXPAND_UNROLL; ++k) {
-            const unsigned e = e0 + lane + 32u * k;
-            lab[k] = e < e_hi ? __ldcs(&col[loc(e)]) : -1;
-            if (WT) wv[k] = e < e_hi ? __ldcs(&wt[loc(e)]) : 0.0f;
-        }
-#pragma unroll
-        for (int k = 0; k < EXPAND_UNROLL; ++k)
-            if (lab[k] >= 0) lab[k] = PACK ? ld_label3(plab, lab[k], keep) : ld_hint(&labels[lab[k]], keep);
-        if (WT) {
-#pragma unroll
-            for (int k = 0; k < EXPAND_UNROLL; ++k)
-                if (lab[k] >= 0) {
-                    const unsigned long long f = w_fixed(wv[k]);
-                    if (lab[k] == c) w_in += f; else w_out += f;
-                }
-        }
-        unsigned msk[EXPAND_UNROLL];
-        int tot = 0, cut = 0;
-#pragma unroll
-        for (int k = 0; k < EXPAND_UNROLL; ++k) {
-            if (HI) cut += __popc(__ballot_sync(0xffffffffu, lab[k] >= 0 && lab[k] != c));
-            msk[k] = __ballot_sync(0xffffffffu, HI ? lab[k] > c : (lab[k] >= 0 && lab[k] != c));
-            tot += __popc(msk[k]);
-        }
-        if (HI && cut && lane == 0) atomicAdd(&inter[c], cut);
-        if (tot == 0) continue;
-        int pos = 0;
-        if (lane == 0) pos = atomicAdd(HI ? &hi[c] : &inter[c], tot);
-        unsigned at = cbase + (unsigned)__shfl_sync(0xffffffffu, pos, 0);
-#pragma unroll
-        for (int k = 0; k < EXPAND_UNROLL; ++k) {
-            if ((msk[k] >> lane) & 1u) {
-                __stcs(&nbr[at + __popc(msk[k] & lt)], lab[k]);
-                if (WT) __stcs(&nbrw[at + __popc(msk[k] & lt)], wv[k]);
-            }
-            at += __popc(msk[k]);
-        }
-    }
-}
-
-// Adds a warp's intra and cut weight sums of community c to its limbs (wl:
-// six words per community, intra then cut).
-__device__ __forceinline__ void flush_weights(unsigned long long *wl, int c, u128 w_in, u128 w_out, int lane)
-{
-    for (int d = 16; d > 0; d >>= 1) {
-        w_in += shfl_down_u128(w_in, d);
-        w_out += shfl_down_u128(w_out, d);
-    }
-    if (lane == 0) {
-        if (w_in) limbs_add(wl + (size_t)c * 6, (i128)w_in);
-        if (w_out) limbs_add(wl + (size_t)c * 6 + 3, (i128)w_out);
-    }
-}
+// Phase A (the far-end label gathers) lives in qm_expand.cuh: expand_chunk is one
+// warp's share of it.
 
 template <bool WT, bool PACK, bool HI>
 __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__restrict__ row_ptr,
@@ -905,75 +789,11 @@ __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__re
     __shared__ int cw_s[EXPAND_THREADS / 32][32];
     if (*status) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    unsigned *offw = offs_s[w];
-    long long *rsw = rs_s[w];
-    int *cw = cw_s[w];
     const unsigned long long keep = l2_policy_evict_last();
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long p0 = ((long long)blockIdx.x * (blockDim.x >> 5) + w) * 32; p0 < n; p0 += nwarps * 32) {
-        const int nm = (int)min(32LL, n - p0);
-        const unsigned base = __ldg(&aoff[p0]);
-        int u = -2;
-        if (lane < nm) {
-            u = __ldcs(&members[p0 + lane]);
-            offw[lane] = __ldg(&aoff[p0 + lane]) - base;
-            rsw[lane] = __ldg(&row_ptr[u]);
-            cw[lane] = ld_hint(&labels[u], keep);
-        }
-        if (lane == 0) offw[nm] = __ldg(&aoff[p0 + nm]) - base;
-        __syncwarp();
-        const int u_prev = __shfl_up_sync(0xffffffffu, u, 1);
-        const bool valid = lane < nm;
-        const bool newrun = valid && (lane == 0 || cw[lane] != cw[lane - 1]);
-        unsigned runs = __ballot_sync(0xffffffffu, newrun);
-        const unsigned segs = __ballot_sync(0xffffffffu, newrun || (valid && u != u_prev + 1));
-        int cur_c = -1;
-        unsigned cbase = 0;
-        if (__popc(segs) <= EXPAND_MAX_SEGS) {
-            unsigned rem = segs;
-            while (rem) {
-                const int lo = __ffs(rem) - 1;
-                rem &= rem - 1;
-                const int hi = rem ? __ffs(rem) - 1 : nm;
-                const unsigned e_lo = offw[lo], e_hi = offw[hi];
-                if (e_lo == e_hi) continue;
-                const int c = cw[lo];
-                if (!own.owns(c)) continue;
-                if (c != cur_c) {
-                    cur_c = c;
-                    if (lane == 0) cbase = __ldg(&aoff[__ldg(&start[c])]);
-                    cbase = __shfl_sync(0xffffffffu, cbase, 0);
-                }
-                const long long cs = rsw[lo] - (long long)e_lo;  // CSR index of arc e is cs + e
-                u128 w_in = 0, w_out = 0;
-                expand_range<WT, PACK, HI>(e_lo, e_hi, c, cbase, [cs](unsigned e) { return cs + (long long)e; }, col,
-                                           labels, plab, inter, inter_hi, nbr, keep, lane, wt, nbrw, w_in, w_out);
-                if (WT) flush_weights(wl, c, w_in, w_out, lane);
-            }
-        } else {
-            while (runs) {
-                const int m_lo = __ffs(runs) - 1;
-                runs &= runs - 1;
-                const int m_hi = runs ? __ffs(runs) - 1 : nm;
-                const unsigned e_lo = offw[m_lo], e_hi = offw[m_hi];
-                if (e_lo == e_hi) continue;
-                const int c = cw[m_lo];
-                if (!own.owns(c)) continue;
-                if (lane == 0) cbase = __ldg(&aoff[__ldg(&start[c])]);
-                cbase = __shfl_sync(0xffffffffu, cbase, 0);
-                u128 w_in = 0, w_out = 0;
-                expand_range<WT, PACK, HI>(
-                    e_lo, e_hi, c, cbase,
-                    [=](unsigned e) {
-                        const int o = m_lo + upper_bound_smem(offw + m_lo, m_hi - m_lo, e) - 1;
-                        return rsw[o] + (long long)(e - offw[o]);
-                    },
-                    col, labels, plab, inter, inter_hi, nbr, keep, lane, wt, nbrw, w_in, w_out);
-                if (WT) flush_weights(wl, c, w_in, w_out, lane);
-            }
-        }
-        __syncwarp();
-    }
+    for (long long p0 = ((long long)blockIdx.x * (blockDim.x >> 5) + w) * 32; p0 < n; p0 += nwarps * 32)
+        expand_chunk<WT, PACK, HI>(p0, n, row_ptr, col, labels, plab, members, aoff, start, inter, inter_hi, nbr,
+                                   own, wt, nbrw, wl, offs_s[w], rs_s[w], cw_s[w], keep, lane);
 }
 
 #include "qm_binned.cuh"
