@@ -652,8 +652,12 @@ __device__ __forceinline__ unsigned long long bu_add_n(const EpochTable &t, unsi
 }
 
 // count_run (phase B of the plain path) with warp-aggregated updates: the same
-// record, the same bits.  Every warp of the group walks the run in warp-uniform
-// steps so that its lanes can merge equal keys.
+// record, the same bits.  Every warp of the group walks the run in
+// warp-uniform steps of BU_CU entries a lane, all loaded (with their
+// reciprocals) before the table updates, so that its lanes can merge equal
+// keys and several loads are in flight.
+constexpr int BU_CU = 4;
+
 template <class TAB>
 __device__ __forceinline__ void count_run_agg(const CountCtx &x, const RunHdr &h, const int *src, const TAB &tab,
                                               unsigned &epoch, int gtid, int gsize, unsigned long long *red)
@@ -670,22 +674,33 @@ __device__ __forceinline__ void count_run_agg(const CountCtx &x, const RunHdr &h
         bool ok = true;
         for (unsigned r = 0; r < R && ok; ++r) {
             epoch = etab_next_epoch(tab, epoch, gtid, gsize);
-            for (unsigned e0 = (unsigned)(gtid & ~31); e0 < m; e0 += (unsigned)gsize) {
-                const unsigned e = e0 + (unsigned)lane;
-                int lv = e < m ? __ldcs(&src[e]) : -1;
-                if (lv >= 0 && (!QM_CHK(lv, x.K, 6) || lv < c || (R > 1 && tab_split((unsigned)lv, R) != r))) lv = -1;
-                const unsigned act = __ballot_sync(0xffffffffu, lv >= 0);
-                if (lv < 0) continue;
-                const unsigned peers = __match_any_sync(act, lv);
-                if (lane != __ffs(peers) - 1) continue;
-                const Rcp rj = ld_rcp(&x.recip[lv]);
-                bool first = false;
-                const unsigned long long q2 = bu_add_n(tab, (unsigned)lv, (unsigned)__popc(peers), epoch, first);
-                if (q2 == 0ull) continue;  // overflow: this pass is discarded
-                if (q2 == 1ull) u192_add_rcp(inner, rj);
-                else u192_mac(inner, q2, rj);
-                cnt2 += q2;
-                slots += first ? 1ull : 0ull;
+            for (unsigned e0 = (unsigned)(gtid & ~31) * BU_CU; e0 < m; e0 += (unsigned)gsize * BU_CU) {
+                int lv[BU_CU];
+                Rcp rj[BU_CU];
+#pragma unroll
+                for (int k = 0; k < BU_CU; ++k) {
+                    const unsigned e = e0 + (unsigned)lane + 32u * k;
+                    lv[k] = e < m ? __ldcs(&src[e]) : -1;
+                    if (lv[k] >= 0 && (!QM_CHK(lv[k], x.K, 6) || lv[k] < c || (R > 1 && tab_split((unsigned)lv[k], R) != r)))
+                        lv[k] = -1;
+                }
+#pragma unroll
+                for (int k = 0; k < BU_CU; ++k)
+                    if (lv[k] >= 0) rj[k] = ld_rcp(&x.recip[lv[k]]);
+#pragma unroll
+                for (int k = 0; k < BU_CU; ++k) {
+                    const unsigned act = __ballot_sync(0xffffffffu, lv[k] >= 0);
+                    if (lv[k] < 0) continue;
+                    const unsigned peers = __match_any_sync(act, lv[k]);
+                    if (lane != __ffs(peers) - 1) continue;
+                    bool first = false;
+                    const unsigned long long q2 = bu_add_n(tab, (unsigned)lv[k], (unsigned)__popc(peers), epoch, first);
+                    if (q2 == 0ull) continue;  // overflow: this pass is discarded
+                    if (q2 == 1ull) u192_add_rcp(inner, rj[k]);
+                    else u192_mac(inner, q2, rj[k]);
+                    cnt2 += q2;
+                    slots += first ? 1ull : 0ull;
+                }
             }
             group_sync_n(gsize);
             if (*(volatile int *)tab.overflow) ok = false;
@@ -709,10 +724,84 @@ __device__ __forceinline__ void count_run_agg(const CountCtx &x, const RunHdr &h
     }
 }
 
-// Phase B of community c of one candidate with a group: its record.
+// Phase B with a direct-mapped 16-bit counter per label id (two to a 32-bit
+// word of shared memory), for candidates whose K ids all fit: a first pass
+// adds each entry to its key's counter; a second pass takes each key's count
+// at its first visit (an atomic AND that also clears the counter) and adds
+// |E_cj|^2 Rcp_j for it, so the counters are back at zero for the next run.
+// The record is the same as count_run's: the same exact integer sums.  Runs
+// must be shorter than 2^16 entries.
+__device__ __forceinline__ void count_run_direct(const CountCtx &x, const RunHdr &h, const int *src, unsigned *w16,
+                                                 int gtid, int gsize, unsigned long long *red)
+{
+    const unsigned m = h.m;
+    const int c = h.c;
+    for (unsigned e = (unsigned)gtid; e < m; e += (unsigned)gsize) {
+        const int lv = __ldg(&src[e]);
+        if (lv > c && QM_CHK(lv, x.K, 6)) atomicAdd(&w16[lv >> 1], 1u << ((lv & 1) << 4));
+    }
+    group_sync_n(gsize);
+    unsigned long long slots = 0, cnt2 = 0;
+    U192 inner, inner_full;
+    u192_zero(inner);
+    u192_zero(inner_full);
+    for (unsigned e0 = (unsigned)gtid; e0 < m; e0 += (unsigned)gsize * BU_CU) {
+        int lv[BU_CU];
+        unsigned cnt[BU_CU];
+        Rcp rj[BU_CU];
+#pragma unroll
+        for (int k = 0; k < BU_CU; ++k) {
+            const unsigned e = e0 + (unsigned)gsize * k;
+            lv[k] = e < m ? __ldg(&src[e]) : -1;
+            if (lv[k] <= c || !QM_CHK(lv[k], x.K, 6)) lv[k] = -1;
+        }
+#pragma unroll
+        for (int k = 0; k < BU_CU; ++k) {
+            cnt[k] = 0u;
+            if (lv[k] >= 0) {
+                const unsigned sh = ((unsigned)lv[k] & 1u) << 4;
+                cnt[k] = (atomicAnd(&w16[lv[k] >> 1], ~(0xFFFFu << sh)) >> sh) & 0xFFFFu;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < BU_CU; ++k)
+            if (cnt[k]) rj[k] = ld_rcp(&x.recip[lv[k]]);
+#pragma unroll
+        for (int k = 0; k < BU_CU; ++k) {
+            if (!cnt[k]) continue;
+            const unsigned long long q = (unsigned long long)cnt[k] * cnt[k];
+            if (q == 1ull) u192_add_rcp(inner, rj[k]);
+            else u192_mac(inner, q, rj[k]);
+            cnt2 += q;
+            slots += 1ull;
+        }
+    }
+    group_totals<false>(slots, cnt2, inner, inner_full, gsize, red);
+    if (gtid == 0) put_record(x, h.c, h.vol, m, slots, cnt2, inner, inner_full);
+    if (gsize == 32) __syncwarp();
+}
+
+// The run header of community c of one candidate: its packed run and volume.
+__device__ __forceinline__ RunHdr bu_run(const BuSlice &S, int c)
+{
+    const unsigned a0 = __ldcg(&S.aoff[__ldcg(&S.start[c])]), a1 = __ldcg(&S.aoff[__ldcg(&S.start[c + 1])]);
+    return RunHdr{c, a0, (unsigned)__ldcg(&S.inter_hi[c]), a1 - a0};
+}
+
+// A group's shared-memory counting region: `words` 32-bit words that serve
+// either as direct 16-bit counters (count_run_direct, left all zero) or as an
+// epoch-tagged hash table (count_run_agg, left tagged: `dirty`).
+struct BuRegion {
+    unsigned *w;
+    int words;
+    bool dirty;
+    unsigned epoch;
+};
+
+// Phase B of one community of one candidate with a group: its record.
 template <class TAB>
-__device__ __forceinline__ void bu_count_one(const BatchItem &I, const BuSlice &S, int c, const TAB &tab,
-                                             unsigned &epoch, int gtid, int gsize, unsigned long long *red)
+__device__ __forceinline__ void bu_count_one(const BatchItem &I, const BuSlice &S, const RunHdr &h, const TAB &tab,
+                                             BuRegion &rg, int gtid, int gsize, unsigned long long *red)
 {
     CountCtx x;
     x.nbr = S.nbr;
@@ -724,9 +813,18 @@ __device__ __forceinline__ void bu_count_one(const BatchItem &I, const BuSlice &
     x.K = I.K;
     x.err = I.status;
     x.full = 0;
-    const unsigned a0 = __ldcg(&S.aoff[__ldcg(&S.start[c])]), a1 = __ldcg(&S.aoff[__ldcg(&S.start[c + 1])]);
-    const RunHdr h{c, a0, (unsigned)__ldcg(&S.inter_hi[c]), a1 - a0};
-    count_run_agg<TAB>(x, h, S.nbr + a0, tab, epoch, gtid, gsize, red);
+    if ((long long)I.K <= 2LL * rg.words && h.m < (1u << 16)) {
+        if (rg.dirty) {  // a hash pass left tagged slots: clear them once
+            for (int i = gtid; i < rg.words; i += gsize) rg.w[i] = 0u;
+            group_sync_n(gsize);
+            rg.dirty = false;
+            rg.epoch = 0;
+        }
+        count_run_direct(x, h, S.nbr + h.a0, rg.w, gtid, gsize, red);
+        return;
+    }
+    rg.dirty = true;
+    count_run_agg<TAB>(x, h, S.nbr + h.a0, tab, rg.epoch, gtid, gsize, red);
 }
 
 struct BuArgs {
@@ -744,9 +842,10 @@ constexpr int BU_COUNT_SLOT_OFF = 256 * 8 + 256;
 
 // Phase B over every scored candidate's communities: runs a warp's table holds
 // at 3/4 load are counted by single warps (phase 0), the others by whole blocks
-// (phase 1), each with the epoch-tagged tables of the plain path.
+// (phase 1), with direct counters when the candidate's ids fit the group's
+// region, else with the epoch-tagged tables of the plain path.
 template <class TAB>
-__global__ void __launch_bounds__(BATCH_MAX_THREADS) k_bu_count(BuArgs a)
+__global__ void __launch_bounds__(BATCH_MAX_THREADS, 1) k_bu_count(BuArgs a)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int s_i;
@@ -759,9 +858,9 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS) k_bu_count(BuArgs a)
     for (int i = tid; i < cap_w * W; i += T) slot[i] = 0ull;
     for (int i = tid; i <= W; i += T) ovf[i] = 0;
     block_sync();
-    unsigned epoch = 0;
     if (a.phase == 0) {
         const TAB tab = make_table<TAB>(slot + (size_t)wid * cap_w, cap_w, &ovf[wid]);
+        BuRegion rg{(unsigned *)(slot + (size_t)wid * cap_w), 2 * cap_w, false, 0u};
         const unsigned fill_w = (unsigned)(3 * cap_w / 4);
         const int units = __ldg(&b.kpre[a.count]);
         const int chunk = claim_chunk(units, (long long)gridDim.x * W);
@@ -773,17 +872,18 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS) k_bu_count(BuArgs a)
             if (base >= units) break;
             // each lane sizes one unit of the chunk; the warp then counts the
             // small runs in order and lists the others
-            int it = -1, c = 0;
+            int it = -1;
+            RunHdr h{0, 0u, 0u, 0u};
             bool small = false;
             if (lane < chunk && base + lane < units) {
                 it = look = bu_item(b.kpre, a.count, base + lane, look);
-                c = base + lane - __ldg(&b.kpre[it]);
+                const int c = base + lane - __ldg(&b.kpre[it]);
                 const BatchItem &I = a.items[it];
                 if ((I.flags & 1) && !bu_dead(I)) {
-                    const int *st = b.start + (size_t)it * ((size_t)b.k_max + 1);
-                    if (__ldcg(&st[c + 1]) > __ldcg(&st[c])) {
-                        const unsigned m = (unsigned)__ldcg(&b.inter_hi[(size_t)it * b.k_max + c]);
-                        small = m <= fill_w;
+                    const BuSlice S = bu_slice(b, it);
+                    if (__ldcg(&S.start[c + 1]) > __ldcg(&S.start[c])) {
+                        h = bu_run(S, c);
+                        small = h.m <= fill_w;
                         if (!small) b.big_s[atomicAdd(&b.ctr[BU_NBIG_S], 1)] = bu_key(it, c);
                     }
                 }
@@ -792,13 +892,16 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS) k_bu_count(BuArgs a)
             while (mask) {
                 const int j = __ffs(mask) - 1;
                 mask &= mask - 1;
-                const int itj = __shfl_sync(0xffffffffu, it, j), cj = __shfl_sync(0xffffffffu, c, j);
-                bu_count_one<TAB>(a.items[itj], bu_slice(b, itj), cj, tab, epoch, lane, 32, red);
+                const int itj = __shfl_sync(0xffffffffu, it, j);
+                const RunHdr hj{__shfl_sync(0xffffffffu, h.c, j), __shfl_sync(0xffffffffu, h.a0, j),
+                                __shfl_sync(0xffffffffu, h.m, j), __shfl_sync(0xffffffffu, h.vol, j)};
+                bu_count_one<TAB>(a.items[itj], bu_slice(b, itj), hj, tab, rg, lane, 32, red);
             }
         }
         return;
     }
     const TAB tab = make_table<TAB>(slot, cap_w * W, &ovf[W]);
+    BuRegion rg{(unsigned *)slot, 2 * cap_w * W, false, 0u};
     const int nbig = *(volatile int *)&b.ctr[BU_NBIG_S];
     for (;;) {
         if (tid == 0) s_i = atomicAdd(&b.ctr[BU_NEXT_BIG_S], 1);
@@ -808,7 +911,8 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS) k_bu_count(BuArgs a)
         if (i >= nbig) break;
         const unsigned long long key = __ldcg(&b.big_s[i]);
         const int it = (int)(key >> 32), c = (int)(key & 0xFFFFFFFFull);
-        bu_count_one<TAB>(a.items[it], bu_slice(b, it), c, tab, epoch, tid, T, red);
+        const BuSlice S = bu_slice(b, it);
+        bu_count_one<TAB>(a.items[it], S, bu_run(S, c), tab, rg, tid, T, red);
     }
 }
 
@@ -842,7 +946,7 @@ __device__ __forceinline__ void bu_cells_one(const BatchItem &I, const BuSlice &
 // Cells of every compared candidate's found communities: single warps take
 // the communities whose members fit a warp's table (phase 0), whole blocks the
 // others (phase 1).
-__global__ void __launch_bounds__(BATCH_MAX_THREADS) k_bu_cells(BuArgs a)
+__global__ void __launch_bounds__(BATCH_MAX_THREADS, 1) k_bu_cells(BuArgs a)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int s_i;

@@ -1,5 +1,7 @@
-"""The batched persistent launch: every result must equal, bit for bit, the
-plain one-partition call on the same inputs (which itself matches the oracle),
+"""The batched calls (the two-phase pipeline over all candidates, and the
+one-block-per-item kernel for graphs beyond its run limit): every result must
+equal, bit for bit, the plain one-partition call on the same inputs (which
+itself matches the oracle),
 and at the benchmark's batched shape (1,024 candidates per launch on 100,000-node
 graphs with mixing 0.1, 0.3 and 0.5) every item matches the oracle."""
 import os
@@ -120,6 +122,52 @@ def test_autotune_batched_keeps_results(qm, setup):
         assert oq == ref_q and oc == ref_c, shape
     with pytest.raises(qm.QmError):                      # more threads than the kernel's launch bound
         qm.set_batch_tuning(graph, max(Ks), 1024, 96 * 1024, 128)
+
+
+def test_batched_count_paths(qm, setup):
+    """Candidates whose label ids exceed a group's direct counters take the
+    hashed count, runs too long for a warp take whole blocks, and a batch that
+    mixes them (under small and large launch shapes) still gives the plain
+    bits for scoring and comparison."""
+    g, graph, L, Ks = setup
+    n = L.shape[1]
+    rng = np.random.default_rng(5)
+    rows, ks = [L[0], L[1]], [Ks[0], Ks[1]]
+    for K in (n, n // 2, 6_000):  # mostly tiny communities over many ids
+        rows.append(torch.from_numpy(rng.integers(0, K, n).astype(np.int32)))
+        ks.append(K)
+    giant = g.labels.clone()
+    giant[: n // 2] = 0  # one community of half the nodes: a long run
+    rows.append(giant)
+    ks.append(g.K)
+    M = torch.stack(rows).cuda()
+    truth = g.labels.cuda()
+    for shape in ((256, 32 * 1024, 128), (512, 96 * 1024, 128)):
+        qm.set_batch_tuning(graph, max(ks), *shape)
+        sq = qm.score_batched(graph, M, ks)
+        oq, oc = qm.evaluate_batched(graph, M, ks, truth, g.K)
+        for p in range(len(ks)):
+            ref = qm.score(graph, M[p], ks[p])
+            assert sq[p] == ref and oq[p] == ref, (shape, p)
+            assert oc[p] == qm.compare(truth, M[p], g.K, ks[p]), (shape, p)
+
+
+def test_dense_graph_batches(qm, oracle_mod):
+    """A graph whose arcs exceed the two-phase batched pipeline's run limit
+    (2^24 - 1) is batched by the one-block-per-item kernel: the same bits as
+    the plain calls."""
+    from paper_1507_05492_gb300 import gen
+    g = gen.lfr_graph(gen.LfrParams(n=120_000, k_mean=150, k_max=300, s_min=400, s_max=1500, seed=71),
+                      device="cuda")
+    assert g.col.numel() > (1 << 24) - 1
+    graph = qm.Graph(g.row_ptr, g.col)
+    labs, Ks = gen.candidate_batch(g.labels, 4, seed=30_000, k_range=(50, 400))
+    oq, oc = qm.evaluate_batched(graph, labs, Ks, g.labels, g.K)
+    for p in range(len(Ks)):
+        assert oq[p] == qm.score(graph, labs[p], Ks[p]), p
+        assert oc[p] == qm.compare(g.labels, labs[p], g.K, Ks[p]), p
+    check_quality(oq[1], oracle_mod.score(g.row_ptr.cpu().numpy(), g.col.cpu().numpy(), labs[1].cpu().numpy(),
+                                          Ks[1]), "dense batch item 1")
 
 
 @pytest.mark.parametrize("workload", ["lfr100k_mu01", "lfr100k_mu03", "lfr100k_mu05"])
