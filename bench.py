@@ -410,6 +410,32 @@ def bench_headline(args, world, rank, local):
     assert qe == q, "host-buffer path differs from the device path"
     e2e_value = edges_all / (e2e_ms / 1e3)
 
+    # phase B by sorting each community's run (algorithm 6) against the default
+    # hashed count (algorithm 1), on the same graph and partition
+    count_variants = None
+    if not args.no_extras and world == 1:
+        vsteps = max(1, args.steps // 2)
+
+        def per_kernel(traces, steps):
+            tot = {}
+            for tr in traces:
+                for name, t in tr:
+                    tot[name] = tot.get(name, 0.0) + t / steps
+            return {k: round(v, 3) for k, v in sorted(tot.items(), key=lambda x: -x[1])}
+
+        qm.set_tuning(graph, K, 512, 96 * 1024, 48, 6)
+        for _ in range(2):
+            qm.score(graph, labels, K)
+        ms6, q6, tr6, _ = _timed_steps(qm, graph, labels, K, vsteps, stream, torch)
+        qm.set_tuning(graph, K, 512, 96 * 1024, 48, 1)  # the default shape again
+        assert q6 == q, "sorted and hashed counts disagree"
+        count_variants = {
+            "what": "phase B of the two-phase pipeline: each community's packed run hashed (algorithm 1, "
+                    "k_count + k_count_long) or radix-sorted and run-length counted (algorithm 6, "
+                    "k_count_sort + k_count_long); same graph, partition and launch shape, identical results",
+            "hash": {"ms_per_step": ms_max / args.steps, "kernel_ms": per_kernel(step_kernels, args.steps)},
+            "sort": {"ms_per_step": ms6 / vsteps, "kernel_ms": per_kernel(tr6, vsteps)}}
+
     # metrics with ground truth at the same size: the planted partition as the
     # truth against a copy with 20% of the nodes moved (Eqs. 1-7)
     cmp = None
@@ -532,6 +558,7 @@ def bench_headline(args, world, rank, local):
         unordered=unordered,
         compare=cmp,
         detect=detect,
+        count_variants=count_variants,
     )
     graph.close()
     del labels, lab_h
@@ -780,7 +807,8 @@ def run_ours(args):
                        {"value": res["value"], "unit": UNIT, "ms_per_step": res["ms_per_step"]}}
                       | ({"as_given": res["unordered"]} if res["unordered"] else {}),
             "extras": extras | ({"compare": res["compare"]} if res["compare"] else {})
-                      | ({"detect": res["detect"]} if res["detect"] else {}),
+                      | ({"detect": res["detect"]} if res["detect"] else {})
+                      | ({"count_variants": res["count_variants"]} if res["count_variants"] else {}),
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -359,7 +359,13 @@ qm_status qm_debug_set_stage_wait(int64_t polls);
  *      21-bit ids to a 64-bit word (8/3 bytes a node instead of 4, so a larger
  *      share of it stays in L2); algorithm 1 does this on graphs of more than
  *      2^22 nodes;
- *   5  as 1, never packed.
+ *   5  as 1, never packed;
+ *   6  as 1, but the second kernel sorts each community's segment by label
+ *      (a radix sort in shared memory, 8-bit digits) and counts the equal-label
+ *      stretches instead of hashing the labels (Eq. (9)'s |E_cj| are those
+ *      stretches' lengths); segments longer than a block's sort buffers are
+ *      hashed as in 1.  Needs threads * 256 entries of sort buffers per block
+ *      (else the shape is refused).
  * Packing needs K <= 2^21; with more label ids the 32-bit labels are gathered.
  * All give bit-identical results.  Weighted graphs take algorithm 1 whatever
  * is set.

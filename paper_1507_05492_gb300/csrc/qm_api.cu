@@ -398,7 +398,10 @@ static Shape resolve_plain(Shape s)
     auto key = std::make_tuple(s.threads, s.smem_bytes, s.algo);
     auto it = occ.find(key);
     if (it == occ.end())
-        it = occ.emplace(key, std::max(1, s.algo ? count_blocks_per_sm(s) : score_blocks_per_sm(s))).first;
+        it = occ.emplace(key, std::max(1, s.algo == ALGO_SORT ? sort_blocks_per_sm(s)
+                                          : s.algo            ? count_blocks_per_sm(s)
+                                                              : score_blocks_per_sm(s)))
+                 .first;
     s.blocks_per_sm = it->second;
     return s;
 }
@@ -446,8 +449,9 @@ static Shape shape_for(qm_graph *g, int K, bool batched)
 static bool shape_ok(const qm_tuning *t)
 {
     return t && t->threads >= 64 && t->threads <= 1024 && t->threads % 32 == 0 && t->smem_bytes >= 16384 &&
-           t->smem_bytes <= MAX_DYN_SMEM && t->big_community >= 1 && (t->algorithm >= 0 && t->algorithm <= 5) &&
-           plan_smem(t->threads, t->smem_bytes).max_used_w >= 32;
+           t->smem_bytes <= MAX_DYN_SMEM && t->big_community >= 1 && (t->algorithm >= 0 && t->algorithm <= ALGO_SORT) &&
+           plan_smem(t->threads, t->smem_bytes).max_used_w >= 32 &&
+           (t->algorithm != ALGO_SORT || sort_shape_ok(t->threads, t->smem_bytes));
 }
 
 extern "C" {
@@ -1862,7 +1866,7 @@ qm_status qm_autotune(const qm_graph *gc, const int32_t *labels, int32_t K, qm_m
     float best_ms = 1e30f;
     Shape best = default_shape();
     qm_quality q;
-    for (int al : {2, 5, 1, 0})
+    for (int al : {2, 5, 1, ALGO_SORT, 0})
     for (int th : threads_c)
         for (int sm : smem_c)
             for (int bg : big_c) {
@@ -1870,6 +1874,7 @@ qm_status qm_autotune(const qm_graph *gc, const int32_t *labels, int32_t K, qm_m
                 if (al == 0 && g->wt) continue;           // weighted graphs: two-phase pipeline only
                 if (al == 2 && (g->wt || g->n <= BIN_MIN_NODES)) continue;  // binning can pay beyond L2 only
                 if (al == 5 && (g->wt || !packs_labels(1, false, g->n, K))) continue;  // 1 is 5 there
+                if (al == ALGO_SORT && g->wt) continue;   // weighted runs carry weights: hashed only
                 Shape sh;
                 sh.threads = th;
                 sh.smem_bytes = sm;

@@ -33,8 +33,13 @@ struct Shape {
     int smem_bytes;     // dynamic shared memory per block
     int big_community;  // communities with more members are scored by a whole block
     int blocks_per_sm;  // resident blocks per SM (filled in from occupancy)
-    int algo = 0;       // 0: one-kernel community pass, 1: expand + count (two phases)
+    int algo = 0;       // 0: one-kernel community pass, 1: expand + count (two phases); see ALGO_*
 };
+
+// Two-phase pipeline whose phase B sorts each community's run and
+// run-length encodes it (k_count_sort) instead of hashing it (k_count);
+// gathers as algorithm 1.
+constexpr int ALGO_SORT = 6;
 
 // Carving of the dynamic shared memory of a community-major block.
 struct SmemPlan {
@@ -134,11 +139,11 @@ inline int bin_mode_of(int algo, bool weighted) { return (!weighted && (algo == 
 // 1): their label array is well beyond what L2 keeps.
 constexpr long long PACK_MIN_NODES = 1LL << 22;
 // Whether a two-phase call gathers from the packed copy: algorithm 4 always,
-// algorithm 1 on graphs above PACK_MIN_NODES; unweighted graphs and label ids
-// below 2^21 only.
+// algorithms 1 and ALGO_SORT on graphs above PACK_MIN_NODES; unweighted graphs
+// and label ids below 2^21 only.
 inline bool packs_labels(int algo, bool weighted, long long n, int K)
 {
-    return !weighted && K <= (1 << 21) && (algo == 4 || (algo == 1 && n > PACK_MIN_NODES));
+    return !weighted && K <= (1 << 21) && (algo == 4 || ((algo == 1 || algo == ALGO_SORT) && n > PACK_MIN_NODES));
 }
 // The autotuner tries the binned gathers on graphs with more nodes than this:
 // their label array (4 bytes a node) is beyond what L2 serves at random.
@@ -180,6 +185,9 @@ int launch_weight_check(const GraphDev &g, const float *wt, int full, int *statu
 int launch_compare(const int *truth, const int *found, long long n, int ka, int kb,
                    const CompareWs &ws, const Shape &sh, int num_sms, cudaStream_t s, TraceFn tr);
 int count_blocks_per_sm(const Shape &sh);
+int sort_blocks_per_sm(const Shape &sh);
+// Whether k_count_sort can run with this block shape (its warps' buffers fit).
+bool sort_shape_ok(int threads, int smem_bytes);
 
 // Generic exclusive scan (qm_kernels.cu) and the graph reorder (qm_reorder.cu).
 size_t scan_tmp_elems(long long n);

@@ -1020,6 +1020,202 @@ __global__ void __launch_bounds__(1024) k_count_long(CountCtx x, const RunHdr *l
     for (int i = blockIdx.x; i < n; i += gridDim.x) count_run_general(x, lng[i], tb, threadIdx.x, blockDim.x, red);
 }
 
+// ------------------------------------------------------------------ phase B by sorting (algorithm 6)
+//
+// The same per-community records as k_count, from sorted runs instead of hash
+// tables (Eq. (9)'s |E_cj| are the lengths of the equal-label stretches of
+// c's run once it is sorted).  A group stages the run in shared memory, sorts
+// it by label with a least-significant-digit radix sort (8-bit digits; each
+// warp histograms a contiguous tile, the digit offsets are scanned over warps
+// and digits, and each warp scatters its tile in order, lanes ranked among
+// equal digits by __match_any_sync, so every pass is stable), then each
+// stretch's first entry finds its end by binary search and adds
+// |E_cj|^2 Rcp_j.  Runs of up to SORT_WARP_CAP entries are sorted by single
+// warps, longer ones up to the block's buffers by whole blocks; longer runs
+// take k_count_long.
+constexpr int SORT_BINS = 256;
+constexpr int SORT_WARP_CAP = 256;
+
+struct SortPlan {
+    int red_off, hist_off, buf_off;
+    int cap;  // entries of each of the block's two buffers
+    int bytes;
+};
+
+static SortPlan plan_sort(int T, int S)
+{
+    SortPlan p;
+    const int W = T / 32;
+    int off = 0;
+    p.red_off = off;
+    off += 256 * 8;
+    p.hist_off = off;
+    off += W * SORT_BINS * 4;
+    p.buf_off = off;
+    p.cap = std::max(0, (S - off) / 8) / 32 * 32;
+    p.bytes = off + p.cap * 8;
+    return p;
+}
+
+// Sorts run h (entries nbr[a0 .. a0 + m)) with a group and writes its record.
+// A and B are the group's buffers (at least m entries each), hist its
+// per-warp digit counters (SORT_BINS per warp); `passes` covers the bits of
+// the largest label id.
+template <bool FULL>
+__device__ __forceinline__ void sort_count_run(const CountCtx &x, const RunHdr &h, int *A, int *B, unsigned *hist,
+                                               int passes, int gtid, int gsize, unsigned long long *red)
+{
+    const int m = (int)h.m, c = h.c, lane = threadIdx.x & 31, wl = gtid >> 5, nw = gsize >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int i = gtid; i < m; i += gsize) A[i] = __ldcs(&x.nbr[h.a0 + i]);
+    group_sync_n(gsize);
+    const int per = (m + nw - 1) / nw, t0 = min(m, wl * per), t1 = min(m, t0 + per);
+    unsigned *hw = hist + wl * SORT_BINS;
+    const int dpt = max(1, SORT_BINS / gsize), d0 = gtid * dpt;  // digits whose offsets this thread forms
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = 8 * pass;
+        for (int d = lane; d < SORT_BINS; d += 32) hw[d] = 0u;
+        __syncwarp();
+        for (int i = t0 + lane; i < t1; i += 32) atomicAdd(&hw[((unsigned)A[i] >> shift) & 255u], 1u);
+        group_sync_n(gsize);
+        // offset of (warp w, digit d): all entries of smaller digits, then those
+        // of digit d in warps before w
+        unsigned tot[8], sum = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            tot[k] = 0u;
+            const int d = d0 + k;
+            if (k < dpt && d < SORT_BINS) {
+                unsigned t = 0;
+                for (int w = 0; w < nw; ++w) {
+                    const unsigned v = hist[w * SORT_BINS + d];
+                    hist[w * SORT_BINS + d] = t;
+                    t += v;
+                }
+                tot[k] = t;
+                sum += t;
+            }
+        }
+        unsigned excl;
+        group_exclusive_scan(sum, excl, gsize, red);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int d = d0 + k;
+            if (k < dpt && d < SORT_BINS) {
+                for (int w = 0; w < nw; ++w) hist[w * SORT_BINS + d] += excl;
+                excl += tot[k];
+            }
+        }
+        group_sync_n(gsize);
+        for (int i0 = t0; i0 < t1; i0 += 32) {
+            const int i = i0 + lane;
+            const bool valid = i < t1;
+            const unsigned act = __ballot_sync(0xffffffffu, valid);
+            int key = 0, pos = 0;
+            unsigned d = 0u, peers = 0u;
+            if (valid) {
+                key = A[i];
+                d = ((unsigned)key >> shift) & 255u;
+                peers = __match_any_sync(act, d);
+                pos = (int)hw[d] + __popc(peers & lt);
+            }
+            __syncwarp();
+            if (valid) {
+                B[pos] = key;
+                if (lane == __ffs(peers) - 1) hw[d] += (unsigned)__popc(peers);
+            }
+            __syncwarp();
+        }
+        group_sync_n(gsize);
+        int *t = A;
+        A = B;
+        B = t;
+    }
+    unsigned long long slots = 0, cnt2 = 0;
+    U192 inner, inner_full;
+    u192_zero(inner);
+    u192_zero(inner_full);
+    for (int i = gtid; i < m; i += gsize) {
+        const int key = A[i];
+        if (i > 0 && A[i - 1] == key) continue;  // not the first of its stretch
+        int lo = i + 1, hi = m;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (A[mid] == key) lo = mid + 1; else hi = mid;
+        }
+        if (!QM_CHK(key, x.K, 7)) continue;
+        const unsigned long long cnt = (unsigned long long)(lo - i), q = cnt * cnt;
+        const Rcp rj = ld_rcp(&x.recip[key]);
+        if (FULL) u192_mac(inner_full, q, rj);
+        if (!FULL || key > c) {
+            u192_mac(inner, q, rj);
+            ++slots;
+            cnt2 += q;
+        }
+    }
+    group_totals<FULL>(slots, cnt2, inner, inner_full, gsize, red);
+    if (gtid == 0) put_record(x, h.c, h.vol, (unsigned)m, slots, cnt2, inner, inner_full);
+    group_sync_n(gsize);  // the buffers are reused by the next run
+}
+
+struct CountSortArgs {
+    CountCtx x;
+    const RunHdr *big;    // runs for whole blocks
+    const RunHdr *small;  // runs for single warps
+    int *counters;
+    const int *status;
+    SortPlan plan;
+    int passes;
+};
+
+template <bool FULL>
+__global__ void __launch_bounds__(1024) k_count_sort(CountSortArgs a)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ int s_i;
+    if (*a.status) return;
+    const SortPlan &p = a.plan;
+    unsigned long long *red = (unsigned long long *)(sm + p.red_off);
+    unsigned *hist = (unsigned *)(sm + p.hist_off);
+    int *buf = (int *)(sm + p.buf_off);
+    const int T = blockDim.x, W = T >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+    const int nbig = a.counters[C_BIG_COUNT];
+    for (;;) {
+        if (tid == 0) s_i = atomicAdd(&a.counters[C_BIG_NEXT], 1);
+        block_sync();
+        const int i = s_i;
+        block_sync();
+        if (i >= nbig) break;
+        sort_count_run<FULL>(a.x, a.big[i], buf, buf + p.cap, hist, a.passes, tid, T, red);
+    }
+    int *wa = buf + wid * 2 * SORT_WARP_CAP;
+    const int nsmall = a.counters[C_SMALL_COUNT];
+    const int chunk = claim_chunk(nsmall, (long long)gridDim.x * W);
+    for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&a.counters[C_SMALL_NEXT], chunk);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= nsmall) break;
+        const int top = min(nsmall, base + chunk);
+        for (int i = base; i < top; ++i)
+            sort_count_run<FULL>(a.x, a.small[i], wa, wa + SORT_WARP_CAP, hist + wid * SORT_BINS, a.passes, lane, 32,
+                                 red);
+    }
+}
+
+bool sort_shape_ok(int threads, int smem_bytes)
+{
+    const SortPlan p = plan_sort(threads, smem_bytes);
+    return p.cap >= (threads / 32) * SORT_WARP_CAP && p.bytes <= smem_bytes;
+}
+
+int sort_blocks_per_sm(const Shape &sh)
+{
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_count_sort<false>, sh.threads, sh.smem_bytes);
+    return nb;
+}
+
 // Block reduction of per-thread sums into the partition's global limbs.
 __device__ __forceinline__ void flush_score_threads(const ScoreAcc &acc, unsigned long long *g,
                                                     unsigned long long *red)
@@ -1082,6 +1278,8 @@ void prepare_kernels()
     cudaFuncSetAttribute(k_count<EpochTable, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     cudaFuncSetAttribute(k_count<EpochTable32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     cudaFuncSetAttribute(k_count_long, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+    cudaFuncSetAttribute(k_count_sort<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+    cudaFuncSetAttribute(k_count_sort<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     cudaFuncSetAttribute(k_count_w, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     cudaFuncSetAttribute(k_expand_bin, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          bin_smem_bytes_per_warp(BIN_MAX) * (EXPAND_THREADS / 32));
@@ -1444,10 +1642,17 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
         packed_len = hi ? ws.inter_hi : ws.inter;
     }
     const CountPlan cp = plan_count(sh.threads, sh.smem_bytes);
+    const bool sorted = sh.algo == ALGO_SORT;
+    const SortPlan sp = plan_sort(sh.threads, sh.smem_bytes);
     TRACE("k_classify");
-    k_classify<<<grid_for(K, 256, num_sms, 4), 256, 0, s>>>(ws.start, ws.aoff, packed_len, K, cp.fill_w, cp.fill_g,
-                                                            cp.fill, ws.hdr_big, ws.hdr_small, ws.hdr_long,
-                                                            ws.hdr_mid, ws.counters, ws.status, own);
+    if (sorted)  // warps sort runs up to SORT_WARP_CAP, blocks up to their buffers
+        k_classify<<<grid_for(K, 256, num_sms, 4), 256, 0, s>>>(ws.start, ws.aoff, packed_len, K, SORT_WARP_CAP,
+                                                                SORT_WARP_CAP, sp.cap, ws.hdr_big, ws.hdr_small,
+                                                                ws.hdr_long, ws.hdr_mid, ws.counters, ws.status, own);
+    else
+        k_classify<<<grid_for(K, 256, num_sms, 4), 256, 0, s>>>(ws.start, ws.aoff, packed_len, K, cp.fill_w,
+                                                                cp.fill_g, cp.fill, ws.hdr_big, ws.hdr_small,
+                                                                ws.hdr_long, ws.hdr_mid, ws.counters, ws.status, own);
     ++launches;
     CountKArgs a;
     a.x.nbr = ws.nbr;
@@ -1465,14 +1670,29 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
     a.status = ws.status;
     a.plan = cp;
     a.stage_wait = g_stage_wait.load();
-    TRACE("k_count");
     const int count_grid = community_grid(K, num_sms, sh);  // sh.blocks_per_sm: occupancy resolved by the caller
     // S_c of every community only when its per-community Qds term is asked for
     a.x.full = (pc && pc->qds) ? 1 : 0;
-    if (K < (1 << 24) - 1) {
+    if (sorted) {
+        CountSortArgs sa;
+        sa.x = a.x;
+        sa.big = ws.hdr_big;
+        sa.small = ws.hdr_small;
+        sa.counters = ws.counters;
+        sa.status = ws.status;
+        sa.plan = sp;
+        int bits = 1;
+        while (bits < 31 && (1LL << bits) < (long long)K) ++bits;
+        sa.passes = (bits + 7) / 8;
+        TRACE("k_count_sort");
+        if (sa.x.full) k_count_sort<true><<<count_grid, sh.threads, sh.smem_bytes, s>>>(sa);
+        else k_count_sort<false><<<count_grid, sh.threads, sh.smem_bytes, s>>>(sa);
+    } else if (K < (1 << 24) - 1) {
+        TRACE("k_count");
         if (a.x.full) k_count<EpochTable32, true><<<count_grid, sh.threads, sh.smem_bytes, s>>>(a);
         else k_count<EpochTable32, false><<<count_grid, sh.threads, sh.smem_bytes, s>>>(a);
     } else {
+        TRACE("k_count");
         if (a.x.full) k_count<EpochTable, true><<<count_grid, sh.threads, sh.smem_bytes, s>>>(a);
         else k_count<EpochTable, false><<<count_grid, sh.threads, sh.smem_bytes, s>>>(a);
     }

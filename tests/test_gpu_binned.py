@@ -1,7 +1,9 @@
-"""The variants of the far-end label gathers of the two-phase pipeline:
-through destination-window bins (algorithms 2 and 3) and from the copy of the
-labels packed three to a word (algorithm 4; algorithm 5 never packs).  The
-packed runs hold the same multisets whatever the gathers, so every result must
+"""The variants of the two-phase pipeline: far-end label gathers through
+destination-window bins (algorithms 2 and 3) and from the copy of the labels
+packed three to a word (algorithm 4; algorithm 5 never packs), and the count of
+each community's run by sorting it (algorithm 6) instead of hashing it.  The
+packed runs hold the same multisets whatever the gathers, and a sorted run has
+the same equal-label stretches as the hashed counts, so every result must
 equal the direct pipeline's bit for bit and match the oracle, on LFR-style graphs with several windows and a
 ragged last window, the degenerate partitions, a hub whose run takes the long
 path, isolated nodes, label ids beyond 24 bits, reordered graphs, sharded
@@ -29,7 +31,7 @@ def gen():
     return g
 
 
-def by_algo(qm, graph, lab, K, algos=(1, 2, 3, 4, 5), per_community=False):
+def by_algo(qm, graph, lab, K, algos=(1, 2, 3, 4, 5, 6), per_community=False):
     out = {}
     for a in algos:
         qm.set_tuning(graph, K, 512, 96 * 1024, 48, a)
@@ -112,7 +114,7 @@ def test_reordered_sharded_and_host_labels(qm, gen):
     reord = qm.Graph(*to_dev(g.row_ptr, g.col), reorder=True)
     lab = gen.perturb(g.labels, g.K, 0.2, seed=14)
     ref = by_algo(qm, plain, lab.cuda(), g.K, algos=(1,))[1]
-    for a in (2, 3, 4, 5):
+    for a in (2, 3, 4, 5, 6):
         for graph in (plain, reord):
             qm.set_tuning(graph, g.K, 512, 96 * 1024, 48, a)
             assert qm.score(graph, lab.cuda(), g.K) == ref
@@ -131,4 +133,4 @@ def test_weighted_graph_ignores_binning(qm, gen):
     w = ((key * 2654435761) % 1000).to(torch.float32) / 100.0 + 0.25
     graph = qm.Graph(*to_dev(g.row_ptr, g.col), weights=w.cuda())
     res = by_algo(qm, graph, g.labels.cuda(), g.K)
-    assert all(res[a] == res[1] for a in (2, 3, 4, 5))
+    assert all(res[a] == res[1] for a in (2, 3, 4, 5, 6))
