@@ -96,7 +96,10 @@ typedef struct qm_graph qm_graph; /* opaque; owns a device copy of the CSR */
  *            hit nearby memory.  Costs one pass per round over the arcs and
  *            4 bytes per node, at load time only.
  *   out      receives the handle; free it with qm_free_graph
- * The arrays are copied: the caller may free them when the call returns.
+ * The arrays are copied: the caller may free them when the call returns.  An
+ * unweighted graph with fewer than 2^32 arcs also keeps its upper rows (the
+ * arcs (u, v) with v >= u, for tuning algorithm 7): 8 bytes a node and 4 bytes
+ * an undirected edge more on the device.
  * Errors: QM_EINVAL (n_nodes < 1, n_arcs odd or 0, bad CSR with QM_VALIDATE),
  * QM_EOVERFLOW, QM_ENOMEM, QM_ECUDA.
  */
@@ -365,10 +368,20 @@ qm_status qm_debug_set_stage_wait(int64_t polls);
  *      stretches instead of hashing the labels (Eq. (9)'s |E_cj| are those
  *      stretches' lengths); segments longer than a block's sort buffers are
  *      hashed as in 1.  Needs threads * 256 entries of sort buffers per block
- *      (else the shape is refused).
+ *      (else the shape is refused);
+ *   7  as 1, but each undirected edge is gathered once, from its lower node
+ *      id, through a copy of the graph's upper rows (arcs to itself and higher
+ *      ids) made at load time (unweighted graphs with fewer than 2^32 arcs;
+ *      8 bytes a node and 4 an edge): an edge inside c adds to 2|E_c^in|, an
+ *      edge to another community puts one entry into the run of the smaller
+ *      id, appended to that run's segment from wherever it is found.  Half the
+ *      far-end gathers, at the price of scattered appends: faster on graphs in
+ *      a random node order whose label array exceeds L2 (the default for
+ *      untuned graphs loaded without QM_REORDER above 2^26 nodes), slower on
+ *      reordered or smaller graphs.  Sharded calls run 1 instead.
  * Packing needs K <= 2^21; with more label ids the 32-bit labels are gathered.
  * All give bit-identical results.  Weighted graphs take algorithm 1 whatever
- * is set.
+ * is set; algorithm 7 needs the upper rows, else it runs as 1.
  */
 typedef struct {
     int32_t threads;

@@ -336,6 +336,8 @@ struct qm_graph {
     int *col;
     int *inv = nullptr;  // QM_REORDER: new node id -> caller's node id (else null)
     float *wt = nullptr; // weighted graph: edge weights parallel to col (else null)
+    long long *up_ptr = nullptr;  // unweighted graphs: upper rows (GraphDev::up_ptr)
+    int *up_col = nullptr;
     long long n, n_arcs, max_degree;
     size_t bytes;
     std::mutex mu;
@@ -443,13 +445,17 @@ static Shape shape_for(qm_graph *g, int K, bool batched)
     auto it = m.find(bucket_of(g->n, g->n_arcs, K));
     Shape s = it != m.end() ? it->second : (batched ? default_batch_shape() : default_shape());
     if (!batched && g->wt && s.algo != 1) s = default_shape();  // weighted graphs: two-phase pipeline, direct gathers
+    // untuned large graphs in their given (unclustered) node order: each edge
+    // gathered once pays there (measured at 10^8 nodes; slower at 3.2*10^7,
+    // whose packed labels stay in L2, and on reordered graphs)
+    if (!batched && it == m.end() && g->up_ptr && !g->inv && g->n > HALF_MIN_NODES) s.algo = ALGO_HALF;
     return batched ? resolve_batched(s) : resolve_plain(s);
 }
 
 static bool shape_ok(const qm_tuning *t)
 {
     return t && t->threads >= 64 && t->threads <= 1024 && t->threads % 32 == 0 && t->smem_bytes >= 16384 &&
-           t->smem_bytes <= MAX_DYN_SMEM && t->big_community >= 1 && (t->algorithm >= 0 && t->algorithm <= ALGO_SORT) &&
+           t->smem_bytes <= MAX_DYN_SMEM && t->big_community >= 1 && (t->algorithm >= 0 && t->algorithm <= ALGO_HALF) &&
            plan_smem(t->threads, t->smem_bytes).max_used_w >= 32 &&
            (t->algorithm != ALGO_SORT || sort_shape_ok(t->threads, t->smem_bytes));
 }
@@ -638,6 +644,21 @@ static qm_status load_impl(const int64_t *row_ptr, const int32_t *col, const flo
         }
         g->bytes += (size_t)n_nodes * 4;
     }
+    if (!weight && n_arcs < (1LL << 32)) {
+        // the upper rows, for gathering each undirected edge once (ALGO_HALF)
+        long long up_arcs = 0;
+        int L = 0;
+        const int r = build_upper_rows(g->d, num_sms_of(dev), s, &g->up_ptr, &g->up_col, &up_arcs, &L);
+        if (r != 0) {
+            cleanup();
+            cudaFree(g->inv);
+            return cuda_fail((cudaError_t)(-r), "upper rows");
+        }
+        g_launches += L;
+        g->d.up_ptr = g->up_ptr;
+        g->d.up_col = g->up_col;
+        g->bytes += (size_t)(n_nodes + 1) * 8 + (size_t)up_arcs * 4;
+    }
     *out = g.release();
     return QM_OK;
 }
@@ -664,6 +685,8 @@ qm_status qm_free_graph(qm_graph *g)
     cudaFree(g->col);
     cudaFree(g->inv);
     cudaFree(g->wt);
+    cudaFree(g->up_ptr);
+    cudaFree(g->up_col);
     delete g;
     return QM_OK;
 }
@@ -1866,7 +1889,7 @@ qm_status qm_autotune(const qm_graph *gc, const int32_t *labels, int32_t K, qm_m
     float best_ms = 1e30f;
     Shape best = default_shape();
     qm_quality q;
-    for (int al : {2, 5, 1, ALGO_SORT, 0})
+    for (int al : {2, 5, 1, ALGO_HALF, ALGO_SORT, 0})
     for (int th : threads_c)
         for (int sm : smem_c)
             for (int bg : big_c) {
@@ -1875,6 +1898,7 @@ qm_status qm_autotune(const qm_graph *gc, const int32_t *labels, int32_t K, qm_m
                 if (al == 2 && (g->wt || g->n <= BIN_MIN_NODES)) continue;  // binning can pay beyond L2 only
                 if (al == 5 && (g->wt || !packs_labels(1, false, g->n, K))) continue;  // 1 is 5 there
                 if (al == ALGO_SORT && g->wt) continue;   // weighted runs carry weights: hashed only
+                if (al == ALGO_HALF && !g->up_ptr) continue;  // no upper rows (weighted or huge graphs)
                 Shape sh;
                 sh.threads = th;
                 sh.smem_bytes = sm;

@@ -4,6 +4,8 @@
 // (qm_batched.cu).
 #pragma once
 
+#include <climits>
+
 #include "qm_community.cuh"
 
 namespace qm {
@@ -204,6 +206,163 @@ __device__ __forceinline__ void expand_chunk(long long p0, long long n, const lo
                 },
                 col, labels, plab, inter, inter_hi, nbr, keep, lane, wt, nbrw, w_in, w_out);
             if (WT) flush_weights(wl, c, w_in, w_out, lane);
+        }
+    }
+    __syncwarp();
+}
+
+
+// ---------------------------------------------------------------- half-edge gathers
+//
+// On a graph that also holds its upper rows (each node's arcs to itself and to
+// higher node ids, a self-loop stored as ~u), every undirected edge is gathered
+// once, from its lower end.  An arc of a member of c to community l != c puts
+// one entry into the run of the smaller of the two ids: l packed into c's
+// segment when l > c, c appended to l's segment (through l's run cursor and
+// segment base cbase[l]) when l < c; with FULL both.  Arcs inside c add 2 (a
+// self-loop 1) to same2[c], so E_c^out = vol(c) - same2[c] and the runs hold the
+// same multisets as gathering every arc from both ends.
+template <bool PACK, bool FULL, class LOC>
+__device__ __forceinline__ void expand_range_half(unsigned e_lo, unsigned e_hi, int c, unsigned cbase_c, LOC loc,
+                                                  const int *__restrict__ up_col, const int *__restrict__ labels,
+                                                  const unsigned long long *__restrict__ plab, int *same2,
+                                                  int *cursor, const unsigned *__restrict__ cbase,
+                                                  int *__restrict__ nbr, unsigned long long keep, int lane)
+{
+    const unsigned lt = (1u << lane) - 1u;
+    for (unsigned e0 = e_lo; e0 < e_hi; e0 += 32u * EXPAND_UNROLL) {
+        int lab[EXPAND_UNROLL];
+        unsigned intra = 0;
+#pragma unroll
+        for (int k = 0; k < EXPAND_UNROLL; ++k) {
+            const unsigned e = e0 + lane + 32u * k;
+            lab[k] = e < e_hi ? __ldcs(&up_col[loc(e)]) : INT_MIN;
+        }
+#pragma unroll
+        for (int k = 0; k < EXPAND_UNROLL; ++k) {
+            if (lab[k] == INT_MIN) {
+                lab[k] = -1;
+            } else if (lab[k] < 0) {  // a self-loop: one arc inside c
+                intra += 1u;
+                lab[k] = -1;
+            } else {
+                lab[k] = PACK ? ld_label3(plab, lab[k], keep) : ld_hint(&labels[lab[k]], keep);
+                if (lab[k] == c) {
+                    intra += 2u;
+                    lab[k] = -1;
+                }
+            }
+        }
+        intra = __reduce_add_sync(0xffffffffu, intra);
+        if (intra && lane == 0) atomicAdd(&same2[c], (int)intra);
+        // entries for c's own run
+        unsigned msk[EXPAND_UNROLL];
+        int tot = 0;
+#pragma unroll
+        for (int k = 0; k < EXPAND_UNROLL; ++k) {
+            msk[k] = __ballot_sync(0xffffffffu, FULL ? lab[k] >= 0 : lab[k] > c);
+            tot += __popc(msk[k]);
+        }
+        if (tot) {
+            int pos = 0;
+            if (lane == 0) pos = atomicAdd(&cursor[c], tot);
+            unsigned at = cbase_c + (unsigned)__shfl_sync(0xffffffffu, pos, 0);
+#pragma unroll
+            for (int k = 0; k < EXPAND_UNROLL; ++k) {
+                if ((msk[k] >> lane) & 1u) __stcs(&nbr[at + __popc(msk[k] & lt)], lab[k]);
+                at += __popc(msk[k]);
+            }
+        }
+        // c appended to the runs of the smaller neighbouring ids (FULL: all),
+        // lanes of one destination merged into one cursor update; all cursor
+        // updates and segment bases of the step are in flight at once
+        unsigned peers[EXPAND_UNROLL];
+        int base[EXPAND_UNROLL];
+        unsigned cb[EXPAND_UNROLL];
+#pragma unroll
+        for (int k = 0; k < EXPAND_UNROLL; ++k) {
+            const bool rem = FULL ? lab[k] >= 0 : (lab[k] >= 0 && lab[k] < c);
+            const unsigned rm = __ballot_sync(0xffffffffu, rem);
+            peers[k] = rem ? __match_any_sync(rm, lab[k]) : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < EXPAND_UNROLL; ++k) {
+            base[k] = 0;
+            if (peers[k] && lane == __ffs(peers[k]) - 1) base[k] = atomicAdd(&cursor[lab[k]], __popc(peers[k]));
+            if (peers[k]) cb[k] = __ldg(&cbase[lab[k]]);
+        }
+#pragma unroll
+        for (int k = 0; k < EXPAND_UNROLL; ++k) {
+            if (!peers[k]) continue;
+            const int b = __shfl_sync(peers[k], base[k], __ffs(peers[k]) - 1);
+            nbr[cb[k] + (unsigned)(b + __popc(peers[k] & lt))] = c;
+        }
+    }
+}
+
+// One warp's share of the half-edge phase A: as expand_chunk, over the
+// members' upper rows (up_ptr / up_col), with the in-chunk arc offsets summed
+// in the warp and each community's segment base read from cbase.
+template <bool PACK, bool FULL>
+__device__ __forceinline__ void expand_chunk_half(long long p0, long long n, const long long *__restrict__ up_ptr,
+                                                  const int *__restrict__ up_col, const int *__restrict__ labels,
+                                                  const unsigned long long *__restrict__ plab,
+                                                  const int *__restrict__ members, const unsigned *__restrict__ cbase,
+                                                  int *same2, int *cursor, int *__restrict__ nbr, unsigned *offw,
+                                                  long long *rsw, int *cw, unsigned long long keep, int lane)
+{
+    const int nm = (int)min(32LL, n - p0);
+    int u = -2;
+    unsigned d = 0;
+    if (lane < nm) {
+        u = __ldcs(&members[p0 + lane]);
+        rsw[lane] = __ldg(&up_ptr[u]);
+        d = (unsigned)(__ldg(&up_ptr[u + 1]) - rsw[lane]);
+        cw[lane] = ld_hint(&labels[u], keep);
+    }
+    unsigned inc = d;
+#pragma unroll
+    for (int s2 = 1; s2 < 32; s2 <<= 1) {
+        const unsigned t = __shfl_up_sync(0xffffffffu, inc, s2);
+        if (lane >= s2) inc += t;
+    }
+    if (lane < nm) offw[lane] = inc - d;
+    if (lane == nm - 1) offw[nm] = inc;
+    __syncwarp();
+    const int u_prev = __shfl_up_sync(0xffffffffu, u, 1);
+    const bool valid = lane < nm;
+    const bool newrun = valid && (lane == 0 || cw[lane] != cw[lane - 1]);
+    unsigned runs = __ballot_sync(0xffffffffu, newrun);
+    const unsigned segs = __ballot_sync(0xffffffffu, newrun || (valid && u != u_prev + 1));
+    if (__popc(segs) <= EXPAND_MAX_SEGS) {
+        unsigned rem = segs;
+        while (rem) {
+            const int lo = __ffs(rem) - 1;
+            rem &= rem - 1;
+            const int hi = rem ? __ffs(rem) - 1 : nm;
+            const unsigned e_lo = offw[lo], e_hi = offw[hi];
+            if (e_lo == e_hi) continue;
+            const int c = cw[lo];
+            const long long cs = rsw[lo] - (long long)e_lo;  // upper-row index of arc e is cs + e
+            expand_range_half<PACK, FULL>(e_lo, e_hi, c, __ldg(&cbase[c]),
+                                          [cs](unsigned e) { return cs + (long long)e; }, up_col, labels, plab,
+                                          same2, cursor, cbase, nbr, keep, lane);
+        }
+    } else {
+        while (runs) {
+            const int m_lo = __ffs(runs) - 1;
+            runs &= runs - 1;
+            const int m_hi = runs ? __ffs(runs) - 1 : nm;
+            const unsigned e_lo = offw[m_lo], e_hi = offw[m_hi];
+            if (e_lo == e_hi) continue;
+            const int c = cw[m_lo];
+            expand_range_half<PACK, FULL>(
+                e_lo, e_hi, c, __ldg(&cbase[c]),
+                [=](unsigned e) {
+                    const int o = m_lo + upper_bound_smem(offw + m_lo, m_hi - m_lo, e) - 1;
+                    return rsw[o] + (long long)(e - offw[o]);
+                },
+                up_col, labels, plab, same2, cursor, cbase, nbr, keep, lane);
         }
     }
     __syncwarp();

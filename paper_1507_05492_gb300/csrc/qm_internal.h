@@ -24,6 +24,10 @@ struct GraphDev {
     long long max_degree;
     const int *inv = nullptr;  // loaded with QM_REORDER: new node id -> caller's node id
     const float *wt = nullptr; // weighted graph: [n_arcs] edge weights parallel to col
+    // unweighted graphs: the upper rows (arcs (u, v) with v >= u, a self-loop
+    // stored as ~u), for gathering each undirected edge once (ALGO_HALF)
+    const long long *up_ptr = nullptr;  // [n + 1]
+    const int *up_col = nullptr;
     unsigned long long w_lo = 0, w_hi = 0;  // weighted graph: total weight W * 2^43 (128-bit)
 };
 
@@ -40,6 +44,14 @@ struct Shape {
 // run-length encodes it (k_count_sort) instead of hashing it (k_count);
 // gathers as algorithm 1.
 constexpr int ALGO_SORT = 6;
+// Two-phase pipeline whose phase A gathers each undirected edge once, from its
+// lower end, through the graph's upper rows (k_expand_half); otherwise as
+// algorithm 1.  Unsharded, unweighted, unbinned calls on graphs that hold the
+// upper rows; others run algorithm 1.
+constexpr int ALGO_HALF = 7;
+// Untuned calls take ALGO_HALF on graphs in their given node order with more
+// nodes than this.
+constexpr long long HALF_MIN_NODES = 1LL << 26;
 
 // Carving of the dynamic shared memory of a community-major block.
 struct SmemPlan {
@@ -139,11 +151,12 @@ inline int bin_mode_of(int algo, bool weighted) { return (!weighted && (algo == 
 // 1): their label array is well beyond what L2 keeps.
 constexpr long long PACK_MIN_NODES = 1LL << 22;
 // Whether a two-phase call gathers from the packed copy: algorithm 4 always,
-// algorithms 1 and ALGO_SORT on graphs above PACK_MIN_NODES; unweighted graphs
-// and label ids below 2^21 only.
+// algorithms 1, ALGO_SORT and ALGO_HALF on graphs above PACK_MIN_NODES;
+// unweighted graphs and label ids below 2^21 only.
 inline bool packs_labels(int algo, bool weighted, long long n, int K)
 {
-    return !weighted && K <= (1 << 21) && (algo == 4 || ((algo == 1 || algo == ALGO_SORT) && n > PACK_MIN_NODES));
+    return !weighted && K <= (1 << 21) &&
+           (algo == 4 || ((algo == 1 || algo == ALGO_SORT || algo == ALGO_HALF) && n > PACK_MIN_NODES));
 }
 // The autotuner tries the binned gathers on graphs with more nodes than this:
 // their label array (4 bytes a node) is beyond what L2 serves at random.
@@ -199,6 +212,11 @@ int launch_permute_labels(const int *labels, const int *inv, long long n, int P,
 // or minus a CUDA error code (nothing allocated then).
 int reorder_graph(const GraphDev &g, int rounds, int num_sms, cudaStream_t s, long long **row_ptr_out, int **col_out,
                   int **inv_out, int *launches, float **wt_out = nullptr);
+// The upper rows of a symmetric CSR (see GraphDev::up_ptr): device arrays
+// owned by the caller afterwards.  Needs n_arcs < 2^32.  Returns 0, or minus
+// a CUDA error code.
+int build_upper_rows(const GraphDev &g, int num_sms, cudaStream_t s, long long **up_ptr_out, int **up_col_out,
+                     long long *up_arcs, int *launches);
 // qm_label_propagation on the device: `rounds` rounds from the caller's node
 // ids, then the labels present are ranked into [0, K'): out (caller order,
 // n entries) and hist[n] = K' (device).  lab0, lab1: n ints; hist: n + 1;

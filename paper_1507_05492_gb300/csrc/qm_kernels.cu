@@ -796,16 +796,50 @@ __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__re
                                    own, wt, nbrw, wl, offs_s[w], rs_s[w], cw_s[w], keep, lane);
 }
 
+// Half-edge phase A (ALGO_HALF): as k_expand over the upper rows; same2 (the
+// `inter` array) receives 2|E_c^in| and cursor (`inter_hi`) the run lengths.
+template <bool PACK, bool FULL>
+__global__ void __launch_bounds__(EXPAND_THREADS) k_expand_half(const long long *__restrict__ up_ptr,
+                                                                const int *__restrict__ up_col,
+                                                                const int *__restrict__ labels,
+                                                                const unsigned long long *__restrict__ plab,
+                                                                const int *__restrict__ members,
+                                                                const unsigned *__restrict__ cbase, long long n,
+                                                                int *same2, int *cursor, int *__restrict__ nbr,
+                                                                const int *status)
+{
+    __shared__ unsigned offs_s[EXPAND_THREADS / 32][33];
+    __shared__ long long rs_s[EXPAND_THREADS / 32][32];
+    __shared__ int cw_s[EXPAND_THREADS / 32][32];
+    if (*status) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned long long keep = l2_policy_evict_last();
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long p0 = ((long long)blockIdx.x * (blockDim.x >> 5) + w) * 32; p0 < n; p0 += nwarps * 32)
+        expand_chunk_half<PACK, FULL>(p0, n, up_ptr, up_col, labels, plab, members, cbase, same2, cursor, nbr,
+                                      offs_s[w], rs_s[w], cw_s[w], keep, lane);
+}
+
+// Each community's segment base, cbase[c] = aoff[start[c]] (for the appends
+// of the half-edge phase A into other communities' runs).
+__global__ void k_cbase(const int *start, const unsigned *aoff, int K, unsigned *cbase, const int *status)
+{
+    if (*status) return;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < K; c += gridDim.x * blockDim.x)
+        cbase[c] = aoff[start[c]];
+}
+
 #include "qm_binned.cuh"
 
 // One header per non-empty community, sorted into four lists by run length
 // m (the community's packed entries, an upper bound on the distinct keys its
 // count will see): m <= warp_fill for single warps, up to group_fill for groups
 // of warps, up to block_fill for whole blocks of k_count, longer runs for
-// k_count_long.  Appends are warp-aggregated.
+// k_count_long.  Appends are warp-aggregated.  After the half-edge phase A,
+// cut_from_intra (the `inter` array) turns from 2|E_c^in| into the cut arcs.
 __global__ void k_classify(const int *start, const unsigned *aoff, const int *mlen, int K, int warp_fill,
                            int group_fill, int block_fill, RunHdr *big, RunHdr *small, RunHdr *lng, RunHdr *mid,
-                           int *counters, const int *status, Shard own)
+                           int *counters, const int *status, Shard own, int *cut_from_intra)
 {
     if (*status) return;
     const int lane = threadIdx.x & 31;
@@ -820,6 +854,8 @@ __global__ void k_classify(const int *start, const unsigned *aoff, const int *ml
             if (s1 > s0 && own.owns(c)) {
                 const unsigned a0 = aoff[s0];
                 h = RunHdr{c, a0, (unsigned)mlen[c], aoff[s1] - a0};
+                // half-edge phase A left 2|E_c^in| there: the cut arcs are the rest of the volume
+                if (cut_from_intra) cut_from_intra[c] = (int)(h.vol - (unsigned)cut_from_intra[c]);
                 cls = h.m > (unsigned)block_fill ? 2
                       : h.m > (unsigned)group_fill ? 0
                       : h.m > (unsigned)warp_fill ? 3 : 1;
@@ -1591,7 +1627,37 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
         return launch_weighted_tail(g, K, ws, pc, num_sms, s, tr, own, launches);
     }
     const int *packed_len = ws.inter;  // entries of each community's packed run
-    if (ws.bin_pool) {
+    const bool half = sh.algo == ALGO_HALF && g.up_ptr && shard_p == 1 && !ws.bin_pool;
+    if (half) {
+        // each undirected edge gathered once, from its lower end; the scatter
+        // cursors are free now and take the segment bases
+        unsigned *cbase = (unsigned *)ws.cursor;
+        const bool full = pc && pc->qds;
+        const dim3 eg(expand_grid(n, num_sms)), eb(EXPAND_THREADS);
+        TRACE("k_cbase");
+        k_cbase<<<grid_for(K, 256, num_sms, 4), 256, 0, s>>>(ws.start, ws.aoff, K, cbase, ws.status);
+        ++launches;
+        if (ws.plab) {
+            TRACE("k_pack3");
+            k_pack3<<<grid_for((n + 2) / 3, 256, num_sms, 8), 256, 0, s>>>(labels, n, ws.plab, ws.status);
+            ++launches;
+        }
+        TRACE("k_expand_half");
+        if (ws.plab && full)
+            k_expand_half<true, true><<<eg, eb, 0, s>>>(g.up_ptr, g.up_col, labels, ws.plab, ws.members, cbase, n,
+                                                        ws.inter, ws.inter_hi, ws.nbr, ws.status);
+        else if (ws.plab)
+            k_expand_half<true, false><<<eg, eb, 0, s>>>(g.up_ptr, g.up_col, labels, ws.plab, ws.members, cbase, n,
+                                                         ws.inter, ws.inter_hi, ws.nbr, ws.status);
+        else if (full)
+            k_expand_half<false, true><<<eg, eb, 0, s>>>(g.up_ptr, g.up_col, labels, nullptr, ws.members, cbase, n,
+                                                         ws.inter, ws.inter_hi, ws.nbr, ws.status);
+        else
+            k_expand_half<false, false><<<eg, eb, 0, s>>>(g.up_ptr, g.up_col, labels, nullptr, ws.members, cbase, n,
+                                                          ws.inter, ws.inter_hi, ws.nbr, ws.status);
+        ++launches;
+        packed_len = ws.inter_hi;
+    } else if (ws.bin_pool) {
         BinArgs ba;
         ba.pool = ws.bin_pool;
         ba.list = ws.bin_list;
@@ -1648,11 +1714,13 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
     if (sorted)  // warps sort runs up to SORT_WARP_CAP, blocks up to their buffers
         k_classify<<<grid_for(K, 256, num_sms, 4), 256, 0, s>>>(ws.start, ws.aoff, packed_len, K, SORT_WARP_CAP,
                                                                 SORT_WARP_CAP, sp.cap, ws.hdr_big, ws.hdr_small,
-                                                                ws.hdr_long, ws.hdr_mid, ws.counters, ws.status, own);
+                                                                ws.hdr_long, ws.hdr_mid, ws.counters, ws.status, own,
+                                                                half ? ws.inter : nullptr);
     else
         k_classify<<<grid_for(K, 256, num_sms, 4), 256, 0, s>>>(ws.start, ws.aoff, packed_len, K, cp.fill_w,
                                                                 cp.fill_g, cp.fill, ws.hdr_big, ws.hdr_small,
-                                                                ws.hdr_long, ws.hdr_mid, ws.counters, ws.status, own);
+                                                                ws.hdr_long, ws.hdr_mid, ws.counters, ws.status, own,
+                                                                half ? ws.inter : nullptr);
     ++launches;
     CountKArgs a;
     a.x.nbr = ws.nbr;

@@ -11,6 +11,7 @@
 // loaded, and each scoring call gathers its labels through the permutation.
 // Every metric is invariant under renumbering and summed exactly, so the
 // results are bit-identical with and without the reorder.
+#include <algorithm>
 #include <climits>
 #include <cstdio>
 
@@ -258,6 +259,96 @@ int reorder_graph(const GraphDev &g, int rounds, int num_sms, cudaStream_t s, lo
     *col_out = col2;
     *inv_out = inv;
     if (wt_out) *wt_out = wt2;
+    if (launches) *launches = L;
+    return 0;
+}
+
+// ------------------------------------------------------------------ upper rows
+
+// Arcs of node u to itself or to higher ids, one warp per row.
+__global__ void k_up_degrees(const long long *__restrict__ row_ptr, const int *__restrict__ col, long long n,
+                             int *deg)
+{
+    const int lane = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += nw) {
+        const long long rs = __ldg(&row_ptr[u]), re = __ldg(&row_ptr[u + 1]);
+        int cnt = 0;
+        for (long long e = rs + lane; e < re; e += 32) cnt += __ldg(&col[e]) >= u ? 1 : 0;
+        cnt = __reduce_add_sync(0xffffffffu, cnt);
+        if (lane == 0) deg[u] = cnt;
+    }
+}
+
+// Copies those arcs in row order, a self-loop as ~u; one warp per row.
+__global__ void k_up_fill(const long long *__restrict__ row_ptr, const int *__restrict__ col, long long n,
+                          const long long *__restrict__ up_ptr, int *__restrict__ up_col)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += nw) {
+        const long long rs = __ldg(&row_ptr[u]), re = __ldg(&row_ptr[u + 1]);
+        long long at = __ldg(&up_ptr[u]);
+        for (long long e0 = rs; e0 < re; e0 += 32) {
+            const long long e = e0 + lane;
+            const int v = e < re ? __ldg(&col[e]) : -1;
+            const bool keep = e < re && v >= u;
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (keep) up_col[at + __popc(m & lt)] = v == u ? ~v : v;
+            at += __popc(m);
+        }
+    }
+}
+
+int build_upper_rows(const GraphDev &g, int num_sms, cudaStream_t s, long long **up_ptr_out, int **up_col_out,
+                     long long *up_arcs, int *launches)
+{
+    const long long n = g.n;
+    int *deg = nullptr, *tmp = nullptr;
+    long long *up_ptr = nullptr;
+    int *up_col = nullptr;
+    unsigned *total_h = nullptr;
+    auto bad = [&](cudaError_t e) {
+        cudaFree(deg);
+        cudaFree(tmp);
+        cudaFree(up_ptr);
+        cudaFree(up_col);
+        cudaFreeHost(total_h);
+        return e == cudaSuccess ? (int)cudaErrorUnknown : (int)e;
+    };
+    if (g.n_arcs >= (1LL << 32)) return -bad(cudaErrorInvalidValue);
+    cudaError_t e = cudaSuccess;
+    int L = 0;
+    const size_t tmp_elems = scan_tmp_elems(n + 1) + 64;
+    if ((e = cudaMalloc(&deg, (size_t)(n + 1) * 4)) != cudaSuccess) return -bad(e);
+    if ((e = cudaMalloc(&tmp, tmp_elems * 4)) != cudaSuccess) return -bad(e);
+    if ((e = cudaMalloc(&up_ptr, (size_t)(n + 1) * 8)) != cudaSuccess) return -bad(e);
+    if ((e = cudaMallocHost(&total_h, 16)) != cudaSuccess) return -bad(e);
+    if ((e = cudaMemsetAsync(tmp, 0, tmp_elems * 4, s)) != cudaSuccess) return -bad(e);
+    const int g1 = grid_of(n, 512, num_sms, 8), gw = grid_of(n * 32, 256, num_sms, 8);
+    k_up_degrees<<<gw, 256, 0, s>>>(g.row_ptr, g.col, n, deg);
+    ++L;
+    int *status = tmp + tmp_elems - 32, *counters = tmp + tmp_elems - 16;
+    const int l2 = scan_offsets(deg, (int)n, deg, tmp, counters, status, s);  // deg[n] = total
+    if (l2 < 0) return -bad(cudaGetLastError());
+    L += l2;
+    k_widen<<<g1, 512, 0, s>>>((const unsigned *)deg, n, up_ptr);
+    ++L;
+    if ((e = cudaMemcpyAsync(total_h, deg + n, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return -bad(e);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return -bad(e);
+    const long long total = (long long)total_h[0];
+    if ((e = cudaMalloc(&up_col, (size_t)std::max(total, 1LL) * 4)) != cudaSuccess) return -bad(e);
+    k_up_fill<<<gw, 256, 0, s>>>(g.row_ptr, g.col, n, up_ptr, up_col);
+    ++L;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return -bad(e);
+    if ((e = cudaGetLastError()) != cudaSuccess) return -bad(e);
+    cudaFree(deg);
+    cudaFree(tmp);
+    cudaFreeHost(total_h);
+    *up_ptr_out = up_ptr;
+    *up_col_out = up_col;
+    if (up_arcs) *up_arcs = total;
     if (launches) *launches = L;
     return 0;
 }

@@ -465,7 +465,8 @@ def get_tuning(graph: Graph, K: int) -> dict:
 
 def set_tuning(graph: Graph, K: int, threads: int, smem_bytes: int, big_community: int, algorithm: int = 1):
     """algorithm 0: one-kernel community pass; 1: expand + count (two phases); 2-5: variants of 1's
-    gathers; 6: as 1 with a sort + run-length count of each community's labels (include/qm.h)."""
+    gathers; 6: as 1 with a sort + run-length count of each community's labels; 7: as 1 with each
+    undirected edge gathered once (include/qm.h)."""
     t = QmTuning(threads, smem_bytes, big_community, 0, algorithm)
     _check(lib().qm_set_tuning(graph.handle, int(K), ctypes.byref(t)), "qm_set_tuning")
 

@@ -1,10 +1,13 @@
 """The variants of the two-phase pipeline: far-end label gathers through
 destination-window bins (algorithms 2 and 3) and from the copy of the labels
 packed three to a word (algorithm 4; algorithm 5 never packs), and the count of
-each community's run by sorting it (algorithm 6) instead of hashing it.  The
+each community's run by sorting it (algorithm 6) instead of hashing it, and the
+half-edge gathers (algorithm 7).  The
 packed runs hold the same multisets whatever the gathers, and a sorted run has
-the same equal-label stretches as the hashed counts, so every result must
-equal the direct pipeline's bit for bit and match the oracle, on LFR-style graphs with several windows and a
+the same equal-label stretches as the hashed counts; gathering each undirected
+edge once from its lower end (algorithm 7) puts the same entries into the same
+runs; so every result must equal the direct pipeline's bit for bit and match
+the oracle, on LFR-style graphs with several windows and a
 ragged last window, the degenerate partitions, a hub whose run takes the long
 path, isolated nodes, label ids beyond 24 bits, reordered graphs, sharded
 calls and per-community output."""
@@ -31,7 +34,7 @@ def gen():
     return g
 
 
-def by_algo(qm, graph, lab, K, algos=(1, 2, 3, 4, 5, 6), per_community=False):
+def by_algo(qm, graph, lab, K, algos=(1, 2, 3, 4, 5, 6, 7), per_community=False):
     out = {}
     for a in algos:
         qm.set_tuning(graph, K, 512, 96 * 1024, 48, a)
@@ -114,7 +117,7 @@ def test_reordered_sharded_and_host_labels(qm, gen):
     reord = qm.Graph(*to_dev(g.row_ptr, g.col), reorder=True)
     lab = gen.perturb(g.labels, g.K, 0.2, seed=14)
     ref = by_algo(qm, plain, lab.cuda(), g.K, algos=(1,))[1]
-    for a in (2, 3, 4, 5, 6):
+    for a in (2, 3, 4, 5, 6, 7):
         for graph in (plain, reord):
             qm.set_tuning(graph, g.K, 512, 96 * 1024, 48, a)
             assert qm.score(graph, lab.cuda(), g.K) == ref
@@ -133,4 +136,31 @@ def test_weighted_graph_ignores_binning(qm, gen):
     w = ((key * 2654435761) % 1000).to(torch.float32) / 100.0 + 0.25
     graph = qm.Graph(*to_dev(g.row_ptr, g.col), weights=w.cuda())
     res = by_algo(qm, graph, g.labels.cuda(), g.K)
-    assert all(res[a] == res[1] for a in (2, 3, 4, 5, 6))
+    assert all(res[a] == res[1] for a in (2, 3, 4, 5, 6, 7))
+
+
+def test_half_edge_self_loops_and_repeats(qm, gen):
+    """Self-loops (one arc each) and repeated edges, which the library takes
+    unvalidated (the oracle refuses such graphs): the half-edge gathers count a
+    self-loop once inside its community and each copy of an edge once, as the
+    gathers from both ends do."""
+    rp, col = random_graph(3000, 12_000, seed=21)
+    n = 3000
+    src = np.repeat(np.arange(n), np.diff(rp))
+    rng = np.random.default_rng(21)
+    loops = rng.choice(n, 200, replace=False)
+    dup = rng.choice(len(col), 500, replace=False)
+    a, b = src[dup], col[dup].astype(np.int64)
+    src2 = np.concatenate([src, loops, a, b])
+    dst2 = np.concatenate([col.astype(np.int64), loops, b, a])
+    order = np.lexsort((dst2, src2))
+    src2, dst2 = src2[order], dst2[order]
+    rp2 = np.zeros(n + 1, np.int64)
+    np.add.at(rp2, src2 + 1, 1)
+    rp2 = np.cumsum(rp2)
+    col2 = dst2.astype(np.int32)
+    graph = qm.Graph(*to_dev(rp2, col2))
+    for lab, K in ((rng.integers(0, 40, n).astype(np.int32), 40), (rng.integers(0, 900, n).astype(np.int32), 900)):
+        res = by_algo(qm, graph, torch.from_numpy(lab).cuda(), K, algos=(1, 7))
+        assert res[7] == res[1], K
+        assert res[1]["intra_edges_total"] > 0 and res[1]["cut_edges_total"] > 0
