@@ -529,8 +529,18 @@ static qm_status load_impl(const int64_t *row_ptr, const int32_t *col, const flo
     g->row_ptr = nullptr;
     g->col = nullptr;
     cudaError_t e = cudaMalloc(&g->row_ptr, (size_t)(n_nodes + 1) * 8);
+    if (e == cudaErrorMemoryAllocation) {  // cached scratch blocks may hold the memory: free them, retry
+        cudaGetLastError();
+        g_pool.trim();
+        e = cudaMalloc(&g->row_ptr, (size_t)(n_nodes + 1) * 8);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(row_ptr)");
     e = cudaMalloc(&g->col, (size_t)n_arcs * 4);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        g_pool.trim();
+        e = cudaMalloc(&g->col, (size_t)n_arcs * 4);
+    }
     if (e != cudaSuccess) {
         cudaFree(g->row_ptr);
         return cuda_fail(e, "cudaMalloc(col)");
@@ -623,7 +633,12 @@ static qm_status load_impl(const int64_t *row_ptr, const int32_t *col, const flo
         long long *row2 = nullptr;
         int *col2 = nullptr, *inv = nullptr, L = 0;
         float *wt2 = nullptr;
-        const int r = reorder_graph(g->d, QM_REORDER_ROUNDS, num_sms_of(dev), s, &row2, &col2, &inv, &L, &wt2);
+        int r = reorder_graph(g->d, QM_REORDER_ROUNDS, num_sms_of(dev), s, &row2, &col2, &inv, &L, &wt2);
+        if (r == -(int)cudaErrorMemoryAllocation) {  // cached scratch blocks may hold the memory: free them, retry
+            cudaGetLastError();
+            g_pool.trim();
+            r = reorder_graph(g->d, QM_REORDER_ROUNDS, num_sms_of(dev), s, &row2, &col2, &inv, &L, &wt2);
+        }
         if (r != 0) {
             cleanup();
             return cuda_fail((cudaError_t)(-r), "graph reorder");
@@ -648,7 +663,12 @@ static qm_status load_impl(const int64_t *row_ptr, const int32_t *col, const flo
         // the upper rows, for gathering each undirected edge once (ALGO_HALF)
         long long up_arcs = 0;
         int L = 0;
-        const int r = build_upper_rows(g->d, num_sms_of(dev), s, &g->up_ptr, &g->up_col, &up_arcs, &L);
+        int r = build_upper_rows(g->d, num_sms_of(dev), s, &g->up_ptr, &g->up_col, &up_arcs, &L);
+        if (r == -(int)cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            g_pool.trim();
+            r = build_upper_rows(g->d, num_sms_of(dev), s, &g->up_ptr, &g->up_col, &up_arcs, &L);
+        }
         if (r != 0) {
             cleanup();
             cudaFree(g->inv);
@@ -1020,7 +1040,7 @@ struct BatchDesc {
 };
 
 // Runs the two-phase batched pipeline (qm_batched.h) over `d.items`, in waves
-// that keep the scratch within a quarter of free memory and the unit counts
+// that keep the scratch within an eighth of free memory and the unit counts
 // within int range.  Labels must already be on the device and every item's arc
 // count at most BATCH_UNITS_MAX_ARCS.
 static qm_status run_batched_units(int dev, BatchDesc &d, const Shape &sh0, qm_quality *out_q, qm_compare *out_c,
@@ -1040,7 +1060,7 @@ static qm_status run_batched_units(int dev, BatchDesc &d, const Shape &sh0, qm_q
     auto scratch = [&](int per) { return batch_units_bytes(per, d.n_max, a_max, d.k_max, d.kt_max, cells); };
     int per = count;
     while (per > 1 && ((long long)per * std::max<long long>(d.k_max, (d.n_max + 31) / 32) >= (1LL << 30) ||
-                       scratch(per) > free_b / 4))
+                       scratch(per) > free_b / 8))
         per = (per + 1) / 2;
     const int waves = (count + per - 1) / per;
     const size_t items_b = al256((size_t)count * sizeof(BatchItem));

@@ -59,6 +59,8 @@ def test_ten_million_nodes_against_whole_oracle(qm, oracle_mod):
 def test_hundred_million_nodes_against_whole_oracle(qm, oracle_mod):
     from helpers import check_compare
     from paper_1507_05492_gb300 import gen
+    qm.release_cache()  # scratch cached by earlier tests
+    torch.cuda.empty_cache()
     g = gen.lfr_graph(gen.config_params("lfr100m"), device="cuda")
     found = gen.perturb(g.labels, g.K, 0.2, seed=9)
     rp, col, lab = g.row_ptr.cpu().numpy(), g.col.cpu().numpy(), g.labels.cpu().numpy()
