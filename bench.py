@@ -375,6 +375,8 @@ def bench_headline(args, world, rank, local):
     torch.cuda.empty_cache()
     stream = torch.cuda.current_stream()
 
+    if args.algorithm is not None:
+        qm.set_tuning(graph, K, 512, 96 * 1024, 48, args.algorithm)
     # warm-up (also selects the launch shape)
     for _ in range(args.warmup):
         q = qm.score(graph, labels, K)
@@ -839,6 +841,9 @@ def main():
                     help="time only the metrics with ground truth (Eqs. 1-7) on the workload")
     ap.add_argument("--only-batched", action="store_true",
                     help="time only the batched launch (--batch candidates, default launch shape)")
+    ap.add_argument("--algorithm", type=int, default=None,
+                    help="score with this tuning algorithm (include/qm.h; default launch shape) instead of "
+                         "the untuned default")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

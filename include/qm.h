@@ -256,12 +256,18 @@ qm_status qm_compare_covers(const int64_t *truth_ptr, const int32_t *truth_memb,
                             int64_t n_nodes, qm_mem where, qm_compare *out, void *stream);
 
 /*
- * Batched calls.  On graphs of up to 2^21 nodes the items run in one
- * persistent kernel, one block per item, replayed from a captured CUDA graph.
- * On larger graphs one block per item would not fill the GPU, so every item
- * runs the plain full-GPU pipelines one after another, all captured into one
- * CUDA graph launched once, with one copy of all results at the end.  Either
- * way each result is bit-identical to the plain call on that item.
+ * Batched calls.  On graphs of up to 2^21 nodes and 2^24 - 1 arcs the items
+ * run the two-phase pipeline of the plain path with every phase spread over
+ * all items at once (label histograms and counting sort, far-end gathers,
+ * per-community counts with direct or hashed counters, contingency cells, then
+ * the FP64 terms of all items), replayed from a captured CUDA graph; the
+ * scratch grows with the items (about 11 MB per item of 10^5 nodes and 10^6
+ * edges), so large batches run in waves of at most an eighth of free device
+ * memory.  Denser graphs of up to 2^21 nodes run one persistent kernel, one
+ * block per item.  On larger graphs every item runs the plain full-GPU
+ * pipelines one after another, all captured into one CUDA graph launched
+ * once, with one copy of all results at the end.  Every way each result is
+ * bit-identical to the plain call on that item.
  *
  * qm_score_partitions_batched -- score P partitions of one graph in a single
  * launch.
@@ -397,16 +403,18 @@ qm_status qm_get_tuning(const qm_graph *g, int32_t K, qm_tuning *t);
 qm_status qm_set_tuning(const qm_graph *g, int32_t K, const qm_tuning *t);
 
 /*
- * The same for the batched kernel (qm_score_partitions_batched,
+ * The same for the batched calls (qm_score_partitions_batched,
  * qm_evaluate_partitions_batched), keyed by the batch's largest K.
- * qm_autotune_batched times candidate shapes (threads, shared memory, the
- * block/warp community-size split) on the caller's batch, exactly as
- * qm_evaluate_partitions_batched (truth != NULL) or
+ * qm_autotune_batched times candidate shapes on the caller's batch, exactly
+ * as qm_evaluate_partitions_batched (truth != NULL) or
  * qm_score_partitions_batched (truth == NULL) would run it, and caches the
- * fastest; the batch's results are the same bits for every shape.  The
- * algorithm field is ignored (the batched kernel has one pipeline), and the
- * batched kernel takes at most 512 threads a block (qm_set_batch_tuning
- * returns QM_EINVAL for more).
+ * fastest; the batch's results are the same bits for every shape.  The shape
+ * sets the threads and shared memory of the per-community counting and cells
+ * kernels (a warp's share of the shared memory bounds the runs it counts and
+ * the communities it compares; larger ones go to whole blocks); the
+ * block/warp community-size split applies to the one-block-per-item kernel
+ * only.  The algorithm field is ignored, and the batched kernels take at most
+ * 512 threads a block (qm_set_batch_tuning returns QM_EINVAL for more).
  */
 qm_status qm_autotune_batched(const qm_graph *g, const int32_t *labels, int32_t P, const int32_t *K,
                               const int32_t *truth, int32_t k_truth, qm_mem where, void *stream,
