@@ -1152,9 +1152,10 @@ static qm_status run_batched_units(int dev, BatchDesc &d, const Shape &sh0, qm_q
     trace_collect();
     const int *st_h = (const int *)(H + items_b + q_b + c_b);
     for (int i = 0; i < count; ++i) {
-        if (st_h[i] & 1) return fail(QM_EINVAL, "item " + std::to_string(i) + ": a label lies outside its range");
-        if (st_h[i] & 2) return fail(QM_EOVERFLOW, "item " + std::to_string(i) + ": a community borders too many communities");
-        if (st_h[i]) return fail(QM_ECUDA, "item " + std::to_string(i) + ": device status " + std::to_string(st_h[i]));
+        const std::string item = "item " + std::to_string(i);
+        if (st_h[i] & 1) return fail(QM_EINVAL, item + ": a label lies outside its range");
+        if (st_h[i] & 2) return fail(QM_EOVERFLOW, item + ": a community borders too many communities");
+        if (st_h[i]) return fail(QM_ECUDA, item + ": device status " + std::to_string(st_h[i]));
     }
     const qm_quality *qh = (const qm_quality *)(H + items_b);
     const qm_compare *ch = (const qm_compare *)(H + items_b + q_b);

@@ -353,7 +353,7 @@ BatchUnits carve_batch_units(void *base, int count, long long n_max, long long a
     b.tpre = (int *)take((C + 1) * 4);
     b.cpre = (int *)take((C + 1) * 4);
     b.kpre = (int *)take((C + 1) * 4);
-    b.logt = (double *)take((LOGT_MAX + 1) * 8);
+    b.logt = (double *)take(LOGT_WORDS * 8);
     b.zero = p;
     b.cv = (unsigned long long *)take(C * Kx * 8);
     b.inter = (int *)take(C * Kx * 4);
@@ -416,12 +416,14 @@ __device__ __forceinline__ unsigned long long bu_key(int it, int c)
 
 __device__ __forceinline__ bool bu_dead(const BatchItem &I) { return *(volatile int *)I.status != 0; }
 
-// log(N / i) for i = 1 .. LOGT_MAX (the same expression as the plain
-// comparison's table, so the same bits).
+// log(N / i) and i / N for i = 1 .. LOGT_MAX (the same expressions as the
+// plain comparison's tables, so the same bits).
 __global__ void k_bu_logt(double *logt, long long N)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= LOGT_MAX; i += gridDim.x * blockDim.x)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= LOGT_MAX; i += gridDim.x * blockDim.x) {
         logt[i] = i == 0 ? 0.0 : log_ratio(N, i);
+        logt[LOGT_MAX + 1 + i] = nmi_over(i, N);
+    }
 }
 
 // The candidate holding unit u of a prefix (pre[p] <= u < pre[p + 1]), cur a guess.
@@ -681,7 +683,8 @@ __device__ __forceinline__ void count_run_agg(const CountCtx &x, const RunHdr &h
                 for (int k = 0; k < BU_CU; ++k) {
                     const unsigned e = e0 + (unsigned)lane + 32u * k;
                     lv[k] = e < m ? __ldcs(&src[e]) : -1;
-                    if (lv[k] >= 0 && (!QM_CHK(lv[k], x.K, 6) || lv[k] < c || (R > 1 && tab_split((unsigned)lv[k], R) != r)))
+                    if (lv[k] >= 0 &&
+                        (!QM_CHK(lv[k], x.K, 6) || lv[k] < c || (R > 1 && tab_split((unsigned)lv[k], R) != r)))
                         lv[k] = -1;
                 }
 #pragma unroll
@@ -1074,8 +1077,10 @@ __global__ void __launch_bounds__(BU_FIN_THREADS) k_bu_fin(const BatchItem *item
                 atomicMax(&S.rowmax_r[cl.a], (unsigned long long)__double_as_longlong(f_ratio(n, na, nb)));
                 const double l1 = cell_log(n, na, nb);
                 acc.vi += fp_from_double(vi_term_l(n, l1), SC_VI);
-                const double lr = (logt && n <= LOGT_MAX) ? __ldg(&logt[n]) : log_ratio(x.N, n);
-                acc.hnum += fp_from_double(nmi_num_term_l(n, x.N, l1, lr), SC_H);
+                const bool tab = logt && n <= LOGT_MAX;
+                const double lr = tab ? __ldg(&logt[n]) : log_ratio(x.N, n);
+                const double q = tab ? __ldg(&logt[LOGT_MAX + 1 + n]) : nmi_over(n, x.N);
+                acc.hnum += fp_from_double(nmi_num_term_q(q, l1, lr), SC_H);
             }
             for (int c = tid; c < I.K; c += T) {
                 const long long nb = __ldcg(&S.start[c + 1]) - __ldcg(&S.start[c]);

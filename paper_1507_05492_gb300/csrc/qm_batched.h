@@ -45,7 +45,7 @@ struct BatchUnits {
     int *kpre;                     // [count + 1] prefix of the candidates' label-id counts
     unsigned long long *big_s;     // [units] (candidate << 32 | community) counted by whole blocks
     unsigned long long *big_c;     // [units] compared by whole blocks
-    double *logt;                  // [LOGT_MAX + 1] log(N / i) for N = logt_n
+    double *logt;                  // [LOGT_WORDS] log(N / i), then i / N, for N = logt_n
     int *ncells;                   // [count] cells written (zeroed)
     unsigned long long *gcell;     // [count][2] column maxima and cell counts of the comparisons (zeroed)
     int *ctr;                      // [16] list lengths and claim counters (zeroed)
@@ -71,7 +71,7 @@ BatchUnits carve_batch_units(void *base, int count, long long n_max, long long a
 int launch_batch_units(const BatchItem *items_dev, int count, const BatchUnits &b, long long logt_n,
                        const Shape &sh, int num_sms, cudaStream_t s);
 
-// Fills a wave's log table, log(N / i) for i = 1 .. LOGT_MAX (stream-ordered).
+// Fills a wave's tables, log(N / i) and i / N for i = 1 .. LOGT_MAX (stream-ordered).
 void launch_batch_logt(double *logt, long long N, cudaStream_t s);
 
 // Resident blocks per SM of the count and cells kernels for a launch shape.

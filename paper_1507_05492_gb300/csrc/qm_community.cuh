@@ -51,7 +51,7 @@ struct CompareCtx {
     long long N;
     int ka, kb;
     int *err;
-    const double *logt = nullptr;  // log(N / n) for 1 <= n <= LOGT_MAX (plain comparison), or null
+    const double *logt = nullptr;  // plain comparison: log(N / n), then n / N, 1 <= n <= LOGT_MAX; or null
     int *size_a_acc = nullptr;     // plain comparison: |c| summed from the cells (zeroed), or null
 };
 

@@ -400,11 +400,24 @@ __device__ __forceinline__ double log_ratio(long long N, long long n)
 // Eq. (1) term n log(n^2 / (n_a n_b)) from the cell's logarithm l1.
 __device__ __forceinline__ double vi_term_l(long long n, double l1) { return __dmul_rn((double)n, l1); }
 
-// Eq. (2) numerator term (n/N) log(n N / (n_a n_b)) = (n/N) (l1 + log(N/n)).
+// Eq. (2) numerator term (n/N) log(n N / (n_a n_b)) = (n/N) (l1 + log(N/n)),
+// from the quotient n/N (nmi_over: the same division, tabulated by callers that
+// form many cells of one N).
+__device__ __forceinline__ double nmi_over(long long n, long long N) { return __ddiv_rn((double)n, (double)N); }
+
+__device__ __forceinline__ double nmi_num_term_q(double n_over_N, double l1, double log_n_over)
+{
+    return __dmul_rn(n_over_N, __dadd_rn(l1, log_n_over));
+}
+
 __device__ __forceinline__ double nmi_num_term_l(long long n, long long N, double l1, double log_n_over)
 {
-    return __dmul_rn(__ddiv_rn((double)n, (double)N), __dadd_rn(l1, log_n_over));
+    return nmi_num_term_q(nmi_over(n, N), l1, log_n_over);
 }
+
+// A comparison's tables for cells and communities of at most LOGT_MAX nodes:
+// log(N / i) at [i] and i / N at [LOGT_MAX + 1 + i], i = 1 .. LOGT_MAX.
+constexpr int LOGT_WORDS = 2 * (LOGT_MAX + 1);
 
 // Eq. (2) denominator term (n_c/N) log(n_c/N) of one community.
 __device__ __forceinline__ double entropy_term(long long nc, long long N)

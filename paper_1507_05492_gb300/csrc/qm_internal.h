@@ -128,7 +128,7 @@ struct CompareWs {
     int *members;               // [n]
     qmk::Cell *cells;  // contingency cells of the counting pass ([n])
     int *scan_tmp;
-    double *logt;               // [LOGT_MAX + 1] log(N / n)
+    double *logt;               // [LOGT_WORDS] log(N / n), then n / N (LOGT_MAX + 1 each)
     size_t zero_bytes;
     size_t bytes;  // total bytes carved (compare_ws_bytes)
 };

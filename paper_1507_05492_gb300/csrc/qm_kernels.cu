@@ -169,7 +169,7 @@ CompareWs carve_compare_ws(void *base, long long n, int ka, int kb)
     w.scan_tmp = (int *)p;
     p += align_up((size_t)(scan_tiles(kb) + 1) * 4, 256);
     w.logt = (double *)p;
-    p += align_up((size_t)(LOGT_MAX + 1) * 8, 256);
+    p += align_up((size_t)LOGT_WORDS * 8, 256);
     w.bytes = (size_t)(p - (char *)base);
     return w;
 }
@@ -615,18 +615,23 @@ __global__ void k_compare_cells(CompareCtx x, const Cell *cells, const int *coun
         atomicMax(&x.rowmax_r[c.a], (unsigned long long)__double_as_longlong(f_ratio(n, na, nb)));
         const double l1 = cell_log(n, na, nb);
         acc.vi += fp_from_double(vi_term_l(n, l1), SC_VI);
-        acc.hnum += fp_from_double(nmi_num_term_l(n, x.N, l1, n <= LOGT_MAX ? __ldg(&x.logt[n]) : log_ratio(x.N, n)),
+        const bool tab = n <= LOGT_MAX;
+        acc.hnum += fp_from_double(nmi_num_term_q(tab ? __ldg(&x.logt[LOGT_MAX + 1 + n]) : nmi_over(n, x.N), l1,
+                                                  tab ? __ldg(&x.logt[n]) : log_ratio(x.N, n)),
                                    SC_H);
     }
     flush_compare(acc, g, red);
 }
 
-// log(N / n) for n = 1 .. LOGT_MAX (contingency cells and community sizes are
-// mostly small, so k_compare_cells then takes one logarithm per cell).
+// log(N / n) and n / N for n = 1 .. LOGT_MAX (contingency cells and community
+// sizes are mostly small, so k_compare_cells then takes one logarithm and no
+// division per cell at most).
 __global__ void k_log_table(double *logt, long long N)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= LOGT_MAX; i += gridDim.x * blockDim.x)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= LOGT_MAX; i += gridDim.x * blockDim.x) {
         logt[i] = i == 0 ? 0.0 : log_ratio(N, i);
+        logt[LOGT_MAX + 1 + i] = nmi_over(i, N);
+    }
 }
 
 // Column side of every found community b: C(|b|, 2), its entropy term, the count.
