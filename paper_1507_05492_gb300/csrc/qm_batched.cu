@@ -540,6 +540,88 @@ __global__ void __launch_bounds__(256) k_bu_scatter(const BatchItem *items, int 
     }
 }
 
+// A warp's share of phase A for the batched pipeline: expand_chunk, except
+// that when the chunk's members are not a few runs of consecutive node ids
+// (the usual case for candidate partitions), the owner of each arc of the
+// chunk is tabulated once (each lane writes its member's index over its arc
+// range, up to BU_OWN_CAP arcs) instead of searched for arc by arc.
+constexpr int BU_OWN_CAP = 2048;
+
+__device__ __forceinline__ void bu_expand_chunk(long long p0, long long n, const long long *__restrict__ row_ptr,
+                                                const int *__restrict__ col, const int *__restrict__ labels,
+                                                const int *__restrict__ members, const unsigned *__restrict__ aoff,
+                                                const int *__restrict__ start, int *inter, int *inter_hi,
+                                                int *__restrict__ nbr, unsigned *offw, long long *rsw, int *cw,
+                                                unsigned char *own, unsigned long long keep, int lane)
+{
+    const int nm = (int)min(32LL, n - p0);
+    const unsigned base = __ldg(&aoff[p0]);
+    int u = -2;
+    if (lane < nm) {
+        u = __ldcs(&members[p0 + lane]);
+        offw[lane] = __ldg(&aoff[p0 + lane]) - base;
+        rsw[lane] = __ldg(&row_ptr[u]);
+        cw[lane] = ld_hint(&labels[u], keep);
+    }
+    if (lane == 0) offw[nm] = __ldg(&aoff[p0 + nm]) - base;
+    __syncwarp();
+    const int u_prev = __shfl_up_sync(0xffffffffu, u, 1);
+    const bool valid = lane < nm;
+    const bool newrun = valid && (lane == 0 || cw[lane] != cw[lane - 1]);
+    unsigned runs = __ballot_sync(0xffffffffu, newrun);
+    const unsigned segs = __ballot_sync(0xffffffffu, newrun || (valid && u != u_prev + 1));
+    u128 w_in = 0, w_out = 0;
+    if (__popc(segs) <= EXPAND_MAX_SEGS) {
+        unsigned rem = segs;
+        while (rem) {
+            const int lo = __ffs(rem) - 1;
+            rem &= rem - 1;
+            const int hi = rem ? __ffs(rem) - 1 : nm;
+            const unsigned e_lo = offw[lo], e_hi = offw[hi];
+            if (e_lo == e_hi) continue;
+            const int c = cw[lo];
+            const unsigned cbase = __ldg(&aoff[__ldg(&start[c])]);
+            const long long cs = rsw[lo] - (long long)e_lo;  // CSR index of arc e is cs + e
+            expand_range<false, false, true>(e_lo, e_hi, c, cbase, [cs](unsigned e) { return cs + (long long)e; },
+                                             col, labels, nullptr, inter, inter_hi, nbr, keep, lane, nullptr, nullptr,
+                                             w_in, w_out);
+        }
+    } else {
+        const bool tab = offw[nm] <= (unsigned)BU_OWN_CAP;
+        if (tab) {
+            const unsigned a = lane < nm ? offw[lane] : 0u, z = lane < nm ? offw[lane + 1] : 0u;
+            for (unsigned e = a; e < z; ++e) own[e] = (unsigned char)lane;
+            __syncwarp();
+        }
+        while (runs) {
+            const int m_lo = __ffs(runs) - 1;
+            runs &= runs - 1;
+            const int m_hi = runs ? __ffs(runs) - 1 : nm;
+            const unsigned e_lo = offw[m_lo], e_hi = offw[m_hi];
+            if (e_lo == e_hi) continue;
+            const int c = cw[m_lo];
+            const unsigned cbase = __ldg(&aoff[__ldg(&start[c])]);
+            if (tab)
+                expand_range<false, false, true>(
+                    e_lo, e_hi, c, cbase,
+                    [=](unsigned e) {
+                        const int o = own[e];
+                        return rsw[o] + (long long)(e - offw[o]);
+                    },
+                    col, labels, nullptr, inter, inter_hi, nbr, keep, lane, nullptr, nullptr, w_in, w_out);
+            else
+                expand_range<false, false, true>(
+                    e_lo, e_hi, c, cbase,
+                    [=](unsigned e) {
+                        const int o = m_lo + upper_bound_smem(offw + m_lo, m_hi - m_lo, e) - 1;
+                        return rsw[o] + (long long)(e - offw[o]);
+                    },
+                    col, labels, nullptr, inter, inter_hi, nbr, keep, lane, nullptr, nullptr, w_in, w_out);
+        }
+    }
+    __syncwarp();
+}
+
 // Phase A over every scored candidate: warp by warp over (candidate, 32
 // member positions) units, in unit order, so the warps in flight share a few
 // candidates' label arrays in L2.
@@ -548,6 +630,7 @@ __global__ void __launch_bounds__(EXPAND_THREADS) k_bu_expand(const BatchItem *i
     __shared__ unsigned offs_s[EXPAND_THREADS / 32][33];
     __shared__ long long rs_s[EXPAND_THREADS / 32][32];
     __shared__ int cw_s[EXPAND_THREADS / 32][32];
+    __shared__ unsigned char own_s[EXPAND_THREADS / 32][BU_OWN_CAP];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned long long keep = l2_policy_evict_last();
     const int units = __ldg(&b.cpre[count]);
@@ -559,9 +642,8 @@ __global__ void __launch_bounds__(EXPAND_THREADS) k_bu_expand(const BatchItem *i
         if (!(I.flags & 1) || bu_dead(I)) continue;
         const BuSlice S = bu_slice(b, it);
         const long long p0 = (long long)(u - __ldg(&b.cpre[it])) * 32;
-        expand_chunk<false, false, true>(p0, I.n, I.row_ptr, I.col, I.labels, nullptr, S.members, S.aoff, S.start,
-                                         S.inter, S.inter_hi, S.nbr, Shard{0, 1}, nullptr, nullptr, nullptr,
-                                         offs_s[w], rs_s[w], cw_s[w], keep, lane);
+        bu_expand_chunk(p0, I.n, I.row_ptr, I.col, I.labels, S.members, S.aoff, S.start, S.inter, S.inter_hi, S.nbr,
+                        offs_s[w], rs_s[w], cw_s[w], own_s[w], keep, lane);
     }
 }
 
@@ -739,9 +821,16 @@ __device__ __forceinline__ void count_run_direct(const CountCtx &x, const RunHdr
 {
     const unsigned m = h.m;
     const int c = h.c;
-    for (unsigned e = (unsigned)gtid; e < m; e += (unsigned)gsize) {
-        const int lv = __ldg(&src[e]);
-        if (lv > c && QM_CHK(lv, x.K, 6)) atomicAdd(&w16[lv >> 1], 1u << ((lv & 1) << 4));
+    for (unsigned e0 = (unsigned)gtid; e0 < m; e0 += (unsigned)gsize * BU_CU) {
+        int lv[BU_CU];
+#pragma unroll
+        for (int k = 0; k < BU_CU; ++k) {
+            const unsigned e = e0 + (unsigned)gsize * k;
+            lv[k] = e < m ? __ldg(&src[e]) : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < BU_CU; ++k)
+            if (lv[k] > c && QM_CHK(lv[k], x.K, 6)) atomicAdd(&w16[lv[k] >> 1], 1u << ((lv[k] & 1) << 4));
     }
     group_sync_n(gsize);
     unsigned long long slots = 0, cnt2 = 0;
