@@ -1102,6 +1102,7 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS, 1) k_bu_cells(BuArgs a)
 }
 
 constexpr int BU_FIN_THREADS = 256;
+constexpr int BU_CELLS_SMEM = 48 * 1024;  // shared memory of a k_bu_cells block at most
 
 // Row maximum of the Eq. (3) ratio 2 n / (n_a + n_b) over a truth community's
 // cells, kept as the exact fraction (n << 32 | n_a + n_b) of the largest
@@ -1267,9 +1268,16 @@ int launch_batch_units(const BatchItem *items_dev, int count, const BatchUnits &
         ++L;
     }
     if (bb.cells) {
+        // a found community's distinct truth labels are at most its members,
+        // so the cells need smaller tables than the counts: more blocks per SM
+        const int smem_c = std::min(sh.smem_bytes, BU_CELLS_SMEM);
+        a.plan = plan_smem(sh.threads, smem_c);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bu_cells, sh.threads, smem_c);
+        const int grid_c = num_sms * std::max(1, per_sm);
         for (int ph = 0; ph < 2; ++ph) {
             a.phase = ph;
-            k_bu_cells<<<grid, sh.threads, sh.smem_bytes, s>>>(a);
+            k_bu_cells<<<grid_c, sh.threads, smem_c, s>>>(a);
             ++L;
         }
     }
