@@ -344,6 +344,16 @@ qm_status qm_release_cache(void);
 qm_status qm_debug_set_stage_wait(int64_t polls);
 
 /*
+ * qm_debug_set_batch_wave -- test hook for the batched calls (no counterpart
+ * in the paper).  Large batches of the two-phase batched pipeline run in waves
+ * of items sized by free device memory; items > 0 caps every later call's wave
+ * at that many items (so that a test can drive the wave loop with a small
+ * batch), 0 restores the automatic size.  Results do not depend on it.
+ * Errors: QM_EINVAL for items < 0.
+ */
+qm_status qm_debug_set_batch_wave(int32_t items);
+
+/*
  * Tuning.  qm_autotune times the candidate launch shapes of the scoring and
  * batched kernels on the given inputs and caches the fastest per size bucket
  * (log2 n_nodes, log2 n_arcs, log2 K).  qm_get_tuning reports the shape the

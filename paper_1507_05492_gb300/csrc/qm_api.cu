@@ -249,6 +249,7 @@ struct GraphKey {
 
 static std::mutex g_graph_mu;
 static std::map<GraphKey, cudaGraphExec_t> g_graphs;
+static std::atomic<int> g_batch_wave{0};  // qm_debug_set_batch_wave: wave size cap of the batched pipeline
 
 // A captured CUDA graph of one plain scoring call on a small graph (see
 // score_impl), valid for the scratch blocks and the graph it was captured with.
@@ -1062,6 +1063,7 @@ static qm_status run_batched_units(int dev, BatchDesc &d, const Shape &sh0, qm_q
     while (per > 1 && ((long long)per * std::max<long long>(d.k_max, (d.n_max + 31) / 32) >= (1LL << 30) ||
                        scratch(per) > free_b / 8))
         per = (per + 1) / 2;
+    if (const int cap = g_batch_wave.load(); cap > 0) per = std::min(per, cap);
     const int waves = (count + per - 1) / per;
     const size_t items_b = al256((size_t)count * sizeof(BatchItem));
     const size_t q_b = al256((size_t)count * sizeof(qm_quality));
@@ -1706,6 +1708,13 @@ qm_status qm_compare_covers(const int64_t *truth_ptr, const int32_t *truth_memb,
     st = cover_status(*(int *)pin.ptr());
     if (st != QM_OK) return st;
     std::memcpy(out, pin.ptr() + 256, sizeof(qm_compare));
+    return QM_OK;
+}
+
+qm_status qm_debug_set_batch_wave(int32_t items)
+{
+    if (items < 0) return fail(QM_EINVAL, "items must be >= 0");
+    g_batch_wave.store(items);
     return QM_OK;
 }
 

@@ -97,6 +97,7 @@ def _signatures(lib):
         "qm_workspace_bytes": [_P, _I32, _I32, _I32, _P],
         "qm_release_cache": [],
         "qm_debug_set_stage_wait": [_I64],
+        "qm_debug_set_batch_wave": [_I32],
         "qm_score_cover": [_P, _P, _P, _I32, S, _P, _P],
         "qm_compare_covers": [_P, _P, _I32, _P, _P, _I32, _I64, S, _P, _P],
         "qm_autotune": [_P, _P, _I32, S, _P, _P],
@@ -580,6 +581,12 @@ def trace_read() -> list[tuple[str, float]]:
 
 def release_cache():
     _check(lib().qm_release_cache(), "qm_release_cache")
+
+
+def debug_set_batch_wave(items: int):
+    """qm_debug_set_batch_wave: cap the batched pipeline's waves at `items`
+    items for later calls (0: automatic).  A test hook for the wave loop."""
+    _check(lib().qm_debug_set_batch_wave(int(items)), "qm_debug_set_batch_wave")
 
 
 def debug_set_stage_wait(polls: int):

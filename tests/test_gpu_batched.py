@@ -152,6 +152,24 @@ def test_batched_count_paths(qm, setup):
             assert oc[p] == qm.compare(truth, M[p], g.K, ks[p]), (shape, p)
 
 
+def test_batched_waves(qm, setup):
+    """Batches larger than a wave run wave after wave (tables, counters and
+    prefixes reset per wave) with the same bits as one wave."""
+    g, graph, L, Ks = setup
+    truth = g.labels.cuda()
+    ref_q, ref_c = qm.evaluate_batched(graph, L.cuda(), Ks, truth, g.K)
+    try:
+        for items in (1, 5, 7):
+            qm.debug_set_batch_wave(items)
+            oq, oc = qm.evaluate_batched(graph, L.cuda(), Ks, truth, g.K)
+            assert oq == ref_q and oc == ref_c, items
+            assert qm.score_batched(graph, L.cuda(), Ks) == ref_q, items
+    finally:
+        qm.debug_set_batch_wave(0)
+    with pytest.raises(qm.QmError):
+        qm.debug_set_batch_wave(-1)
+
+
 def test_dense_graph_batches(qm, oracle_mod):
     """A graph whose arcs exceed the two-phase batched pipeline's run limit
     (2^24 - 1) is batched by the one-block-per-item kernel: the same bits as
