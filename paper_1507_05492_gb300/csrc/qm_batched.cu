@@ -1104,22 +1104,6 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS, 1) k_bu_cells(BuArgs a)
 constexpr int BU_FIN_THREADS = 256;
 constexpr int BU_CELLS_SMEM = 48 * 1024;  // shared memory of a k_bu_cells block at most
 
-// Row maximum of the Eq. (3) ratio 2 n / (n_a + n_b) over a truth community's
-// cells, kept as the exact fraction (n << 32 | n_a + n_b) of the largest
-// n / (n_a + n_b), compared by cross-multiplication (both below 2^31, so the
-// products fit 64 bits): the FP64 division is then taken once per row instead
-// of once per cell.
-__device__ __forceinline__ void bu_rowmax_ratio(unsigned long long *slot, unsigned long long n, unsigned long long d)
-{
-    const unsigned long long key = (n << 32) | d;
-    unsigned long long cur = *(volatile unsigned long long *)slot;
-    while (cur == 0ull || n * (cur & 0xFFFFFFFFull) > (cur >> 32) * d) {
-        const unsigned long long prev = atomicCAS(slot, cur, key);
-        if (prev == cur) return;
-        cur = prev;
-    }
-}
-
 // One block per candidate: the FP64 terms of every community record (Eq. (9),
 // Sec. II-B.3) and of every contingency cell, column and row (Eqs. 1-7), all
 // lanes busy, summed in fixed point; then the final results.
@@ -1180,7 +1164,7 @@ __global__ void __launch_bounds__(BU_FIN_THREADS) k_bu_fin(const BatchItem *item
                 const long long nb = __ldcg(&S.start[cl.b + 1]) - __ldcg(&S.start[cl.b]);
                 acc.a11 += (unsigned long long)(n * (n - 1) / 2);
                 atomicMax(&S.rowmax_n[cl.a], (unsigned)n);
-                bu_rowmax_ratio(&S.rowmax_r[cl.a], (unsigned long long)n, (unsigned long long)(na + nb));
+                rowmax_ratio_update(&S.rowmax_r[cl.a], (unsigned long long)n, (unsigned long long)(na + nb));
                 const double l1 = cell_log(n, na, nb);
                 acc.vi += fp_from_double(vi_term_l(n, l1), SC_VI);
                 const bool tab = logt && n <= LOGT_MAX;
@@ -1198,14 +1182,7 @@ __global__ void __launch_bounds__(BU_FIN_THREADS) k_bu_fin(const BatchItem *item
             __threadfence();
             block_sync();  // this candidate's row maxima are complete
             for (int r = tid; r < x.ka; r += T) {
-                // the largest ratio's F term, formed once per row: rounding is
-                // monotone, so it is the largest of the cells' rounded ratios
-                const unsigned long long key = __ldcg(&S.rowmax_r[r]);
-                if (key) {
-                    const long long n = (long long)(key >> 32), d = (long long)(key & 0xFFFFFFFFull);
-                    const long long na = __ldcg(&S.size_a[r]);
-                    S.rowmax_r[r] = (unsigned long long)__double_as_longlong(f_ratio(n, na, d - na));
-                }
+                rowmax_ratio_settle(&S.rowmax_r[r], __ldcg(&S.size_a[r]));
                 compare_row(x, r, acc);
             }
             CompareTotals t;

@@ -1024,6 +1024,34 @@ __device__ __forceinline__ void terms_from_record(const unsigned long long *rc, 
     *cond_o = cond;
 }
 
+// Row maximum of the Eq. (3) ratio 2 n / (n_a + n_b) over a truth community's
+// cells, for the passes that form all cells before the rows: kept as the exact
+// fraction (n << 32 | n_a + n_b) of the largest n / (n_a + n_b), compared by
+// cross-multiplication (both below 2^31, so the products fit 64 bits), and
+// turned into the ratio's double once per row (rowmax_ratio_settle) instead of
+// dividing for every cell.  Rounding is monotone, so the largest correctly
+// rounded ratio is the rounded largest ratio: the same bits.
+__device__ __forceinline__ void rowmax_ratio_update(unsigned long long *slot, unsigned long long n,
+                                                    unsigned long long d)
+{
+    const unsigned long long key = (n << 32) | d;
+    unsigned long long cur = *(volatile unsigned long long *)slot;
+    while (cur == 0ull || n * (cur & 0xFFFFFFFFull) > (cur >> 32) * d) {
+        const unsigned long long prev = atomicCAS(slot, cur, key);
+        if (prev == cur) return;
+        cur = prev;
+    }
+}
+
+// The row's fraction (rowmax_ratio_update) as the bits of its f_ratio double.
+__device__ __forceinline__ void rowmax_ratio_settle(unsigned long long *slot, long long na)
+{
+    const unsigned long long key = __ldcg(slot);
+    if (!key) return;
+    const long long n = (long long)(key >> 32), d = (long long)(key & 0xFFFFFFFFull);
+    *slot = (unsigned long long)__double_as_longlong(f_ratio(n, na, d - na));
+}
+
 // Row side of the contingency table for truth community a (Eqs. 2-4).
 __device__ __forceinline__ void compare_row(const CompareCtx &x, int a, CompareAcc &acc)
 {

@@ -590,14 +590,17 @@ __global__ void k_compare_rows(CompareCtx x, unsigned long long *g, const int *s
     if (*status) return;
     CompareAcc acc;
     compare_acc_zero(acc);
-    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < x.ka; a += gridDim.x * blockDim.x)
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < x.ka; a += gridDim.x * blockDim.x) {
+        rowmax_ratio_settle(&x.rowmax_r[a], __ldcg(&x.size_a[a]));
         compare_row(x, a, acc);
+    }
     flush_compare(acc, g, red);
 }
 
 // Terms of every contingency cell (Eqs. 1-4), in parallel over the cell list:
 // the pair count, the VI and NMI-numerator terms, and the row maxima of the
-// F-measure and NVD (Eqs. 3-4) through atomicMax per truth community.
+// F-measure and NVD (Eqs. 3-4) per truth community (NVD's by atomicMax, F's as
+// an exact fraction that k_compare_rows turns into its ratio).
 __global__ void k_compare_cells(CompareCtx x, const Cell *cells, const int *counters, const int *size_b,
                                 unsigned long long *g, const int *status)
 {
@@ -612,7 +615,7 @@ __global__ void k_compare_cells(CompareCtx x, const Cell *cells, const int *coun
         const long long n = c.n, na = __ldg(&x.size_a[c.a]), nb = __ldg(&size_b[c.b]);
         acc.a11 += (unsigned long long)(n * (n - 1) / 2);
         atomicMax(&x.rowmax_n[c.a], (unsigned)n);
-        atomicMax(&x.rowmax_r[c.a], (unsigned long long)__double_as_longlong(f_ratio(n, na, nb)));
+        rowmax_ratio_update(&x.rowmax_r[c.a], (unsigned long long)n, (unsigned long long)(na + nb));
         const double l1 = cell_log(n, na, nb);
         acc.vi += fp_from_double(vi_term_l(n, l1), SC_VI);
         const bool tab = n <= LOGT_MAX;
