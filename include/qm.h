@@ -94,7 +94,10 @@ typedef struct qm_graph qm_graph; /* opaque; owns a device copy of the CSR */
  *            through the permutation on the device) and returns the same bits
  *            as without the flag; the gathers of neighbour labels then mostly
  *            hit nearby memory.  Costs one pass per round over the arcs and
- *            4 bytes per node, at load time only.
+ *            4 bytes per node, at load time only; above 2^24 nodes about 4.1
+ *            bytes per node more hold the index arrays that bring the
+ *            caller's labels into the stored order in two sequential passes
+ *            instead of one random gather (see qm_debug_set_perm_buckets).
  *   out      receives the handle; free it with qm_free_graph
  * The arrays are copied: the caller may free them when the call returns.  An
  * unweighted graph with fewer than 2^32 arcs also keeps its upper rows (the
@@ -352,6 +355,26 @@ qm_status qm_debug_set_stage_wait(int64_t polls);
  * Errors: QM_EINVAL for items < 0.
  */
 qm_status qm_debug_set_batch_wave(int32_t items);
+
+/*
+ * qm_debug_set_perm_buckets -- test hook for graphs loaded with QM_REORDER
+ * (no counterpart in the paper).  A scoring call on such a graph first brings
+ * the caller's labels into the stored order.  On graphs of more than
+ * min_nodes nodes (default 2^24) this takes two passes through shared memory,
+ * with sequential global reads and writes: labels are grouped per tile of
+ * 2^tile_bits caller ids by the window of 2^window_bits new ids they go to,
+ * then placed per window; shared memory holds the labels as 3 bytes while
+ * K <= 2^24.  By default windows and tiles hold 2^16 ids (tiles of 2^15 or
+ * 2^14 where the windows of a larger graph need the room).  Index arrays for
+ * this are built at load (4 bytes a node plus two ints per tile and window).
+ * Smaller graphs, graphs with more than 8192 windows, and calls whose labels
+ * do not fit the shared memory gather the labels directly.  The setting
+ * applies to graphs loaded afterwards (so that a test can drive the two
+ * passes on a small graph); results do not depend on it.  A negative
+ * argument restores its default (for the bits: the automatic choice).
+ * Errors: QM_EINVAL for window_bits or tile_bits of 0 or above 16.
+ */
+qm_status qm_debug_set_perm_buckets(int32_t window_bits, int32_t tile_bits, int64_t min_nodes);
 
 /*
  * Tuning.  qm_autotune times the candidate launch shapes of the scoring and

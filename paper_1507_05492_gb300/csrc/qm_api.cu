@@ -251,6 +251,17 @@ static std::mutex g_graph_mu;
 static std::map<GraphKey, cudaGraphExec_t> g_graphs;
 static std::atomic<int> g_batch_wave{0};  // qm_debug_set_batch_wave: wave size cap of the batched pipeline
 
+// Renumbered graphs of more than PB_MIN_NODES nodes permute the caller's labels
+// in two passes through shared memory (PermBuckets): tiles of 2^16 caller ids
+// and windows of 2^16 new ids (up to 4479 windows fit the shared memory of
+// pass 1), else tiles of 2^15, then 2^14.  Below that size the label array
+// mostly stays in L2 and the plain gather is cheaper.  A test may set the
+// sizes (qm_debug_set_perm_buckets; 0 = automatic).
+constexpr long long PB_MIN_NODES = 1LL << 24;
+static std::atomic<int> g_pb_wb{0};
+static std::atomic<int> g_pb_tb{0};
+static std::atomic<long long> g_pb_min_nodes{PB_MIN_NODES};
+
 // A captured CUDA graph of one plain scoring call on a small graph (see
 // score_impl), valid for the scratch blocks and the graph it was captured with.
 struct PlainKey {
@@ -339,6 +350,7 @@ struct qm_graph {
     float *wt = nullptr; // weighted graph: edge weights parallel to col (else null)
     long long *up_ptr = nullptr;  // unweighted graphs: upper rows (GraphDev::up_ptr)
     int *up_col = nullptr;
+    PermBuckets pb;               // QM_REORDER on large graphs: the labels' two-pass permutation
     long long n, n_arcs, max_degree;
     size_t bytes;
     std::mutex mu;
@@ -659,6 +671,30 @@ static qm_status load_impl(const int64_t *row_ptr, const int32_t *col, const flo
             g->d.wt = wt2;
         }
         g->bytes += (size_t)n_nodes * 4;
+        if (n_nodes > g_pb_min_nodes.load()) {
+            const int wb0 = g_pb_wb.load(), tb0 = g_pb_tb.load();
+            const int shapes[3][2] = {{16, 16}, {16, 15}, {16, 14}};
+            int r = 1;
+            for (int k = 0; k < 3 && r == 1; ++k) {
+                const int wb = wb0 ? wb0 : shapes[k][0], tb = tb0 ? tb0 : shapes[k][1];
+                r = build_perm_buckets(inv, n_nodes, wb, tb, num_sms_of(dev), s, &g->pb, &L);
+                if (r == -(int)cudaErrorMemoryAllocation) {
+                    cudaGetLastError();
+                    g_pool.trim();
+                    r = build_perm_buckets(inv, n_nodes, wb, tb, num_sms_of(dev), s, &g->pb, &L);
+                }
+                if (wb0 && tb0) break;
+            }
+            if (r < 0) {
+                cleanup();
+                cudaFree(g->inv);
+                return cuda_fail((cudaError_t)(-r), "label permutation buckets");
+            }
+            if (r == 0) {  // (1: the sizes do not fit the two passes; the labels are gathered directly)
+                g_launches += L;
+                g->bytes += g->pb.bytes;
+            }
+        }
     }
     if (!weight && n_arcs < (1LL << 32)) {
         // the upper rows, for gathering each undirected edge once (ALGO_HALF)
@@ -673,6 +709,7 @@ static qm_status load_impl(const int64_t *row_ptr, const int32_t *col, const flo
         if (r != 0) {
             cleanup();
             cudaFree(g->inv);
+            free_perm_buckets(&g->pb);
             return cuda_fail((cudaError_t)(-r), "upper rows");
         }
         g_launches += L;
@@ -708,6 +745,7 @@ qm_status qm_free_graph(qm_graph *g)
     cudaFree(g->wt);
     cudaFree(g->up_ptr);
     cudaFree(g->up_col);
+    free_perm_buckets(&g->pb);
     delete g;
     return QM_OK;
 }
@@ -733,6 +771,7 @@ qm_status qm_workspace_bytes(const qm_graph *g, int32_t K, int32_t with_compare,
                         score2_ws_bytes(g->n, g->n_arcs, K, wt, 0, packs_labels(1, wt, g->n, K))) +
                al256((size_t)g->n * 4);
     if (g->inv) b += al256((size_t)g->n * 4);
+    if (g->pb.lpos) b += al256((size_t)g->n * 4);
     if (with_compare) b += compare_ws_bytes(g->n, k_truth, K) + al256((size_t)g->n * 4);
     *bytes = b;
     return QM_OK;
@@ -764,6 +803,8 @@ static qm_status score_impl(qm_graph *g, const int32_t *labels, int32_t K, qm_me
     if (where == QM_HOST || graphed) need += al256((size_t)n * 4);
     const size_t perm_off = need;
     if (g->inv) need += al256((size_t)n * 4);
+    const size_t pb_off = need;
+    if (g->pb.lpos) need += al256((size_t)n * 4);
     const size_t pc_off = need;
     const bool pc_host = pc && where == QM_HOST;
     if (pc_host) need += al256((size_t)K * 8) * 8;
@@ -790,7 +831,16 @@ static qm_status score_impl(qm_graph *g, const int32_t *labels, int32_t K, qm_me
         bool sizes_ready = false;
         if (g->inv) {  // the graph is stored renumbered: gather the labels into its order
             int32_t *pl = (int32_t *)(ws.ptr() + perm_off);
-            if (sh.algo) {  // the two-phase pipeline takes the community sizes from the gather
+            // two passes through shared memory where the graph has them (the two-phase
+            // pipeline then takes the community sizes from the second), else one gather
+            const int lp = g->pb.lpos ? launch_permute_buckets(dl, g->pb, n, (int *)(ws.ptr() + pb_off), pl,
+                                                               sh.algo ? w.size : nullptr, K, w.status, nsm, st, tr)
+                                      : 0;
+            if (lp < 0) return -1;
+            if (lp > 0) {
+                sizes_ready = sh.algo != 0;
+                L += lp - 1;
+            } else if (sh.algo) {  // the two-phase pipeline takes the community sizes from the gather
                 if (tr) tr("k_permute_hist", st);
                 if (launch_permute_hist(dl, g->inv, n, pl, K, w, nsm, st) < 0) return -1;
                 sizes_ready = true;
@@ -1715,6 +1765,16 @@ qm_status qm_debug_set_batch_wave(int32_t items)
 {
     if (items < 0) return fail(QM_EINVAL, "items must be >= 0");
     g_batch_wave.store(items);
+    return QM_OK;
+}
+
+qm_status qm_debug_set_perm_buckets(int32_t window_bits, int32_t tile_bits, int64_t min_nodes)
+{
+    if (window_bits == 0 || window_bits > PB_MAX_BITS || tile_bits == 0 || tile_bits > PB_MAX_BITS)
+        return fail(QM_EINVAL, "window_bits and tile_bits must be in [1, 16]");
+    g_pb_wb.store(window_bits < 0 ? 0 : window_bits);
+    g_pb_tb.store(tile_bits < 0 ? 0 : tile_bits);
+    g_pb_min_nodes.store(min_nodes < 0 ? PB_MIN_NODES : (long long)min_nodes);
     return QM_OK;
 }
 

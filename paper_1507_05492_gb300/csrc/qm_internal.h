@@ -207,6 +207,35 @@ size_t scan_tmp_elems(long long n);
 int scan_offsets(const int *in, int n, int *out, int *tmp, int *counters, const int *status, cudaStream_t s);
 int launch_permute_labels(const int *labels, const int *inv, long long n, int P, int *out, int num_sms,
                           cudaStream_t s);
+// Bucketed label permutation of a renumbered graph (qm_reorder.cu): built
+// once at load, it turns the gather out[j] = labels[inv[j]] into two passes
+// with sequential global reads and writes (the random part in shared memory)
+// through a scratch array of n ints.  Caller ids are cut into tiles of 2^tb,
+// new ids into windows of 2^wb.
+constexpr int PB_MAX_BITS = 16;        // 16-bit positions inside tiles and windows
+constexpr int PB_MAX_WINDOWS = 8192;   // the build counts windows in shared memory
+struct PermBuckets {
+    unsigned short *lpos = nullptr;  // [n] caller id -> position in its tile's order (grouped by window)
+    unsigned short *dloc = nullptr;  // [n] slot -> new id inside its window
+    int *toff = nullptr;             // [ntiles][nw] first slot of each (tile, window) group
+    int *tlb = nullptr;              // [ntiles][nw + 1] first tile position of each group
+    int wb = 0, tb = 0, nw = 0, ntiles = 0;
+    size_t smem_max = 0;             // shared memory a block may take on the graph's device
+    size_t bytes = 0;
+};
+// Device arrays owned by the caller afterwards.  Returns 0, 1 when the sizes
+// do not fit the two passes (nothing built), or minus a CUDA error code
+// (nothing allocated then).
+int build_perm_buckets(const int *inv, long long n, int wb, int tb, int num_sms, cudaStream_t s, PermBuckets *out,
+                       int *launches);
+void free_perm_buckets(PermBuckets *pb);
+// out[j] = labels[inv[j]] by the two passes (tmp: n ints), labels outside
+// [0, K) flagged in bit 0 of *status; with `size`, also the community sizes,
+// as k_hist.  Returns launches, 0 when K is too large for the passes' shared
+// memory (nothing launched: gather the labels instead), or -1.
+int launch_permute_buckets(const int *labels, const PermBuckets &pb, long long n, int *tmp, int *out, int *size,
+                           int K, int *status, int num_sms, cudaStream_t s,
+                           void (*tr)(const char *, cudaStream_t) = nullptr);
 // Builds the renumbered CSR (row_ptr, col: new device allocations) and inv
 // (new id -> old id) of g from `rounds` label-propagation rounds.  Returns 0,
 // or minus a CUDA error code (nothing allocated then).

@@ -188,6 +188,8 @@ __device__ __forceinline__ void hist_add_warp(int *size, int l, unsigned act)
     if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&size[l], __popc(peers));
 }
 
+constexpr int HIST_UNROLL = 4;
+
 __global__ void k_hist(const int *__restrict__ a, int ka, int *size_a, const int *__restrict__ b,
                        int kb, int *size_b, long long n, int *status, int use_smem)
 {
@@ -198,28 +200,40 @@ __global__ void k_hist(const int *__restrict__ a, int ka, int *size_a, const int
     }
     bool bad = false;
     const int lane = threadIdx.x & 31;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < n; i0 += stride) {
-        const long long i = i0 + lane;
-        const bool in = i < n;
-        const int la = in ? __ldcs(&a[i]) : 0;
-        const bool oka = in && (unsigned)la < (unsigned)ka;
-        if (in && !oka) bad = true;
-        if (use_smem) {
-            if (oka) atomicAdd(&sh[la], 1);
-        } else {
-            const unsigned act = __ballot_sync(0xffffffffu, oka);
-            if (oka) hist_add_warp(size_a, la, act);
+    // each warp takes HIST_UNROLL * 32 consecutive labels a step, all loads
+    // issued before the first count
+    const long long wg = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long step = ((long long)gridDim.x * blockDim.x >> 5) * (32 * HIST_UNROLL);
+    for (long long i0 = wg * (32 * HIST_UNROLL); i0 < n; i0 += step) {
+        int va[HIST_UNROLL], vb[HIST_UNROLL];
+#pragma unroll
+        for (int q = 0; q < HIST_UNROLL; ++q) {
+            const long long i = i0 + q * 32 + lane;
+            va[q] = i < n ? __ldcs(&a[i]) : 0;
+            vb[q] = (b && i < n) ? __ldcs(&b[i]) : 0;
         }
-        if (b) {
-            const int lb = in ? __ldcs(&b[i]) : 0;
-            const bool okb = in && (unsigned)lb < (unsigned)kb;
-            if (in && !okb) bad = true;
+#pragma unroll
+        for (int q = 0; q < HIST_UNROLL; ++q) {
+            const bool in = i0 + q * 32 + lane < n;
+            const int la = va[q];
+            const bool oka = in && (unsigned)la < (unsigned)ka;
+            if (in && !oka) bad = true;
             if (use_smem) {
-                if (okb) atomicAdd(&sh[ka + lb], 1);
+                if (oka) atomicAdd(&sh[la], 1);
             } else {
-                const unsigned act = __ballot_sync(0xffffffffu, okb);
-                if (okb) hist_add_warp(size_b, lb, act);
+                const unsigned act = __ballot_sync(0xffffffffu, oka);
+                if (oka) hist_add_warp(size_a, la, act);
+            }
+            if (b) {
+                const int lb = vb[q];
+                const bool okb = in && (unsigned)lb < (unsigned)kb;
+                if (in && !okb) bad = true;
+                if (use_smem) {
+                    if (okb) atomicAdd(&sh[ka + lb], 1);
+                } else {
+                    const unsigned act = __ballot_sync(0xffffffffu, okb);
+                    if (okb) hist_add_warp(size_b, lb, act);
+                }
             }
         }
     }

@@ -98,6 +98,7 @@ def _signatures(lib):
         "qm_release_cache": [],
         "qm_debug_set_stage_wait": [_I64],
         "qm_debug_set_batch_wave": [_I32],
+        "qm_debug_set_perm_buckets": [_I32, _I32, _I64],
         "qm_score_cover": [_P, _P, _P, _I32, S, _P, _P],
         "qm_compare_covers": [_P, _P, _I32, _P, _P, _I32, _I64, S, _P, _P],
         "qm_autotune": [_P, _P, _I32, S, _P, _P],
@@ -587,6 +588,16 @@ def debug_set_batch_wave(items: int):
     """qm_debug_set_batch_wave: cap the batched pipeline's waves at `items`
     items for later calls (0: automatic).  A test hook for the wave loop."""
     _check(lib().qm_debug_set_batch_wave(int(items)), "qm_debug_set_batch_wave")
+
+
+def debug_set_perm_buckets(window_bits: int = -1, tile_bits: int = -1, min_nodes: int = -1):
+    """qm_debug_set_perm_buckets: graphs loaded with QM_REORDER afterwards
+    bring labels into their node order in two passes (tiles of 2**tile_bits
+    caller ids, windows of 2**window_bits new ids) when they have more than
+    min_nodes nodes (negative: the defaults, automatic bits and 2**24).  A test hook
+    for the two-pass permutation."""
+    _check(lib().qm_debug_set_perm_buckets(int(window_bits), int(tile_bits), int(min_nodes)),
+           "qm_debug_set_perm_buckets")
 
 
 def debug_set_stage_wait(polls: int):

@@ -101,3 +101,61 @@ def test_out_of_range_label_rejected(qm, setup, algo):
         qm.score(reord, bad.cuda(), K)
     assert qm.score(reord, labels.cuda(), K) == qm.score(plain, labels.cuda(), K)
 
+
+
+def bucketed_graph(qm, g, wb, tb):
+    """The graph loaded with QM_REORDER and the two-pass label permutation
+    forced on: tiles of 2**tb caller ids, windows of 2**wb new ids."""
+    qm.debug_set_perm_buckets(wb, tb, 0)
+    try:
+        return qm.Graph(*to_dev(g.row_ptr, g.col), reorder=True)
+    finally:
+        qm.debug_set_perm_buckets(-1, -1, -1)
+
+
+# 60,000 nodes: (10, 12) gives 59 windows and 15 tiles; (8, 2) 235 windows and
+# 15,000 tiles of 4 ids; (15, 16) two windows and one tile; (16, 16) (what
+# a graph of up to 293M nodes gets by default) one of each, too large for
+# 4-byte labels in shared memory, so that K > 2^24 gathers directly; (1, 15) would need 30,000 windows, more than the
+# passes take, so that graph always gathers its labels directly.
+@pytest.mark.parametrize("wb,tb,algos", [(10, 12, (1, 0, 4, 7)), (8, 2, (1, 0)), (15, 16, (1,)), (16, 16, (1, 0)),
+                                         (1, 15, (1,))])
+def test_two_pass_permutation_identical(qm, setup, oracle_mod, wb, tb, algos):
+    g, plain, reord, parts = setup
+    gb = bucketed_graph(qm, g, wb, tb)
+    nw, nt = -(-g.n // 2 ** wb), -(-g.n // 2 ** tb)
+    extra = 4 * g.n + 4 * nw * nt + 4 * nt * (nw + 1) if nw <= 8192 else 0
+    assert gb.info()["device_bytes"] == reord.info()["device_bytes"] + extra
+    # labels of 25 bits (shared memory holds them as 4 bytes, or they are gathered)
+    wide = (torch.where(g.labels % 2 == 1, g.labels + 2 ** 24, g.labels), 2 ** 24 + g.K)
+    for algo in algos:
+        for gr in (plain, gb):
+            qm.set_tuning(gr, wide[1], 512, 96 * 1024, 48, algo)
+        assert qm.score(plain, wide[0].cuda(), wide[1]) == qm.score(gb, wide[0].cuda(), wide[1]), algo
+        for labels, K in parts:
+            for gr in (plain, gb):
+                qm.set_tuning(gr, K, 512, 96 * 1024, 48, algo)
+            a = qm.score(plain, labels.cuda(), K, per_community=True)
+            b = qm.score(gb, labels.cuda(), K, per_community=True)
+            c = qm.score(gb, labels.numpy(), K)
+            pa, pb = a.pop("per_community"), b.pop("per_community")
+            assert a == b == c, (algo, K)
+            for key in pa:
+                assert torch.equal(pa[key].cpu(), pb[key].cpu()), (algo, key)
+    labels, K = parts[1]
+    o = oracle_mod.score(g.row_ptr.numpy(), g.col.numpy(), labels.numpy(), K)
+    check_quality(qm.score(gb, labels.cuda(), K), o, "two-pass permutation, perturbed")
+    bad = labels.clone()
+    bad[777] = -1                                    # a label below the range
+    for algo in algos:
+        qm.set_tuning(gb, K, 512, 96 * 1024, 48, algo)
+        with pytest.raises(RuntimeError):
+            qm.score(gb, bad.cuda(), K)
+    assert qm.score(gb, labels.cuda(), K) == qm.score(plain, labels.cuda(), K)
+
+
+def test_perm_bucket_hook_rejects_bad_bits(qm):
+    for wb, tb in ((0, 10), (17, 10), (10, 0), (10, 17)):
+        with pytest.raises(RuntimeError):
+            qm.debug_set_perm_buckets(wb, tb, 0)
+    qm.debug_set_perm_buckets(-1, -1, -1)
