@@ -641,6 +641,13 @@ __device__ __forceinline__ int ld_hint(const int *ptr, unsigned long long pol)
     return v;
 }
 
+// Largest load of a phase-B counting table: a run is given to a table that
+// it fills to at most COUNT_FILL_NUM / COUNT_FILL_DEN of its slots (beyond
+// that, the probe chains of linear probing grow, and a warp waits for its
+// longest).
+constexpr int COUNT_FILL_NUM = 3, COUNT_FILL_DEN = 4;
+__host__ __device__ constexpr long long count_fill(long long cap) { return cap * COUNT_FILL_NUM / COUNT_FILL_DEN; }
+
 // Epoch-tagged counting tables (phase B).  A group's table is reused for
 // community after community: every slot carries the epoch it was written in
 // and counts as empty unless that is the group's current epoch, so a new
@@ -742,6 +749,75 @@ struct EpochTable32 {
     }
 };
 
+// Four consecutive words of shared memory in one load, read afresh.
+__device__ __forceinline__ uint4 ld_shared_v4_volatile(const unsigned *p)
+{
+    uint4 v;
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ld.volatile.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(a));
+    return v;
+}
+
+// The words of EpochTable32, probed four slots at a time: a key's probe
+// sequence starts at the aligned group of four slots that holds
+// tab_hash(k, cap), and one 16-byte load reads a whole group, so the longest
+// chain of probes in a warp (which the warp waits for) is about a quarter as
+// long.  The table lives in shared memory, 16-byte aligned, with cap a
+// multiple of 4.
+struct EpochTable32V {
+    unsigned *key;   // [cap]
+    unsigned *rep;   // [cap], right after key
+    int cap;
+    int *overflow;
+
+    // a later occurrence of the key in slot h: its repeat count
+    __device__ __forceinline__ int repeat(unsigned h, unsigned epoch) const
+    {
+        unsigned w = ((volatile unsigned *)rep)[h];
+        for (int r = 0; r < 2 * cap + 64; ++r) {
+            const bool same = (w >> 24) == epoch;
+            const unsigned prev = atomicCAS(&rep[h], w, same ? w + 1u : ((epoch << 24) | 1u));
+            if (prev == w) return 1 + (same ? (int)(w & 0xFFFFFFu) : 0);
+            w = prev;
+        }
+        *overflow = 1;
+        return -1;
+    }
+
+    __device__ __forceinline__ int add(unsigned k, unsigned epoch) const
+    {
+        const unsigned tag = (epoch << 24) | (k + 1u);
+        unsigned g = tab_hash(k, cap) & ~3u;
+        const int limit = cap / 4 + 16;
+        for (int step = 0; step < limit; ++step) {
+            if (!QM_CHK(g + 3u, cap, 8)) return -1;
+            const uint4 w = ld_shared_v4_volatile(key + g);
+            const unsigned c4[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                unsigned cur = c4[s];
+                if (cur != tag && (cur >> 24) != epoch) {  // a slot free in this epoch: claim it
+                    cur = atomicCAS(&key[g + s], cur, tag);
+                    if (cur == c4[s]) return 0;
+                    // taken meanwhile (by this key, or another one)
+                }
+                if (cur == tag) return repeat(g + s, epoch);
+            }
+            if ((step & 3) == 3 && *(volatile int *)overflow) return -1;
+            g = (g + 4u >= (unsigned)cap) ? 0u : g + 4u;
+        }
+        *overflow = 1;
+        return -1;
+    }
+
+    __device__ __forceinline__ void wipe(int gtid, int gsize) const
+    {
+        for (int i = gtid; i < 2 * cap; i += gsize) key[i] = 0u;  // key and rep are contiguous
+    }
+};
+
 // Table over `cap` slots at `base` (8 bytes each).
 template <class TAB>
 __device__ __forceinline__ TAB make_table(unsigned long long *base, int cap, int *overflow);
@@ -754,6 +830,11 @@ template <>
 __device__ __forceinline__ EpochTable32 make_table<EpochTable32>(unsigned long long *base, int cap, int *overflow)
 {
     return EpochTable32{(unsigned *)base, (unsigned *)base + cap, cap, overflow};
+}
+template <>
+__device__ __forceinline__ EpochTable32V make_table<EpochTable32V>(unsigned long long *base, int cap, int *overflow)
+{
+    return EpochTable32V{(unsigned *)base, (unsigned *)base + cap, cap, overflow};
 }
 
 // Next epoch of a group (all its threads hold the same value); wipes the
@@ -867,7 +948,7 @@ __device__ __forceinline__ void count_run(const CountCtx &x, const RunHdr &h, co
                                           unsigned &epoch, int gtid, int gsize, unsigned long long *red)
 {
     const unsigned m = h.m;
-    const unsigned fill = (unsigned)(3 * tab.cap / 4);
+    const unsigned fill = (unsigned)count_fill(tab.cap);
     unsigned R = m <= fill ? 1u : (unsigned)min((unsigned long long)R_MAX, ((unsigned long long)m + fill - 1) / fill);
     const int c = h.c;
     for (;;) {

@@ -74,23 +74,24 @@ CountPlan plan_count(int T, int S)
     p.bar_off = off;
     off += 16;
     p.stage_off = off;
-    // 8 bytes per slot plus two staging buffers of 3/4 of the slots (4 bytes each, + 8 entries of slack)
+    // 8 bytes per slot plus two staging buffers of the largest load (4 bytes an
+    // entry, + 8 entries of slack)
     const int rest = S - off;
-    int cap = (rest - 2 * 4 * 12) / 14;
-    cap = (cap / W) * W;
+    int cap = (int)((long long)(rest - 2 * 4 * 12) * COUNT_FILL_DEN / (8 * COUNT_FILL_DEN + 8 * COUNT_FILL_NUM));
+    cap = (cap / (4 * W)) * (4 * W);  // the warps' and groups' tables: multiples of 4 slots (EpochTable32V)
     p.cap = cap;
-    p.fill = 3 * cap / 4;
+    p.fill = (int)count_fill(cap);
     p.stage_elems = (p.fill + 8 + 3) & ~3;
     off += 2 * p.stage_elems * 4;
     p.slot_off = off;
     off += cap * 8;
     p.cap_w = cap / W;
-    p.fill_w = 3 * p.cap_w / 4;
+    p.fill_w = (int)count_fill(p.cap_w);
     // four groups of W/4 warps, each with a quarter of the table, take the
     // runs between a warp's and the block's reach
     p.ng = (W >= 8 && W % 4 == 0) ? 4 : 1;
     p.cap_g = cap / p.ng;
-    p.fill_g = p.ng > 1 ? 3 * p.cap_g / 4 : p.fill_w;
+    p.fill_g = p.ng > 1 ? (int)count_fill(p.cap_g) : p.fill_w;
     p.bytes = off;
     return p;
 }
@@ -1332,9 +1333,9 @@ void prepare_kernels()
     cudaFuncSetAttribute(k_score_cm, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     cudaFuncSetAttribute(k_compare_cm, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     cudaFuncSetAttribute(k_count<EpochTable, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
-    cudaFuncSetAttribute(k_count<EpochTable32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+    cudaFuncSetAttribute(k_count<EpochTable32V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     cudaFuncSetAttribute(k_count<EpochTable, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
-    cudaFuncSetAttribute(k_count<EpochTable32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+    cudaFuncSetAttribute(k_count<EpochTable32V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     cudaFuncSetAttribute(k_count_long, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     cudaFuncSetAttribute(k_count_sort<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     cudaFuncSetAttribute(k_count_sort<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
@@ -1351,7 +1352,7 @@ void prepare_kernels()
 int count_blocks_per_sm(const Shape &sh)
 {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_count<EpochTable32, false>, sh.threads, sh.smem_bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_count<EpochTable32V, false>, sh.threads, sh.smem_bytes);
     return nb;
 }
 
@@ -1779,8 +1780,8 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
         else k_count_sort<false><<<count_grid, sh.threads, sh.smem_bytes, s>>>(sa);
     } else if (K < (1 << 24) - 1) {
         TRACE("k_count");
-        if (a.x.full) k_count<EpochTable32, true><<<count_grid, sh.threads, sh.smem_bytes, s>>>(a);
-        else k_count<EpochTable32, false><<<count_grid, sh.threads, sh.smem_bytes, s>>>(a);
+        if (a.x.full) k_count<EpochTable32V, true><<<count_grid, sh.threads, sh.smem_bytes, s>>>(a);
+        else k_count<EpochTable32V, false><<<count_grid, sh.threads, sh.smem_bytes, s>>>(a);
     } else {
         TRACE("k_count");
         if (a.x.full) k_count<EpochTable, true><<<count_grid, sh.threads, sh.smem_bytes, s>>>(a);
