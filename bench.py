@@ -47,7 +47,7 @@ FALLBACK_HBM = 6800.0
 # The translation unit that defines the kernels of the scoring step, with the
 # headers it includes; the DRAM records under profiles/ name its hash.
 STEP_SOURCES = ("qm_kernels.cu", "qm_community.cuh", "qm_device.cuh", "qm_finalize.cuh", "qm_expand.cuh",
-                "qm_binned.cuh", "qm_weighted.cuh", "qm_internal.h")
+                "qm_binned.cuh", "qm_weighted.cuh", "qm_internal.h", "qm_reorder.cu")
 
 
 def kernel_source_hash() -> str:

@@ -59,14 +59,40 @@ __device__ __forceinline__ int ld_label3(const unsigned long long *plab, int v, 
     return (int)((w >> (PACK_BITS * r)) & 0x1FFFFFull);
 }
 
+// Block encoding of the labels of a renumbered graph, for the far-end gathers
+// (built per call by k_pack_blocks).  Along the stored node order the labels
+// of a partition that follows the graph's clusters change rarely, so 16
+// consecutive nodes mostly carry one or two labels: one 64-bit word per 16
+// nodes holds labels A ([0, 21)) and B ([21, 42)) and a 16-bit mask ([42, 58))
+// whose bit i selects B for the block's node i.  A block of three or more
+// labels has bit 63 set and, in bits [0, 32), the offset (in 32-bit words from
+// the array's start) of its 16 labels in the exception area after the block
+// words.  Half a byte a node instead of the packed copy's 8/3, so that the
+// whole encoding of 10^8 nodes stays in L2.
+constexpr int BLK_NODES = 16;
+
+__device__ __forceinline__ int ld_label_blk(const unsigned long long *blab, int v, unsigned long long pol)
+{
+    unsigned long long w;
+    asm("ld.global.nc.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(w) : "l"(blab + ((unsigned)v >> 4)), "l"(pol));
+    const unsigned i = (unsigned)v & 15u;
+    if (!(w >> 63)) return (int)((w >> (((w >> (42u + i)) & 1ull) ? PACK_BITS : 0)) & 0x1FFFFFull);
+    return ld_hint((const int *)blab + ((unsigned)w + i), pol);
+}
+
+// Label sources of the far-end gathers: the labels as given, the packed copy,
+// or the block encoding.
+enum { LAB_PLAIN = 0, LAB_PACK3 = 1, LAB_BLOCKS = 2 };
+
 // Gathers the labels of arcs [e_lo, e_hi) of a run of community c (loc(e) is
-// the CSR index of arc e), counts those != c in inter[c] (the cut arcs of c)
+// the CSR index of arc e; plab is the packed copy or the block encoding, as
+// LAB says), counts those != c in inter[c] (the cut arcs of c)
 // and packs them into c's segment at cbase; with HI only the labels above c are
 // packed (each unordered pair of communities is counted by its smaller id), and
 // hi[c] counts them.  On a weighted graph (WT) the arc weights travel with the
 // packed labels (nbrw) and each lane sums the fixed-point weights of its intra
 // and cut arcs.
-template <bool WT, bool PACK, bool HI, class LOC>
+template <bool WT, int LAB, bool HI, class LOC>
 __device__ __forceinline__ void expand_range(unsigned e_lo, unsigned e_hi, int c, unsigned cbase, LOC loc,
                                              const int *__restrict__ col, const int *__restrict__ labels,
                                              const unsigned long long *__restrict__ plab,
@@ -86,7 +112,10 @@ __device__ __forceinline__ void expand_range(unsigned e_lo, unsigned e_hi, int c
         }
 #pragma unroll
         for (int k = 0; k < EXPAND_UNROLL; ++k)
-            if (lab[k] >= 0) lab[k] = PACK ? ld_label3(plab, lab[k], keep) : ld_hint(&labels[lab[k]], keep);
+            if (lab[k] >= 0)
+                lab[k] = LAB == LAB_BLOCKS  ? ld_label_blk(plab, lab[k], keep)
+                         : LAB == LAB_PACK3 ? ld_label3(plab, lab[k], keep)
+                                            : ld_hint(&labels[lab[k]], keep);
         if (WT) {
 #pragma unroll
             for (int k = 0; k < EXPAND_UNROLL; ++k)
@@ -137,7 +166,7 @@ __device__ __forceinline__ void flush_weights(unsigned long long *wl, int c, u12
 // end), their runs of one community each, and the gathers of those runs'
 // arcs.  offw (33 entries), rsw and cw (32 each) are the warp's shared-memory
 // slices.
-template <bool WT, bool PACK, bool HI>
+template <bool WT, int LAB, bool HI>
 __device__ __forceinline__ void expand_chunk(long long p0, long long n, const long long *__restrict__ row_ptr,
                                              const int *__restrict__ col, const int *__restrict__ labels,
                                              const unsigned long long *__restrict__ plab,
@@ -182,7 +211,7 @@ __device__ __forceinline__ void expand_chunk(long long p0, long long n, const lo
             }
             const long long cs = rsw[lo] - (long long)e_lo;  // CSR index of arc e is cs + e
             u128 w_in = 0, w_out = 0;
-            expand_range<WT, PACK, HI>(e_lo, e_hi, c, cbase, [cs](unsigned e) { return cs + (long long)e; }, col,
+            expand_range<WT, LAB, HI>(e_lo, e_hi, c, cbase, [cs](unsigned e) { return cs + (long long)e; }, col,
                                        labels, plab, inter, inter_hi, nbr, keep, lane, wt, nbrw, w_in, w_out);
             if (WT) flush_weights(wl, c, w_in, w_out, lane);
         }
@@ -198,7 +227,7 @@ __device__ __forceinline__ void expand_chunk(long long p0, long long n, const lo
             if (lane == 0) cbase = __ldg(&aoff[__ldg(&start[c])]);
             cbase = __shfl_sync(0xffffffffu, cbase, 0);
             u128 w_in = 0, w_out = 0;
-            expand_range<WT, PACK, HI>(
+            expand_range<WT, LAB, HI>(
                 e_lo, e_hi, c, cbase,
                 [=](unsigned e) {
                     const int o = m_lo + upper_bound_smem(offw + m_lo, m_hi - m_lo, e) - 1;

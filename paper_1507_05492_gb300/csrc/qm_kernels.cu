@@ -23,7 +23,7 @@ namespace qm {
 using namespace qmk;
 
 enum { C_BIG_COUNT = 0, C_BIG_NEXT = 1, C_SMALL_NEXT = 2, C_OVF_COUNT = 3, C_OVF_NEXT = 4, C_SMALL_COUNT = 5,
-       C_LONG_COUNT = 6, C_NCELLS = 7, C_MID_COUNT = 8 };
+       C_LONG_COUNT = 6, C_NCELLS = 7, C_MID_COUNT = 8, C_BX_COUNT = 9, C_BX_BAD = 10 };
 
 constexpr int SCAN_TILE = 4096;   // elements per block in the multi-block scan
 constexpr int SCAN_SINGLE_MAX = 1 << 16;
@@ -775,11 +775,12 @@ __global__ void k_scatter_deg(const int *__restrict__ labels, const long long *_
 }
 
 // The packed label copy read by the far-end gathers (PACK_BITS-bit ids, three
-// to a word; see qm_expand.cuh).
+// to a word; see qm_expand.cuh).  After k_pack_blocks (bx_bad set) only when
+// the block encoding did not fit.
 __global__ void k_pack3(const int *__restrict__ labels, long long n, unsigned long long *__restrict__ plab,
-                        const int *status)
+                        const int *status, const int *bx_bad)
 {
-    if (*status) return;
+    if (*status || (bx_bad && !*bx_bad)) return;
     const long long words = (n + 2) / 3;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < words;
          t += (long long)gridDim.x * blockDim.x) {
@@ -791,10 +792,84 @@ __global__ void k_pack3(const int *__restrict__ labels, long long n, unsigned lo
     }
 }
 
-// Phase A (the far-end label gathers) lives in qm_expand.cuh: expand_chunk is one
-// warp's share of it.
+// The block encoding of the labels (ld_label_blk in qm_expand.cuh) in the
+// buffer of the packed copy, which is larger: a half-warp per block of 16
+// nodes, each warp taking PACKB_UNROLL pairs of blocks a step with all their
+// loads issued first.  Blocks of three or more labels take exception slots
+// (one atomic per warp and block pair; the order is whatever the atomics give)
+// while fewer than xcap are taken; a warp that finds them gone sets *bad and
+// stops (as does every later one that needs a slot), and the packed copy
+// replaces the encoding.
+constexpr int PACKB_UNROLL = 4;
 
-template <bool WT, bool PACK, bool HI>
+__global__ void k_pack_blocks(const int *__restrict__ labels, long long n, unsigned long long *__restrict__ blab,
+                              long long xcap, int *xcount, int *bad, const int *status)
+{
+    if (*status) return;
+    const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
+    const unsigned hmask = 0xFFFFu << (16 * half);
+    const long long nb = (n + BLK_NODES - 1) / BLK_NODES;
+    const unsigned xbase = (unsigned)(2 * nb);  // first word of the exception area
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    for (long long b0 = wg * 2 * PACKB_UNROLL; b0 < nb; b0 += 2 * PACKB_UNROLL * nwarps) {
+        int lv[PACKB_UNROLL];
+#pragma unroll
+        for (int q = 0; q < PACKB_UNROLL; ++q) {
+            const long long i = (b0 + 2 * q + half) * BLK_NODES + hl;
+            lv[q] = i < n ? __ldcs(&labels[i]) : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < PACKB_UNROLL; ++q) {
+            const long long b = b0 + 2 * q + half;
+            const bool inb = b < nb, real = inb && b * BLK_NODES + hl < n;
+            int l = lv[q];
+            const int A = __shfl_sync(0xffffffffu, l, 16 * half);
+            if (!real) l = A;  // nodes past the end take the block's first label
+            const unsigned notA = __ballot_sync(0xffffffffu, l != A) & hmask;
+            const int B = __shfl_sync(0xffffffffu, l, notA ? __ffs(notA) - 1 : 16 * half);
+            const bool exc = (__ballot_sync(0xffffffffu, l != A && l != B) & hmask) != 0;
+            const unsigned isB = (__ballot_sync(0xffffffffu, l == B && B != A) & hmask) >> (16 * half);
+            const unsigned need = __ballot_sync(0xffffffffu, hl == 0 && inb && exc);
+            int x0 = 0;
+            if (lane == 0 && need) x0 = atomicAdd(xcount, __popc(need));
+            x0 = __shfl_sync(0xffffffffu, x0, 0);
+            if (need && x0 >= xcap) {  // the slots ran out (here or in another warp): give up the encoding
+                if (lane == 0) atomicExch(bad, 1);
+                return;
+            }
+            const int x = x0 + __popc(need & ((1u << (16 * half)) - 1u));
+            unsigned long long word;
+            if (!exc) {
+                word = (unsigned long long)(A & 0x1FFFFF) | ((unsigned long long)(B & 0x1FFFFF) << PACK_BITS) |
+                       ((unsigned long long)isB << 42);
+            } else {
+                if (x < xcap) {
+                    if (inb) ((int *)blab)[xbase + (unsigned)x * BLK_NODES + hl] = l;
+                } else if (hl == 0 && inb) {
+                    atomicExch(bad, 1);
+                }
+                word = (1ull << 63) | (unsigned long long)(xbase + (unsigned)min((long long)x, xcap) * BLK_NODES);
+            }
+            if (inb && hl == 0) blab[b] = word;
+        }
+    }
+}
+
+// Exception slots of the block encoding: a sixteenth of the blocks, and what
+// the packed copy's buffer leaves after the block words.
+static long long blocks_xcap(long long n)
+{
+    const long long nb = (n + BLK_NODES - 1) / BLK_NODES, words = (n + 2) / 3;
+    return std::max(0LL, std::min(nb / 16, (2 * words - 2 * nb) / BLK_NODES));
+}
+
+// Phase A (the far-end label gathers) lives in qm_expand.cuh: expand_chunk is one
+// warp's share of it.  LAB is the label source of the gathers; with bx_bad (the
+// block encoding was tried) the LAB_BLOCKS launch runs when it fits and the
+// LAB_PACK3 launch when it does not.
+
+template <bool WT, int LAB, bool HI>
 __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__restrict__ row_ptr,
                                                            const int *__restrict__ col,
                                                            const int *__restrict__ labels,
@@ -805,17 +880,19 @@ __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__re
                                                            int *inter, int *inter_hi, int *__restrict__ nbr,
                                                            const int *status,
                                                            Shard own, const float *__restrict__ wt,
-                                                           float *__restrict__ nbrw, unsigned long long *wl)
+                                                           float *__restrict__ nbrw, unsigned long long *wl,
+                                                           const int *bx_bad = nullptr)
 {
     __shared__ unsigned offs_s[EXPAND_THREADS / 32][33];
     __shared__ long long rs_s[EXPAND_THREADS / 32][32];
     __shared__ int cw_s[EXPAND_THREADS / 32][32];
     if (*status) return;
+    if (bx_bad && (LAB == LAB_BLOCKS) == (*bx_bad != 0)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned long long keep = l2_policy_evict_last();
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
     for (long long p0 = ((long long)blockIdx.x * (blockDim.x >> 5) + w) * 32; p0 < n; p0 += nwarps * 32)
-        expand_chunk<WT, PACK, HI>(p0, n, row_ptr, col, labels, plab, members, aoff, start, inter, inter_hi, nbr,
+        expand_chunk<WT, LAB, HI>(p0, n, row_ptr, col, labels, plab, members, aoff, start, inter, inter_hi, nbr,
                                    own, wt, nbrw, wl, offs_s[w], rs_s[w], cw_s[w], keep, lane);
 }
 
@@ -1643,7 +1720,7 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
                             ws.counters, ws.scan_tmp, ws.status, s, tr);
     if (g.wt) {
         TRACE("k_expand");
-        k_expand<true, false, false><<<expand_grid(n, num_sms), EXPAND_THREADS, 0, s>>>(g.row_ptr, g.col, labels, nullptr, ws.members, ws.aoff,
+        k_expand<true, LAB_PLAIN, false><<<expand_grid(n, num_sms), EXPAND_THREADS, 0, s>>>(g.row_ptr, g.col, labels, nullptr, ws.members, ws.aoff,
                                                               ws.start, n, ws.inter, nullptr, ws.nbr, ws.status, own, g.wt,
                                                               ws.nbrw, ws.wl);
         ++launches;
@@ -1662,7 +1739,7 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
         ++launches;
         if (ws.plab) {
             TRACE("k_pack3");
-            k_pack3<<<grid_for((n + 2) / 3, 256, num_sms, 8), 256, 0, s>>>(labels, n, ws.plab, ws.status);
+            k_pack3<<<grid_for((n + 2) / 3, 256, num_sms, 8), 256, 0, s>>>(labels, n, ws.plab, ws.status, nullptr);
             ++launches;
         }
         TRACE("k_expand_half");
@@ -1705,26 +1782,51 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
         // counted by its smaller id only, so only the labels above c are packed
         const bool hi = !(pc && pc->qds);
         const dim3 eg(expand_grid(n, num_sms)), eb(EXPAND_THREADS);
+        // on a renumbered graph the block encoding is tried first (the packed
+        // copy, in the same buffer, only when it does not fit)
+        const bool blocks = ws.plab && g.inv;
+        int *const bx_bad = blocks ? &ws.counters[C_BX_BAD] : nullptr;
+        if (blocks) {
+            TRACE("k_pack_blocks");
+            const long long nb = (n + BLK_NODES - 1) / BLK_NODES;
+            k_pack_blocks<<<grid_for((nb + 2 * PACKB_UNROLL - 1) / (2 * PACKB_UNROLL) * 32, 256, num_sms, 8), 256, 0,
+                            s>>>(
+                labels, n, ws.plab, blocks_xcap(n), &ws.counters[C_BX_COUNT], bx_bad, ws.status);
+            ++launches;
+        }
         if (ws.plab) {
             TRACE("k_pack3");
-            k_pack3<<<grid_for((n + 2) / 3, 256, num_sms, 8), 256, 0, s>>>(labels, n, ws.plab, ws.status);
+            k_pack3<<<grid_for((n + 2) / 3, 256, num_sms, 8), 256, 0, s>>>(labels, n, ws.plab, ws.status, bx_bad);
             ++launches;
         }
         TRACE("k_expand");
+        if (blocks) {
+            if (hi)
+                k_expand<false, LAB_BLOCKS, true><<<eg, eb, 0, s>>>(g.row_ptr, g.col, labels, ws.plab, ws.members,
+                                                                    ws.aoff, ws.start, n, ws.inter, ws.inter_hi,
+                                                                    ws.nbr, ws.status, own, nullptr, nullptr,
+                                                                    nullptr, bx_bad);
+            else
+                k_expand<false, LAB_BLOCKS, false><<<eg, eb, 0, s>>>(g.row_ptr, g.col, labels, ws.plab, ws.members,
+                                                                     ws.aoff, ws.start, n, ws.inter, nullptr, ws.nbr,
+                                                                     ws.status, own, nullptr, nullptr, nullptr,
+                                                                     bx_bad);
+            ++launches;
+        }
         if (ws.plab && hi)
-            k_expand<false, true, true><<<eg, eb, 0, s>>>(g.row_ptr, g.col, labels, ws.plab, ws.members, ws.aoff,
-                                                          ws.start, n, ws.inter, ws.inter_hi, ws.nbr, ws.status, own,
-                                                          nullptr, nullptr, nullptr);
+            k_expand<false, LAB_PACK3, true><<<eg, eb, 0, s>>>(g.row_ptr, g.col, labels, ws.plab, ws.members,
+                                                               ws.aoff, ws.start, n, ws.inter, ws.inter_hi, ws.nbr,
+                                                               ws.status, own, nullptr, nullptr, nullptr, bx_bad);
         else if (ws.plab)
-            k_expand<false, true, false><<<eg, eb, 0, s>>>(g.row_ptr, g.col, labels, ws.plab, ws.members, ws.aoff,
-                                                           ws.start, n, ws.inter, nullptr, ws.nbr, ws.status, own,
-                                                           nullptr, nullptr, nullptr);
+            k_expand<false, LAB_PACK3, false><<<eg, eb, 0, s>>>(g.row_ptr, g.col, labels, ws.plab, ws.members,
+                                                                ws.aoff, ws.start, n, ws.inter, nullptr, ws.nbr,
+                                                                ws.status, own, nullptr, nullptr, nullptr, bx_bad);
         else if (hi)
-            k_expand<false, false, true><<<eg, eb, 0, s>>>(g.row_ptr, g.col, labels, nullptr, ws.members, ws.aoff,
+            k_expand<false, LAB_PLAIN, true><<<eg, eb, 0, s>>>(g.row_ptr, g.col, labels, nullptr, ws.members, ws.aoff,
                                                            ws.start, n, ws.inter, ws.inter_hi, ws.nbr, ws.status,
                                                            own, nullptr, nullptr, nullptr);
         else
-            k_expand<false, false, false><<<eg, eb, 0, s>>>(g.row_ptr, g.col, labels, nullptr, ws.members,
+            k_expand<false, LAB_PLAIN, false><<<eg, eb, 0, s>>>(g.row_ptr, g.col, labels, nullptr, ws.members,
                                                             ws.aoff, ws.start, n, ws.inter, nullptr, ws.nbr,
                                                             ws.status, own, nullptr, nullptr, nullptr);
         ++launches;

@@ -31,6 +31,7 @@ def setup(qm):
     rng = np.random.default_rng(21)
     parts = [(g.labels, g.K),
              (gen.perturb(g.labels, g.K, 0.3, seed=3), g.K),
+             (gen.perturb(g.labels, g.K, 0.002, seed=5), g.K),  # a few blocks of three labels
              (torch.from_numpy(rng.integers(0, 500, g.n).astype(np.int32)), 500),
              (torch.arange(g.n, dtype=torch.int32), g.n),
              (torch.zeros(g.n, dtype=torch.int32), 1)]
