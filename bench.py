@@ -44,8 +44,9 @@ PROFILE_DIR = os.path.join(ROOT, "profiles")
 FALLBACK_HBM = 6800.0
 
 
-# The translation unit that defines the kernels of the scoring step, with the
-# headers it includes; the DRAM records under profiles/ name its hash.
+# The translation units that define the kernels of the scoring step (the label
+# permutation of renumbered graphs included), with the headers they include;
+# the DRAM records under profiles/ name their hash.
 STEP_SOURCES = ("qm_kernels.cu", "qm_community.cuh", "qm_device.cuh", "qm_finalize.cuh", "qm_expand.cuh",
                 "qm_binned.cuh", "qm_weighted.cuh", "qm_internal.h", "qm_reorder.cu")
 

@@ -400,7 +400,12 @@ qm_status qm_debug_set_perm_buckets(int32_t window_bits, int32_t tile_bits, int6
  *   4  as 1, with the far-end labels always gathered from a copy packed three
  *      21-bit ids to a 64-bit word (8/3 bytes a node instead of 4, so a larger
  *      share of it stays in L2); algorithm 1 does this on graphs of more than
- *      2^22 nodes;
+ *      2^22 nodes.  On a graph loaded with QM_REORDER the gathers first try a
+ *      block encoding built per call (per 16 consecutive nodes two labels and
+ *      a 16-bit mask, blocks of three or more labels apart: half a byte a
+ *      node when the partition follows the stored order, so that it stays in
+ *      L2), falling back to the packed copy when too many blocks hold three
+ *      or more labels; algorithm 1 does this above 2^26 nodes;
  *   5  as 1, never packed;
  *   6  as 1, but the second kernel sorts each community's segment by label
  *      (a radix sort in shared memory, 8-bit digits) and counts the equal-label

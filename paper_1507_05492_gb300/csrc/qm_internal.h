@@ -153,6 +153,13 @@ constexpr long long PACK_MIN_NODES = 1LL << 22;
 // Whether a two-phase call gathers from the packed copy: algorithm 4 always,
 // algorithms 1, ALGO_SORT and ALGO_HALF on graphs above PACK_MIN_NODES;
 // unweighted graphs and label ids below 2^21 only.
+// Renumbered graphs of more nodes than this gather from the block encoding of
+// the labels (qm_expand.cuh) instead of the packed copy (tuning algorithm 4:
+// at any size): below it the packed copy mostly stays in L2 already and the
+// encoding's pass and decode cost more than they save.
+constexpr long long BLOCKS_MIN_NODES = 1LL << 26;
+inline bool label_blocks(int algo, long long n) { return algo == 4 || n > BLOCKS_MIN_NODES; }
+
 inline bool packs_labels(int algo, bool weighted, long long n, int K)
 {
     return !weighted && K <= (1 << 21) &&

@@ -1782,9 +1782,10 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
         // counted by its smaller id only, so only the labels above c are packed
         const bool hi = !(pc && pc->qds);
         const dim3 eg(expand_grid(n, num_sms)), eb(EXPAND_THREADS);
-        // on a renumbered graph the block encoding is tried first (the packed
-        // copy, in the same buffer, only when it does not fit)
-        const bool blocks = ws.plab && g.inv;
+        // on a renumbered graph above BLOCKS_MIN_NODES nodes (any size with
+        // algorithm 4) the block encoding is tried first (the packed copy, in
+        // the same buffer, only when it does not fit)
+        const bool blocks = ws.plab && g.inv && label_blocks(sh.algo, n);
         int *const bx_bad = blocks ? &ws.counters[C_BX_BAD] : nullptr;
         if (blocks) {
             TRACE("k_pack_blocks");

@@ -8,7 +8,9 @@
 // of the gathered labels neighbours in memory.  The clusters come from the
 // graph alone (a few synchronous label-propagation rounds, never from a
 // partition being scored), the renumbering is done once when the graph is
-// loaded, and each scoring call gathers its labels through the permutation.
+// loaded, and each scoring call brings its labels into the stored order (a
+// gather through the permutation, or on large graphs the two passes through
+// shared memory at the end of this file).
 // Every metric is invariant under renumbering and summed exactly, so the
 // results are bit-identical with and without the reorder.
 #include <algorithm>
