@@ -870,7 +870,7 @@ static long long blocks_xcap(long long n)
 // LAB_PACK3 launch when it does not.
 
 template <bool WT, int LAB, bool HI>
-__global__ void __launch_bounds__(EXPAND_THREADS) k_expand(const long long *__restrict__ row_ptr,
+__global__ void __launch_bounds__(EXPAND_THREADS, 6) k_expand(const long long *__restrict__ row_ptr,
                                                            const int *__restrict__ col,
                                                            const int *__restrict__ labels,
                                                            const unsigned long long *__restrict__ plab,
@@ -1651,10 +1651,26 @@ static int community_grid(long long K, int num_sms, const Shape &sh)
 
 // k_expand: 8 blocks per SM, or fewer when the graph has fewer member chunks
 // (32 member positions per warp, EXPAND_THREADS / 32 warps per block).
-static int expand_grid(long long n, int num_sms)
+// k_expand: one wave of resident blocks (each takes an equal grid-stride
+// share, so blocks of a second wave would start late and end the kernel late),
+// or fewer when the graph has fewer member chunks.
+static int expand_grid(long long n, int num_sms, int per_sm = 8)
 {
     const long long per_block = 32LL * (EXPAND_THREADS / 32);
-    return (int)std::max<long long>(1, std::min<long long>((long long)num_sms * 8, (n + per_block - 1) / per_block));
+    return (int)std::max<long long>(1,
+                                    std::min<long long>((long long)num_sms * per_sm, (n + per_block - 1) / per_block));
+}
+
+template <bool WT, int LAB, bool HI>
+static int expand_per_sm()
+{
+    static std::atomic<int> v{0};
+    if (!v.load()) {
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_expand<WT, LAB, HI>, EXPAND_THREADS, 0);
+        v.store(std::max(1, std::min(nb, 8)));
+    }
+    return v.load();
 }
 
 // Weighted graphs after k_expand<true>: one block per community counts and
@@ -1803,31 +1819,38 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
         TRACE("k_expand");
         if (blocks) {
             if (hi)
-                k_expand<false, LAB_BLOCKS, true><<<eg, eb, 0, s>>>(g.row_ptr, g.col, labels, ws.plab, ws.members,
+                k_expand<false, LAB_BLOCKS, true><<<expand_grid(n, num_sms, expand_per_sm<false, LAB_BLOCKS, true>()),
+                                                    eb, 0, s>>>(g.row_ptr, g.col, labels, ws.plab, ws.members,
                                                                     ws.aoff, ws.start, n, ws.inter, ws.inter_hi,
                                                                     ws.nbr, ws.status, own, nullptr, nullptr,
                                                                     nullptr, bx_bad);
             else
-                k_expand<false, LAB_BLOCKS, false><<<eg, eb, 0, s>>>(g.row_ptr, g.col, labels, ws.plab, ws.members,
+                k_expand<false, LAB_BLOCKS, false><<<expand_grid(n, num_sms,
+                                                                 expand_per_sm<false, LAB_BLOCKS, false>()),
+                                                     eb, 0, s>>>(g.row_ptr, g.col, labels, ws.plab, ws.members,
                                                                      ws.aoff, ws.start, n, ws.inter, nullptr, ws.nbr,
                                                                      ws.status, own, nullptr, nullptr, nullptr,
                                                                      bx_bad);
             ++launches;
         }
         if (ws.plab && hi)
-            k_expand<false, LAB_PACK3, true><<<eg, eb, 0, s>>>(g.row_ptr, g.col, labels, ws.plab, ws.members,
+            k_expand<false, LAB_PACK3, true><<<expand_grid(n, num_sms, expand_per_sm<false, LAB_PACK3, true>()), eb,
+                                               0, s>>>(g.row_ptr, g.col, labels, ws.plab, ws.members,
                                                                ws.aoff, ws.start, n, ws.inter, ws.inter_hi, ws.nbr,
                                                                ws.status, own, nullptr, nullptr, nullptr, bx_bad);
         else if (ws.plab)
-            k_expand<false, LAB_PACK3, false><<<eg, eb, 0, s>>>(g.row_ptr, g.col, labels, ws.plab, ws.members,
+            k_expand<false, LAB_PACK3, false><<<expand_grid(n, num_sms, expand_per_sm<false, LAB_PACK3, false>()), eb,
+                                                0, s>>>(g.row_ptr, g.col, labels, ws.plab, ws.members,
                                                                 ws.aoff, ws.start, n, ws.inter, nullptr, ws.nbr,
                                                                 ws.status, own, nullptr, nullptr, nullptr, bx_bad);
         else if (hi)
-            k_expand<false, LAB_PLAIN, true><<<eg, eb, 0, s>>>(g.row_ptr, g.col, labels, nullptr, ws.members, ws.aoff,
+            k_expand<false, LAB_PLAIN, true><<<expand_grid(n, num_sms, expand_per_sm<false, LAB_PLAIN, true>()), eb,
+                                               0, s>>>(g.row_ptr, g.col, labels, nullptr, ws.members, ws.aoff,
                                                            ws.start, n, ws.inter, ws.inter_hi, ws.nbr, ws.status,
                                                            own, nullptr, nullptr, nullptr);
         else
-            k_expand<false, LAB_PLAIN, false><<<eg, eb, 0, s>>>(g.row_ptr, g.col, labels, nullptr, ws.members,
+            k_expand<false, LAB_PLAIN, false><<<expand_grid(n, num_sms, expand_per_sm<false, LAB_PLAIN, false>()), eb,
+                                                0, s>>>(g.row_ptr, g.col, labels, nullptr, ws.members,
                                                             ws.aoff, ws.start, n, ws.inter, nullptr, ws.nbr,
                                                             ws.status, own, nullptr, nullptr, nullptr);
         ++launches;
