@@ -867,10 +867,12 @@ static long long blocks_xcap(long long n)
 // Phase A (the far-end label gathers) lives in qm_expand.cuh: expand_chunk is one
 // warp's share of it.  LAB is the label source of the gathers; with bx_bad (the
 // block encoding was tried) the LAB_BLOCKS launch runs when it fits and the
-// LAB_PACK3 launch when it does not.
+// LAB_PACK3 launch when it does not.  Register budgets: 40 for the block
+// encoding (six resident blocks; its gathers hit L2 and wait on latency), 48
+// for the others (64 with weights).
 
 template <bool WT, int LAB, bool HI>
-__global__ void __launch_bounds__(EXPAND_THREADS, 6) k_expand(const long long *__restrict__ row_ptr,
+__global__ void __launch_bounds__(EXPAND_THREADS, LAB == LAB_BLOCKS ? 6 : WT ? 4 : 5) k_expand(const long long *__restrict__ row_ptr,
                                                            const int *__restrict__ col,
                                                            const int *__restrict__ labels,
                                                            const unsigned long long *__restrict__ plab,
@@ -1651,9 +1653,12 @@ static int community_grid(long long K, int num_sms, const Shape &sh)
 
 // k_expand: 8 blocks per SM, or fewer when the graph has fewer member chunks
 // (32 member positions per warp, EXPAND_THREADS / 32 warps per block).
-// k_expand: one wave of resident blocks (each takes an equal grid-stride
-// share, so blocks of a second wave would start late and end the kernel late),
-// or fewer when the graph has fewer member chunks.
+// k_expand: per_sm blocks per SM, or fewer when the graph has fewer member
+// chunks.  The gathers from the block encoding (L2-resident, bound by latency)
+// take one wave of resident blocks: each block has an equal grid-stride share,
+// so blocks of a second wave would start late and end the kernel late.  The
+// DRAM-bound gathers from the packed copy keep 8 blocks per SM (measured
+// faster there).
 static int expand_grid(long long n, int num_sms, int per_sm = 8)
 {
     const long long per_block = 32LL * (EXPAND_THREADS / 32);
@@ -1834,23 +1839,19 @@ int launch_score2(const GraphDev &g, const int *labels, int K, const ScoreWs &ws
             ++launches;
         }
         if (ws.plab && hi)
-            k_expand<false, LAB_PACK3, true><<<expand_grid(n, num_sms, expand_per_sm<false, LAB_PACK3, true>()), eb,
-                                               0, s>>>(g.row_ptr, g.col, labels, ws.plab, ws.members,
+            k_expand<false, LAB_PACK3, true><<<eg, eb, 0, s>>>(g.row_ptr, g.col, labels, ws.plab, ws.members,
                                                                ws.aoff, ws.start, n, ws.inter, ws.inter_hi, ws.nbr,
                                                                ws.status, own, nullptr, nullptr, nullptr, bx_bad);
         else if (ws.plab)
-            k_expand<false, LAB_PACK3, false><<<expand_grid(n, num_sms, expand_per_sm<false, LAB_PACK3, false>()), eb,
-                                                0, s>>>(g.row_ptr, g.col, labels, ws.plab, ws.members,
+            k_expand<false, LAB_PACK3, false><<<eg, eb, 0, s>>>(g.row_ptr, g.col, labels, ws.plab, ws.members,
                                                                 ws.aoff, ws.start, n, ws.inter, nullptr, ws.nbr,
                                                                 ws.status, own, nullptr, nullptr, nullptr, bx_bad);
         else if (hi)
-            k_expand<false, LAB_PLAIN, true><<<expand_grid(n, num_sms, expand_per_sm<false, LAB_PLAIN, true>()), eb,
-                                               0, s>>>(g.row_ptr, g.col, labels, nullptr, ws.members, ws.aoff,
+            k_expand<false, LAB_PLAIN, true><<<eg, eb, 0, s>>>(g.row_ptr, g.col, labels, nullptr, ws.members, ws.aoff,
                                                            ws.start, n, ws.inter, ws.inter_hi, ws.nbr, ws.status,
                                                            own, nullptr, nullptr, nullptr);
         else
-            k_expand<false, LAB_PLAIN, false><<<expand_grid(n, num_sms, expand_per_sm<false, LAB_PLAIN, false>()), eb,
-                                                0, s>>>(g.row_ptr, g.col, labels, nullptr, ws.members,
+            k_expand<false, LAB_PLAIN, false><<<eg, eb, 0, s>>>(g.row_ptr, g.col, labels, nullptr, ws.members,
                                                             ws.aoff, ws.start, n, ws.inter, nullptr, ws.nbr,
                                                             ws.status, own, nullptr, nullptr, nullptr);
         ++launches;
