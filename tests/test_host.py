@@ -67,6 +67,12 @@ def test_host_argument_checks_without_gpu(libpath):
         == qm.QM_EINVAL
     assert l.qm_load_graph(rp.ctypes.data, col.ctypes.data, 1 << 31, 2, qm.QM_HOST, 0, None, ctypes.byref(h)) \
         == qm.QM_EOVERFLOW
+    # the test hooks check their arguments on the host too
+    for wb, tb in ((0, 10), (17, 10), (10, 0), (10, 17)):
+        assert l.qm_debug_set_perm_buckets(wb, tb, 0) == qm.QM_EINVAL, (wb, tb)
+    assert l.qm_debug_set_perm_buckets(-1, -1, -1) == qm.QM_OK
+    assert l.qm_debug_set_batch_wave(-1) == qm.QM_EINVAL
+    assert l.qm_debug_set_batch_wave(0) == qm.QM_OK
 
 
 # ------------------------------------------------------------------ generator
